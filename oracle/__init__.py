@@ -1,0 +1,256 @@
+"""ctypes view of the FP64 CPU oracle (dvm_oracle.c).
+
+TEST INFRASTRUCTURE ONLY.  The oracle is the slow, obviously correct CPU
+statement of the DVM Boltzmann step (paper Sec. 2.1, Sec. 3, Eqs. 1-6, the BGK
+form of Sec. 4).  Only tests/, __graft_entry__.smoke() and bench.py's
+cpu_baseline / reference leg may import it; the product package never does.
+
+Parity status of each function is recorded in the design notes; every
+function here is pinned by a -m "not gpu" test under tests/test_oracle_*.py.
+"""
+import ctypes as C
+import numpy as np
+
+from . import build as _build
+
+BC_PERIODIC, BC_INFLOW, BC_OUTFLOW, BC_WALL = 0, 1, 2, 3
+PRED_NONE, PRED_BALL, PRED_SHELL = 0, 1, 2
+COLL_NONE, COLL_BGK, COLL_HS = 0, 1, 2
+
+
+class TreeSpec(C.Structure):
+    _fields_ = [("dim", C.c_int), ("base_level", C.c_int), ("max_level", C.c_int),
+                ("pred", C.c_int), ("c", C.c_double * 3), ("r", C.c_double),
+                ("beta", C.c_double), ("solid", C.c_int), ("bc", C.c_int * 6)]
+
+
+def make_spec(dim, base_level, max_level, pred=PRED_NONE, c=(0.5, 0.5, 0.5),
+              r=0.0, beta=0.0, solid=0, bc=(0,) * 6):
+    s = TreeSpec()
+    s.dim, s.base_level, s.max_level, s.pred = dim, base_level, max_level, pred
+    for d in range(3):
+        s.c[d] = c[d]
+    s.r, s.beta, s.solid = r, beta, int(solid)
+    for q in range(6):
+        s.bc[q] = bc[q]
+    return s
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = C.CDLL(path)
+        P = C.c_void_p
+        d_p = C.POINTER(C.c_double)
+        i64 = C.c_int64
+        L.orc_splitmix64.restype = C.c_uint64
+        L.orc_splitmix64.argtypes = [C.c_uint64, C.c_uint64]
+        L.orc_vgrid_size.restype = i64
+        L.orc_vgrid.argtypes = [P, P, P, P, P, P]
+        L.orc_build_tree.argtypes = [C.POINTER(TreeSpec), i64, C.POINTER(i64), P, P, P]
+        L.orc_create.restype = P
+        L.orc_create.argtypes = [C.POINTER(TreeSpec), P, P, P]
+        L.orc_destroy.argtypes = [P]
+        for nm in ("orc_nleaves", "orc_ncells", "orc_nv", "orc_n_faces", "orc_n_bfaces", "orc_hs_nkept"):
+            getattr(L, nm).restype = i64
+            getattr(L, nm).argtypes = [P]
+        L.orc_get_leaves.argtypes = [P, P, P, P]
+        L.orc_cell_centres.argtypes = [P, P, P]
+        L.orc_get_faces.argtypes = [P, P, P, P, P]
+        L.orc_get_bfaces.argtypes = [P, P, P, P, P, P, P]
+        L.orc_set_freestream.argtypes = [P, C.c_double, P, C.c_double]
+        L.orc_init_maxwellian.argtypes = [P, C.c_int, P, P, P, P]
+        L.orc_get_f.argtypes = [P, P]
+        L.orc_set_f.argtypes = [P, P]
+        L.orc_dt_cfl.restype = C.c_double
+        L.orc_dt_cfl.argtypes = [P, C.c_double]
+        L.orc_transport.argtypes = [P, C.c_double]
+        L.orc_moments.argtypes = [P, P, P, P]
+        L.orc_totals.argtypes = [P, P]
+        L.orc_bgk.argtypes = [P, C.c_double, C.c_double, P]
+        L.orc_hs_tables.argtypes = [P, C.c_int, C.c_uint64]
+        L.orc_hs_get_tables.argtypes = [P, P, P, P, P, P, P]
+        L.orc_hs_collide.argtypes = [P, C.c_double, C.c_double, P, P, P]
+        L.orc_step.argtypes = [P, C.c_int, C.c_double, C.c_int, C.c_double]
+        L.orc_solve.argtypes = [C.c_int, P, P, P]
+        _lib = L
+    return _lib
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data
+
+
+def splitmix64(seed, n):
+    return int(lib().orc_splitmix64(seed, n))
+
+
+def vgrid(n, lo, hi):
+    n = np.asarray(n, dtype=np.int32)
+    lo = np.asarray(lo, dtype=np.float64)
+    hi = np.asarray(hi, dtype=np.float64)
+    nv = int(np.prod(n.astype(np.int64)))
+    xi = np.zeros((nv, 3))
+    k = np.zeros((nv, 3), dtype=np.int32)
+    dV = np.zeros(1)
+    if lib().orc_vgrid(_p(n), _p(lo), _p(hi), _p(xi), _p(k), _p(dV)):
+        raise ValueError("bad velocity grid")
+    return xi, k, float(dV[0])
+
+
+def build_tree(spec):
+    n = C.c_int64(0)
+    rc = lib().orc_build_tree(C.byref(spec), 0, C.byref(n), None, None, None)
+    if rc:
+        raise ValueError("tree build failed %d" % rc)
+    keys = np.zeros(n.value, dtype=np.uint64)
+    lev = np.zeros(n.value, dtype=np.uint8)
+    sol = np.zeros(n.value, dtype=np.uint8)
+    rc = lib().orc_build_tree(C.byref(spec), n.value, C.byref(n), _p(keys), _p(lev), _p(sol))
+    if rc:
+        raise ValueError("tree build failed %d" % rc)
+    return keys, lev, sol
+
+
+def solve(A, b):
+    A = np.array(A, dtype=np.float64, order="C")
+    b = np.array(b, dtype=np.float64)
+    x = np.zeros_like(b)
+    if lib().orc_solve(len(b), _p(A), _p(b), _p(x)):
+        raise np.linalg.LinAlgError("singular")
+    return x
+
+
+class Problem:
+    """One tree + velocity grid + state, all in FP64 on the host."""
+
+    def __init__(self, spec, n, lo, hi):
+        self.spec = spec
+        n = np.asarray(n, dtype=np.int32)
+        lo = np.asarray(lo, dtype=np.float64)
+        hi = np.asarray(hi, dtype=np.float64)
+        self._h = lib().orc_create(C.byref(spec), _p(n), _p(lo), _p(hi))
+        if not self._h:
+            raise ValueError("oracle problem creation failed")
+        self.nleaves = lib().orc_nleaves(self._h)
+        self.ncells = lib().orc_ncells(self._h)
+        self.nv = lib().orc_nv(self._h)
+        self.xi, self.k, self.dV = vgrid(n, lo, hi)
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h and _lib is not None:
+            _lib.orc_destroy(h)
+            self._h = None
+
+    def leaves(self):
+        keys = np.zeros(self.nleaves, dtype=np.uint64)
+        lev = np.zeros(self.nleaves, dtype=np.uint8)
+        sol = np.zeros(self.nleaves, dtype=np.uint8)
+        lib().orc_get_leaves(self._h, _p(keys), _p(lev), _p(sol))
+        return keys, lev, sol
+
+    def centres(self):
+        xyz = np.zeros((self.ncells, 3))
+        h = np.zeros(self.ncells)
+        lib().orc_cell_centres(self._h, _p(xyz), _p(h))
+        return xyz, h
+
+    def faces(self):
+        nf = lib().orc_n_faces(self._h)
+        m = np.zeros(nf, dtype=np.int64)
+        p = np.zeros(nf, dtype=np.int64)
+        ax = np.zeros(nf, dtype=np.uint8)
+        ar = np.zeros(nf)
+        lib().orc_get_faces(self._h, _p(m), _p(p), _p(ax), _p(ar))
+        return m, p, ax, ar
+
+    def bfaces(self):
+        nb = lib().orc_n_bfaces(self._h)
+        leaf = np.zeros(nb, dtype=np.int64)
+        ax = np.zeros(nb, dtype=np.uint8)
+        side = np.zeros(nb, dtype=np.uint8)
+        kind = np.zeros(nb, dtype=np.uint8)
+        other = np.zeros(nb, dtype=np.int64)
+        ar = np.zeros(nb)
+        lib().orc_get_bfaces(self._h, _p(leaf), _p(ax), _p(side), _p(kind), _p(other), _p(ar))
+        return leaf, ax, side, kind, other, ar
+
+    def set_freestream(self, rho, u, T):
+        u = np.asarray(u, dtype=np.float64)
+        lib().orc_set_freestream(self._h, rho, _p(u), T)
+
+    def init_maxwellian(self, w, rho, u, T):
+        """w, rho, T: [ncells, nmix]; u: [ncells, nmix, 3]."""
+        w = np.ascontiguousarray(np.asarray(w, dtype=np.float64).reshape(self.ncells, -1))
+        nmix = w.shape[1]
+        rho = np.ascontiguousarray(np.asarray(rho, dtype=np.float64).reshape(self.ncells, nmix))
+        u = np.ascontiguousarray(np.asarray(u, dtype=np.float64).reshape(self.ncells, nmix, 3))
+        T = np.ascontiguousarray(np.asarray(T, dtype=np.float64).reshape(self.ncells, nmix))
+        lib().orc_init_maxwellian(self._h, nmix, _p(w), _p(rho), _p(u), _p(T))
+
+    def get_f(self):
+        f = np.zeros((self.ncells, self.nv))
+        lib().orc_get_f(self._h, _p(f))
+        return f
+
+    def set_f(self, f):
+        f = np.ascontiguousarray(f, dtype=np.float64).reshape(self.ncells, self.nv)
+        lib().orc_set_f(self._h, _p(f))
+
+    def dt_cfl(self, cfl):
+        return lib().orc_dt_cfl(self._h, cfl)
+
+    def transport(self, dt):
+        if lib().orc_transport(self._h, dt):
+            raise RuntimeError("transport failed")
+
+    def moments(self):
+        rho = np.zeros(self.ncells)
+        u = np.zeros((self.ncells, 3))
+        T = np.zeros(self.ncells)
+        lib().orc_moments(self._h, _p(rho), _p(u), _p(T))
+        return rho, u, T
+
+    def totals(self):
+        out = np.zeros(5)
+        lib().orc_totals(self._h, _p(out))
+        return out
+
+    def bgk(self, dt, kn, want_q=False):
+        q = np.zeros((self.ncells, self.nv)) if want_q else None
+        if lib().orc_bgk(self._h, dt, kn, _p(q)):
+            raise RuntimeError("BGK failed (non-positive moments or singular system)")
+        return q
+
+    def hs_tables(self, trials, seed):
+        lib().orc_hs_tables(self._h, trials, seed)
+
+    def hs_get_tables(self):
+        nk = lib().orc_hs_nkept(self._h)
+        start = np.zeros(self.nv + 1, dtype=np.int64)
+        gam = np.zeros(nk, dtype=np.int32)
+        l = np.zeros(nk, dtype=np.int32)
+        m = np.zeros(nk, dtype=np.int32)
+        b = np.zeros(nk)
+        disc = np.zeros(1, dtype=np.int64)
+        if lib().orc_hs_get_tables(self._h, _p(start), _p(gam), _p(l), _p(m), _p(b), _p(disc)):
+            raise RuntimeError("no tables")
+        return start, gam, l, m, b, int(disc[0])
+
+    def hs_collide(self, dt, kn, want=False):
+        q = np.zeros((self.ncells, self.nv)) if want else None
+        B = np.zeros((self.ncells, self.nv)) if want else None
+        Cc = np.zeros((self.ncells, self.nv)) if want else None
+        if lib().orc_hs_collide(self._h, dt, kn, _p(q), _p(B), _p(Cc)):
+            raise RuntimeError("hard-sphere collision failed")
+        return q, B, Cc
+
+    def step(self, nsteps, dt, coll, kn):
+        rc = lib().orc_step(self._h, nsteps, dt, coll, kn)
+        if rc:
+            raise RuntimeError("oracle step failed %d" % rc)

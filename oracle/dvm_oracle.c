@@ -1,0 +1,985 @@
+/*
+ * FP64 CPU oracle for the explicit DVM Boltzmann step on a quad/octree.
+ *
+ * TEST INFRASTRUCTURE ONLY: loaded by the tests, the smoke check and the
+ * CPU-baseline leg of the benchmark, never by the product path.  It shares
+ * no code with the CUDA library.
+ *
+ * Paper: Zabelok, Arslanbekov, Kolobov, "Adaptive Kinetic-Fluid Solvers for
+ * Heterogeneous Computing Architectures".
+ *   - tree mesh, 2:1 balance for direct and diagonal neighbours ... Sec. 2.1
+ *   - Morton (N-order) ordering of the leaves ...................... Sec. 2.1
+ *   - discrete velocities at cell centres of a uniform grid ........ Sec. 3
+ *   - finite-volume advection ........................... Sec. 3.1, Eq. 2
+ *   - 8 sign groups of velocity points, stored contiguously ........ Sec. 3.1
+ *   - discrete collision integral, B, C, conservative correction Eqs. 3-6
+ *   - BGK relaxation form ........................................... Sec. 4
+ * Where the paper leaves a choice open, the reading used here is the one
+ * listed with the library's design notes (first-order upwind fluxes,
+ * CFL definition, Lie splitting, seeded hard-sphere trials, the DVM-BGK
+ * collision frequency, boundary kinds).
+ */
+#include "dvm_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#ifndef M_PI
+#define M_PI 3.14159265358979323846
+#endif
+
+typedef struct {
+    int lev;
+    int32_t i[3];      /* integer box coordinates at the box's own level */
+    uint64_t key;      /* Morton key of the anchor at the deepest level  */
+    uint8_t solid;
+} leaf_t;
+
+struct orc_problem {
+    orc_tree_spec spec;
+    int L;
+    int64_t nleaves;
+    leaf_t *lv;
+    int64_t ncells;
+    int64_t *cell_of_leaf;
+    int64_t *leaf_of_cell;
+    /* interior faces */
+    int64_t nf;
+    int64_t *fm, *fp;
+    uint8_t *fax;
+    double *farea;
+    /* boundary faces */
+    int64_t nbf;
+    int64_t *bl, *bother;
+    uint8_t *bax, *bside, *bkind;
+    double *barea;
+    /* velocity grid */
+    int n[3];
+    double lo[3], hi[3], h[3], dV;
+    int64_t nv;
+    double *xi;
+    int32_t *k;
+    int64_t *mirror[3];
+    /* state */
+    double *f;
+    double fs_rho, fs_u[3], fs_T;
+    double *finf;
+    /* hard-sphere tables (CSR over nodes) */
+    int hs_trials;
+    int64_t hs_nkept;
+    int64_t *hs_start;
+    int32_t *hs_gam, *hs_l, *hs_m;
+    double *hs_b;
+    int64_t hs_discarded;
+};
+
+/* ------------------------------------------------------------------------ */
+/* SplitMix64 (Steele, Lea, Flood 2014): output n of the stream whose state
+ * starts at `seed` and advances by the golden-ratio increment each draw.   */
+uint64_t orc_splitmix64(uint64_t seed, uint64_t n)
+{
+    uint64_t z = seed + (n + 1u) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+static double unif53(uint64_t seed, uint64_t n)
+{
+    return (double)(orc_splitmix64(seed, n) >> 11) * 0x1.0p-53;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Velocity grid.  Nodes are cell centres of a uniform grid (Sec. 3):
+ * xi_d(k) = lo_d + (k + 1/2) h_d with h_d = (hi_d - lo_d)/n_d.  The nodes are
+ * grouped by the signs of their three components (Sec. 3.1 step 1): group
+ * o = 4[xi_x>0] + 2[xi_y>0] + [xi_z>0], so group 0 is (-,-,-) and group 1 is
+ * (-,-,+).  Inside a group the nodes are ordered lexicographically by the
+ * distance index m_d (m_d = 0 nearest to zero), z fastest. */
+int64_t orc_vgrid_size(const int n[3])
+{
+    return (int64_t)n[0] * n[1] * n[2];
+}
+
+static int axis_index(int n, int positive, int m)
+{
+    return positive ? n / 2 + m : n / 2 - 1 - m;
+}
+
+int orc_vgrid(const int n[3], const double lo[3], const double hi[3],
+              double *xi, int32_t *k, double *dV)
+{
+    for (int d = 0; d < 3; d++)
+        if (n[d] <= 0 || n[d] % 2 != 0 || !(hi[d] > lo[d])) return -1;
+    double h[3];
+    for (int d = 0; d < 3; d++) h[d] = (hi[d] - lo[d]) / n[d];
+    int half[3] = {n[0] / 2, n[1] / 2, n[2] / 2};
+    int64_t v = 0;
+    for (int o = 0; o < 8; o++) {
+        int pos[3] = {(o >> 2) & 1, (o >> 1) & 1, o & 1};
+        for (int mx = 0; mx < half[0]; mx++)
+            for (int my = 0; my < half[1]; my++)
+                for (int mz = 0; mz < half[2]; mz++) {
+                    int kk[3] = {axis_index(n[0], pos[0], mx),
+                                 axis_index(n[1], pos[1], my),
+                                 axis_index(n[2], pos[2], mz)};
+                    for (int d = 0; d < 3; d++) {
+                        if (xi) xi[3 * v + d] = lo[d] + ((double)kk[d] + 0.5) * h[d];
+                        if (k) k[3 * v + d] = kk[d];
+                    }
+                    v++;
+                }
+    }
+    if (dV) *dV = h[0] * h[1] * h[2];
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Tree (Sec. 2.1): boxes obtained by repeated halving; leaves are cells.    */
+
+static uint64_t morton(int dim, int L, const int32_t a[3])
+{
+    uint64_t key = 0;
+    for (int b = 0; b < L; b++)
+        for (int d = 0; d < dim; d++)
+            key |= (uint64_t)((a[d] >> b) & 1) << (dim * b + d);
+    return key;
+}
+
+static void set_key(leaf_t *x, int dim, int L)
+{
+    int32_t a[3] = {0, 0, 0};
+    for (int d = 0; d < dim; d++) a[d] = x->i[d] << (L - x->lev);
+    x->key = morton(dim, L, a);
+}
+
+static int periodic_axis(const orc_tree_spec *s, int d)
+{
+    return s->bc[2 * d] == ORC_BC_PERIODIC;
+}
+
+/* squared distance from point c to the box, and to its farthest point */
+static double box_dmin2(const orc_tree_spec *s, int lev, const int32_t i[3])
+{
+    double h = ldexp(1.0, -lev), d2 = 0.0;
+    for (int d = 0; d < s->dim; d++) {
+        double lo = i[d] * h, hi = (i[d] + 1) * h, t = 0.0;
+        if (s->c[d] < lo) t = lo - s->c[d];
+        else if (s->c[d] > hi) t = s->c[d] - hi;
+        d2 += t * t;
+    }
+    return d2;
+}
+
+static double box_dmax2(const orc_tree_spec *s, int lev, const int32_t i[3])
+{
+    double h = ldexp(1.0, -lev), d2 = 0.0;
+    for (int d = 0; d < s->dim; d++) {
+        double a = fabs(i[d] * h - s->c[d]), b = fabs((i[d] + 1) * h - s->c[d]);
+        double t = a > b ? a : b;
+        d2 += t * t;
+    }
+    return d2;
+}
+
+static int refine_pred(const orc_tree_spec *s, const leaf_t *x)
+{
+    if (x->lev >= s->max_level) return 0;
+    if (s->pred == ORC_PRED_BALL) {
+        return box_dmin2(s, x->lev, x->i) <= s->r * s->r;
+    }
+    if (s->pred == ORC_PRED_SHELL) {
+        double h = ldexp(1.0, -x->lev);
+        double rp = s->r + s->beta * h, rm = s->r - s->beta * h;
+        if (!(box_dmin2(s, x->lev, x->i) <= rp * rp)) return 0;
+        return rm <= 0.0 || box_dmax2(s, x->lev, x->i) >= rm * rm;
+    }
+    return 0;
+}
+
+static int is_solid(const orc_tree_spec *s, const leaf_t *x)
+{
+    if (!s->solid) return 0;
+    double h = ldexp(1.0, -x->lev), d2 = 0.0;
+    for (int d = 0; d < s->dim; d++) {
+        double t = (x->i[d] + 0.5) * h - s->c[d];
+        d2 += t * t;
+    }
+    return d2 < s->r * s->r;
+}
+
+static int cmp_leaf(const void *a, const void *b)
+{
+    uint64_t x = ((const leaf_t *)a)->key, y = ((const leaf_t *)b)->key;
+    return x < y ? -1 : x > y;
+}
+
+/* index of the leaf containing the deepest-level cell with Morton key `key`:
+ * the last leaf whose anchor key is <= key (leaves cover contiguous key
+ * ranges in Morton order). */
+static int64_t locate(const leaf_t *lv, int64_t n, uint64_t key)
+{
+    int64_t lo = 0, hi = n - 1, ans = -1;
+    while (lo <= hi) {
+        int64_t mid = lo + (hi - lo) / 2;
+        if (lv[mid].key <= key) { ans = mid; lo = mid + 1; }
+        else hi = mid - 1;
+    }
+    return ans;
+}
+
+static int64_t locate_cell(const leaf_t *lv, int64_t n, int dim, int L,
+                           int lev, const int32_t c[3])
+{
+    int32_t a[3] = {0, 0, 0};
+    for (int d = 0; d < dim; d++) a[d] = c[d] << (L - lev);
+    return locate(lv, n, morton(dim, L, a));
+}
+
+typedef struct { leaf_t *v; int64_t n, cap; } leafvec;
+
+static int push(leafvec *lv, leaf_t x)
+{
+    if (lv->n == lv->cap) {
+        int64_t nc = lv->cap ? 2 * lv->cap : 1024;
+        leaf_t *nv = (leaf_t *)realloc(lv->v, (size_t)nc * sizeof(leaf_t));
+        if (!nv) return -1;
+        lv->v = nv;
+        lv->cap = nc;
+    }
+    lv->v[lv->n++] = x;
+    return 0;
+}
+
+static int push_children(leafvec *out, const leaf_t *x, int dim, int L)
+{
+    int nch = 1 << dim;
+    for (int c = 0; c < nch; c++) {
+        leaf_t y;
+        memset(&y, 0, sizeof y);
+        y.lev = x->lev + 1;
+        for (int d = 0; d < dim; d++) y.i[d] = 2 * x->i[d] + ((c >> d) & 1);
+        set_key(&y, dim, L);
+        if (push(out, y)) return -1;
+    }
+    return 0;
+}
+
+/* 1 if some leaf touching x (across a face, edge or corner, periodic sides
+ * wrapped) is more than one level finer than x. */
+static int violates_balance(const orc_tree_spec *s, int L, const leaf_t *lv,
+                            int64_t n, const leaf_t *x)
+{
+    int dim = s->dim, lev = x->lev + 2;
+    if (lev > L) return 0;
+    int32_t N = (int32_t)1 << lev;
+    int lo3 = dim == 3 ? -1 : 0, hi3 = dim == 3 ? 4 : 0;
+    for (int oz = lo3; oz <= hi3; oz++)
+        for (int oy = -1; oy <= 4; oy++)
+            for (int ox = -1; ox <= 4; ox++) {
+                int off[3] = {ox, oy, oz};
+                int inside = 1;
+                for (int d = 0; d < dim; d++)
+                    if (off[d] < 0 || off[d] > 3) inside = 0;
+                if (inside) continue;
+                int32_t c[3] = {0, 0, 0};
+                int ok = 1;
+                for (int d = 0; d < dim; d++) {
+                    c[d] = 4 * x->i[d] + off[d];
+                    if (c[d] < 0 || c[d] >= N) {
+                        if (periodic_axis(s, d)) c[d] = (c[d] + N) % N;
+                        else ok = 0;
+                    }
+                }
+                if (!ok) continue;
+                int64_t b = locate_cell(lv, n, dim, L, lev, c);
+                if (b >= 0 && lv[b].lev >= lev) return 1;
+            }
+    return 0;
+}
+
+static int check_spec(const orc_tree_spec *s)
+{
+    if (s->dim != 2 && s->dim != 3) return -1;
+    if (s->base_level < 1 || s->max_level < s->base_level) return -1;
+    if (s->max_level * s->dim > 63) return -1;
+    for (int d = 0; d < s->dim; d++)
+        if ((s->bc[2 * d] == ORC_BC_PERIODIC) != (s->bc[2 * d + 1] == ORC_BC_PERIODIC))
+            return -1;
+    return 0;
+}
+
+static int build_tree(const orc_tree_spec *s, leafvec *out)
+{
+    int dim = s->dim, L = s->max_level;
+    leafvec cur = {0, 0, 0};
+    int32_t N = (int32_t)1 << s->base_level;
+    int32_t nz = dim == 3 ? N : 1;
+    for (int32_t z = 0; z < nz; z++)
+        for (int32_t y = 0; y < N; y++)
+            for (int32_t x = 0; x < N; x++) {
+                leaf_t t;
+                memset(&t, 0, sizeof t);
+                t.lev = s->base_level;
+                t.i[0] = x; t.i[1] = y; t.i[2] = z;
+                set_key(&t, dim, L);
+                if (push(&cur, t)) return -1;
+            }
+    /* refinement by the predicate, to a fixpoint */
+    for (;;) {
+        leafvec nxt = {0, 0, 0};
+        int changed = 0;
+        for (int64_t a = 0; a < cur.n; a++) {
+            if (refine_pred(s, &cur.v[a])) {
+                if (push_children(&nxt, &cur.v[a], dim, L)) return -1;
+                changed = 1;
+            } else if (push(&nxt, cur.v[a])) return -1;
+        }
+        free(cur.v);
+        cur = nxt;
+        if (!changed) break;
+    }
+    /* 2:1 balance for direct and diagonal neighbours, to a fixpoint */
+    for (;;) {
+        qsort(cur.v, (size_t)cur.n, sizeof(leaf_t), cmp_leaf);
+        char *mark = (char *)calloc((size_t)cur.n, 1);
+        int64_t nmark = 0;
+        for (int64_t a = 0; a < cur.n; a++)
+            if (violates_balance(s, L, cur.v, cur.n, &cur.v[a])) { mark[a] = 1; nmark++; }
+        if (nmark == 0) { free(mark); break; }
+        leafvec nxt = {0, 0, 0};
+        for (int64_t a = 0; a < cur.n; a++) {
+            if (mark[a]) { if (push_children(&nxt, &cur.v[a], dim, L)) return -1; }
+            else if (push(&nxt, cur.v[a])) return -1;
+        }
+        free(mark);
+        free(cur.v);
+        cur = nxt;
+    }
+    for (int64_t a = 0; a < cur.n; a++) cur.v[a].solid = (uint8_t)is_solid(s, &cur.v[a]);
+    *out = cur;
+    return 0;
+}
+
+int orc_build_tree(const orc_tree_spec *spec, int64_t cap, int64_t *n,
+                   uint64_t *keys, uint8_t *levels, uint8_t *solid)
+{
+    if (check_spec(spec)) return -1;
+    leafvec t;
+    if (build_tree(spec, &t)) return -2;
+    *n = t.n;
+    if (t.n > cap) { free(t.v); return cap == 0 ? 0 : -3; }
+    for (int64_t a = 0; a < t.n; a++) {
+        if (keys) keys[a] = t.v[a].key;
+        if (levels) levels[a] = (uint8_t)t.v[a].lev;
+        if (solid) solid[a] = t.v[a].solid;
+    }
+    free(t.v);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Faces.  One interior face per fine subface between two fluid leaves,
+ * recorded from its minus side; boundary faces on the domain sides and
+ * towards solid leaves.  Area = (edge of the finer box)^(dim-1).            */
+
+typedef struct { int64_t m, p; uint8_t ax; double area; uint64_t km, kp; } iface_t;
+typedef struct { int64_t l, o; uint8_t ax, side, kind; double area; uint64_t kl, ko; } bface_t;
+
+static int cmp_iface(const void *a, const void *b)
+{
+    const iface_t *x = (const iface_t *)a, *y = (const iface_t *)b;
+    if (x->ax != y->ax) return x->ax < y->ax ? -1 : 1;
+    if (x->km != y->km) return x->km < y->km ? -1 : 1;
+    if (x->kp != y->kp) return x->kp < y->kp ? -1 : 1;
+    return 0;
+}
+
+static int cmp_bface(const void *a, const void *b)
+{
+    const bface_t *x = (const bface_t *)a, *y = (const bface_t *)b;
+    if (x->kind != y->kind) return x->kind < y->kind ? -1 : 1;
+    if (x->ax != y->ax) return x->ax < y->ax ? -1 : 1;
+    if (x->side != y->side) return x->side < y->side ? -1 : 1;
+    if (x->kl != y->kl) return x->kl < y->kl ? -1 : 1;
+    if (x->ko != y->ko) return x->ko < y->ko ? -1 : 1;
+    return 0;
+}
+
+static int build_faces(orc_problem *p)
+{
+    const orc_tree_spec *s = &p->spec;
+    int dim = s->dim, L = p->L;
+    int64_t icap = 1024, bcap = 1024, ni = 0, nb = 0;
+    iface_t *fi = (iface_t *)malloc((size_t)icap * sizeof(iface_t));
+    bface_t *fb = (bface_t *)malloc((size_t)bcap * sizeof(bface_t));
+    if (!fi || !fb) return -1;
+    for (int64_t a = 0; a < p->nleaves; a++) {
+        const leaf_t *A = &p->lv[a];
+        if (A->solid) continue;
+        for (int d = 0; d < dim; d++)
+            for (int side = 0; side < 2; side++) {
+                int32_t N = (int32_t)1 << A->lev;
+                int32_t c[3] = {A->i[0], A->i[1], A->i[2]};
+                c[d] += side ? 1 : -1;
+                if (c[d] < 0 || c[d] >= N) {
+                    if (periodic_axis(s, d)) c[d] = (c[d] + N) % N;
+                    else {
+                        if (nb == bcap) { bcap *= 2; fb = (bface_t *)realloc(fb, (size_t)bcap * sizeof(bface_t)); }
+                        bface_t t = {a, -1, (uint8_t)d, (uint8_t)side, (uint8_t)s->bc[2 * d + side],
+                                     ldexp(1.0, -A->lev * (dim - 1)), A->key, 0};
+                        fb[nb++] = t;
+                        continue;
+                    }
+                }
+                int64_t nbrs[4];
+                int nn = 0;
+                double area;
+                int64_t b = locate_cell(p->lv, p->nleaves, dim, L, A->lev, c);
+                if (p->lv[b].lev <= A->lev) {
+                    nbrs[nn++] = b;
+                    area = ldexp(1.0, -A->lev * (dim - 1));
+                } else {
+                    /* the finer neighbours: children of c on the side facing A */
+                    int nsub = 1 << (dim - 1);
+                    for (int t = 0; t < nsub; t++) {
+                        int32_t cc[3] = {0, 0, 0};
+                        int bit = 0;
+                        for (int e = 0; e < dim; e++) {
+                            if (e == d) cc[e] = 2 * c[e] + (side ? 0 : 1);
+                            else cc[e] = 2 * c[e] + ((t >> bit++) & 1);
+                        }
+                        int64_t bb = locate_cell(p->lv, p->nleaves, dim, L, A->lev + 1, cc);
+                        if (p->lv[bb].lev != A->lev + 1) { free(fi); free(fb); return -2; }
+                        nbrs[nn++] = bb;
+                    }
+                    area = ldexp(1.0, -(A->lev + 1) * (dim - 1));
+                }
+                for (int t = 0; t < nn; t++) {
+                    int64_t bb = nbrs[t];
+                    if (p->lv[bb].solid) {
+                        if (nb == bcap) { bcap *= 2; fb = (bface_t *)realloc(fb, (size_t)bcap * sizeof(bface_t)); }
+                        bface_t w = {a, bb, (uint8_t)d, (uint8_t)side, ORC_BC_WALL, area,
+                                     A->key, p->lv[bb].key};
+                        fb[nb++] = w;
+                    } else if (side == 1) {
+                        if (ni == icap) { icap *= 2; fi = (iface_t *)realloc(fi, (size_t)icap * sizeof(iface_t)); }
+                        iface_t w = {a, bb, (uint8_t)d, area, A->key, p->lv[bb].key};
+                        fi[ni++] = w;
+                    }
+                }
+            }
+    }
+    qsort(fi, (size_t)ni, sizeof(iface_t), cmp_iface);
+    qsort(fb, (size_t)nb, sizeof(bface_t), cmp_bface);
+    p->nf = ni;
+    p->fm = (int64_t *)malloc((size_t)(ni + 1) * sizeof(int64_t));
+    p->fp = (int64_t *)malloc((size_t)(ni + 1) * sizeof(int64_t));
+    p->fax = (uint8_t *)malloc((size_t)(ni + 1));
+    p->farea = (double *)malloc((size_t)(ni + 1) * sizeof(double));
+    for (int64_t q = 0; q < ni; q++) {
+        p->fm[q] = fi[q].m; p->fp[q] = fi[q].p; p->fax[q] = fi[q].ax; p->farea[q] = fi[q].area;
+    }
+    p->nbf = nb;
+    p->bl = (int64_t *)malloc((size_t)(nb + 1) * sizeof(int64_t));
+    p->bother = (int64_t *)malloc((size_t)(nb + 1) * sizeof(int64_t));
+    p->bax = (uint8_t *)malloc((size_t)(nb + 1));
+    p->bside = (uint8_t *)malloc((size_t)(nb + 1));
+    p->bkind = (uint8_t *)malloc((size_t)(nb + 1));
+    p->barea = (double *)malloc((size_t)(nb + 1) * sizeof(double));
+    for (int64_t q = 0; q < nb; q++) {
+        p->bl[q] = fb[q].l; p->bother[q] = fb[q].o; p->bax[q] = fb[q].ax;
+        p->bside[q] = fb[q].side; p->bkind[q] = fb[q].kind; p->barea[q] = fb[q].area;
+    }
+    free(fi);
+    free(fb);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+
+static double maxwellian(double rho, const double u[3], double T, const double xi[3])
+{
+    double q = 0.0;
+    for (int d = 0; d < 3; d++) q += (xi[d] - u[d]) * (xi[d] - u[d]);
+    return rho * pow(2.0 * M_PI * T, -1.5) * exp(-q / (2.0 * T));
+}
+
+orc_problem *orc_create(const orc_tree_spec *spec, const int n[3],
+                        const double lo[3], const double hi[3])
+{
+    if (check_spec(spec)) return NULL;
+    orc_problem *p = (orc_problem *)calloc(1, sizeof(orc_problem));
+    if (!p) return NULL;
+    p->spec = *spec;
+    p->L = spec->max_level;
+    leafvec t;
+    if (build_tree(spec, &t)) { free(p); return NULL; }
+    p->lv = t.v;
+    p->nleaves = t.n;
+    p->cell_of_leaf = (int64_t *)malloc((size_t)t.n * sizeof(int64_t));
+    p->leaf_of_cell = (int64_t *)malloc((size_t)t.n * sizeof(int64_t));
+    for (int64_t a = 0; a < t.n; a++) {
+        if (p->lv[a].solid) p->cell_of_leaf[a] = -1;
+        else { p->cell_of_leaf[a] = p->ncells; p->leaf_of_cell[p->ncells++] = a; }
+    }
+    if (build_faces(p)) { orc_destroy(p); return NULL; }
+    for (int d = 0; d < 3; d++) { p->n[d] = n[d]; p->lo[d] = lo[d]; p->hi[d] = hi[d]; }
+    p->nv = orc_vgrid_size(n);
+    p->xi = (double *)malloc((size_t)p->nv * 3 * sizeof(double));
+    p->k = (int32_t *)malloc((size_t)p->nv * 3 * sizeof(int32_t));
+    if (orc_vgrid(n, lo, hi, p->xi, p->k, &p->dV)) { orc_destroy(p); return NULL; }
+    for (int d = 0; d < 3; d++) p->h[d] = (hi[d] - lo[d]) / n[d];
+    /* mirror maps: the node whose component d is reflected (k -> n-1-k) */
+    int64_t *idx = (int64_t *)malloc((size_t)p->nv * sizeof(int64_t));
+    for (int64_t v = 0; v < p->nv; v++) {
+        const int32_t *kk = &p->k[3 * v];
+        idx[((int64_t)kk[0] * n[1] + kk[1]) * n[2] + kk[2]] = v;
+    }
+    for (int d = 0; d < 3; d++) {
+        p->mirror[d] = (int64_t *)malloc((size_t)p->nv * sizeof(int64_t));
+        for (int64_t v = 0; v < p->nv; v++) {
+            int32_t kk[3] = {p->k[3 * v], p->k[3 * v + 1], p->k[3 * v + 2]};
+            kk[d] = n[d] - 1 - kk[d];
+            p->mirror[d][v] = idx[((int64_t)kk[0] * n[1] + kk[1]) * n[2] + kk[2]];
+        }
+    }
+    free(idx);
+    p->f = (double *)calloc((size_t)(p->ncells * p->nv), sizeof(double));
+    p->finf = (double *)calloc((size_t)p->nv, sizeof(double));
+    if (!p->f || !p->finf) { orc_destroy(p); return NULL; }
+    double u0[3] = {0, 0, 0};
+    orc_set_freestream(p, 1.0, u0, 1.0);
+    return p;
+}
+
+void orc_destroy(orc_problem *p)
+{
+    if (!p) return;
+    free(p->lv); free(p->cell_of_leaf); free(p->leaf_of_cell);
+    free(p->fm); free(p->fp); free(p->fax); free(p->farea);
+    free(p->bl); free(p->bother); free(p->bax); free(p->bside); free(p->bkind); free(p->barea);
+    free(p->xi); free(p->k);
+    for (int d = 0; d < 3; d++) free(p->mirror[d]);
+    free(p->f); free(p->finf);
+    free(p->hs_start); free(p->hs_gam); free(p->hs_l); free(p->hs_m); free(p->hs_b);
+    free(p);
+}
+
+int64_t orc_nleaves(const orc_problem *p) { return p->nleaves; }
+int64_t orc_ncells(const orc_problem *p) { return p->ncells; }
+int64_t orc_nv(const orc_problem *p) { return p->nv; }
+int64_t orc_n_faces(const orc_problem *p) { return p->nf; }
+int64_t orc_n_bfaces(const orc_problem *p) { return p->nbf; }
+
+int orc_get_leaves(const orc_problem *p, uint64_t *keys, uint8_t *levels, uint8_t *solid)
+{
+    for (int64_t a = 0; a < p->nleaves; a++) {
+        if (keys) keys[a] = p->lv[a].key;
+        if (levels) levels[a] = (uint8_t)p->lv[a].lev;
+        if (solid) solid[a] = p->lv[a].solid;
+    }
+    return 0;
+}
+
+int orc_cell_centres(const orc_problem *p, double *xyz, double *h)
+{
+    for (int64_t c = 0; c < p->ncells; c++) {
+        const leaf_t *x = &p->lv[p->leaf_of_cell[c]];
+        double hh = ldexp(1.0, -x->lev);
+        for (int d = 0; d < 3; d++)
+            xyz[3 * c + d] = d < p->spec.dim ? (x->i[d] + 0.5) * hh : 0.5;
+        if (h) h[c] = hh;
+    }
+    return 0;
+}
+
+int orc_get_faces(const orc_problem *p, int64_t *minus, int64_t *plus,
+                  uint8_t *axis, double *area)
+{
+    for (int64_t q = 0; q < p->nf; q++) {
+        minus[q] = p->fm[q]; plus[q] = p->fp[q]; axis[q] = p->fax[q]; area[q] = p->farea[q];
+    }
+    return 0;
+}
+
+int orc_get_bfaces(const orc_problem *p, int64_t *leaf, uint8_t *axis,
+                   uint8_t *side, uint8_t *kind, int64_t *other, double *area)
+{
+    for (int64_t q = 0; q < p->nbf; q++) {
+        leaf[q] = p->bl[q]; axis[q] = p->bax[q]; side[q] = p->bside[q];
+        kind[q] = p->bkind[q]; other[q] = p->bother[q]; area[q] = p->barea[q];
+    }
+    return 0;
+}
+
+int orc_set_freestream(orc_problem *p, double rho, const double u[3], double T)
+{
+    p->fs_rho = rho;
+    p->fs_T = T;
+    for (int d = 0; d < 3; d++) p->fs_u[d] = u[d];
+    for (int64_t v = 0; v < p->nv; v++) p->finf[v] = maxwellian(rho, u, T, &p->xi[3 * v]);
+    return 0;
+}
+
+int orc_init_maxwellian(orc_problem *p, int nmix, const double *w,
+                        const double *rho, const double *u, const double *T)
+{
+    for (int64_t c = 0; c < p->ncells; c++)
+        for (int64_t v = 0; v < p->nv; v++) {
+            double s = 0.0;
+            for (int m = 0; m < nmix; m++) {
+                int64_t q = c * nmix + m;
+                s += w[q] * maxwellian(rho[q], &u[3 * q], T[q], &p->xi[3 * v]);
+            }
+            p->f[c * p->nv + v] = s;
+        }
+    return 0;
+}
+
+int orc_get_f(const orc_problem *p, double *f)
+{
+    memcpy(f, p->f, (size_t)(p->ncells * p->nv) * sizeof(double));
+    return 0;
+}
+
+int orc_set_f(orc_problem *p, const double *f)
+{
+    memcpy(p->f, f, (size_t)(p->ncells * p->nv) * sizeof(double));
+    return 0;
+}
+
+/* dt = CFL * h_min / max_i sum_{d < dim} |xi_{d,i}| */
+double orc_dt_cfl(const orc_problem *p, double cfl)
+{
+    int maxlev = -1;
+    for (int64_t c = 0; c < p->ncells; c++) {
+        int l = p->lv[p->leaf_of_cell[c]].lev;
+        if (l > maxlev) maxlev = l;
+    }
+    double smax = 0.0;
+    for (int64_t v = 0; v < p->nv; v++) {
+        double s = 0.0;
+        for (int d = 0; d < p->spec.dim; d++) s += fabs(p->xi[3 * v + d]);
+        if (s > smax) smax = s;
+    }
+    return cfl * ldexp(1.0, -maxlev) / smax;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Transport, Eq. 2 written as a sum of upwind face fluxes:
+ *   f*_j = f_j - (dt / V_j) sum_{faces of j} (xi . n_out) A f_upwind
+ * The upwind value is the cell on the side the velocity comes from; at a
+ * domain side it is the ghost value (inflow: freestream Maxwellian;
+ * outflow: the cell's own value; specular wall: the cell's value at the
+ * reflected velocity). */
+int orc_transport(orc_problem *p, double dt)
+{
+    int dim = p->spec.dim;
+    int64_t nv = p->nv;
+    double *fs = (double *)malloc((size_t)(p->ncells * nv) * sizeof(double));
+    if (!fs) return -1;
+    memcpy(fs, p->f, (size_t)(p->ncells * nv) * sizeof(double));
+    const double *f = p->f;
+#pragma omp parallel for schedule(static)
+    for (int64_t v = 0; v < nv; v++) {
+        for (int64_t q = 0; q < p->nf; q++) {
+            int d = p->fax[q];
+            int64_t a = p->cell_of_leaf[p->fm[q]], b = p->cell_of_leaf[p->fp[q]];
+            double Va = ldexp(1.0, -p->lv[p->fm[q]].lev * dim);
+            double Vb = ldexp(1.0, -p->lv[p->fp[q]].lev * dim);
+            double x = p->xi[3 * v + d];
+            double up = x > 0.0 ? f[a * nv + v] : f[b * nv + v];
+            double flux = x * p->farea[q] * up;
+            fs[a * nv + v] -= dt * flux / Va;
+            fs[b * nv + v] += dt * flux / Vb;
+        }
+        for (int64_t q = 0; q < p->nbf; q++) {
+            int d = p->bax[q];
+            int64_t a = p->cell_of_leaf[p->bl[q]];
+            double Va = ldexp(1.0, -p->lv[p->bl[q]].lev * dim);
+            double xn = (p->bside[q] ? 1.0 : -1.0) * p->xi[3 * v + d];
+            double up;
+            if (xn > 0.0) up = f[a * nv + v];
+            else if (p->bkind[q] == ORC_BC_INFLOW) up = p->finf[v];
+            else if (p->bkind[q] == ORC_BC_WALL) up = f[a * nv + p->mirror[d][v]];
+            else up = f[a * nv + v];
+            fs[a * nv + v] -= dt * xn * p->barea[q] * up / Va;
+        }
+    }
+    free(p->f);
+    p->f = fs;
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Moments: rho = sum f dV, rho u = sum xi f dV, E = sum |xi|^2/2 f dV,
+ * T = (2E/rho - |u|^2)/3 (velocities in thermal units). */
+static void cell_moments(const orc_problem *p, const double *f, double *rho,
+                         double u[3], double *T)
+{
+    double s0 = 0.0, s1[3] = {0, 0, 0}, s2 = 0.0;
+    for (int64_t v = 0; v < p->nv; v++) {
+        const double *x = &p->xi[3 * v];
+        s0 += f[v];
+        for (int d = 0; d < 3; d++) s1[d] += x[d] * f[v];
+        s2 += (x[0] * x[0] + x[1] * x[1] + x[2] * x[2]) * f[v];
+    }
+    *rho = s0 * p->dV;
+    double uu = 0.0;
+    for (int d = 0; d < 3; d++) { u[d] = s1[d] / s0; uu += u[d] * u[d]; }
+    *T = (s2 / s0 - uu) / 3.0;
+}
+
+int orc_moments(const orc_problem *p, double *rho, double *u, double *T)
+{
+    for (int64_t c = 0; c < p->ncells; c++)
+        cell_moments(p, &p->f[c * p->nv], &rho[c], &u[3 * c], &T[c]);
+    return 0;
+}
+
+int orc_totals(const orc_problem *p, double out[5])
+{
+    for (int r = 0; r < 5; r++) out[r] = 0.0;
+    int dim = p->spec.dim;
+    for (int64_t c = 0; c < p->ncells; c++) {
+        double V = ldexp(1.0, -p->lv[p->leaf_of_cell[c]].lev * dim);
+        for (int64_t v = 0; v < p->nv; v++) {
+            const double *x = &p->xi[3 * v];
+            double fv = p->f[c * p->nv + v] * p->dV * V;
+            out[0] += fv;
+            out[1] += x[0] * fv;
+            out[2] += x[1] * fv;
+            out[3] += x[2] * fv;
+            out[4] += (x[0] * x[0] + x[1] * x[1] + x[2] * x[2]) * fv;
+        }
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+
+int orc_solve(int n, double *A, double *b, double *x)
+{
+    for (int c = 0; c < n; c++) {
+        int piv = c;
+        for (int r = c + 1; r < n; r++)
+            if (fabs(A[r * n + c]) > fabs(A[piv * n + c])) piv = r;
+        if (!(fabs(A[piv * n + c]) > 0.0) || !isfinite(A[piv * n + c])) return -1;
+        if (piv != c) {
+            for (int q = 0; q < n; q++) { double t = A[c * n + q]; A[c * n + q] = A[piv * n + q]; A[piv * n + q] = t; }
+            double t = b[c]; b[c] = b[piv]; b[piv] = t;
+        }
+        for (int r = c + 1; r < n; r++) {
+            double m = A[r * n + c] / A[c * n + c];
+            for (int q = c; q < n; q++) A[r * n + q] -= m * A[c * n + q];
+            b[r] -= m * b[c];
+        }
+    }
+    for (int r = n - 1; r >= 0; r--) {
+        double s = b[r];
+        for (int q = r + 1; q < n; q++) s -= A[r * n + q] * x[q];
+        x[r] = s / A[r * n + r];
+        if (!isfinite(x[r])) return -1;
+    }
+    return 0;
+}
+
+static void psi5(const double *x, double ps[5])
+{
+    ps[0] = 1.0; ps[1] = x[0]; ps[2] = x[1]; ps[3] = x[2];
+    ps[4] = x[0] * x[0] + x[1] * x[1] + x[2] * x[2];
+}
+
+/* Conservative BGK: the discrete Maxwellian of the cell's moments times the
+ * polynomial 1 + d0 + d.xi + d2 |xi|^2 (the correction form of Eq. 6) whose
+ * five coefficients make its discrete moments equal those of f; then
+ * f <- f + dt nu (M~ - f), nu = sqrt(8/pi) rho sqrt(T) / Kn. */
+int orc_bgk(orc_problem *p, double dt, double kn, double *q)
+{
+    int64_t nv = p->nv;
+    int err = 0;
+#pragma omp parallel for schedule(dynamic, 16) reduction(| : err)
+    for (int64_t c = 0; c < p->ncells; c++) {
+        double *f = &p->f[c * nv];
+        double rho, u[3], T;
+        cell_moments(p, f, &rho, u, &T);
+        double *M = (double *)malloc((size_t)nv * sizeof(double));
+        double A[25] = {0}, rhs[5] = {0}, d[5];
+        for (int64_t v = 0; v < nv; v++) {
+            double ps[5];
+            psi5(&p->xi[3 * v], ps);
+            M[v] = maxwellian(rho, u, T, &p->xi[3 * v]);
+            for (int r = 0; r < 5; r++) {
+                for (int s = 0; s < 5; s++) A[r * 5 + s] += ps[r] * ps[s] * M[v] * p->dV;
+                rhs[r] += ps[r] * (f[v] - M[v]) * p->dV;
+            }
+        }
+        if (!(rho > 0.0) || !(T > 0.0) || orc_solve(5, A, rhs, d)) { err = 1; free(M); continue; }
+        double nu = sqrt(8.0 / M_PI) * rho * sqrt(T) / kn;
+        for (int64_t v = 0; v < nv; v++) {
+            double ps[5];
+            psi5(&p->xi[3 * v], ps);
+            double P = 1.0;
+            for (int r = 0; r < 5; r++) P += d[r] * ps[r];
+            double Q = nu * (M[v] * P - f[v]);
+            if (q) q[c * nv + v] = Q;
+            f[v] += dt * Q;
+        }
+        free(M);
+    }
+    return err ? -1 : 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Hard-sphere trials.  For node i and trial k the stream index is i*M + k
+ * and draws 3s, 3s+1, 3s+2 give the partner gamma (uniform over the nodes)
+ * and the unit vector omega (z = 2u - 1, phi = 2 pi u').  The post-collision
+ * pair xi' = c + |g| omega / 2, xi'_* = c - |g| omega / 2 (c the mean of xi_i
+ * and xi_gamma) is mapped to its nearest nodes l, m; a trial whose l or m
+ * falls outside the grid is dropped.  With M_kept kept trials,
+ * b = c = Nv dV |g| / (sqrt(2) M_kept), the Monte-Carlo weights of
+ * I = 1/(4 sqrt(2) pi) int int (f'f'_* - f f_*) |g| dOmega dxi_*. */
+static int nearest_node(const orc_problem *p, const double x[3], int32_t kk[3])
+{
+    for (int d = 0; d < 3; d++) {
+        double t = (x[d] - p->lo[d]) / p->h[d] - 0.5;
+        double r = round(t);
+        if (!(r >= 0.0) || r > (double)(p->n[d] - 1)) return 0;
+        kk[d] = (int32_t)r;
+    }
+    return 1;
+}
+
+int orc_hs_tables(orc_problem *p, int trials, uint64_t seed)
+{
+    int64_t nv = p->nv;
+    int64_t *idx = (int64_t *)malloc((size_t)nv * sizeof(int64_t));
+    for (int64_t v = 0; v < nv; v++) {
+        const int32_t *kk = &p->k[3 * v];
+        idx[((int64_t)kk[0] * p->n[1] + kk[1]) * p->n[2] + kk[2]] = v;
+    }
+    free(p->hs_start); free(p->hs_gam); free(p->hs_l); free(p->hs_m); free(p->hs_b);
+    int64_t cap = nv * trials;
+    p->hs_start = (int64_t *)malloc((size_t)(nv + 1) * sizeof(int64_t));
+    p->hs_gam = (int32_t *)malloc((size_t)cap * sizeof(int32_t));
+    p->hs_l = (int32_t *)malloc((size_t)cap * sizeof(int32_t));
+    p->hs_m = (int32_t *)malloc((size_t)cap * sizeof(int32_t));
+    p->hs_b = (double *)malloc((size_t)cap * sizeof(double));
+    int64_t nk = 0, disc = 0;
+    for (int64_t i = 0; i < nv; i++) {
+        p->hs_start[i] = nk;
+        const double *xa = &p->xi[3 * i];
+        for (int k = 0; k < trials; k++) {
+            uint64_t s = (uint64_t)i * (uint64_t)trials + (uint64_t)k;
+            double u0 = unif53(seed, 3 * s), u1 = unif53(seed, 3 * s + 1), u2 = unif53(seed, 3 * s + 2);
+            int64_t gam = (int64_t)(u0 * (double)nv);
+            const double *xb = &p->xi[3 * gam];
+            double g2 = 0.0;
+            for (int d = 0; d < 3; d++) g2 += (xa[d] - xb[d]) * (xa[d] - xb[d]);
+            double gn = sqrt(g2);
+            double z = 2.0 * u1 - 1.0, phi = 2.0 * M_PI * u2;
+            double st = sqrt(fmax(0.0, 1.0 - z * z));
+            double w[3] = {st * cos(phi), st * sin(phi), z};
+            double xp[3], xq[3];
+            for (int d = 0; d < 3; d++) {
+                double c = 0.5 * (xa[d] + xb[d]);
+                xp[d] = c + 0.5 * gn * w[d];
+                xq[d] = c - 0.5 * gn * w[d];
+            }
+            int32_t kp[3], kq[3];
+            if (!nearest_node(p, xp, kp) || !nearest_node(p, xq, kq)) { disc++; continue; }
+            p->hs_gam[nk] = (int32_t)gam;
+            p->hs_l[nk] = (int32_t)idx[((int64_t)kp[0] * p->n[1] + kp[1]) * p->n[2] + kp[2]];
+            p->hs_m[nk] = (int32_t)idx[((int64_t)kq[0] * p->n[1] + kq[1]) * p->n[2] + kq[2]];
+            p->hs_b[nk] = gn;
+            nk++;
+        }
+        for (int64_t q = p->hs_start[i]; q < nk; q++)
+            p->hs_b[q] = (double)nv * p->dV * p->hs_b[q] / (sqrt(2.0) * (double)trials);
+    }
+    p->hs_start[nv] = nk;
+    p->hs_nkept = nk;
+    p->hs_discarded = disc;
+    p->hs_trials = trials;
+    free(idx);
+    return 0;
+}
+
+int64_t orc_hs_nkept(const orc_problem *p) { return p->hs_nkept; }
+
+int orc_hs_get_tables(const orc_problem *p, int64_t *start, int32_t *gam,
+                      int32_t *l, int32_t *m, double *b, int64_t *discarded)
+{
+    if (!p->hs_start) return -1;
+    memcpy(start, p->hs_start, (size_t)(p->nv + 1) * sizeof(int64_t));
+    memcpy(gam, p->hs_gam, (size_t)p->hs_nkept * sizeof(int32_t));
+    memcpy(l, p->hs_l, (size_t)p->hs_nkept * sizeof(int32_t));
+    memcpy(m, p->hs_m, (size_t)p->hs_nkept * sizeof(int32_t));
+    memcpy(b, p->hs_b, (size_t)p->hs_nkept * sizeof(double));
+    *discarded = p->hs_discarded;
+    return 0;
+}
+
+/* Eqs. 4-6: B_i = sum_k b f_gamma, C_i = sum_k c f_l f_m (b = c),
+ * I_i = -f_i P_i B_i + C_i with P = 1 + d0 + d.xi + d2 |xi|^2 chosen so that
+ * sum_i psi_r I_i dV = 0 for psi = (1, xi, |xi|^2); then f <- f + dt/Kn I. */
+int orc_hs_collide(orc_problem *p, double dt, double kn, double *q,
+                   double *Bout, double *Cout)
+{
+    if (!p->hs_start) return -1;
+    int64_t nv = p->nv;
+    int err = 0;
+#pragma omp parallel for schedule(dynamic, 4) reduction(| : err)
+    for (int64_t c = 0; c < p->ncells; c++) {
+        double *f = &p->f[c * nv];
+        double *B = (double *)malloc((size_t)nv * sizeof(double));
+        double *C = (double *)malloc((size_t)nv * sizeof(double));
+        for (int64_t i = 0; i < nv; i++) {
+            double sb = 0.0, sc = 0.0;
+            for (int64_t t = p->hs_start[i]; t < p->hs_start[i + 1]; t++) {
+                sb += p->hs_b[t] * f[p->hs_gam[t]];
+                sc += p->hs_b[t] * f[p->hs_l[t]] * f[p->hs_m[t]];
+            }
+            B[i] = sb;
+            C[i] = sc;
+        }
+        double A[25] = {0}, rhs[5] = {0}, d[5];
+        for (int64_t i = 0; i < nv; i++) {
+            double ps[5];
+            psi5(&p->xi[3 * i], ps);
+            for (int r = 0; r < 5; r++) {
+                for (int s = 0; s < 5; s++) A[r * 5 + s] += ps[r] * ps[s] * f[i] * B[i] * p->dV;
+                rhs[r] += ps[r] * (C[i] - f[i] * B[i]) * p->dV;
+            }
+        }
+        if (orc_solve(5, A, rhs, d)) { err = 1; free(B); free(C); continue; }
+        for (int64_t i = 0; i < nv; i++) {
+            double ps[5];
+            psi5(&p->xi[3 * i], ps);
+            double P = 1.0;
+            for (int r = 0; r < 5; r++) P += d[r] * ps[r];
+            double I = -f[i] * P * B[i] + C[i];
+            if (q) q[c * nv + i] = I;
+            if (Bout) Bout[c * nv + i] = B[i];
+            if (Cout) Cout[c * nv + i] = C[i];
+            f[i] += dt / kn * I;
+        }
+        free(B);
+        free(C);
+    }
+    return err ? -1 : 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Lie splitting: transport, then the collision update on f*. */
+int orc_step(orc_problem *p, int nsteps, double dt, int coll, double kn)
+{
+    for (int s = 0; s < nsteps; s++) {
+        if (orc_transport(p, dt)) return -1;
+        if (coll == 1 && orc_bgk(p, dt, kn, NULL)) return -2;
+        if (coll == 2 && orc_hs_collide(p, dt, kn, NULL, NULL, NULL)) return -3;
+    }
+    return 0;
+}

@@ -1,0 +1,115 @@
+/*
+ * FP64 CPU oracle for the explicit discrete-velocity (DVM) Boltzmann step on a
+ * tree-based adaptive Cartesian mesh (Zabelok, Arslanbekov, Kolobov, "Adaptive
+ * Kinetic-Fluid Solvers for Heterogeneous Computing Architectures", Sec. 2.1,
+ * Sec. 3, Eqs. 1-6).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This library is the slow, obviously correct
+ * statement of what the GPU path computes.  Only the test-suite, the smoke
+ * check and the CPU-baseline leg of the benchmark may load it; the product
+ * path never does.  It shares no code, header or table with the CUDA library.
+ *
+ * Everything is IEEE double.  Loops follow the paper's definitions directly:
+ * no blocking, no fusion.
+ */
+#ifndef DVM_ORACLE_H
+#define DVM_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Boundary kinds for the six domain sides (x-, x+, y-, y+, z-, z+). */
+enum { ORC_BC_PERIODIC = 0, ORC_BC_INFLOW = 1, ORC_BC_OUTFLOW = 2, ORC_BC_WALL = 3 };
+
+/* Refinement predicates. */
+enum { ORC_PRED_NONE = 0, ORC_PRED_BALL = 1, ORC_PRED_SHELL = 2 };
+
+typedef struct {
+    int dim;            /* 2 or 3 physical dimensions                       */
+    int base_level;     /* uniform starting level                           */
+    int max_level;      /* deepest level a refinement may reach             */
+    int pred;           /* ORC_PRED_*                                       */
+    double c[3];        /* predicate centre                                 */
+    double r;           /* ball radius / sphere radius                      */
+    double beta;        /* shell half-width in units of the box size        */
+    int solid;          /* 1: leaves whose centre is inside the sphere are solid */
+    int bc[6];          /* ORC_BC_* per side; periodic must come in pairs   */
+} orc_tree_spec;
+
+typedef struct orc_problem orc_problem;
+
+/* SplitMix64 output number n (0-based) of the stream seeded with `seed`. */
+uint64_t orc_splitmix64(uint64_t seed, uint64_t n);
+
+/* ---- velocity grid (Sec. 3, Sec. 3.1 steps 1-3) ---- */
+int64_t orc_vgrid_size(const int n[3]);
+/* xi: [Nv][3] node values in octant-block order; k: [Nv][3] axis indices */
+int orc_vgrid(const int n[3], const double lo[3], const double hi[3],
+              double *xi, int32_t *k, double *dV);
+
+/* ---- tree (Sec. 2.1) ---- */
+int orc_build_tree(const orc_tree_spec *spec, int64_t cap, int64_t *n,
+                   uint64_t *keys, uint8_t *levels, uint8_t *solid);
+
+/* ---- problem object ---- */
+orc_problem *orc_create(const orc_tree_spec *spec, const int n[3],
+                        const double lo[3], const double hi[3]);
+void orc_destroy(orc_problem *p);
+int64_t orc_nleaves(const orc_problem *p);
+int64_t orc_ncells(const orc_problem *p);
+int64_t orc_nv(const orc_problem *p);
+int orc_get_leaves(const orc_problem *p, uint64_t *keys, uint8_t *levels, uint8_t *solid);
+int orc_cell_centres(const orc_problem *p, double *xyz /* [ncells][3] */, double *h);
+int64_t orc_n_faces(const orc_problem *p);
+int64_t orc_n_bfaces(const orc_problem *p);
+/* interior faces: leaf indices (into the Morton leaf list), axis, area */
+int orc_get_faces(const orc_problem *p, int64_t *minus, int64_t *plus,
+                  uint8_t *axis, double *area);
+/* boundary faces: fluid leaf, axis, side (0 = -, 1 = +), kind, other leaf
+ * (-1 for a domain side), area */
+int orc_get_bfaces(const orc_problem *p, int64_t *leaf, uint8_t *axis,
+                   uint8_t *side, uint8_t *kind, int64_t *other, double *area);
+
+int orc_set_freestream(orc_problem *p, double rho, const double u[3], double T);
+/* f_j = sum_m w[j,m] M(rho[j,m], u[j,m,:], T[j,m]) at every node */
+int orc_init_maxwellian(orc_problem *p, int nmix, const double *w,
+                        const double *rho, const double *u, const double *T);
+int orc_get_f(const orc_problem *p, double *f);
+int orc_set_f(orc_problem *p, const double *f);
+double orc_dt_cfl(const orc_problem *p, double cfl);
+
+/* One transport sub-step (Eq. 2 in flux form): f <- f* */
+int orc_transport(orc_problem *p, double dt);
+/* moments of the stored f: rho, u[3], T per cell */
+int orc_moments(const orc_problem *p, double *rho, double *u, double *T);
+/* conserved totals sum_j V_j sum_i psi_r f ΔV, r = 0..4 */
+int orc_totals(const orc_problem *p, double out[5]);
+/* Conservative BGK relaxation of the stored f (forward Euler).  If q is
+ * non-null it receives the collision term nu (M~ - f) per element. */
+int orc_bgk(orc_problem *p, double dt, double kn, double *q);
+
+/* Hard-sphere tables (Eqs. 3-5 with the seeded trial construction). */
+int orc_hs_tables(orc_problem *p, int trials, uint64_t seed);
+int64_t orc_hs_nkept(const orc_problem *p);
+/* per node i: first kept trial index, count of kept trials (CSR) */
+int orc_hs_get_tables(const orc_problem *p, int64_t *start, int32_t *gam,
+                      int32_t *l, int32_t *m, double *b, int64_t *discarded);
+/* Conservative hard-sphere collision of the stored f (Eq. 6) with forward
+ * Euler.  q (optional): collision term I per element; Bout, Cout optional. */
+int orc_hs_collide(orc_problem *p, double dt, double kn, double *q,
+                   double *Bout, double *Cout);
+
+/* Full steps: transport, then collision on f* (Lie splitting).
+ * coll: 0 none, 1 BGK, 2 hard sphere. */
+int orc_step(orc_problem *p, int nsteps, double dt, int coll, double kn);
+
+/* Gaussian elimination with partial pivoting on an n x n system (n <= 8);
+ * A is row-major and is overwritten.  Returns 0, or -1 if singular. */
+int orc_solve(int n, double *A, double *b, double *x);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
