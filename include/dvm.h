@@ -1,0 +1,214 @@
+/*
+ * libdvm — explicit discrete-velocity (DVM) Boltzmann step on a tree-based
+ * adaptive Cartesian mesh, on one GB300 (sm_103a).
+ *
+ * Method: Zabelok, Arslanbekov, Kolobov, "Adaptive Kinetic-Fluid Solvers for
+ * Heterogeneous Computing Architectures" — the quad/octree mesh with 2:1
+ * balance for direct and diagonal neighbours and Morton ordering (Sec. 2.1),
+ * the non-dimensional Boltzmann equation df/dt + xi.grad f = I(f,f)/Kn
+ * (Sec. 3, Eq. 1), the discrete velocity method on a uniform velocity grid
+ * (Sec. 3), the finite-volume advection scheme (Sec. 3.1, Eq. 2) with the
+ * velocity points grouped by the signs of their components (Sec. 3.1 steps
+ * 1-4), the discrete collision integral with collision frequency B, inverse
+ * integral C and the five-coefficient conservative correction (Sec. 3.2,
+ * Eqs. 3-6), and the BGK relaxation form (Sec. 4).
+ *
+ * Conventions for every entry point:
+ *   - Returns a dvm_status; DVM_OK is 0 and every failure is negative.  The
+ *     message of the last failure is available from dvm_last_error().
+ *   - Host arrays passed in are owned by the caller and copied before the
+ *     call returns; host arrays passed out are caller-allocated with the
+ *     sizes stated below.
+ *   - Device memory is owned by the library (cudaMalloc, or the allocator set
+ *     with dvm_set_allocator) and freed by dvm_destroy.
+ *   - Calls must come in the order create -> build_tree -> set_velocity_grid
+ *     -> (set_collision_tables) -> init_maxwellian/set_f -> step; a call out
+ *     of order returns DVM_ESTATE.
+ *   - Work is queued on the stream set by dvm_set_stream (default: the legacy
+ *     default stream).  dvm_step synchronises that stream once per call to
+ *     read the device status word; no kernel traps or spins.
+ *   - A context is not thread-safe; use one context per host thread.
+ *
+ * Velocity ordering (Sec. 3.1 step 1): the Nv = nx*ny*nz nodes are stored as
+ * 8 contiguous sign groups o = 4[xi_x>0] + 2[xi_y>0] + [xi_z>0]; inside a
+ * group, node (mx, my, mz) (m = 0 is the node nearest zero on that axis)
+ * sits at ((mx*ny/2) + my)*nz/2 + mz.  f is stored [cell][velocity], cells
+ * being the non-solid leaves in Morton order.
+ */
+#ifndef DVM_H
+#define DVM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dvm_ctx dvm_ctx;
+
+typedef enum {
+    DVM_OK = 0,
+    DVM_EINVAL = -1,        /* bad argument                                     */
+    DVM_ENOMEM = -2,        /* device or host allocation failed                 */
+    DVM_ECUDA = -3,         /* a CUDA runtime call failed                       */
+    DVM_ESTATE = -4,        /* call out of order                                */
+    DVM_EUNSTABLE = -5,     /* non-finite or non-positive moments, singular 5x5 system, nu*dt > 1 */
+    DVM_EBOUNDS = -6,       /* a table index outside its array (checked on the host) */
+    DVM_ETIMEOUT = -7,      /* reserved: a bounded device wait gave up          */
+    DVM_ENOTIMPL = -9       /* configuration not supported by this build        */
+} dvm_status;
+
+enum { DVM_F64 = 0, DVM_F32 = 1, DVM_BF16 = 2 };
+enum { DVM_COLL_NONE = 0, DVM_COLL_BGK = 1, DVM_COLL_HS = 2 };
+enum { DVM_BC_PERIODIC = 0, DVM_BC_INFLOW = 1, DVM_BC_OUTFLOW = 2, DVM_BC_WALL = 3 };
+enum { DVM_PRED_NONE = 0, DVM_PRED_BALL = 1, DVM_PRED_SHELL = 2 };
+
+typedef struct {
+    int precision;   /* storage of f: DVM_F64 (FP64 arithmetic throughout), DVM_F32 or
+                        DVM_BF16 (FP32 arithmetic, FP64 moment finish and 5x5 solve) */
+    int collision;   /* DVM_COLL_*                                                  */
+    double kn;       /* Knudsen number of Eq. 1                                     */
+} dvm_config;
+
+/* Tree specification (Sec. 2.1).  The domain is [0,1]^dim.  Starting from the
+ * uniform level base_level, a box of level l < max_level is split while the
+ * predicate holds:
+ *   DVM_PRED_BALL:  squared distance from c to the box <= r*r;
+ *   DVM_PRED_SHELL: the box meets the band r - beta*h <= |x - c| <= r + beta*h
+ *                   (h = 2^-l), tested on squared distances.
+ * The result is then balanced 2:1 across faces, edges and corners (periodic
+ * sides wrapped).  With solid = 1 a leaf whose centre is strictly inside the
+ * sphere |x - c| < r is solid: it carries no f, and its faces with fluid
+ * leaves are specular walls.  bc[2d], bc[2d+1] are the kinds of the minus and
+ * plus sides of axis d; periodic must come in pairs. */
+typedef struct {
+    int dim;          /* 2 or 3                  */
+    int base_level;   /* >= 1                    */
+    int max_level;    /* <= 19                   */
+    int pred;         /* DVM_PRED_*              */
+    double c[3];
+    double r;
+    double beta;
+    int solid;
+    int bc[6];
+} dvm_tree_spec;
+
+/* Create a context.  *out receives the handle.  Mesh calls are host work;
+ * the current CUDA device is first used by dvm_set_velocity_grid, which
+ * returns DVM_ECUDA when no device is available. */
+int dvm_create(dvm_ctx **out, const dvm_config *cfg);
+
+/* Release all device and host memory of the context (NULL is a no-op). */
+void dvm_destroy(dvm_ctx *ctx);
+
+/* Message of the last failure on this context ("" if none). */
+const char *dvm_last_error(const dvm_ctx *ctx);
+
+/* Queue all later work on `stream` (a cudaStream_t; NULL = default stream). */
+int dvm_set_stream(dvm_ctx *ctx, void *stream);
+
+/* Route device allocations through alloc(bytes, user) / free(ptr, user)
+ * (for example a framework's caching allocator).  Must be called before
+ * dvm_build_tree.  Passing NULL functions restores cudaMalloc/cudaFree. */
+int dvm_set_allocator(dvm_ctx *ctx, void *(*alloc_fn)(size_t, void *),
+                      void (*free_fn)(void *, void *), void *user);
+
+/* Build the balanced tree, its Morton order, the face lists and the
+ * per-cell upwind stencils (Sec. 2.1; Sec. 3.1 step 4).  Host work, once per
+ * mesh.  Rebuilding discards f. */
+int dvm_build_tree(dvm_ctx *ctx, const dvm_tree_spec *spec);
+
+/* Split every leaf i with flag[i] != 0 (indices into the Morton leaf list of
+ * dvm_get_leaves, nleaves entries), rebalance, and rebuild faces and
+ * stencils (Sec. 3.1: the stencil tables are redone whenever the mesh
+ * changes).  f is discarded. */
+int dvm_refine(dvm_ctx *ctx, const uint8_t *flag, int64_t nleaves);
+
+/* Sizes: leaves (including solid ones), cells (non-solid leaves), interior
+ * faces, boundary faces, velocity nodes (0 before set_velocity_grid).  Any
+ * pointer may be NULL. */
+int dvm_get_counts(const dvm_ctx *ctx, int64_t *nleaves, int64_t *ncells,
+                   int64_t *nfaces, int64_t *nbfaces, int64_t *nv);
+
+/* Leaves in Morton order: key = bit-interleaved anchor coordinates at depth
+ * max_level (bit b of x -> bit dim*b, y -> dim*b+1, z -> dim*b+2), level and
+ * solid flag.  Arrays of nleaves entries. */
+int dvm_get_leaves(const dvm_ctx *ctx, uint64_t *keys, uint8_t *levels, uint8_t *solid);
+
+/* Interior faces (one per fine subface between fluid leaves, across
+ * periodic sides too), sorted by (axis, key(minus), key(plus)): leaf indices,
+ * axis, area = (edge of the finer leaf)^(dim-1).  Arrays of nfaces entries. */
+int dvm_get_faces(const dvm_ctx *ctx, int64_t *minus, int64_t *plus, uint8_t *axis, double *area);
+
+/* Boundary faces of fluid leaves, sorted by (kind, axis, side, key(leaf),
+ * key(other)): domain sides (other = -1) and walls towards solid leaves.
+ * Arrays of nbfaces entries. */
+int dvm_get_bfaces(const dvm_ctx *ctx, int64_t *leaf, uint8_t *axis, uint8_t *side,
+                   uint8_t *kind, int64_t *other, double *area);
+
+/* Cell centres [ncells][3] (z = 0.5 in 2D) and edge lengths [ncells]. */
+int dvm_cell_centres(const dvm_ctx *ctx, double *xyz, double *h);
+
+/* Uniform velocity grid (Sec. 3): n[d] even, lo[d] = -hi[d] (a mirror-
+ * symmetric grid, so that sign groups and specular reflection map nodes to
+ * nodes).  Nodes xi_d(k) = lo_d + (k + 1/2) (hi_d - lo_d)/n_d in FP64.
+ * nz/2 must be a multiple of 4 (FP32/BF16) or 2 (FP64).  Allocates f. */
+int dvm_set_velocity_grid(dvm_ctx *ctx, const int n[3], const double lo[3], const double hi[3]);
+
+/* Node values in storage order, [nv][3] FP64. */
+int dvm_get_velocities(const dvm_ctx *ctx, double *xi);
+
+/* Freestream (rho, u, T) sampled as the inflow ghost Maxwellian. */
+int dvm_set_freestream(dvm_ctx *ctx, double rho, const double u[3], double T);
+
+/* f_j = sum_m w[j][m] M(rho[j][m], u[j][m][:], T[j][m]) at every node, with
+ * M = rho (2 pi T)^(-3/2) exp(-|xi - u|^2 / (2T)) evaluated in FP64 on the
+ * device and rounded to the storage precision.  Arrays are per cell:
+ * w, rho, T [ncells][nmix], u [ncells][nmix][3]. */
+int dvm_init_maxwellian(dvm_ctx *ctx, int nmix, const double *w, const double *rho,
+                        const double *u, const double *T);
+
+/* Copy f to/from the host as FP64 [ncells][nv] (converted from/to storage). */
+int dvm_get_f(dvm_ctx *ctx, double *f, int64_t count);
+int dvm_set_f(dvm_ctx *ctx, const double *f, int64_t count);
+
+/* Copy f to/from host memory in the storage format (ncells*nv elements of
+ * 8, 4 or 2 bytes; pinned memory gives asynchronous copies on the stream). */
+int dvm_upload_f(dvm_ctx *ctx, const void *host, int64_t bytes);
+int dvm_download_f(dvm_ctx *ctx, void *host, int64_t bytes);
+
+/* Device address and size in bytes of the current f buffer (read-only view
+ * for inspection; valid until the next dvm_step or rebuild). */
+int dvm_f_device(const dvm_ctx *ctx, void **ptr, int64_t *bytes);
+
+/* dt = CFL * h_min / max_i sum_{d<dim} |xi_{d,i}| over the fluid cells. */
+int dvm_dt_cfl(const dvm_ctx *ctx, double cfl, double *dt);
+
+/* Hard-sphere trial tables for Eqs. 3-5 (required for DVM_COLL_HS). */
+int dvm_set_collision_tables(dvm_ctx *ctx, int trials, uint64_t seed);
+
+/* nsteps explicit steps of size dt: transport (Eq. 2), moments of f*, then
+ * the collision update on f* (Lie splitting): BGK relaxation towards the
+ * conservatively corrected discrete Maxwellian, or Eqs. 3-6, with forward
+ * Euler.  Returns DVM_EUNSTABLE if any cell met a non-positive density or
+ * temperature, a singular correction system or nu*dt > 1. */
+int dvm_step(dvm_ctx *ctx, int nsteps, double dt);
+
+/* Moments of the stored f per cell: rho = sum f dV, u = sum xi f dV / rho,
+ * T = (sum |xi|^2 f dV / rho - |u|^2) / 3.  Host arrays rho, T [ncells],
+ * u [ncells][3]. */
+int dvm_moments(dvm_ctx *ctx, double *rho, double *u, double *T);
+
+/* Moments (rho, u, T) of the post-transport state f* of the last step, as
+ * used by its collision update (equal, by conservation, to those of the
+ * post-collision state up to storage rounding). */
+int dvm_step_moments(dvm_ctx *ctx, double *rho, double *u, double *T);
+
+/* Number of kernel launches the library has queued in this process. */
+int dvm_launch_count(int64_t *count);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -54,6 +54,9 @@ struct orc_problem {
     int64_t *bl, *bother;
     uint8_t *bax, *bside, *bkind;
     double *barea;
+    /* faces touching each cell, interior faces first, each list in face order:
+     * entry >= 0 is interior face q, entry < 0 is boundary face -1-q */
+    int64_t *cf_start, *cf_list;
     /* velocity grid */
     int n[3];
     double lo[3], hi[3], h[3], dV;
@@ -494,6 +497,27 @@ static int build_faces(orc_problem *p)
     }
     free(fi);
     free(fb);
+    /* per-cell face lists */
+    p->cf_start = (int64_t *)calloc((size_t)(p->ncells + 1), sizeof(int64_t));
+    p->cf_list = (int64_t *)malloc((size_t)(2 * ni + nb + 1) * sizeof(int64_t));
+    for (int64_t q = 0; q < ni; q++) {
+        p->cf_start[p->cell_of_leaf[p->fm[q]] + 1]++;
+        p->cf_start[p->cell_of_leaf[p->fp[q]] + 1]++;
+    }
+    for (int64_t q = 0; q < nb; q++) p->cf_start[p->cell_of_leaf[p->bl[q]] + 1]++;
+    for (int64_t c = 0; c < p->ncells; c++) p->cf_start[c + 1] += p->cf_start[c];
+    int64_t *fill = (int64_t *)malloc((size_t)(p->ncells + 1) * sizeof(int64_t));
+    memcpy(fill, p->cf_start, (size_t)(p->ncells + 1) * sizeof(int64_t));
+    for (int64_t q = 0; q < ni; q++) {
+        int64_t a = p->cell_of_leaf[p->fm[q]], b = p->cell_of_leaf[p->fp[q]];
+        p->cf_list[fill[a]++] = q;
+        p->cf_list[fill[b]++] = q;
+    }
+    for (int64_t q = 0; q < nb; q++) {
+        int64_t a = p->cell_of_leaf[p->bl[q]];
+        p->cf_list[fill[a]++] = -1 - q;
+    }
+    free(fill);
     return 0;
 }
 
@@ -559,6 +583,7 @@ void orc_destroy(orc_problem *p)
     if (!p) return;
     free(p->lv); free(p->cell_of_leaf); free(p->leaf_of_cell);
     free(p->fm); free(p->fp); free(p->fax); free(p->farea);
+    free(p->cf_start); free(p->cf_list);
     free(p->bl); free(p->bother); free(p->bax); free(p->bside); free(p->bkind); free(p->barea);
     free(p->xi); free(p->k);
     for (int d = 0; d < 3; d++) free(p->mirror[d]);
@@ -680,32 +705,39 @@ int orc_transport(orc_problem *p, double dt)
     int64_t nv = p->nv;
     double *fs = (double *)malloc((size_t)(p->ncells * nv) * sizeof(double));
     if (!fs) return -1;
-    memcpy(fs, p->f, (size_t)(p->ncells * nv) * sizeof(double));
     const double *f = p->f;
-#pragma omp parallel for schedule(static)
-    for (int64_t v = 0; v < nv; v++) {
-        for (int64_t q = 0; q < p->nf; q++) {
-            int d = p->fax[q];
-            int64_t a = p->cell_of_leaf[p->fm[q]], b = p->cell_of_leaf[p->fp[q]];
-            double Va = ldexp(1.0, -p->lv[p->fm[q]].lev * dim);
-            double Vb = ldexp(1.0, -p->lv[p->fp[q]].lev * dim);
-            double x = p->xi[3 * v + d];
-            double up = x > 0.0 ? f[a * nv + v] : f[b * nv + v];
-            double flux = x * p->farea[q] * up;
-            fs[a * nv + v] -= dt * flux / Va;
-            fs[b * nv + v] += dt * flux / Vb;
-        }
-        for (int64_t q = 0; q < p->nbf; q++) {
-            int d = p->bax[q];
-            int64_t a = p->cell_of_leaf[p->bl[q]];
-            double Va = ldexp(1.0, -p->lv[p->bl[q]].lev * dim);
-            double xn = (p->bside[q] ? 1.0 : -1.0) * p->xi[3 * v + d];
-            double up;
-            if (xn > 0.0) up = f[a * nv + v];
-            else if (p->bkind[q] == ORC_BC_INFLOW) up = p->finf[v];
-            else if (p->bkind[q] == ORC_BC_WALL) up = f[a * nv + p->mirror[d][v]];
-            else up = f[a * nv + v];
-            fs[a * nv + v] -= dt * xn * p->barea[q] * up / Va;
+#pragma omp parallel for schedule(dynamic, 8)
+    for (int64_t c = 0; c < p->ncells; c++) {
+        double *out = &fs[c * nv];
+        const double *own = &f[c * nv];
+        double V = ldexp(1.0, -p->lv[p->leaf_of_cell[c]].lev * dim);
+        for (int64_t v = 0; v < nv; v++) out[v] = own[v];
+        for (int64_t e = p->cf_start[c]; e < p->cf_start[c + 1]; e++) {
+            int64_t q = p->cf_list[e];
+            if (q >= 0) {
+                /* interior face: flux from minus to plus along +axis */
+                int d = p->fax[q];
+                int64_t a = p->cell_of_leaf[p->fm[q]], b = p->cell_of_leaf[p->fp[q]];
+                double sgn = (a == c) ? 1.0 : -1.0; /* outward normal of this cell */
+                for (int64_t v = 0; v < nv; v++) {
+                    double x = p->xi[3 * v + d];
+                    double up = x > 0.0 ? f[a * nv + v] : f[b * nv + v];
+                    double flux = x * p->farea[q] * up;
+                    out[v] -= sgn * dt * flux / V;
+                }
+            } else {
+                q = -1 - q;
+                int d = p->bax[q];
+                for (int64_t v = 0; v < nv; v++) {
+                    double xn = (p->bside[q] ? 1.0 : -1.0) * p->xi[3 * v + d];
+                    double up;
+                    if (xn > 0.0) up = own[v];
+                    else if (p->bkind[q] == ORC_BC_INFLOW) up = p->finf[v];
+                    else if (p->bkind[q] == ORC_BC_WALL) up = own[p->mirror[d][v]];
+                    else up = own[v];
+                    out[v] -= dt * xn * p->barea[q] * up / V;
+                }
+            }
         }
     }
     free(p->f);

@@ -1,0 +1,295 @@
+"""Python binding of libdvm: argument marshalling over the C ABI in include/dvm.h.
+
+Every step of the DVM path runs in the library's CUDA kernels; this module only
+loads libdvm.so (built in-tree by `_build.py`), converts numpy/torch buffers to
+pointers and raises on error codes.  There is no CPU fallback: if the shared
+library is missing or no CUDA device is present, construction raises.
+
+Paper: Zabelok, Arslanbekov, Kolobov, "Adaptive Kinetic-Fluid Solvers for
+Heterogeneous Computing Architectures" (Sec. 2.1 tree mesh, Sec. 3 DVM,
+Sec. 3.1 Eq. 2 advection, Sec. 3.2 Eqs. 3-6 collision integral).
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libdvm.so")
+
+F64, F32, BF16 = 0, 1, 2
+COLL_NONE, COLL_BGK, COLL_HS = 0, 1, 2
+BC_PERIODIC, BC_INFLOW, BC_OUTFLOW, BC_WALL = 0, 1, 2, 3
+PRED_NONE, PRED_BALL, PRED_SHELL = 0, 1, 2
+
+STATUS = {0: "DVM_OK", -1: "DVM_EINVAL", -2: "DVM_ENOMEM", -3: "DVM_ECUDA", -4: "DVM_ESTATE",
+          -5: "DVM_EUNSTABLE", -6: "DVM_EBOUNDS", -7: "DVM_ETIMEOUT", -9: "DVM_ENOTIMPL"}
+
+# every entry point declared in include/dvm.h
+EXPORTS = [
+    "dvm_create", "dvm_destroy", "dvm_last_error", "dvm_set_stream", "dvm_set_allocator",
+    "dvm_build_tree", "dvm_refine", "dvm_get_counts", "dvm_get_leaves", "dvm_get_faces",
+    "dvm_get_bfaces", "dvm_cell_centres", "dvm_set_velocity_grid", "dvm_get_velocities",
+    "dvm_set_freestream", "dvm_init_maxwellian", "dvm_get_f", "dvm_set_f", "dvm_upload_f",
+    "dvm_download_f", "dvm_f_device", "dvm_dt_cfl", "dvm_set_collision_tables", "dvm_step",
+    "dvm_moments", "dvm_step_moments", "dvm_launch_count",
+]
+
+
+class DvmError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s (%d): %s" % (STATUS.get(code, "?"), code, msg))
+        self.code = code
+
+
+class Config(C.Structure):
+    _fields_ = [("precision", C.c_int), ("collision", C.c_int), ("kn", C.c_double)]
+
+
+class TreeSpec(C.Structure):
+    _fields_ = [("dim", C.c_int), ("base_level", C.c_int), ("max_level", C.c_int),
+                ("pred", C.c_int), ("c", C.c_double * 3), ("r", C.c_double),
+                ("beta", C.c_double), ("solid", C.c_int), ("bc", C.c_int * 6)]
+
+
+def tree_spec(dim, base_level, max_level, pred=PRED_NONE, c=(0.5, 0.5, 0.5), r=0.0,
+              beta=0.0, solid=0, bc=(0,) * 6):
+    s = TreeSpec()
+    s.dim, s.base_level, s.max_level, s.pred = dim, base_level, max_level, pred
+    for d in range(3):
+        s.c[d] = c[d]
+    s.r, s.beta, s.solid = r, beta, int(solid)
+    for q in range(6):
+        s.bc[q] = bc[q]
+    return s
+
+
+_lib = None
+
+
+def lib():
+    """Load libdvm.so; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError("libdvm.so not built: run __graft_entry__.build() "
+                              "(or python -m paper_1503_00707_gb300._build)")
+        L = C.CDLL(LIB_PATH)
+        P, i64, d = C.c_void_p, C.c_int64, C.c_double
+        sig = {
+            "dvm_create": [C.POINTER(P), C.POINTER(Config)],
+            "dvm_destroy": [P],
+            "dvm_last_error": [P],
+            "dvm_set_stream": [P, P],
+            "dvm_set_allocator": [P, P, P, P],
+            "dvm_build_tree": [P, C.POINTER(TreeSpec)],
+            "dvm_refine": [P, P, i64],
+            "dvm_get_counts": [P, P, P, P, P, P],
+            "dvm_get_leaves": [P, P, P, P],
+            "dvm_get_faces": [P, P, P, P, P],
+            "dvm_get_bfaces": [P, P, P, P, P, P, P],
+            "dvm_cell_centres": [P, P, P],
+            "dvm_set_velocity_grid": [P, P, P, P],
+            "dvm_get_velocities": [P, P],
+            "dvm_set_freestream": [P, d, P, d],
+            "dvm_init_maxwellian": [P, C.c_int, P, P, P, P],
+            "dvm_get_f": [P, P, i64],
+            "dvm_set_f": [P, P, i64],
+            "dvm_upload_f": [P, P, i64],
+            "dvm_download_f": [P, P, i64],
+            "dvm_f_device": [P, P, P],
+            "dvm_dt_cfl": [P, d, P],
+            "dvm_set_collision_tables": [P, C.c_int, C.c_uint64],
+            "dvm_step": [P, C.c_int, d],
+            "dvm_moments": [P, P, P, P],
+            "dvm_step_moments": [P, P, P, P],
+            "dvm_launch_count": [P],
+        }
+        for name, args in sig.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = C.c_int
+        L.dvm_destroy.restype = None
+        L.dvm_last_error.restype = C.c_char_p
+        _lib = L
+    return _lib
+
+
+def _p(a):
+    return None if a is None else C.c_void_p(a.ctypes.data)
+
+
+class Solver:
+    """One DVM problem on the current CUDA device (thin wrapper over dvm_ctx)."""
+
+    def __init__(self, precision=F32, collision=COLL_BGK, kn=0.1, stream=None):
+        L = lib()
+        cfg = Config(precision, collision, kn)
+        h = C.c_void_p()
+        rc = L.dvm_create(C.byref(h), C.byref(cfg))
+        if rc:
+            raise DvmError(rc, "dvm_create failed (bad config)")
+        self._h = h
+        self.precision = precision
+        self.collision = collision
+        if stream is not None:
+            self.set_stream(stream)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().dvm_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _chk(self, rc):
+        if rc:
+            msg = lib().dvm_last_error(self._h)
+            raise DvmError(rc, msg.decode() if msg else "")
+
+    # ---- setup
+    def set_stream(self, stream):
+        """stream: a torch.cuda.Stream, an int handle, or None."""
+        handle = getattr(stream, "cuda_stream", stream)
+        self._chk(lib().dvm_set_stream(self._h, C.c_void_p(handle or 0)))
+
+    def build_tree(self, spec):
+        self._chk(lib().dvm_build_tree(self._h, C.byref(spec)))
+        self.counts()
+
+    def refine(self, flags):
+        flags = np.ascontiguousarray(flags, dtype=np.uint8)
+        self._chk(lib().dvm_refine(self._h, _p(flags), len(flags)))
+        self.counts()
+
+    def counts(self):
+        v = [C.c_int64() for _ in range(5)]
+        self._chk(lib().dvm_get_counts(self._h, *[C.byref(x) for x in v]))
+        self.nleaves, self.ncells, self.nfaces, self.nbfaces, self.nv = [x.value for x in v]
+        return self.nleaves, self.ncells, self.nfaces, self.nbfaces, self.nv
+
+    def leaves(self):
+        n = self.nleaves
+        keys, lev, sol = np.zeros(n, np.uint64), np.zeros(n, np.uint8), np.zeros(n, np.uint8)
+        self._chk(lib().dvm_get_leaves(self._h, _p(keys), _p(lev), _p(sol)))
+        return keys, lev, sol
+
+    def faces(self):
+        n = self.nfaces
+        m, p, ax, ar = np.zeros(n, np.int64), np.zeros(n, np.int64), np.zeros(n, np.uint8), np.zeros(n)
+        self._chk(lib().dvm_get_faces(self._h, _p(m), _p(p), _p(ax), _p(ar)))
+        return m, p, ax, ar
+
+    def bfaces(self):
+        n = self.nbfaces
+        leaf, ax, side, kind = np.zeros(n, np.int64), np.zeros(n, np.uint8), np.zeros(n, np.uint8), np.zeros(n, np.uint8)
+        other, ar = np.zeros(n, np.int64), np.zeros(n)
+        self._chk(lib().dvm_get_bfaces(self._h, _p(leaf), _p(ax), _p(side), _p(kind), _p(other), _p(ar)))
+        return leaf, ax, side, kind, other, ar
+
+    def centres(self):
+        xyz, h = np.zeros((self.ncells, 3)), np.zeros(self.ncells)
+        self._chk(lib().dvm_cell_centres(self._h, _p(xyz), _p(h)))
+        return xyz, h
+
+    def set_velocity_grid(self, n, lo, hi):
+        n = np.ascontiguousarray(n, dtype=np.int32)
+        lo = np.ascontiguousarray(lo, dtype=np.float64)
+        hi = np.ascontiguousarray(hi, dtype=np.float64)
+        self._chk(lib().dvm_set_velocity_grid(self._h, _p(n), _p(lo), _p(hi)))
+        self.counts()
+
+    def velocities(self):
+        xi = np.zeros((self.nv, 3))
+        self._chk(lib().dvm_get_velocities(self._h, _p(xi)))
+        return xi
+
+    def set_freestream(self, rho, u, T):
+        u = np.ascontiguousarray(u, dtype=np.float64)
+        self._chk(lib().dvm_set_freestream(self._h, float(rho), _p(u), float(T)))
+
+    def init_maxwellian(self, w, rho, u, T):
+        nc = self.ncells
+        w = np.ascontiguousarray(np.asarray(w, np.float64).reshape(nc, -1))
+        k = w.shape[1]
+        rho = np.ascontiguousarray(np.asarray(rho, np.float64).reshape(nc, k))
+        u = np.ascontiguousarray(np.asarray(u, np.float64).reshape(nc, k, 3))
+        T = np.ascontiguousarray(np.asarray(T, np.float64).reshape(nc, k))
+        self._chk(lib().dvm_init_maxwellian(self._h, k, _p(w), _p(rho), _p(u), _p(T)))
+
+    def set_collision_tables(self, trials, seed):
+        self._chk(lib().dvm_set_collision_tables(self._h, int(trials), int(seed)))
+
+    # ---- state
+    def get_f(self):
+        f = np.zeros((self.ncells, self.nv))
+        self._chk(lib().dvm_get_f(self._h, _p(f), f.size))
+        return f
+
+    def set_f(self, f):
+        f = np.ascontiguousarray(f, dtype=np.float64).reshape(self.ncells, self.nv)
+        self._chk(lib().dvm_set_f(self._h, _p(f), f.size))
+
+    def f_bytes(self):
+        ptr, nb = C.c_void_p(), C.c_int64()
+        self._chk(lib().dvm_f_device(self._h, C.byref(ptr), C.byref(nb)))
+        return nb.value
+
+    def f_device_ptr(self):
+        ptr, nb = C.c_void_p(), C.c_int64()
+        self._chk(lib().dvm_f_device(self._h, C.byref(ptr), C.byref(nb)))
+        return ptr.value, nb.value
+
+    def upload_f(self, host_ptr, nbytes):
+        """host_ptr: integer address of host memory in the storage format."""
+        self._chk(lib().dvm_upload_f(self._h, C.c_void_p(host_ptr), int(nbytes)))
+
+    def download_f(self, host_ptr, nbytes):
+        self._chk(lib().dvm_download_f(self._h, C.c_void_p(host_ptr), int(nbytes)))
+
+    def dt_cfl(self, cfl):
+        dt = C.c_double()
+        self._chk(lib().dvm_dt_cfl(self._h, float(cfl), C.byref(dt)))
+        return dt.value
+
+    def step(self, nsteps, dt):
+        self._chk(lib().dvm_step(self._h, int(nsteps), float(dt)))
+
+    def moments(self):
+        rho, u, T = np.zeros(self.ncells), np.zeros((self.ncells, 3)), np.zeros(self.ncells)
+        self._chk(lib().dvm_moments(self._h, _p(rho), _p(u), _p(T)))
+        return rho, u, T
+
+    def step_moments(self, out=None):
+        """Moments of the last step's f*; `out` (optional) is a (rho, u, T) tuple
+        of preallocated float64 arrays."""
+        if out is None:
+            out = (np.zeros(self.ncells), np.zeros((self.ncells, 3)), np.zeros(self.ncells))
+        self._chk(lib().dvm_step_moments(self._h, *[_p(a) for a in out]))
+        return out
+
+    @staticmethod
+    def launch_count():
+        n = C.c_int64()
+        rc = lib().dvm_launch_count(C.byref(n))
+        if rc:
+            raise DvmError(rc, "dvm_launch_count")
+        return n.value
+
+
+def solver_from_config(cfg, precision=None, collision=None, kn=None, stream=None):
+    """Build a Solver for one of the workload dictionaries (tree, velocity
+    grid, freestream), without initialising f."""
+    prec = {"f64": F64, "f32": F32, "bf16": BF16}[precision or cfg["precision"]] \
+        if not isinstance(precision, int) else precision
+    coll = cfg["coll"] if collision is None else collision
+    s = Solver(prec, coll, cfg["kn"] if kn is None else kn, stream=stream)
+    s.build_tree(tree_spec(cfg["dim"], cfg["base_level"], cfg["max_level"], cfg["pred"], cfg["c"],
+                           cfg["r"], cfg["beta"], cfg["solid"], cfg["bc"]))
+    s.set_velocity_grid(cfg["n"], cfg["lo"], cfg["hi"])
+    s.set_freestream(cfg["fs_rho"], cfg["fs_u"], cfg["fs_T"])
+    return s

@@ -1,0 +1,654 @@
+// C ABI of libdvm (declared in include/dvm.h): context, state checks, device
+// memory, host<->device transfers and the step loop.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/dvm.h"
+#include "hs.hpp"
+#include "kernels.hpp"
+#include "mesh.hpp"
+
+struct dvm_ctx {
+    dvm_config cfg{};
+    std::string err;
+    cudaStream_t stream = nullptr;
+    void *(*alloc_fn)(size_t, void *) = nullptr;
+    void (*free_fn)(void *, void *) = nullptr;
+    void *alloc_user = nullptr;
+    int state = 0;  // 0 created, 1 mesh, 2 velocity grid, 3 f set
+    dvm::Mesh mesh;
+    // velocity grid
+    int n[3] = {0, 0, 0}, half[3] = {0, 0, 0};
+    int nv = 0, P = 0;
+    double lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0}, hv[3] = {0, 0, 0}, dV = 0;
+    std::vector<double> xi;
+    double amag[96] = {0};
+    float amag_f[96] = {0};
+    double fs_rho = 1.0, fs_u[3] = {0, 0, 0}, fs_T = 1.0;
+    // device
+    void *d_f[2] = {nullptr, nullptr};
+    int cur = 0;
+    size_t f_elems = 0;
+    int32_t *d_src = nullptr;
+    void *d_w = nullptr;
+    uint8_t *d_cnt = nullptr;
+    void *d_invh = nullptr;
+    void *d_finf = nullptr;
+    double *d_amag = nullptr;
+    float *d_amag_f = nullptr;
+    double *d_xi = nullptr;
+    double *d_mom = nullptr;     // step moments [ncells][5]
+    double *d_mom2 = nullptr;    // moments of stored f
+    int *d_status = nullptr;
+    bool have_step_moments = false;
+    bool mesh_on_device = false;
+    dvm::HsTables hs;
+};
+
+namespace {
+
+int fail(dvm_ctx *c, int code, const std::string &msg)
+{
+    if (c) c->err = msg;
+    return code;
+}
+
+size_t elem_size(int prec) { return prec == DVM_F64 ? 8 : prec == DVM_F32 ? 4 : 2; }
+size_t tc_size(int prec) { return prec == DVM_F64 ? 8 : 4; }
+
+void *dev_alloc(dvm_ctx *c, size_t bytes)
+{
+    if (bytes == 0) bytes = 16;
+    if (c->alloc_fn) return c->alloc_fn(bytes, c->alloc_user);
+    void *p = nullptr;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return p;
+}
+
+void dev_free(dvm_ctx *c, void *&p)
+{
+    if (!p) return;
+    if (c->free_fn) c->free_fn(p, c->alloc_user);
+    else cudaFree(p);
+    p = nullptr;
+}
+
+template <typename T> T *dev_alloc_t(dvm_ctx *c, size_t count)
+{
+    return static_cast<T *>(dev_alloc(c, count * sizeof(T)));
+}
+
+int cuda_check(dvm_ctx *c, cudaError_t e, const char *what)
+{
+    if (e == cudaSuccess) return DVM_OK;
+    return fail(c, DVM_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+void free_mesh_buffers(dvm_ctx *c)
+{
+    dev_free(c, reinterpret_cast<void *&>(c->d_src));
+    dev_free(c, c->d_w);
+    dev_free(c, reinterpret_cast<void *&>(c->d_cnt));
+    dev_free(c, c->d_invh);
+}
+
+void free_grid_buffers(dvm_ctx *c)
+{
+    dev_free(c, c->d_f[0]);
+    dev_free(c, c->d_f[1]);
+    dev_free(c, c->d_finf);
+    dev_free(c, reinterpret_cast<void *&>(c->d_amag));
+    dev_free(c, reinterpret_cast<void *&>(c->d_amag_f));
+    dev_free(c, reinterpret_cast<void *&>(c->d_xi));
+    dev_free(c, reinterpret_cast<void *&>(c->d_mom));
+    dev_free(c, reinterpret_cast<void *&>(c->d_mom2));
+    c->f_elems = 0;
+    c->have_step_moments = false;
+}
+
+int64_t ncells_of(const dvm_ctx *c) { return (int64_t)c->mesh.leaf_of_cell.size(); }
+
+// The mesh is host work; the device is first touched by set_velocity_grid.
+int ensure_device(dvm_ctx *c)
+{
+    if (c->d_status) return DVM_OK;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+        cudaGetLastError();
+        return fail(c, DVM_ECUDA, "no CUDA device available");
+    }
+    if (cudaMalloc(&c->d_status, sizeof(int)) != cudaSuccess || cudaMemset(c->d_status, 0, sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        c->d_status = nullptr;
+        return fail(c, DVM_ECUDA, "device status word allocation failed");
+    }
+    return DVM_OK;
+}
+
+int upload_mesh(dvm_ctx *c)
+{
+    free_mesh_buffers(c);
+    const dvm::Mesh &m = c->mesh;
+    const int64_t nc = ncells_of(c);
+    const size_t tcs = tc_size(c->cfg.precision);
+    c->d_src = dev_alloc_t<int32_t>(c, nc * 24);
+    c->d_w = dev_alloc(c, nc * 24 * tcs);
+    c->d_cnt = dev_alloc_t<uint8_t>(c, nc * 8);
+    c->d_invh = dev_alloc(c, nc * tcs);
+    if (!c->d_src || !c->d_w || !c->d_cnt || !c->d_invh) return fail(c, DVM_ENOMEM, "device allocation (stencils)");
+    std::vector<double> invh(nc);
+    for (int64_t q = 0; q < nc; q++) invh[q] = std::ldexp(1.0, m.leaves[m.leaf_of_cell[q]].lev);
+    int rc = cuda_check(c, cudaMemcpy(c->d_src, m.st_src.data(), nc * 24 * sizeof(int32_t), cudaMemcpyHostToDevice), "copy stencils");
+    if (rc) return rc;
+    rc = cuda_check(c, cudaMemcpy(c->d_cnt, m.st_cnt.data(), nc * 8, cudaMemcpyHostToDevice), "copy stencil counts");
+    if (rc) return rc;
+    if (c->cfg.precision == DVM_F64) {
+        rc = cuda_check(c, cudaMemcpy(c->d_w, m.st_w.data(), nc * 24 * 8, cudaMemcpyHostToDevice), "copy weights");
+        if (rc) return rc;
+        rc = cuda_check(c, cudaMemcpy(c->d_invh, invh.data(), nc * 8, cudaMemcpyHostToDevice), "copy 1/h");
+    } else {
+        std::vector<float> w(m.st_w.begin(), m.st_w.end()), ih(invh.begin(), invh.end());
+        rc = cuda_check(c, cudaMemcpy(c->d_w, w.data(), nc * 24 * 4, cudaMemcpyHostToDevice), "copy weights");
+        if (rc) return rc;
+        rc = cuda_check(c, cudaMemcpy(c->d_invh, ih.data(), nc * 4, cudaMemcpyHostToDevice), "copy 1/h");
+    }
+    return rc;
+}
+
+double maxwellian(double rho, const double u[3], double T, const double *x)
+{
+    double d2 = 0.0;
+    for (int d = 0; d < 3; d++) d2 += (x[d] - u[d]) * (x[d] - u[d]);
+    const double tp = 2.0 * M_PI * T;
+    return rho / (tp * std::sqrt(tp)) * std::exp(-d2 / (2.0 * T));
+}
+
+int upload_freestream(dvm_ctx *c)
+{
+    if (!c->d_finf) return DVM_OK;
+    std::vector<double> m(c->nv);
+    for (int v = 0; v < c->nv; v++) m[v] = maxwellian(c->fs_rho, c->fs_u, c->fs_T, &c->xi[3 * v]);
+    if (c->cfg.precision == DVM_F64)
+        return cuda_check(c, cudaMemcpy(c->d_finf, m.data(), c->nv * 8, cudaMemcpyHostToDevice), "copy freestream");
+    std::vector<float> mf(m.begin(), m.end());
+    return cuda_check(c, cudaMemcpy(c->d_finf, mf.data(), c->nv * 4, cudaMemcpyHostToDevice), "copy freestream");
+}
+
+}  // namespace
+
+extern "C" {
+
+int dvm_create(dvm_ctx **out, const dvm_config *cfg)
+{
+    if (!out || !cfg) return DVM_EINVAL;
+    *out = nullptr;
+    if (cfg->precision < DVM_F64 || cfg->precision > DVM_BF16) return DVM_EINVAL;
+    if (cfg->collision < DVM_COLL_NONE || cfg->collision > DVM_COLL_HS) return DVM_EINVAL;
+    if (cfg->collision != DVM_COLL_NONE && !(cfg->kn > 0.0)) return DVM_EINVAL;
+    dvm_ctx *c = new (std::nothrow) dvm_ctx();
+    if (!c) return DVM_ENOMEM;
+    c->cfg = *cfg;
+    *out = c;
+    return DVM_OK;
+}
+
+void dvm_destroy(dvm_ctx *c)
+{
+    if (!c) return;
+    free_grid_buffers(c);
+    free_mesh_buffers(c);
+    dvm::hs_free(c->hs, [c](void *p) { void *q = p; dev_free(c, q); });
+    if (c->d_status) cudaFree(c->d_status);
+    delete c;
+}
+
+const char *dvm_last_error(const dvm_ctx *c) { return c ? c->err.c_str() : "null context"; }
+
+int dvm_set_stream(dvm_ctx *c, void *stream)
+{
+    if (!c) return DVM_EINVAL;
+    c->stream = static_cast<cudaStream_t>(stream);
+    return DVM_OK;
+}
+
+int dvm_set_allocator(dvm_ctx *c, void *(*alloc_fn)(size_t, void *), void (*free_fn)(void *, void *), void *user)
+{
+    if (!c) return DVM_EINVAL;
+    if (c->state != 0) return fail(c, DVM_ESTATE, "set the allocator before building the tree");
+    if ((alloc_fn == nullptr) != (free_fn == nullptr)) return fail(c, DVM_EINVAL, "give both allocator functions or neither");
+    c->alloc_fn = alloc_fn;
+    c->free_fn = free_fn;
+    c->alloc_user = user;
+    return DVM_OK;
+}
+
+static int after_mesh(dvm_ctx *c)
+{
+    free_grid_buffers(c);
+    free_mesh_buffers(c);
+    c->mesh_on_device = false;
+    c->state = 1;
+    if (c->nv > 0) {
+        int n[3] = {c->n[0], c->n[1], c->n[2]};
+        double lo[3] = {c->lo[0], c->lo[1], c->lo[2]}, hi[3] = {c->hi[0], c->hi[1], c->hi[2]};
+        return dvm_set_velocity_grid(c, n, lo, hi);
+    }
+    return DVM_OK;
+}
+
+int dvm_build_tree(dvm_ctx *c, const dvm_tree_spec *spec)
+{
+    if (!c || !spec) return DVM_EINVAL;
+    std::string err;
+    int rc = dvm::build_mesh(*spec, c->mesh, err);
+    if (rc) return fail(c, rc, err);
+    return after_mesh(c);
+}
+
+int dvm_refine(dvm_ctx *c, const uint8_t *flag, int64_t n)
+{
+    if (!c || !flag) return DVM_EINVAL;
+    if (c->state < 1) return fail(c, DVM_ESTATE, "build the tree first");
+    std::string err;
+    int rc = dvm::refine_mesh(c->mesh, flag, n, err);
+    if (rc) return fail(c, rc, err);
+    return after_mesh(c);
+}
+
+int dvm_get_counts(const dvm_ctx *c, int64_t *nleaves, int64_t *ncells, int64_t *nfaces, int64_t *nbfaces, int64_t *nv)
+{
+    if (!c) return DVM_EINVAL;
+    if (nleaves) *nleaves = (int64_t)c->mesh.leaves.size();
+    if (ncells) *ncells = ncells_of(c);
+    if (nfaces) *nfaces = (int64_t)c->mesh.fm.size();
+    if (nbfaces) *nbfaces = (int64_t)c->mesh.bl.size();
+    if (nv) *nv = c->nv;
+    return DVM_OK;
+}
+
+int dvm_get_leaves(const dvm_ctx *c, uint64_t *keys, uint8_t *levels, uint8_t *solid)
+{
+    if (!c) return DVM_EINVAL;
+    if (c->state < 1) return DVM_ESTATE;
+    for (size_t q = 0; q < c->mesh.leaves.size(); q++) {
+        if (keys) keys[q] = c->mesh.leaves[q].key;
+        if (levels) levels[q] = (uint8_t)c->mesh.leaves[q].lev;
+        if (solid) solid[q] = c->mesh.leaves[q].solid;
+    }
+    return DVM_OK;
+}
+
+int dvm_get_faces(const dvm_ctx *c, int64_t *minus, int64_t *plus, uint8_t *axis, double *area)
+{
+    if (!c) return DVM_EINVAL;
+    if (c->state < 1) return DVM_ESTATE;
+    const dvm::Mesh &m = c->mesh;
+    for (size_t q = 0; q < m.fm.size(); q++) {
+        if (minus) minus[q] = m.fm[q];
+        if (plus) plus[q] = m.fp[q];
+        if (axis) axis[q] = m.fax[q];
+        if (area) area[q] = m.farea[q];
+    }
+    return DVM_OK;
+}
+
+int dvm_get_bfaces(const dvm_ctx *c, int64_t *leaf, uint8_t *axis, uint8_t *side, uint8_t *kind, int64_t *other, double *area)
+{
+    if (!c) return DVM_EINVAL;
+    if (c->state < 1) return DVM_ESTATE;
+    const dvm::Mesh &m = c->mesh;
+    for (size_t q = 0; q < m.bl.size(); q++) {
+        if (leaf) leaf[q] = m.bl[q];
+        if (axis) axis[q] = m.bax[q];
+        if (side) side[q] = m.bside[q];
+        if (kind) kind[q] = m.bkind[q];
+        if (other) other[q] = m.bother[q];
+        if (area) area[q] = m.barea[q];
+    }
+    return DVM_OK;
+}
+
+int dvm_cell_centres(const dvm_ctx *c, double *xyz, double *h)
+{
+    if (!c || !xyz) return DVM_EINVAL;
+    if (c->state < 1) return DVM_ESTATE;
+    const dvm::Mesh &m = c->mesh;
+    for (size_t q = 0; q < m.leaf_of_cell.size(); q++) {
+        const dvm::Leaf &x = m.leaves[m.leaf_of_cell[q]];
+        const double hh = std::ldexp(1.0, -x.lev);
+        for (int d = 0; d < 3; d++) xyz[3 * q + d] = d < m.spec.dim ? (x.i[d] + 0.5) * hh : 0.5;
+        if (h) h[q] = hh;
+    }
+    return DVM_OK;
+}
+
+int dvm_set_velocity_grid(dvm_ctx *c, const int n[3], const double lo[3], const double hi[3])
+{
+    if (!c || !n || !lo || !hi) return DVM_EINVAL;
+    if (c->state < 1) return fail(c, DVM_ESTATE, "build the tree first");
+    const int vec = c->cfg.precision == DVM_F64 ? 2 : 4;
+    for (int d = 0; d < 3; d++) {
+        if (n[d] < 2 || n[d] % 2 || n[d] > 64) return fail(c, DVM_EINVAL, "each n must be even and at most 64");
+        if (!(hi[d] > 0.0) || lo[d] != -hi[d]) return fail(c, DVM_EINVAL, "the velocity grid must be symmetric (lo = -hi)");
+    }
+    if ((n[2] / 2) % vec) return fail(c, DVM_EINVAL, "nz/2 must be a multiple of the vector width");
+    int drc = ensure_device(c);
+    if (drc) return drc;
+    if (!c->mesh_on_device) {
+        drc = upload_mesh(c);
+        if (drc) return drc;
+        c->mesh_on_device = true;
+    }
+    free_grid_buffers(c);
+    for (int d = 0; d < 3; d++) {
+        c->n[d] = n[d];
+        c->half[d] = n[d] / 2;
+        c->lo[d] = lo[d];
+        c->hi[d] = hi[d];
+        c->hv[d] = (hi[d] - lo[d]) / n[d];
+    }
+    c->dV = c->hv[0] * c->hv[1] * c->hv[2];
+    c->nv = n[0] * n[1] * n[2];
+    c->P = c->nv / 8;
+    // node values lo + (k + 1/2) h in sign-group order
+    c->xi.assign(3 * (size_t)c->nv, 0.0);
+    int v = 0;
+    for (int o = 0; o < 8; o++)
+        for (int mx = 0; mx < c->half[0]; mx++)
+            for (int my = 0; my < c->half[1]; my++)
+                for (int mz = 0; mz < c->half[2]; mz++, v++) {
+                    const int m3[3] = {mx, my, mz};
+                    for (int d = 0; d < 3; d++) {
+                        const bool pos = (o >> (2 - d)) & 1;
+                        const int k = pos ? c->half[d] + m3[d] : c->half[d] - 1 - m3[d];
+                        c->xi[3 * (size_t)v + d] = c->lo[d] + ((double)k + 0.5) * c->hv[d];
+                    }
+                }
+    for (int d = 0; d < 3; d++)
+        for (int m = 0; m < 32; m++) {
+            const double val = m < c->half[d] ? c->lo[d] + ((double)(c->half[d] + m) + 0.5) * c->hv[d] : 0.0;
+            c->amag[32 * d + m] = val;
+            c->amag_f[32 * d + m] = (float)val;
+        }
+    const int64_t nc = ncells_of(c);
+    c->f_elems = (size_t)nc * c->nv;
+    const size_t fb = c->f_elems * elem_size(c->cfg.precision);
+    c->d_f[0] = dev_alloc(c, fb);
+    c->d_f[1] = dev_alloc(c, fb);
+    c->d_finf = dev_alloc(c, c->nv * tc_size(c->cfg.precision));
+    c->d_amag = dev_alloc_t<double>(c, 96);
+    c->d_amag_f = dev_alloc_t<float>(c, 96);
+    c->d_xi = dev_alloc_t<double>(c, 3 * (size_t)c->nv);
+    c->d_mom = dev_alloc_t<double>(c, 5 * (size_t)nc);
+    c->d_mom2 = dev_alloc_t<double>(c, 5 * (size_t)nc);
+    if (!c->d_f[0] || !c->d_f[1] || !c->d_finf || !c->d_amag || !c->d_amag_f || !c->d_xi || !c->d_mom || !c->d_mom2) {
+        free_grid_buffers(c);
+        return fail(c, DVM_ENOMEM, "device allocation (f buffers)");
+    }
+    int rc = cuda_check(c, cudaMemcpy(c->d_amag, c->amag, sizeof c->amag, cudaMemcpyHostToDevice), "copy |xi|");
+    if (!rc) rc = cuda_check(c, cudaMemcpy(c->d_amag_f, c->amag_f, sizeof c->amag_f, cudaMemcpyHostToDevice), "copy |xi|");
+    if (!rc) rc = cuda_check(c, cudaMemcpy(c->d_xi, c->xi.data(), c->xi.size() * 8, cudaMemcpyHostToDevice), "copy xi");
+    if (!rc) rc = upload_freestream(c);
+    if (rc) return rc;
+    c->cur = 0;
+    c->state = 2;
+    return DVM_OK;
+}
+
+int dvm_get_velocities(const dvm_ctx *c, double *xi)
+{
+    if (!c || !xi) return DVM_EINVAL;
+    if (c->state < 2) return DVM_ESTATE;
+    std::memcpy(xi, c->xi.data(), c->xi.size() * sizeof(double));
+    return DVM_OK;
+}
+
+int dvm_set_freestream(dvm_ctx *c, double rho, const double u[3], double T)
+{
+    if (!c || !u || !(rho > 0.0) || !(T > 0.0)) return DVM_EINVAL;
+    c->fs_rho = rho;
+    c->fs_T = T;
+    for (int d = 0; d < 3; d++) c->fs_u[d] = u[d];
+    return upload_freestream(c);
+}
+
+int dvm_init_maxwellian(dvm_ctx *c, int nmix, const double *w, const double *rho, const double *u, const double *T)
+{
+    if (!c || nmix < 1 || !w || !rho || !u || !T) return DVM_EINVAL;
+    if (c->state < 2) return fail(c, DVM_ESTATE, "set the velocity grid first");
+    const int64_t nc = ncells_of(c);
+    const size_t k = (size_t)nc * nmix;
+    for (size_t q = 0; q < k; q++)
+        if (!(rho[q] >= 0.0) || !(T[q] > 0.0)) return fail(c, DVM_EINVAL, "need rho >= 0 and T > 0");
+    double *dw = dev_alloc_t<double>(c, k), *dr = dev_alloc_t<double>(c, k);
+    double *du = dev_alloc_t<double>(c, 3 * k), *dT = dev_alloc_t<double>(c, k);
+    int rc = DVM_OK;
+    if (!dw || !dr || !du || !dT) rc = fail(c, DVM_ENOMEM, "device allocation (init)");
+    if (!rc) rc = cuda_check(c, cudaMemcpy(dw, w, k * 8, cudaMemcpyHostToDevice), "copy w");
+    if (!rc) rc = cuda_check(c, cudaMemcpy(dr, rho, k * 8, cudaMemcpyHostToDevice), "copy rho");
+    if (!rc) rc = cuda_check(c, cudaMemcpy(du, u, 3 * k * 8, cudaMemcpyHostToDevice), "copy u");
+    if (!rc) rc = cuda_check(c, cudaMemcpy(dT, T, k * 8, cudaMemcpyHostToDevice), "copy T");
+    if (!rc) rc = dvm::launch_init_maxwellian(c->cfg.precision, c->d_f[c->cur], nc, c->nv, nmix, dw, dr, du, dT, c->d_xi, c->stream);
+    if (!rc) rc = cuda_check(c, cudaStreamSynchronize(c->stream), "init_maxwellian");
+    void *p;
+    p = dw; dev_free(c, p);
+    p = dr; dev_free(c, p);
+    p = du; dev_free(c, p);
+    p = dT; dev_free(c, p);
+    if (!rc) {
+        c->state = 3;
+        c->have_step_moments = false;
+    }
+    return rc;
+}
+
+static int convert_chunks(dvm_ctx *c, double *host_out, const double *host_in, int64_t count)
+{
+    const int64_t total = (int64_t)c->f_elems;
+    if (count != total) return fail(c, DVM_EINVAL, "count must be ncells*nv");
+    const int64_t chunk = std::min<int64_t>(total, 1 << 24);
+    double *stage = dev_alloc_t<double>(c, chunk);
+    if (!stage) return fail(c, DVM_ENOMEM, "device allocation (staging)");
+    const size_t es = elem_size(c->cfg.precision);
+    int rc = DVM_OK;
+    for (int64_t s = 0; s < total && !rc; s += chunk) {
+        const int64_t n = std::min(chunk, total - s);
+        char *fdev = static_cast<char *>(c->d_f[c->cur]) + s * es;
+        if (host_out) {
+            rc = dvm::launch_to_f64(c->cfg.precision, fdev, stage, n, c->stream);
+            if (!rc) rc = cuda_check(c, cudaMemcpyAsync(host_out + s, stage, n * 8, cudaMemcpyDeviceToHost, c->stream), "copy f");
+        } else {
+            rc = cuda_check(c, cudaMemcpyAsync(stage, host_in + s, n * 8, cudaMemcpyHostToDevice, c->stream), "copy f");
+            if (!rc) rc = dvm::launch_from_f64(c->cfg.precision, stage, fdev, n, c->stream);
+        }
+        if (!rc) rc = cuda_check(c, cudaStreamSynchronize(c->stream), "convert f");
+    }
+    void *p = stage;
+    dev_free(c, p);
+    return rc;
+}
+
+int dvm_get_f(dvm_ctx *c, double *f, int64_t count)
+{
+    if (!c || !f) return DVM_EINVAL;
+    if (c->state < 3) return fail(c, DVM_ESTATE, "f is not set");
+    return convert_chunks(c, f, nullptr, count);
+}
+
+int dvm_set_f(dvm_ctx *c, const double *f, int64_t count)
+{
+    if (!c || !f) return DVM_EINVAL;
+    if (c->state < 2) return fail(c, DVM_ESTATE, "set the velocity grid first");
+    int rc = convert_chunks(c, nullptr, f, count);
+    if (!rc) {
+        c->state = 3;
+        c->have_step_moments = false;
+    }
+    return rc;
+}
+
+int dvm_upload_f(dvm_ctx *c, const void *host, int64_t bytes)
+{
+    if (!c || !host) return DVM_EINVAL;
+    if (c->state < 2) return fail(c, DVM_ESTATE, "set the velocity grid first");
+    if ((size_t)bytes != c->f_elems * elem_size(c->cfg.precision)) return fail(c, DVM_EINVAL, "byte count differs from the f buffer");
+    int rc = cuda_check(c, cudaMemcpyAsync(c->d_f[c->cur], host, bytes, cudaMemcpyHostToDevice, c->stream), "upload f");
+    if (!rc) {
+        c->state = 3;
+        c->have_step_moments = false;
+    }
+    return rc;
+}
+
+int dvm_download_f(dvm_ctx *c, void *host, int64_t bytes)
+{
+    if (!c || !host) return DVM_EINVAL;
+    if (c->state < 3) return fail(c, DVM_ESTATE, "f is not set");
+    if ((size_t)bytes != c->f_elems * elem_size(c->cfg.precision)) return fail(c, DVM_EINVAL, "byte count differs from the f buffer");
+    int rc = cuda_check(c, cudaMemcpyAsync(host, c->d_f[c->cur], bytes, cudaMemcpyDeviceToHost, c->stream), "download f");
+    if (!rc) rc = cuda_check(c, cudaStreamSynchronize(c->stream), "download f");
+    return rc;
+}
+
+int dvm_f_device(const dvm_ctx *c, void **ptr, int64_t *bytes)
+{
+    if (!c || !ptr) return DVM_EINVAL;
+    if (c->state < 2) return DVM_ESTATE;
+    *ptr = c->d_f[c->cur];
+    if (bytes) *bytes = (int64_t)(c->f_elems * elem_size(c->cfg.precision));
+    return DVM_OK;
+}
+
+int dvm_dt_cfl(const dvm_ctx *c, double cfl, double *dt)
+{
+    if (!c || !dt || !(cfl > 0.0)) return DVM_EINVAL;
+    if (c->state < 2) return DVM_ESTATE;
+    double smax = 0.0;
+    for (int v = 0; v < c->nv; v++) {
+        double s = 0.0;
+        for (int d = 0; d < c->mesh.spec.dim; d++) s += std::fabs(c->xi[3 * (size_t)v + d]);
+        smax = std::max(smax, s);
+    }
+    *dt = cfl * std::ldexp(1.0, -c->mesh.max_cell_level) / smax;
+    return DVM_OK;
+}
+
+int dvm_set_collision_tables(dvm_ctx *c, int trials, uint64_t seed)
+{
+    if (!c || trials < 1) return DVM_EINVAL;
+    if (c->state < 2) return fail(c, DVM_ESTATE, "set the velocity grid first");
+    std::string err;
+    int rc = dvm::hs_build(c->hs, c->n, c->lo, c->hv, c->xi, trials, seed, err,
+                           [c](size_t b) { return dev_alloc(c, b); },
+                           [c](void *p) { void *q = p; dev_free(c, q); });
+    if (rc) return fail(c, rc, err);
+    return DVM_OK;
+}
+
+int dvm_step(dvm_ctx *c, int nsteps, double dt)
+{
+    if (!c || nsteps < 0) return DVM_EINVAL;
+    if (c->state < 3) return fail(c, DVM_ESTATE, "f is not set");
+    if (!(dt > 0.0) || !std::isfinite(dt)) return fail(c, DVM_EINVAL, "dt must be positive");
+    if (c->cfg.collision == DVM_COLL_HS && !c->hs.ready) return fail(c, DVM_ESTATE, "set the collision tables first");
+    dvm::StepParams p{};
+    p.dim = c->mesh.spec.dim;
+    p.prec = c->cfg.precision;
+    p.coll = c->cfg.collision == DVM_COLL_HS ? DVM_COLL_NONE : c->cfg.collision;
+    p.ncells = ncells_of(c);
+    p.nv = c->nv;
+    p.P = c->P;
+    for (int d = 0; d < 3; d++) { p.half[d] = c->half[d]; p.n[d] = c->n[d]; p.hv[d] = c->hv[d]; }
+    p.st_src = c->d_src;
+    p.st_w = c->d_w;
+    p.st_cnt = c->d_cnt;
+    p.inv_h = c->d_invh;
+    p.finf = c->d_finf;
+    p.amag = c->d_amag;
+    p.amag_f = c->d_amag_f;
+    p.dt = dt;
+    p.kn = c->cfg.kn;
+    p.dV = c->dV;
+    p.mom_out = c->d_mom;
+    p.status = c->d_status;
+    p.stream = c->stream;
+    if (c->cfg.collision == DVM_COLL_HS) {
+        int rc = dvm::hs_prepare(c->hs, p.ncells, [c](size_t b) { return dev_alloc(c, b); },
+                                 [c](void *q) { void *r = q; dev_free(c, r); });
+        if (rc) return fail(c, rc, "hard-sphere scratch allocation failed");
+    }
+    for (int s = 0; s < nsteps; s++) {
+        p.f_in = c->d_f[c->cur];
+        p.f_out = c->d_f[1 - c->cur];
+        int rc = dvm::launch_step(p);
+        if (rc) return fail(c, rc, rc == DVM_ENOTIMPL ? "velocity grid too large for the step kernel" : "step launch failed");
+        if (c->cfg.collision == DVM_COLL_HS) {
+            rc = dvm::launch_hs_collide(c->hs, p, c->d_f[1 - c->cur], c->cfg.kn, dt);
+            if (rc) return fail(c, rc, "hard-sphere collision launch failed");
+        }
+        c->cur = 1 - c->cur;
+    }
+    c->have_step_moments = nsteps > 0 || c->have_step_moments;
+    int st = 0;
+    int rc = cuda_check(c, cudaMemcpyAsync(&st, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "read status");
+    if (!rc) rc = cuda_check(c, cudaStreamSynchronize(c->stream), "step");
+    if (rc) return rc;
+    if (st) {
+        cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream);
+        std::string why;
+        if (st & dvm::ST_NONPOS) why += " non-positive density or temperature;";
+        if (st & dvm::ST_SINGULAR) why += " singular correction system;";
+        if (st & dvm::ST_NUDT) why += " relaxation factor above 1 (dt too large for Kn);";
+        return fail(c, DVM_EUNSTABLE, "unstable step:" + why);
+    }
+    return DVM_OK;
+}
+
+static int copy_moments(dvm_ctx *c, const double *dsrc, double *rho, double *u, double *T)
+{
+    const int64_t nc = ncells_of(c);
+    std::vector<double> h(5 * (size_t)nc);
+    int rc = cuda_check(c, cudaMemcpyAsync(h.data(), dsrc, h.size() * 8, cudaMemcpyDeviceToHost, c->stream), "copy moments");
+    if (!rc) rc = cuda_check(c, cudaStreamSynchronize(c->stream), "moments");
+    if (rc) return rc;
+    for (int64_t q = 0; q < nc; q++) {
+        if (rho) rho[q] = h[5 * q];
+        if (u) for (int d = 0; d < 3; d++) u[3 * q + d] = h[5 * q + 1 + d];
+        if (T) T[q] = h[5 * q + 4];
+    }
+    return DVM_OK;
+}
+
+int dvm_moments(dvm_ctx *c, double *rho, double *u, double *T)
+{
+    if (!c) return DVM_EINVAL;
+    if (c->state < 3) return fail(c, DVM_ESTATE, "f is not set");
+    int rc = dvm::launch_moments(c->cfg.precision, c->d_f[c->cur], ncells_of(c), c->nv, c->d_xi, c->dV, c->d_mom2, c->stream);
+    if (rc) return fail(c, rc, "moments launch failed");
+    return copy_moments(c, c->d_mom2, rho, u, T);
+}
+
+int dvm_step_moments(dvm_ctx *c, double *rho, double *u, double *T)
+{
+    if (!c) return DVM_EINVAL;
+    if (!c->have_step_moments) return fail(c, DVM_ESTATE, "no step has run since f was set");
+    return copy_moments(c, c->d_mom, rho, u, T);
+}
+
+int dvm_launch_count(int64_t *count)
+{
+    if (!count) return DVM_EINVAL;
+    *count = dvm::launches_issued();
+    return DVM_OK;
+}
+
+}  // extern "C"

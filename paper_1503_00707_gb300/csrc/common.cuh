@@ -1,0 +1,169 @@
+// Device helpers shared by the step kernels: vectorised storage access,
+// double-float accumulation and warp reductions.
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <cstdint>
+
+namespace dvm {
+
+// ---------------------------------------------------------------- storage
+// One "quad" is the unit a thread loads: 16 bytes of FP32 (4 values) or FP64
+// (2 values), or 8 bytes of BF16 (4 values).  Loads go through the read-only
+// path; stores stream (evict-first) so that L2 keeps the upwind neighbours.
+template <typename TS> struct Store;
+
+template <> struct Store<double> {
+    static constexpr int VEC = 2;
+    using TC = double;
+    __device__ static inline void load(const double *p, double v[2])
+    {
+        const double2 t = __ldg(reinterpret_cast<const double2 *>(p));
+        v[0] = t.x; v[1] = t.y;
+    }
+    __device__ static inline void store(double *p, const double v[2])
+    {
+        __stcs(reinterpret_cast<double2 *>(p), make_double2(v[0], v[1]));
+    }
+};
+
+template <> struct Store<float> {
+    static constexpr int VEC = 4;
+    using TC = float;
+    __device__ static inline void load(const float *p, float v[4])
+    {
+        const float4 t = __ldg(reinterpret_cast<const float4 *>(p));
+        v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+    }
+    __device__ static inline void store(float *p, const float v[4])
+    {
+        __stcs(reinterpret_cast<float4 *>(p), make_float4(v[0], v[1], v[2], v[3]));
+    }
+};
+
+template <> struct Store<__nv_bfloat16> {
+    static constexpr int VEC = 4;
+    using TC = float;
+    __device__ static inline void load(const __nv_bfloat16 *p, float v[4])
+    {
+        const uint2 raw = __ldg(reinterpret_cast<const uint2 *>(p));
+        __nv_bfloat162 a = *reinterpret_cast<const __nv_bfloat162 *>(&raw.x);
+        __nv_bfloat162 b = *reinterpret_cast<const __nv_bfloat162 *>(&raw.y);
+        const float2 fa = __bfloat1622float2(a), fb = __bfloat1622float2(b);
+        v[0] = fa.x; v[1] = fa.y; v[2] = fb.x; v[3] = fb.y;
+    }
+    __device__ static inline void store(__nv_bfloat16 *p, const float v[4])
+    {
+        __nv_bfloat162 a = __floats2bfloat162_rn(v[0], v[1]);
+        __nv_bfloat162 b = __floats2bfloat162_rn(v[2], v[3]);
+        uint2 raw;
+        raw.x = *reinterpret_cast<const uint32_t *>(&a);
+        raw.y = *reinterpret_cast<const uint32_t *>(&b);
+        __stcs(reinterpret_cast<uint2 *>(p), raw);
+    }
+};
+
+// ---------------------------------------------------------------- double-float
+// An unevaluated sum hi + lo of two FP32 numbers (Dekker/Knuth).  Addition
+// uses the branch-free TwoSum; a product of two floats is split exactly with
+// one FMA.  About 48 significant bits, enough for FP64-class moment sums
+// without FP64 arithmetic per element.
+struct FF {
+    float hi, lo;
+};
+
+__device__ inline FF ff_make(float a) { return {a, 0.0f}; }
+
+__device__ inline FF ff_add(FF a, FF b)
+{
+    const float s = a.hi + b.hi;
+    const float bb = s - a.hi;
+    float e = (a.hi - (s - bb)) + (b.hi - bb);
+    e += a.lo;
+    e += b.lo;
+    const float h = s + e;
+    return {h, e - (h - s)};
+}
+
+__device__ inline FF ff_prod(float a, float b)
+{
+    const float p = a * b;
+    return {p, fmaf(a, b, -p)};
+}
+
+__device__ inline double ff_to_double(FF a) { return (double)a.hi + (double)a.lo; }
+
+template <typename TC> struct Red;
+
+template <> struct Red<float> {
+    using T = FF;
+    __device__ static inline T zero() { return {0.0f, 0.0f}; }
+    __device__ static inline T from(float a) { return ff_make(a); }
+    __device__ static inline T mul(float a, float b) { return ff_prod(a, b); }
+    __device__ static inline T add(T a, T b) { return ff_add(a, b); }
+    __device__ static inline T shfl_down(T a, int off)
+    {
+        return {__shfl_down_sync(0xffffffffu, a.hi, off), __shfl_down_sync(0xffffffffu, a.lo, off)};
+    }
+    __device__ static inline double to_double(T a) { return ff_to_double(a); }
+};
+
+template <> struct Red<double> {
+    using T = double;
+    __device__ static inline T zero() { return 0.0; }
+    __device__ static inline T from(double a) { return a; }
+    __device__ static inline T mul(double a, double b) { return a * b; }
+    __device__ static inline T add(T a, T b) { return a + b; }
+    __device__ static inline T shfl_down(T a, int off) { return __shfl_down_sync(0xffffffffu, a, off); }
+    __device__ static inline double to_double(T a) { return a; }
+};
+
+__device__ inline double warp_allsum(double v)
+{
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    return v;
+}
+
+// Gaussian elimination with partial pivoting, n = 5, FP64.  Returns false if
+// a pivot is zero or a result is not finite.
+__device__ inline bool solve5(double A[25], double b[5], double x[5])
+{
+#pragma unroll
+    for (int c = 0; c < 5; c++) {
+        int piv = c;
+        double best = fabs(A[c * 5 + c]);
+#pragma unroll
+        for (int r = c + 1; r < 5; r++) {
+            const double v = fabs(A[r * 5 + c]);
+            if (v > best) { best = v; piv = r; }
+        }
+        if (!(best > 0.0) || !isfinite(best)) return false;
+        if (piv != c) {
+#pragma unroll
+            for (int q = 0; q < 5; q++) {
+                const double t = A[c * 5 + q]; A[c * 5 + q] = A[piv * 5 + q]; A[piv * 5 + q] = t;
+            }
+            const double t = b[c]; b[c] = b[piv]; b[piv] = t;
+        }
+        const double inv = 1.0 / A[c * 5 + c];
+#pragma unroll
+        for (int r = c + 1; r < 5; r++) {
+            const double m = A[r * 5 + c] * inv;
+#pragma unroll
+            for (int q = c; q < 5; q++) A[r * 5 + q] -= m * A[c * 5 + q];
+            b[r] -= m * b[c];
+        }
+    }
+#pragma unroll
+    for (int r = 4; r >= 0; r--) {
+        double s = b[r];
+#pragma unroll
+        for (int q = r + 1; q < 5; q++) s -= A[r * 5 + q] * x[q];
+        x[r] = s / A[r * 5 + r];
+        if (!isfinite(x[r])) return false;
+    }
+    return true;
+}
+
+}  // namespace dvm

@@ -1,0 +1,121 @@
+// Host construction of the hard-sphere trial tables for Eqs. 3-5.
+//
+// For node i and trial k (stream index s = i*M + k, SplitMix64 draws 3s,
+// 3s+1, 3s+2): the partner gamma is uniform over the Nv nodes; the unit
+// vector omega has z = 2u - 1 and azimuth 2 pi u'.  The post-collision pair
+// xi' = c + |g| omega / 2, xi'_* = c - |g| omega / 2 around the pair's mean c
+// is snapped to the nearest nodes l, m (round half away from zero); a trial
+// whose l or m falls off the grid contributes nothing.  The weights
+// b = c = Nv dV |g| / (sqrt(2) M) are the Monte-Carlo weights of the
+// hard-sphere integral (1/(4 sqrt(2) pi)) int int (f'f'_* - f f_*)|g| dOmega
+// dxi_*, normalised so that a unit Maxwellian has mean collision frequency
+// sqrt(8/pi) (mean free path Kn).
+#include "hs.hpp"
+
+#include <cmath>
+#include <cstring>
+
+#include "../../include/dvm.h"
+
+namespace dvm {
+
+uint64_t splitmix64_at(uint64_t seed, uint64_t n)
+{
+    uint64_t x = seed + (n + 1) * 0x9E3779B97F4A7C15ull;
+    x ^= x >> 30;
+    x *= 0xBF58476D1CE4E5B9ull;
+    x ^= x >> 27;
+    x *= 0x94D049BB133111EBull;
+    x ^= x >> 31;
+    return x;
+}
+
+static double uniform01(uint64_t seed, uint64_t n)
+{
+    return std::ldexp((double)(splitmix64_at(seed, n) >> 11), -53);
+}
+
+void hs_free(HsTables &t, const DevFree &dfree)
+{
+    if (t.dev) dfree(t.dev);
+    if (t.d_corr) dfree(t.d_corr);
+    if (t.d_bc) dfree(t.d_bc);
+    t.dev = nullptr;
+    t.d_corr = nullptr;
+    t.d_bc = nullptr;
+    t.bc_cells = 0;
+    t.ready = false;
+}
+
+int hs_build(HsTables &t, const int n[3], const double lo[3], const double h[3],
+             const std::vector<double> &xi, int trials, uint64_t seed, std::string &err,
+             const DevAlloc &alloc, const DevFree &dfree)
+{
+    hs_free(t, dfree);
+    const int nv = n[0] * n[1] * n[2];
+    if (nv > 65535) { err = "hard-sphere tables need Nv < 65536"; return DVM_ENOTIMPL; }
+    // natural (kx, ky, kz) -> storage index
+    std::vector<int32_t> where((size_t)nv, -1);
+    for (int v = 0; v < nv; v++) {
+        int k[3];
+        for (int d = 0; d < 3; d++) k[d] = (int)std::lround((xi[3 * (size_t)v + d] - lo[d]) / h[d] - 0.5);
+        where[((size_t)k[0] * n[1] + k[1]) * n[2] + k[2]] = v;
+    }
+    const double dV = h[0] * h[1] * h[2];
+    const double scale = (double)nv * dV / (std::sqrt(2.0) * (double)trials);
+    t.host.assign((size_t)trials * nv * 4, 0u);
+    t.discarded = 0;
+    for (int i = 0; i < nv; i++) {
+        const double *a = &xi[3 * (size_t)i];
+        for (int k = 0; k < trials; k++) {
+            const uint64_t s = (uint64_t)i * (uint64_t)trials + (uint64_t)k;
+            const double u0 = uniform01(seed, 3 * s), u1 = uniform01(seed, 3 * s + 1), u2 = uniform01(seed, 3 * s + 2);
+            const int gam = (int)(u0 * (double)nv);
+            const double *b = &xi[3 * (size_t)gam];
+            double g2 = 0.0;
+            for (int d = 0; d < 3; d++) g2 += (a[d] - b[d]) * (a[d] - b[d]);
+            const double gn = std::sqrt(g2);
+            const double z = 2.0 * u1 - 1.0, phi = 2.0 * M_PI * u2;
+            const double st = std::sqrt(std::fmax(0.0, 1.0 - z * z));
+            const double om[3] = {st * std::cos(phi), st * std::sin(phi), z};
+            int kp[3], kq[3];
+            bool ok = true;
+            for (int d = 0; d < 3 && ok; d++) {
+                const double mid = 0.5 * (a[d] + b[d]);
+                const double xp = mid + 0.5 * gn * om[d], xq = mid - 0.5 * gn * om[d];
+                const double tp = std::round((xp - lo[d]) / h[d] - 0.5);
+                const double tq = std::round((xq - lo[d]) / h[d] - 0.5);
+                if (!(tp >= 0.0) || tp > n[d] - 1 || !(tq >= 0.0) || tq > n[d] - 1) ok = false;
+                else { kp[d] = (int)tp; kq[d] = (int)tq; }
+            }
+            uint32_t *e = &t.host[((size_t)k * nv + i) * 4];
+            if (!ok) {
+                t.discarded++;
+                e[0] = (uint32_t)i | ((uint32_t)i << 16);
+                e[1] = (uint32_t)i;
+                e[2] = 0u;  // b = +0.0f
+                continue;
+            }
+            const int l = where[((size_t)kp[0] * n[1] + kp[1]) * n[2] + kp[2]];
+            const int m = where[((size_t)kq[0] * n[1] + kq[1]) * n[2] + kq[2]];
+            const float bw = (float)(scale * gn);
+            e[0] = (uint32_t)gam | ((uint32_t)l << 16);
+            e[1] = (uint32_t)m;
+            std::memcpy(&e[2], &bw, 4);
+        }
+    }
+    t.dev = alloc(t.host.size() * 4);
+    if (!t.dev) { err = "device allocation (collision tables)"; return DVM_ENOMEM; }
+    if (cudaMemcpy(t.dev, t.host.data(), t.host.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaGetLastError();
+        err = "copy collision tables";
+        return DVM_ECUDA;
+    }
+    t.trials = trials;
+    t.seed = seed;
+    t.nv = nv;
+    t.ready = true;
+    return DVM_OK;
+}
+
+}  // namespace dvm

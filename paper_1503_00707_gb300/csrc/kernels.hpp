@@ -1,0 +1,57 @@
+// Launch interface between the C ABI layer and the CUDA kernels.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace dvm {
+
+// Status bits raised by the step kernels (OR-ed into one device word).
+enum : int {
+    ST_NONPOS = 1,      // non-positive or non-finite density/temperature
+    ST_SINGULAR = 2,    // singular or non-finite 5x5 correction system
+    ST_NUDT = 4,        // relaxation factor nu*dt (or dt/Kn * max P B) above 1
+};
+
+struct StepParams {
+    int dim;              // 2 or 3 physical dimensions
+    int prec;             // DVM_F64 / DVM_F32 / DVM_BF16
+    int coll;             // DVM_COLL_NONE / DVM_COLL_BGK
+    int64_t ncells;
+    int nv;               // velocity nodes per cell
+    int P;                // nodes per sign group = nv / 8
+    int half[3];          // n[d] / 2
+    int n[3];
+    const void *f_in;     // [ncells][nv] storage precision
+    void *f_out;
+    const int32_t *st_src;   // [ncells][6][4]
+    const void *st_w;        // [ncells][6][4]  compute precision
+    const uint8_t *st_cnt;   // [ncells][8]
+    const void *inv_h;       // [ncells]        compute precision
+    const void *finf;        // [nv] inflow ghost, compute precision
+    const double *amag;      // [3][32] |xi| of the positive-side nodes m = 0..half-1
+    const float *amag_f;     // same, rounded to FP32
+    double dt, kn, dV;
+    double hv[3];            // velocity spacing per axis
+    double *mom_out;         // [ncells][5]: rho, u[3], T of f*
+    int *status;
+    cudaStream_t stream;
+};
+
+int launch_step(const StepParams &p);
+
+// f[c][v] = sum_m w[c][m] M(rho[c][m], u[c][m], T[c][m]; xi_v), FP64 math
+int launch_init_maxwellian(int prec, void *f, int64_t ncells, int nv, int nmix,
+                           const double *w, const double *rho, const double *u,
+                           const double *T, const double *xi, cudaStream_t s);
+
+// Moments of the stored f in FP64: out [ncells][5] = rho, u[3], T
+int launch_moments(int prec, const void *f, int64_t ncells, int nv, const double *xi,
+                   double dV, double *out, cudaStream_t s);
+
+// Convert count elements between storage precision and FP64.
+int launch_to_f64(int prec, const void *src, double *dst, int64_t count, cudaStream_t s);
+int launch_from_f64(int prec, const double *src, void *dst, int64_t count, cudaStream_t s);
+
+int64_t launches_issued();
+
+}  // namespace dvm
