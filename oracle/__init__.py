@@ -47,6 +47,7 @@ def lib():
         P = C.c_void_p
         d_p = C.POINTER(C.c_double)
         i64 = C.c_int64
+        L.orc_threads.restype = C.c_int
         L.orc_splitmix64.restype = C.c_uint64
         L.orc_splitmix64.argtypes = [C.c_uint64, C.c_uint64]
         L.orc_vgrid_size.restype = i64
@@ -83,6 +84,10 @@ def lib():
 
 def _p(a):
     return None if a is None else a.ctypes.data
+
+
+def threads():
+    return int(lib().orc_threads())
 
 
 def splitmix64(seed, n):

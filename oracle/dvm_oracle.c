@@ -24,6 +24,9 @@
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #ifndef M_PI
 #define M_PI 3.14159265358979323846
@@ -80,6 +83,15 @@ struct orc_problem {
 /* ------------------------------------------------------------------------ */
 /* SplitMix64 (Steele, Lea, Flood 2014): output n of the stream whose state
  * starts at `seed` and advances by the golden-ratio increment each draw.   */
+int orc_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
 uint64_t orc_splitmix64(uint64_t seed, uint64_t n)
 {
     uint64_t z = seed + (n + 1u) * 0x9E3779B97F4A7C15ull;

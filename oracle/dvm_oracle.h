@@ -40,6 +40,9 @@ typedef struct {
 
 typedef struct orc_problem orc_problem;
 
+/* Number of OpenMP threads the oracle's parallel loops use. */
+int orc_threads(void);
+
 /* SplitMix64 output number n (0-based) of the stream seeded with `seed`. */
 uint64_t orc_splitmix64(uint64_t seed, uint64_t n);
 

@@ -58,6 +58,9 @@ CONFIGS = {
     "c3_sphere_m5": _sphere_flow(5, 9, 0.1, 7.5, 24, 8.0, 5.0, 0.01, 100, "f32"),
     # the same flow on levels 5-7 (oracle-sized)
     "c3_sphere_m5_reduced": _sphere_flow(5, 7, 0.1, 7.5, 24, 8.0, 5.0, 0.01, 10, "f32"),
+    # the same flow on levels 4-6 with a thinner band (17.7k cells): the
+    # oracle finishes a step in seconds, for parity tests and the CPU baseline
+    "c3_sphere_m5_small": _sphere_flow(4, 6, 0.1, 3.0, 24, 8.0, 5.0, 0.01, 3, "f32"),
     # periodic box, level 4 plus a central ball at level 5 (~16.6k leaves);
     # 16^3 on [-6,6]^3; hard-sphere collisions, Kn=0.02; bimodal start.
     "c4_hs_bimodal": dict(
