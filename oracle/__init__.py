@@ -78,6 +78,12 @@ def lib():
         L.orc_hs_collide.argtypes = [P, C.c_double, C.c_double, P, P, P]
         L.orc_step.argtypes = [P, C.c_int, C.c_double, C.c_int, C.c_double]
         L.orc_solve.argtypes = [C.c_int, P, P, P]
+        L.orc_kn_local.argtypes = [P, C.c_double, P]
+        L.orc_hermite_project.argtypes = [P, P, P, P]
+        L.orc_hermite_target.argtypes = [P, P, P, P]
+        L.orc_mlp_forward.argtypes = [C.c_int64, P, P, P]
+        L.orc_mlp_backward.argtypes = [C.c_int64, P, P, P, P, P]
+        L.orc_learned_collide.argtypes = [P, C.c_double, C.c_double, P, C.c_double, P, P]
         _lib = L
     return _lib
 
@@ -119,6 +125,28 @@ def build_tree(spec):
     if rc:
         raise ValueError("tree build failed %d" % rc)
     return keys, lev, sol
+
+
+MLP_NPARAM = 164672
+MLP_SHAPES = [((256, 64), 256), ((256, 256), 256), ((256, 256), 256), ((64, 256), 64)]
+
+
+def mlp_forward(params, x):
+    params = np.ascontiguousarray(params, dtype=np.float64)
+    x = np.ascontiguousarray(x, dtype=np.float64).reshape(-1, 64)
+    y = np.zeros_like(x)
+    lib().orc_mlp_forward(x.shape[0], _p(params), _p(x), _p(y))
+    return y
+
+
+def mlp_backward(params, x, t):
+    params = np.ascontiguousarray(params, dtype=np.float64)
+    x = np.ascontiguousarray(x, dtype=np.float64).reshape(-1, 64)
+    t = np.ascontiguousarray(t, dtype=np.float64).reshape(-1, 64)
+    g = np.zeros(MLP_NPARAM)
+    loss = np.zeros(1)
+    lib().orc_mlp_backward(x.shape[0], _p(params), _p(x), _p(t), _p(g), _p(loss))
+    return g, float(loss[0])
 
 
 def solve(A, b):
@@ -254,6 +282,33 @@ class Problem:
         if lib().orc_hs_collide(self._h, dt, kn, _p(q), _p(B), _p(Cc)):
             raise RuntimeError("hard-sphere collision failed")
         return q, B, Cc
+
+    def kn_local(self, kn):
+        out = np.zeros(self.ncells)
+        lib().orc_kn_local(self._h, kn, _p(out))
+        return out
+
+    def hermite_project(self, f=None):
+        a = np.zeros((self.ncells, 64))
+        mom = np.zeros((self.ncells, 5))
+        ff = None if f is None else np.ascontiguousarray(f, dtype=np.float64)
+        lib().orc_hermite_project(self._h, _p(ff), _p(a), _p(mom))
+        return a, mom
+
+    def hermite_target(self, I, mom):
+        o = np.zeros((self.ncells, 64))
+        I = np.ascontiguousarray(I, dtype=np.float64)
+        mom = np.ascontiguousarray(mom, dtype=np.float64)
+        lib().orc_hermite_target(self._h, _p(I), _p(mom), _p(o))
+        return o
+
+    def learned_collide(self, dt, kn, params, threshold, want_q=False):
+        params = np.ascontiguousarray(params, dtype=np.float64)
+        used = np.zeros(self.ncells, dtype=np.int32)
+        q = np.zeros((self.ncells, self.nv)) if want_q else None
+        if lib().orc_learned_collide(self._h, dt, kn, _p(params), threshold, _p(used), _p(q)):
+            raise RuntimeError("learned collision failed")
+        return used, q
 
     def step(self, nsteps, dt, coll, kn):
         rc = lib().orc_step(self._h, nsteps, dt, coll, kn)

@@ -1027,3 +1027,299 @@ int orc_step(orc_problem *p, int nsteps, double dt, int coll, double kn)
     }
     return 0;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Local Knudsen number.  The gradient of a moment q at cell j is the
+ * weighted least-squares fit over its fluid face neighbours k,
+ *   min_g sum_k w_k (q_k - q_j - g.(x_k - x_j))^2,  w_k = A_k / |x_k - x_j|^2,
+ * which is exact for linear fields on any 2:1 stencil (a component with no
+ * neighbour spread, e.g. a cell walled in along that axis, is set to 0). */
+int orc_kn_local(const orc_problem *p, double kn, double *out)
+{
+    int64_t nc = p->ncells;
+    int dim = p->spec.dim;
+    double *rho = (double *)malloc((size_t)nc * sizeof(double));
+    double *u = (double *)malloc((size_t)nc * 3 * sizeof(double));
+    double *T = (double *)malloc((size_t)nc * sizeof(double));
+    double *xc = (double *)malloc((size_t)nc * 3 * sizeof(double));
+    orc_moments(p, rho, u, T);
+    orc_cell_centres(p, xc, NULL);
+    for (int64_t c = 0; c < nc; c++) {
+        double q[5] = {rho[c], T[c], u[3 * c], u[3 * c + 1], u[3 * c + 2]};
+        double N[9] = {0}, R[5][3] = {{0}};
+        for (int64_t e = p->cf_start[c]; e < p->cf_start[c + 1]; e++) {
+            int64_t f = p->cf_list[e];
+            if (f < 0) continue; /* boundary face: no fluid neighbour */
+            int64_t a = p->cell_of_leaf[p->fm[f]], b = p->cell_of_leaf[p->fp[f]];
+            int64_t nb = (a == c) ? b : a;
+            double d[3] = {0, 0, 0}, d2 = 0.0;
+            for (int k = 0; k < dim; k++) {
+                d[k] = xc[3 * nb + k] - xc[3 * c + k];
+                if (p->spec.bc[2 * k] == ORC_BC_PERIODIC) {
+                    if (d[k] > 0.5) d[k] -= 1.0;
+                    if (d[k] < -0.5) d[k] += 1.0;
+                }
+                d2 += d[k] * d[k];
+            }
+            double w = p->farea[f] / d2;
+            double qn[5] = {rho[nb], T[nb], u[3 * nb], u[3 * nb + 1], u[3 * nb + 2]};
+            for (int r = 0; r < dim; r++) {
+                for (int k = 0; k < dim; k++) N[r * 3 + k] += w * d[r] * d[k];
+                for (int m = 0; m < 5; m++) R[m][r] += w * d[r] * (qn[m] - q[m]);
+            }
+        }
+        double grad[5][3] = {{0}};
+        for (int m = 0; m < 5; m++) {
+            double A[9], bb[3], g[3] = {0, 0, 0};
+            for (int r = 0; r < dim; r++) {
+                for (int k = 0; k < dim; k++) A[r * dim + k] = N[r * 3 + k];
+                bb[r] = R[m][r];
+            }
+            if (orc_solve(dim, A, bb, g) == 0)
+                for (int r = 0; r < dim; r++) grad[m][r] = g[r];
+        }
+        double gr = 0, gT = 0, gu = 0;
+        for (int d = 0; d < 3; d++) {
+            gr += grad[0][d] * grad[0][d];
+            gT += grad[1][d] * grad[1][d];
+            for (int k = 2; k < 5; k++) gu += grad[k][d] * grad[k][d];
+        }
+        double m = sqrt(gr) / rho[c];
+        if (sqrt(gT) / T[c] > m) m = sqrt(gT) / T[c];
+        if (sqrt(gu) / sqrt(T[c]) > m) m = sqrt(gu) / sqrt(T[c]);
+        out[c] = kn / rho[c] * m;
+    }
+    free(rho); free(u); free(T); free(xc);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Hermite modes. */
+static void hermite4(double x, double h[4])
+{
+    h[0] = 1.0;
+    h[1] = x;
+    h[2] = (x * x - 1.0) / sqrt(2.0);
+    h[3] = (x * x * x - 3.0 * x) / sqrt(6.0);
+}
+
+static double mode_value(const double hx[4], const double hy[4], const double hz[4], int m)
+{
+    return hx[m >> 4] * hy[(m >> 2) & 3] * hz[m & 3];
+}
+
+int orc_hermite_project(const orc_problem *p, const double *f, double *a, double *mom)
+{
+    const double *F = f ? f : p->f;
+    for (int64_t c = 0; c < p->ncells; c++) {
+        const double *fc = &F[c * p->nv];
+        double rho, u[3], T;
+        cell_moments(p, fc, &rho, u, &T);
+        double sq = sqrt(T);
+        double acc[64] = {0};
+        for (int64_t v = 0; v < p->nv; v++) {
+            const double *x = &p->xi[3 * v];
+            double hx[4], hy[4], hz[4];
+            hermite4((x[0] - u[0]) / sq, hx);
+            hermite4((x[1] - u[1]) / sq, hy);
+            hermite4((x[2] - u[2]) / sq, hz);
+            for (int m = 0; m < 64; m++) acc[m] += fc[v] * mode_value(hx, hy, hz, m);
+        }
+        for (int m = 0; m < 64; m++) a[c * 64 + m] = acc[m] * p->dV / rho;
+        if (mom) {
+            mom[c * 5] = rho;
+            for (int d = 0; d < 3; d++) mom[c * 5 + 1 + d] = u[d];
+            mom[c * 5 + 4] = T;
+        }
+    }
+    return 0;
+}
+
+int orc_hermite_target(const orc_problem *p, const double *I, const double *mom, double *o)
+{
+    for (int64_t c = 0; c < p->ncells; c++) {
+        const double *ic = &I[c * p->nv];
+        double rho = mom[c * 5], T = mom[c * 5 + 4];
+        const double *u = &mom[c * 5 + 1];
+        double sq = sqrt(T);
+        double acc[64] = {0};
+        for (int64_t v = 0; v < p->nv; v++) {
+            const double *x = &p->xi[3 * v];
+            double hx[4], hy[4], hz[4];
+            hermite4((x[0] - u[0]) / sq, hx);
+            hermite4((x[1] - u[1]) / sq, hy);
+            hermite4((x[2] - u[2]) / sq, hz);
+            for (int m = 0; m < 64; m++) acc[m] += ic[v] * mode_value(hx, hy, hz, m);
+        }
+        for (int m = 0; m < 64; m++) o[c * 64 + m] = acc[m] * p->dV / (rho * rho * sq);
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* MLP 64 -> 256 -> 256 -> 256 -> 64 with SiLU. */
+static const int mlp_in[4] = {64, 256, 256, 256};
+static const int mlp_out[4] = {256, 256, 256, 64};
+
+static double silu(double x) { return x / (1.0 + exp(-x)); }
+static double silu_grad(double x)
+{
+    double s = 1.0 / (1.0 + exp(-x));
+    return s * (1.0 + x * (1.0 - s));
+}
+
+static const double *layer_W(const double *params, int l)
+{
+    size_t off = 0;
+    for (int k = 0; k < l; k++) off += (size_t)mlp_in[k] * mlp_out[k] + mlp_out[k];
+    return params + off;
+}
+
+/* z[l] are pre-activations of layer l (0..3), per sample */
+static void mlp_sample(const double *params, const double *x, double *z[4], double *h[4], double *y)
+{
+    const double *in = x;
+    for (int l = 0; l < 4; l++) {
+        const double *W = layer_W(params, l);
+        const double *b = W + (size_t)mlp_in[l] * mlp_out[l];
+        for (int o = 0; o < mlp_out[l]; o++) {
+            double s = b[o];
+            for (int i = 0; i < mlp_in[l]; i++) s += W[(size_t)o * mlp_in[l] + i] * in[i];
+            z[l][o] = s;
+            h[l][o] = l < 3 ? silu(s) : s;
+        }
+        in = h[l];
+    }
+    for (int o = 0; o < 64; o++) y[o] = h[3][o];
+}
+
+int orc_mlp_forward(int64_t n, const double *params, const double *x, double *y)
+{
+#pragma omp parallel for schedule(static)
+    for (int64_t s = 0; s < n; s++) {
+        double zb[4][256], hb[4][256];
+        double *z[4] = {zb[0], zb[1], zb[2], zb[3]}, *h[4] = {hb[0], hb[1], hb[2], hb[3]};
+        mlp_sample(params, &x[s * 64], z, h, &y[s * 64]);
+    }
+    return 0;
+}
+
+int orc_mlp_backward(int64_t n, const double *params, const double *x, const double *t,
+                     double *grad, double *loss)
+{
+    memset(grad, 0, (size_t)ORC_MLP_NPARAM * sizeof(double));
+    double L = 0.0;
+    const double scale = 2.0 / ((double)n * 64.0);
+    for (int64_t s = 0; s < n; s++) {
+        double zb[4][256], hb[4][256], y[64];
+        double *z[4] = {zb[0], zb[1], zb[2], zb[3]}, *h[4] = {hb[0], hb[1], hb[2], hb[3]};
+        mlp_sample(params, &x[s * 64], z, h, y);
+        double delta[256], next[256];
+        for (int o = 0; o < 64; o++) {
+            double r = y[o] - t[s * 64 + o];
+            L += r * r;
+            delta[o] = scale * r; /* dL/dz of the linear output layer */
+        }
+        for (int l = 3; l >= 0; l--) {
+            const double *in = l ? h[l - 1] : &x[s * 64];
+            size_t off = (size_t)(layer_W(params, l) - params);
+            double *gW = grad + off;
+            double *gb = gW + (size_t)mlp_in[l] * mlp_out[l];
+            const double *W = params + off;
+            for (int o = 0; o < mlp_out[l]; o++) {
+                gb[o] += delta[o];
+                for (int i = 0; i < mlp_in[l]; i++) gW[(size_t)o * mlp_in[l] + i] += delta[o] * in[i];
+            }
+            if (l == 0) break;
+            for (int i = 0; i < mlp_in[l]; i++) {
+                double sacc = 0.0;
+                for (int o = 0; o < mlp_out[l]; o++) sacc += W[(size_t)o * mlp_in[l] + i] * delta[o];
+                next[i] = sacc * silu_grad(z[l - 1][i]);
+            }
+            for (int i = 0; i < mlp_in[l]; i++) delta[i] = next[i];
+        }
+    }
+    *loss = L / ((double)n * 64.0);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Learned collision with conservative projection, entropy check, fallback. */
+int orc_learned_collide(orc_problem *p, double dt, double kn, const double *params,
+                        double kn_threshold, int32_t *used, double *q)
+{
+    int64_t nc = p->ncells, nv = p->nv;
+    double *knl = (double *)malloc((size_t)nc * sizeof(double));
+    orc_kn_local(p, kn, knl);
+    double *a = (double *)malloc((size_t)nc * 64 * sizeof(double));
+    double *o = (double *)malloc((size_t)nc * 64 * sizeof(double));
+    double *mom = (double *)malloc((size_t)nc * 5 * sizeof(double));
+    orc_hermite_project(p, NULL, a, mom);
+    orc_mlp_forward(nc, params, a, o);
+    /* the plain operator for every cell (the fallback and the judge) */
+    double *qhs = NULL;
+    if (p->hs_start) {
+        double *f0 = (double *)malloc((size_t)(nc * nv) * sizeof(double));
+        memcpy(f0, p->f, (size_t)(nc * nv) * sizeof(double));
+        qhs = (double *)malloc((size_t)(nc * nv) * sizeof(double));
+        if (orc_hs_collide(p, 0.0, 1.0, qhs, NULL, NULL)) { free(f0); return -1; }
+        memcpy(p->f, f0, (size_t)(nc * nv) * sizeof(double));
+        free(f0);
+    }
+    int err = 0;
+    for (int64_t c = 0; c < nc; c++) {
+        double *f = &p->f[c * nv];
+        double rho = mom[c * 5], T = mom[c * 5 + 4];
+        const double *u = &mom[c * 5 + 1];
+        double sq = sqrt(T);
+        double *Q = (double *)malloc((size_t)nv * sizeof(double));
+        int ok = knl[c] < kn_threshold;
+        if (ok) {
+            double A[25] = {0}, rhs[5] = {0}, cc[5];
+            double *M = (double *)malloc((size_t)nv * sizeof(double));
+            for (int64_t v = 0; v < nv; v++) {
+                const double *x = &p->xi[3 * v];
+                double g[3], hx[4], hy[4], hz[4];
+                for (int d = 0; d < 3; d++) g[d] = (x[d] - u[d]) / sq;
+                hermite4(g[0], hx);
+                hermite4(g[1], hy);
+                hermite4(g[2], hz);
+                double s = 0.0;
+                for (int m = 0; m < 64; m++) s += o[c * 64 + m] * mode_value(hx, hy, hz, m);
+                M[v] = maxwellian(rho, u, T, x);
+                Q[v] = rho * sq * M[v] * s;
+                double ph[5] = {1.0, g[0], g[1], g[2], g[0] * g[0] + g[1] * g[1] + g[2] * g[2] - 3.0};
+                for (int r = 0; r < 5; r++) {
+                    for (int k = 0; k < 5; k++) A[r * 5 + k] += ph[r] * ph[k] * M[v] * p->dV;
+                    rhs[r] += ph[r] * Q[v] * p->dV;
+                }
+            }
+            if (orc_solve(5, A, rhs, cc)) ok = 0;
+            double ent = 0.0;
+            for (int64_t v = 0; v < nv && ok; v++) {
+                const double *x = &p->xi[3 * v];
+                double g[3];
+                for (int d = 0; d < 3; d++) g[d] = (x[d] - u[d]) / sq;
+                double ph[5] = {1.0, g[0], g[1], g[2], g[0] * g[0] + g[1] * g[1] + g[2] * g[2] - 3.0};
+                double corr = 0.0;
+                for (int r = 0; r < 5; r++) corr += cc[r] * ph[r];
+                Q[v] -= M[v] * corr;
+                ent += Q[v] * log(f[v] > 0.0 ? f[v] : 1e-300) * p->dV;
+            }
+            if (ok && !(ent <= 0.0)) ok = 0;
+            free(M);
+        }
+        if (!ok) {
+            if (!qhs) { err = 1; free(Q); continue; }
+            for (int64_t v = 0; v < nv; v++) Q[v] = qhs[c * nv + v];
+        }
+        if (used) used[c] = ok;
+        for (int64_t v = 0; v < nv; v++) {
+            if (q) q[c * nv + v] = Q[v];
+            f[v] += dt / kn * Q[v];
+        }
+        free(Q);
+    }
+    free(knl); free(a); free(o); free(mom); free(qhs);
+    return err ? -1 : 0;
+}

@@ -108,6 +108,42 @@ int orc_hs_collide(orc_problem *p, double dt, double kn, double *q,
  * coll: 0 none, 1 BGK, 2 hard sphere. */
 int orc_step(orc_problem *p, int nsteps, double dt, int coll, double kn);
 
+/* ---- local Knudsen number (continuum-breakdown sensor, Sec. 2.3, Sec. 3.4) ----
+ * Kn_loc = (Kn / rho) max(|grad rho|/rho, |grad T|/T, |grad u|/sqrt(T)) from
+ * the moments of the stored f (|grad u| the Frobenius norm); gradients are
+ * weighted least-squares fits over the fluid face neighbours (exact for
+ * linear fields across hanging faces). */
+int orc_kn_local(const orc_problem *p, double kn, double *out);
+
+/* ---- Hermite modes (learned collision operator) ----
+ * h_0 = 1, h_1 = x, h_2 = (x^2 - 1)/sqrt(2), h_3 = (x^3 - 3x)/sqrt(6);
+ * mode m = 16a + 4b + c is h_a(g_x) h_b(g_y) h_c(g_z), g = (xi - u)/sqrt(T).
+ * a[c][m] = sum_i f_i H_m dV / rho with (rho, u, T) the moments of f;
+ * mom[c] = (rho, u, T).  f = NULL uses the stored f. */
+int orc_hermite_project(const orc_problem *p, const double *f, double *a, double *mom);
+/* o[c][m] = sum_i I_i H_m dV / (rho^2 sqrt(T)) for a collision term I given
+ * the cell's (rho, u, T) */
+int orc_hermite_target(const orc_problem *p, const double *I, const double *mom, double *o);
+
+/* ---- MLP 64 -> 256 -> 256 -> 256 -> 64, SiLU hidden activations ----
+ * params (ORC_MLP_NPARAM doubles): W1[256][64] b1[256] W2[256][256] b2[256]
+ * W3[256][256] b3[256] W4[64][256] b4[64], W[out][in].  Loss: mean over the
+ * n*64 outputs of (y - t)^2. */
+#define ORC_MLP_NPARAM 164672
+int orc_mlp_forward(int64_t n, const double *params, const double *x, double *y);
+int orc_mlp_backward(int64_t n, const double *params, const double *x, const double *t,
+                     double *grad, double *loss);
+
+/* Learned collision update of the stored f: cells with Kn_loc < threshold
+ * take I = rho sqrt(T) M sum_m o_m H_m (o = MLP(a)), made exactly
+ * conservative by subtracting M (c0 + c.g + c4 (|g|^2 - 3)) with the five
+ * c solving the discrete moment system; a cell whose corrected term fails
+ * the entropy check sum I ln f dV <= 0 falls back to the hard-sphere term
+ * (tables must be set).  used[c] = 1 where the learned term was applied.
+ * f <- f + dt/Kn I. */
+int orc_learned_collide(orc_problem *p, double dt, double kn, const double *params,
+                        double kn_threshold, int32_t *used, double *q);
+
 /* Gaussian elimination with partial pivoting on an n x n system (n <= 8);
  * A is row-major and is overwritten.  Returns 0, or -1 if singular. */
 int orc_solve(int n, double *A, double *b, double *x);
