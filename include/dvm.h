@@ -188,6 +188,14 @@ int dvm_dt_cfl(const dvm_ctx *ctx, double cfl, double *dt);
 /* Hard-sphere trial tables for Eqs. 3-5 (required for DVM_COLL_HS). */
 int dvm_set_collision_tables(dvm_ctx *ctx, int trials, uint64_t seed);
 
+/* Copy of the hard-sphere trial tables (node-major, entry e = i*trials + k,
+ * nv*trials entries each): partner gamma, post-collision nodes l and m
+ * (storage indices) and weight b = c (FP32; 0 for a discarded trial, whose
+ * indices then point at node i).  *discarded receives the number of
+ * discarded trials. */
+int dvm_get_collision_tables(const dvm_ctx *ctx, int32_t *gam, int32_t *l, int32_t *m,
+                             float *b, int64_t *discarded);
+
 /* nsteps explicit steps of size dt: transport (Eq. 2), moments of f*, then
  * the collision update on f* (Lie splitting): BGK relaxation towards the
  * conservatively corrected discrete Maxwellian, or Eqs. 3-6, with forward

@@ -32,7 +32,7 @@ EXPORTS = [
     "dvm_get_bfaces", "dvm_cell_centres", "dvm_set_velocity_grid", "dvm_get_velocities",
     "dvm_set_freestream", "dvm_init_maxwellian", "dvm_get_f", "dvm_set_f", "dvm_upload_f",
     "dvm_download_f", "dvm_f_device", "dvm_dt_cfl", "dvm_set_collision_tables", "dvm_step",
-    "dvm_moments", "dvm_step_moments", "dvm_launch_count",
+    "dvm_moments", "dvm_step_moments", "dvm_launch_count", "dvm_get_collision_tables",
 ]
 
 
@@ -104,6 +104,7 @@ def lib():
             "dvm_moments": [P, P, P, P],
             "dvm_step_moments": [P, P, P, P],
             "dvm_launch_count": [P],
+            "dvm_get_collision_tables": [P, P, P, P, P, P],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -223,6 +224,14 @@ class Solver:
 
     def set_collision_tables(self, trials, seed):
         self._chk(lib().dvm_set_collision_tables(self._h, int(trials), int(seed)))
+
+    def collision_tables(self, trials):
+        n = self.nv * trials
+        gam, l, m = np.zeros(n, np.int32), np.zeros(n, np.int32), np.zeros(n, np.int32)
+        b = np.zeros(n, np.float32)
+        disc = C.c_int64()
+        self._chk(lib().dvm_get_collision_tables(self._h, _p(gam), _p(l), _p(m), _p(b), C.byref(disc)))
+        return gam, l, m, b, disc.value
 
     # ---- state
     def get_f(self):

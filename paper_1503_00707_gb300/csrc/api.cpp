@@ -39,7 +39,6 @@ struct dvm_ctx {
     void *d_w = nullptr;
     uint8_t *d_cnt = nullptr;
     void *d_invh = nullptr;
-    void *d_finf = nullptr;
     double *d_amag = nullptr;
     float *d_amag_f = nullptr;
     double *d_xi = nullptr;
@@ -105,7 +104,6 @@ void free_grid_buffers(dvm_ctx *c)
 {
     dev_free(c, c->d_f[0]);
     dev_free(c, c->d_f[1]);
-    dev_free(c, c->d_finf);
     dev_free(c, reinterpret_cast<void *&>(c->d_amag));
     dev_free(c, reinterpret_cast<void *&>(c->d_amag_f));
     dev_free(c, reinterpret_cast<void *&>(c->d_xi));
@@ -147,7 +145,26 @@ int upload_mesh(dvm_ctx *c)
     if (!c->d_src || !c->d_w || !c->d_cnt || !c->d_invh) return fail(c, DVM_ENOMEM, "device allocation (stencils)");
     std::vector<double> invh(nc);
     for (int64_t q = 0; q < nc; q++) invh[q] = std::ldexp(1.0, m.leaves[m.leaf_of_cell[q]].lev);
-    int rc = cuda_check(c, cudaMemcpy(c->d_src, m.st_src.data(), nc * 24 * sizeof(int32_t), cudaMemcpyHostToDevice), "copy stencils");
+    // Device encoding of a stencil source: the cell to read (bits 0-27) and
+    // the sign-group flip applied to the group index (bits 28-30).  The
+    // inflow ghost is the extra cell `nc` that holds the freestream
+    // Maxwellian; outflow reads the cell itself; a specular wall reads the
+    // cell itself in the group mirrored along the face's axis.
+    std::vector<int32_t> enc(m.st_src.size());
+    for (int64_t q = 0; q < nc; q++)
+        for (int list = 0; list < 6; list++)
+            for (int e = 0; e < dvm::MAX_SRC; e++) {
+                const size_t k = ((size_t)q * 6 + list) * dvm::MAX_SRC + e;
+                const int32_t s0 = m.st_src[k];
+                int32_t v;
+                if (s0 >= 0) v = s0;
+                else if (s0 == dvm::SRC_INFLOW) v = (int32_t)nc;
+                else if (s0 == dvm::SRC_OUTFLOW) v = (int32_t)q;
+                else v = (int32_t)q | ((4 >> (list / 2)) << 28);
+                enc[k] = v;
+            }
+    if (nc >= (1 << 28)) return fail(c, DVM_ENOTIMPL, "more than 2^28 cells");
+    int rc = cuda_check(c, cudaMemcpy(c->d_src, enc.data(), nc * 24 * sizeof(int32_t), cudaMemcpyHostToDevice), "copy stencils");
     if (rc) return rc;
     rc = cuda_check(c, cudaMemcpy(c->d_cnt, m.st_cnt.data(), nc * 8, cudaMemcpyHostToDevice), "copy stencil counts");
     if (rc) return rc;
@@ -172,15 +189,27 @@ double maxwellian(double rho, const double u[3], double T, const double *x)
     return rho / (tp * std::sqrt(tp)) * std::exp(-d2 / (2.0 * T));
 }
 
+// The inflow ghost: one extra cell after the last one in both f buffers,
+// holding the freestream Maxwellian sampled at the nodes (FP64, rounded to
+// the storage precision).  Steps read it and never write it.
 int upload_freestream(dvm_ctx *c)
 {
-    if (!c->d_finf) return DVM_OK;
+    if (!c->d_f[0]) return DVM_OK;
     std::vector<double> m(c->nv);
     for (int v = 0; v < c->nv; v++) m[v] = maxwellian(c->fs_rho, c->fs_u, c->fs_T, &c->xi[3 * v]);
-    if (c->cfg.precision == DVM_F64)
-        return cuda_check(c, cudaMemcpy(c->d_finf, m.data(), c->nv * 8, cudaMemcpyHostToDevice), "copy freestream");
-    std::vector<float> mf(m.begin(), m.end());
-    return cuda_check(c, cudaMemcpy(c->d_finf, mf.data(), c->nv * 4, cudaMemcpyHostToDevice), "copy freestream");
+    double *stage = nullptr;
+    if (cudaMalloc(&stage, c->nv * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, DVM_ENOMEM, "device allocation (freestream)");
+    }
+    int rc = cuda_check(c, cudaMemcpy(stage, m.data(), c->nv * 8, cudaMemcpyHostToDevice), "copy freestream");
+    const size_t es = elem_size(c->cfg.precision);
+    for (int b = 0; b < 2 && !rc; b++)
+        rc = dvm::launch_from_f64(c->cfg.precision, stage, static_cast<char *>(c->d_f[b]) + c->f_elems * es,
+                                  c->nv, c->stream);
+    if (!rc) rc = cuda_check(c, cudaStreamSynchronize(c->stream), "freestream");
+    cudaFree(stage);
+    return rc;
 }
 
 }  // namespace
@@ -382,15 +411,16 @@ int dvm_set_velocity_grid(dvm_ctx *c, const int n[3], const double lo[3], const 
     const int64_t nc = ncells_of(c);
     c->f_elems = (size_t)nc * c->nv;
     const size_t fb = c->f_elems * elem_size(c->cfg.precision);
-    c->d_f[0] = dev_alloc(c, fb);
-    c->d_f[1] = dev_alloc(c, fb);
-    c->d_finf = dev_alloc(c, c->nv * tc_size(c->cfg.precision));
+    // one extra cell: the inflow ghost
+    const size_t fbg = fb + (size_t)c->nv * elem_size(c->cfg.precision);
+    c->d_f[0] = dev_alloc(c, fbg);
+    c->d_f[1] = dev_alloc(c, fbg);
     c->d_amag = dev_alloc_t<double>(c, 96);
     c->d_amag_f = dev_alloc_t<float>(c, 96);
     c->d_xi = dev_alloc_t<double>(c, 3 * (size_t)c->nv);
     c->d_mom = dev_alloc_t<double>(c, 5 * (size_t)nc);
     c->d_mom2 = dev_alloc_t<double>(c, 5 * (size_t)nc);
-    if (!c->d_f[0] || !c->d_f[1] || !c->d_finf || !c->d_amag || !c->d_amag_f || !c->d_xi || !c->d_mom || !c->d_mom2) {
+    if (!c->d_f[0] || !c->d_f[1] || !c->d_amag || !c->d_amag_f || !c->d_xi || !c->d_mom || !c->d_mom2) {
         free_grid_buffers(c);
         return fail(c, DVM_ENOMEM, "device allocation (f buffers)");
     }
@@ -546,11 +576,28 @@ int dvm_set_collision_tables(dvm_ctx *c, int trials, uint64_t seed)
 {
     if (!c || trials < 1) return DVM_EINVAL;
     if (c->state < 2) return fail(c, DVM_ESTATE, "set the velocity grid first");
+    if (c->cfg.precision != DVM_F32) return fail(c, DVM_ENOTIMPL, "the hard-sphere operator runs on FP32 storage");
     std::string err;
     int rc = dvm::hs_build(c->hs, c->n, c->lo, c->hv, c->xi, trials, seed, err,
                            [c](size_t b) { return dev_alloc(c, b); },
                            [c](void *p) { void *q = p; dev_free(c, q); });
     if (rc) return fail(c, rc, err);
+    return DVM_OK;
+}
+
+int dvm_get_collision_tables(const dvm_ctx *c, int32_t *gam, int32_t *l, int32_t *m, float *b, int64_t *discarded)
+{
+    if (!c) return DVM_EINVAL;
+    if (!c->hs.ready) return DVM_ESTATE;
+    const size_t n = c->hs.host_b.size();
+    for (size_t q = 0; q < n; q++) {
+        const uint32_t w0 = c->hs.host_idx[2 * q], w1 = c->hs.host_idx[2 * q + 1];
+        if (gam) gam[q] = (int32_t)(w0 & 0xffffu);
+        if (l) l[q] = (int32_t)(w0 >> 16);
+        if (m) m[q] = (int32_t)w1;
+        if (b) b[q] = c->hs.host_b[q];
+    }
+    if (discarded) *discarded = c->hs.discarded;
     return DVM_OK;
 }
 
@@ -572,7 +619,6 @@ int dvm_step(dvm_ctx *c, int nsteps, double dt)
     p.st_w = c->d_w;
     p.st_cnt = c->d_cnt;
     p.inv_h = c->d_invh;
-    p.finf = c->d_finf;
     p.amag = c->d_amag;
     p.amag_f = c->d_amag_f;
     p.dt = dt;
@@ -602,6 +648,10 @@ int dvm_step(dvm_ctx *c, int nsteps, double dt)
     int rc = cuda_check(c, cudaMemcpyAsync(&st, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "read status");
     if (!rc) rc = cuda_check(c, cudaStreamSynchronize(c->stream), "step");
     if (rc) return rc;
+    if (st & dvm::ST_TIMEOUT) {
+        cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream);
+        return fail(c, DVM_ETIMEOUT, "a bounded wait for an asynchronous tile copy gave up");
+    }
     if (st) {
         cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream);
         std::string why;

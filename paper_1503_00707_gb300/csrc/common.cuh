@@ -125,31 +125,32 @@ __device__ inline double warp_allsum(double v)
     return v;
 }
 
-// Gaussian elimination with partial pivoting, n = 5, FP64.  Returns false if
-// a pivot is zero or a result is not finite.
-__device__ inline bool solve5(double A[25], double b[5], double x[5])
+// Gaussian elimination with partial pivoting, n = 5.  Returns false if a
+// pivot is zero or a result is not finite.
+template <typename T>
+__device__ inline bool solve5(T A[25], T b[5], T x[5])
 {
 #pragma unroll
     for (int c = 0; c < 5; c++) {
         int piv = c;
-        double best = fabs(A[c * 5 + c]);
+        T best = fabs(A[c * 5 + c]);
 #pragma unroll
         for (int r = c + 1; r < 5; r++) {
-            const double v = fabs(A[r * 5 + c]);
+            const T v = fabs(A[r * 5 + c]);
             if (v > best) { best = v; piv = r; }
         }
-        if (!(best > 0.0) || !isfinite(best)) return false;
+        if (!(best > (T)0) || !isfinite(best)) return false;
         if (piv != c) {
 #pragma unroll
             for (int q = 0; q < 5; q++) {
-                const double t = A[c * 5 + q]; A[c * 5 + q] = A[piv * 5 + q]; A[piv * 5 + q] = t;
+                const T t = A[c * 5 + q]; A[c * 5 + q] = A[piv * 5 + q]; A[piv * 5 + q] = t;
             }
-            const double t = b[c]; b[c] = b[piv]; b[piv] = t;
+            const T t = b[c]; b[c] = b[piv]; b[piv] = t;
         }
-        const double inv = 1.0 / A[c * 5 + c];
+        const T inv = (T)1 / A[c * 5 + c];
 #pragma unroll
         for (int r = c + 1; r < 5; r++) {
-            const double m = A[r * 5 + c] * inv;
+            const T m = A[r * 5 + c] * inv;
 #pragma unroll
             for (int q = c; q < 5; q++) A[r * 5 + q] -= m * A[c * 5 + q];
             b[r] -= m * b[c];
@@ -157,7 +158,7 @@ __device__ inline bool solve5(double A[25], double b[5], double x[5])
     }
 #pragma unroll
     for (int r = 4; r >= 0; r--) {
-        double s = b[r];
+        T s = b[r];
 #pragma unroll
         for (int q = r + 1; q < 5; q++) s -= A[r * 5 + q] * x[q];
         x[r] = s / A[r * 5 + r];
@@ -165,5 +166,89 @@ __device__ inline bool solve5(double A[25], double b[5], double x[5])
     }
     return true;
 }
+
+}  // namespace dvm
+
+namespace dvm {
+
+// ---------------------------------------------------------------- double-float numbers
+// Arithmetic on unevaluated pairs hi + lo of FP32 values (Dekker 1971, with
+// FMA-based exact products): about 48 significant bits on the FP32 pipe,
+// used for the per-cell reductions and scalars where FP64 (1/64 of the FP32
+// rate on this GPU) would serialise the cell.
+struct ffn {
+    float hi, lo;
+};
+
+__device__ inline ffn ffn_norm(float s, float e)
+{
+    const float h = s + e;
+    return {h, e - (h - s)};
+}
+
+__device__ inline ffn operator+(ffn a, ffn b)
+{
+    const FF r = ff_add({a.hi, a.lo}, {b.hi, b.lo});
+    return {r.hi, r.lo};
+}
+__device__ inline ffn operator-(ffn a) { return {-a.hi, -a.lo}; }
+__device__ inline ffn operator-(ffn a, ffn b) { return a + (-b); }
+__device__ inline ffn operator*(ffn a, ffn b)
+{
+    const float p = a.hi * b.hi;
+    float e = fmaf(a.hi, b.hi, -p);
+    e = fmaf(a.hi, b.lo, e);
+    e = fmaf(a.lo, b.hi, e);
+    return ffn_norm(p, e);
+}
+__device__ inline ffn operator*(ffn a, float b)
+{
+    const float p = a.hi * b;
+    float e = fmaf(a.hi, b, -p);
+    e = fmaf(a.lo, b, e);
+    return ffn_norm(p, e);
+}
+__device__ inline ffn operator/(ffn a, ffn b)
+{
+    const float q1 = a.hi / b.hi;
+    const ffn r1 = a - b * q1;
+    const float q2 = r1.hi / b.hi;
+    const ffn r2 = r1 - b * q2;
+    const float q3 = r2.hi / b.hi;
+    return ffn_norm(q1, q2) + ffn{q3, 0.0f};
+}
+
+template <typename TC> struct Num;
+
+template <> struct Num<float> {
+    using X = ffn;
+    __device__ static inline X make(float v) { return {v, 0.0f}; }
+    __device__ static inline X from_double_host_split(float hi, float lo) { return {hi, lo}; }
+    __device__ static inline float tc(X v) { return v.hi + v.lo; }
+    __device__ static inline float f(X v) { return v.hi + v.lo; }
+    __device__ static inline bool finite_pos(X v) { return isfinite(v.hi) && v.hi > 0.0f; }
+    __device__ static inline X shfl_xor(X v, int m)
+    {
+        return {__shfl_xor_sync(0xffffffffu, v.hi, m), __shfl_xor_sync(0xffffffffu, v.lo, m)};
+    }
+    // 1/sqrt(v): FP32 estimate refined by one Newton step in double-float
+    __device__ static inline X rsqrt(X v)
+    {
+        const float y = rsqrtf(v.hi);
+        const ffn e = ffn{1.0f, 0.0f} - v * y * y;
+        return ffn_norm(y, 0.5f * y * e.hi);
+    }
+};
+
+template <> struct Num<double> {
+    using X = double;
+    __device__ static inline X make(double v) { return v; }
+    __device__ static inline X from_double_host_split(float hi, float lo) { return (double)hi + (double)lo; }
+    __device__ static inline double tc(X v) { return v; }
+    __device__ static inline float f(X v) { return (float)v; }
+    __device__ static inline bool finite_pos(X v) { return isfinite(v) && v > 0.0; }
+    __device__ static inline X shfl_xor(X v, int m) { return __shfl_xor_sync(0xffffffffu, v, m); }
+    __device__ static inline X rsqrt(X v) { return 1.0 / sqrt(v); }
+};
 
 }  // namespace dvm

@@ -37,11 +37,13 @@ static double uniform01(uint64_t seed, uint64_t n)
 
 void hs_free(HsTables &t, const DevFree &dfree)
 {
-    if (t.dev) dfree(t.dev);
-    if (t.d_corr) dfree(t.d_corr);
+    if (t.d_idx) dfree(t.d_idx);
+    if (t.d_b) dfree(t.d_b);
+    if (t.d_xi) dfree(t.d_xi);
     if (t.d_bc) dfree(t.d_bc);
-    t.dev = nullptr;
-    t.d_corr = nullptr;
+    t.d_idx = nullptr;
+    t.d_b = nullptr;
+    t.d_xi = nullptr;
     t.d_bc = nullptr;
     t.bc_cells = 0;
     t.ready = false;
@@ -54,6 +56,10 @@ int hs_build(HsTables &t, const int n[3], const double lo[3], const double h[3],
     hs_free(t, dfree);
     const int nv = n[0] * n[1] * n[2];
     if (nv > 65535) { err = "hard-sphere tables need Nv < 65536"; return DVM_ENOTIMPL; }
+    if (!hs_trials_supported(trials)) {
+        err = "trials per node must be 32, 64, ..., 1024 (a power-of-two multiple of 32)";
+        return DVM_ENOTIMPL;
+    }
     // natural (kx, ky, kz) -> storage index
     std::vector<int32_t> where((size_t)nv, -1);
     for (int v = 0; v < nv; v++) {
@@ -63,7 +69,8 @@ int hs_build(HsTables &t, const int n[3], const double lo[3], const double h[3],
     }
     const double dV = h[0] * h[1] * h[2];
     const double scale = (double)nv * dV / (std::sqrt(2.0) * (double)trials);
-    t.host.assign((size_t)trials * nv * 4, 0u);
+    t.host_idx.assign((size_t)trials * nv * 2, 0u);
+    t.host_b.assign((size_t)trials * nv, 0.0f);
     t.discarded = 0;
     for (int i = 0; i < nv; i++) {
         const double *a = &xi[3 * (size_t)i];
@@ -88,25 +95,32 @@ int hs_build(HsTables &t, const int n[3], const double lo[3], const double h[3],
                 if (!(tp >= 0.0) || tp > n[d] - 1 || !(tq >= 0.0) || tq > n[d] - 1) ok = false;
                 else { kp[d] = (int)tp; kq[d] = (int)tq; }
             }
-            uint32_t *e = &t.host[((size_t)k * nv + i) * 4];
+            const size_t q = (size_t)i * trials + k;
+            uint32_t *e = &t.host_idx[2 * q];
             if (!ok) {
                 t.discarded++;
                 e[0] = (uint32_t)i | ((uint32_t)i << 16);
                 e[1] = (uint32_t)i;
-                e[2] = 0u;  // b = +0.0f
+                t.host_b[q] = 0.0f;
                 continue;
             }
             const int l = where[((size_t)kp[0] * n[1] + kp[1]) * n[2] + kp[2]];
             const int m = where[((size_t)kq[0] * n[1] + kq[1]) * n[2] + kq[2]];
-            const float bw = (float)(scale * gn);
             e[0] = (uint32_t)gam | ((uint32_t)l << 16);
             e[1] = (uint32_t)m;
-            std::memcpy(&e[2], &bw, 4);
+            t.host_b[q] = (float)(scale * gn);
         }
     }
-    t.dev = alloc(t.host.size() * 4);
-    if (!t.dev) { err = "device allocation (collision tables)"; return DVM_ENOMEM; }
-    if (cudaMemcpy(t.dev, t.host.data(), t.host.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess) {
+    std::vector<float> xf(3 * (size_t)nv);
+    for (int v = 0; v < nv; v++)
+        for (int d = 0; d < 3; d++) xf[(size_t)d * nv + v] = (float)xi[3 * (size_t)v + d];
+    t.d_idx = alloc(t.host_idx.size() * 4);
+    t.d_b = static_cast<float *>(alloc(t.host_b.size() * 4));
+    t.d_xi = static_cast<float *>(alloc(xf.size() * 4));
+    if (!t.d_idx || !t.d_b || !t.d_xi) { err = "device allocation (collision tables)"; return DVM_ENOMEM; }
+    if (cudaMemcpy(t.d_idx, t.host_idx.data(), t.host_idx.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(t.d_b, t.host_b.data(), t.host_b.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(t.d_xi, xf.data(), xf.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess) {
         cudaGetLastError();
         err = "copy collision tables";
         return DVM_ECUDA;

@@ -16,12 +16,14 @@ struct HsTables {
     uint64_t seed = 0;
     int nv = 0;
     int64_t discarded = 0;
-    // [trials][nv] entries {gamma | l << 16, m, bits(b), 0}; a discarded
-    // trial keeps b = 0 and points at the node itself.
-    std::vector<uint32_t> host;
-    void *dev = nullptr;
-    double *d_corr = nullptr;   // per-cell scratch, see k_hs.cu
-    float *d_bc = nullptr;      // per-cell B and C scratch [ncells][2][nv]
+    // Node-major tables, entry e = i*trials + k: idx {gamma | l << 16, m},
+    // weight b (= c).  A discarded trial keeps b = 0 and points at node i.
+    std::vector<uint32_t> host_idx;   // [nv*trials][2]
+    std::vector<float> host_b;        // [nv*trials]
+    void *d_idx = nullptr;
+    float *d_b = nullptr;
+    float *d_xi = nullptr;            // node velocities [3][nv], FP32
+    float *d_bc = nullptr;            // scratch: B and C of every cell [ncells][nv][2]
     int64_t bc_cells = 0;
 };
 
@@ -42,5 +44,8 @@ int hs_prepare(HsTables &t, int64_t ncells, const DevAlloc &alloc, const DevFree
 // f (storage precision, already holding f* from the transport launch) is
 // updated in place: f <- f* + dt/Kn * I(f*).
 int launch_hs_collide(HsTables &t, const StepParams &p, void *f, double kn, double dt);
+
+// Trials per node that the register-resident table layout supports.
+bool hs_trials_supported(int trials);
 
 }  // namespace dvm

@@ -1,12 +1,304 @@
-// Hard-sphere collision kernel (paper Sec. 3.2, Eqs. 3-6).
+// Hard-sphere discrete collision integral (paper Sec. 3.2, Eqs. 3-6).
+//
+// The trial table (gamma, l, m, b for every node i and trial k) is the same
+// for all cells (Sec. 3.2), and each trial needs three random gathers from a
+// cell's f.  The paper's kernel keeps one node's table in shared memory and
+// gathers f across cells from a velocity-major copy; here the roles are
+// swapped to keep every gather on chip:
+//
+//  k_hs_bc   table-stationary: a CTA holds the trials of 64 nodes in
+//            registers (32 per thread) and streams cells through a
+//            double-buffered shared-memory tile, each tile a single bulk
+//            copy (cp.async.bulk, completion on an mbarrier).  It writes
+//            B_i = sum_k b f_gamma (Eq. 4) and C_i = sum_k c f_l f_m (Eq. 5)
+//            for its nodes to a per-cell scratch array.
+//  k_hs_corr per cell: the five coefficients of P (Eq. 6) from the moment
+//            system, solved in the centred basis (1, c, |c|^2 - 3),
+//            c = (xi - u)/sqrt(T), then I = -f P B + C and
+//            f <- f + dt/Kn I in place.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+
 #include "../../include/dvm.h"
 #include "common.cuh"
 #include "hs.hpp"
 
 namespace dvm {
 
-int hs_prepare(HsTables &, int64_t, const DevAlloc &, const DevFree &) { return DVM_ENOTIMPL; }
+void count_launch();
 
-int launch_hs_collide(HsTables &, const StepParams &, void *, double, double) { return DVM_ENOTIMPL; }
+namespace {
+
+constexpr int HT = 256;   // threads per CTA of k_hs_bc
+constexpr int HE = 32;    // trials held per thread
+constexpr int CT = 256;   // threads per CTA of k_hs_corr
+constexpr uint32_t WAIT_POLLS = 1u << 22;
+
+__device__ inline uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ inline void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ inline void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+
+__device__ inline void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ inline void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ inline bool mbar_try_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait: gives up after WAIT_POLLS polls (with back-off).
+__device__ inline bool mbar_wait(uint64_t *bar, uint32_t parity)
+{
+    for (uint32_t t = 0; t < WAIT_POLLS; t++) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (t > 32) __nanosleep(128);
+    }
+    return false;
+}
+
+__global__ void __launch_bounds__(HT, 2)
+    k_hs_bc(const float *__restrict__ fs, float2 *__restrict__ bc, int64_t ncells, int nv, int M,
+            const uint2 *__restrict__ idx, const float *__restrict__ bw, int64_t cells_per_cta, int *status)
+{
+    extern __shared__ __align__(128) float tile[];  // [2][nv]
+    __shared__ __align__(8) uint64_t bar[2];
+    __shared__ int abort_flag;
+
+    const int tid = threadIdx.x;
+    const int tpn = M / HE;  // threads per node (power of two, <= 32)
+    const int npc = HT / tpn;
+    const int node = blockIdx.x * npc + tid / tpn;
+    const bool valid = node < nv;
+    const int64_t e0 = (int64_t)(valid ? node : 0) * M + (tid % tpn) * HE;
+    uint32_t w0[HE], w1[HE];
+    float b[HE];
+#pragma unroll
+    for (int e = 0; e < HE; e++) {
+        const uint2 t = idx[e0 + e];
+        w0[e] = t.x;
+        w1[e] = t.y;
+        b[e] = valid ? bw[e0 + e] : 0.0f;
+    }
+    const int64_t c0 = (int64_t)blockIdx.y * cells_per_cta;
+    const int64_t c1 = c0 + cells_per_cta < ncells ? c0 + cells_per_cta : ncells;
+    const uint32_t bytes = (uint32_t)nv * 4u;
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        abort_flag = 0;
+        mbar_fence_init();
+    }
+    __syncthreads();
+    // copies issued into / completions seen on each buffer (uniform over the CTA)
+    int issued[2] = {0, 0}, done[2] = {0, 0};
+    if (c0 < c1) {
+        if (tid == 0) {
+            mbar_expect_tx(&bar[0], bytes);
+            bulk_g2s(tile, fs + c0 * nv, bytes, &bar[0]);
+        }
+        issued[0]++;
+    }
+    for (int64_t c = c0; c < c1; c++) {
+        const int j = (int)(c - c0), s = j & 1;
+        if (c + 1 < c1) {
+            // buffer s^1 was last read in the previous iteration, which ended
+            // with a barrier
+            if (tid == 0) {
+                mbar_expect_tx(&bar[s ^ 1], bytes);
+                bulk_g2s(tile + (size_t)(s ^ 1) * nv, fs + (c + 1) * nv, bytes, &bar[s ^ 1]);
+            }
+            issued[s ^ 1]++;
+        }
+        if (mbar_wait(&bar[s], (uint32_t)done[s] & 1u)) done[s]++;
+        else abort_flag = 1;
+        const float *t = tile + (size_t)s * nv;
+        float B = 0.0f, C = 0.0f;
+#pragma unroll
+        for (int e = 0; e < HE; e++) {
+            const float fg = t[w0[e] & 0xffffu];
+            const float fl = t[w0[e] >> 16];
+            const float fm = t[w1[e]];
+            B = fmaf(b[e], fg, B);
+            C = fmaf(b[e], fl * fm, C);
+        }
+        for (int m = 1; m < tpn; m <<= 1) {
+            B += __shfl_xor_sync(0xffffffffu, B, m);
+            C += __shfl_xor_sync(0xffffffffu, C, m);
+        }
+        if (valid && tid % tpn == 0) bc[c * nv + node] = make_float2(B, C);
+        __syncthreads();
+        if (abort_flag) {
+            // a tile never arrived: report, give the copies in flight a bounded
+            // time to land, and stop
+            if (tid == 0) {
+                atomicOr(status, ST_TIMEOUT);
+                for (int q = 0; q < 2; q++)
+                    while (done[q] < issued[q] && mbar_wait(&bar[q], (uint32_t)done[q] & 1u)) done[q]++;
+            }
+            return;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(CT)
+    k_hs_corr(float *__restrict__ f, const float2 *__restrict__ bc, const float *__restrict__ xi3,
+              const double *__restrict__ mom, int nv, float dtkn, int *status)
+{
+    __shared__ float red[CT / 32][20];
+    __shared__ float sd[6];
+    const int64_t cell = blockIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const double *mo = mom + cell * 5;
+    const float ux = (float)mo[1], uy = (float)mo[2], uz = (float)mo[3];
+    const float T = (float)mo[4];
+    const float ist = T > 0.0f ? rsqrtf(T) : 0.0f;
+    float *fc = f + cell * (int64_t)nv;
+    const float2 *bcc = bc + cell * (int64_t)nv;
+    float acc[20];
+#pragma unroll
+    for (int k = 0; k < 20; k++) acc[k] = 0.0f;
+    for (int v = tid; v < nv; v += CT) {
+        const float fv = fc[v];
+        const float2 q = bcc[v];
+        const float cx = (xi3[v] - ux) * ist, cy = (xi3[nv + v] - uy) * ist, cz = (xi3[2 * nv + v] - uz) * ist;
+        const float ph[5] = {1.0f, cx, cy, cz, cx * cx + cy * cy + cz * cz - 3.0f};
+        const float fB = fv * q.x, g = q.y - fB;
+#pragma unroll
+        for (int r = 0, k = 0; r < 5; r++) {
+#pragma unroll
+            for (int c = r; c < 5; c++, k++) acc[k] = fmaf(ph[r] * ph[c], fB, acc[k]);
+            acc[15 + r] = fmaf(ph[r], g, acc[15 + r]);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 20; k++) {
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) acc[k] += __shfl_down_sync(0xffffffffu, acc[k], off);
+        if (lane == 0) red[warp][k] = acc[k];
+    }
+    __syncthreads();
+    if (warp == 0) {
+        ffn s[20];
+#pragma unroll
+        for (int k = 0; k < 20; k++) {
+            s[k] = ffn{lane < CT / 32 ? red[lane][k] : 0.0f, 0.0f};
+#pragma unroll
+            for (int m = 16; m > 0; m >>= 1)
+                s[k] = s[k] + ffn{__shfl_xor_sync(0xffffffffu, s[k].hi, m), __shfl_xor_sync(0xffffffffu, s[k].lo, m)};
+        }
+        if (lane == 0) {
+            float A[25], rhs[5], d[5];
+            int k = 0;
+            for (int r = 0; r < 5; r++)
+                for (int c = r; c < 5; c++) {
+                    const float v = s[k++].hi;
+                    A[r * 5 + c] = v;
+                    A[c * 5 + r] = v;
+                }
+            for (int r = 0; r < 5; r++) rhs[r] = s[15 + r].hi + s[15 + r].lo;
+            int ok = solve5<float>(A, rhs, d);
+            if (!ok) {
+                atomicOr(status, ST_SINGULAR);
+                for (int r = 0; r < 5; r++) d[r] = 0.0f;
+            }
+            for (int r = 0; r < 5; r++) sd[r] = d[r];
+            sd[5] = ok ? 1.0f : 0.0f;
+        }
+    }
+    __syncthreads();
+    const float d0 = sd[0], dx = sd[1], dy = sd[2], dz = sd[3], d4 = sd[4];
+    float worst = 0.0f;
+    for (int v = tid; v < nv; v += CT) {
+        const float fv = fc[v];
+        const float2 q = bcc[v];
+        const float cx = (xi3[v] - ux) * ist, cy = (xi3[nv + v] - uy) * ist, cz = (xi3[2 * nv + v] - uz) * ist;
+        const float P = 1.0f + d0 + dx * cx + dy * cy + dz * cz + d4 * (cx * cx + cy * cy + cz * cz - 3.0f);
+        const float loss = P * q.x;
+        worst = fmaxf(worst, dtkn * loss);
+        fc[v] = fmaf(dtkn, q.y - fv * loss, fv);
+    }
+    if (worst > 1.0f) atomicOr(status, ST_NUDT);
+}
+
+}  // namespace
+
+bool hs_trials_supported(int trials)
+{
+    if (trials < HE || trials % HE) return false;
+    const int tpn = trials / HE;
+    return tpn <= 32 && (tpn & (tpn - 1)) == 0;
+}
+
+int hs_prepare(HsTables &t, int64_t ncells, const DevAlloc &alloc, const DevFree &dfree)
+{
+    if (!t.ready) return DVM_ESTATE;
+    if (t.d_bc && t.bc_cells == ncells) return DVM_OK;
+    if (t.d_bc) dfree(t.d_bc);
+    t.d_bc = static_cast<float *>(alloc((size_t)ncells * t.nv * 2 * sizeof(float)));
+    t.bc_cells = t.d_bc ? ncells : 0;
+    return t.d_bc ? DVM_OK : DVM_ENOMEM;
+}
+
+int launch_hs_collide(HsTables &t, const StepParams &p, void *f, double kn, double dt)
+{
+    if (p.prec != DVM_F32) return DVM_ENOTIMPL;
+    if (!t.ready || t.nv != p.nv || !t.d_bc) return DVM_ESTATE;
+    const int tpn = t.trials / HE, npc = HT / tpn;
+    const int chunks = (p.nv + npc - 1) / npc;
+    const size_t dyn = 2 * (size_t)p.nv * sizeof(float);
+    static bool configured = false;
+    if (!configured) {
+        if (cudaFuncSetAttribute(k_hs_bc, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) != cudaSuccess)
+            return DVM_ECUDA;
+        configured = true;
+    }
+    if (dyn > 200 * 1024) return DVM_ENOTIMPL;
+    int dev = 0, nsm = 0, occ = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_hs_bc, HT, dyn) != cudaSuccess || occ < 1)
+        return DVM_ENOTIMPL;
+    int64_t splits = std::max<int64_t>(1, (2 * (int64_t)nsm * occ + chunks - 1) / chunks);
+    splits = std::min<int64_t>(splits, p.ncells);
+    const int64_t per = (p.ncells + splits - 1) / splits;
+    splits = (p.ncells + per - 1) / per;
+    const dim3 grid((unsigned)chunks, (unsigned)splits);
+    k_hs_bc<<<grid, HT, dyn, p.stream>>>(static_cast<const float *>(f), reinterpret_cast<float2 *>(t.d_bc),
+                                          p.ncells, p.nv, t.trials, static_cast<const uint2 *>(t.d_idx), t.d_b,
+                                          per, p.status);
+    count_launch();
+    if (cudaGetLastError() != cudaSuccess) return DVM_ECUDA;
+    k_hs_corr<<<(unsigned)p.ncells, CT, 0, p.stream>>>(static_cast<float *>(f),
+                                                      reinterpret_cast<const float2 *>(t.d_bc), t.d_xi,
+                                                      p.mom_out, p.nv, (float)(dt / kn), p.status);
+    count_launch();
+    return cudaGetLastError() == cudaSuccess ? DVM_OK : DVM_ECUDA;
+}
 
 }  // namespace dvm

@@ -1,24 +1,33 @@
 // Fused DVM step: upwind transport (Eq. 2) -> moments of f* -> conservative
-// BGK relaxation, one CTA per cell, f* kept in registers between the phases.
+// BGK relaxation, with f* held on chip between the phases.
 //
 // Layout (paper Sec. 3.1 steps 1-3): f[cell][group][position], 8 sign groups
-// per cell.  Thread t of a cell owns the same "quad" of positions (4 FP32 /
-// BF16 or 2 FP64 values along z) in all 8 groups, so every warp reads 32
-// consecutive quads of one group (coalesced 16-byte loads) and the stencil
-// of Eq. 2 is uniform across the warp: it depends on the group only through
-// the signs of the velocity components (Sec. 3.1).
+// per cell.  A compute thread owns the same "quad" of positions (4 FP32/BF16
+// or 2 FP64 values along z) in all 8 groups: every warp reads 32 consecutive
+// quads of one group (coalesced 16-byte loads) and the stencil of Eq. 2 is
+// warp-uniform, since it depends on the group only through the signs of the
+// velocity components (Sec. 3.1).
 //
-// Phase 1: f*_i = f_i - dt sum_d |xi_d,i| (f_i / h - sum_k w_k src_k,i) with
-//   the upwind sources of the cell's side facing the incoming velocity.
-// Phase 2: the seven sums sum f, sum j_d f, sum j_d^2 f (j_d the odd integer
-//   with xi_d = (h_d/2) j_d) in FP32 per thread, double-float across threads,
-//   FP64 at the end -> rho, u, T.
-// Phase 3 (warp 0): the discrete Maxwellian factorises over the tensor grid,
-//   so the 5x5 moment matrix sum psi_r psi_s M dV comes from 1D sums of the
-//   per-axis factors (FP64); Gauss with pivoting gives d of the correction
-//   polynomial (the Eq. 6 form) that makes M~ = M (1 + d.psi) carry the
-//   moments of f*.
-// Phase 4: f^{n+1} = f* + nu dt (M~ - f*), nu = sqrt(8/pi) rho sqrt(T) / Kn.
+// Persistent CTAs walk the Morton-ordered cells with stride gridDim.x, so the
+// CTAs in flight cover a contiguous Morton window and upwind neighbours are
+// served from L2.  Each CTA has NCW compute warps and one solver warp and
+// overlaps cells in a two-stage pipeline with one barrier per cell:
+//
+//   iteration i, compute warps:  phase 1 of cell c_i        | barrier | phase 3 of c_{i-1}
+//   iteration i, solver warp:    phase 2 of c_{i-1},        | barrier |
+//                                prefetch stencil of c_{i+1}
+//
+// Phase 1: f*_i = f_i - dt sum_d |xi_d,i| (f_i / h - sum_k w_k src_k,i) into a
+//   shared buffer; per-thread FP32 partials of the seven sums sum f,
+//   sum j_d f, sum j_d^2 f (xi_d = (h_d/2) j_d with j_d an odd integer),
+//   reduced per warp.
+// Phase 2 (solver warp): double-float sum of the warp partials -> rho, u, T;
+//   the discrete Maxwellian factorises over the tensor grid, so its moments
+//   in the centred basis phi = (1, c, |c|^2 - 3), c = (xi - u)/sqrt(T), are
+//   products of 1D sums; the five coefficients d of M~ = M (1 + d.phi) (the
+//   correction form of Eq. 6) make M~ carry the moments of f*.  The defects
+//   of M's own moments (the right-hand side) are formed in double-float.
+// Phase 3: f^{n+1} = f* + nu dt (M~ - f*), nu = sqrt(8/pi) rho sqrt(T) / Kn.
 #include <atomic>
 #include <cmath>
 
@@ -35,46 +44,82 @@ void count_launch() { g_launches.fetch_add(1); }
 
 namespace {
 
-constexpr int MAXT = 512;
-constexpr int NAX = 64;  // nodes per velocity axis supported
+constexpr int MAXCW = 14;     // compute warps per CTA (at most)
+constexpr int NAX = 32;       // velocity nodes per axis supported
+constexpr int MAXT = MAXCW * 32 + 32;
 
 template <typename TC> __device__ inline TC tc_exp(TC x);
 template <> __device__ inline float tc_exp<float>(float x) { return expf(x); }
 template <> __device__ inline double tc_exp<double>(double x) { return exp(x); }
+
+// coefficient slots written by the solver warp for phase 3
+enum { CF_PRE = 0, CF_UX, CF_UY, CF_UZ, CF_IST, CF_D0, CF_DX, CF_DY, CF_DZ, CF_D4, CF_NUDT, CF_N };
+
+template <typename TC> struct StepSmem {
+    int32_t src[2][24];
+    TC w[2][24];
+    int cnt[2][8];
+    TC invh[2];
+    TC red[2][MAXCW][7];
+    TC g[2][3][NAX];
+    TC coef[2][CF_N];
+    int ok[2];
+};
+
+template <typename TC> struct Consts {
+    using N = Num<TC>;
+    using X = typename N::X;
+    X dV, hh[3], hh2[3], third, c15, one;
+};
+
+template <typename TC>
+__device__ inline typename Num<TC>::X split(double v)
+{
+    if constexpr (sizeof(TC) == 8) {
+        return v;
+    } else {
+        const float hi = (float)v;
+        return ffn{hi, (float)(v - (double)hi)};
+    }
+}
 
 template <typename TS, int DIM, int COLL>
 __global__ void __launch_bounds__(MAXT, 2) k_step(const StepParams p)
 {
     using S = Store<TS>;
     using TC = typename S::TC;
-    using R = Red<TC>;
-    using RT = typename R::T;
+    using N = Num<TC>;
+    using X = typename N::X;
     constexpr int VEC = S::VEC;
 
-    __shared__ int32_t s_src[24];
-    __shared__ TC s_w[24];
-    __shared__ int s_cnt[6];
-    __shared__ TC s_g[3][NAX];
-    __shared__ RT s_red[MAXT / 32][7];
-    __shared__ TC s_coef[7];
-    __shared__ int s_ok;
+    __shared__ StepSmem<TC> sm;
+    extern __shared__ __align__(16) unsigned char dsm[];
+    TC *buf = reinterpret_cast<TC *>(dsm);  // [2][nv] f* of two cells
 
-    const int64_t cell = blockIdx.x;
-    const int t = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int ncw = (blockDim.x >> 5) - 1;  // compute warps; the last warp solves
+    const bool solver = warp == ncw;
     const int Q = p.P / VEC;
-    const bool active = t < Q;
-    if (t < 24) {
-        s_src[t] = p.st_src[cell * 24 + t];
-        s_w[t] = static_cast<const TC *>(p.st_w)[cell * 24 + t];
-    }
-    if (t < 6) s_cnt[t] = p.st_cnt[cell * 8 + t];
-    const TC invh = static_cast<const TC *>(p.inv_h)[cell];
-    __syncthreads();
+    const int64_t G = gridDim.x;
+    const int64_t ncell_cta = (p.ncells - blockIdx.x + G - 1) / G;
 
-    const int hz = p.half[2], hy = p.half[1];
-    const int p0 = active ? t * VEC : 0;
-    const int mz0 = p0 % hz, my = (p0 / hz) % hy, mx = p0 / (hz * hy);
-    TC ax, ay, az[VEC], jz[VEC];
+    // ---- stencil prefetch (solver warp): cell -> slot
+    auto load_stencil = [&](int64_t cell, int slot) {
+        if (lane < 24) {
+            sm.src[slot][lane] = p.st_src[cell * 24 + lane];
+            sm.w[slot][lane] = static_cast<const TC *>(p.st_w)[cell * 24 + lane];
+        }
+        if (lane < 6) sm.cnt[slot][lane] = p.st_cnt[cell * 8 + lane];
+        if (lane == 0) sm.invh[slot] = static_cast<const TC *>(p.inv_h)[cell];
+    };
+    if (solver && ncell_cta > 0) load_stencil(blockIdx.x, 0);
+
+    // ---- per-thread position (compute warps)
+    const bool active = !solver && tid < Q;
+    const int hz = p.half[2], hyy = p.half[1], hxx = p.half[0];
+    const int p0 = active ? tid * VEC : 0;
+    const int mz0 = p0 % hz, my = (p0 / hz) % hyy, mx = p0 / (hz * hyy);
+    TC ax, ay, az[VEC];
     if constexpr (sizeof(TC) == 8) {
         ax = p.amag[mx];
         ay = p.amag[32 + my];
@@ -86,213 +131,310 @@ __global__ void __launch_bounds__(MAXT, 2) k_step(const StepParams p)
 #pragma unroll
         for (int e = 0; e < VEC; e++) az[e] = p.amag_f[64 + mz0 + e];
     }
-#pragma unroll
-    for (int e = 0; e < VEC; e++) jz[e] = (TC)(2 * (mz0 + e) + 1);
     const TC jx = (TC)(2 * mx + 1), jy = (TC)(2 * my + 1);
-
     const TS *__restrict__ fin = static_cast<const TS *>(p.f_in);
     TS *__restrict__ fout = static_cast<TS *>(p.f_out);
-    const TC *__restrict__ finf = static_cast<const TC *>(p.finf);
-    const int64_t cbase = cell * (int64_t)p.nv;
     const TC dt = (TC)p.dt;
 
-    TC fs[8][VEC];
-    TC aS0 = 0, aX = 0, aY = 0, aZ1 = 0, aZ2 = 0;
+    // ---- solver constants, split once into shared memory
+    __shared__ Consts<TC> K;
+    if (solver && lane == 0) {
+        K.dV = split<TC>(p.dV);
+        for (int d = 0; d < 3; d++) {
+            K.hh[d] = split<TC>(0.5 * p.hv[d]);
+            K.hh2[d] = split<TC>(0.25 * p.hv[d] * p.hv[d]);
+        }
+        K.third = split<TC>(1.0 / 3.0);
+        K.c15 = split<TC>(0.06349363593424097);  // (2 pi)^(-3/2)
+        K.one = split<TC>(1.0);
+    }
+    __syncthreads();
+
+    for (int64_t it = 0; it <= ncell_cta; it++) {
+        const int b = (int)(it & 1), bp = b ^ 1;
+        const int64_t cell = blockIdx.x + it * G;            // c_i (valid if it < ncell_cta)
+        const int64_t prev = blockIdx.x + (it - 1) * G;      // c_{i-1} (valid if it >= 1)
+
+        if (!solver) {
+            // ================= phase 1: transport of c_i into buf[b]
+            if (it < ncell_cta) {
+                // per-thread partials: sum f, sum s_x f, sum s_y f, sum j_z s_z f, sum j_z^2 f
+                TC a0 = 0, ax1 = 0, ay1 = 0, az1 = 0, az2 = 0;
+                if (active) {
+                    const int64_t cbase = cell * (int64_t)p.nv;
+                    const TC invh = sm.invh[b];
+                    TC *bb = buf + (size_t)b * p.nv;
 #pragma unroll
-    for (int o = 0; o < 8; o++) {
-        const int off = o * p.P + p0;
-        TC self[VEC];
+                    for (int o = 0; o < 8; o++) {
+                        const int off = o * p.P + p0;
+                        TC self[VEC], acc[VEC];
+                        S::load(fin + cbase + off, self);
 #pragma unroll
-        for (int e = 0; e < VEC; e++) self[e] = 0;
-        TC acc[VEC];
+                        for (int e = 0; e < VEC; e++) acc[e] = 0;
 #pragma unroll
-        for (int e = 0; e < VEC; e++) acc[e] = 0;
-        if (active) {
-            S::load(fin + cbase + off, self);
+                        for (int d = 0; d < DIM; d++) {
+                            const int list = 2 * d + (((o >> (2 - d)) & 1) ? 0 : 1);
+                            TC sd[VEC];
+                            // every list has at least one source; the first
+                            // one is loaded unconditionally so it can be hoisted
+                            const int cnt = sm.cnt[b][list];
+                            {
+                                const int32_t src = sm.src[b][list * 4];
+                                const TC w = sm.w[b][list * 4];
+                                TC v[VEC];
+                                S::load(fin + (int64_t)(src & 0x0fffffff) * p.nv + (o ^ (src >> 28)) * p.P + p0, v);
 #pragma unroll
-            for (int d = 0; d < DIM; d++) {
-                const int pos = (o >> (2 - d)) & 1;
-                const int list = 2 * d + (pos ? 0 : 1);
-                TC sd[VEC];
+                                for (int e = 0; e < VEC; e++) sd[e] = w * v[e];
+                            }
+                            for (int q = 1; q < cnt; q++) {
+                                const int32_t src = sm.src[b][list * 4 + q];
+                                const TC w = sm.w[b][list * 4 + q];
+                                TC v[VEC];
+                                S::load(fin + (int64_t)(src & 0x0fffffff) * p.nv + (o ^ (src >> 28)) * p.P + p0, v);
 #pragma unroll
-                for (int e = 0; e < VEC; e++) sd[e] = 0;
-                const int cnt = s_cnt[list];
-                for (int q = 0; q < cnt; q++) {
-                    const int32_t src = s_src[list * 4 + q];
-                    const TC w = s_w[list * 4 + q];
-                    TC v[VEC];
-                    if (src >= 0) {
-                        S::load(fin + (int64_t)src * p.nv + off, v);
-                    } else if (src == SRC_INFLOW) {
+                                for (int e = 0; e < VEC; e++) sd[e] = fma(w, v[e], sd[e]);
+                            }
 #pragma unroll
-                        for (int e = 0; e < VEC; e++) v[e] = finf[off + e];
-                    } else if (src == SRC_OUTFLOW) {
+                            for (int e = 0; e < VEC; e++) {
+                                const TC a = d == 0 ? ax : (d == 1 ? ay : az[e]);
+                                acc[e] = fma(a, fma(self[e], invh, -sd[e]), acc[e]);
+                            }
+                        }
+                        TC fs[VEC], r0 = 0, r1 = 0, r2 = 0;
 #pragma unroll
-                        for (int e = 0; e < VEC; e++) v[e] = self[e];
-                    } else {
-                        S::load(fin + cbase + (o ^ (4 >> d)) * p.P + p0, v);
+                        for (int e = 0; e < VEC; e++) {
+                            fs[e] = fma(-dt, acc[e], self[e]);
+                            const TC jz = (TC)(2 * (mz0 + e) + 1);
+                            r0 += fs[e];
+                            r1 = fma(jz, fs[e], r1);
+                            r2 = fma(jz * jz, fs[e], r2);
+                        }
+                        a0 += r0;
+                        ax1 += (o & 4) ? r0 : -r0;
+                        ay1 += (o & 2) ? r0 : -r0;
+                        az1 += (o & 1) ? r1 : -r1;
+                        az2 += r2;
+                        if constexpr (VEC == 4)
+                            *reinterpret_cast<float4 *>(bb + off) = make_float4(fs[0], fs[1], fs[2], fs[3]);
+                        else
+                            *reinterpret_cast<double2 *>(bb + off) = make_double2(fs[0], fs[1]);
                     }
-#pragma unroll
-                    for (int e = 0; e < VEC; e++) sd[e] = fma(w, v[e], sd[e]);
                 }
+                // seven integer-weighted partial sums of this thread
+                TC m[7];
+                m[0] = a0;
+                m[1] = jx * ax1;
+                m[2] = jy * ay1;
+                m[3] = az1;
+                m[4] = jx * jx * a0;
+                m[5] = jy * jy * a0;
+                m[6] = az2;
 #pragma unroll
-                for (int e = 0; e < VEC; e++) {
-                    const TC a = d == 0 ? ax : (d == 1 ? ay : az[e]);
-                    acc[e] = fma(a, fma(self[e], invh, -sd[e]), acc[e]);
+                for (int k = 0; k < 7; k++) {
+#pragma unroll
+                    for (int off = 16; off > 0; off >>= 1) m[k] += __shfl_down_sync(0xffffffffu, m[k], off);
+                    if (lane == 0) sm.red[b][warp][k] = m[k];
                 }
-            }
-        }
-        TC r0 = 0, r1 = 0, r2 = 0;
-#pragma unroll
-        for (int e = 0; e < VEC; e++) {
-            fs[o][e] = fma(-dt, acc[e], self[e]);
-            r0 += fs[o][e];
-            r1 = fma(jz[e], fs[o][e], r1);
-            r2 = fma(jz[e] * jz[e], fs[o][e], r2);
-        }
-        aS0 += r0;
-        aX += (o & 4) ? r0 : -r0;
-        aY += (o & 2) ? r0 : -r0;
-        aZ1 += (o & 1) ? r1 : -r1;
-        aZ2 += r2;
-    }
-
-    // ---- block reduction of the seven integer-weighted sums
-    RT m[7];
-    m[0] = R::from(aS0);
-    m[1] = R::mul(jx, aX);
-    m[2] = R::mul(jy, aY);
-    m[3] = R::from(aZ1);
-    m[4] = R::mul(jx * jx, aS0);
-    m[5] = R::mul(jy * jy, aS0);
-    m[6] = R::from(aZ2);
-    const int lane = t & 31, warp = t >> 5, nwarps = (blockDim.x + 31) >> 5;
-#pragma unroll
-    for (int k = 0; k < 7; k++)
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) m[k] = R::add(m[k], R::shfl_down(m[k], off));
-    if (lane == 0)
-#pragma unroll
-        for (int k = 0; k < 7; k++) s_red[warp][k] = m[k];
-    __syncthreads();
-
-    if (warp == 0) {
-        double Ssum[7];
-#pragma unroll
-        for (int k = 0; k < 7; k++) {
-            RT v = lane < nwarps ? s_red[lane][k] : R::zero();
-#pragma unroll
-            for (int off = 16; off > 0; off >>= 1) v = R::add(v, R::shfl_down(v, off));
-            Ssum[k] = __shfl_sync(0xffffffffu, R::to_double(v), 0);
-        }
-        const double hx2 = 0.5 * p.hv[0], hy2 = 0.5 * p.hv[1], hz2 = 0.5 * p.hv[2];
-        const double s0 = Ssum[0];
-        const double rho = p.dV * s0;
-        const double ux = hx2 * Ssum[1] / s0, uy = hy2 * Ssum[2] / s0, uz = hz2 * Ssum[3] / s0;
-        const double e2 = (hx2 * hx2 * Ssum[4] + hy2 * hy2 * Ssum[5] + hz2 * hz2 * Ssum[6]) / s0;
-        const double T = (e2 - (ux * ux + uy * uy + uz * uz)) / 3.0;
-        int flags = 0;
-        if (!(s0 > 0.0) || !(T > 0.0) || !isfinite(T) || !isfinite(ux + uy + uz)) flags |= ST_NONPOS;
-        if (COLL == DVM_COLL_BGK && flags == 0) {
-            const double u[3] = {ux, uy, uz};
-            double m1[3][5];
-#pragma unroll
-            for (int d = 0; d < 3; d++)
-#pragma unroll
-                for (int q = 0; q < 5; q++) m1[d][q] = 0.0;
-#pragma unroll
-            for (int d = 0; d < 3; d++) {
-                const int nd = p.n[d], hd = p.half[d];
-                for (int l = lane; l < nd; l += 32) {
-                    const int mm = l < hd ? hd - 1 - l : l - hd;
-                    const double mag = p.amag[d * 32 + mm];
-                    const double xi = l < hd ? -mag : mag;
-                    const double arg = -(xi - u[d]) * (xi - u[d]) / (2.0 * T);
-                    const TC g = tc_exp<TC>((TC)arg);
-                    s_g[d][l] = g;
-                    double pw = (double)g;
-                    m1[d][0] += pw; pw *= xi;
-                    m1[d][1] += pw; pw *= xi;
-                    m1[d][2] += pw; pw *= xi;
-                    m1[d][3] += pw; pw *= xi;
-                    m1[d][4] += pw;
-                }
-            }
-#pragma unroll
-            for (int d = 0; d < 3; d++)
-#pragma unroll
-                for (int q = 0; q < 5; q++) m1[d][q] = warp_allsum(m1[d][q]);
-            if (lane == 0) {
-                const double twopiT = 2.0 * 3.14159265358979323846 * T;
-                const double cn = rho / (twopiT * sqrt(twopiT));
-                const double G = cn * p.dV;
-                auto E = [&](int a, int b, int c) { return G * m1[0][a] * m1[1][b] * m1[2][c]; };
-                double A[25], rhs[5], dd[5];
-                A[0] = E(0, 0, 0);
-                A[1] = E(1, 0, 0); A[2] = E(0, 1, 0); A[3] = E(0, 0, 1);
-                A[4] = E(2, 0, 0) + E(0, 2, 0) + E(0, 0, 2);
-                A[6] = E(2, 0, 0); A[7] = E(1, 1, 0); A[8] = E(1, 0, 1);
-                A[9] = E(3, 0, 0) + E(1, 2, 0) + E(1, 0, 2);
-                A[12] = E(0, 2, 0); A[13] = E(0, 1, 1);
-                A[14] = E(2, 1, 0) + E(0, 3, 0) + E(0, 1, 2);
-                A[18] = E(0, 0, 2);
-                A[19] = E(2, 0, 1) + E(0, 2, 1) + E(0, 0, 3);
-                A[24] = E(4, 0, 0) + E(0, 4, 0) + E(0, 0, 4) +
-                        2.0 * (E(2, 2, 0) + E(2, 0, 2) + E(0, 2, 2));
-                for (int r = 0; r < 5; r++)
-                    for (int c = 0; c < r; c++) A[r * 5 + c] = A[c * 5 + r];
-                const double F[5] = {rho, rho * ux, rho * uy, rho * uz,
-                                     p.dV * (hx2 * hx2 * Ssum[4] + hy2 * hy2 * Ssum[5] + hz2 * hz2 * Ssum[6])};
-                for (int r = 0; r < 5; r++) rhs[r] = F[r] - A[r * 5];
-                if (!solve5(A, rhs, dd)) flags |= ST_SINGULAR;
-                const double nudt = sqrt(8.0 / 3.14159265358979323846) * rho * sqrt(T) / p.kn * p.dt;
-                if (nudt > 1.0) flags |= ST_NUDT;
-                s_coef[0] = (TC)cn;
-                for (int q = 0; q < 5; q++) s_coef[1 + q] = (TC)dd[q];
-                s_coef[6] = (TC)nudt;
-            }
-        }
-        if (lane == 0) {
-            double *mo = p.mom_out + cell * 5;
-            mo[0] = rho; mo[1] = ux; mo[2] = uy; mo[3] = uz; mo[4] = T;
-            if (flags) atomicOr(p.status, flags);
-            s_ok = (flags & (ST_NONPOS | ST_SINGULAR)) == 0;
-        }
-    }
-    __syncthreads();
-
-    if (!active) return;
-    const bool collide = COLL == DVM_COLL_BGK && s_ok;
-    TC cn = 0, d0 = 0, dxx = 0, dyy = 0, dzz = 0, d2 = 0, nudt = 0;
-    if (collide) {
-        cn = s_coef[0]; d0 = s_coef[1]; dxx = s_coef[2]; dyy = s_coef[3]; dzz = s_coef[4];
-        d2 = s_coef[5]; nudt = s_coef[6];
-    }
-    const int hx = p.half[0], hyy = p.half[1], hzz = p.half[2];
-#pragma unroll
-    for (int o = 0; o < 8; o++) {
-        const int off = o * p.P + p0;
-        TC out[VEC];
-        if (collide) {
-            const bool px = o & 4, py = o & 2, pz = o & 1;
-            const TC xx = px ? ax : -ax, yy = py ? ay : -ay;
-            const int kx = px ? hx + mx : hx - 1 - mx;
-            const int ky = py ? hyy + my : hyy - 1 - my;
-            const TC cxy = cn * s_g[0][kx] * s_g[1][ky];
-            const TC pxy = (TC)1 + d0 + dxx * xx + dyy * yy + d2 * (xx * xx + yy * yy);
-#pragma unroll
-            for (int e = 0; e < VEC; e++) {
-                const TC zz = pz ? az[e] : -az[e];
-                const int kz = pz ? hzz + mz0 + e : hzz - 1 - mz0 - e;
-                const TC mt = cxy * s_g[2][kz] * (pxy + dzz * zz + d2 * zz * zz);
-                out[e] = fma(nudt, mt - fs[o][e], fs[o][e]);
             }
         } else {
+            // ================= phase 2 (solver warp): cell c_{i-1}
+            if (it >= 1) {
+                X Ssum[7];
 #pragma unroll
-            for (int e = 0; e < VEC; e++) out[e] = fs[o][e];
+                for (int k = 0; k < 7; k++) {
+                    Ssum[k] = N::make(lane < ncw ? sm.red[bp][lane][k] : (TC)0);
+#pragma unroll
+                    for (int m = 16; m > 0; m >>= 1) Ssum[k] = Ssum[k] + N::shfl_xor(Ssum[k], m);
+                }
+                const X s0 = Ssum[0];
+                const X rho = s0 * K.dV;
+                const X inv = K.one / s0;
+                const X ux = Ssum[1] * inv * K.hh[0];
+                const X uy = Ssum[2] * inv * K.hh[1];
+                const X uz = Ssum[3] * inv * K.hh[2];
+                const X e2 = (Ssum[4] * K.hh2[0] + Ssum[5] * K.hh2[1] + Ssum[6] * K.hh2[2]) * inv;
+                const X T = (e2 - (ux * ux + uy * uy + uz * uz)) * K.third;
+                int flags = 0;
+                if (!N::finite_pos(s0) || !N::finite_pos(T) || !isfinite(N::f(ux) + N::f(uy) + N::f(uz)))
+                    flags |= ST_NONPOS;
+                const TC uT[3] = {N::tc(ux), N::tc(uy), N::tc(uz)};
+                if (COLL == DVM_COLL_BGK && flags == 0) {
+                    const X isT = N::rsqrt(T);
+                    const TC isTt = N::tc(isT);
+                    const X Kc = rho * K.c15 * isT * isT * isT;  // rho (2 pi T)^(-3/2)
+                    const X KdV = Kc * K.dV;
+                    X G0[3], G2[3];
+                    TC G1[3], G3[3], G4[3];
+#pragma unroll
+                    for (int d = 0; d < 3; d++) {
+                        G0[d] = N::make((TC)0); G2[d] = N::make((TC)0);
+                        G1[d] = 0; G3[d] = 0; G4[d] = 0;
+                        const int hd = p.half[d];
+                        if (lane < p.n[d]) {
+                            const int mm = lane < hd ? hd - 1 - lane : lane - hd;
+                            TC xi;
+                            if constexpr (sizeof(TC) == 8) xi = p.amag[d * 32 + mm];
+                            else xi = p.amag_f[d * 32 + mm];
+                            if (lane < hd) xi = -xi;
+                            const TC c = (xi - uT[d]) * isTt;
+                            const TC g = tc_exp<TC>((TC)-0.5 * c * c);
+                            sm.g[bp][d][lane] = g;
+                            G0[d] = N::make(g);
+                            G2[d] = N::make(g) * c * c;
+                            G1[d] = g * c;
+                            G3[d] = G1[d] * c * c;
+                            G4[d] = G3[d] * c;
+                        }
+#pragma unroll
+                        for (int m = 16; m > 0; m >>= 1) {
+                            G0[d] = G0[d] + N::shfl_xor(G0[d], m);
+                            G2[d] = G2[d] + N::shfl_xor(G2[d], m);
+                            G1[d] += __shfl_xor_sync(0xffffffffu, G1[d], m);
+                            G3[d] += __shfl_xor_sync(0xffffffffu, G3[d], m);
+                            G4[d] += __shfl_xor_sync(0xffffffffu, G4[d], m);
+                        }
+                    }
+                    if (lane == 0) {
+                        // moments of M in the centred basis; defects in double-float
+                        const X P0 = G0[0] * G0[1] * G0[2];
+                        const X Q2 = G2[0] * G0[1] * G0[2] + G0[0] * G2[1] * G0[2] + G0[0] * G0[1] * G2[2];
+                        const TC r0 = N::tc(rho - KdV * P0);
+                        const TC b04 = N::tc(KdV * (Q2 - P0 - P0 - P0));
+                        const TC k = N::tc(KdV);
+                        TC g0[3], g2[3];
+                        for (int d = 0; d < 3; d++) { g0[d] = N::tc(G0[d]); g2[d] = N::tc(G2[d]); }
+                        const TC p0v = g0[0] * g0[1] * g0[2];
+                        TC A[25], rhs[5], dd[5];
+                        A[0] = N::tc(KdV * P0);
+                        A[1] = k * G1[0] * g0[1] * g0[2];
+                        A[2] = k * g0[0] * G1[1] * g0[2];
+                        A[3] = k * g0[0] * g0[1] * G1[2];
+                        A[4] = b04;
+                        A[6] = k * g2[0] * g0[1] * g0[2];
+                        A[7] = k * G1[0] * G1[1] * g0[2];
+                        A[8] = k * G1[0] * g0[1] * G1[2];
+                        A[9] = k * (G3[0] * g0[1] * g0[2] + G1[0] * g2[1] * g0[2] + G1[0] * g0[1] * g2[2] -
+                                    (TC)3 * G1[0] * g0[1] * g0[2]);
+                        A[12] = k * g0[0] * g2[1] * g0[2];
+                        A[13] = k * g0[0] * G1[1] * G1[2];
+                        A[14] = k * (g2[0] * G1[1] * g0[2] + g0[0] * G3[1] * g0[2] + g0[0] * G1[1] * g2[2] -
+                                     (TC)3 * g0[0] * G1[1] * g0[2]);
+                        A[18] = k * g0[0] * g0[1] * g2[2];
+                        A[19] = k * (g2[0] * g0[1] * G1[2] + g0[0] * g2[1] * G1[2] + g0[0] * g0[1] * G3[2] -
+                                     (TC)3 * g0[0] * g0[1] * G1[2]);
+                        const TC s2 = g2[0] * g0[1] * g0[2] + g0[0] * g2[1] * g0[2] + g0[0] * g0[1] * g2[2];
+                        A[24] = k * (G4[0] * g0[1] * g0[2] + g0[0] * G4[1] * g0[2] + g0[0] * g0[1] * G4[2] +
+                                     (TC)2 * (g2[0] * g2[1] * g0[2] + g2[0] * g0[1] * g2[2] + g0[0] * g2[1] * g2[2]) -
+                                     (TC)6 * s2 + (TC)9 * p0v);
+#pragma unroll
+                        for (int r = 0; r < 5; r++)
+#pragma unroll
+                            for (int c2 = 0; c2 < r; c2++) A[r * 5 + c2] = A[c2 * 5 + r];
+                        rhs[0] = r0;
+                        rhs[1] = -A[1];
+                        rhs[2] = -A[2];
+                        rhs[3] = -A[3];
+                        rhs[4] = -b04;
+                        if (!solve5<TC>(A, rhs, dd)) flags |= ST_SINGULAR;
+                        const TC rhot = N::tc(rho), Tt = N::tc(T);
+                        const TC nudt = (TC)(1.5957691216057308 * p.dt / p.kn) * rhot * sqrt(Tt);
+                        if (nudt > (TC)1) flags |= ST_NUDT;
+                        TC *cf = sm.coef[bp];
+                        cf[CF_PRE] = N::tc(Kc);
+                        cf[CF_UX] = uT[0]; cf[CF_UY] = uT[1]; cf[CF_UZ] = uT[2];
+                        cf[CF_IST] = isTt;
+                        cf[CF_D0] = dd[0]; cf[CF_DX] = dd[1]; cf[CF_DY] = dd[2]; cf[CF_DZ] = dd[3];
+                        cf[CF_D4] = dd[4];
+                        cf[CF_NUDT] = nudt;
+                    }
+                }
+                if (lane == 0) {
+                    double *mo = p.mom_out + prev * 5;
+                    mo[0] = (double)N::tc(rho);
+                    mo[1] = (double)N::tc(ux); mo[2] = (double)N::tc(uy); mo[3] = (double)N::tc(uz);
+                    mo[4] = (double)N::tc(T);
+                    if constexpr (sizeof(TC) == 4) {
+                        mo[0] = (double)rho.hi + (double)rho.lo;
+                        mo[1] = (double)ux.hi + (double)ux.lo;
+                        mo[2] = (double)uy.hi + (double)uy.lo;
+                        mo[3] = (double)uz.hi + (double)uz.lo;
+                        mo[4] = (double)T.hi + (double)T.lo;
+                    }
+                    if (flags) atomicOr(p.status, flags);
+                    sm.ok[bp] = COLL == DVM_COLL_BGK && (flags & (ST_NONPOS | ST_SINGULAR)) == 0;
+                }
+            }
+            // prefetch the stencil of c_{i+1}
+            if (it + 1 < ncell_cta) load_stencil(blockIdx.x + (it + 1) * G, bp);
         }
-        S::store(fout + cbase + off, out);
+        __syncthreads();
+
+        // ================= phase 3 (compute warps): collision of c_{i-1}
+        if (!solver && it >= 1 && active) {
+            const int64_t cbase = prev * (int64_t)p.nv;
+            const TC *bb = buf + (size_t)bp * p.nv;
+            const bool collide = sm.ok[bp];
+            const TC *cf = sm.coef[bp];
+            const TC pre = cf[CF_PRE], ux = cf[CF_UX], uy = cf[CF_UY], uz = cf[CF_UZ], ist = cf[CF_IST];
+            const TC d0 = cf[CF_D0], dx = cf[CF_DX], dy = cf[CF_DY], dz = cf[CF_DZ], d4 = cf[CF_D4];
+            const TC nudt = cf[CF_NUDT];
+#pragma unroll
+            for (int o = 0; o < 8; o++) {
+                const int off = o * p.P + p0;
+                TC fs[VEC], out[VEC];
+                if constexpr (VEC == 4) {
+                    const float4 t = *reinterpret_cast<const float4 *>(bb + off);
+                    fs[0] = t.x; fs[1] = t.y; fs[2] = t.z; fs[3] = t.w;
+                } else {
+                    const double2 t = *reinterpret_cast<const double2 *>(bb + off);
+                    fs[0] = t.x; fs[1] = t.y;
+                }
+                if (collide) {
+                    const bool px = o & 4, py = o & 2, pz = o & 1;
+                    const TC cx = ((px ? ax : -ax) - ux) * ist, cy = ((py ? ay : -ay) - uy) * ist;
+                    const int kx = px ? hxx + mx : hxx - 1 - mx;
+                    const int ky = py ? hyy + my : hyy - 1 - my;
+                    const TC cxy = pre * sm.g[bp][0][kx] * sm.g[bp][1][ky];
+                    const TC pxy = (TC)1 + d0 + dx * cx + dy * cy + d4 * (cx * cx + cy * cy - (TC)3);
+#pragma unroll
+                    for (int e = 0; e < VEC; e++) {
+                        const TC cz = ((pz ? az[e] : -az[e]) - uz) * ist;
+                        const int kz = pz ? hz + mz0 + e : hz - 1 - mz0 - e;
+                        const TC mt = cxy * sm.g[bp][2][kz] * (pxy + dz * cz + d4 * cz * cz);
+                        out[e] = fma(nudt, mt - fs[e], fs[e]);
+                    }
+                } else {
+#pragma unroll
+                    for (int e = 0; e < VEC; e++) out[e] = fs[e];
+                }
+                S::store(fout + cbase + off, out);
+            }
+        }
     }
+}
+
+template <typename TS, int DIM, int COLL>
+int launch_kernel(const StepParams &p, int ncw)
+{
+    using TC = typename Store<TS>::TC;
+    auto kern = k_step<TS, DIM, COLL>;
+    const int threads = (ncw + 1) * 32;
+    const size_t dyn = 2 * (size_t)p.nv * sizeof(TC);
+    static bool configured = false;
+    if (!configured) {
+        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) != cudaSuccess)
+            return DVM_ECUDA;
+        configured = true;
+    }
+    int dev = 0, nsm = 0, occ = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, dyn) != cudaSuccess || occ < 1)
+        return DVM_ENOTIMPL;
+    const int64_t grid = std::min<int64_t>(p.ncells, (int64_t)nsm * occ);
+    kern<<<(unsigned)grid, threads, dyn, p.stream>>>(p);
+    count_launch();
+    return cudaGetLastError() == cudaSuccess ? DVM_OK : DVM_ECUDA;
 }
 
 template <typename TS, int DIM>
@@ -300,18 +442,13 @@ int launch_typed(const StepParams &p)
 {
     const int vec = Store<TS>::VEC;
     if (p.P % vec != 0 || p.half[2] % vec != 0) return DVM_EINVAL;
-    const int Q = p.P / vec;
-    if (Q > MAXT) return DVM_ENOTIMPL;
     for (int d = 0; d < 3; d++)
         if (p.n[d] > NAX) return DVM_ENOTIMPL;
-    const int threads = (Q + 31) / 32 * 32;
-    const dim3 grid((unsigned)p.ncells);
-    if (p.coll == DVM_COLL_BGK)
-        k_step<TS, DIM, DVM_COLL_BGK><<<grid, threads, 0, p.stream>>>(p);
-    else
-        k_step<TS, DIM, DVM_COLL_NONE><<<grid, threads, 0, p.stream>>>(p);
-    count_launch();
-    return cudaGetLastError() == cudaSuccess ? DVM_OK : DVM_ECUDA;
+    const int Q = p.P / vec;
+    const int ncw = (Q + 31) / 32;
+    if (ncw > MAXCW) return DVM_ENOTIMPL;
+    if (p.coll == DVM_COLL_BGK) return launch_kernel<TS, DIM, DVM_COLL_BGK>(p, ncw);
+    return launch_kernel<TS, DIM, DVM_COLL_NONE>(p, ncw);
 }
 
 }  // namespace

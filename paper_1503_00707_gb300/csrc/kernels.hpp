@@ -10,6 +10,7 @@ enum : int {
     ST_NONPOS = 1,      // non-positive or non-finite density/temperature
     ST_SINGULAR = 2,    // singular or non-finite 5x5 correction system
     ST_NUDT = 4,        // relaxation factor nu*dt (or dt/Kn * max P B) above 1
+    ST_TIMEOUT = 8,     // a bounded wait on an asynchronous copy gave up
 };
 
 struct StepParams {
@@ -21,13 +22,12 @@ struct StepParams {
     int P;                // nodes per sign group = nv / 8
     int half[3];          // n[d] / 2
     int n[3];
-    const void *f_in;     // [ncells][nv] storage precision
+    const void *f_in;     // [ncells + 1][nv] storage precision (last: inflow ghost)
     void *f_out;
-    const int32_t *st_src;   // [ncells][6][4]
+    const int32_t *st_src;   // [ncells][6][4]: source cell | group flip << 28
     const void *st_w;        // [ncells][6][4]  compute precision
     const uint8_t *st_cnt;   // [ncells][8]
     const void *inv_h;       // [ncells]        compute precision
-    const void *finf;        // [nv] inflow ghost, compute precision
     const double *amag;      // [3][32] |xi| of the positive-side nodes m = 0..half-1
     const float *amag_f;     // same, rounded to FP32
     double dt, kn, dV;
