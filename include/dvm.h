@@ -213,6 +213,32 @@ int dvm_moments(dvm_ctx *ctx, double *rho, double *u, double *T);
  * post-collision state up to storage rounding). */
 int dvm_step_moments(dvm_ctx *ctx, double *rho, double *u, double *T);
 
+/* Size in bytes of the fixed device scratch used by dvm_hs_collide_noalloc. */
+#define DVM_HS_NOALLOC_SCRATCH_BYTES (64u << 20)
+
+/* Hard-sphere collision update f <- f + dt/Kn I(f) (the Eq. 3-6 operator of
+ * dvm_step, without transport) on caller-owned device memory, allocating
+ * nothing.  The paper has no counterpart: this entry point is for callers
+ * that must not allocate device memory while they run, such as a framework
+ * that owns all device memory through its own pool, code that records
+ * work into a CUDA graph, or a real-time loop sized once at start-up.
+ *   f       device pointer, FP32 [ncells][nv] in the library's velocity
+ *           order, read and written in place (owned by the caller);
+ *   ncells  number of cells in f; needs ncells * (8 nv + 40) bytes of
+ *           scratch, at most DVM_HS_NOALLOC_SCRATCH_BYTES: larger sizes
+ *           return DVM_EINVAL before any work is queued;
+ *   dt      time step.
+ * Uses the context's velocity grid, collision tables, Kn and stream, all
+ * set up beforehand (DVM_ESTATE otherwise; FP32 storage only).  Scratch is
+ * a fixed array in the library's device image: every GPU that loads the
+ * library holds it until the process exits, every call shares it (its
+ * contents are those of the last call; nothing in it needs to start at
+ * zero), and calls whose work overlaps on the GPU race on it.  The first
+ * call on a device looks up the array's device address; make that first
+ * call before any stream capture.  Like dvm_step it synchronises the stream
+ * once to read the status word. */
+int dvm_hs_collide_noalloc(dvm_ctx *ctx, float *f, int64_t ncells, double dt);
+
 /* Number of kernel launches the library has queued in this process. */
 int dvm_launch_count(int64_t *count);
 

@@ -33,7 +33,9 @@ EXPORTS = [
     "dvm_set_freestream", "dvm_init_maxwellian", "dvm_get_f", "dvm_set_f", "dvm_upload_f",
     "dvm_download_f", "dvm_f_device", "dvm_dt_cfl", "dvm_set_collision_tables", "dvm_step",
     "dvm_moments", "dvm_step_moments", "dvm_launch_count", "dvm_get_collision_tables",
+    "dvm_hs_collide_noalloc",
 ]
+HS_NOALLOC_SCRATCH_BYTES = 64 << 20
 
 
 class DvmError(RuntimeError):
@@ -105,6 +107,7 @@ def lib():
             "dvm_step_moments": [P, P, P, P],
             "dvm_launch_count": [P],
             "dvm_get_collision_tables": [P, P, P, P, P, P],
+            "dvm_hs_collide_noalloc": [P, P, i64, d],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -232,6 +235,11 @@ class Solver:
         disc = C.c_int64()
         self._chk(lib().dvm_get_collision_tables(self._h, _p(gam), _p(l), _p(m), _p(b), C.byref(disc)))
         return gam, l, m, b, disc.value
+
+    def hs_collide_noalloc(self, f_dev_ptr, ncells, dt):
+        """Collision update of caller-owned device f (FP32) with no device
+        allocation; f_dev_ptr is an integer device address."""
+        self._chk(lib().dvm_hs_collide_noalloc(self._h, C.c_void_p(f_dev_ptr), int(ncells), float(dt)))
 
     # ---- state
     def get_f(self):

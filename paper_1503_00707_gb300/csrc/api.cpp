@@ -694,6 +694,38 @@ int dvm_step_moments(dvm_ctx *c, double *rho, double *u, double *T)
     return copy_moments(c, c->d_mom, rho, u, T);
 }
 
+int dvm_hs_collide_noalloc(dvm_ctx *c, float *f, int64_t ncells, double dt)
+{
+    if (!c || !f || ncells < 1) return DVM_EINVAL;
+    if (c->state < 2 || !c->hs.ready) return fail(c, DVM_ESTATE, "set the velocity grid and the collision tables first");
+    if (c->cfg.precision != DVM_F32) return fail(c, DVM_ENOTIMPL, "the hard-sphere operator runs on FP32 storage");
+    if (!(dt > 0.0) || !std::isfinite(dt)) return fail(c, DVM_EINVAL, "dt must be positive");
+    const double need = (double)ncells * (8.0 * c->nv + 40.0);
+    if (need > (double)DVM_HS_NOALLOC_SCRATCH_BYTES)
+        return fail(c, DVM_EINVAL, "ncells * (8 nv + 40) bytes exceed the fixed scratch of "
+                                   "DVM_HS_NOALLOC_SCRATCH_BYTES");
+    dvm::StepParams p{};
+    p.dim = c->mesh.spec.dim;
+    p.prec = c->cfg.precision;
+    p.ncells = ncells;
+    p.nv = c->nv;
+    p.P = c->P;
+    p.status = c->d_status;
+    p.stream = c->stream;
+    int rc = dvm::launch_hs_collide_noalloc(c->hs, p, f, c->d_xi, c->dV, c->cfg.kn, dt);
+    if (rc) return fail(c, rc, rc == DVM_EINVAL ? "scratch too small" : "hard-sphere launch failed");
+    int st = 0;
+    rc = cuda_check(c, cudaMemcpyAsync(&st, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "read status");
+    if (!rc) rc = cuda_check(c, cudaStreamSynchronize(c->stream), "hard-sphere collision");
+    if (rc) return rc;
+    if (st) {
+        cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream);
+        if (st & dvm::ST_TIMEOUT) return fail(c, DVM_ETIMEOUT, "a bounded wait for an asynchronous tile copy gave up");
+        return fail(c, DVM_EUNSTABLE, "unstable collision update (singular correction or dt/Kn max(P B) > 1)");
+    }
+    return DVM_OK;
+}
+
 int dvm_launch_count(int64_t *count)
 {
     if (!count) return DVM_EINVAL;

@@ -6,6 +6,7 @@
 #include <string>
 #include <vector>
 
+#include "../../include/dvm.h"
 #include "kernels.hpp"
 
 namespace dvm {
@@ -44,6 +45,13 @@ int hs_prepare(HsTables &t, int64_t ncells, const DevAlloc &alloc, const DevFree
 // f (storage precision, already holding f* from the transport launch) is
 // updated in place: f <- f* + dt/Kn * I(f*).
 int launch_hs_collide(HsTables &t, const StepParams &p, void *f, double kn, double dt);
+
+// The same update on caller-owned f with a fixed, statically allocated
+// device scratch (no allocation).  Needs p.ncells * (8 nv + 40) bytes of
+// scratch at most DVM_HS_NOALLOC_SCRATCH_BYTES (else DVM_EINVAL); xi is the
+// node table [nv][3] in FP64 and dV the velocity cell volume.
+int launch_hs_collide_noalloc(HsTables &t, const StepParams &p, float *f, const double *xi, double dV,
+                              double kn, double dt);
 
 // Trials per node that the register-resident table layout supports.
 bool hs_trials_supported(int trials);

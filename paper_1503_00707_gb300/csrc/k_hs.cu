@@ -20,6 +20,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 
 #include "../../include/dvm.h"
 #include "common.cuh"
@@ -297,6 +298,83 @@ int launch_hs_collide(HsTables &t, const StepParams &p, void *f, double kn, doub
     k_hs_corr<<<(unsigned)p.ncells, CT, 0, p.stream>>>(static_cast<float *>(f),
                                                       reinterpret_cast<const float2 *>(t.d_bc), t.d_xi,
                                                       p.mom_out, p.nv, (float)(dt / kn), p.status);
+    count_launch();
+    return cudaGetLastError() == cudaSuccess ? DVM_OK : DVM_ECUDA;
+}
+
+// ---------------------------------------------------------------- allocation-free variant
+namespace {
+
+// Fixed scratch for dvm_hs_collide_noalloc.  It is part of the library's
+// device image, so every GPU that loads the library holds it until the
+// process exits; all calls share it.
+constexpr size_t NOALLOC_BYTES = (size_t)DVM_HS_NOALLOC_SCRATCH_BYTES;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];
+
+std::mutex g_noalloc_mu;
+void *g_noalloc_ptr[256] = {nullptr};
+
+// Device address of the fixed scratch on the current device.  In host code
+// g_noalloc_scratch names a host-side stand-in, so the address is looked up
+// once per device, with that device current.
+int noalloc_scratch(void **ptr)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) {
+        cudaGetLastError();
+        return DVM_ECUDA;
+    }
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+            cudaGetLastError();
+            return DVM_ECUDA;
+        }
+        g_noalloc_ptr[dev] = p;
+    }
+    *ptr = g_noalloc_ptr[dev];
+    return DVM_OK;
+}
+
+}  // namespace
+
+int launch_hs_collide_noalloc(HsTables &t, const StepParams &p, float *f, const double *xi, double dV,
+                              double kn, double dt)
+{
+    if (p.prec != DVM_F32) return DVM_ENOTIMPL;
+    if (!t.ready || t.nv != p.nv) return DVM_ESTATE;
+    const size_t need_bc = (size_t)p.ncells * p.nv * 2 * sizeof(float);
+    if (need_bc + (size_t)p.ncells * 5 * sizeof(double) > NOALLOC_BYTES) return DVM_EINVAL;
+    void *base = nullptr;
+    int rc = noalloc_scratch(&base);
+    if (rc) return rc;
+    float *bc = static_cast<float *>(base);
+    double *mom = reinterpret_cast<double *>(static_cast<unsigned char *>(base) + need_bc);
+    rc = launch_moments(DVM_F32, f, p.ncells, p.nv, xi, dV, mom, p.stream);
+    if (rc) return rc;
+    const int tpn = t.trials / HE, npc = HT / tpn;
+    const int chunks = (p.nv + npc - 1) / npc;
+    const size_t dyn = 2 * (size_t)p.nv * sizeof(float);
+    if (dyn > 200 * 1024) return DVM_ENOTIMPL;
+    if (cudaFuncSetAttribute(k_hs_bc, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) != cudaSuccess)
+        return DVM_ECUDA;
+    int dev = 0, nsm = 0, occ = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_hs_bc, HT, dyn) != cudaSuccess || occ < 1)
+        return DVM_ENOTIMPL;
+    int64_t splits = std::max<int64_t>(1, (2 * (int64_t)nsm * occ + chunks - 1) / chunks);
+    splits = std::min<int64_t>(splits, p.ncells);
+    const int64_t per = (p.ncells + splits - 1) / splits;
+    splits = (p.ncells + per - 1) / per;
+    k_hs_bc<<<dim3((unsigned)chunks, (unsigned)splits), HT, dyn, p.stream>>>(
+        f, reinterpret_cast<float2 *>(bc), p.ncells, p.nv, t.trials, static_cast<const uint2 *>(t.d_idx), t.d_b,
+        per, p.status);
+    count_launch();
+    if (cudaGetLastError() != cudaSuccess) return DVM_ECUDA;
+    k_hs_corr<<<(unsigned)p.ncells, CT, 0, p.stream>>>(f, reinterpret_cast<const float2 *>(bc), t.d_xi, mom, p.nv,
+                                                      (float)(dt / kn), p.status);
     count_launch();
     return cudaGetLastError() == cudaSuccess ? DVM_OK : DVM_ECUDA;
 }
