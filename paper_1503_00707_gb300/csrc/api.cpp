@@ -45,6 +45,7 @@ struct dvm_ctx {
     double *d_mom = nullptr;     // step moments [ncells][5]
     double *d_mom2 = nullptr;    // moments of stored f
     int *d_status = nullptr;
+    unsigned long long *d_counter = nullptr;
     bool have_step_moments = false;
     bool mesh_on_device = false;
     dvm::HsTables hs;
@@ -124,11 +125,13 @@ int ensure_device(dvm_ctx *c)
         cudaGetLastError();
         return fail(c, DVM_ECUDA, "no CUDA device available");
     }
-    if (cudaMalloc(&c->d_status, sizeof(int)) != cudaSuccess || cudaMemset(c->d_status, 0, sizeof(int)) != cudaSuccess) {
+    if (cudaMalloc(&c->d_status, 16) != cudaSuccess || cudaMemset(c->d_status, 0, 16) != cudaSuccess) {
         cudaGetLastError();
         c->d_status = nullptr;
         return fail(c, DVM_ECUDA, "device status word allocation failed");
     }
+    // the step kernel's cell dispenser shares the allocation
+    c->d_counter = reinterpret_cast<unsigned long long *>(c->d_status + 2);
     return DVM_OK;
 }
 
@@ -626,6 +629,7 @@ int dvm_step(dvm_ctx *c, int nsteps, double dt)
     p.dV = c->dV;
     p.mom_out = c->d_mom;
     p.status = c->d_status;
+    p.counter = c->d_counter;
     p.stream = c->stream;
     if (c->cfg.collision == DVM_COLL_HS) {
         int rc = dvm::hs_prepare(c->hs, p.ncells, [c](size_t b) { return dev_alloc(c, b); },
@@ -635,6 +639,10 @@ int dvm_step(dvm_ctx *c, int nsteps, double dt)
     for (int s = 0; s < nsteps; s++) {
         p.f_in = c->d_f[c->cur];
         p.f_out = c->d_f[1 - c->cur];
+        if (cudaMemsetAsync(c->d_counter, 0, sizeof(unsigned long long), c->stream) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(c, DVM_ECUDA, "counter reset failed");
+        }
         int rc = dvm::launch_step(p);
         if (rc) return fail(c, rc, rc == DVM_ENOTIMPL ? "velocity grid too large for the step kernel" : "step launch failed");
         if (c->cfg.collision == DVM_COLL_HS) {

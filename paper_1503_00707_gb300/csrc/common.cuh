@@ -25,6 +25,11 @@ template <> struct Store<double> {
     {
         __stcs(reinterpret_cast<double2 *>(p), make_double2(v[0], v[1]));
     }
+    __device__ static inline void load_shared(const double *p, double v[2])
+    {
+        const double2 t = *reinterpret_cast<const double2 *>(p);
+        v[0] = t.x; v[1] = t.y;
+    }
 };
 
 template <> struct Store<float> {
@@ -38,6 +43,11 @@ template <> struct Store<float> {
     __device__ static inline void store(float *p, const float v[4])
     {
         __stcs(reinterpret_cast<float4 *>(p), make_float4(v[0], v[1], v[2], v[3]));
+    }
+    __device__ static inline void load_shared(const float *p, float v[4])
+    {
+        const float4 t = *reinterpret_cast<const float4 *>(p);
+        v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
     }
 };
 
@@ -60,6 +70,14 @@ template <> struct Store<__nv_bfloat16> {
         raw.x = *reinterpret_cast<const uint32_t *>(&a);
         raw.y = *reinterpret_cast<const uint32_t *>(&b);
         __stcs(reinterpret_cast<uint2 *>(p), raw);
+    }
+    __device__ static inline void load_shared(const __nv_bfloat16 *p, float v[4])
+    {
+        const uint2 raw = *reinterpret_cast<const uint2 *>(p);
+        __nv_bfloat162 a = *reinterpret_cast<const __nv_bfloat162 *>(&raw.x);
+        __nv_bfloat162 b = *reinterpret_cast<const __nv_bfloat162 *>(&raw.y);
+        const float2 fa = __bfloat1622float2(a), fb = __bfloat1622float2(b);
+        v[0] = fa.x; v[1] = fa.y; v[2] = fb.x; v[3] = fb.y;
     }
 };
 

@@ -8,14 +8,23 @@
 // warp-uniform, since it depends on the group only through the signs of the
 // velocity components (Sec. 3.1).
 //
-// Persistent CTAs walk the Morton-ordered cells with stride gridDim.x, so the
-// CTAs in flight cover a contiguous Morton window and upwind neighbours are
-// served from L2.  Each CTA has NCW compute warps and one solver warp and
-// overlaps cells in a two-stage pipeline with one barrier per cell:
+// Persistent CTAs take the Morton-ordered cells from a global counter, two
+// cells ahead of their pipeline, so the cells in flight on the whole GPU form
+// one contiguous Morton window and upwind neighbours are served from L2 (a
+// fixed round-robin assignment lets the CTAs drift apart over thousands of
+// cells and spreads the window far beyond L2).  Each CTA has NCW compute warps and one solver warp and
+// overlaps cells in a pipeline with one barrier per cell:
 //
 //   iteration i, compute warps:  phase 1 of cell c_i        | barrier | phase 3 of c_{i-1}
-//   iteration i, solver warp:    phase 2 of c_{i-1},        | barrier |
+//   iteration i, solver warp:    phase 2 of c_{i-1},        | barrier | bulk copy of c_{i+2}
 //                                prefetch stencil of c_{i+1}
+//
+// A cell's own f arrives as one bulk copy (cp.async.bulk, completion on an
+// mbarrier) into one of four shared tiles, issued two cells ahead; phase 1
+// reads it from shared memory and writes f* over it in place (FP32/FP64
+// storage; BF16 storage keeps f* in a separate FP32 buffer).  Only the upwind
+// neighbours are read through L2.  Waits on the tiles are bounded and report
+// DVM_ETIMEOUT instead of hanging.
 //
 // Phase 1: f*_i = f_i - dt sum_d |xi_d,i| (f_i / h - sum_k w_k src_k,i) into a
 //   shared buffer; per-thread FP32 partials of the seven sums sum f,
@@ -32,6 +41,7 @@
 #include <cmath>
 
 #include "../../include/dvm.h"
+#include "async.cuh"
 #include "common.cuh"
 #include "kernels.hpp"
 #include "mesh.hpp"
@@ -47,6 +57,7 @@ namespace {
 constexpr int MAXCW = 14;     // compute warps per CTA (at most)
 constexpr int NAX = 32;       // velocity nodes per axis supported
 constexpr int MAXT = MAXCW * 32 + 32;
+constexpr int NTILE = 4;      // shared tiles holding cells' own f
 
 template <typename TC> __device__ inline TC tc_exp(TC x);
 template <> __device__ inline float tc_exp<float>(float x) { return expf(x); }
@@ -83,8 +94,15 @@ __device__ inline typename Num<TC>::X split(double v)
     }
 }
 
+template <typename TS> constexpr size_t step_dyn_smem(int nv)
+{
+    using TC = typename Store<TS>::TC;
+    return sizeof(TS) == sizeof(TC) ? (size_t)NTILE * nv * sizeof(TS)
+                                    : (size_t)NTILE * nv * sizeof(TS) + 2 * (size_t)nv * sizeof(TC);
+}
+
 template <typename TS, int DIM, int COLL>
-__global__ void __launch_bounds__(MAXT, 2) k_step(const StepParams p)
+__global__ void __launch_bounds__(MAXT, 1) k_step(const StepParams p)
 {
     using S = Store<TS>;
     using TC = typename S::TC;
@@ -92,16 +110,24 @@ __global__ void __launch_bounds__(MAXT, 2) k_step(const StepParams p)
     using X = typename N::X;
     constexpr int VEC = S::VEC;
 
+    constexpr bool INPLACE = sizeof(TS) == sizeof(TC);
     __shared__ StepSmem<TC> sm;
-    extern __shared__ __align__(16) unsigned char dsm[];
-    TC *buf = reinterpret_cast<TC *>(dsm);  // [2][nv] f* of two cells
+    __shared__ __align__(8) uint64_t bar[NTILE];
+    __shared__ int abort_flag;
+    __shared__ int64_t cellq[NTILE];  // cell of pipeline iteration i at i % NTILE (-1: none left)
+    extern __shared__ __align__(128) unsigned char dsm[];
+    TS *tiles = reinterpret_cast<TS *>(dsm);  // [NTILE][nv] own f of upcoming cells
+    TC *fsep = reinterpret_cast<TC *>(dsm + (size_t)NTILE * p.nv * sizeof(TS));  // [2][nv] (BF16 storage)
+    // f* of pipeline iteration i
+    auto fstar = [&](int64_t i) -> TC * {
+        if constexpr (INPLACE) return reinterpret_cast<TC *>(tiles + (size_t)(i % NTILE) * p.nv);
+        else return fsep + (size_t)(i & 1) * p.nv;
+    };
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int ncw = (blockDim.x >> 5) - 1;  // compute warps; the last warp solves
     const bool solver = warp == ncw;
     const int Q = p.P / VEC;
-    const int64_t G = gridDim.x;
-    const int64_t ncell_cta = (p.ncells - blockIdx.x + G - 1) / G;
 
     // ---- stencil prefetch (solver warp): cell -> slot
     auto load_stencil = [&](int64_t cell, int slot) {
@@ -112,7 +138,35 @@ __global__ void __launch_bounds__(MAXT, 2) k_step(const StepParams p)
         if (lane < 6) sm.cnt[slot][lane] = p.st_cnt[cell * 8 + lane];
         if (lane == 0) sm.invh[slot] = static_cast<const TC *>(p.inv_h)[cell];
     };
-    if (solver && ncell_cta > 0) load_stencil(blockIdx.x, 0);
+    const uint32_t tile_bytes = (uint32_t)p.nv * (uint32_t)sizeof(TS);
+    const TS *__restrict__ fin_all = static_cast<const TS *>(p.f_in);
+    // solver lane 0: take the next cell for pipeline iteration i and start the
+    // bulk copy of its own f into tile i % NTILE
+    auto issue = [&](int64_t i) {
+        const int t = (int)(i % NTILE);
+        const int64_t cell = (int64_t)atomicAdd(p.counter, 1ull);
+        if (cell >= p.ncells) {
+            cellq[t] = -1;
+            return;
+        }
+        cellq[t] = cell;
+        mbar_expect_tx(&bar[t], tile_bytes);
+        bulk_g2s(tiles + (size_t)t * p.nv, fin_all + cell * (int64_t)p.nv, tile_bytes, &bar[t]);
+    };
+    if (tid == 0) {
+        for (int t = 0; t < NTILE; t++) mbar_init(&bar[t], 1);
+        abort_flag = 0;
+        mbar_fence_init();
+    }
+    __syncthreads();
+    if (solver) {
+        if (lane == 0) {
+            issue(0);
+            issue(1);
+        }
+        __syncwarp();
+        if (cellq[0] >= 0) load_stencil(cellq[0], 0);
+    }
 
     // ---- per-thread position (compute warps)
     const bool active = !solver && tid < Q;
@@ -150,25 +204,28 @@ __global__ void __launch_bounds__(MAXT, 2) k_step(const StepParams p)
     }
     __syncthreads();
 
-    for (int64_t it = 0; it <= ncell_cta; it++) {
+    for (int64_t it = 0;; it++) {
         const int b = (int)(it & 1), bp = b ^ 1;
-        const int64_t cell = blockIdx.x + it * G;            // c_i (valid if it < ncell_cta)
-        const int64_t prev = blockIdx.x + (it - 1) * G;      // c_{i-1} (valid if it >= 1)
+        const int64_t cell = cellq[it % NTILE];                          // c_i, or -1
+        const int64_t prev = it >= 1 ? cellq[(it - 1) % NTILE] : -1;     // c_{i-1}, or -1
+        if (cell < 0 && prev < 0) break;
 
         if (!solver) {
-            // ================= phase 1: transport of c_i into buf[b]
-            if (it < ncell_cta) {
+            // ================= phase 1: transport of c_i into its tile
+            if (cell >= 0) {
                 // per-thread partials: sum f, sum s_x f, sum s_y f, sum j_z s_z f, sum j_z^2 f
                 TC a0 = 0, ax1 = 0, ay1 = 0, az1 = 0, az2 = 0;
+                const int tl = (int)(it % NTILE);
+                if (!mbar_wait(&bar[tl], (uint32_t)(it / NTILE) & 1u)) abort_flag = 1;
                 if (active) {
-                    const int64_t cbase = cell * (int64_t)p.nv;
                     const TC invh = sm.invh[b];
-                    TC *bb = buf + (size_t)b * p.nv;
+                    const TS *own = tiles + (size_t)tl * p.nv;
+                    TC *bb = fstar(it);
 #pragma unroll
                     for (int o = 0; o < 8; o++) {
                         const int off = o * p.P + p0;
                         TC self[VEC], acc[VEC];
-                        S::load(fin + cbase + off, self);
+                        S::load_shared(own + off, self);
 #pragma unroll
                         for (int e = 0; e < VEC; e++) acc[e] = 0;
 #pragma unroll
@@ -238,7 +295,7 @@ __global__ void __launch_bounds__(MAXT, 2) k_step(const StepParams p)
             }
         } else {
             // ================= phase 2 (solver warp): cell c_{i-1}
-            if (it >= 1) {
+            if (prev >= 0) {
                 X Ssum[7];
 #pragma unroll
                 for (int k = 0; k < 7; k++) {
@@ -364,15 +421,30 @@ __global__ void __launch_bounds__(MAXT, 2) k_step(const StepParams p)
                     sm.ok[bp] = COLL == DVM_COLL_BGK && (flags & (ST_NONPOS | ST_SINGULAR)) == 0;
                 }
             }
-            // prefetch the stencil of c_{i+1}
-            if (it + 1 < ncell_cta) load_stencil(blockIdx.x + (it + 1) * G, bp);
+            // prefetch the stencil of c_{i+1} (its cell was taken by lane 0 two
+            // iterations ago)
+            __syncwarp();
+            const int64_t next = cellq[(it + 1) % NTILE];
+            if (next >= 0) load_stencil(next, bp);
         }
         __syncthreads();
+        if (abort_flag) {
+            // a tile never arrived: report it, give the copies in flight
+            // (cells it and it+1 at most) a bounded time to land, stop
+            if (solver && lane == 0) {
+                atomicOr(p.status, ST_TIMEOUT);
+                for (int64_t i = it; i <= it + 1; i++)
+                    if (cellq[i % NTILE] >= 0) mbar_wait(&bar[i % NTILE], (uint32_t)(i / NTILE) & 1u);
+            }
+            return;
+        }
+        // the tile of c_{i-2} was drained by phase 3 of the previous iteration
+        if (solver && lane == 0) issue(it + 2);
 
         // ================= phase 3 (compute warps): collision of c_{i-1}
-        if (!solver && it >= 1 && active) {
+        if (!solver && prev >= 0 && active) {
             const int64_t cbase = prev * (int64_t)p.nv;
-            const TC *bb = buf + (size_t)bp * p.nv;
+            const TC *bb = fstar(it - 1);
             const bool collide = sm.ok[bp];
             const TC *cf = sm.coef[bp];
             const TC pre = cf[CF_PRE], ux = cf[CF_UX], uy = cf[CF_UY], uz = cf[CF_UZ], ist = cf[CF_IST];
@@ -410,19 +482,22 @@ __global__ void __launch_bounds__(MAXT, 2) k_step(const StepParams p)
                 S::store(fout + cbase + off, out);
             }
         }
+        // order this thread's generic accesses to the tiles before the bulk
+        // copies that will refill them
+        if (!solver) fence_proxy_async();
     }
 }
 
 template <typename TS, int DIM, int COLL>
 int launch_kernel(const StepParams &p, int ncw)
 {
-    using TC = typename Store<TS>::TC;
     auto kern = k_step<TS, DIM, COLL>;
     const int threads = (ncw + 1) * 32;
-    const size_t dyn = 2 * (size_t)p.nv * sizeof(TC);
+    const size_t dyn = step_dyn_smem<TS>(p.nv);
+    if (dyn > 220 * 1024) return DVM_ENOTIMPL;
     static bool configured = false;
     if (!configured) {
-        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) != cudaSuccess)
+        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024) != cudaSuccess)
             return DVM_ECUDA;
         configured = true;
     }

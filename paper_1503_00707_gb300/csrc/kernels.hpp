@@ -34,6 +34,7 @@ struct StepParams {
     double hv[3];            // velocity spacing per axis
     double *mom_out;         // [ncells][5]: rho, u[3], T of f*
     int *status;
+    unsigned long long *counter;  // cell dispenser of the step kernel, zeroed before each launch
     cudaStream_t stream;
 };
 
