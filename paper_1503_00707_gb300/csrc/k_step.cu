@@ -216,6 +216,22 @@ __global__ void __launch_bounds__(MAXT, 1) k_step(const StepParams p)
                 // per-thread partials: sum f, sum s_x f, sum s_y f, sum j_z s_z f, sum j_z^2 f
                 TC a0 = 0, ax1 = 0, ay1 = 0, az1 = 0, az2 = 0;
                 const int tl = (int)(it % NTILE);
+                // first upwind source of every axis for group o: these loads do
+                // not depend on the tile, so two groups are in flight before
+                // the tile is awaited and one more is issued per group
+                auto load_first = [&](int o, TC (&nb)[3][VEC]) {
+#pragma unroll
+                    for (int d = 0; d < DIM; d++) {
+                        const int list = 2 * d + (((o >> (2 - d)) & 1) ? 0 : 1);
+                        const int32_t src = sm.src[b][list * 4];
+                        S::load(fin + (int64_t)(src & 0x0fffffff) * p.nv + (o ^ (src >> 28)) * p.P + p0, nb[d]);
+                    }
+                };
+                TC nbA[3][VEC], nbB[3][VEC];
+                if (active) {
+                    load_first(0, nbA);
+                    load_first(1, nbB);
+                }
                 if (!mbar_wait(&bar[tl], (uint32_t)(it / NTILE) & 1u)) abort_flag = 1;
                 if (active) {
                     const TC invh = sm.invh[b];
@@ -223,6 +239,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_step(const StepParams p)
                     TC *bb = fstar(it);
 #pragma unroll
                     for (int o = 0; o < 8; o++) {
+                        TC (&cur)[3][VEC] = (o & 1) ? nbB : nbA;
                         const int off = o * p.P + p0;
                         TC self[VEC], acc[VEC];
                         S::load_shared(own + off, self);
@@ -232,17 +249,11 @@ __global__ void __launch_bounds__(MAXT, 1) k_step(const StepParams p)
                         for (int d = 0; d < DIM; d++) {
                             const int list = 2 * d + (((o >> (2 - d)) & 1) ? 0 : 1);
                             TC sd[VEC];
-                            // every list has at least one source; the first
-                            // one is loaded unconditionally so it can be hoisted
-                            const int cnt = sm.cnt[b][list];
-                            {
-                                const int32_t src = sm.src[b][list * 4];
-                                const TC w = sm.w[b][list * 4];
-                                TC v[VEC];
-                                S::load(fin + (int64_t)(src & 0x0fffffff) * p.nv + (o ^ (src >> 28)) * p.P + p0, v);
+                            const TC w0 = sm.w[b][list * 4];
 #pragma unroll
-                                for (int e = 0; e < VEC; e++) sd[e] = w * v[e];
-                            }
+                            for (int e = 0; e < VEC; e++) sd[e] = w0 * cur[d][e];
+                            // further sources: the fine neighbours behind a coarse face
+                            const int cnt = sm.cnt[b][list];
                             for (int q = 1; q < cnt; q++) {
                                 const int32_t src = sm.src[b][list * 4 + q];
                                 const TC w = sm.w[b][list * 4 + q];
@@ -257,6 +268,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_step(const StepParams p)
                                 acc[e] = fma(a, fma(self[e], invh, -sd[e]), acc[e]);
                             }
                         }
+                        if (o + 2 < 8) load_first(o + 2, cur);
                         TC fs[VEC], r0 = 0, r1 = 0, r2 = 0;
 #pragma unroll
                         for (int e = 0; e < VEC; e++) {
