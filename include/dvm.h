@@ -213,6 +213,35 @@ int dvm_moments(dvm_ctx *ctx, double *rho, double *u, double *T);
  * post-collision state up to storage rounding). */
 int dvm_step_moments(dvm_ctx *ctx, double *rho, double *u, double *T);
 
+/* ---- learned collision operator: the network --------------------------------
+ * 64 -> 256 -> 256 -> 256 -> 64 multilayer perceptron with SiLU hidden
+ * activations (not in the paper).  Parameters are a flat FP32 vector of
+ * DVM_MLP_NPARAM values: W1[256][64] b1[256] W2[256][256] b2[256]
+ * W3[256][256] b3[256] W4[64][256] b4[64], W[out][in].  The device keeps
+ * FP32 master weights and BF16 copies; inference and training run on the
+ * tensor cores with BF16 operands and FP32 accumulation.  Host arrays are
+ * caller-owned; x and t are [n][64] FP32 rows. */
+#define DVM_MLP_NPARAM 164672
+
+/* Set (and reset the optimiser state of) the network's weights. */
+int dvm_learned_set_weights(dvm_ctx *ctx, const float *params);
+
+/* Copy the FP32 master weights out. */
+int dvm_learned_get_weights(dvm_ctx *ctx, float *params);
+
+/* y = MLP(x) for n rows (x rounded to BF16, BF16 activations). */
+int dvm_mlp_forward(dvm_ctx *ctx, const float *x, int64_t n, float *y);
+
+/* Mean squared error over the n*64 outputs against targets t and, if grad
+ * is not NULL, its gradient with respect to the parameters. */
+int dvm_mlp_loss_grad(dvm_ctx *ctx, const float *x, const float *t, int64_t n, float *grad, double *loss);
+
+/* Train on (x, t) with Adam (beta 0.9/0.999, eps 1e-8): `epochs` passes over
+ * a seeded permutation of the rows in batches of `batch` rows.  *loss
+ * receives the mean training loss of the last epoch. */
+int dvm_learned_train(dvm_ctx *ctx, const float *x, const float *t, int64_t n, int epochs, int batch,
+                      double lr, uint64_t seed, double *loss);
+
 /* Size in bytes of the fixed device scratch used by dvm_hs_collide_noalloc. */
 #define DVM_HS_NOALLOC_SCRATCH_BYTES (64u << 20)
 

@@ -33,8 +33,10 @@ EXPORTS = [
     "dvm_set_freestream", "dvm_init_maxwellian", "dvm_get_f", "dvm_set_f", "dvm_upload_f",
     "dvm_download_f", "dvm_f_device", "dvm_dt_cfl", "dvm_set_collision_tables", "dvm_step",
     "dvm_moments", "dvm_step_moments", "dvm_launch_count", "dvm_get_collision_tables",
-    "dvm_hs_collide_noalloc",
+    "dvm_hs_collide_noalloc", "dvm_learned_set_weights", "dvm_learned_get_weights",
+    "dvm_mlp_forward", "dvm_mlp_loss_grad", "dvm_learned_train",
 ]
+MLP_NPARAM = 164672
 HS_NOALLOC_SCRATCH_BYTES = 64 << 20
 
 
@@ -108,6 +110,11 @@ def lib():
             "dvm_launch_count": [P],
             "dvm_get_collision_tables": [P, P, P, P, P, P],
             "dvm_hs_collide_noalloc": [P, P, i64, d],
+            "dvm_learned_set_weights": [P, P],
+            "dvm_learned_get_weights": [P, P],
+            "dvm_mlp_forward": [P, P, i64, P],
+            "dvm_mlp_loss_grad": [P, P, P, i64, P, P],
+            "dvm_learned_train": [P, P, P, i64, C.c_int, C.c_int, d, C.c_uint64, P],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -240,6 +247,39 @@ class Solver:
         """Collision update of caller-owned device f (FP32) with no device
         allocation; f_dev_ptr is an integer device address."""
         self._chk(lib().dvm_hs_collide_noalloc(self._h, C.c_void_p(f_dev_ptr), int(ncells), float(dt)))
+
+    # ---- learned operator network
+    def set_weights(self, params):
+        params = np.ascontiguousarray(params, dtype=np.float32)
+        assert params.size == MLP_NPARAM
+        self._chk(lib().dvm_learned_set_weights(self._h, _p(params)))
+
+    def get_weights(self):
+        out = np.zeros(MLP_NPARAM, np.float32)
+        self._chk(lib().dvm_learned_get_weights(self._h, _p(out)))
+        return out
+
+    def mlp_forward(self, x):
+        x = np.ascontiguousarray(x, dtype=np.float32).reshape(-1, 64)
+        y = np.zeros_like(x)
+        self._chk(lib().dvm_mlp_forward(self._h, _p(x), x.shape[0], _p(y)))
+        return y
+
+    def mlp_loss_grad(self, x, t, want_grad=True):
+        x = np.ascontiguousarray(x, dtype=np.float32).reshape(-1, 64)
+        t = np.ascontiguousarray(t, dtype=np.float32).reshape(-1, 64)
+        g = np.zeros(MLP_NPARAM, np.float32) if want_grad else None
+        loss = C.c_double()
+        self._chk(lib().dvm_mlp_loss_grad(self._h, _p(x), _p(t), x.shape[0], _p(g), C.byref(loss)))
+        return loss.value, g
+
+    def train(self, x, t, epochs, batch, lr, seed=0):
+        x = np.ascontiguousarray(x, dtype=np.float32).reshape(-1, 64)
+        t = np.ascontiguousarray(t, dtype=np.float32).reshape(-1, 64)
+        loss = C.c_double()
+        self._chk(lib().dvm_learned_train(self._h, _p(x), _p(t), x.shape[0], int(epochs), int(batch),
+                                          float(lr), int(seed), C.byref(loss)))
+        return loss.value
 
     # ---- state
     def get_f(self):

@@ -13,6 +13,7 @@
 #include "hs.hpp"
 #include "kernels.hpp"
 #include "mesh.hpp"
+#include "mlp.hpp"
 
 struct dvm_ctx {
     dvm_config cfg{};
@@ -49,6 +50,8 @@ struct dvm_ctx {
     bool have_step_moments = false;
     bool mesh_on_device = false;
     dvm::HsTables hs;
+    dvm::Mlp mlp;
+    bool mlp_set = false;
 };
 
 namespace {
@@ -239,6 +242,7 @@ void dvm_destroy(dvm_ctx *c)
     free_grid_buffers(c);
     free_mesh_buffers(c);
     dvm::hs_free(c->hs, [c](void *p) { void *q = p; dev_free(c, q); });
+    dvm::mlp_free(c->mlp, [c](void *p) { void *q = p; dev_free(c, q); });
     if (c->d_status) cudaFree(c->d_status);
     delete c;
 }
@@ -732,6 +736,140 @@ int dvm_hs_collide_noalloc(dvm_ctx *c, float *f, int64_t ncells, double dt)
         return fail(c, DVM_EUNSTABLE, "unstable collision update (singular correction or dt/Kn max(P B) > 1)");
     }
     return DVM_OK;
+}
+
+// ---------------------------------------------------------------- network
+static int mlp_ready(dvm_ctx *c)
+{
+    int rc = ensure_device(c);
+    if (rc) return rc;
+    rc = dvm::mlp_init(c->mlp, [c](size_t b) { return dev_alloc(c, b); });
+    return rc ? fail(c, rc, "device allocation (network)") : DVM_OK;
+}
+
+static int status_check(dvm_ctx *c)
+{
+    int st = 0;
+    int rc = cuda_check(c, cudaMemcpyAsync(&st, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "read status");
+    if (!rc) rc = cuda_check(c, cudaStreamSynchronize(c->stream), "network");
+    if (rc) return rc;
+    if (st) {
+        cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream);
+        return fail(c, st & dvm::ST_TIMEOUT ? DVM_ETIMEOUT : DVM_EUNSTABLE, "network kernel reported an error");
+    }
+    return DVM_OK;
+}
+
+int dvm_learned_set_weights(dvm_ctx *c, const float *params)
+{
+    if (!c || !params) return DVM_EINVAL;
+    int rc = mlp_ready(c);
+    if (rc) return rc;
+    rc = cuda_check(c, cudaMemcpy(c->mlp.w, params, DVM_MLP_NPARAM * 4, cudaMemcpyHostToDevice), "copy weights");
+    if (!rc) rc = cuda_check(c, cudaMemset(c->mlp.m, 0, DVM_MLP_NPARAM * 4), "reset optimiser");
+    if (!rc) rc = cuda_check(c, cudaMemset(c->mlp.v, 0, DVM_MLP_NPARAM * 4), "reset optimiser");
+    c->mlp.steps = 0;
+    if (!rc) rc = dvm::mlp_cast(c->mlp, c->stream);
+    if (!rc) rc = cuda_check(c, cudaStreamSynchronize(c->stream), "cast weights");
+    c->mlp_set = !rc;
+    return rc;
+}
+
+int dvm_learned_get_weights(dvm_ctx *c, float *params)
+{
+    if (!c || !params) return DVM_EINVAL;
+    if (!c->mlp_set) return fail(c, DVM_ESTATE, "no weights set");
+    return cuda_check(c, cudaMemcpy(params, c->mlp.w, DVM_MLP_NPARAM * 4, cudaMemcpyDeviceToHost), "copy weights");
+}
+
+namespace {
+struct DevArr {
+    dvm_ctx *c;
+    void *p = nullptr;
+    DevArr(dvm_ctx *cc, size_t bytes) : c(cc) { p = dev_alloc(cc, bytes); }
+    ~DevArr() { dev_free(c, p); }
+    float *f() { return static_cast<float *>(p); }
+};
+}  // namespace
+
+int dvm_mlp_forward(dvm_ctx *c, const float *x, int64_t n, float *y)
+{
+    if (!c || !x || !y || n < 1) return DVM_EINVAL;
+    if (!c->mlp_set) return fail(c, DVM_ESTATE, "no weights set");
+    int rc = dvm::mlp_reserve(c->mlp, n, [c](size_t b) { return dev_alloc(c, b); }, [c](void *p) { void *q = p; dev_free(c, q); });
+    if (rc) return fail(c, rc, "device allocation (network work buffers)");
+    DevArr dx(c, (size_t)n * 64 * 4), dy(c, (size_t)n * 64 * 4);
+    if (!dx.p || !dy.p) return fail(c, DVM_ENOMEM, "device allocation (network rows)");
+    rc = cuda_check(c, cudaMemcpyAsync(dx.p, x, (size_t)n * 256, cudaMemcpyHostToDevice, c->stream), "copy x");
+    if (!rc) rc = dvm::mlp_forward(c->mlp, dx.f(), n, dy.f(), c->d_status, c->stream);
+    if (rc) return fail(c, rc, "network forward failed");
+    rc = cuda_check(c, cudaMemcpyAsync(y, dy.p, (size_t)n * 256, cudaMemcpyDeviceToHost, c->stream), "copy y");
+    return rc ? rc : status_check(c);
+}
+
+int dvm_mlp_loss_grad(dvm_ctx *c, const float *x, const float *t, int64_t n, float *grad, double *loss)
+{
+    if (!c || !x || !t || n < 1) return DVM_EINVAL;
+    if (!c->mlp_set) return fail(c, DVM_ESTATE, "no weights set");
+    int rc = dvm::mlp_reserve(c->mlp, n, [c](size_t b) { return dev_alloc(c, b); }, [c](void *p) { void *q = p; dev_free(c, q); });
+    if (rc) return fail(c, rc, "device allocation (network work buffers)");
+    DevArr dx(c, (size_t)n * 256), dt(c, (size_t)n * 256);
+    if (!dx.p || !dt.p) return fail(c, DVM_ENOMEM, "device allocation (network rows)");
+    rc = cuda_check(c, cudaMemcpyAsync(dx.p, x, (size_t)n * 256, cudaMemcpyHostToDevice, c->stream), "copy x");
+    if (!rc) rc = cuda_check(c, cudaMemcpyAsync(dt.p, t, (size_t)n * 256, cudaMemcpyHostToDevice, c->stream), "copy t");
+    if (!rc) rc = dvm::mlp_grad(c->mlp, dx.f(), dt.f(), n, c->d_status, c->stream);
+    if (rc) return fail(c, rc, "network gradient failed");
+    double L = 0.0;
+    rc = cuda_check(c, cudaMemcpyAsync(&L, c->mlp.loss, 8, cudaMemcpyDeviceToHost, c->stream), "copy loss");
+    if (!rc && grad) rc = cuda_check(c, cudaMemcpyAsync(grad, c->mlp.g, DVM_MLP_NPARAM * 4, cudaMemcpyDeviceToHost, c->stream), "copy grad");
+    if (!rc) rc = status_check(c);
+    if (!rc && loss) *loss = L / ((double)n * 64.0);
+    return rc;
+}
+
+int dvm_learned_train(dvm_ctx *c, const float *x, const float *t, int64_t n, int epochs, int batch, double lr,
+                      uint64_t seed, double *loss)
+{
+    if (!c || !x || !t || n < 1 || epochs < 1 || batch < 1 || !(lr > 0.0)) return DVM_EINVAL;
+    if (!c->mlp_set) return fail(c, DVM_ESTATE, "no weights set");
+    const int64_t nb = std::min<int64_t>(batch, n);
+    int rc = dvm::mlp_reserve(c->mlp, nb, [c](size_t b) { return dev_alloc(c, b); }, [c](void *p) { void *q = p; dev_free(c, q); });
+    if (rc) return fail(c, rc, "device allocation (network work buffers)");
+    DevArr dx(c, (size_t)n * 256), dt(c, (size_t)n * 256);
+    if (!dx.p || !dt.p) return fail(c, DVM_ENOMEM, "device allocation (training rows)");
+    std::vector<int64_t> perm(n);
+    std::vector<float> xs((size_t)n * 64), ts((size_t)n * 64);
+    double last = 0.0;
+    for (int e = 0; e < epochs && !rc; e++) {
+        // seeded Fisher-Yates permutation of the rows
+        for (int64_t q = 0; q < n; q++) perm[q] = q;
+        for (int64_t q = n - 1; q > 0; q--) {
+            const uint64_t r = dvm::splitmix64_at(seed + (uint64_t)e, (uint64_t)q) % (uint64_t)(q + 1);
+            std::swap(perm[q], perm[(int64_t)r]);
+        }
+        for (int64_t q = 0; q < n; q++) {
+            std::memcpy(&xs[(size_t)q * 64], x + perm[q] * 64, 256);
+            std::memcpy(&ts[(size_t)q * 64], t + perm[q] * 64, 256);
+        }
+        rc = cuda_check(c, cudaMemcpyAsync(dx.p, xs.data(), (size_t)n * 256, cudaMemcpyHostToDevice, c->stream), "copy x");
+        if (!rc) rc = cuda_check(c, cudaMemcpyAsync(dt.p, ts.data(), (size_t)n * 256, cudaMemcpyHostToDevice, c->stream), "copy t");
+        double sum = 0.0;
+        int64_t rows = 0;
+        for (int64_t s0 = 0; s0 < n && !rc; s0 += nb) {
+            const int64_t m = std::min(nb, n - s0);
+            rc = dvm::mlp_grad(c->mlp, dx.f() + s0 * 64, dt.f() + s0 * 64, m, c->d_status, c->stream);
+            if (!rc) rc = dvm::mlp_adam(c->mlp, lr, c->stream);
+            double L = 0.0;
+            if (!rc) rc = cuda_check(c, cudaMemcpyAsync(&L, c->mlp.loss, 8, cudaMemcpyDeviceToHost, c->stream), "copy loss");
+            if (!rc) rc = cuda_check(c, cudaStreamSynchronize(c->stream), "train");
+            sum += L;
+            rows += m;
+        }
+        last = sum / ((double)rows * 64.0);
+    }
+    if (!rc) rc = status_check(c);
+    if (!rc && loss) *loss = last;
+    return rc;
 }
 
 int dvm_launch_count(int64_t *count)
