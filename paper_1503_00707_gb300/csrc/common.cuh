@@ -143,44 +143,46 @@ __device__ inline double warp_allsum(double v)
     return v;
 }
 
-// Gaussian elimination with partial pivoting, n = 5.  Returns false if a
-// pivot is zero or a result is not finite.
+// Solve A x = b for a symmetric positive definite 5x5 A (the moment systems
+// sum_i phi_r phi_s w_i with positive weights w_i) by an LDL^T factorisation.
+// Every index is a compile-time constant, so the whole solve stays in
+// registers (no local memory).  Returns false if a pivot is not positive or
+// a result is not finite.
 template <typename T>
-__device__ inline bool solve5(T A[25], T b[5], T x[5])
+__device__ inline bool solve5(const T A[25], const T b[5], T x[5])
 {
+    T L[5][5], D[5];
 #pragma unroll
-    for (int c = 0; c < 5; c++) {
-        int piv = c;
-        T best = fabs(A[c * 5 + c]);
+    for (int j = 0; j < 5; j++) {
+        T d = A[j * 5 + j];
 #pragma unroll
-        for (int r = c + 1; r < 5; r++) {
-            const T v = fabs(A[r * 5 + c]);
-            if (v > best) { best = v; piv = r; }
-        }
-        if (!(best > (T)0) || !isfinite(best)) return false;
-        if (piv != c) {
+        for (int k = 0; k < j; k++) d -= L[j][k] * L[j][k] * D[k];
+        if (!(d > (T)0) || !isfinite(d)) return false;
+        D[j] = d;
+        const T inv = (T)1 / d;
 #pragma unroll
-            for (int q = 0; q < 5; q++) {
-                const T t = A[c * 5 + q]; A[c * 5 + q] = A[piv * 5 + q]; A[piv * 5 + q] = t;
-            }
-            const T t = b[c]; b[c] = b[piv]; b[piv] = t;
-        }
-        const T inv = (T)1 / A[c * 5 + c];
+        for (int i = j + 1; i < 5; i++) {
+            T s = A[i * 5 + j];
 #pragma unroll
-        for (int r = c + 1; r < 5; r++) {
-            const T m = A[r * 5 + c] * inv;
-#pragma unroll
-            for (int q = c; q < 5; q++) A[r * 5 + q] -= m * A[c * 5 + q];
-            b[r] -= m * b[c];
+            for (int k = 0; k < j; k++) s -= L[i][k] * L[j][k] * D[k];
+            L[i][j] = s * inv;
         }
     }
+    T y[5];
 #pragma unroll
-    for (int r = 4; r >= 0; r--) {
-        T s = b[r];
+    for (int i = 0; i < 5; i++) {
+        T s = b[i];
 #pragma unroll
-        for (int q = r + 1; q < 5; q++) s -= A[r * 5 + q] * x[q];
-        x[r] = s / A[r * 5 + r];
-        if (!isfinite(x[r])) return false;
+        for (int k = 0; k < i; k++) s -= L[i][k] * y[k];
+        y[i] = s;
+    }
+#pragma unroll
+    for (int i = 4; i >= 0; i--) {
+        T s = y[i] / D[i];
+#pragma unroll
+        for (int k = i + 1; k < 5; k++) s -= L[k][i] * x[k];
+        x[i] = s;
+        if (!isfinite(s)) return false;
     }
     return true;
 }
