@@ -84,6 +84,7 @@ def lib():
         L.orc_mlp_forward.argtypes = [C.c_int64, P, P, P]
         L.orc_mlp_backward.argtypes = [C.c_int64, P, P, P, P, P]
         L.orc_learned_collide.argtypes = [P, C.c_double, C.c_double, P, C.c_double, P, P]
+        L.orc_learned_apply.argtypes = [P, C.c_double, C.c_double, P, P, C.c_double, P, P]
         _lib = L
     return _lib
 
@@ -307,6 +308,15 @@ class Problem:
         used = np.zeros(self.ncells, dtype=np.int32)
         q = np.zeros((self.ncells, self.nv)) if want_q else None
         if lib().orc_learned_collide(self._h, dt, kn, _p(params), threshold, _p(used), _p(q)):
+            raise RuntimeError("learned collision failed")
+        return used, q
+
+    def learned_apply(self, dt, kn, knl, o, threshold, want_q=False):
+        knl = np.ascontiguousarray(knl, dtype=np.float64)
+        o = np.ascontiguousarray(o, dtype=np.float64).reshape(self.ncells, 64)
+        used = np.zeros(self.ncells, dtype=np.int32)
+        q = np.zeros((self.ncells, self.nv)) if want_q else None
+        if lib().orc_learned_apply(self._h, dt, kn, _p(knl), _p(o), threshold, _p(used), _p(q)):
             raise RuntimeError("learned collision failed")
         return used, q
 

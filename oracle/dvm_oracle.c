@@ -1244,33 +1244,27 @@ int orc_mlp_backward(int64_t n, const double *params, const double *x, const dou
 }
 
 /* ------------------------------------------------------------------------ */
-/* Learned collision with conservative projection, entropy check, fallback. */
-int orc_learned_collide(orc_problem *p, double dt, double kn, const double *params,
-                        double kn_threshold, int32_t *used, double *q)
+/* Learned collision with conservative projection, entropy check, fallback:
+ * the application of given network outputs o, gated by the given local Kn. */
+int orc_learned_apply(orc_problem *p, double dt, double kn, const double *knl, const double *o,
+                      double kn_threshold, int32_t *used, double *q)
 {
     int64_t nc = p->ncells, nv = p->nv;
-    double *knl = (double *)malloc((size_t)nc * sizeof(double));
-    orc_kn_local(p, kn, knl);
-    double *a = (double *)malloc((size_t)nc * 64 * sizeof(double));
-    double *o = (double *)malloc((size_t)nc * 64 * sizeof(double));
-    double *mom = (double *)malloc((size_t)nc * 5 * sizeof(double));
-    orc_hermite_project(p, NULL, a, mom);
-    orc_mlp_forward(nc, params, a, o);
     /* the plain operator for every cell (the fallback and the judge) */
     double *qhs = NULL;
     if (p->hs_start) {
         double *f0 = (double *)malloc((size_t)(nc * nv) * sizeof(double));
         memcpy(f0, p->f, (size_t)(nc * nv) * sizeof(double));
         qhs = (double *)malloc((size_t)(nc * nv) * sizeof(double));
-        if (orc_hs_collide(p, 0.0, 1.0, qhs, NULL, NULL)) { free(f0); return -1; }
+        if (orc_hs_collide(p, 0.0, 1.0, qhs, NULL, NULL)) { free(f0); free(qhs); return -1; }
         memcpy(p->f, f0, (size_t)(nc * nv) * sizeof(double));
         free(f0);
     }
     int err = 0;
     for (int64_t c = 0; c < nc; c++) {
         double *f = &p->f[c * nv];
-        double rho = mom[c * 5], T = mom[c * 5 + 4];
-        const double *u = &mom[c * 5 + 1];
+        double rho, u[3], T;
+        cell_moments(p, f, &rho, u, &T);
         double sq = sqrt(T);
         double *Q = (double *)malloc((size_t)nv * sizeof(double));
         int ok = knl[c] < kn_threshold;
@@ -1320,6 +1314,22 @@ int orc_learned_collide(orc_problem *p, double dt, double kn, const double *para
         }
         free(Q);
     }
-    free(knl); free(a); free(o); free(mom); free(qhs);
+    free(qhs);
     return err ? -1 : 0;
+}
+
+/* The whole learned update: local Kn, projection, network, application. */
+int orc_learned_collide(orc_problem *p, double dt, double kn, const double *params,
+                        double kn_threshold, int32_t *used, double *q)
+{
+    int64_t nc = p->ncells;
+    double *knl = (double *)malloc((size_t)nc * sizeof(double));
+    double *a = (double *)malloc((size_t)nc * 64 * sizeof(double));
+    double *o = (double *)malloc((size_t)nc * 64 * sizeof(double));
+    orc_kn_local(p, kn, knl);
+    orc_hermite_project(p, NULL, a, NULL);
+    orc_mlp_forward(nc, params, a, o);
+    int rc = orc_learned_apply(p, dt, kn, knl, o, kn_threshold, used, q);
+    free(knl); free(a); free(o);
+    return rc;
 }

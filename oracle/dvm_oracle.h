@@ -143,6 +143,11 @@ int orc_mlp_backward(int64_t n, const double *params, const double *x, const dou
  * f <- f + dt/Kn I. */
 int orc_learned_collide(orc_problem *p, double dt, double kn, const double *params,
                         double kn_threshold, int32_t *used, double *q);
+/* The same update from given local Kn numbers knl [ncells] and network
+ * outputs o [ncells][64] (orc_learned_collide = orc_kn_local, then
+ * orc_hermite_project, orc_mlp_forward and this). */
+int orc_learned_apply(orc_problem *p, double dt, double kn, const double *knl, const double *o,
+                      double kn_threshold, int32_t *used, double *q);
 
 /* Gaussian elimination with partial pivoting on an n x n system (n <= 8);
  * A is row-major and is overwritten.  Returns 0, or -1 if singular. */
