@@ -60,7 +60,7 @@ typedef enum {
 } dvm_status;
 
 enum { DVM_F64 = 0, DVM_F32 = 1, DVM_BF16 = 2 };
-enum { DVM_COLL_NONE = 0, DVM_COLL_BGK = 1, DVM_COLL_HS = 2 };
+enum { DVM_COLL_NONE = 0, DVM_COLL_BGK = 1, DVM_COLL_HS = 2, DVM_COLL_LEARNED = 3 };
 enum { DVM_BC_PERIODIC = 0, DVM_BC_INFLOW = 1, DVM_BC_OUTFLOW = 2, DVM_BC_WALL = 3 };
 enum { DVM_PRED_NONE = 0, DVM_PRED_BALL = 1, DVM_PRED_SHELL = 2 };
 
@@ -241,6 +241,50 @@ int dvm_mlp_loss_grad(dvm_ctx *ctx, const float *x, const float *t, int64_t n, f
  * receives the mean training loss of the last epoch. */
 int dvm_learned_train(dvm_ctx *ctx, const float *x, const float *t, int64_t n, int epochs, int batch,
                       double lr, uint64_t seed, double *loss);
+
+/* ---- learned collision operator: the step ------------------------------------
+ * DVM_COLL_LEARNED steps (FP32 storage; every n even, at most 32, n_z/2 a
+ * multiple of 4; hard-sphere tables, network weights and the threshold
+ * set) replace the collision update of Eqs. 3-6 by, per cell:
+ *   1. the local Knudsen number Kn_loc = (Kn/rho) max(|grad rho|/rho,
+ *      |grad T|/T, |grad u|/sqrt(T)) (gradients by face-weighted least
+ *      squares over the face neighbours, w = A/|d|^2);
+ *   2. if Kn_loc < threshold: a_m = sum_i f_i H_m(c_i) dV / rho on the 64
+ *      tensor Hermite modes H_m = He_a(c_x) He_b(c_y) He_c(c_z), a, b, c < 4
+ *      (orthonormal probabilists' Hermite, m = 16a + 4b + c), with
+ *      c = (xi - u)/sqrt(T); o = network(a);
+ *      Q_i = M_i (rho sqrt(T) sum_m o_m H_m(c_i) - sum_r d_r phi_r(c_i)),
+ *      phi = (1, c, |c|^2 - 3), d such that Q carries no mass, momentum or
+ *      energy (the correction form of Eq. 6, solved in FP64 and accepted
+ *      only if its residual is below 1e-12 of the system's scale);
+ *      accepted if sum_i Q_i ln f_i <= 0 (f_i <= 0 read as 1e-300):
+ *      f += dt/Kn Q;
+ *   3. every other cell: the hard-sphere update of Eqs. 3-6.
+ * The paper has no learned operator; it is the network, gating and checks
+ * of this library. */
+
+/* Knudsen threshold below which a cell may use the learned term. */
+int dvm_learned_configure(dvm_ctx *ctx, double kn_threshold);
+
+/* One learned collision update (no transport) of the stored f in place,
+ * with its intermediate results: host arrays (each may be NULL) knl
+ * [ncells] FP64, a and o [ncells][64], used [ncells] (1 = learned term
+ * applied), q [ncells][nv] (the applied learned term; 0 in cells that fell
+ * back).  o_in (host [ncells][64], may be NULL) replaces the network's
+ * output.  Moments come from the stored f in FP64. */
+int dvm_learned_collide(dvm_ctx *ctx, double dt, const float *o_in, double *knl, float *a, float *o,
+                        int32_t *used, float *q);
+
+/* Training pairs from the stored f (FP32 storage, hard-sphere tables set):
+ * a [ncells][64] as above and the target o [ncells][64] =
+ * sum_i I_i H_m(c_i) dV / (rho^2 sqrt(T)), I the hard-sphere term of
+ * Eqs. 3-6 (the inverse of the reconstruction in step 2 up to the
+ * correction).  f is not changed. */
+int dvm_learned_pairs(dvm_ctx *ctx, float *a, float *o);
+
+/* Number of cells that fell back to the hard-sphere operator in the last
+ * learned collision update (synchronises the stream). */
+int dvm_learned_fallback_count(dvm_ctx *ctx, int64_t *n);
 
 /* Size in bytes of the fixed device scratch used by dvm_hs_collide_noalloc. */
 #define DVM_HS_NOALLOC_SCRATCH_BYTES (64u << 20)

@@ -18,7 +18,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libdvm.so")
 
 F64, F32, BF16 = 0, 1, 2
-COLL_NONE, COLL_BGK, COLL_HS = 0, 1, 2
+COLL_NONE, COLL_BGK, COLL_HS, COLL_LEARNED = 0, 1, 2, 3
 BC_PERIODIC, BC_INFLOW, BC_OUTFLOW, BC_WALL = 0, 1, 2, 3
 PRED_NONE, PRED_BALL, PRED_SHELL = 0, 1, 2
 
@@ -34,7 +34,8 @@ EXPORTS = [
     "dvm_download_f", "dvm_f_device", "dvm_dt_cfl", "dvm_set_collision_tables", "dvm_step",
     "dvm_moments", "dvm_step_moments", "dvm_launch_count", "dvm_get_collision_tables",
     "dvm_hs_collide_noalloc", "dvm_learned_set_weights", "dvm_learned_get_weights",
-    "dvm_mlp_forward", "dvm_mlp_loss_grad", "dvm_learned_train",
+    "dvm_mlp_forward", "dvm_mlp_loss_grad", "dvm_learned_train", "dvm_learned_configure",
+    "dvm_learned_collide", "dvm_learned_pairs", "dvm_learned_fallback_count",
 ]
 MLP_NPARAM = 164672
 HS_NOALLOC_SCRATCH_BYTES = 64 << 20
@@ -115,6 +116,10 @@ def lib():
             "dvm_mlp_forward": [P, P, i64, P],
             "dvm_mlp_loss_grad": [P, P, P, i64, P, P],
             "dvm_learned_train": [P, P, P, i64, C.c_int, C.c_int, d, C.c_uint64, P],
+            "dvm_learned_configure": [P, d],
+            "dvm_learned_collide": [P, d, P, P, P, P, P, P],
+            "dvm_learned_pairs": [P, P, P],
+            "dvm_learned_fallback_count": [P, P],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -280,6 +285,37 @@ class Solver:
         self._chk(lib().dvm_learned_train(self._h, _p(x), _p(t), x.shape[0], int(epochs), int(batch),
                                           float(lr), int(seed), C.byref(loss)))
         return loss.value
+
+    # ---- learned collision
+    def learned_configure(self, kn_threshold):
+        self._chk(lib().dvm_learned_configure(self._h, float(kn_threshold)))
+
+    def learned_collide(self, dt, o=None, want=("knl", "a", "o", "used", "q")):
+        """One learned collision update of the stored f; returns the requested
+        intermediates (knl, a, o, used, q) as numpy arrays."""
+        nc, nv = self.ncells, self.nv
+        o_in = None if o is None else np.ascontiguousarray(o, dtype=np.float32).reshape(nc, 64)
+        out = {
+            "knl": np.zeros(nc) if "knl" in want else None,
+            "a": np.zeros((nc, 64), np.float32) if "a" in want else None,
+            "o": np.zeros((nc, 64), np.float32) if "o" in want else None,
+            "used": np.zeros(nc, np.int32) if "used" in want else None,
+            "q": np.zeros((nc, nv), np.float32) if "q" in want else None,
+        }
+        self._chk(lib().dvm_learned_collide(self._h, float(dt), _p(o_in), _p(out["knl"]), _p(out["a"]),
+                                            _p(out["o"]), _p(out["used"]), _p(out["q"])))
+        return {k: v for k, v in out.items() if v is not None}
+
+    def learned_pairs(self):
+        a = np.zeros((self.ncells, 64), np.float32)
+        o = np.zeros((self.ncells, 64), np.float32)
+        self._chk(lib().dvm_learned_pairs(self._h, _p(a), _p(o)))
+        return a, o
+
+    def learned_fallback_count(self):
+        n = C.c_int64()
+        self._chk(lib().dvm_learned_fallback_count(self._h, C.byref(n)))
+        return n.value
 
     # ---- state
     def get_f(self):

@@ -12,6 +12,7 @@
 #include "../../include/dvm.h"
 #include "hs.hpp"
 #include "kernels.hpp"
+#include "learned.hpp"
 #include "mesh.hpp"
 #include "mlp.hpp"
 
@@ -52,6 +53,18 @@ struct dvm_ctx {
     dvm::HsTables hs;
     dvm::Mlp mlp;
     bool mlp_set = false;
+    // learned collision: Knudsen threshold, sensor stencil and per-cell buffers
+    double kn_thr = 0.0;
+    bool learned_cfg = false;
+    int64_t l_cells = 0;            // cells the buffers below hold (0: not allocated)
+    int32_t *d_kn_start = nullptr, *d_kn_nb = nullptr;
+    double *d_kn_coef = nullptr;
+    double *d_knl = nullptr;        // local Kn per cell
+    float *d_la = nullptr;          // network input a [ncells][64]
+    float *d_lo = nullptr;          // network output o [ncells][64]
+    int32_t *d_used = nullptr;      // 1 where the learned term was applied
+    int32_t *d_list = nullptr;      // cells left to the hard-sphere operator
+    int *d_lcount = nullptr;        // their number
 };
 
 namespace {
@@ -96,8 +109,23 @@ int cuda_check(dvm_ctx *c, cudaError_t e, const char *what)
     return fail(c, DVM_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
 }
 
+void free_learned_buffers(dvm_ctx *c)
+{
+    dev_free(c, reinterpret_cast<void *&>(c->d_kn_start));
+    dev_free(c, reinterpret_cast<void *&>(c->d_kn_nb));
+    dev_free(c, reinterpret_cast<void *&>(c->d_kn_coef));
+    dev_free(c, reinterpret_cast<void *&>(c->d_knl));
+    dev_free(c, reinterpret_cast<void *&>(c->d_la));
+    dev_free(c, reinterpret_cast<void *&>(c->d_lo));
+    dev_free(c, reinterpret_cast<void *&>(c->d_used));
+    dev_free(c, reinterpret_cast<void *&>(c->d_list));
+    dev_free(c, reinterpret_cast<void *&>(c->d_lcount));
+    c->l_cells = 0;
+}
+
 void free_mesh_buffers(dvm_ctx *c)
 {
+    free_learned_buffers(c);
     dev_free(c, reinterpret_cast<void *&>(c->d_src));
     dev_free(c, c->d_w);
     dev_free(c, reinterpret_cast<void *&>(c->d_cnt));
@@ -218,6 +246,106 @@ int upload_freestream(dvm_ctx *c)
     return rc;
 }
 
+// Buffers of the learned collision for the current mesh, the sensor
+// stencil, and network work space for one row per cell.
+int learned_prepare(dvm_ctx *c)
+{
+    const int64_t nc = ncells_of(c);
+    if (!dvm::learned_grid_supported(c->n))
+        return fail(c, DVM_ENOTIMPL, "velocity grid not supported by the learned kernels (n <= 32 even, n_z/2 % 4 == 0)");
+    if (c->cfg.precision != DVM_F32) return fail(c, DVM_ENOTIMPL, "the learned collision needs FP32 storage");
+    if (c->l_cells != nc) {
+        free_learned_buffers(c);
+        dvm::KnStencil ks;
+        dvm::build_kn_stencil(c->mesh, ks);
+        const size_t ne = ks.nb.size();
+        c->d_kn_start = dev_alloc_t<int32_t>(c, (size_t)nc + 1);
+        c->d_kn_nb = dev_alloc_t<int32_t>(c, ne);
+        c->d_kn_coef = dev_alloc_t<double>(c, 3 * ne);
+        c->d_knl = dev_alloc_t<double>(c, (size_t)nc);
+        c->d_la = dev_alloc_t<float>(c, (size_t)nc * 64);
+        c->d_lo = dev_alloc_t<float>(c, (size_t)nc * 64);
+        c->d_used = dev_alloc_t<int32_t>(c, (size_t)nc);
+        c->d_list = dev_alloc_t<int32_t>(c, (size_t)nc);
+        c->d_lcount = dev_alloc_t<int>(c, 4);
+        if (!c->d_kn_start || !c->d_kn_nb || !c->d_kn_coef || !c->d_knl || !c->d_la || !c->d_lo || !c->d_used ||
+            !c->d_list || !c->d_lcount) {
+            free_learned_buffers(c);
+            return fail(c, DVM_ENOMEM, "device allocation (learned collision)");
+        }
+        int rc = cuda_check(c, cudaMemcpy(c->d_kn_start, ks.start.data(), ks.start.size() * 4, cudaMemcpyHostToDevice), "copy sensor stencil");
+        if (!rc && ne) rc = cuda_check(c, cudaMemcpy(c->d_kn_nb, ks.nb.data(), ne * 4, cudaMemcpyHostToDevice), "copy sensor stencil");
+        if (!rc && ne) rc = cuda_check(c, cudaMemcpy(c->d_kn_coef, ks.coef.data(), ne * 24, cudaMemcpyHostToDevice), "copy sensor stencil");
+        if (rc) {
+            free_learned_buffers(c);
+            return rc;
+        }
+        c->l_cells = nc;
+    }
+    int rc = DVM_OK;
+    if (c->mlp_set) {
+        rc = dvm::mlp_reserve(c->mlp, nc, [c](size_t b) { return dev_alloc(c, b); }, [c](void *p) { void *q = p; dev_free(c, q); });
+        if (rc) return fail(c, rc, "device allocation (network work buffers)");
+    }
+    rc = dvm::hs_prepare(c->hs, nc, [c](size_t b) { return dev_alloc(c, b); }, [c](void *q) { void *r = q; dev_free(c, r); });
+    return rc ? fail(c, rc, "hard-sphere scratch allocation failed") : DVM_OK;
+}
+
+dvm::StepParams collision_params(dvm_ctx *c, double *mom)
+{
+    dvm::StepParams p{};
+    p.dim = c->mesh.spec.dim;
+    p.prec = c->cfg.precision;
+    p.ncells = ncells_of(c);
+    p.nv = c->nv;
+    p.P = c->P;
+    p.mom_out = mom;
+    p.status = c->d_status;
+    p.stream = c->stream;
+    return p;
+}
+
+// Learned collision update of f (FP32, [ncells][nv]) whose moments are mom:
+// sensor, projection, network (or the given device o), application with the
+// checks, then the hard-sphere operator on the cells left over.
+int learned_collide_device(dvm_ctx *c, float *f, double *mom, double dt, const float *o_in, float *q_out)
+{
+    const int64_t nc = ncells_of(c);
+    int rc = dvm::launch_kn_local(mom, c->d_kn_start, c->d_kn_nb, c->d_kn_coef, nc, c->cfg.kn, c->d_knl, c->stream);
+    if (!rc) rc = cuda_check(c, cudaMemsetAsync(c->d_lcount, 0, sizeof(int), c->stream), "reset fallback count");
+    if (rc) return rc;
+    const float *o = o_in;
+    if (!o) {
+        rc = dvm::launch_hermite_project(f, mom, c->d_amag, nc, c->n, c->dV, 0, nullptr, nullptr, c->d_la,
+                                         c->d_status, c->stream);
+        if (!rc) rc = dvm::mlp_forward(c->mlp, c->d_la, nc, c->d_lo, c->d_status, c->stream);
+        if (rc) return fail(c, rc, "projection or network launch failed");
+        o = c->d_lo;
+    }
+    rc = dvm::launch_learned_apply(f, mom, o, c->d_knl, c->kn_thr, c->d_amag, nc, c->n, dt / c->cfg.kn, c->d_used,
+                                   c->d_list, c->d_lcount, q_out, c->d_status, c->stream);
+    if (rc) return fail(c, rc, "learned collision launch failed");
+    dvm::StepParams p = collision_params(c, mom);
+    rc = dvm::launch_hs_general(c->hs, p, f, c->d_list, c->d_lcount, nullptr, c->cfg.kn, dt);
+    return rc ? fail(c, rc, "hard-sphere fallback launch failed") : DVM_OK;
+}
+
+int read_status(dvm_ctx *c, const char *what)
+{
+    int st = 0;
+    int rc = cuda_check(c, cudaMemcpyAsync(&st, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "read status");
+    if (!rc) rc = cuda_check(c, cudaStreamSynchronize(c->stream), what);
+    if (rc) return rc;
+    if (!st) return DVM_OK;
+    cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream);
+    if (st & dvm::ST_TIMEOUT) return fail(c, DVM_ETIMEOUT, "a bounded wait for an asynchronous tile copy gave up");
+    std::string why;
+    if (st & dvm::ST_NONPOS) why += " non-positive density or temperature;";
+    if (st & dvm::ST_SINGULAR) why += " singular correction system;";
+    if (st & dvm::ST_NUDT) why += " relaxation factor above 1 (dt too large for Kn);";
+    return fail(c, DVM_EUNSTABLE, std::string("unstable ") + what + ":" + why);
+}
+
 }  // namespace
 
 extern "C" {
@@ -227,7 +355,7 @@ int dvm_create(dvm_ctx **out, const dvm_config *cfg)
     if (!out || !cfg) return DVM_EINVAL;
     *out = nullptr;
     if (cfg->precision < DVM_F64 || cfg->precision > DVM_BF16) return DVM_EINVAL;
-    if (cfg->collision < DVM_COLL_NONE || cfg->collision > DVM_COLL_HS) return DVM_EINVAL;
+    if (cfg->collision < DVM_COLL_NONE || cfg->collision > DVM_COLL_LEARNED) return DVM_EINVAL;
     if (cfg->collision != DVM_COLL_NONE && !(cfg->kn > 0.0)) return DVM_EINVAL;
     dvm_ctx *c = new (std::nothrow) dvm_ctx();
     if (!c) return DVM_ENOMEM;
@@ -613,11 +741,14 @@ int dvm_step(dvm_ctx *c, int nsteps, double dt)
     if (!c || nsteps < 0) return DVM_EINVAL;
     if (c->state < 3) return fail(c, DVM_ESTATE, "f is not set");
     if (!(dt > 0.0) || !std::isfinite(dt)) return fail(c, DVM_EINVAL, "dt must be positive");
-    if (c->cfg.collision == DVM_COLL_HS && !c->hs.ready) return fail(c, DVM_ESTATE, "set the collision tables first");
+    if ((c->cfg.collision == DVM_COLL_HS || c->cfg.collision == DVM_COLL_LEARNED) && !c->hs.ready)
+        return fail(c, DVM_ESTATE, "set the collision tables first");
+    if (c->cfg.collision == DVM_COLL_LEARNED && (!c->mlp_set || !c->learned_cfg))
+        return fail(c, DVM_ESTATE, "set the network weights and the Knudsen threshold first");
     dvm::StepParams p{};
     p.dim = c->mesh.spec.dim;
     p.prec = c->cfg.precision;
-    p.coll = c->cfg.collision == DVM_COLL_HS ? DVM_COLL_NONE : c->cfg.collision;
+    p.coll = c->cfg.collision == DVM_COLL_BGK ? DVM_COLL_BGK : DVM_COLL_NONE;
     p.ncells = ncells_of(c);
     p.nv = c->nv;
     p.P = c->P;
@@ -640,6 +771,10 @@ int dvm_step(dvm_ctx *c, int nsteps, double dt)
                                  [c](void *q) { void *r = q; dev_free(c, r); });
         if (rc) return fail(c, rc, "hard-sphere scratch allocation failed");
     }
+    if (c->cfg.collision == DVM_COLL_LEARNED) {
+        int rc = learned_prepare(c);
+        if (rc) return rc;
+    }
     for (int s = 0; s < nsteps; s++) {
         p.f_in = c->d_f[c->cur];
         p.f_out = c->d_f[1 - c->cur];
@@ -652,6 +787,10 @@ int dvm_step(dvm_ctx *c, int nsteps, double dt)
         if (c->cfg.collision == DVM_COLL_HS) {
             rc = dvm::launch_hs_collide(c->hs, p, c->d_f[1 - c->cur], c->cfg.kn, dt);
             if (rc) return fail(c, rc, "hard-sphere collision launch failed");
+        }
+        if (c->cfg.collision == DVM_COLL_LEARNED) {
+            rc = learned_collide_device(c, static_cast<float *>(c->d_f[1 - c->cur]), c->d_mom, dt, nullptr, nullptr);
+            if (rc) return rc;
         }
         c->cur = 1 - c->cur;
     }
@@ -869,6 +1008,86 @@ int dvm_learned_train(dvm_ctx *c, const float *x, const float *t, int64_t n, int
     }
     if (!rc) rc = status_check(c);
     if (!rc && loss) *loss = last;
+    return rc;
+}
+
+int dvm_learned_configure(dvm_ctx *c, double kn_threshold)
+{
+    if (!c || !(kn_threshold >= 0.0)) return DVM_EINVAL;
+    c->kn_thr = kn_threshold;
+    c->learned_cfg = true;
+    return DVM_OK;
+}
+
+int dvm_learned_collide(dvm_ctx *c, double dt, const float *o_in, double *knl, float *a, float *o, int32_t *used,
+                        float *q)
+{
+    if (!c || !(dt > 0.0)) return DVM_EINVAL;
+    if (c->state < 3) return fail(c, DVM_ESTATE, "f is not set");
+    if (!c->hs.ready) return fail(c, DVM_ESTATE, "set the collision tables first");
+    if (!c->learned_cfg || (!o_in && !c->mlp_set)) return fail(c, DVM_ESTATE, "set the network weights and the Knudsen threshold first");
+    int rc = learned_prepare(c);
+    if (rc) return rc;
+    const int64_t nc = ncells_of(c);
+    float *f = static_cast<float *>(c->d_f[c->cur]);
+    rc = dvm::launch_moments(DVM_F32, f, nc, c->nv, c->d_xi, c->dV, c->d_mom2, c->stream);
+    if (rc) return fail(c, rc, "moments launch failed");
+    if (o_in) rc = cuda_check(c, cudaMemcpyAsync(c->d_lo, o_in, (size_t)nc * 256, cudaMemcpyHostToDevice, c->stream), "copy o");
+    if (!rc && o_in && a)
+        rc = dvm::launch_hermite_project(f, c->d_mom2, c->d_amag, nc, c->n, c->dV, 0, nullptr, nullptr, c->d_la,
+                                         c->d_status, c->stream);
+    if (rc) return fail(c, rc, "projection launch failed");
+    DevArr dq(c, q ? (size_t)nc * c->nv * 4 : 16);
+    if (!dq.p) return fail(c, DVM_ENOMEM, "device allocation (collision term)");
+    if (q) rc = cuda_check(c, cudaMemsetAsync(dq.p, 0, (size_t)nc * c->nv * 4, c->stream), "clear q");
+    if (!rc) rc = learned_collide_device(c, f, c->d_mom2, dt, o_in ? c->d_lo : nullptr, q ? dq.f() : nullptr);
+    if (rc) return rc;
+    rc = read_status(c, "learned collision");
+    if (rc) return rc;
+    if (knl) rc = cuda_check(c, cudaMemcpy(knl, c->d_knl, (size_t)nc * 8, cudaMemcpyDeviceToHost), "copy Kn");
+    if (!rc && a) rc = cuda_check(c, cudaMemcpy(a, c->d_la, (size_t)nc * 256, cudaMemcpyDeviceToHost), "copy a");
+    if (!rc && o) rc = cuda_check(c, cudaMemcpy(o, c->d_lo, (size_t)nc * 256, cudaMemcpyDeviceToHost), "copy o");
+    if (!rc && used) rc = cuda_check(c, cudaMemcpy(used, c->d_used, (size_t)nc * 4, cudaMemcpyDeviceToHost), "copy used");
+    if (!rc && q) rc = cuda_check(c, cudaMemcpy(q, dq.p, (size_t)nc * c->nv * 4, cudaMemcpyDeviceToHost), "copy q");
+    c->have_step_moments = false;
+    return rc;
+}
+
+int dvm_learned_pairs(dvm_ctx *c, float *a, float *o)
+{
+    if (!c || !a || !o) return DVM_EINVAL;
+    if (c->state < 3) return fail(c, DVM_ESTATE, "f is not set");
+    if (!c->hs.ready) return fail(c, DVM_ESTATE, "set the collision tables first");
+    if (c->cfg.precision != DVM_F32) return fail(c, DVM_ENOTIMPL, "training pairs need FP32 storage");
+    if (!dvm::learned_grid_supported(c->n)) return fail(c, DVM_ENOTIMPL, "velocity grid not supported by the learned kernels");
+    const int64_t nc = ncells_of(c);
+    int rc = dvm::hs_prepare(c->hs, nc, [c](size_t b) { return dev_alloc(c, b); }, [c](void *q) { void *r = q; dev_free(c, r); });
+    if (rc) return fail(c, rc, "hard-sphere scratch allocation failed");
+    DevArr dq(c, (size_t)nc * c->nv * 4), da(c, (size_t)nc * 256), dout(c, (size_t)nc * 256);
+    if (!dq.p || !da.p || !dout.p) return fail(c, DVM_ENOMEM, "device allocation (training pairs)");
+    float *f = static_cast<float *>(c->d_f[c->cur]);
+    rc = dvm::launch_moments(DVM_F32, f, nc, c->nv, c->d_xi, c->dV, c->d_mom2, c->stream);
+    if (!rc) rc = dvm::launch_hermite_project(f, c->d_mom2, c->d_amag, nc, c->n, c->dV, 0, nullptr, nullptr, da.f(),
+                                              c->d_status, c->stream);
+    dvm::StepParams p = collision_params(c, c->d_mom2);
+    if (!rc) rc = dvm::launch_hs_general(c->hs, p, f, nullptr, nullptr, dq.f(), c->cfg.kn, 0.0);
+    if (!rc) rc = dvm::launch_hermite_project(dq.f(), c->d_mom2, c->d_amag, nc, c->n, c->dV, 1, nullptr, nullptr,
+                                              dout.f(), c->d_status, c->stream);
+    if (rc) return fail(c, rc, "training-pair launch failed");
+    rc = read_status(c, "training pairs");
+    if (!rc) rc = cuda_check(c, cudaMemcpy(a, da.p, (size_t)nc * 256, cudaMemcpyDeviceToHost), "copy a");
+    if (!rc) rc = cuda_check(c, cudaMemcpy(o, dout.p, (size_t)nc * 256, cudaMemcpyDeviceToHost), "copy o");
+    return rc;
+}
+
+int dvm_learned_fallback_count(dvm_ctx *c, int64_t *n)
+{
+    if (!c || !n) return DVM_EINVAL;
+    if (!c->d_lcount) return fail(c, DVM_ESTATE, "no learned collision has run");
+    int v = 0;
+    int rc = cuda_check(c, cudaMemcpyAsync(&v, c->d_lcount, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "copy count");
+    if (!rc) rc = cuda_check(c, cudaStreamSynchronize(c->stream), "count");
+    *n = v;
     return rc;
 }
 

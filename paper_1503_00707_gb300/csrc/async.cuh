@@ -58,3 +58,19 @@ __device__ inline bool mbar_wait(uint64_t *bar, uint32_t parity)
 }
 
 }  // namespace dvm
+
+namespace dvm {
+
+// Bulk copy shared -> global in the bulk-group completion mechanism: the
+// issuing thread commits the group and waits until the copy has finished
+// reading shared memory before that memory is reused or released.
+__device__ inline void bulk_s2g(void *dst, const void *src, uint32_t bytes)
+{
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(smem_u32(src)),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ inline void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ inline void bulk_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+
+}  // namespace dvm

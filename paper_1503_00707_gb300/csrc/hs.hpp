@@ -46,6 +46,13 @@ int hs_prepare(HsTables &t, int64_t ncells, const DevAlloc &alloc, const DevFree
 // updated in place: f <- f* + dt/Kn * I(f*).
 int launch_hs_collide(HsTables &t, const StepParams &p, void *f, double kn, double dt);
 
+// The update restricted to the cells list[0 .. *count-1] (device list and
+// count, count <= p.ncells), or, if q_out is not NULL, the term I(f) of every
+// cell written to q_out [ncells][nv] with f left unchanged.  p.mom_out holds
+// the moments of f per cell.
+int launch_hs_general(HsTables &t, const StepParams &p, float *f, const int32_t *list, const int *count,
+                      float *q_out, double kn, double dt);
+
 // The same update on caller-owned f with a fixed, statically allocated
 // device scratch (no allocation).  Needs p.ncells * (8 nv + 40) bytes of
 // scratch at most DVM_HS_NOALLOC_SCRATCH_BYTES (else DVM_EINVAL); xi is the

@@ -39,7 +39,8 @@ constexpr int CT = 256;   // threads per CTA of k_hs_corr
 
 __global__ void __launch_bounds__(HT, 2)
     k_hs_bc(const float *__restrict__ fs, float2 *__restrict__ bc, int64_t ncells, int nv, int M,
-            const uint2 *__restrict__ idx, const float *__restrict__ bw, int64_t cells_per_cta, int *status)
+            const uint2 *__restrict__ idx, const float *__restrict__ bw, int64_t cells_per_cta,
+            const int32_t *__restrict__ list, const int *__restrict__ count, int *status)
 {
     extern __shared__ __align__(128) float tile[];  // [2][nv]
     __shared__ __align__(8) uint64_t bar[2];
@@ -60,8 +61,15 @@ __global__ void __launch_bounds__(HT, 2)
         w1[e] = t.y;
         b[e] = valid ? bw[e0 + e] : 0.0f;
     }
-    const int64_t c0 = (int64_t)blockIdx.y * cells_per_cta;
-    const int64_t c1 = c0 + cells_per_cta < ncells ? c0 + cells_per_cta : ncells;
+    // rows c0..c1-1 of this CTA: cells, or entries of the cell list
+    int64_t nrows = ncells, per = cells_per_cta;
+    if (list) {
+        nrows = *count;
+        per = (nrows + gridDim.y - 1) / gridDim.y;
+    }
+    const int64_t c0 = (int64_t)blockIdx.y * per;
+    const int64_t c1 = c0 + per < nrows ? c0 + per : nrows;
+    auto src = [&](int64_t r) { return fs + (list ? (int64_t)list[r] : r) * nv; };
     const uint32_t bytes = (uint32_t)nv * 4u;
     if (tid == 0) {
         mbar_init(&bar[0], 1);
@@ -75,7 +83,7 @@ __global__ void __launch_bounds__(HT, 2)
     if (c0 < c1) {
         if (tid == 0) {
             mbar_expect_tx(&bar[0], bytes);
-            bulk_g2s(tile, fs + c0 * nv, bytes, &bar[0]);
+            bulk_g2s(tile, src(c0), bytes, &bar[0]);
         }
         issued[0]++;
     }
@@ -86,7 +94,7 @@ __global__ void __launch_bounds__(HT, 2)
             // with a barrier
             if (tid == 0) {
                 mbar_expect_tx(&bar[s ^ 1], bytes);
-                bulk_g2s(tile + (size_t)(s ^ 1) * nv, fs + (c + 1) * nv, bytes, &bar[s ^ 1]);
+                bulk_g2s(tile + (size_t)(s ^ 1) * nv, src(c + 1), bytes, &bar[s ^ 1]);
             }
             issued[s ^ 1]++;
         }
@@ -123,18 +131,22 @@ __global__ void __launch_bounds__(HT, 2)
 
 __global__ void __launch_bounds__(CT)
     k_hs_corr(float *__restrict__ f, const float2 *__restrict__ bc, const float *__restrict__ xi3,
-              const double *__restrict__ mom, int nv, float dtkn, int *status)
+              const double *__restrict__ mom, int nv, float dtkn, const int32_t *__restrict__ list,
+              const int *__restrict__ count, float *__restrict__ q_out, int *status)
 {
     __shared__ float red[CT / 32][20];
     __shared__ float sd[6];
-    const int64_t cell = blockIdx.x;
+    // row blockIdx.x of B and C belongs to this cell (an entry of the list, if any)
+    const int64_t row = blockIdx.x;
+    if (list && row >= (int64_t)*count) return;
+    const int64_t cell = list ? (int64_t)list[row] : row;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const double *mo = mom + cell * 5;
     const float ux = (float)mo[1], uy = (float)mo[2], uz = (float)mo[3];
     const float T = (float)mo[4];
     const float ist = T > 0.0f ? rsqrtf(T) : 0.0f;
     float *fc = f + cell * (int64_t)nv;
-    const float2 *bcc = bc + cell * (int64_t)nv;
+    const float2 *bcc = bc + row * (int64_t)nv;
     float acc[20];
 #pragma unroll
     for (int k = 0; k < 20; k++) acc[k] = 0.0f;
@@ -196,7 +208,8 @@ __global__ void __launch_bounds__(CT)
         const float P = 1.0f + d0 + dx * cx + dy * cy + dz * cz + d4 * (cx * cx + cy * cy + cz * cz - 3.0f);
         const float loss = P * q.x;
         worst = fmaxf(worst, dtkn * loss);
-        fc[v] = fmaf(dtkn, q.y - fv * loss, fv);
+        if (q_out) q_out[cell * (int64_t)nv + v] = q.y - fv * loss;  // the term I alone, f kept
+        else fc[v] = fmaf(dtkn, q.y - fv * loss, fv);
     }
     if (worst > 1.0f) atomicOr(status, ST_NUDT);
 }
@@ -246,12 +259,48 @@ int launch_hs_collide(HsTables &t, const StepParams &p, void *f, double kn, doub
     const dim3 grid((unsigned)chunks, (unsigned)splits);
     k_hs_bc<<<grid, HT, dyn, p.stream>>>(static_cast<const float *>(f), reinterpret_cast<float2 *>(t.d_bc),
                                           p.ncells, p.nv, t.trials, static_cast<const uint2 *>(t.d_idx), t.d_b,
-                                          per, p.status);
+                                          per, nullptr, nullptr, p.status);
     count_launch();
     if (cudaGetLastError() != cudaSuccess) return DVM_ECUDA;
     k_hs_corr<<<(unsigned)p.ncells, CT, 0, p.stream>>>(static_cast<float *>(f),
                                                       reinterpret_cast<const float2 *>(t.d_bc), t.d_xi,
-                                                      p.mom_out, p.nv, (float)(dt / kn), p.status);
+                                                      p.mom_out, p.nv, (float)(dt / kn), nullptr, nullptr, nullptr,
+                                                      p.status);
+    count_launch();
+    return cudaGetLastError() == cudaSuccess ? DVM_OK : DVM_ECUDA;
+}
+
+// The update on the cells of a device list only (*count entries, at most
+// p.ncells), or, with q_out, the term I of every cell without the update.
+int launch_hs_general(HsTables &t, const StepParams &p, float *f, const int32_t *list, const int *count,
+                      float *q_out, double kn, double dt)
+{
+    if (p.prec != DVM_F32) return DVM_ENOTIMPL;
+    if (!t.ready || t.nv != p.nv || !t.d_bc || t.bc_cells < p.ncells) return DVM_ESTATE;
+    if (p.ncells <= 0) return DVM_OK;
+    const int tpn = t.trials / HE, npc = HT / tpn;
+    const int chunks = (p.nv + npc - 1) / npc;
+    const size_t dyn = 2 * (size_t)p.nv * sizeof(float);
+    if (dyn > 200 * 1024) return DVM_ENOTIMPL;
+    if (cudaFuncSetAttribute(k_hs_bc, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) != cudaSuccess)
+        return DVM_ECUDA;
+    int dev = 0, nsm = 0, occ = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_hs_bc, HT, dyn) != cudaSuccess || occ < 1)
+        return DVM_ENOTIMPL;
+    int64_t splits = std::max<int64_t>(1, (2 * (int64_t)nsm * occ + chunks - 1) / chunks);
+    splits = std::min<int64_t>(splits, p.ncells);
+    const int64_t per = (p.ncells + splits - 1) / splits;
+    splits = (p.ncells + per - 1) / per;
+    k_hs_bc<<<dim3((unsigned)chunks, (unsigned)splits), HT, dyn, p.stream>>>(
+        f, reinterpret_cast<float2 *>(t.d_bc), p.ncells, p.nv, t.trials, static_cast<const uint2 *>(t.d_idx), t.d_b,
+        per, list, count, p.status);
+    count_launch();
+    if (cudaGetLastError() != cudaSuccess) return DVM_ECUDA;
+    k_hs_corr<<<(unsigned)p.ncells, CT, 0, p.stream>>>(f, reinterpret_cast<const float2 *>(t.d_bc), t.d_xi,
+                                                      p.mom_out, p.nv, q_out ? 0.0f : (float)(dt / kn), list, count,
+                                                      q_out, p.status);
     count_launch();
     return cudaGetLastError() == cudaSuccess ? DVM_OK : DVM_ECUDA;
 }
@@ -324,11 +373,11 @@ int launch_hs_collide_noalloc(HsTables &t, const StepParams &p, float *f, const 
     splits = (p.ncells + per - 1) / per;
     k_hs_bc<<<dim3((unsigned)chunks, (unsigned)splits), HT, dyn, p.stream>>>(
         f, reinterpret_cast<float2 *>(bc), p.ncells, p.nv, t.trials, static_cast<const uint2 *>(t.d_idx), t.d_b,
-        per, p.status);
+        per, nullptr, nullptr, p.status);
     count_launch();
     if (cudaGetLastError() != cudaSuccess) return DVM_ECUDA;
     k_hs_corr<<<(unsigned)p.ncells, CT, 0, p.stream>>>(f, reinterpret_cast<const float2 *>(bc), t.d_xi, mom, p.nv,
-                                                      (float)(dt / kn), p.status);
+                                                      (float)(dt / kn), nullptr, nullptr, nullptr, p.status);
     count_launch();
     return cudaGetLastError() == cudaSuccess ? DVM_OK : DVM_ECUDA;
 }

@@ -1,0 +1,540 @@
+// Learned collision operator (not in the paper: the network, its gating by
+// the local Knudsen number and its checks).  Per cell:
+//
+//   k_kn      local Knudsen number Kn_loc = (Kn/rho) max(|grad rho|/rho,
+//             |grad T|/T, |grad u|/sqrt(T)), gradients by weighted least
+//             squares over the face neighbours (coefficients precomputed on
+//             the host from the geometry);
+//   k_proj    a_m = sum_i f_i H_m(c_i) dV / rho (mode 0) or
+//             o_m = sum_i I_i H_m(c_i) dV / (rho^2 sqrt(T)) (mode 1), the
+//             projection on the 64 tensor Hermite modes H_m = He_a He_b He_c
+//             (orthonormal probabilists' Hermite, a, b, c < 4) in the
+//             Maxwellian-normalised velocity c = (xi - u)/sqrt(T);
+//   k_lapply  Q_i = M_i (rho sqrt(T) sum_m o_m H_m(c_i) - d.phi_i), with the
+//             five coefficients d of the centred basis phi = (1, c, |c|^2 - 3)
+//             chosen so that Q carries no mass, momentum or energy (the
+//             correction form of Eq. 6 applied to the reconstructed term);
+//             the cell keeps f + dt/Kn Q only if sum Q ln f <= 0 (entropy)
+//             and the 5x5 solve is exact to its residual, else it joins the
+//             list of cells left to the hard-sphere operator.
+//
+// Velocity nodes come in the step kernel's group layout: node (ix, iy, iz)
+// of group o = 4 sx + 2 sy + sz sits at o P + (mx Hy + my) Hz + mz, with
+// ix = Hx + mx for sx = 1 and Hx - 1 - mx for sx = 0.  The Hermite modes,
+// the Maxwellian and the moment basis all factorise over the axes, so the
+// projection and the reconstruction are separable contractions on per-axis
+// tables in shared memory, and the moment system is built from per-axis
+// sums.  A cell's f arrives in shared memory as one bulk copy; the updated
+// f leaves it the same way.
+#include <cuda_runtime.h>
+
+#include <cmath>
+
+#include "../../include/dvm.h"
+#include "async.cuh"
+#include "common.cuh"
+#include "kernels.hpp"
+#include "learned.hpp"
+
+namespace dvm {
+
+void count_launch();
+
+namespace {
+
+constexpr int PT = 128;   // threads of k_proj
+constexpr int AT = 256;   // threads of k_lapply
+constexpr int MAXN = 32;  // velocity nodes per axis
+
+constexpr float RS2 = 0.70710678118654752f;  // 1/sqrt(2)
+constexpr float RS6 = 0.40824829046386302f;  // 1/sqrt(6)
+
+// ---------------------------------------------------------------- local Kn
+__global__ void k_kn(const double *__restrict__ mom, const int32_t *__restrict__ start,
+                     const int32_t *__restrict__ nb, const double *__restrict__ coef, int64_t ncells, double kn,
+                     double *__restrict__ knl)
+{
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncells) return;
+    const double *m = mom + c * 5;
+    const double q[5] = {m[0], m[4], m[1], m[2], m[3]};  // rho, T, u
+    double g[5][3] = {};
+    for (int e = start[c]; e < start[c + 1]; e++) {
+        const double *mn = mom + (int64_t)nb[e] * 5;
+        const double dq[5] = {mn[0] - q[0], mn[4] - q[1], mn[1] - q[2], mn[2] - q[3], mn[3] - q[4]};
+        const double w0 = coef[3 * (int64_t)e], w1 = coef[3 * (int64_t)e + 1], w2 = coef[3 * (int64_t)e + 2];
+#pragma unroll
+        for (int k = 0; k < 5; k++) {
+            g[k][0] = fma(w0, dq[k], g[k][0]);
+            g[k][1] = fma(w1, dq[k], g[k][1]);
+            g[k][2] = fma(w2, dq[k], g[k][2]);
+        }
+    }
+    double gr = 0, gT = 0, gu = 0;
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+        gr += g[0][d] * g[0][d];
+        gT += g[1][d] * g[1][d];
+        gu += g[2][d] * g[2][d] + g[3][d] * g[3][d] + g[4][d] * g[4][d];
+    }
+    double mm = sqrt(gr) / q[0];
+    const double t1 = sqrt(gT) / q[1], t2 = sqrt(gu) / sqrt(q[1]);
+    if (t1 > mm) mm = t1;
+    if (t2 > mm) mm = t2;
+    knl[c] = kn / q[0] * mm;
+}
+
+// ---------------------------------------------------------------- helpers
+// per-axis tables: H[d][i] = (He_1, He_2, He_3, exp(-c^2/2)) and G[d][i] = c
+// at node i of axis d, c = (xi - u_d) / sqrt(T)
+__device__ inline void axis_tables(const double *amag, int3 n, const float u[3], float ist, float4 (*H)[MAXN],
+                                   float (*G)[MAXN], int tid, int nthreads)
+{
+    const int tot = n.x + n.y + n.z;
+    for (int k = tid; k < tot; k += nthreads) {
+        const int d = k < n.x ? 0 : (k < n.x + n.y ? 1 : 2);
+        const int i = k - (d == 0 ? 0 : (d == 1 ? n.x : n.x + n.y));
+        const int nd = d == 0 ? n.x : (d == 1 ? n.y : n.z);
+        const int hd = nd / 2;
+        float xi = (float)amag[d * 32 + (i < hd ? hd - 1 - i : i - hd)];
+        if (i < hd) xi = -xi;
+        const float c = (xi - u[d]) * ist;
+        const float c2 = c * c;
+        H[d][i] = make_float4(c, (c2 - 1.0f) * RS2, (c2 - 3.0f) * c * RS6, expf(-0.5f * c2));
+        if (G) G[d][i] = c;
+    }
+}
+
+// Sum of v[0..63] over the warp, scattered: lane l ends with the sums of
+// entries 2l and 2l+1 in v[0] and v[1] (62 shuffles instead of 320).
+__device__ inline void warp_reduce_scatter64(float (&v)[64], int lane)
+{
+#pragma unroll
+    for (int s = 0; s < 5; s++) {
+        const int off = 16 >> s, half = 32 >> s;
+        const bool up = lane & off;
+#pragma unroll
+        for (int i = 0; i < half; i++) {
+            const float send = up ? v[i] : v[half + i];
+            const float keep = up ? v[half + i] : v[i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+        }
+    }
+}
+
+// Bounded wait for a CTA's single tile copy; on failure every thread learns
+// it through *abort and thread 0 gives the copy one more bounded wait.
+__device__ inline bool tile_arrived(uint64_t *bar, int *abort, int *status)
+{
+    if (!mbar_wait(bar, 0)) *abort = 1;
+    __syncthreads();
+    if (*abort) {
+        if (threadIdx.x == 0) {
+            atomicOr(status, ST_TIMEOUT);
+            mbar_wait(bar, 0);
+        }
+        return false;
+    }
+    return true;
+}
+
+// ---------------------------------------------------------------- projection
+template <int MODE>
+__global__ void __launch_bounds__(PT) k_proj(const float *__restrict__ f, const double *__restrict__ mom,
+                                             const double *__restrict__ amag, int3 n, double dV,
+                                             const int32_t *__restrict__ list, const int *__restrict__ count,
+                                             float *__restrict__ out, int *status)
+{
+    extern __shared__ __align__(128) float tile[];  // [nv]
+    __shared__ float4 H[3][MAXN];
+    __shared__ float red[PT / 32][64];
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ int abort_flag;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (list && (int64_t)blockIdx.x >= (int64_t)*count) return;
+    const int64_t row = blockIdx.x;
+    const int64_t cell = list ? (int64_t)list[row] : row;
+    const int nv = n.x * n.y * n.z;
+    const uint32_t bytes = (uint32_t)nv * 4u;
+    if (tid == 0) {
+        mbar_init(&bar, 1);
+        abort_flag = 0;
+        mbar_fence_init();
+    }
+    __syncthreads();
+    if (tid == 0) {
+        mbar_expect_tx(&bar, bytes);
+        bulk_g2s(tile, f + cell * nv, bytes, &bar);
+    }
+    const double *mo = mom + cell * 5;
+    const double rho = mo[0], T = mo[4];
+    const float u[3] = {(float)mo[1], (float)mo[2], (float)mo[3]};
+    const float ist = T > 0.0 ? (float)(1.0 / sqrt(T)) : 0.0f;
+    axis_tables(amag, n, u, ist, H, nullptr, tid, PT);
+    if (!tile_arrived(&bar, &abort_flag, status)) return;
+
+    float acc[64];
+#pragma unroll
+    for (int k = 0; k < 64; k++) acc[k] = 0.0f;
+    const int Hx = n.x / 2, Hy = n.y / 2, Hz = n.z / 2, P = Hx * Hy * Hz;
+    for (int pp = tid; pp < n.x * n.y; pp += PT) {
+        const int ix = pp / n.y, iy = pp - ix * n.y;
+        const int sx = ix >= Hx, sy = iy >= Hy;
+        const int mx = sx ? ix - Hx : Hx - 1 - ix, my = sy ? iy - Hy : Hy - 1 - iy;
+        // contraction over z: t_c = sum_iz f He_c(iz)
+        float t0 = 0.0f, t1 = 0.0f, t2 = 0.0f, t3 = 0.0f;
+#pragma unroll
+        for (int sz = 0; sz < 2; sz++) {
+            const float *hp = tile + (4 * sx + 2 * sy + sz) * P + (mx * Hy + my) * Hz;
+            for (int mz = 0; mz < Hz; mz += 4) {
+                const float4 v4 = *reinterpret_cast<const float4 *>(hp + mz);
+                const float vv[4] = {v4.x, v4.y, v4.z, v4.w};
+#pragma unroll
+                for (int e = 0; e < 4; e++) {
+                    const float4 h = H[2][sz ? Hz + mz + e : Hz - 1 - mz - e];
+                    t0 += vv[e];
+                    t1 = fmaf(vv[e], h.x, t1);
+                    t2 = fmaf(vv[e], h.y, t2);
+                    t3 = fmaf(vv[e], h.z, t3);
+                }
+            }
+        }
+        const float4 hx = H[0][ix], hy = H[1][iy];
+        const float wx[4] = {1.0f, hx.x, hx.y, hx.z}, wy[4] = {1.0f, hy.x, hy.y, hy.z};
+        const float tz[4] = {t0, t1, t2, t3};
+#pragma unroll
+        for (int a = 0; a < 4; a++)
+#pragma unroll
+            for (int b = 0; b < 4; b++) {
+                const float w = wx[a] * wy[b];
+#pragma unroll
+                for (int c = 0; c < 4; c++) acc[16 * a + 4 * b + c] = fmaf(w, tz[c], acc[16 * a + 4 * b + c]);
+            }
+    }
+    warp_reduce_scatter64(acc, lane);
+    red[warp][2 * lane] = acc[0];
+    red[warp][2 * lane + 1] = acc[1];
+    __syncthreads();
+    if (tid < 64) {
+        float s = 0.0f;
+#pragma unroll
+        for (int w = 0; w < PT / 32; w++) s += red[w][tid];
+        const double scale = MODE == 0 ? dV / rho : dV / (rho * rho * sqrt(T));
+        out[row * 64 + tid] = (float)((double)s * scale);
+    }
+}
+
+// ---------------------------------------------------------------- apply
+__global__ void __launch_bounds__(AT) k_lapply(float *__restrict__ f, const double *__restrict__ mom,
+                                               const float *__restrict__ o, const double *__restrict__ knl,
+                                               double thr, const double *__restrict__ amag, int3 n, float dtkn,
+                                               int32_t *__restrict__ used, int32_t *__restrict__ list,
+                                               int *__restrict__ count, float *__restrict__ q_out, int *status)
+{
+    extern __shared__ __align__(128) float dsm[];
+    __shared__ float4 H[3][MAXN];
+    __shared__ float G[3][MAXN];
+    __shared__ float S1[16][MAXN];
+    __shared__ float4 ZT[MAXN];  // (exp(-cz^2/2), d3 cz + d4 cz^2, cz^2/2, 0)
+    __shared__ float os[64];
+    __shared__ float sums[3][14];
+    __shared__ float rred[2][5];
+    __shared__ double cc[5];
+    __shared__ double ered[AT / 32];
+    __shared__ int good;
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ int abort_flag;
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t cell = blockIdx.x;
+    if (!(knl[cell] < thr)) {
+        // above the Knudsen threshold (or undefined): the plain operator
+        if (tid == 0) {
+            used[cell] = 0;
+            list[atomicAdd(count, 1)] = (int32_t)cell;
+        }
+        return;
+    }
+    const int nv = n.x * n.y * n.z;
+    const uint32_t bytes = (uint32_t)nv * 4u;
+    float *tile = dsm;                                             // [nv]
+    float4 *S2 = reinterpret_cast<float4 *>(dsm + nv);            // [ny][nz]: modes a = 0..3
+    if (tid == 0) {
+        mbar_init(&bar, 1);
+        abort_flag = 0;
+        mbar_fence_init();
+    }
+    __syncthreads();
+    if (tid == 0) {
+        mbar_expect_tx(&bar, bytes);
+        bulk_g2s(tile, f + cell * nv, bytes, &bar);
+    }
+    const double *mo = mom + cell * 5;
+    const double rho = mo[0], T = mo[4];
+    const bool valid = rho > 0.0 && T > 0.0 && isfinite(rho) && isfinite(T);
+    const double sq = valid ? sqrt(T) : 1.0;
+    const float u[3] = {(float)mo[1], (float)mo[2], (float)mo[3]};
+    const float ist = (float)(1.0 / sq);
+    const double Mc = valid ? rho * 0.06349363593424097 / (T * sq) : 1.0;  // rho (2 pi T)^(-3/2)
+    const float Mcf = (float)Mc, lnMc = (float)log(Mc), rsq = (float)(rho * sq);
+    if (tid < 64) os[tid] = o[cell * 64 + tid];
+    axis_tables(amag, n, u, ist, H, G, tid, AT);
+    __syncthreads();
+    const int nz = n.z;
+    // per-axis sums: E_k = sum e c^k (k < 5), G_ak = sum e He_a c^k (a = 1..3, k < 3)
+    if (tid < 42) {
+        const int d = tid / 14, k = tid % 14;
+        const int nd = d == 0 ? n.x : (d == 1 ? n.y : n.z);
+        float s = 0.0f;
+        for (int i = 0; i < nd; i++) {
+            const float4 h = H[d][i];
+            const float c = G[d][i];
+            float t;
+            if (k < 5) {
+                t = h.w;
+                for (int q = 0; q < k; q++) t *= c;
+            } else {
+                const int a = (k - 5) / 3, kk = (k - 5) % 3;
+                t = h.w * (a == 0 ? h.x : (a == 1 ? h.y : h.z));
+                for (int q = 0; q < kk; q++) t *= c;
+            }
+            s += t;
+        }
+        sums[d][k] = s;
+    }
+    // S1[4a+b][iz] = sum_c o_abc He_c(iz)
+    for (int idx = tid; idx < 16 * nz; idx += AT) {
+        const int ab = idx / nz, iz = idx - ab * nz;
+        const float4 h = H[2][iz];
+        const float *om = os + 4 * ab;
+        S1[ab][iz] = om[0] + om[1] * h.x + om[2] * h.y + om[3] * h.z;
+    }
+    __syncthreads();
+    // S2[iy][iz][a] = sum_b S1[4a+b][iz] He_b(iy)
+    for (int idx = tid; idx < n.y * nz; idx += AT) {
+        const int iy = idx / nz, iz = idx - iy * nz;
+        const float4 h = H[1][iy];
+        float r[4];
+#pragma unroll
+        for (int a = 0; a < 4; a++)
+            r[a] = S1[4 * a][iz] + S1[4 * a + 1][iz] * h.x + S1[4 * a + 2][iz] * h.y + S1[4 * a + 3][iz] * h.z;
+        S2[idx] = make_float4(r[0], r[1], r[2], r[3]);
+    }
+    // moments of the reconstructed term: sum_m o_m R_r(m), R_r = sum e H_m phi_r
+    if (tid < 64) {
+        const int a = tid >> 4, b = (tid >> 2) & 3, c = tid & 3;
+        float gx[3], gy[3], gz[3];
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            gx[k] = a == 0 ? sums[0][k] : sums[0][5 + 3 * (a - 1) + k];
+            gy[k] = b == 0 ? sums[1][k] : sums[1][5 + 3 * (b - 1) + k];
+            gz[k] = c == 0 ? sums[2][k] : sums[2][5 + 3 * (c - 1) + k];
+        }
+        const float w = os[tid];
+        float r[5];
+        r[0] = gx[0] * gy[0] * gz[0];
+        r[1] = gx[1] * gy[0] * gz[0];
+        r[2] = gx[0] * gy[1] * gz[0];
+        r[3] = gx[0] * gy[0] * gz[1];
+        r[4] = gx[2] * gy[0] * gz[0] + gx[0] * gy[2] * gz[0] + gx[0] * gy[0] * gz[2] - 3.0f * r[0];
+#pragma unroll
+        for (int k = 0; k < 5; k++) {
+            r[k] *= w;
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) r[k] += __shfl_xor_sync(0xffffffffu, r[k], off);
+        }
+        if (lane == 0)
+#pragma unroll
+            for (int k = 0; k < 5; k++) rred[warp][k] = r[k];
+    }
+    __syncthreads();
+    if (tid == 0) {
+        // the moment system over dV Mc: A_rs = sum e phi_r phi_s from per-axis sums
+        double X[5], Y[5], Z[5];
+        for (int k = 0; k < 5; k++) { X[k] = sums[0][k]; Y[k] = sums[1][k]; Z[k] = sums[2][k]; }
+        double A[25], rhs[5], x[5];
+        const double a00 = X[0] * Y[0] * Z[0];
+        const double s2 = X[2] * Y[0] * Z[0] + X[0] * Y[2] * Z[0] + X[0] * Y[0] * Z[2];
+        A[0] = a00;
+        A[1] = X[1] * Y[0] * Z[0];
+        A[2] = X[0] * Y[1] * Z[0];
+        A[3] = X[0] * Y[0] * Z[1];
+        A[4] = s2 - 3.0 * a00;
+        A[6] = X[2] * Y[0] * Z[0];
+        A[7] = X[1] * Y[1] * Z[0];
+        A[8] = X[1] * Y[0] * Z[1];
+        A[9] = X[3] * Y[0] * Z[0] + X[1] * Y[2] * Z[0] + X[1] * Y[0] * Z[2] - 3.0 * A[1];
+        A[12] = X[0] * Y[2] * Z[0];
+        A[13] = X[0] * Y[1] * Z[1];
+        A[14] = X[2] * Y[1] * Z[0] + X[0] * Y[3] * Z[0] + X[0] * Y[1] * Z[2] - 3.0 * A[2];
+        A[18] = X[0] * Y[0] * Z[2];
+        A[19] = X[2] * Y[0] * Z[1] + X[0] * Y[2] * Z[1] + X[0] * Y[0] * Z[3] - 3.0 * A[3];
+        A[24] = X[4] * Y[0] * Z[0] + X[0] * Y[4] * Z[0] + X[0] * Y[0] * Z[4] +
+                2.0 * (X[2] * Y[2] * Z[0] + X[2] * Y[0] * Z[2] + X[0] * Y[2] * Z[2]) - 6.0 * s2 + 9.0 * a00;
+        for (int r = 0; r < 5; r++)
+            for (int c = 0; c < r; c++) A[r * 5 + c] = A[c * 5 + r];
+        for (int r = 0; r < 5; r++) rhs[r] = (double)rsq * ((double)rred[0][r] + (double)rred[1][r]);
+        double A0[25], b0[5];
+        for (int k = 0; k < 25; k++) A0[k] = A[k];
+        for (int k = 0; k < 5; k++) b0[k] = rhs[k];
+        bool ok = valid && solve5<double>(A, rhs, x);
+        if (ok) {
+            // conservation residual of the correction, in FP64
+            double rn = 0.0, sc = 0.0;
+            for (int r = 0; r < 5; r++) {
+                double s = -b0[r], t = fabs(b0[r]);
+                for (int c = 0; c < 5; c++) {
+                    s += A0[r * 5 + c] * x[c];
+                    t += fabs(A0[r * 5 + c] * x[c]);
+                }
+                rn = fmax(rn, fabs(s));
+                sc = fmax(sc, t);
+            }
+            ok = rn <= 1e-12 * sc;
+        }
+        for (int k = 0; k < 5; k++) cc[k] = ok ? x[k] : 0.0;
+        good = ok ? 1 : 0;
+    }
+    __syncthreads();
+    const float d0 = (float)cc[0], d1 = (float)cc[1], d2 = (float)cc[2], d3 = (float)cc[3], d4 = (float)cc[4];
+    for (int iz = tid; iz < nz; iz += AT) {
+        const float c = G[2][iz];
+        ZT[iz] = make_float4(H[2][iz].w, c * (d3 + d4 * c), 0.5f * c * c, 0.0f);
+    }
+    if (!tile_arrived(&bar, &abort_flag, status)) return;  // includes a barrier
+
+    const int Hx = n.x / 2, Hy = n.y / 2, Hz = nz / 2, P = Hx * Hy * Hz;
+    // Q at node (pencil constants, mz + e): M (rho sqrt(T) s - d.phi)
+    auto pencil = [&](int pp, auto &&visit) {
+        const int ix = pp / n.y, iy = pp - ix * n.y;
+        const int sx = ix >= Hx, sy = iy >= Hy;
+        const int mx = sx ? ix - Hx : Hx - 1 - ix, my = sy ? iy - Hy : Hy - 1 - iy;
+        const float4 hx = H[0][ix], hy = H[1][iy];
+        const float gx = G[0][ix], gy = G[1][iy];
+        const float w0 = rsq, w1 = rsq * hx.x, w2 = rsq * hx.y, w3 = rsq * hx.z;
+        const float K0 = d0 + d1 * gx + d2 * gy + d4 * (gx * gx + gy * gy - 3.0f);
+        const float Pxy = Mcf * hx.w * hy.w;
+        const float Lxy = lnMc - 0.5f * (gx * gx + gy * gy);
+        const float4 *s2row = S2 + iy * nz;
+#pragma unroll
+        for (int sz = 0; sz < 2; sz++) {
+            const int base = (4 * sx + 2 * sy + sz) * P + (mx * Hy + my) * Hz;
+            for (int mz = 0; mz < Hz; mz += 4) {
+                float4 *fp = reinterpret_cast<float4 *>(tile + base + mz);
+                float fv[4] = {fp->x, fp->y, fp->z, fp->w};
+                float Q[4], lnM[4];
+#pragma unroll
+                for (int e = 0; e < 4; e++) {
+                    const int iz = sz ? Hz + mz + e : Hz - 1 - mz - e;
+                    const float4 s = s2row[iz];
+                    const float4 z = ZT[iz];
+                    const float sv = fmaf(w3, s.w, fmaf(w2, s.z, fmaf(w1, s.y, w0 * s.x)));
+                    Q[e] = Pxy * z.x * (sv - K0 - z.y);
+                    lnM[e] = Lxy - z.z;
+                }
+                visit(fp, fv, Q, lnM, base + mz);
+            }
+        }
+    };
+    float ent = 0.0f;
+    if (good) {
+        for (int pp = tid; pp < n.x * n.y; pp += AT)
+            pencil(pp, [&](float4 *, const float (&fv)[4], const float (&Q)[4], const float (&lnM)[4], int) {
+#pragma unroll
+                for (int e = 0; e < 4; e++) {
+                    const float x = fv[e];
+                    // ln f, with ln(1e-300) standing in for f <= 0
+                    const float lf = x >= 1.17549435e-38f ? __logf(x) : (x > 0.0f ? logf(x) : -690.77552789821f);
+                    ent = fmaf(Q[e], lf - lnM[e], ent);
+                }
+            });
+    }
+    double e64 = (double)ent;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) e64 += __shfl_xor_sync(0xffffffffu, e64, off);
+    if (lane == 0) ered[warp] = e64;
+    __syncthreads();
+    if (tid == 0) {
+        double s = 0.0;
+        for (int w = 0; w < AT / 32; w++) s += ered[w];
+        good = good && isfinite(s) && s <= 0.0;
+    }
+    __syncthreads();
+    if (!good) {
+        if (tid == 0) {
+            used[cell] = 0;
+            list[atomicAdd(count, 1)] = (int32_t)cell;
+        }
+        return;
+    }
+    float *qc = q_out ? q_out + cell * nv : nullptr;
+    for (int pp = tid; pp < n.x * n.y; pp += AT)
+        pencil(pp, [&](float4 *fp, const float (&fv)[4], const float (&Q)[4], const float (&)[4], int v) {
+            *fp = make_float4(fmaf(dtkn, Q[0], fv[0]), fmaf(dtkn, Q[1], fv[1]), fmaf(dtkn, Q[2], fv[2]),
+                              fmaf(dtkn, Q[3], fv[3]));
+            if (qc) *reinterpret_cast<float4 *>(qc + v) = make_float4(Q[0], Q[1], Q[2], Q[3]);
+        });
+    fence_proxy_async();
+    __syncthreads();
+    if (tid == 0) {
+        used[cell] = 1;
+        bulk_s2g(f + cell * nv, tile, bytes);
+        bulk_commit();
+        bulk_wait_read_all();
+    }
+}
+
+bool grid_ok(const int n[3])
+{
+    for (int d = 0; d < 3; d++)
+        if (n[d] > MAXN || n[d] < 2 || n[d] % 2) return false;
+    return (n[2] / 2) % 4 == 0;
+}
+
+}  // namespace
+
+bool learned_grid_supported(const int n[3]) { return grid_ok(n); }
+
+int launch_kn_local(const double *mom, const int32_t *start, const int32_t *nb, const double *coef, int64_t ncells,
+                    double kn, double *knl, cudaStream_t s)
+{
+    if (ncells <= 0) return DVM_OK;
+    k_kn<<<(unsigned)((ncells + 255) / 256), 256, 0, s>>>(mom, start, nb, coef, ncells, kn, knl);
+    count_launch();
+    return cudaGetLastError() == cudaSuccess ? DVM_OK : DVM_ECUDA;
+}
+
+int launch_hermite_project(const float *f, const double *mom, const double *amag, int64_t rows, const int n[3],
+                           double dV, int mode, const int32_t *list, const int *count, float *out, int *status,
+                           cudaStream_t s)
+{
+    if (!grid_ok(n)) return DVM_ENOTIMPL;
+    if (rows <= 0) return DVM_OK;
+    const size_t dyn = (size_t)n[0] * n[1] * n[2] * sizeof(float);
+    if (dyn > 200 * 1024) return DVM_ENOTIMPL;
+    const int3 nn = make_int3(n[0], n[1], n[2]);
+    auto kern = mode == 0 ? k_proj<0> : k_proj<1>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) != cudaSuccess)
+        return DVM_ECUDA;
+    kern<<<(unsigned)rows, PT, dyn, s>>>(f, mom, amag, nn, dV, list, count, out, status);
+    count_launch();
+    return cudaGetLastError() == cudaSuccess ? DVM_OK : DVM_ECUDA;
+}
+
+int launch_learned_apply(float *f, const double *mom, const float *o, const double *knl, double thr,
+                         const double *amag, int64_t ncells, const int n[3], double dtkn, int32_t *used,
+                         int32_t *list, int *count, float *q_out, int *status, cudaStream_t s)
+{
+    if (!grid_ok(n)) return DVM_ENOTIMPL;
+    if (ncells <= 0) return DVM_OK;
+    const size_t dyn = (size_t)n[0] * n[1] * n[2] * sizeof(float) + (size_t)n[1] * n[2] * sizeof(float4);
+    if (dyn > 200 * 1024) return DVM_ENOTIMPL;
+    if (cudaFuncSetAttribute(k_lapply, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) != cudaSuccess)
+        return DVM_ECUDA;
+    k_lapply<<<(unsigned)ncells, AT, dyn, s>>>(f, mom, o, knl, thr, amag, make_int3(n[0], n[1], n[2]), (float)dtkn,
+                                                used, list, count, q_out, status);
+    count_launch();
+    return cudaGetLastError() == cudaSuccess ? DVM_OK : DVM_ECUDA;
+}
+
+}  // namespace dvm

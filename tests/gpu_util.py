@@ -1,5 +1,7 @@
 """Shared set-up for the GPU parity tests: the same seeded workload on the
 CUDA path (through the C ABI) and on the oracle."""
+import math
+
 import numpy as np
 
 import oracle as O
@@ -40,3 +42,22 @@ def rel_linf(a, b):
 def field_errors(s_mom, o_mom):
     (r1, u1, T1), (r2, u2, T2) = s_mom, o_mom
     return {"rho": rel_linf(r1, r2), "u": rel_linf(u1, u2), "T": rel_linf(T1, T2)}
+
+
+def bf16_round(a):
+    """Round float32 values to the nearest BF16 (ties to even), as float32."""
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    u = a.view(np.uint32).astype(np.uint64)
+    r = ((u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000).astype(np.uint32)
+    return r.view(np.float32)
+
+
+def random_params(seed, gain=1.0, bias=0.05):
+    """Seeded network parameters whose weights are exactly representable in
+    BF16, so that the tensor cores and the FP64 oracle use the same values."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for (r, c), nb in O.MLP_SHAPES:
+        out.append(rng.normal(0, gain / math.sqrt(c), size=(r, c)).ravel())
+        out.append(rng.normal(0, bias, size=nb))
+    return bf16_round(np.concatenate(out).astype(np.float32))

@@ -8,6 +8,7 @@ import numpy as np
 import pytest
 
 import oracle as O
+from tests.gpu_util import bf16_round, random_params
 import paper_1503_00707_gb300 as D
 
 pytestmark = pytest.mark.gpu
@@ -20,25 +21,6 @@ def gpu():
         pytest.skip("needs a CUDA GPU")
     from paper_1503_00707_gb300 import _build
     _build.build()
-
-
-def bf16_round(a):
-    """Round float32 values to the nearest BF16 (ties to even), as float32."""
-    a = np.ascontiguousarray(a, dtype=np.float32)
-    u = a.view(np.uint32).astype(np.uint64)
-    r = ((u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000).astype(np.uint32)
-    return r.view(np.float32)
-
-
-def random_params(seed, gain=1.0):
-    rng = np.random.default_rng(seed)
-    out = []
-    for (r, c), nb in O.MLP_SHAPES:
-        out.append(rng.normal(0, gain / math.sqrt(c), size=(r, c)).ravel())
-        out.append(rng.normal(0, 0.05, size=nb))
-    p = np.concatenate(out).astype(np.float32)
-    # weights exactly representable in BF16 so both sides use the same values
-    return bf16_round(p)
 
 
 def rel(a, b):
