@@ -252,12 +252,15 @@ int dvm_learned_train(dvm_ctx *ctx, const float *x, const float *t, int64_t n, i
  *   2. if Kn_loc < threshold: a_m = sum_i f_i H_m(c_i) dV / rho on the 64
  *      tensor Hermite modes H_m = He_a(c_x) He_b(c_y) He_c(c_z), a, b, c < 4
  *      (orthonormal probabilists' Hermite, m = 16a + 4b + c), with
- *      c = (xi - u)/sqrt(T); o = network(a);
+ *      c = (xi - u)/sqrt(T); o = network(a) - network(a_M), a_M the same
+ *      projection of the cell's Maxwellian M(rho, u, T) sampled at the
+ *      nodes (so that the term vanishes at equilibrium);
  *      Q_i = M_i (rho sqrt(T) sum_m o_m H_m(c_i) - sum_r d_r phi_r(c_i)),
  *      phi = (1, c, |c|^2 - 3), d such that Q carries no mass, momentum or
  *      energy (the correction form of Eq. 6, solved in FP64 and accepted
  *      only if its residual is below 1e-12 of the system's scale);
- *      accepted if sum_i Q_i ln f_i <= 0 (f_i <= 0 read as 1e-300):
+ *      accepted if sum_i Q_i ln f_i <= 1e-5 sum_i |Q_i| (entropy production
+ *      non-positive within its rounding; f_i <= 0 read as 1e-300):
  *      f += dt/Kn Q;
  *   3. every other cell: the hard-sphere update of Eqs. 3-6.
  * The paper has no learned operator; it is the network, gating and checks
@@ -268,10 +271,10 @@ int dvm_learned_configure(dvm_ctx *ctx, double kn_threshold);
 
 /* One learned collision update (no transport) of the stored f in place,
  * with its intermediate results: host arrays (each may be NULL) knl
- * [ncells] FP64, a and o [ncells][64], used [ncells] (1 = learned term
+ * [ncells] FP64, a and o [ncells][64] (o = network(a)), used [ncells] (1 = learned term
  * applied), q [ncells][nv] (the applied learned term; 0 in cells that fell
- * back).  o_in (host [ncells][64], may be NULL) replaces the network's
- * output.  Moments come from the stored f in FP64. */
+ * back).  o_in (host [ncells][64], may be NULL) replaces the network
+ * term o(a) - o(a_M).  Moments come from the stored f in FP64. */
 int dvm_learned_collide(dvm_ctx *ctx, double dt, const float *o_in, double *knl, float *a, float *o,
                         int32_t *used, float *q);
 

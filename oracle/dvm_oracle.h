@@ -135,10 +135,12 @@ int orc_mlp_backward(int64_t n, const double *params, const double *x, const dou
                      double *grad, double *loss);
 
 /* Learned collision update of the stored f: cells with Kn_loc < threshold
- * take I = rho sqrt(T) M sum_m o_m H_m (o = MLP(a)), made exactly
+ * take I = rho sqrt(T) M sum_m o_m H_m (o = MLP(a) - MLP(a_M), a_M the
+ * projection of the cell's Maxwellian sampled at the nodes), made exactly
  * conservative by subtracting M (c0 + c.g + c4 (|g|^2 - 3)) with the five
  * c solving the discrete moment system; a cell whose corrected term fails
- * the entropy check sum I ln f dV <= 0 falls back to the hard-sphere term
+ * the entropy check sum I ln f dV <= 1e-5 sum |I| dV (non-positive within
+ * the rounding of its evaluation) falls back to the hard-sphere term
  * (tables must be set).  used[c] = 1 where the learned term was applied.
  * f <- f + dt/Kn I. */
 int orc_learned_collide(orc_problem *p, double dt, double kn, const double *params,

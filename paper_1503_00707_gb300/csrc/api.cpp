@@ -263,8 +263,8 @@ int learned_prepare(dvm_ctx *c)
         c->d_kn_nb = dev_alloc_t<int32_t>(c, ne);
         c->d_kn_coef = dev_alloc_t<double>(c, 3 * ne);
         c->d_knl = dev_alloc_t<double>(c, (size_t)nc);
-        c->d_la = dev_alloc_t<float>(c, (size_t)nc * 64);
-        c->d_lo = dev_alloc_t<float>(c, (size_t)nc * 64);
+        c->d_la = dev_alloc_t<float>(c, (size_t)nc * 128);  // a, then a of the cells' Maxwellians
+        c->d_lo = dev_alloc_t<float>(c, (size_t)nc * 128);  // the network at both
         c->d_used = dev_alloc_t<int32_t>(c, (size_t)nc);
         c->d_list = dev_alloc_t<int32_t>(c, (size_t)nc);
         c->d_lcount = dev_alloc_t<int>(c, 4);
@@ -284,7 +284,7 @@ int learned_prepare(dvm_ctx *c)
     }
     int rc = DVM_OK;
     if (c->mlp_set) {
-        rc = dvm::mlp_reserve(c->mlp, nc, [c](size_t b) { return dev_alloc(c, b); }, [c](void *p) { void *q = p; dev_free(c, q); });
+        rc = dvm::mlp_reserve(c->mlp, 2 * nc, [c](size_t b) { return dev_alloc(c, b); }, [c](void *p) { void *q = p; dev_free(c, q); });
         if (rc) return fail(c, rc, "device allocation (network work buffers)");
     }
     rc = dvm::hs_prepare(c->hs, nc, [c](size_t b) { return dev_alloc(c, b); }, [c](void *q) { void *r = q; dev_free(c, r); });
@@ -314,15 +314,17 @@ int learned_collide_device(dvm_ctx *c, float *f, double *mom, double dt, const f
     int rc = dvm::launch_kn_local(mom, c->d_kn_start, c->d_kn_nb, c->d_kn_coef, nc, c->cfg.kn, c->d_knl, c->stream);
     if (!rc) rc = cuda_check(c, cudaMemsetAsync(c->d_lcount, 0, sizeof(int), c->stream), "reset fallback count");
     if (rc) return rc;
-    const float *o = o_in;
+    const float *o = o_in, *o_eq = nullptr;
     if (!o) {
+        // the network on a and on the projection of each cell's Maxwellian
         rc = dvm::launch_hermite_project(f, mom, c->d_amag, nc, c->n, c->dV, 0, nullptr, nullptr, c->d_la,
-                                         c->d_status, c->stream);
-        if (!rc) rc = dvm::mlp_forward(c->mlp, c->d_la, nc, c->d_lo, c->d_status, c->stream);
+                                         c->d_la + (size_t)nc * 64, c->d_status, c->stream);
+        if (!rc) rc = dvm::mlp_forward(c->mlp, c->d_la, 2 * nc, c->d_lo, c->d_status, c->stream);
         if (rc) return fail(c, rc, "projection or network launch failed");
         o = c->d_lo;
+        o_eq = c->d_lo + (size_t)nc * 64;
     }
-    rc = dvm::launch_learned_apply(f, mom, o, c->d_knl, c->kn_thr, c->d_amag, nc, c->n, dt / c->cfg.kn, c->d_used,
+    rc = dvm::launch_learned_apply(f, mom, o, o_eq, c->d_knl, c->kn_thr, c->d_amag, nc, c->n, dt / c->cfg.kn, c->d_used,
                                    c->d_list, c->d_lcount, q_out, c->d_status, c->stream);
     if (rc) return fail(c, rc, "learned collision launch failed");
     dvm::StepParams p = collision_params(c, mom);
@@ -1035,7 +1037,7 @@ int dvm_learned_collide(dvm_ctx *c, double dt, const float *o_in, double *knl, f
     if (o_in) rc = cuda_check(c, cudaMemcpyAsync(c->d_lo, o_in, (size_t)nc * 256, cudaMemcpyHostToDevice, c->stream), "copy o");
     if (!rc && o_in && a)
         rc = dvm::launch_hermite_project(f, c->d_mom2, c->d_amag, nc, c->n, c->dV, 0, nullptr, nullptr, c->d_la,
-                                         c->d_status, c->stream);
+                                         nullptr, c->d_status, c->stream);
     if (rc) return fail(c, rc, "projection launch failed");
     DevArr dq(c, q ? (size_t)nc * c->nv * 4 : 16);
     if (!dq.p) return fail(c, DVM_ENOMEM, "device allocation (collision term)");
@@ -1068,11 +1070,11 @@ int dvm_learned_pairs(dvm_ctx *c, float *a, float *o)
     float *f = static_cast<float *>(c->d_f[c->cur]);
     rc = dvm::launch_moments(DVM_F32, f, nc, c->nv, c->d_xi, c->dV, c->d_mom2, c->stream);
     if (!rc) rc = dvm::launch_hermite_project(f, c->d_mom2, c->d_amag, nc, c->n, c->dV, 0, nullptr, nullptr, da.f(),
-                                              c->d_status, c->stream);
+                                              nullptr, c->d_status, c->stream);
     dvm::StepParams p = collision_params(c, c->d_mom2);
     if (!rc) rc = dvm::launch_hs_general(c->hs, p, f, nullptr, nullptr, dq.f(), c->cfg.kn, 0.0);
     if (!rc) rc = dvm::launch_hermite_project(dq.f(), c->d_mom2, c->d_amag, nc, c->n, c->dV, 1, nullptr, nullptr,
-                                              dout.f(), c->d_status, c->stream);
+                                              dout.f(), nullptr, c->d_status, c->stream);
     if (rc) return fail(c, rc, "training-pair launch failed");
     rc = read_status(c, "training pairs");
     if (!rc) rc = cuda_check(c, cudaMemcpy(a, da.p, (size_t)nc * 256, cudaMemcpyDeviceToHost), "copy a");

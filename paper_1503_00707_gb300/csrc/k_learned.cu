@@ -10,12 +10,16 @@
 //             projection on the 64 tensor Hermite modes H_m = He_a He_b He_c
 //             (orthonormal probabilists' Hermite, a, b, c < 4) in the
 //             Maxwellian-normalised velocity c = (xi - u)/sqrt(T);
+//             Mode 0 also gives the projection of the cell's own discrete
+//             Maxwellian M(rho, u, T), whose network output is subtracted
+//             below so that the learned term vanishes at equilibrium;
 //   k_lapply  Q_i = M_i (rho sqrt(T) sum_m o_m H_m(c_i) - d.phi_i), with the
 //             five coefficients d of the centred basis phi = (1, c, |c|^2 - 3)
 //             chosen so that Q carries no mass, momentum or energy (the
 //             correction form of Eq. 6 applied to the reconstructed term);
-//             the cell keeps f + dt/Kn Q only if sum Q ln f <= 0 (entropy)
-//             and the 5x5 solve is exact to its residual, else it joins the
+//             the cell keeps f + dt/Kn Q only if sum Q ln f <= 1e-5 sum |Q|
+//             (entropy production non-positive within rounding) and the 5x5
+//             solve is exact to its residual, else it joins the
 //             list of cells left to the hard-sphere operator.
 //
 // Velocity nodes come in the step kernel's group layout: node (ix, iy, iz)
@@ -143,11 +147,12 @@ template <int MODE>
 __global__ void __launch_bounds__(PT) k_proj(const float *__restrict__ f, const double *__restrict__ mom,
                                              const double *__restrict__ amag, int3 n, double dV,
                                              const int32_t *__restrict__ list, const int *__restrict__ count,
-                                             float *__restrict__ out, int *status)
+                                             float *__restrict__ out, float *__restrict__ out_eq, int *status)
 {
     extern __shared__ __align__(128) float tile[];  // [nv]
     __shared__ float4 H[3][MAXN];
     __shared__ float red[PT / 32][64];
+    __shared__ float gsum[3][4];
     __shared__ __align__(8) uint64_t bar;
     __shared__ int abort_flag;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -171,7 +176,19 @@ __global__ void __launch_bounds__(PT) k_proj(const float *__restrict__ f, const 
     const float u[3] = {(float)mo[1], (float)mo[2], (float)mo[3]};
     const float ist = T > 0.0 ? (float)(1.0 / sqrt(T)) : 0.0f;
     axis_tables(amag, n, u, ist, H, nullptr, tid, PT);
-    if (!tile_arrived(&bar, &abort_flag, status)) return;
+    if (!tile_arrived(&bar, &abort_flag, status)) return;  // includes a barrier
+    if (out_eq && tid < 12) {
+        // per-axis sums sum_i exp(-c_i^2/2) He_a(c_i) for the projection of the
+        // cell's own discrete Maxwellian
+        const int d = tid >> 2, a = tid & 3;
+        const int nd = d == 0 ? n.x : (d == 1 ? n.y : n.z);
+        float sacc = 0.0f;
+        for (int i = 0; i < nd; i++) {
+            const float4 h = H[d][i];
+            sacc = fmaf(h.w, a == 0 ? 1.0f : (a == 1 ? h.x : (a == 2 ? h.y : h.z)), sacc);
+        }
+        gsum[d][a] = sacc;
+    }
 
     float acc[64];
 #pragma unroll
@@ -221,12 +238,20 @@ __global__ void __launch_bounds__(PT) k_proj(const float *__restrict__ f, const 
         for (int w = 0; w < PT / 32; w++) s += red[w][tid];
         const double scale = MODE == 0 ? dV / rho : dV / (rho * rho * sqrt(T));
         out[row * 64 + tid] = (float)((double)s * scale);
+        if (out_eq) {
+            // a of M(rho, u, T) sampled at the nodes: dV (2 pi T)^(-3/2) times
+            // the product of per-axis sums
+            const double pre = dV * 0.06349363593424097 / (T * sqrt(T));
+            out_eq[row * 64 + tid] = (float)(pre * (double)gsum[0][tid >> 4] * (double)gsum[1][(tid >> 2) & 3] *
+                                             (double)gsum[2][tid & 3]);
+        }
     }
 }
 
 // ---------------------------------------------------------------- apply
 __global__ void __launch_bounds__(AT) k_lapply(float *__restrict__ f, const double *__restrict__ mom,
-                                               const float *__restrict__ o, const double *__restrict__ knl,
+                                               const float *__restrict__ o, const float *__restrict__ o_eq,
+                                               const double *__restrict__ knl,
                                                double thr, const double *__restrict__ amag, int3 n, float dtkn,
                                                int32_t *__restrict__ used, int32_t *__restrict__ list,
                                                int *__restrict__ count, float *__restrict__ q_out, int *status)
@@ -240,7 +265,7 @@ __global__ void __launch_bounds__(AT) k_lapply(float *__restrict__ f, const doub
     __shared__ float sums[3][14];
     __shared__ float rred[2][5];
     __shared__ double cc[5];
-    __shared__ double ered[AT / 32];
+    __shared__ double ered[AT / 32], qred[AT / 32];
     __shared__ int good;
     __shared__ __align__(8) uint64_t bar;
     __shared__ int abort_flag;
@@ -277,7 +302,7 @@ __global__ void __launch_bounds__(AT) k_lapply(float *__restrict__ f, const doub
     const float ist = (float)(1.0 / sq);
     const double Mc = valid ? rho * 0.06349363593424097 / (T * sq) : 1.0;  // rho (2 pi T)^(-3/2)
     const float Mcf = (float)Mc, lnMc = (float)log(Mc), rsq = (float)(rho * sq);
-    if (tid < 64) os[tid] = o[cell * 64 + tid];
+    if (tid < 64) os[tid] = o[cell * 64 + tid] - (o_eq ? o_eq[cell * 64 + tid] : 0.0f);
     axis_tables(amag, n, u, ist, H, G, tid, AT);
     __syncthreads();
     const int nz = n.z;
@@ -436,7 +461,7 @@ __global__ void __launch_bounds__(AT) k_lapply(float *__restrict__ f, const doub
             }
         }
     };
-    float ent = 0.0f;
+    float ent = 0.0f, qabs = 0.0f;
     if (good) {
         for (int pp = tid; pp < n.x * n.y; pp += AT)
             pencil(pp, [&](float4 *, const float (&fv)[4], const float (&Q)[4], const float (&lnM)[4], int) {
@@ -446,18 +471,31 @@ __global__ void __launch_bounds__(AT) k_lapply(float *__restrict__ f, const doub
                     // ln f, with ln(1e-300) standing in for f <= 0
                     const float lf = x >= 1.17549435e-38f ? __logf(x) : (x > 0.0f ? logf(x) : -690.77552789821f);
                     ent = fmaf(Q[e], lf - lnM[e], ent);
+                    qabs += fabsf(Q[e]);
                 }
             });
     }
-    double e64 = (double)ent;
+    double e64 = (double)ent, q64 = (double)qabs;
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) e64 += __shfl_xor_sync(0xffffffffu, e64, off);
-    if (lane == 0) ered[warp] = e64;
+    for (int off = 16; off > 0; off >>= 1) {
+        e64 += __shfl_xor_sync(0xffffffffu, e64, off);
+        q64 += __shfl_xor_sync(0xffffffffu, q64, off);
+    }
+    if (lane == 0) {
+        ered[warp] = e64;
+        qred[warp] = q64;
+    }
     __syncthreads();
     if (tid == 0) {
-        double s = 0.0;
-        for (int w = 0; w < AT / 32; w++) s += ered[w];
-        good = good && isfinite(s) && s <= 0.0;
+        double s = 0.0, sa = 0.0;
+        for (int w = 0; w < AT / 32; w++) {
+            s += ered[w];
+            sa += qred[w];
+        }
+        // entropy production non-positive within the rounding of its FP32
+        // evaluation (an equilibrium cell, where it is zero up to rounding,
+        // passes)
+        good = good && isfinite(s) && s <= 1e-5 * sa;
     }
     __syncthreads();
     if (!good) {
@@ -505,8 +543,8 @@ int launch_kn_local(const double *mom, const int32_t *start, const int32_t *nb, 
 }
 
 int launch_hermite_project(const float *f, const double *mom, const double *amag, int64_t rows, const int n[3],
-                           double dV, int mode, const int32_t *list, const int *count, float *out, int *status,
-                           cudaStream_t s)
+                           double dV, int mode, const int32_t *list, const int *count, float *out, float *out_eq,
+                           int *status, cudaStream_t s)
 {
     if (!grid_ok(n)) return DVM_ENOTIMPL;
     if (rows <= 0) return DVM_OK;
@@ -516,12 +554,12 @@ int launch_hermite_project(const float *f, const double *mom, const double *amag
     auto kern = mode == 0 ? k_proj<0> : k_proj<1>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) != cudaSuccess)
         return DVM_ECUDA;
-    kern<<<(unsigned)rows, PT, dyn, s>>>(f, mom, amag, nn, dV, list, count, out, status);
+    kern<<<(unsigned)rows, PT, dyn, s>>>(f, mom, amag, nn, dV, list, count, out, mode == 0 ? out_eq : nullptr, status);
     count_launch();
     return cudaGetLastError() == cudaSuccess ? DVM_OK : DVM_ECUDA;
 }
 
-int launch_learned_apply(float *f, const double *mom, const float *o, const double *knl, double thr,
+int launch_learned_apply(float *f, const double *mom, const float *o, const float *o_eq, const double *knl, double thr,
                          const double *amag, int64_t ncells, const int n[3], double dtkn, int32_t *used,
                          int32_t *list, int *count, float *q_out, int *status, cudaStream_t s)
 {
@@ -531,7 +569,7 @@ int launch_learned_apply(float *f, const double *mom, const float *o, const doub
     if (dyn > 200 * 1024) return DVM_ENOTIMPL;
     if (cudaFuncSetAttribute(k_lapply, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) != cudaSuccess)
         return DVM_ECUDA;
-    k_lapply<<<(unsigned)ncells, AT, dyn, s>>>(f, mom, o, knl, thr, amag, make_int3(n[0], n[1], n[2]), (float)dtkn,
+    k_lapply<<<(unsigned)ncells, AT, dyn, s>>>(f, mom, o, o_eq, knl, thr, amag, make_int3(n[0], n[1], n[2]), (float)dtkn,
                                                 used, list, count, q_out, status);
     count_launch();
     return cudaGetLastError() == cudaSuccess ? DVM_OK : DVM_ECUDA;

@@ -33,17 +33,21 @@ int launch_kn_local(const double *mom, const int32_t *start, const int32_t *nb, 
 // order): mode 0 gives a_m = sum f H_m dV / rho, mode 1 gives
 // o_m = sum f H_m dV / (rho^2 sqrt(T)), with (rho, u, T) of the row's cell
 // from mom.  With list != NULL, row r is cell list[r] for r < *count (the
-// launch covers `rows` rows, those beyond *count do nothing).
+// launch covers `rows` rows, those beyond *count do nothing).  In mode 0,
+// out_eq (optional) receives a of the cell's Maxwellian M(rho, u, T)
+// sampled at the nodes.
 int launch_hermite_project(const float *f, const double *mom, const double *amag, int64_t rows, const int n[3],
-                           double dV, int mode, const int32_t *list, const int *count, float *out, int *status,
-                           cudaStream_t s);
+                           double dV, int mode, const int32_t *list, const int *count, float *out, float *out_eq,
+                           int *status, cudaStream_t s);
 
 // Learned collision on f in place for every cell with knl < thr whose
-// corrected term passes the checks: f += dtkn * Q.  used[c] = 1 there;
+// corrected term passes the checks: f += dtkn * Q, Q reconstructed from
+// o - o_eq (o_eq optional: the network at the cell's Maxwellian).
+// used[c] = 1 there;
 // every other cell gets used[c] = 0 and is appended to list (*count, which
 // must start at 0, counts them).  q_out (optional, [ncells][nv]) receives Q
 // of the cells that used it.
-int launch_learned_apply(float *f, const double *mom, const float *o, const double *knl, double thr,
+int launch_learned_apply(float *f, const double *mom, const float *o, const float *o_eq, const double *knl, double thr,
                          const double *amag, int64_t ncells, const int n[3], double dtkn, int32_t *used,
                          int32_t *list, int *count, float *q_out, int *status, cudaStream_t s);
 
