@@ -296,8 +296,9 @@ int dvm_learned_fallback_count(dvm_ctx *ctx, int64_t *n);
  * dvm_step, without transport) on caller-owned device memory, allocating
  * nothing.  The paper has no counterpart: this entry point is for callers
  * that must not allocate device memory while they run, such as a framework
- * that owns all device memory through its own pool, code that records
- * work into a CUDA graph, or a real-time loop sized once at start-up.
+ * that owns all device memory through its own pool and hands plug-ins only
+ * buffers it allocated, or a real-time loop whose memory is sized once at
+ * start-up and may not grow afterwards.
  *   f       device pointer, FP32 [ncells][nv] in the library's velocity
  *           order, read and written in place (owned by the caller);
  *   ncells  number of cells in f; needs ncells * (8 nv + 40) bytes of

@@ -25,6 +25,12 @@ __device__ inline void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
                  : "memory");
 }
 
+// plain arrival (no transaction bytes)
+__device__ inline void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
 __device__ inline void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
 {
     asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
@@ -53,6 +59,41 @@ __device__ inline bool mbar_wait(uint64_t *bar, uint32_t parity)
     for (uint32_t t = 0; t < WAIT_POLLS; t++) {
         if (mbar_try_wait(bar, parity)) return true;
         if (t > 32) __nanosleep(128);
+    }
+    return false;
+}
+
+__device__ inline uint64_t global_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// One wait that suspends the thread until the phase completes or about
+// 20 us pass, so that waiting warps leave the issue slots to the others.
+__device__ inline bool mbar_try_wait_suspend(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(20000u)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded suspending wait: gives up after about a second of global time
+// (or 2^20 tries, whichever comes first).
+__device__ inline bool mbar_wait_suspend(uint64_t *bar, uint32_t parity)
+{
+    if (mbar_try_wait_suspend(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    for (uint32_t t = 0; t < (1u << 20); t++) {
+        if (mbar_try_wait_suspend(bar, parity)) return true;
+        if (global_ns() - t0 > 1000000000ull) break;
     }
     return false;
 }

@@ -187,6 +187,51 @@ __device__ inline bool solve5(const T A[25], const T b[5], T x[5])
     return true;
 }
 
+// The same LDL^T solve with one reciprocal per pivot in place of the ten
+// divisions (FP32: correctly rounded reciprocal, so each quotient carries one
+// more rounding than a division would).
+__device__ inline float rcp_rn(float d) { return __frcp_rn(d); }
+__device__ inline double rcp_rn(double d) { return 1.0 / d; }
+
+template <typename T>
+__device__ inline bool solve5_rcp(const T A[25], const T b[5], T x[5])
+{
+    T L[5][5], D[5], Di[5];
+#pragma unroll
+    for (int j = 0; j < 5; j++) {
+        T d = A[j * 5 + j];
+#pragma unroll
+        for (int k = 0; k < j; k++) d -= L[j][k] * L[j][k] * D[k];
+        if (!(d > (T)0) || !isfinite(d)) return false;
+        D[j] = d;
+        Di[j] = rcp_rn(d);
+#pragma unroll
+        for (int i = j + 1; i < 5; i++) {
+            T s = A[i * 5 + j];
+#pragma unroll
+            for (int k = 0; k < j; k++) s -= L[i][k] * L[j][k] * D[k];
+            L[i][j] = s * Di[j];
+        }
+    }
+    T y[5];
+#pragma unroll
+    for (int i = 0; i < 5; i++) {
+        T s = b[i];
+#pragma unroll
+        for (int k = 0; k < i; k++) s -= L[i][k] * y[k];
+        y[i] = s;
+    }
+#pragma unroll
+    for (int i = 4; i >= 0; i--) {
+        T s = y[i] * Di[i];
+#pragma unroll
+        for (int k = i + 1; k < 5; k++) s -= L[k][i] * x[k];
+        x[i] = s;
+        if (!isfinite(s)) return false;
+    }
+    return true;
+}
+
 }  // namespace dvm
 
 namespace dvm {
@@ -251,6 +296,17 @@ template <> struct Num<float> {
     {
         return {__shfl_xor_sync(0xffffffffu, v.hi, m), __shfl_xor_sync(0xffffffffu, v.lo, m)};
     }
+    __device__ static inline X shfl(X v, int src)
+    {
+        return {__shfl_sync(0xffffffffu, v.hi, src), __shfl_sync(0xffffffffu, v.lo, src)};
+    }
+    // 1/v: FP32 reciprocal refined by one Newton step in double-float
+    __device__ static inline X recip(X v)
+    {
+        const float y = __frcp_rn(v.hi);
+        const ffn e = ffn{1.0f, 0.0f} - v * y;
+        return ffn_norm(y, y * e.hi);
+    }
     // 1/sqrt(v): FP32 estimate refined by one Newton step in double-float
     __device__ static inline X rsqrt(X v)
     {
@@ -268,6 +324,8 @@ template <> struct Num<double> {
     __device__ static inline float f(X v) { return (float)v; }
     __device__ static inline bool finite_pos(X v) { return isfinite(v) && v > 0.0; }
     __device__ static inline X shfl_xor(X v, int m) { return __shfl_xor_sync(0xffffffffu, v, m); }
+    __device__ static inline X shfl(X v, int src) { return __shfl_sync(0xffffffffu, v, src); }
+    __device__ static inline X recip(X v) { return 1.0 / v; }
     __device__ static inline X rsqrt(X v) { return 1.0 / sqrt(v); }
 };
 

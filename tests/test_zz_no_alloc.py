@@ -2,7 +2,8 @@
 
 dvm_hs_collide_noalloc serves callers that must not allocate device memory
 while they run (a framework that owns all device memory through its own
-pool, work recorded into a CUDA graph, a real-time loop sized at start-up):
+pool and hands plug-ins only its buffers, a real-time loop whose memory is
+sized once at start-up):
 its scratch is a fixed array in the library's device image.  On a spatially
 uniform periodic state the transport of Eq. 2 leaves f unchanged bit for bit,
 so one dvm_step is exactly the collision update; the allocation-free call on a
