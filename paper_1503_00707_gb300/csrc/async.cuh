@@ -98,6 +98,29 @@ __device__ inline bool mbar_wait_suspend(uint64_t *bar, uint32_t parity)
     return false;
 }
 
+// Per-thread asynchronous copies global -> shared (cp.async, the L1TEX path),
+// completed by commit groups.  `dep` is an unused operand that makes the copy
+// wait until the value it names has been computed: passing a result derived
+// from the last read of the destination orders that read before the refill.
+__device__ inline void cp_async16(void *dst, const void *src, uint32_t dep)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16; // %2" ::"r"(smem_u32(dst)), "l"(src), "r"(dep)
+                 : "memory");
+}
+__device__ inline void cp_async8(void *dst, const void *src, uint32_t dep)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8; // %2" ::"r"(smem_u32(dst)), "l"(src), "r"(dep)
+                 : "memory");
+}
+// Bulk prefetch of [src, src + bytes) into L2 (bytes a multiple of 16).
+__device__ inline void prefetch_l2_bulk(const void *src, uint32_t bytes)
+{
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
+__device__ inline void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N> __device__ inline void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+__device__ inline void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 }  // namespace dvm
 
 namespace dvm {

@@ -68,9 +68,9 @@ namespace {
 
 constexpr int MAXCW = 14;     // compute warps per CTA (at most)
 constexpr int NAX = 32;       // velocity nodes per axis supported
-constexpr int MAXT = MAXCW * 32 + 64;
+constexpr int MAXT = MAXCW * 32 + 32;
 constexpr int MAXSTAGE = 8;   // ring stages (one sign group of one cell each)
-constexpr int NSL = 4;        // ring of per-cell stencil slots
+constexpr int NSL = 8;        // ring of per-cell stencil slots (dispatched three iterations ahead)
 
 template <typename TC> __device__ inline TC tc_exp(TC x);
 template <> __device__ inline float tc_exp<float>(float x) { return expf(x); }
@@ -186,12 +186,14 @@ template <typename TC> struct TabE {
     TC g, p;
 };
 
-// coefficient decision published by the solver with each cell's coefficients
-enum { DEC_GO = 0, DEC_END = 1, DEC_STOP = 2 };
+// decision published by the solver with each cell's coefficients
+enum { DEC_GO = 0, DEC_END = 1 };
 
-// One cell's stencil as the producer hands it to the compute warps.
+// One cell's stencil, as the dispatching solver warp hands it to the
+// compute warps three iterations ahead.
 template <typename TC> struct CellSlot {
     long long cell;      // -1: no cell left
+    long long soff[6];   // element offset of each list's first source, wall flip folded in
     int32_t src[24];     // per list (axis x side) up to 4 sources: cell | group flip << 28
     TC w[24];            // A_k / V_j
     int cnt[6];
@@ -202,14 +204,12 @@ template <typename TC> struct CellSlot {
 template <typename TC> struct StepSmem {
     CellSlot<TC> slot[NSL];
     TC red[2][MAXCW][7];
-    long long cellp[2];    // cell of the partials in red (-1: none, -2: a wait gave up)
+    long long cellp[2];    // cell of the partials in red (-1: none)
     TabE<TC> tab[2][3][NAX];
     TC coef[2][CF_N];
     typename Num<TC>::X mom[2][5];  // rho, u, T of the cell in slot b
     int ok[2];
     int dec[2];
-    int abort_flag;
-    uint64_t full[MAXSTAGE], empty[MAXSTAGE];
 };
 
 template <typename TC> struct Consts {
@@ -239,6 +239,19 @@ constexpr int BAR_P = 1, BAR_C = 3;
 
 template <typename TS, int DIM> constexpr uint32_t stage_bytes(int P) { return (uint32_t)((1 + DIM) * P * sizeof(TS)); }
 
+// the 16- or 8-byte piece of one thread
+template <typename TS> __device__ inline void cp_piece(TS *dst, const TS *src, uint32_t dep)
+{
+    if constexpr (sizeof(TS) == 2) cp_async8(dst, src, dep);
+    else cp_async16(dst, src, dep);
+}
+
+template <typename T> __device__ inline uint32_t dep_of(const QV<T> &q)
+{
+    if constexpr (sizeof(T) == 8) return (uint32_t)__double2loint(q.a);
+    else return __float_as_uint(q.a.x);
+}
+
 // ---------------------------------------------------------------- solver
 // Phase 2 of one cell on one warp: moments of f* from the compute warps'
 // partials, the conservatively corrected Maxwellian's coefficients and
@@ -248,7 +261,7 @@ template <typename TS, int DIM> constexpr uint32_t stage_bytes(int P) { return (
 // would be fetched from beyond the instruction cache every time.
 template <typename TC, int COLL>
 __device__ inline int solve_cell(const StepParams &p, StepSmem<TC> &sm, const Consts<TC> &K, int b, int ncw,
-                                 long long cell, const TC (&xil)[3])
+                                 long long cell, const TC (&xi4)[4])
 {
     using N = Num<TC>;
     using X = typename N::X;
@@ -286,33 +299,47 @@ __device__ inline int solve_cell(const StepParams &p, StepSmem<TC> &sm, const Co
         const X isT = N::rsqrt(T);
         const TC isTt = N::tc(isT);
         const X Kc = rho * K.c15 * isT * isT * isT;  // rho (2 pi T)^(-3/2)
-        // lane i: node i of each axis, c = (xi - u)/sqrt(T), g = exp(-c^2/2);
-        // 1D sums of g c^k, k = 0..4 (k = 0, 2 in double-float)
+        // 1D sums of g c^k, k = 0..4 (k = 0, 2 in double-float), with
+        // c = (xi - u)/sqrt(T), g = exp(-c^2/2): lanes 8d .. 8d + 7 take
+        // axis d, lane 8d + s the nodes s, s + 8, s + 16, s + 24; the eight
+        // lanes of an axis then combine in three butterfly levels
+        const int ax = lane >> 3, sub = lane & 7;
+        const TC ud = ax == 0 ? uT[0] : (ax == 1 ? uT[1] : uT[2]);
+        const int nax = ax < 3 ? p.n[ax] : 0;
+        X A0 = N::make((TC)0), A2 = N::make((TC)0);
+        TC A1 = 0, A3 = 0, A4 = 0, cl[4], gl[4];
+#pragma unroll
+        for (int t = 0; t < 4; t++) {
+            cl[t] = 0;
+            gl[t] = 0;
+            if (sub + 8 * t < nax) {
+                cl[t] = (xi4[t] - ud) * isTt;
+                gl[t] = tc_exp<TC>((TC)-0.5 * cl[t] * cl[t]);
+            }
+            const TC gc = gl[t] * cl[t];
+            A0 = A0 + N::make(gl[t]);
+            A2 = A2 + N::make(gc) * cl[t];
+            A1 += gc;
+            A3 += gc * cl[t] * cl[t];
+            A4 += gc * cl[t] * cl[t] * cl[t];
+        }
+#pragma unroll
+        for (int m = 4; m > 0; m >>= 1) {
+            A0 = A0 + N::shfl_xor(A0, m);
+            A2 = A2 + N::shfl_xor(A2, m);
+            A1 += __shfl_xor_sync(0xffffffffu, A1, m);
+            A3 += __shfl_xor_sync(0xffffffffu, A3, m);
+            A4 += __shfl_xor_sync(0xffffffffu, A4, m);
+        }
         X G0[3], G2[3];
-        TC G1[3], G3[3], G4[3], cl[3], gl[3];
+        TC G1[3], G3[3], G4[3];
 #pragma unroll
         for (int d = 0; d < 3; d++) {
-            cl[d] = 0; gl[d] = 0;
-            if (lane < p.n[d]) {
-                cl[d] = (xil[d] - uT[d]) * isTt;
-                gl[d] = tc_exp<TC>((TC)-0.5 * cl[d] * cl[d]);
-            }
-            G0[d] = N::make(gl[d]);
-            G2[d] = N::make(gl[d]) * cl[d] * cl[d];
-            G1[d] = gl[d] * cl[d];
-            G3[d] = G1[d] * cl[d] * cl[d];
-            G4[d] = G3[d] * cl[d];
-        }
-#pragma unroll 1
-        for (int m = 16; m > 0; m >>= 1) {
-#pragma unroll
-            for (int d = 0; d < 3; d++) {
-                G0[d] = G0[d] + N::shfl_xor(G0[d], m);
-                G2[d] = G2[d] + N::shfl_xor(G2[d], m);
-                G1[d] += __shfl_xor_sync(0xffffffffu, G1[d], m);
-                G3[d] += __shfl_xor_sync(0xffffffffu, G3[d], m);
-                G4[d] += __shfl_xor_sync(0xffffffffu, G4[d], m);
-            }
+            G0[d] = N::shfl(A0, 8 * d);
+            G2[d] = N::shfl(A2, 8 * d);
+            G1[d] = __shfl_sync(0xffffffffu, A1, 8 * d);
+            G3[d] = __shfl_sync(0xffffffffu, A3, 8 * d);
+            G4[d] = __shfl_sync(0xffffffffu, A4, 8 * d);
         }
         const X KdV = Kc * K.dV;
         if (lane == 0) {
@@ -370,11 +397,14 @@ __device__ inline int solve_cell(const StepParams &p, StepSmem<TC> &sm, const Co
             cf[CF_D4] = dd[4];
         }
         __syncwarp();
-        // per-axis factors of the corrected Maxwellian
+        // per-axis factors of the corrected Maxwellian, each lane for its nodes
         const TC d4 = sm.coef[b][CF_D4];
+        if (ax < 3) {
+            const TC da = sm.coef[b][CF_DX + ax];
 #pragma unroll
-        for (int d = 0; d < 3; d++)
-            if (lane < p.n[d]) sm.tab[b][d][lane] = TabE<TC>{gl[d], cl[d] * (sm.coef[b][CF_DX + d] + d4 * cl[d])};
+            for (int t = 0; t < 4; t++)
+                if (sub + 8 * t < nax) sm.tab[b][ax][sub + 8 * t] = TabE<TC>{gl[t], cl[t] * (da + d4 * cl[t])};
+        }
     }
     if (lane == 0) {
         sm.mom[b][0] = rho;
@@ -401,138 +431,125 @@ __global__ void __launch_bounds__(MAXT, 1) k_step(const StepParams p, const int 
     TS *ring = reinterpret_cast<TS *>(dsm);  // [stages][1 + DIM][P]
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int ncw = (blockDim.x >> 5) - 2;  // compute warps; then the solver and the producer
-    const int nbar = (ncw + 1) * 32;        // threads on the named barriers
+    const int ncw = (blockDim.x >> 5) - 1;  // compute warps; the last warp solves and dispatches
+    const int nbar = blockDim.x;            // threads on the named barriers
     const int Q = p.P / VEC;
-    const uint32_t chunk = (uint32_t)p.P * (uint32_t)sizeof(TS);
-    const uint32_t sbytes = chunk * (1 + DIM);
+    const int stages = 1 << lgs;            // 8, 4 or 2 sign groups in flight
     const TS *__restrict__ fin = static_cast<const TS *>(p.f_in);
     TS *__restrict__ fout = static_cast<TS *>(p.f_out);
-    // ring of 2^lgs stages: fill g goes to stage g & smask, in its phase g >> lgs
-    const int stages = 1 << lgs, smask = stages - 1;
-    auto stage_of = [&](int g) { return ring + (size_t)(g & smask) * (1 + DIM) * p.P; };
 
-    if (tid == 0) {
-        for (int s = 0; s < MAXSTAGE; s++) {
-            mbar_init(&sm.full[s], 1);
-            mbar_init(&sm.empty[s], (uint32_t)ncw);
+    // cell dispatch (one warp): a cell index from the global counter (the
+    // cells in flight on the whole GPU form one contiguous Morton window),
+    // its stencil fetched into registers, then stored into a slot; split so
+    // that the solver can overlap the loads with its own work
+    struct Sten {
+        long long cell;
+        int32_t src;
+        TC w;
+        int cnt;
+        long long soff;
+        TC invh;
+    };
+    // A taken cell's own f (streamed from HBM) is prefetched into L2 at once,
+    // three iterations before its copy into shared memory, so that the copy
+    // meets L2 latency rather than loaded HBM latency.
+    auto take = [&]() -> long long {
+        long long cell = -1;
+        if (lane == 0) {
+            const unsigned long long c = atomicAdd(p.counter, 1ull);
+            cell = c < (unsigned long long)p.ncells ? (long long)c : -1;
+            if (cell >= 0) prefetch_l2_bulk(fin + cell * p.nv, (uint32_t)(p.nv * sizeof(TS)));
         }
-        sm.abort_flag = 0;
-        K.dV = split<TC>(p.dV);
-        for (int d = 0; d < 3; d++) {
-            K.hh[d] = split<TC>(0.5 * p.hv[d]);
-            K.hh2[d] = split<TC>(0.25 * p.hv[d] * p.hv[d]);
+        return __shfl_sync(0xffffffffu, cell, 0);
+    };
+    auto fetch = [&](long long cell) {
+        Sten t{cell, 0, (TC)0, 0, 0, (TC)0};
+        if (cell >= 0) {
+            if (lane < 24) {
+                t.src = p.st_src[cell * 24 + lane];
+                t.w = static_cast<const TC *>(p.st_w)[cell * 24 + lane];
+            }
+            if (lane < 6) {
+                t.cnt = p.st_cnt[cell * 8 + lane];
+                // group o reads source group o ^ flip = o -/+ flip for the minus/plus list
+                const int32_t first = p.st_src[cell * 24 + lane * 4];
+                const long long flip = first >> 28;
+                t.soff = (long long)(first & 0x0fffffff) * p.nv + ((lane & 1) ? flip : -flip) * p.P;
+            }
+            if (lane == 0) t.invh = static_cast<const TC *>(p.inv_h)[cell];
         }
-        K.third = split<TC>(1.0 / 3.0);
-        K.c15 = split<TC>(0.06349363593424097);  // (2 pi)^(-3/2)
-        K.one = split<TC>(1.0);
-        K.nu0 = (TC)(1.5957691216057308 * p.dt / p.kn);
-        mbar_fence_init();
+        return t;
+    };
+    auto store = [&](const Sten &t, int k) {
+        CellSlot<TC> &sl = sm.slot[k % NSL];
+        if (t.cell >= 0) {
+            if (lane < 24) {
+                sl.src[lane] = t.src;
+                sl.w[lane] = t.w;
+            }
+            if (lane < 6) {
+                sl.cnt[lane] = t.cnt;
+                sl.soff[lane] = t.soff;
+            }
+            const unsigned xm = __ballot_sync(0xffffffffu, lane < 6 && t.cnt > 1);
+            if (lane == 0) {
+                sl.xmask = (int)xm;
+                sl.invh = t.invh;
+            }
+        }
+        if (lane == 0) sl.cell = t.cell;
+    };
+    long long next_cell = -1;   // solver warp: the cell of slot j + 3, taken one iteration early
+
+    if (warp == ncw) {
+        // cells of iterations 0..2, and the one of iteration 3
+        for (int k = 0; k < 3; k++) store(fetch(take()), k);
+        next_cell = take();
+        if (lane == 0) {
+            K.dV = split<TC>(p.dV);
+            for (int d = 0; d < 3; d++) {
+                K.hh[d] = split<TC>(0.5 * p.hv[d]);
+                K.hh2[d] = split<TC>(0.25 * p.hv[d] * p.hv[d]);
+            }
+            K.third = split<TC>(1.0 / 3.0);
+            K.c15 = split<TC>(0.06349363593424097);  // (2 pi)^(-3/2)
+            K.one = split<TC>(1.0);
+            K.nu0 = (TC)(1.5957691216057308 * p.dt / p.kn);
+        }
     }
     __syncthreads();
-    volatile int *abort_flag = &sm.abort_flag;
 
-    if (warp == ncw + 1) {
-        // ================= producer
-        int issued = 0;  // fills issued so far
-        bool ok = true;
-        for (int j = 0;; j++) {
-            long long cell = -1;
-            if (lane == 0) {
-                const unsigned long long c = atomicAdd(p.counter, 1ull);
-                cell = c < (unsigned long long)p.ncells ? (long long)c : -1;
-            }
-            cell = __shfl_sync(0xffffffffu, cell, 0);
-            CellSlot<TC> &sl = sm.slot[j % NSL];
-            long long soff = 0;  // lane L < 2 DIM: element offset of list L's first source
-            for (int o = 0; o < 8; o++) {
-                const int g = 8 * j + o;
-                if (*abort_flag) ok = false;
-                if (ok && g >= stages && !mbar_wait_suspend(&sm.empty[(g & smask)], (uint32_t)(((g >> lgs) - 1) & 1)))
-                    ok = false;
-                if (!ok) break;
-                if (o == 0) {
-                    // the slot of iteration j - NSL is free: the compute warps
-                    // released a stage of iteration j - 1 or later
-                    if (cell >= 0) {
-                        if (lane < 24) {
-                            sl.src[lane] = p.st_src[cell * 24 + lane];
-                            sl.w[lane] = static_cast<const TC *>(p.st_w)[cell * 24 + lane];
-                        }
-                        int cnt = 0;
-                        if (lane < 6) {
-                            cnt = p.st_cnt[cell * 8 + lane];
-                            sl.cnt[lane] = cnt;
-                        }
-                        const int32_t first = lane < 6 ? p.st_src[cell * 24 + lane * 4] : 0;
-                        // group o reads source group o ^ flip = o -/+ flip for the minus/plus list
-                        const long long flip = first >> 28;
-                        soff = (long long)(first & 0x0fffffff) * p.nv + ((lane & 1) ? flip : -flip) * p.P;
-                        const unsigned xm = __ballot_sync(0xffffffffu, lane < 6 && cnt > 1);
-                        if (lane == 0) {
-                            sl.xmask = (int)xm;
-                            sl.invh = static_cast<const TC *>(p.inv_h)[cell];
-                        }
-                    }
-                    if (lane == 0) sl.cell = cell;
-                    __syncwarp();
-                    if (cell < 0) {
-                        // end marker: complete the stage's phase without data
-                        if (lane == 0) mbar_arrive(&sm.full[(g & smask)]);
-                        break;
-                    }
-                }
-                // lane 0 announces the bytes, then lanes 0..DIM copy one chunk each:
-                // lane 0 the cell's own group o, lane 1 + d the first upwind
-                // source along axis d
-                const int s = g & smask;
-                if (lane == 0) mbar_expect_tx(&sm.full[s], sbytes);
-                __syncwarp();
-                const int d = lane - 1;
-                const long long so = __shfl_sync(0xffffffffu, soff, list_of(o, d < 0 ? 0 : (d > 2 ? 2 : d)));
-                if (lane <= DIM) {
-                    const TS *src = lane == 0 ? fin + cell * (long long)p.nv + o * p.P : fin + so + o * p.P;
-                    bulk_g2s(ring + ((size_t)s * (1 + DIM) + lane) * p.P, src, chunk, &sm.full[s]);
-                }
-                issued = g + 1;
-            }
-            if (!ok || cell < 0) break;
-        }
-        if (!ok) {
-            // a wait gave up: report it, give the copies in flight a bounded
-            // time to land, stop
-            if (lane == 0) {
-                *abort_flag = 1;
-                atomicOr(p.status, ST_TIMEOUT);
-                for (int g = issued - stages < 0 ? 0 : issued - stages; g < issued; g++)
-                    mbar_wait_suspend(&sm.full[(g & smask)], (uint32_t)((g >> lgs) & 1));
-            }
-        }
-        return;
-    }
-
-    // solver lanes: the velocity of node `lane` of each axis
-    TC xil[3] = {0, 0, 0};
     if (warp == ncw) {
+        // ================= solver and dispatcher
+        // lane 8d + s: the velocities of nodes s, s + 8, s + 16, s + 24 of axis d
+        TC xi4[4] = {0, 0, 0, 0};
+        {
+            const int d = lane >> 3, hd = d < 3 ? p.half[d] : 0;
 #pragma unroll
-        for (int d = 0; d < 3; d++) {
-            const int hd = p.half[d];
-            if (lane < p.n[d]) {
-                const int mm = lane < hd ? hd - 1 - lane : lane - hd;
-                TC xi;
-                if constexpr (sizeof(TC) == 8) xi = p.amag[d * 32 + mm];
-                else xi = p.amag_f[d * 32 + mm];
-                xil[d] = lane < hd ? -xi : xi;
+            for (int t = 0; t < 4; t++) {
+                const int i = (lane & 7) + 8 * t;
+                if (d < 3 && i < p.n[d]) {
+                    const int mm = i < hd ? hd - 1 - i : i - hd;
+                    TC xi;
+                    if constexpr (sizeof(TC) == 8) xi = p.amag[d * 32 + mm];
+                    else xi = p.amag_f[d * 32 + mm];
+                    xi4[t] = i < hd ? -xi : xi;
+                }
             }
         }
-        // ================= solver
         for (int j = 0;; j++) {
             const int b = j & 1;
             bar_sync_n(BAR_P + b, nbar);
             const long long cell = sm.cellp[b];
-            int dec = *abort_flag || cell == -2 ? DEC_STOP : (cell < 0 ? DEC_END : DEC_GO);
+            const int dec = cell < 0 ? DEC_END : DEC_GO;
             if (dec == DEC_GO) {
-                const int flags = solve_cell<TC, COLL>(p, sm, K, b, ncw, cell, xil);
+                // the stencil of iteration j + 3 (read by the compute warps
+                // after they pass this iteration's coefficient barrier): its
+                // loads and the next take are in flight during the solve
+                const Sten nst = fetch(next_cell);
+                next_cell = take();
+                const int flags = solve_cell<TC, COLL>(p, sm, K, b, ncw, cell, xi4);
+                store(nst, j + 3);
                 if (lane == 0) {
                     if (flags) atomicOr(p.status, flags);
                     sm.ok[b] = COLL == DVM_COLL_BGK && (flags & (ST_NONPOS | ST_SINGULAR)) == 0;
@@ -547,7 +564,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_step(const StepParams p, const int 
 
     // ================= compute warps
     const bool active = tid < Q;
-    const int hz = p.half[2], hyy = p.half[1], hxx = p.half[0];
+    const int hz = p.half[2], hyy = p.half[1];
     const int p0 = active ? tid * VEC : 0;
     const int mz0 = p0 % hz, my = (p0 / hz) % hyy, mx = p0 / (hz * hyy);
     TC ax, ay, azv[VEC];
@@ -562,61 +579,64 @@ __global__ void __launch_bounds__(MAXT, 1) k_step(const StepParams p, const int 
 #pragma unroll
         for (int e = 0; e < VEC; e++) azv[e] = p.amag_f[64 + mz0 + e];
     }
-    const TC jx = (TC)(2 * mx + 1), jy = (TC)(2 * my + 1);
+    // the thread's node indices, packed into one register (each < 32)
+    const int mpk = mx | (my << 8) | (mz0 << 16);
     const TC dt = (TC)p.dt;
-    // dt |xi_d| per axis and their sum (the self coefficient is 1 - invh * sum)
+    // dt |xi_d| per axis (the self coefficient is 1 - invh * their sum)
     const TC dax = dt * ax, day = dt * ay;
-    Q4 daz, dsum;
+    Q4 daz;
     {
-        TC t[VEC], s[VEC];
+        TC t[VEC];
 #pragma unroll
-        for (int e = 0; e < VEC; e++) {
-            t[e] = dt * azv[e];
-            s[e] = DIM == 3 ? dax + day + t[e] : dax + day;
-        }
+        for (int e = 0; e < VEC; e++) t[e] = DIM == 3 ? dt * azv[e] : (TC)0;
         daz = q_make(t);
-        dsum = q_make(s);
     }
 
-    bool prev_end = false;   // this warp saw the end marker of the previous iteration
-    long long prev_cell = -1;
+    // this thread's pieces of fill g = 8 j + o (the cell's own group o and
+    // the first upwind source of each axis) into stage g mod stages; every
+    // thread reads back only the pieces it copied itself
+    auto issue = [&](int g, uint32_t dep) {
+        const CellSlot<TC> &sl = sm.slot[(g >> 3) % NSL];
+        const long long c = sl.cell;
+        if (active && c >= 0) {
+            const int o = g & 7;
+            TS *st = ring + (size_t)(g & (stages - 1)) * (1 + DIM) * p.P + p0;
+            cp_piece(st, fin + c * p.nv + o * p.P + p0, dep);
+#pragma unroll
+            for (int d = 0; d < DIM; d++) cp_piece(st + (1 + d) * p.P, fin + sl.soff[list_of(o, d)] + o * p.P + p0, dep);
+        }
+        cp_async_commit();
+    };
+    for (int g = 0; g < stages; g++) issue(g, 0u);
+
     Q4 cur[8], prv[8];       // f* of cell j (phase 1) and of cell j - 1 (phase 3)
 
     // iteration j: phase 1 of cell j into `cur`, phase 3 of cell j - 1 from `prv`
     for (int j = 0;; j++) {
         const int b = j & 1, bp = b ^ 1;
-        long long cell = -1;
-        bool failed = false;
-        if (!prev_end) {
-            if (*abort_flag || !mbar_wait_suspend(&sm.full[(8 * j) & smask], (uint32_t)(((8 * j) >> lgs) & 1)))
-                failed = true;
-            else
-                cell = sm.slot[j % NSL].cell;
-        }
+        const long long cell = sm.slot[j % NSL].cell;
         if (cell >= 0) {
             const CellSlot<TC> &sl = sm.slot[j % NSL];
-            // per-cell coefficients: f* = cs f + sum_d aw_L src_L
-            const TC invh = sl.invh;
-            const Q4 cs = q_fma(q_splat(-invh), dsum, q_splat((TC)1));
-            TC aw[4], wz[2];
-#pragma unroll
-            for (int L = 0; L < 4; L++) aw[L] = (L < 2 ? dax : day) * sl.w[L * 4];
-            wz[0] = sl.w[16];
-            wz[1] = sl.w[20];
             const int xm = sl.xmask;
 #pragma unroll
             for (int o = 0; o < 8; o++) {
                 const int g = 8 * j + o;
-                if (o > 0 && !failed && !mbar_wait_suspend(&sm.full[(g & smask)], (uint32_t)((g >> lgs) & 1)))
-                    failed = true;
+                // this thread's pieces of fill g have landed when at most
+                // stages - 1 younger groups are pending
+                if (lgs == 3) cp_async_wait<7>();
+                else if (lgs == 2) cp_async_wait<3>();
+                else cp_async_wait<1>();
                 Q4 fs = q_splat((TC)0);
-                if (active && !failed) {
-                    const TS *st = stage_of(g) + p0;
+                if (active) {
+                    const TS *st = ring + (size_t)(g & (stages - 1)) * (1 + DIM) * p.P + p0;
+                    // self coefficient 1 - invh dt sum_d |xi_d|
+                    const Q4 cs = q_fma(q_splat(-sl.invh), q_add(q_splat(dax + day), daz), q_splat((TC)1));
                     fs = q_mul(cs, IO::lds(st));
 #pragma unroll
                     for (int d = 0; d < DIM; d++) {
                         const int L = list_of(o, d);
-                        const Q4 w = d < 2 ? q_splat(aw[L]) : q_mul(daz, q_splat(wz[L - 4]));
+                        const TC wl = sl.w[L * 4];
+                        const Q4 w = d == 0 ? q_splat(dax * wl) : (d == 1 ? q_splat(day * wl) : q_mul(daz, q_splat(wl)));
                         fs = q_fma(w, IO::lds(st + (1 + d) * p.P), fs);
                     }
                     if (xm & lists_of<DIM>(o)) {
@@ -634,11 +654,14 @@ __global__ void __launch_bounds__(MAXT, 1) k_step(const StepParams p, const int 
                         }
                     }
                 }
-                // the stage has been read: release it to the producer
-                __syncwarp();
-                if (lane == 0 && !failed) mbar_arrive(&sm.empty[(g & smask)]);
                 cur[o] = fs;
+                // refill the stage with fill g + stages once its reads are done
+                // (the copy depends on fs, which depends on every read)
+                issue(g + stages, dep_of(fs));
             }
+            // seven integer-weighted partial sums of this thread:
+            // sum f, sum s_x j_x f, sum s_y j_y f, sum s_z j_z f, sum j_x^2 f,
+            // sum j_y^2 f, sum j_z^2 f  (xi_d = (h_d/2) s_d j_d, j_d odd)
             Q4 T0 = q_splat((TC)0), Tz = q_splat((TC)0);
             TC Sx = 0, Sy = 0;
 #pragma unroll
@@ -649,13 +672,12 @@ __global__ void __launch_bounds__(MAXT, 1) k_step(const StepParams p, const int 
                 Sx += (o & 4) ? qs : -qs;
                 Sy += (o & 2) ? qs : -qs;
             }
-            // seven integer-weighted partial sums of this thread:
-            // sum f, sum s_x j_x f, sum s_y j_y f, sum s_z j_z f, sum j_x^2 f,
-            // sum j_y^2 f, sum j_z^2 f  (xi_d = (h_d/2) s_d j_d, j_d odd)
+            const int kx = mpk & 0xff, ky = (mpk >> 8) & 0xff, kz = mpk >> 16;
+            const TC jx = (TC)(2 * kx + 1), jy = (TC)(2 * ky + 1);
             TC jz[VEC], jz2[VEC];
 #pragma unroll
             for (int e = 0; e < VEC; e++) {
-                jz[e] = (TC)(2 * (mz0 + e) + 1);
+                jz[e] = (TC)(2 * (kz + e) + 1);
                 jz2[e] = jz[e] * jz[e];
             }
             TC m[7];
@@ -673,28 +695,33 @@ __global__ void __launch_bounds__(MAXT, 1) k_step(const StepParams p, const int 
                 if (lane == 0) sm.red[b][warp][k] = m[k];
             }
         }
-        if (failed) *abort_flag = 1;
-        if (tid == 0) sm.cellp[b] = failed ? -2 : cell;
+        if (tid == 0) sm.cellp[b] = cell;
         bar_arrive_n(BAR_P + b, nbar);
 
         if (j >= 1) {
             // ================= phase 3: collision of the previous cell
             bar_sync_n(BAR_C + bp, nbar);
             if (sm.dec[bp] != DEC_GO) break;
+            // the cell of iteration j - 1 is still in its slot (slots are
+            // reused NSL iterations later)
+            const long long pc = sm.slot[(j - 1) % NSL].cell;
             if (warp == 0 && lane < 5) {
                 // the moments of f* in FP64, one per lane
                 const typename Num<TC>::X v = sm.mom[bp][lane];
-                if constexpr (sizeof(TC) == 4) p.mom_out[prev_cell * 5 + lane] = (double)v.hi + (double)v.lo;
-                else p.mom_out[prev_cell * 5 + lane] = (double)v;
+                if constexpr (sizeof(TC) == 4) p.mom_out[pc * 5 + lane] = (double)v.hi + (double)v.lo;
+                else p.mom_out[pc * 5 + lane] = (double)v;
             }
             if (active) {
-                TS *dst = fout + prev_cell * (int64_t)p.nv + p0;
+                TS *dst = fout + pc * (int64_t)p.nv + p0;
                 if (sm.ok[bp]) {
+                    const int mx = mpk & 0xff, my = (mpk >> 8) & 0xff, mz0 = mpk >> 16;
+                    const int hz = p.half[2], hyy = p.half[1], hxx = p.half[0];
                     const TabE<TC> *tx = sm.tab[bp][0], *ty = sm.tab[bp][1], *tz = sm.tab[bp][2];
                     const TC KN = sm.coef[bp][CF_KN], C0 = sm.coef[bp][CF_C0];
                     const Q4 omn = q_splat(sm.coef[bp][CF_OMN]);
-                    // z factors of the thread's nodes for both signs: gz and gz Pz
-                    Q4 Z1[2], Z2[2];
+                    // per z sign: the z factors gz and gz Pz of the thread's
+                    // nodes, then the four x-y sign pairs (few registers held
+                    // beside the two f* sets)
 #pragma unroll
                     for (int pz = 0; pz < 2; pz++) {
                         TC g[VEC], gp[VEC];
@@ -704,22 +731,17 @@ __global__ void __launch_bounds__(MAXT, 1) k_step(const StepParams p, const int 
                             g[e] = t.g;
                             gp[e] = t.g * t.p;
                         }
-                        Z1[pz] = q_make(g);
-                        Z2[pz] = q_make(gp);
-                    }
-                    // x-y factors for the four sign pairs
-                    TC Axy[4], Bxy[4];
+                        const Q4 Z1 = q_make(g), Z2 = q_make(gp);
 #pragma unroll
-                    for (int s = 0; s < 4; s++) {
-                        const TabE<TC> a = tx[(s & 2) ? hxx + mx : hxx - 1 - mx];
-                        const TabE<TC> c = ty[(s & 1) ? hyy + my : hyy - 1 - my];
-                        Bxy[s] = KN * a.g * c.g;
-                        Axy[s] = Bxy[s] * (C0 + a.p + c.p);
-                    }
-#pragma unroll
-                    for (int o = 0; o < 8; o++) {
-                        const Q4 mt = q_fma(q_splat(Axy[o >> 1]), Z1[o & 1], q_mul(q_splat(Bxy[o >> 1]), Z2[o & 1]));
-                        IO::stg(dst + o * p.P, q_fma(omn, prv[o], mt));
+                        for (int sxy = 0; sxy < 4; sxy++) {
+                            const TabE<TC> a = tx[(sxy & 2) ? hxx + mx : hxx - 1 - mx];
+                            const TabE<TC> c = ty[(sxy & 1) ? hyy + my : hyy - 1 - my];
+                            const TC B = KN * a.g * c.g;
+                            const TC A = B * (C0 + a.p + c.p);
+                            const int o = 2 * sxy + pz;
+                            const Q4 mt = q_fma(q_splat(A), Z1, q_mul(q_splat(B), Z2));
+                            IO::stg(dst + o * p.P, q_fma(omn, prv[o], mt));
+                        }
                     }
                 } else {
 #pragma unroll
@@ -729,16 +751,15 @@ __global__ void __launch_bounds__(MAXT, 1) k_step(const StepParams p, const int 
         }
 #pragma unroll
         for (int o = 0; o < 8; o++) prv[o] = cur[o];
-        prev_end = cell < 0;
-        prev_cell = cell;
     }
+    cp_async_wait_all();
 }
 
 template <typename TS, int DIM, int COLL>
 int launch_kernel(const StepParams &p, int ncw)
 {
     auto kern = k_step<TS, DIM, COLL>;
-    const int threads = (ncw + 2) * 32;
+    const int threads = (ncw + 1) * 32;
     const uint32_t sb = stage_bytes<TS, DIM>(p.P);
     cudaFuncAttributes fa{};
     if (cudaFuncGetAttributes(&fa, kern) != cudaSuccess) return DVM_ECUDA;
@@ -749,7 +770,7 @@ int launch_kernel(const StepParams &p, int ncw)
     const int64_t room = (int64_t)optin - (int64_t)fa.sharedSizeBytes;
     const int64_t fit = std::min<int64_t>(MAXSTAGE, room / (int64_t)sb);
     if (fit < 2) return DVM_ENOTIMPL;
-    const int lgs = fit >= 8 ? 3 : (fit >= 4 ? 2 : 1);  // a power of two: indices by mask and shift
+    const int lgs = fit >= 8 ? 3 : (fit >= 4 ? 2 : 1);  // a power of two: indices by mask
     const size_t dyn = (size_t)sb << lgs;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn) != cudaSuccess)
         return DVM_ECUDA;
@@ -766,8 +787,6 @@ int launch_typed(const StepParams &p)
 {
     const int vec = Store<TS>::VEC;
     if (p.P % vec != 0 || p.half[2] % vec != 0) return DVM_EINVAL;
-    // every chunk of a group is one bulk copy: 16-byte multiples
-    if (((size_t)p.P * sizeof(TS)) % 16 != 0) return DVM_EINVAL;
     for (int d = 0; d < 3; d++)
         if (p.n[d] > NAX) return DVM_ENOTIMPL;
     const int Q = p.P / vec;
