@@ -1,5 +1,5 @@
 // Fused DVM step: upwind transport (Eq. 2) -> moments of f* -> conservative
-// BGK relaxation, with f* held in registers between the phases.
+// BGK relaxation, with f* held on chip between the phases.
 //
 // Layout (paper Sec. 3.1 steps 1-3): f[cell][group][position], 8 sign groups
 // per cell.  A compute thread owns the same "quad" of positions (4 FP32/BF16
@@ -9,45 +9,38 @@
 //
 // Persistent CTAs take the Morton-ordered cells from a global counter, so
 // the cells in flight on the whole GPU form one contiguous Morton window and
-// upwind neighbours are served from L2.  Each CTA has three roles:
+// upwind neighbours are served from L2; each taken cell's f is prefetched
+// into L2 (cp.async.bulk.prefetch) four iterations before it is needed.
 //
-//   producer warp   per cell and sign group o, one stage of a shared-memory
-//                   ring: the cell's own values of group o and, per axis d,
-//                   the values of group o in the first upwind source of the
-//                   list that group o reads (Sec. 3.1 step 4), each a
-//                   contiguous chunk of P values fetched by one bulk copy
-//                   (cp.async.bulk) completing on the stage's "full"
-//                   mbarrier; a stage is refilled once every compute warp
-//                   has released it on its "empty" mbarrier.  The copy
-//                   engine keeps up to a whole cell of loads in flight
-//                   without holding registers.
-//   compute warps   iteration j: phase 1, f*_i = (1 - dt invh sum_d |xi_d,i|) f_i
-//                   + sum_d dt |xi_d,i| sum_k w_k src_k,i on packed FP32
-//                   pairs, from the ring (further sources behind coarse-fine
-//                   faces come from L2), into registers, with per-thread
-//                   FP32 partials of the seven sums sum f, sum j_d f,
-//                   sum j_d^2 f (xi_d = (h_d/2) j_d, j_d odd); then phase 3 of
-//                   the previous cell from its registers straight to HBM.
-//   solver warp     phase 2 of cell j while the compute warps run phase 1 of
-//                   cell j+1: double-float sum of the warp partials ->
-//                   rho, u, T; the discrete Maxwellian factorises over the
-//                   tensor grid, so its moments in the centred basis
-//                   phi = (1, c, |c|^2 - 3), c = (xi - u)/sqrt(T), are
-//                   products of 1D sums; the five coefficients d of
-//                   M~ = M (1 + d.phi) (the correction form of Eq. 6) that
-//                   make M~ carry the moments of f* (defects of M's own
-//                   moments in double-float, LDL^T solve); per-axis tables
-//                   g = exp(-c^2/2), P = d_axis c + d4 c^2.
+// Compute warps, iteration j:
+//   phase 1  f*_i = (1 - dt invh sum_d |xi_d,i|) f_i + sum_d dt |xi_d,i| sum_k
+//            w_k src_k,i for cell j on packed FP32 pairs, into registers.  The
+//            inputs of each sign group (the cell's own values and the first
+//            upwind source of each axis, Sec. 3.1 step 4) come from a 4-stage
+//            shared-memory ring that every thread fills for its own
+//            positions with cp.async, four groups ahead; further sources
+//            behind coarse-fine faces come from L2.  Per-thread FP32 partials
+//            of the seven sums sum f, sum j_d f, sum j_d^2 f (xi_d = (h_d/2)
+//            j_d, j_d odd) are reduced per warp.
+//   phase 3  the collision of cell j - 2, whose f* waits in one of two
+//            shared tiles, straight to HBM; then f* of cell j takes its tile.
+// Two solver warps take the even and the odd cells: phase 2 of cell j
+// (double-float sum of the warp partials -> rho, u, T; the discrete
+// Maxwellian's moments in the centred basis phi = (1, c, |c|^2 - 3),
+// c = (xi - u)/sqrt(T), as products of 1D sums; the five coefficients d of
+// M~ = M (1 + d.phi) (the correction form of Eq. 6) that make M~ carry the
+// moments of f*; per-axis tables g = exp(-c^2/2), P = d_axis c + d4 c^2)
+// runs while the compute warps transport cells j + 1 and j + 2.  Solver warps
+// also dispatch the cells, four iterations ahead.
 //
 // Phase 3: f^{n+1} = (1 - nu dt) f* + nu dt M~ with M~ = rho (2 pi T)^(-3/2)
 //   gx gy gz (1 + d0 - 3 d4 + Px + Py + Pz), nu = sqrt(8/pi) rho sqrt(T)/Kn.
 //
-// Compute warps and the solver meet on named barriers: "partials of cell j
-// ready" and "coefficients of cell j ready", each in two parities.  The
-// solver alone decides when the CTA stops (cells exhausted, or a bounded
-// wait gave up somewhere) and publishes that with the coefficients, so that
-// every warp leaves after the same barrier; nothing waits without a bound
-// except on a named barrier whose partners are sure to arrive.
+// Compute and solver warps meet on named barriers, "partials of cell j
+// ready" and "coefficients of cell j ready", each with four instances used
+// in turn, which makes every reuse of a barrier ordered after its previous
+// completion.  The solvers decide when the CTA stops (no cell left) and
+// publish it with the coefficients; no warp waits on a flag.
 #include <algorithm>
 #include <atomic>
 #include <cmath>
@@ -68,9 +61,10 @@ namespace {
 
 constexpr int MAXCW = 14;     // compute warps per CTA (at most)
 constexpr int NAX = 32;       // velocity nodes per axis supported
-constexpr int MAXT = MAXCW * 32 + 32;
-constexpr int MAXSTAGE = 8;   // ring stages (one sign group of one cell each)
-constexpr int NSL = 8;        // ring of per-cell stencil slots (dispatched three iterations ahead)
+constexpr int MAXT = MAXCW * 32 + 64;
+constexpr int NST = 4;        // ring stages (one sign group of one cell each)
+constexpr int NSS = 4;        // solver result slots (cell j in slot j % NSS)
+constexpr int NSL = 8;        // ring of per-cell stencil slots (dispatched four iterations ahead)
 
 template <typename TC> __device__ inline TC tc_exp(TC x);
 template <> __device__ inline float tc_exp<float>(float x) { return expf(x); }
@@ -193,7 +187,8 @@ enum { DEC_GO = 0, DEC_END = 1 };
 // compute warps three iterations ahead.
 template <typename TC> struct CellSlot {
     long long cell;      // -1: no cell left
-    long long soff[6];   // element offset of each list's first source, wall flip folded in
+    int32_t sidx[6];     // chunk index (cell * 8 + group, in units of P) of each list's first
+                         // source for group 0, wall flip folded in
     int32_t src[24];     // per list (axis x side) up to 4 sources: cell | group flip << 28
     TC w[24];            // A_k / V_j
     int cnt[6];
@@ -203,13 +198,13 @@ template <typename TC> struct CellSlot {
 
 template <typename TC> struct StepSmem {
     CellSlot<TC> slot[NSL];
-    TC red[2][MAXCW][7];
-    long long cellp[2];    // cell of the partials in red (-1: none)
-    TabE<TC> tab[2][3][NAX];
-    TC coef[2][CF_N];
-    typename Num<TC>::X mom[2][5];  // rho, u, T of the cell in slot b
-    int ok[2];
-    int dec[2];
+    TC red[NSS][MAXCW][7];
+    long long cellp[NSS];  // cell of the partials in red (-1: none)
+    TabE<TC> tab[NSS][3][NAX];
+    TC coef[NSS][CF_N];
+    typename Num<TC>::X mom[NSS][5];  // rho, u, T of the cell
+    int ok[NSS];
+    int dec[NSS];
 };
 
 template <typename TC> struct Consts {
@@ -233,11 +228,13 @@ __device__ inline typename Num<TC>::X split(double v)
 __device__ inline void bar_sync_n(int id, int n) { asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory"); }
 __device__ inline void bar_arrive_n(int id, int n) { asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(n) : "memory"); }
 
-// named barriers: 1 + b "partials of a cell of parity b ready",
-// 3 + b "coefficients of a cell of parity b ready"
-constexpr int BAR_P = 1, BAR_C = 3;
+// named barriers: BAR_P + j % 4 "partials of cell j ready",
+// BAR_C + j % 4 "coefficients of cell j ready"
+constexpr int BAR_P = 1, BAR_C = 5;
 
-template <typename TS, int DIM> constexpr uint32_t stage_bytes(int P) { return (uint32_t)((1 + DIM) * P * sizeof(TS)); }
+template <typename TS, int DIM> constexpr size_t stage_bytes(int P) { return (size_t)(1 + DIM) * P * sizeof(TS); }
+// dynamic shared memory: the ring and the two f* tiles
+template <typename TS, int DIM> constexpr size_t step_dyn_bytes(int P) { return NST * stage_bytes<TS, DIM>(P) + (size_t)2 * 8 * P * sizeof(TS); }
 
 // the 16- or 8-byte piece of one thread
 template <typename TS> __device__ inline void cp_piece(TS *dst, const TS *src, uint32_t dep)
@@ -417,7 +414,7 @@ __device__ inline int solve_cell(const StepParams &p, StepSmem<TC> &sm, const Co
 }
 
 template <typename TS, int DIM, int COLL>
-__global__ void __launch_bounds__(MAXT, 1) k_step(const StepParams p, const int lgs)
+__global__ void __launch_bounds__(MAXT, 1) k_step(const StepParams p)
 {
     using S = Store<TS>;
     using IO = QIO<TS>;
@@ -428,31 +425,28 @@ __global__ void __launch_bounds__(MAXT, 1) k_step(const StepParams p, const int 
     __shared__ StepSmem<TC> sm;
     __shared__ Consts<TC> K;
     extern __shared__ __align__(128) unsigned char dsm[];
-    TS *ring = reinterpret_cast<TS *>(dsm);  // [stages][1 + DIM][P]
+    TS *ring = reinterpret_cast<TS *>(dsm);       // [NST][1 + DIM][P]
+    TS *tiles = ring + (size_t)NST * (1 + DIM) * p.P;  // [2][nv]: f* of cells j - 1 and j - 2
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int ncw = (blockDim.x >> 5) - 1;  // compute warps; the last warp solves and dispatches
-    const int nbar = blockDim.x;            // threads on the named barriers
+    const int ncw = (blockDim.x >> 5) - 2;  // compute warps; then the two solver warps
+    const int nbar = (ncw + 1) * 32;        // threads on each named barrier
     const int Q = p.P / VEC;
-    const int stages = 1 << lgs;            // 8, 4 or 2 sign groups in flight
     const TS *__restrict__ fin = static_cast<const TS *>(p.f_in);
     TS *__restrict__ fout = static_cast<TS *>(p.f_out);
 
-    // cell dispatch (one warp): a cell index from the global counter (the
-    // cells in flight on the whole GPU form one contiguous Morton window),
-    // its stencil fetched into registers, then stored into a slot; split so
-    // that the solver can overlap the loads with its own work
+    // cell dispatch (one warp): a cell index from the global counter, its
+    // stencil fetched into registers, then stored into a slot; split so
+    // that a solver overlaps the loads with its own work.  A taken cell's
+    // own f is prefetched into L2 at once.
     struct Sten {
         long long cell;
         int32_t src;
         TC w;
         int cnt;
-        long long soff;
+        int32_t sidx;
         TC invh;
     };
-    // A taken cell's own f (streamed from HBM) is prefetched into L2 at once,
-    // three iterations before its copy into shared memory, so that the copy
-    // meets L2 latency rather than loaded HBM latency.
     auto take = [&]() -> long long {
         long long cell = -1;
         if (lane == 0) {
@@ -473,8 +467,8 @@ __global__ void __launch_bounds__(MAXT, 1) k_step(const StepParams p, const int 
                 t.cnt = p.st_cnt[cell * 8 + lane];
                 // group o reads source group o ^ flip = o -/+ flip for the minus/plus list
                 const int32_t first = p.st_src[cell * 24 + lane * 4];
-                const long long flip = first >> 28;
-                t.soff = (long long)(first & 0x0fffffff) * p.nv + ((lane & 1) ? flip : -flip) * p.P;
+                const int32_t flip = first >> 28;
+                t.sidx = (first & 0x0fffffff) * 8 + ((lane & 1) ? flip : -flip);
             }
             if (lane == 0) t.invh = static_cast<const TC *>(p.inv_h)[cell];
         }
@@ -489,7 +483,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_step(const StepParams p, const int 
             }
             if (lane < 6) {
                 sl.cnt[lane] = t.cnt;
-                sl.soff[lane] = t.soff;
+                sl.sidx[lane] = t.sidx;
             }
             const unsigned xm = __ballot_sync(0xffffffffu, lane < 6 && t.cnt > 1);
             if (lane == 0) {
@@ -499,12 +493,10 @@ __global__ void __launch_bounds__(MAXT, 1) k_step(const StepParams p, const int 
         }
         if (lane == 0) sl.cell = t.cell;
     };
-    long long next_cell = -1;   // solver warp: the cell of slot j + 3, taken one iteration early
 
     if (warp == ncw) {
-        // cells of iterations 0..2, and the one of iteration 3
-        for (int k = 0; k < 3; k++) store(fetch(take()), k);
-        next_cell = take();
+        // cells of iterations 0..3
+        for (int k = 0; k < 4; k++) store(fetch(take()), k);
         if (lane == 0) {
             K.dV = split<TC>(p.dV);
             for (int d = 0; d < 3; d++) {
@@ -519,8 +511,9 @@ __global__ void __launch_bounds__(MAXT, 1) k_step(const StepParams p, const int 
     }
     __syncthreads();
 
-    if (warp == ncw) {
-        // ================= solver and dispatcher
+    if (warp >= ncw) {
+        // ================= solver warps: warp ncw + b takes the cells j = b mod 2
+        const int par = warp - ncw;
         // lane 8d + s: the velocities of nodes s, s + 8, s + 16, s + 24 of axis d
         TC xi4[4] = {0, 0, 0, 0};
         {
@@ -537,26 +530,26 @@ __global__ void __launch_bounds__(MAXT, 1) k_step(const StepParams p, const int 
                 }
             }
         }
-        for (int j = 0;; j++) {
-            const int b = j & 1;
-            bar_sync_n(BAR_P + b, nbar);
-            const long long cell = sm.cellp[b];
+        long long next_cell = take();  // the cell of slot par + 4
+        for (int j = par;; j += 2) {
+            const int q = j % NSS;
+            bar_sync_n(BAR_P + q, nbar);
+            const long long cell = sm.cellp[q];
             const int dec = cell < 0 ? DEC_END : DEC_GO;
             if (dec == DEC_GO) {
-                // the stencil of iteration j + 3 (read by the compute warps
-                // after they pass this iteration's coefficient barrier): its
-                // loads and the next take are in flight during the solve
+                // the stencil of iteration j + 4: its loads and the next take
+                // are in flight during the solve
                 const Sten nst = fetch(next_cell);
                 next_cell = take();
-                const int flags = solve_cell<TC, COLL>(p, sm, K, b, ncw, cell, xi4);
-                store(nst, j + 3);
+                const int flags = solve_cell<TC, COLL>(p, sm, K, q, ncw, cell, xi4);
+                store(nst, j + 4);
                 if (lane == 0) {
                     if (flags) atomicOr(p.status, flags);
-                    sm.ok[b] = COLL == DVM_COLL_BGK && (flags & (ST_NONPOS | ST_SINGULAR)) == 0;
+                    sm.ok[q] = COLL == DVM_COLL_BGK && (flags & (ST_NONPOS | ST_SINGULAR)) == 0;
                 }
             }
-            if (lane == 0) sm.dec[b] = dec;
-            bar_arrive_n(BAR_C + b, nbar);
+            if (lane == 0) sm.dec[q] = dec;
+            bar_arrive_n(BAR_C + q, nbar);
             if (dec != DEC_GO) break;
         }
         return;
@@ -564,79 +557,90 @@ __global__ void __launch_bounds__(MAXT, 1) k_step(const StepParams p, const int 
 
     // ================= compute warps
     const bool active = tid < Q;
-    const int hz = p.half[2], hyy = p.half[1];
     const int p0 = active ? tid * VEC : 0;
-    const int mz0 = p0 % hz, my = (p0 / hz) % hyy, mx = p0 / (hz * hyy);
-    TC ax, ay, azv[VEC];
-    if constexpr (sizeof(TC) == 8) {
-        ax = p.amag[mx];
-        ay = p.amag[32 + my];
-#pragma unroll
-        for (int e = 0; e < VEC; e++) azv[e] = p.amag[64 + mz0 + e];
-    } else {
-        ax = p.amag_f[mx];
-        ay = p.amag_f[32 + my];
-#pragma unroll
-        for (int e = 0; e < VEC; e++) azv[e] = p.amag_f[64 + mz0 + e];
-    }
-    // the thread's node indices, packed into one register (each < 32)
-    const int mpk = mx | (my << 8) | (mz0 << 16);
-    const TC dt = (TC)p.dt;
-    // dt |xi_d| per axis (the self coefficient is 1 - invh * their sum)
-    const TC dax = dt * ax, day = dt * ay;
-    Q4 daz;
+    int mpk;  // the thread's node indices (each < 32) packed into one register
+    TC dax, day;
+    Q4 daz;   // dt |xi_d| per axis (the self coefficient is 1 - invh * their sum)
     {
+        const int hz = p.half[2], hyy = p.half[1];
+        const int mz0 = p0 % hz, my = (p0 / hz) % hyy, mx = p0 / (hz * hyy);
+        mpk = mx | (my << 8) | (mz0 << 16);
+        const TC dt = (TC)p.dt;
         TC t[VEC];
+        if constexpr (sizeof(TC) == 8) {
+            dax = dt * p.amag[mx];
+            day = dt * p.amag[32 + my];
 #pragma unroll
-        for (int e = 0; e < VEC; e++) t[e] = DIM == 3 ? dt * azv[e] : (TC)0;
+            for (int e = 0; e < VEC; e++) t[e] = DIM == 3 ? dt * p.amag[64 + mz0 + e] : (TC)0;
+        } else {
+            dax = dt * p.amag_f[mx];
+            day = dt * p.amag_f[32 + my];
+#pragma unroll
+            for (int e = 0; e < VEC; e++) t[e] = DIM == 3 ? dt * p.amag_f[64 + mz0 + e] : (TC)0;
+        }
         daz = q_make(t);
     }
 
-    // this thread's pieces of fill g = 8 j + o (the cell's own group o and
-    // the first upwind source of each axis) into stage g mod stages; every
-    // thread reads back only the pieces it copied itself
-    auto issue = [&](int g, uint32_t dep) {
-        const CellSlot<TC> &sl = sm.slot[(g >> 3) % NSL];
+    // The chunk indices (units of P values) of the cell whose groups are
+    // being copied: its own group 0 and the first source of each list
+    // (group o adds o).  Each thread reads back only the pieces it copied.
+    const TS *fin_p0 = fin + p0;
+    int idx_own = 0, idx_l[2 * DIM];
+    auto point = [&](int k) -> bool {
+        const CellSlot<TC> &sl = sm.slot[k % NSL];
         const long long c = sl.cell;
-        if (active && c >= 0) {
-            const int o = g & 7;
-            TS *st = ring + (size_t)(g & (stages - 1)) * (1 + DIM) * p.P + p0;
-            cp_piece(st, fin + c * p.nv + o * p.P + p0, dep);
 #pragma unroll
-            for (int d = 0; d < DIM; d++) cp_piece(st + (1 + d) * p.P, fin + sl.soff[list_of(o, d)] + o * p.P + p0, dep);
+        for (int L = 0; L < 2 * DIM; L++) idx_l[L] = sl.sidx[L];
+        idx_own = (int)c * 8;
+        return c >= 0 && active;
+    };
+    // group o of the pointed cell into stage st; dep orders the previous
+    // reads of the stage before the copy
+    auto copy_group = [&](bool on, int o, int st, uint32_t dep) {
+        if (on) {
+            TS *d = ring + (size_t)st * (1 + DIM) * p.P + p0;
+            cp_piece(d, fin_p0 + (size_t)(uint32_t)(idx_own + o) * p.P, dep);
+#pragma unroll
+            for (int a = 0; a < DIM; a++)
+                cp_piece(d + (1 + a) * p.P, fin_p0 + (size_t)(uint32_t)(idx_l[list_of(o, a)] + o) * p.P, dep);
         }
         cp_async_commit();
     };
-    for (int g = 0; g < stages; g++) issue(g, 0u);
+    {
+        const bool on = point(0);
+#pragma unroll
+        for (int o = 0; o < NST; o++) copy_group(on, o, o, 0u);
+    }
 
-    Q4 cur[8], prv[8];       // f* of cell j (phase 1) and of cell j - 1 (phase 3)
-
-    // iteration j: phase 1 of cell j into `cur`, phase 3 of cell j - 1 from `prv`
+    Q4 cur[8];   // f* of cell j
     for (int j = 0;; j++) {
-        const int b = j & 1, bp = b ^ 1;
-        const long long cell = sm.slot[j % NSL].cell;
+        const int q = j % NSS;
+        const CellSlot<TC> &sl = sm.slot[j % NSL];
+        const long long cell = sl.cell;
         if (cell >= 0) {
-            const CellSlot<TC> &sl = sm.slot[j % NSL];
+            // ================= phase 1: transport of cell j
+            bool on = point(j);  // groups 4..7 of this cell are copied first
+            const TC invh = sl.invh;
+            const Q4 cs = q_fma(q_splat(-invh), q_add(q_splat(dax + day), daz), q_splat((TC)1));
+            TC aw[4], wz[2];
+#pragma unroll
+            for (int L = 0; L < 4; L++) aw[L] = (L < 2 ? dax : day) * sl.w[L * 4];
+            wz[0] = sl.w[16];
+            wz[1] = sl.w[20];
             const int xm = sl.xmask;
 #pragma unroll
             for (int o = 0; o < 8; o++) {
-                const int g = 8 * j + o;
-                // this thread's pieces of fill g have landed when at most
-                // stages - 1 younger groups are pending
-                if (lgs == 3) cp_async_wait<7>();
-                else if (lgs == 2) cp_async_wait<3>();
-                else cp_async_wait<1>();
+                // this thread's pieces of group o have landed when at most
+                // NST - 1 younger copy groups are pending
+                cp_async_wait<NST - 1>();
                 Q4 fs = q_splat((TC)0);
                 if (active) {
-                    const TS *st = ring + (size_t)(g & (stages - 1)) * (1 + DIM) * p.P + p0;
-                    // self coefficient 1 - invh dt sum_d |xi_d|
-                    const Q4 cs = q_fma(q_splat(-sl.invh), q_add(q_splat(dax + day), daz), q_splat((TC)1));
+                    const TS *st = ring + (size_t)(o % NST) * (1 + DIM) * p.P + p0;
                     fs = q_mul(cs, IO::lds(st));
 #pragma unroll
                     for (int d = 0; d < DIM; d++) {
                         const int L = list_of(o, d);
-                        const TC wl = sl.w[L * 4];
-                        const Q4 w = d == 0 ? q_splat(dax * wl) : (d == 1 ? q_splat(day * wl) : q_mul(daz, q_splat(wl)));
+                        const Q4 w = d < 2 ? q_splat(aw[L]) : q_mul(daz, q_splat(wz[L - 4]));
                         fs = q_fma(w, IO::lds(st + (1 + d) * p.P), fs);
                     }
                     if (xm & lists_of<DIM>(o)) {
@@ -645,19 +649,20 @@ __global__ void __launch_bounds__(MAXT, 1) k_step(const StepParams p, const int 
                         for (int d = 0; d < DIM; d++) {
                             const int L = list_of(o, d);
                             const Q4 da = d == 0 ? q_splat(dax) : (d == 1 ? q_splat(day) : daz);
-                            for (int q = 1; q < sl.cnt[L]; q++) {
-                                const int32_t src = sl.src[L * 4 + q];
+                            for (int k = 1; k < sl.cnt[L]; k++) {
+                                const int32_t src = sl.src[L * 4 + k];
                                 const Q4 v = IO::ldg(fin + (int64_t)(src & 0x0fffffff) * p.nv +
                                                      (o ^ (src >> 28)) * p.P + p0);
-                                fs = q_fma(q_mul(da, q_splat(sl.w[L * 4 + q])), v, fs);
+                                fs = q_fma(q_mul(da, q_splat(sl.w[L * 4 + k])), v, fs);
                             }
                         }
                     }
                 }
                 cur[o] = fs;
-                // refill the stage with fill g + stages once its reads are done
-                // (the copy depends on fs, which depends on every read)
-                issue(g + stages, dep_of(fs));
+                // refill the stage, NST groups ahead: groups 4..7 of this cell,
+                // then groups 0..3 of the next one
+                if (o == NST) on = point(j + 1);
+                copy_group(on, (o + NST) & 7, o % NST, dep_of(fs));
             }
             // seven integer-weighted partial sums of this thread:
             // sum f, sum s_x j_x f, sum s_y j_y f, sum s_z j_z f, sum j_x^2 f,
@@ -692,36 +697,37 @@ __global__ void __launch_bounds__(MAXT, 1) k_step(const StepParams p, const int 
             for (int k = 0; k < 7; k++) {
 #pragma unroll
                 for (int off = 16; off > 0; off >>= 1) m[k] += __shfl_down_sync(0xffffffffu, m[k], off);
-                if (lane == 0) sm.red[b][warp][k] = m[k];
+                if (lane == 0) sm.red[q][warp][k] = m[k];
             }
         }
-        if (tid == 0) sm.cellp[b] = cell;
-        bar_arrive_n(BAR_P + b, nbar);
+        if (tid == 0) sm.cellp[q] = cell;
+        bar_arrive_n(BAR_P + q, nbar);
 
-        if (j >= 1) {
-            // ================= phase 3: collision of the previous cell
-            bar_sync_n(BAR_C + bp, nbar);
-            if (sm.dec[bp] != DEC_GO) break;
-            // the cell of iteration j - 1 is still in its slot (slots are
+        TS *tile = tiles + (size_t)(j & 1) * p.nv + p0;  // f* of cell j - 2, then of cell j
+        if (j >= 2) {
+            // ================= phase 3: collision of cell j - 2
+            const int q2 = (j - 2) % NSS;
+            bar_sync_n(BAR_C + q2, nbar);
+            if (sm.dec[q2] != DEC_GO) break;
+            // the cell of iteration j - 2 is still in its slot (slots are
             // reused NSL iterations later)
-            const long long pc = sm.slot[(j - 1) % NSL].cell;
+            const long long pc = sm.slot[(j - 2) % NSL].cell;
             if (warp == 0 && lane < 5) {
                 // the moments of f* in FP64, one per lane
-                const typename Num<TC>::X v = sm.mom[bp][lane];
+                const typename Num<TC>::X v = sm.mom[q2][lane];
                 if constexpr (sizeof(TC) == 4) p.mom_out[pc * 5 + lane] = (double)v.hi + (double)v.lo;
                 else p.mom_out[pc * 5 + lane] = (double)v;
             }
             if (active) {
                 TS *dst = fout + pc * (int64_t)p.nv + p0;
-                if (sm.ok[bp]) {
+                if (sm.ok[q2]) {
                     const int mx = mpk & 0xff, my = (mpk >> 8) & 0xff, mz0 = mpk >> 16;
                     const int hz = p.half[2], hyy = p.half[1], hxx = p.half[0];
-                    const TabE<TC> *tx = sm.tab[bp][0], *ty = sm.tab[bp][1], *tz = sm.tab[bp][2];
-                    const TC KN = sm.coef[bp][CF_KN], C0 = sm.coef[bp][CF_C0];
-                    const Q4 omn = q_splat(sm.coef[bp][CF_OMN]);
+                    const TabE<TC> *tx = sm.tab[q2][0], *ty = sm.tab[q2][1], *tz = sm.tab[q2][2];
+                    const TC KN = sm.coef[q2][CF_KN], C0 = sm.coef[q2][CF_C0];
+                    const Q4 omn = q_splat(sm.coef[q2][CF_OMN]);
                     // per z sign: the z factors gz and gz Pz of the thread's
-                    // nodes, then the four x-y sign pairs (few registers held
-                    // beside the two f* sets)
+                    // nodes, then the four x-y sign pairs
 #pragma unroll
                     for (int pz = 0; pz < 2; pz++) {
                         TC g[VEC], gp[VEC];
@@ -740,17 +746,21 @@ __global__ void __launch_bounds__(MAXT, 1) k_step(const StepParams p, const int 
                             const TC A = B * (C0 + a.p + c.p);
                             const int o = 2 * sxy + pz;
                             const Q4 mt = q_fma(q_splat(A), Z1, q_mul(q_splat(B), Z2));
-                            IO::stg(dst + o * p.P, q_fma(omn, prv[o], mt));
+                            IO::stg(dst + o * p.P, q_fma(omn, IO::lds(tile + o * p.P), mt));
                         }
                     }
                 } else {
 #pragma unroll
-                    for (int o = 0; o < 8; o++) IO::stg(dst + o * p.P, prv[o]);
+                    for (int o = 0; o < 8; o++) IO::stg(dst + o * p.P, IO::lds(tile + o * p.P));
                 }
             }
         }
+        // f* of cell j waits in the tile the collision just read (each thread
+        // rewrites only its own positions)
+        if (cell >= 0 && active) {
 #pragma unroll
-        for (int o = 0; o < 8; o++) prv[o] = cur[o];
+            for (int o = 0; o < 8; o++) IO::sts(tile + o * p.P, cur[o]);
+        }
     }
     cp_async_wait_all();
 }
@@ -759,25 +769,21 @@ template <typename TS, int DIM, int COLL>
 int launch_kernel(const StepParams &p, int ncw)
 {
     auto kern = k_step<TS, DIM, COLL>;
-    const int threads = (ncw + 1) * 32;
-    const uint32_t sb = stage_bytes<TS, DIM>(p.P);
+    const int threads = (ncw + 2) * 32;
+    const size_t dyn = step_dyn_bytes<TS, DIM>(p.P);
     cudaFuncAttributes fa{};
     if (cudaFuncGetAttributes(&fa, kern) != cudaSuccess) return DVM_ECUDA;
     int dev = 0, optin = 0, nsm = 0, occ = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    const int64_t room = (int64_t)optin - (int64_t)fa.sharedSizeBytes;
-    const int64_t fit = std::min<int64_t>(MAXSTAGE, room / (int64_t)sb);
-    if (fit < 2) return DVM_ENOTIMPL;
-    const int lgs = fit >= 8 ? 3 : (fit >= 4 ? 2 : 1);  // a power of two: indices by mask
-    const size_t dyn = (size_t)sb << lgs;
+    if (fa.sharedSizeBytes + dyn > (size_t)optin) return DVM_ENOTIMPL;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn) != cudaSuccess)
         return DVM_ECUDA;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, dyn) != cudaSuccess || occ < 1)
         return DVM_ENOTIMPL;
     const int64_t grid = std::min<int64_t>(p.ncells, (int64_t)nsm * occ);
-    kern<<<(unsigned)grid, threads, dyn, p.stream>>>(p, lgs);
+    kern<<<(unsigned)grid, threads, dyn, p.stream>>>(p);
     count_launch();
     return cudaGetLastError() == cudaSuccess ? DVM_OK : DVM_ECUDA;
 }
