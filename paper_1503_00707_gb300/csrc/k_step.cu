@@ -9,8 +9,7 @@
 //
 // Persistent CTAs take the Morton-ordered cells from a global counter, so
 // the cells in flight on the whole GPU form one contiguous Morton window and
-// upwind neighbours are served from L2; each taken cell's f is prefetched
-// into L2 (cp.async.bulk.prefetch) four iterations before it is needed.
+// upwind neighbours are served from L2.
 //
 // Compute warps, iteration j:
 //   phase 1  f*_i = (1 - dt invh sum_d |xi_d,i|) f_i + sum_d dt |xi_d,i| sum_k
@@ -437,27 +436,25 @@ __global__ void __launch_bounds__(MAXT, 1) k_step(const StepParams p)
 
     // cell dispatch (one warp): a cell index from the global counter, its
     // stencil fetched into registers, then stored into a slot; split so
-    // that a solver overlaps the loads with its own work.  A taken cell's
-    // own f is prefetched into L2 at once.
+    // that a solver overlaps the counter's round trip and the loads with its
+    // own work.
+    // raw loaded values only: anything computed from them waits for the
+    // loads, so it is left to store(), after the solve
     struct Sten {
         long long cell;
-        int32_t src;
+        int32_t src, first;
         TC w;
         int cnt;
-        int32_t sidx;
         TC invh;
     };
-    auto take = [&]() -> long long {
-        long long cell = -1;
-        if (lane == 0) {
-            const unsigned long long c = atomicAdd(p.counter, 1ull);
-            cell = c < (unsigned long long)p.ncells ? (long long)c : -1;
-            if (cell >= 0) prefetch_l2_bulk(fin + cell * p.nv, (uint32_t)(p.nv * sizeof(TS)));
-        }
-        return __shfl_sync(0xffffffffu, cell, 0);
+    auto take_issue = [&]() -> unsigned long long { return lane == 0 ? atomicAdd(p.counter, 1ull) : 0ull; };
+    auto take_finish = [&](unsigned long long c) -> long long {
+        c = __shfl_sync(0xffffffffu, c, 0);
+        return c < (unsigned long long)p.ncells ? (long long)c : -1;
     };
+    auto take = [&]() -> long long { return take_finish(take_issue()); };
     auto fetch = [&](long long cell) {
-        Sten t{cell, 0, (TC)0, 0, 0, (TC)0};
+        Sten t{cell, 0, 0, (TC)0, 0, (TC)0};
         if (cell >= 0) {
             if (lane < 24) {
                 t.src = p.st_src[cell * 24 + lane];
@@ -465,10 +462,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_step(const StepParams p)
             }
             if (lane < 6) {
                 t.cnt = p.st_cnt[cell * 8 + lane];
-                // group o reads source group o ^ flip = o -/+ flip for the minus/plus list
-                const int32_t first = p.st_src[cell * 24 + lane * 4];
-                const int32_t flip = first >> 28;
-                t.sidx = (first & 0x0fffffff) * 8 + ((lane & 1) ? flip : -flip);
+                t.first = p.st_src[cell * 24 + lane * 4];
             }
             if (lane == 0) t.invh = static_cast<const TC *>(p.inv_h)[cell];
         }
@@ -483,7 +477,9 @@ __global__ void __launch_bounds__(MAXT, 1) k_step(const StepParams p)
             }
             if (lane < 6) {
                 sl.cnt[lane] = t.cnt;
-                sl.sidx[lane] = t.sidx;
+                // group o reads source group o ^ flip = o -/+ flip for the minus/plus list
+                const int32_t flip = t.first >> 28;
+                sl.sidx[lane] = (t.first & 0x0fffffff) * 8 + ((lane & 1) ? flip : -flip);
             }
             const unsigned xm = __ballot_sync(0xffffffffu, lane < 6 && t.cnt > 1);
             if (lane == 0) {
@@ -540,9 +536,10 @@ __global__ void __launch_bounds__(MAXT, 1) k_step(const StepParams p)
                 // the stencil of iteration j + 4: its loads and the next take
                 // are in flight during the solve
                 const Sten nst = fetch(next_cell);
-                next_cell = take();
+                const unsigned long long nc = take_issue();
                 const int flags = solve_cell<TC, COLL>(p, sm, K, q, ncw, cell, xi4);
                 store(nst, j + 4);
+                next_cell = take_finish(nc);
                 if (lane == 0) {
                     if (flags) atomicOr(p.status, flags);
                     sm.ok[q] = COLL == DVM_COLL_BGK && (flags & (ST_NONPOS | ST_SINGULAR)) == 0;
