@@ -412,7 +412,9 @@ __device__ inline int solve_cell(const StepParams &p, StepSmem<TC> &sm, const Co
     return __shfl_sync(0xffffffffu, flags, 0);
 }
 
-template <typename TS, int DIM, int COLL>
+// PC: the group size P as a compile-time constant (0: read it from p), so
+// that every group offset of the unrolled loops is an immediate.
+template <typename TS, int DIM, int COLL, int PC>
 __global__ void __launch_bounds__(MAXT, 1) k_step(const StepParams p)
 {
     using S = Store<TS>;
@@ -421,16 +423,18 @@ __global__ void __launch_bounds__(MAXT, 1) k_step(const StepParams p)
     using Q4 = QV<TC>;
     constexpr int VEC = S::VEC;
 
+    const int P = PC ? PC : p.P;  // velocity nodes per sign group
+    const int NV = 8 * P;
     __shared__ StepSmem<TC> sm;
     __shared__ Consts<TC> K;
     extern __shared__ __align__(128) unsigned char dsm[];
     TS *ring = reinterpret_cast<TS *>(dsm);       // [NST][1 + DIM][P]
-    TS *tiles = ring + (size_t)NST * (1 + DIM) * p.P;  // [2][nv]: f* of cells j - 1 and j - 2
+    TS *tiles = ring + (size_t)NST * (1 + DIM) * P;  // [2][nv]: f* of cells j - 1 and j - 2
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int ncw = (blockDim.x >> 5) - 2;  // compute warps; then the two solver warps
     const int nbar = (ncw + 1) * 32;        // threads on each named barrier
-    const int Q = p.P / VEC;
+    const int Q = P / VEC;
     const TS *__restrict__ fin = static_cast<const TS *>(p.f_in);
     TS *__restrict__ fout = static_cast<TS *>(p.f_out);
 
@@ -595,11 +599,11 @@ __global__ void __launch_bounds__(MAXT, 1) k_step(const StepParams p)
     // reads of the stage before the copy
     auto copy_group = [&](bool on, int o, int st, uint32_t dep) {
         if (on) {
-            TS *d = ring + (size_t)st * (1 + DIM) * p.P + p0;
-            cp_piece(d, fin_p0 + (size_t)(uint32_t)(idx_own + o) * p.P, dep);
+            TS *d = ring + (size_t)st * (1 + DIM) * P + p0;
+            cp_piece(d, fin_p0 + (size_t)(uint32_t)(idx_own + o) * P, dep);
 #pragma unroll
             for (int a = 0; a < DIM; a++)
-                cp_piece(d + (1 + a) * p.P, fin_p0 + (size_t)(uint32_t)(idx_l[list_of(o, a)] + o) * p.P, dep);
+                cp_piece(d + (1 + a) * P, fin_p0 + (size_t)(uint32_t)(idx_l[list_of(o, a)] + o) * P, dep);
         }
         cp_async_commit();
     };
@@ -632,13 +636,13 @@ __global__ void __launch_bounds__(MAXT, 1) k_step(const StepParams p)
                 cp_async_wait<NST - 1>();
                 Q4 fs = q_splat((TC)0);
                 if (active) {
-                    const TS *st = ring + (size_t)(o % NST) * (1 + DIM) * p.P + p0;
+                    const TS *st = ring + (size_t)(o % NST) * (1 + DIM) * P + p0;
                     fs = q_mul(cs, IO::lds(st));
 #pragma unroll
                     for (int d = 0; d < DIM; d++) {
                         const int L = list_of(o, d);
                         const Q4 w = d < 2 ? q_splat(aw[L]) : q_mul(daz, q_splat(wz[L - 4]));
-                        fs = q_fma(w, IO::lds(st + (1 + d) * p.P), fs);
+                        fs = q_fma(w, IO::lds(st + (1 + d) * P), fs);
                     }
                     if (xm & lists_of<DIM>(o)) {
                         // further sources: the fine neighbours behind a coarse face
@@ -648,8 +652,8 @@ __global__ void __launch_bounds__(MAXT, 1) k_step(const StepParams p)
                             const Q4 da = d == 0 ? q_splat(dax) : (d == 1 ? q_splat(day) : daz);
                             for (int k = 1; k < sl.cnt[L]; k++) {
                                 const int32_t src = sl.src[L * 4 + k];
-                                const Q4 v = IO::ldg(fin + (int64_t)(src & 0x0fffffff) * p.nv +
-                                                     (o ^ (src >> 28)) * p.P + p0);
+                                const Q4 v = IO::ldg(fin + (int64_t)(src & 0x0fffffff) * NV +
+                                                     (o ^ (src >> 28)) * P + p0);
                                 fs = q_fma(q_mul(da, q_splat(sl.w[L * 4 + k])), v, fs);
                             }
                         }
@@ -700,7 +704,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_step(const StepParams p)
         if (tid == 0) sm.cellp[q] = cell;
         bar_arrive_n(BAR_P + q, nbar);
 
-        TS *tile = tiles + (size_t)(j & 1) * p.nv + p0;  // f* of cell j - 2, then of cell j
+        TS *tile = tiles + (size_t)(j & 1) * NV + p0;  // f* of cell j - 2, then of cell j
         if (j >= 2) {
             // ================= phase 3: collision of cell j - 2
             const int q2 = (j - 2) % NSS;
@@ -716,7 +720,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_step(const StepParams p)
                 else p.mom_out[pc * 5 + lane] = (double)v;
             }
             if (active) {
-                TS *dst = fout + pc * (int64_t)p.nv + p0;
+                TS *dst = fout + pc * (int64_t)NV + p0;
                 if (sm.ok[q2]) {
                     const int mx = mpk & 0xff, my = (mpk >> 8) & 0xff, mz0 = mpk >> 16;
                     const int hz = p.half[2], hyy = p.half[1], hxx = p.half[0];
@@ -743,12 +747,12 @@ __global__ void __launch_bounds__(MAXT, 1) k_step(const StepParams p)
                             const TC A = B * (C0 + a.p + c.p);
                             const int o = 2 * sxy + pz;
                             const Q4 mt = q_fma(q_splat(A), Z1, q_mul(q_splat(B), Z2));
-                            IO::stg(dst + o * p.P, q_fma(omn, IO::lds(tile + o * p.P), mt));
+                            IO::stg(dst + o * P, q_fma(omn, IO::lds(tile + o * P), mt));
                         }
                     }
                 } else {
 #pragma unroll
-                    for (int o = 0; o < 8; o++) IO::stg(dst + o * p.P, IO::lds(tile + o * p.P));
+                    for (int o = 0; o < 8; o++) IO::stg(dst + o * P, IO::lds(tile + o * P));
                 }
             }
         }
@@ -756,16 +760,16 @@ __global__ void __launch_bounds__(MAXT, 1) k_step(const StepParams p)
         // rewrites only its own positions)
         if (cell >= 0 && active) {
 #pragma unroll
-            for (int o = 0; o < 8; o++) IO::sts(tile + o * p.P, cur[o]);
+            for (int o = 0; o < 8; o++) IO::sts(tile + o * P, cur[o]);
         }
     }
     cp_async_wait_all();
 }
 
-template <typename TS, int DIM, int COLL>
+template <typename TS, int DIM, int COLL, int PC>
 int launch_kernel(const StepParams &p, int ncw)
 {
-    auto kern = k_step<TS, DIM, COLL>;
+    auto kern = k_step<TS, DIM, COLL, PC>;
     const int threads = (ncw + 2) * 32;
     const size_t dyn = step_dyn_bytes<TS, DIM>(p.P);
     cudaFuncAttributes fa{};
@@ -785,6 +789,17 @@ int launch_kernel(const StepParams &p, int ncw)
     return cudaGetLastError() == cudaSuccess ? DVM_OK : DVM_ECUDA;
 }
 
+// compile-time group sizes for the 24^3 and 16^3 grids of 3D FP32/BF16 runs
+template <typename TS, int DIM, int COLL>
+int launch_sized(const StepParams &p, int ncw)
+{
+    if constexpr (DIM == 3 && sizeof(TS) <= 4) {
+        if (p.P == 1728) return launch_kernel<TS, DIM, COLL, 1728>(p, ncw);
+        if (p.P == 512) return launch_kernel<TS, DIM, COLL, 512>(p, ncw);
+    }
+    return launch_kernel<TS, DIM, COLL, 0>(p, ncw);
+}
+
 template <typename TS, int DIM>
 int launch_typed(const StepParams &p)
 {
@@ -795,8 +810,8 @@ int launch_typed(const StepParams &p)
     const int Q = p.P / vec;
     const int ncw = (Q + 31) / 32;
     if (ncw > MAXCW) return DVM_ENOTIMPL;
-    if (p.coll == DVM_COLL_BGK) return launch_kernel<TS, DIM, DVM_COLL_BGK>(p, ncw);
-    return launch_kernel<TS, DIM, DVM_COLL_NONE>(p, ncw);
+    if (p.coll == DVM_COLL_BGK) return launch_sized<TS, DIM, DVM_COLL_BGK>(p, ncw);
+    return launch_sized<TS, DIM, DVM_COLL_NONE>(p, ncw);
 }
 
 }  // namespace
