@@ -204,6 +204,7 @@ template <typename TC> struct StepSmem {
     typename Num<TC>::X mom[NSS][5];  // rho, u, T of the cell
     int ok[NSS];
     int dec[NSS];
+    TC xin[3][NAX];   // velocity node values per axis, in index order
 };
 
 template <typename TC> struct Consts {
@@ -257,7 +258,7 @@ template <typename T> __device__ inline uint32_t dep_of(const QV<T> &q)
 // would be fetched from beyond the instruction cache every time.
 template <typename TC, int COLL>
 __device__ inline int solve_cell(const StepParams &p, StepSmem<TC> &sm, const Consts<TC> &K, int b, int ncw,
-                                 long long cell, const TC (&xi4)[4])
+                                 long long cell)
 {
     using N = Num<TC>;
     using X = typename N::X;
@@ -303,21 +304,17 @@ __device__ inline int solve_cell(const StepParams &p, StepSmem<TC> &sm, const Co
         const TC ud = ax == 0 ? uT[0] : (ax == 1 ? uT[1] : uT[2]);
         const int nax = ax < 3 ? p.n[ax] : 0;
         X A0 = N::make((TC)0), A2 = N::make((TC)0);
-        TC A1 = 0, A3 = 0, A4 = 0, cl[4], gl[4];
-#pragma unroll
-        for (int t = 0; t < 4; t++) {
-            cl[t] = 0;
-            gl[t] = 0;
-            if (sub + 8 * t < nax) {
-                cl[t] = (xi4[t] - ud) * isTt;
-                gl[t] = tc_exp<TC>((TC)-0.5 * cl[t] * cl[t]);
-            }
-            const TC gc = gl[t] * cl[t];
-            A0 = A0 + N::make(gl[t]);
-            A2 = A2 + N::make(gc) * cl[t];
+        TC A1 = 0, A3 = 0, A4 = 0;
+#pragma unroll 1
+        for (int i = sub; i < nax; i += 8) {
+            const TC c = (sm.xin[ax][i] - ud) * isTt;
+            const TC g = tc_exp<TC>((TC)-0.5 * c * c);
+            const TC gc = g * c;
+            A0 = A0 + N::make(g);
+            A2 = A2 + N::make(gc) * c;
             A1 += gc;
-            A3 += gc * cl[t] * cl[t];
-            A4 += gc * cl[t] * cl[t] * cl[t];
+            A3 += gc * c * c;
+            A4 += gc * c * c * c;
         }
 #pragma unroll
         for (int m = 4; m > 0; m >>= 1) {
@@ -397,9 +394,11 @@ __device__ inline int solve_cell(const StepParams &p, StepSmem<TC> &sm, const Co
         const TC d4 = sm.coef[b][CF_D4];
         if (ax < 3) {
             const TC da = sm.coef[b][CF_DX + ax];
-#pragma unroll
-            for (int t = 0; t < 4; t++)
-                if (sub + 8 * t < nax) sm.tab[b][ax][sub + 8 * t] = TabE<TC>{gl[t], cl[t] * (da + d4 * cl[t])};
+#pragma unroll 1
+            for (int i = sub; i < nax; i += 8) {
+                const TC c = (sm.xin[ax][i] - ud) * isTt;
+                sm.tab[b][ax][i] = TabE<TC>{tc_exp<TC>((TC)-0.5 * c * c), c * (da + d4 * c)};
+            }
         }
     }
     if (lane == 0) {
@@ -497,6 +496,17 @@ __global__ void __launch_bounds__(MAXT, 1) k_step(const StepParams p)
     if (warp == ncw) {
         // cells of iterations 0..3
         for (int k = 0; k < 4; k++) store(fetch(take()), k);
+#pragma unroll
+        for (int d = 0; d < 3; d++) {
+            const int hd = p.half[d];
+            if (lane < p.n[d]) {
+                const int mm = lane < hd ? hd - 1 - lane : lane - hd;
+                TC xi;
+                if constexpr (sizeof(TC) == 8) xi = p.amag[d * 32 + mm];
+                else xi = p.amag_f[d * 32 + mm];
+                sm.xin[d][lane] = lane < hd ? -xi : xi;
+            }
+        }
         if (lane == 0) {
             K.dV = split<TC>(p.dV);
             for (int d = 0; d < 3; d++) {
@@ -514,22 +524,6 @@ __global__ void __launch_bounds__(MAXT, 1) k_step(const StepParams p)
     if (warp >= ncw) {
         // ================= solver warps: warp ncw + b takes the cells j = b mod 2
         const int par = warp - ncw;
-        // lane 8d + s: the velocities of nodes s, s + 8, s + 16, s + 24 of axis d
-        TC xi4[4] = {0, 0, 0, 0};
-        {
-            const int d = lane >> 3, hd = d < 3 ? p.half[d] : 0;
-#pragma unroll
-            for (int t = 0; t < 4; t++) {
-                const int i = (lane & 7) + 8 * t;
-                if (d < 3 && i < p.n[d]) {
-                    const int mm = i < hd ? hd - 1 - i : i - hd;
-                    TC xi;
-                    if constexpr (sizeof(TC) == 8) xi = p.amag[d * 32 + mm];
-                    else xi = p.amag_f[d * 32 + mm];
-                    xi4[t] = i < hd ? -xi : xi;
-                }
-            }
-        }
         long long next_cell = take();  // the cell of slot par + 4
         for (int j = par;; j += 2) {
             const int q = j % NSS;
@@ -541,7 +535,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_step(const StepParams p)
                 // are in flight during the solve
                 const Sten nst = fetch(next_cell);
                 const unsigned long long nc = take_issue();
-                const int flags = solve_cell<TC, COLL>(p, sm, K, q, ncw, cell, xi4);
+                const int flags = solve_cell<TC, COLL>(p, sm, K, q, ncw, cell);
                 store(nst, j + 4);
                 next_cell = take_finish(nc);
                 if (lane == 0) {
