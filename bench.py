@@ -48,6 +48,12 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-learned", action="store_true",
+                    help="skip the learned-vs-plain collision leg")
+    ap.add_argument("--learned-only", action="store_true",
+                    help="run only the learned-vs-plain collision leg")
+    ap.add_argument("--learned-config", default="c5_sphere_m3_hs")
+    ap.add_argument("--learned-steps", type=int, default=10)
     return ap.parse_args()
 
 
@@ -165,6 +171,112 @@ def run_reference(args):
     return 0
 
 
+# ---------------------------------------------------------------- learned vs plain
+# Network 64 -> 256 -> 256 -> 256 -> 64: (rows, cols) of each weight matrix and
+# the bias length, in the flat parameter order of the C ABI.
+MLP_LAYERS = [((256, 64), 256), ((256, 256), 256), ((256, 256), 256), ((64, 256), 64)]
+
+
+def init_params(seed):
+    """Seeded starting weights (normal, std 1/sqrt(fan-in); zero biases)."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    out = []
+    for (r, c), nb in MLP_LAYERS:
+        out.append(rng.normal(0.0, 1.0 / math.sqrt(c), size=(r, c)).ravel())
+        out.append(np.zeros(nb))
+    return np.concatenate(out).astype(np.float32)
+
+
+def learned_leg(args):
+    """The learned collision operator against the plain hard-sphere operator on
+    the same GPU: the network is trained on the GPU (the library's tcgen05
+    forward/backward and Adam) on (a, o) pairs that the hard-sphere operator
+    makes along the relaxation of the bimodal periodic box; then the Mach-3
+    sphere flow runs the same steps under each operator from the same state.
+    Reported: cell-updates/s of each (CUDA events, whole dvm_step calls:
+    transport, collision, fallback), the relative L-infinity error of rho, u
+    and T of the learned run against the plain run, and the cells that fell
+    back to the plain operator in the last step."""
+    import numpy as np
+    import torch
+    import paper_1503_00707_gb300 as D
+
+    seed = W.SEED
+    # training pairs: the bimodal box on a level-3/4 tree, pairs every 20 steps
+    c4 = dict(W.CONFIGS["c4_hs_bimodal"])
+    c4.update(base_level=3, max_level=4)
+    s = D.solver_from_config(c4, D.F32, D.COLL_HS)
+    xyz, _ = s.centres()
+    s.init_maxwellian(*W.initial_state(c4, xyz))
+    s.set_collision_tables(c4["trials"], seed)
+    dt4 = s.dt_cfl(c4["cfl"]) / 32
+    X, T = [], []
+    for _ in range(60):
+        a, o = s.learned_pairs()
+        X.append(a)
+        T.append(o)
+        s.step(20, dt4)
+    s.close()
+    X, T = np.concatenate(X), np.concatenate(T)
+    net = D.Solver(D.F32, D.COLL_NONE, 1.0)
+    net.set_weights(init_params(seed))
+    loss0, _ = net.mlp_loss_grad(X, T, want_grad=False)
+    t0 = time.perf_counter()
+    loss = net.train(X, T, epochs=20, batch=1024, lr=1e-3, seed=seed)
+    train_s = time.perf_counter() - t0
+    sys.stderr.write("learned leg: %d pairs, loss %.4g -> %.4g in %.1f s\n" % (X.shape[0], loss0, loss, train_s))
+    weights = net.get_weights()
+    net.close()
+
+    cfg = W.CONFIGS[args.learned_config]
+    res = {}
+    for name, coll in (("plain", D.COLL_HS), ("learned", D.COLL_LEARNED)):
+        stream = torch.cuda.Stream()
+        s = D.solver_from_config(cfg, D.F32, coll, stream=stream)
+        xyz, _ = s.centres()
+        s.init_maxwellian(*W.initial_state(cfg, xyz))
+        s.set_collision_tables(cfg["trials"], seed)
+        if coll == D.COLL_LEARNED:
+            s.set_weights(weights)
+            s.learned_configure(0.05)
+        # explicit Euler on the collision term needs dt/Kn max(P B) <= 1
+        dt = s.dt_cfl(cfg["cfl"]) / 10
+        s.step(1, dt)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s.step(args.learned_steps, dt)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        sys.stderr.write("learned leg: %s %.1f ms per step on %d cells\n" % (name, ms / args.learned_steps, s.ncells))
+        res[name] = {"value": s.ncells * s.nv * args.learned_steps / (ms / 1e3), "unit": UNIT,
+                     "ms_per_step": ms / args.learned_steps, "moments": s.moments(),
+                     "cells": s.ncells,
+                     "fallback": s.learned_fallback_count() if coll == D.COLL_LEARNED else None}
+        s.close()
+
+    def rel(a, b):
+        return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+    (r1, u1, T1), (r2, u2, T2) = res["learned"]["moments"], res["plain"]["moments"]
+    nc = res["plain"]["cells"]
+    return {
+        "workload": "%s: Mach-3 sphere flow, %d cells x 24^3 velocities, hard-sphere integral with %d "
+                    "trials per node (plain) vs the learned operator gated at Kn_loc < 0.05 with "
+                    "hard-sphere fallback, %d timed steps after 1, from the freestream"
+                    % (args.learned_config, nc, cfg["trials"], args.learned_steps),
+        "plain": {"value": res["plain"]["value"], "unit": UNIT, "ms_per_step": res["plain"]["ms_per_step"]},
+        "learned": {"value": res["learned"]["value"], "unit": UNIT,
+                    "ms_per_step": res["learned"]["ms_per_step"]},
+        "speedup": res["learned"]["value"] / res["plain"]["value"],
+        "field_rel_linf": {"rho": rel(r1, r2), "u": rel(u1, u2), "T": rel(T1, T2)},
+        "fallback_cells": res["learned"]["fallback"], "cells": nc,
+        "training": {"pairs": int(X.shape[0]), "epochs": 20, "loss_start": loss0, "loss_end": loss,
+                     "seconds": train_s},
+    }
+
+
 # ---------------------------------------------------------------- our arm
 def _peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -280,6 +392,12 @@ def run_ours(args):
             e2e = {"value": None, "unit": UNIT, "h2d_bytes_per_step": fbytes, "d2h_bytes_per_step": ncells * 40,
                    "skipped": "host memory available (%d GB) below 2.5x the f buffer" % (avail >> 30)}
 
+    f_gb = s.f_bytes() / 1e9
+    s.close()
+    learned = None
+    if rank == 0 and not args.no_learned:
+        learned = learned_leg(args)
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -288,11 +406,11 @@ def run_ours(args):
             "config": {"workload": workload_desc(args.config, cfg, ncells, nv, args.precision),
                        "cells": ncells, "velocities": nv, "f_values": ncells * nv,
                        "storage": args.precision, "parallelism": "replicas" if world > 1 else "single GPU",
-                       "l2": "inputs larger than L2 (f is %.1f GB)" % (s.f_bytes() / 1e9)},
+                       "l2": "inputs larger than L2 (f is %.1f GB)" % f_gb},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
+            "learned_vs_plain": learned,
         }
         print(json.dumps(line), flush=True)
-    s.close()
     if world > 1:
         torch.distributed.destroy_process_group()
     return 0
@@ -302,6 +420,13 @@ def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.learned_only:
+        import torch
+        from paper_1503_00707_gb300 import _build
+        _build.build()
+        torch.cuda.set_device(0)
+        print(json.dumps({"learned_vs_plain": learned_leg(args)}), flush=True)
+        return 0
     return run_ours(args)
 
 
