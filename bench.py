@@ -278,6 +278,22 @@ def learned_leg(args):
 
 
 # ---------------------------------------------------------------- our arm
+def job_rate(ms_local, world, updates_per_rank):
+    """Whole-job rate of N ranks that each processed updates_per_rank in their
+    own timed region: the slowest rank's time (max over ranks, an all-reduce
+    on the process group's backend) and all ranks' updates over it."""
+    ms = float(ms_local)
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.barrier()
+        ms = float(t.item())
+    return ms, world * updates_per_rank / (ms / 1e3)
+
+
 def _peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -348,12 +364,7 @@ def run_ours(args):
     launches = D.Solver.launch_count() - l0
     ms = e0.elapsed_time(e1)
     clk = clocks.stop()
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        torch.distributed.barrier()
-        ms = float(t.item())
-    value = world * ncells * nv * args.steps / (ms / 1e3)
+    ms, value = job_rate(ms, world, ncells * nv * args.steps)
     per_launch_s = ms / 1e3 / args.steps
     peak, peak_kind = _peaks()
     achieved = bytes_per_update * ncells * nv / per_launch_s / 1e9
