@@ -431,7 +431,11 @@ __global__ void __launch_bounds__(MAXT, 1) k_step(const StepParams p)
     TS *tiles = ring + (size_t)NST * (1 + DIM) * P;  // [2][nv]: f* of cells j - 1 and j - 2
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int ncw = (blockDim.x >> 5) - 2;  // compute warps; then the two solver warps
+    // warps 0 and 1 solve (the lowest warp numbers, so that a scheduler that
+    // favours older warps gives the serial per-cell work precedence); warps
+    // 2 .. ncw + 1 compute, thread ctid of them
+    const int ncw = (blockDim.x >> 5) - 2;
+    const int cw = warp - 2, ctid = tid - 64;
     const int nbar = (ncw + 1) * 32;        // threads on each named barrier
     const int Q = P / VEC;
     const TS *__restrict__ fin = static_cast<const TS *>(p.f_in);
@@ -493,7 +497,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_step(const StepParams p)
         if (lane == 0) sl.cell = t.cell;
     };
 
-    if (warp == ncw) {
+    if (warp == 0) {
         // cells of iterations 0..3
         for (int k = 0; k < 4; k++) store(fetch(take()), k);
 #pragma unroll
@@ -521,9 +525,9 @@ __global__ void __launch_bounds__(MAXT, 1) k_step(const StepParams p)
     }
     __syncthreads();
 
-    if (warp >= ncw) {
-        // ================= solver warps: warp ncw + b takes the cells j = b mod 2
-        const int par = warp - ncw;
+    if (warp < 2) {
+        // ================= solver warps: warp b takes the cells j = b mod 2
+        const int par = warp;
         long long next_cell = take();  // the cell of slot par + 4
         for (int j = par;; j += 2) {
             const int q = j % NSS;
@@ -551,8 +555,8 @@ __global__ void __launch_bounds__(MAXT, 1) k_step(const StepParams p)
     }
 
     // ================= compute warps
-    const bool active = tid < Q;
-    const int p0 = active ? tid * VEC : 0;
+    const bool active = ctid < Q;
+    const int p0 = active ? ctid * VEC : 0;
     int mpk;  // the thread's node indices (each < 32) packed into one register
     TC dax, day;
     Q4 daz;   // dt |xi_d| per axis (the self coefficient is 1 - invh * their sum)
@@ -692,10 +696,10 @@ __global__ void __launch_bounds__(MAXT, 1) k_step(const StepParams p)
             for (int k = 0; k < 7; k++) {
 #pragma unroll
                 for (int off = 16; off > 0; off >>= 1) m[k] += __shfl_down_sync(0xffffffffu, m[k], off);
-                if (lane == 0) sm.red[q][warp][k] = m[k];
+                if (lane == 0) sm.red[q][cw][k] = m[k];
             }
         }
-        if (tid == 0) sm.cellp[q] = cell;
+        if (ctid == 0) sm.cellp[q] = cell;
         bar_arrive_n(BAR_P + q, nbar);
 
         TS *tile = tiles + (size_t)(j & 1) * NV + p0;  // f* of cell j - 2, then of cell j
@@ -707,7 +711,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_step(const StepParams p)
             // the cell of iteration j - 2 is still in its slot (slots are
             // reused NSL iterations later)
             const long long pc = sm.slot[(j - 2) % NSL].cell;
-            if (warp == 0 && lane < 5) {
+            if (cw == 0 && lane < 5) {
                 // the moments of f* in FP64, one per lane
                 const typename Num<TC>::X v = sm.mom[q2][lane];
                 if constexpr (sizeof(TC) == 4) p.mom_out[pc * 5 + lane] = (double)v.hi + (double)v.lo;
