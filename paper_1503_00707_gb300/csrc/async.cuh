@@ -112,6 +112,9 @@ __device__ inline void cp_async8(void *dst, const void *src, uint32_t dep)
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8; // %2" ::"r"(smem_u32(dst)), "l"(src), "r"(dep)
                  : "memory");
 }
+// Prefetch of the line holding src into L2.
+__device__ inline void prefetch_l2(const void *src) { asm volatile("prefetch.global.L2 [%0];" ::"l"(src)); }
+
 // Bulk prefetch of [src, src + bytes) into L2 (bytes a multiple of 16).
 __device__ inline void prefetch_l2_bulk(const void *src, uint32_t bytes)
 {

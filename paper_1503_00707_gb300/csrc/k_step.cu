@@ -619,6 +619,10 @@ __global__ void __launch_bounds__(MAXT, 1) k_step(const StepParams p)
         if (cell >= 0) {
             // ================= phase 1: transport of cell j
             bool on = point(j);  // groups 4..7 of this cell are copied first
+            // the next cell's own values (an HBM stream) are prefetched into L2
+            // one cell ahead, so that their copies four groups later hit L2
+            const long long nxt = sm.slot[(j + 1) % NSL].cell;
+            const TS *pf = fin_p0 + (size_t)(nxt < 0 ? 0 : nxt) * NV;
             const TC invh = sl.invh;
             const Q4 cs = q_fma(q_splat(-invh), q_add(q_splat(dax + day), daz), q_splat((TC)1));
             TC aw[4], wz[2];
@@ -658,6 +662,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_step(const StepParams p)
                     }
                 }
                 cur[o] = fs;
+                if (active && nxt >= 0) prefetch_l2(pf + o * P);
                 // refill the stage, NST groups ahead: groups 4..7 of this cell,
                 // then groups 0..3 of the next one
                 if (o == NST) on = point(j + 1);
