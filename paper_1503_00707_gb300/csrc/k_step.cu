@@ -243,6 +243,29 @@ template <typename TS> __device__ inline void cp_piece(TS *dst, const TS *src, u
     else cp_async16(dst, src, dep);
 }
 
+// Warp totals of seven per-lane sums by reduce-scatter: each butterfly level
+// sends only the half of the sums that the partner keeps, so that three
+// levels leave lane l with the sum (l >> 2) over the eight lanes that differ
+// from it in bits 2-4, and two full levels finish it.  9 shuffles instead of
+// 35.  Returns, in lane l, the warp total of sum l >> 2 (l < 28).
+template <typename TC> __device__ inline TC warp_reduce7(const TC (&m)[7], int lane)
+{
+    TC a[4], b[2];
+    const bool h4 = lane & 16, h3 = lane & 8, h2 = lane & 4;
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+        const TC lo = m[i], hi = i < 3 ? m[4 + i] : (TC)0;
+        a[i] = (h4 ? hi : lo) + __shfl_xor_sync(0xffffffffu, h4 ? lo : hi, 16);
+    }
+#pragma unroll
+    for (int i = 0; i < 2; i++)
+        b[i] = (h3 ? a[2 + i] : a[i]) + __shfl_xor_sync(0xffffffffu, h3 ? a[i] : a[2 + i], 8);
+    TC c = (h2 ? b[1] : b[0]) + __shfl_xor_sync(0xffffffffu, h2 ? b[0] : b[1], 4);
+    c += __shfl_xor_sync(0xffffffffu, c, 2);
+    c += __shfl_xor_sync(0xffffffffu, c, 1);
+    return c;
+}
+
 template <typename T> __device__ inline uint32_t dep_of(const QV<T> &q)
 {
     if constexpr (sizeof(T) == 8) return (uint32_t)__double2loint(q.a);
@@ -697,12 +720,8 @@ __global__ void __launch_bounds__(MAXT, 1) k_step(const StepParams p)
             m[4] = jx * jx * m[0];
             m[5] = jy * jy * m[0];
             m[6] = q_sum(q_mul(q_make(jz2), T0));
-#pragma unroll
-            for (int k = 0; k < 7; k++) {
-#pragma unroll
-                for (int off = 16; off > 0; off >>= 1) m[k] += __shfl_down_sync(0xffffffffu, m[k], off);
-                if (lane == 0) sm.red[q][cw][k] = m[k];
-            }
+            const TC tot = warp_reduce7<TC>(m, lane);
+            if ((lane & 3) == 0 && lane < 28) sm.red[q][cw][lane >> 2] = tot;
         }
         if (ctid == 0) sm.cellp[q] = cell;
         bar_arrive_n(BAR_P + q, nbar);
