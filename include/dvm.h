@@ -55,7 +55,7 @@ typedef enum {
     DVM_ESTATE = -4,        /* call out of order                                */
     DVM_EUNSTABLE = -5,     /* non-finite or non-positive moments, singular 5x5 system, nu*dt > 1 */
     DVM_EBOUNDS = -6,       /* a table index outside its array (checked on the host) */
-    DVM_ETIMEOUT = -7,      /* reserved: a bounded device wait gave up          */
+    DVM_ETIMEOUT = -7,      /* a bounded device wait gave up (hard-sphere tile copies) */
     DVM_ENOTIMPL = -9       /* configuration not supported by this build        */
 } dvm_status;
 
