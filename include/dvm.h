@@ -26,7 +26,8 @@
  *     of order returns DVM_ESTATE.
  *   - Work is queued on the stream set by dvm_set_stream (default: the legacy
  *     default stream).  dvm_step synchronises that stream once per call to
- *     read the device status word; no kernel traps or spins.
+ *     read the device status word.  No kernel traps; every device wait is
+ *     bounded and reports DVM_ETIMEOUT.
  *   - A context is not thread-safe; use one context per host thread.
  *
  * Velocity ordering (Sec. 3.1 step 1): the Nv = nx*ny*nz nodes are stored as
@@ -288,6 +289,31 @@ int dvm_learned_pairs(dvm_ctx *ctx, float *a, float *o);
 /* Number of cells that fell back to the hard-sphere operator in the last
  * learned collision update (synchronises the stream). */
 int dvm_learned_fallback_count(dvm_ctx *ctx, int64_t *n);
+
+/* ---- Morton-range partition (Sec. 3.3) -----------------------------------
+ * The multi-GPU decomposition of the step: the Morton-ordered cells split into
+ * nparts contiguous ranges of equal work (every cell carries Nv velocities;
+ * the first ncells % nparts ranges hold one cell more), and the upwind halo
+ * of each range, the cells outside it that its advection stencils read. */
+
+/* Range [*c0, *c1) of part `part` and its halo: *nghost cells, written to
+ * ghosts (ascending global cell indices, capacity cap; may be NULL).  Host
+ * work, after dvm_build_tree; no device is touched.  DVM_EINVAL for
+ * nparts < 1, part outside [0, nparts), nparts > ncells or cap too small. */
+int dvm_partition_info(const dvm_ctx *ctx, int nparts, int part, int64_t *c0, int64_t *c1, int64_t *nghost,
+                       int64_t *ghosts, int64_t cap);
+
+/* nsteps steps of the stored f (transport and BGK collisions only) run as
+ * nparts partitions on the current device, the way separate GPUs would run
+ * them.  Each part holds its own cells, a copy of its halo and the inflow
+ * ghost in buffers of its own.  Before every step the halo rows are copied
+ * from their owners' buffers: this is the exchange a multi-GPU run makes
+ * between ranks.  Each part then runs the step kernel on its own cells.  The
+ * result (f and the step moments) is copied back into the context's state,
+ * bit-identical to dvm_step.  Allocates and frees the part buffers per call
+ * (about twice the f of the mesh).  Errors as dvm_step; DVM_ENOTIMPL for the
+ * hard-sphere and learned collisions. */
+int dvm_step_partitioned(dvm_ctx *ctx, int nparts, int nsteps, double dt);
 
 /* Size in bytes of the fixed device scratch used by dvm_hs_collide_noalloc. */
 #define DVM_HS_NOALLOC_SCRATCH_BYTES (64u << 20)

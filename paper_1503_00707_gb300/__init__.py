@@ -36,6 +36,7 @@ EXPORTS = [
     "dvm_hs_collide_noalloc", "dvm_learned_set_weights", "dvm_learned_get_weights",
     "dvm_mlp_forward", "dvm_mlp_loss_grad", "dvm_learned_train", "dvm_learned_configure",
     "dvm_learned_collide", "dvm_learned_pairs", "dvm_learned_fallback_count",
+    "dvm_partition_info", "dvm_step_partitioned",
 ]
 MLP_NPARAM = 164672
 HS_NOALLOC_SCRATCH_BYTES = 64 << 20
@@ -120,6 +121,8 @@ def lib():
             "dvm_learned_collide": [P, d, P, P, P, P, P, P],
             "dvm_learned_pairs": [P, P, P],
             "dvm_learned_fallback_count": [P, P],
+            "dvm_partition_info": [P, C.c_int, C.c_int, P, P, P, P, i64],
+            "dvm_step_partitioned": [P, C.c_int, C.c_int, d],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -316,6 +319,19 @@ class Solver:
         n = C.c_int64()
         self._chk(lib().dvm_learned_fallback_count(self._h, C.byref(n)))
         return n.value
+
+    # ---- Morton-range partition
+    def partition_info(self, nparts, part):
+        """(c0, c1, ghosts): the owned cell range of `part` and its halo."""
+        c0, c1, ng = C.c_int64(), C.c_int64(), C.c_int64()
+        self._chk(lib().dvm_partition_info(self._h, int(nparts), int(part), C.byref(c0), C.byref(c1),
+                                           C.byref(ng), None, 0))
+        g = np.zeros(ng.value, np.int64)
+        self._chk(lib().dvm_partition_info(self._h, int(nparts), int(part), None, None, None, _p(g), g.size))
+        return c0.value, c1.value, g
+
+    def step_partitioned(self, nparts, nsteps, dt):
+        self._chk(lib().dvm_step_partitioned(self._h, int(nparts), int(nsteps), float(dt)))
 
     # ---- state
     def get_f(self):

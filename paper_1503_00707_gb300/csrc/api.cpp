@@ -14,6 +14,7 @@
 #include "kernels.hpp"
 #include "learned.hpp"
 #include "mesh.hpp"
+#include "partition.hpp"
 #include "mlp.hpp"
 
 struct dvm_ctx {
@@ -180,23 +181,9 @@ int upload_mesh(dvm_ctx *c)
     std::vector<double> invh(nc);
     for (int64_t q = 0; q < nc; q++) invh[q] = std::ldexp(1.0, m.leaves[m.leaf_of_cell[q]].lev);
     // Device encoding of a stencil source: the cell to read (bits 0-27) and
-    // the sign-group flip applied to the group index (bits 28-30).  The
-    // inflow ghost is the extra cell `nc` that holds the freestream
-    // Maxwellian; outflow reads the cell itself; a specular wall reads the
-    // cell itself in the group mirrored along the face's axis.
-    std::vector<int32_t> enc(m.st_src.size());
-    for (int64_t q = 0; q < nc; q++)
-        for (int list = 0; list < 6; list++)
-            for (int e = 0; e < dvm::MAX_SRC; e++) {
-                const size_t k = ((size_t)q * 6 + list) * dvm::MAX_SRC + e;
-                const int32_t s0 = m.st_src[k];
-                int32_t v;
-                if (s0 >= 0) v = s0;
-                else if (s0 == dvm::SRC_INFLOW) v = (int32_t)nc;
-                else if (s0 == dvm::SRC_OUTFLOW) v = (int32_t)q;
-                else v = (int32_t)q | ((4 >> (list / 2)) << 28);
-                enc[k] = v;
-            }
+    // the sign-group flip applied to the group index (bits 28-30).
+    std::vector<int32_t> enc;
+    dvm::encode_stencils(m.st_src, nc, enc);
     if (nc >= (1 << 28)) return fail(c, DVM_ENOTIMPL, "more than 2^28 cells");
     int rc = cuda_check(c, cudaMemcpy(c->d_src, enc.data(), nc * 24 * sizeof(int32_t), cudaMemcpyHostToDevice), "copy stencils");
     if (rc) return rc;
@@ -812,6 +799,177 @@ int dvm_step(dvm_ctx *c, int nsteps, double dt)
         if (st & dvm::ST_SINGULAR) why += " singular correction system;";
         if (st & dvm::ST_NUDT) why += " relaxation factor above 1 (dt too large for Kn);";
         return fail(c, DVM_EUNSTABLE, "unstable step:" + why);
+    }
+    return DVM_OK;
+}
+
+int dvm_partition_info(const dvm_ctx *c, int nparts, int part, int64_t *c0, int64_t *c1, int64_t *nghost,
+                       int64_t *ghosts, int64_t cap)
+{
+    if (!c || nparts < 1 || part < 0 || part >= nparts) return DVM_EINVAL;
+    dvm_ctx *cc = const_cast<dvm_ctx *>(c);
+    if (c->state < 1) return fail(cc, DVM_ESTATE, "build the tree first");
+    const int64_t nc = ncells_of(c);
+    if (nparts > nc) return fail(cc, DVM_EINVAL, "more parts than cells");
+    std::vector<int32_t> enc;
+    dvm::encode_stencils(c->mesh.st_src, nc, enc);
+    std::vector<dvm::Part> parts;
+    dvm::partition_cells(nc, nparts, enc, c->mesh.st_cnt, parts);
+    const dvm::Part &pt = parts[part];
+    if (c0) *c0 = pt.c0;
+    if (c1) *c1 = pt.c1;
+    if (nghost) *nghost = (int64_t)pt.ghosts.size();
+    if (ghosts) {
+        if (cap < (int64_t)pt.ghosts.size()) return fail(cc, DVM_EINVAL, "ghost buffer too small");
+        std::copy(pt.ghosts.begin(), pt.ghosts.end(), ghosts);
+    }
+    return DVM_OK;
+}
+
+int dvm_step_partitioned(dvm_ctx *c, int nparts, int nsteps, double dt)
+{
+    if (!c || nsteps < 0 || nparts < 1) return DVM_EINVAL;
+    if (c->state < 3) return fail(c, DVM_ESTATE, "f is not set");
+    if (!(dt > 0.0) || !std::isfinite(dt)) return fail(c, DVM_EINVAL, "dt must be positive");
+    if (c->cfg.collision != DVM_COLL_BGK && c->cfg.collision != DVM_COLL_NONE)
+        return fail(c, DVM_ENOTIMPL, "the partitioned step runs transport and BGK only");
+    const int64_t nc = ncells_of(c);
+    if (nparts > nc) return fail(c, DVM_EINVAL, "more parts than cells");
+    const size_t es = elem_size(c->cfg.precision), tcs = tc_size(c->cfg.precision);
+    const int64_t row = (int64_t)c->nv * (int64_t)es;
+
+    std::vector<int32_t> enc;
+    dvm::encode_stencils(c->mesh.st_src, nc, enc);
+    std::vector<dvm::Part> parts;
+    dvm::partition_cells(nc, nparts, enc, c->mesh.st_cnt, parts);
+
+    // per part: two f buffers of (owned + ghosts + inflow ghost) rows and the
+    // stencils in local numbering; the weights, counts and 1/h are slices of
+    // the global arrays
+    struct Dev {
+        void *f[2] = {nullptr, nullptr};
+        int32_t *src = nullptr;
+        double *mom = nullptr;
+    };
+    std::vector<Dev> dev(nparts);
+    std::vector<void *> tmp;  // everything to free
+    auto alloc = [&](size_t bytes) {
+        void *q = dev_alloc(c, bytes);
+        if (q) tmp.push_back(q);
+        return q;
+    };
+    int rc = DVM_OK;
+    std::vector<int64_t> halo;  // {dst part, dst row, src part, src row}
+    for (int p = 0; p < nparts && !rc; p++) {
+        const dvm::Part &pt = parts[p];
+        const int64_t nloc = pt.c1 - pt.c0, ng = (int64_t)pt.ghosts.size(), rows = nloc + ng + 1;
+        Dev &d = dev[p];
+        d.f[0] = alloc((size_t)rows * row);
+        d.f[1] = alloc((size_t)rows * row);
+        d.src = static_cast<int32_t *>(alloc((size_t)nloc * 24 * sizeof(int32_t)));
+        d.mom = static_cast<double *>(alloc((size_t)nloc * 5 * sizeof(double)));
+        if (!d.f[0] || !d.f[1] || !d.src || !d.mom) {
+            rc = fail(c, DVM_ENOMEM, "device allocation (partitions)");
+            break;
+        }
+        std::vector<int32_t> local;
+        dvm::local_stencils(pt, nc, enc, local);
+        rc = cuda_check(c, cudaMemcpy(d.src, local.data(), local.size() * sizeof(int32_t), cudaMemcpyHostToDevice),
+                        "copy local stencils");
+        // owned rows and the inflow ghost row into the first buffer, the inflow
+        // ghost also into the second
+        const char *g = static_cast<const char *>(c->d_f[c->cur]);
+        if (!rc)
+            rc = cuda_check(c, cudaMemcpyAsync(d.f[0], g + pt.c0 * row, (size_t)nloc * row, cudaMemcpyDeviceToDevice,
+                                               c->stream), "scatter f");
+        for (int b = 0; b < 2 && !rc; b++)
+            rc = cuda_check(c, cudaMemcpyAsync(static_cast<char *>(d.f[b]) + (nloc + ng) * row, g + nc * row, row,
+                                               cudaMemcpyDeviceToDevice, c->stream), "inflow ghost");
+        for (int64_t k = 0; k < ng; k++) {
+            const int64_t s = pt.ghosts[k];
+            int q = 0;
+            while (parts[q].c1 <= s) q++;
+            halo.insert(halo.end(), {(int64_t)p, nloc + k, (int64_t)q, s - parts[q].c0});
+        }
+    }
+    // the two sets of current buffers (step parity) and the halo list
+    void **d_bufs = nullptr;
+    int64_t *d_halo = nullptr;
+    if (!rc) {
+        d_bufs = static_cast<void **>(alloc(2 * nparts * sizeof(void *)));
+        d_halo = static_cast<int64_t *>(alloc(std::max<size_t>(halo.size(), 4) * sizeof(int64_t)));
+        if (!d_bufs || !d_halo) rc = fail(c, DVM_ENOMEM, "device allocation (halo)");
+    }
+    if (!rc) {
+        std::vector<void *> hb(2 * nparts);
+        for (int p = 0; p < nparts; p++) {
+            hb[p] = dev[p].f[0];
+            hb[nparts + p] = dev[p].f[1];
+        }
+        rc = cuda_check(c, cudaMemcpy(d_bufs, hb.data(), hb.size() * sizeof(void *), cudaMemcpyHostToDevice), "buffers");
+        if (!rc && !halo.empty())
+            rc = cuda_check(c, cudaMemcpy(d_halo, halo.data(), halo.size() * sizeof(int64_t), cudaMemcpyHostToDevice),
+                            "halo list");
+    }
+
+    dvm::StepParams base{};
+    base.dim = c->mesh.spec.dim;
+    base.prec = c->cfg.precision;
+    base.coll = c->cfg.collision == DVM_COLL_BGK ? DVM_COLL_BGK : DVM_COLL_NONE;
+    base.nv = c->nv;
+    base.P = c->P;
+    for (int d = 0; d < 3; d++) { base.half[d] = c->half[d]; base.n[d] = c->n[d]; base.hv[d] = c->hv[d]; }
+    base.amag = c->d_amag;
+    base.amag_f = c->d_amag_f;
+    base.dt = dt;
+    base.kn = c->cfg.kn;
+    base.dV = c->dV;
+    base.status = c->d_status;
+    base.counter = c->d_counter;
+    base.stream = c->stream;
+    for (int s = 0; s < nsteps && !rc; s++) {
+        const int b = s & 1;
+        // the halo exchange: every ghost row from its owner's current buffer
+        rc = dvm::launch_copy_rows(d_bufs + b * nparts, d_halo, (int64_t)halo.size() / 4, row, c->stream);
+        if (rc) rc = fail(c, rc, "halo exchange launch failed");
+        for (int p = 0; p < nparts && !rc; p++) {
+            const dvm::Part &pt = parts[p];
+            dvm::StepParams q = base;
+            q.ncells = pt.c1 - pt.c0;
+            q.f_in = dev[p].f[b];
+            q.f_out = dev[p].f[1 - b];
+            q.st_src = dev[p].src;
+            q.st_w = static_cast<const char *>(c->d_w) + pt.c0 * 24 * tcs;
+            q.st_cnt = c->d_cnt + pt.c0 * 8;
+            q.inv_h = static_cast<const char *>(c->d_invh) + pt.c0 * tcs;
+            q.mom_out = dev[p].mom;
+            rc = cuda_check(c, cudaMemsetAsync(c->d_counter, 0, sizeof(unsigned long long), c->stream), "counter reset");
+            if (!rc) rc = dvm::launch_step(q);
+            if (rc && rc != DVM_ECUDA) rc = fail(c, rc, "step launch failed");
+        }
+    }
+    // owned rows and step moments back into the global state
+    const int fb = nsteps & 1;
+    char *g = static_cast<char *>(c->d_f[c->cur]);
+    for (int p = 0; p < nparts && !rc && nsteps > 0; p++) {
+        const dvm::Part &pt = parts[p];
+        const int64_t nloc = pt.c1 - pt.c0;
+        rc = cuda_check(c, cudaMemcpyAsync(g + pt.c0 * row, dev[p].f[fb], (size_t)nloc * row, cudaMemcpyDeviceToDevice,
+                                           c->stream), "gather f");
+        if (!rc)
+            rc = cuda_check(c, cudaMemcpyAsync(c->d_mom + pt.c0 * 5, dev[p].mom, (size_t)nloc * 5 * sizeof(double),
+                                               cudaMemcpyDeviceToDevice, c->stream), "gather moments");
+    }
+    int st = 0;
+    if (!rc) rc = cuda_check(c, cudaMemcpyAsync(&st, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "read status");
+    const int rs = cuda_check(c, cudaStreamSynchronize(c->stream), "partitioned step");
+    if (!rc) rc = rs;
+    for (void *q : tmp) dev_free(c, q);
+    if (rc) return rc;
+    c->have_step_moments = nsteps > 0 || c->have_step_moments;
+    if (st) {
+        cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream);
+        return fail(c, DVM_EUNSTABLE, "unstable step (non-positive moments, singular system or nu dt > 1)");
     }
     return DVM_OK;
 }

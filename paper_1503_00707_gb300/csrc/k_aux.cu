@@ -1,5 +1,6 @@
 // Auxiliary kernels outside the timed step: Maxwellian initialisation,
 // moments of the stored f, and precision conversions for host transfers.
+#include <algorithm>
 #include <cmath>
 
 #include "../../include/dvm.h"
@@ -110,7 +111,30 @@ int last_status()
     return cudaGetLastError() == cudaSuccess ? DVM_OK : DVM_ECUDA;
 }
 
+// Row copies between buffers: entry r of rows is {destination buffer, row,
+// source buffer, row}; rows are row_bytes long (a multiple of 16).
+__global__ void k_copy_rows(void *const *bufs, const int64_t *rows, int64_t n, int64_t row_bytes)
+{
+    const int64_t n16 = row_bytes / 16;
+    for (int64_t r = blockIdx.x; r < n; r += gridDim.x) {
+        const int64_t *e = rows + 4 * r;
+        const uint4 *src = reinterpret_cast<const uint4 *>(static_cast<const char *>(bufs[e[2]]) + e[3] * row_bytes);
+        uint4 *dst = reinterpret_cast<uint4 *>(static_cast<char *>(bufs[e[0]]) + e[1] * row_bytes);
+        for (int64_t i = threadIdx.x; i < n16; i += blockDim.x) dst[i] = src[i];
+    }
+}
+
 }  // namespace
+
+int launch_copy_rows(void *const *bufs, const int64_t *rows, int64_t n, int64_t row_bytes, cudaStream_t s)
+{
+    if (n <= 0) return DVM_OK;
+    if (row_bytes % 16 != 0) return DVM_EINVAL;
+    const unsigned grid = (unsigned)std::min<int64_t>(n, 1 << 16);
+    k_copy_rows<<<grid, 256, 0, s>>>(bufs, rows, n, row_bytes);
+    count_launch();
+    return cudaGetLastError() == cudaSuccess ? DVM_OK : DVM_ECUDA;
+}
 
 int launch_init_maxwellian(int prec, void *f, int64_t ncells, int nv, int nmix, const double *w,
                            const double *rho, const double *u, const double *T, const double *xi,

@@ -53,6 +53,10 @@ int launch_moments(int prec, const void *f, int64_t ncells, int nv, const double
 int launch_to_f64(int prec, const void *src, double *dst, int64_t count, cudaStream_t s);
 int launch_from_f64(int prec, const double *src, void *dst, int64_t count, cudaStream_t s);
 
+// Copies of whole rows (one cell's f) between buffers: rows [n][4] =
+// {destination buffer, row, source buffer, row} indexing bufs (device arrays).
+int launch_copy_rows(void *const *bufs, const int64_t *rows, int64_t n, int64_t row_bytes, cudaStream_t s);
+
 int64_t launches_issued();
 
 }  // namespace dvm
