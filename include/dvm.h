@@ -57,7 +57,7 @@ typedef enum {
     DVM_EUNSTABLE = -5,     /* non-finite or non-positive moments, singular 5x5 system, nu*dt > 1 */
     DVM_EBOUNDS = -6,       /* a table index outside its array (checked on the host) */
     DVM_ETIMEOUT = -7,      /* a bounded device wait gave up (hard-sphere tile copies) */
-    DVM_ENOTIMPL = -9       /* configuration not supported by this build        */
+    DVM_ENOTIMPL = -9       /* configuration not supported by the library         */
 } dvm_status;
 
 enum { DVM_F64 = 0, DVM_F32 = 1, DVM_BF16 = 2 };

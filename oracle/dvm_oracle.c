@@ -1250,7 +1250,7 @@ int orc_learned_apply(orc_problem *p, double dt, double kn, const double *knl, c
                       double kn_threshold, int32_t *used, double *q)
 {
     int64_t nc = p->ncells, nv = p->nv;
-    /* the plain operator for every cell (the fallback and the judge) */
+    /* the plain operator for every cell (the fallback, and the yardstick of the learned error) */
     double *qhs = NULL;
     if (p->hs_start) {
         double *f0 = (double *)malloc((size_t)(nc * nv) * sizeof(double));
