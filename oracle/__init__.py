@@ -74,6 +74,11 @@ def lib():
         L.orc_totals.argtypes = [P, P]
         L.orc_bgk.argtypes = [P, C.c_double, C.c_double, P]
         L.orc_hs_tables.argtypes = [P, C.c_int, C.c_uint64]
+        L.orc_hs_tables_lattice.argtypes = [P, C.c_int, C.c_uint64]
+        L.orc_korobov_a.argtypes = [C.c_int64]
+        L.orc_korobov_a.restype = C.c_int64
+        L.orc_trial_uniforms.argtypes = [C.c_int, C.c_uint64, C.c_int64, C.c_int64, C.c_int64, P]
+        L.orc_trial_uniforms.restype = None
         L.orc_hs_get_tables.argtypes = [P, P, P, P, P, P, P]
         L.orc_hs_collide.argtypes = [P, C.c_double, C.c_double, P, P, P]
         L.orc_step.argtypes = [P, C.c_int, C.c_double, C.c_int, C.c_double]
@@ -91,6 +96,16 @@ def lib():
 
 def _p(a):
     return None if a is None else a.ctypes.data
+
+
+def korobov_a(M):
+    return int(lib().orc_korobov_a(int(M)))
+
+
+def trial_uniforms(lattice, seed, i, k, M):
+    u = np.zeros(5)
+    lib().orc_trial_uniforms(int(lattice), int(seed), int(i), int(k), int(M), _p(u))
+    return u
 
 
 def threads():
@@ -261,8 +276,11 @@ class Problem:
             raise RuntimeError("BGK failed (non-positive moments or singular system)")
         return q
 
-    def hs_tables(self, trials, seed):
-        lib().orc_hs_tables(self._h, trials, seed)
+    def hs_tables(self, trials, seed, lattice=False):
+        if lattice:
+            assert lib().orc_hs_tables_lattice(self._h, trials, seed) == 0
+        else:
+            lib().orc_hs_tables(self._h, trials, seed)
 
     def hs_get_tables(self):
         nk = lib().orc_hs_nkept(self._h)

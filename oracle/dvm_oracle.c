@@ -896,7 +896,59 @@ static int nearest_node(const orc_problem *p, const double x[3], int32_t kk[3])
     return 1;
 }
 
-int orc_hs_tables(orc_problem *p, int trials, uint64_t seed)
+/* Korobov rank-1 lattice of M points in [0,1)^5 (the quadrature family of
+ * the paper's Ref. [5] for the collision integral): point k is
+ * frac(k (1, a, a^2, a^3, a^4 mod M) / M).  The multiplier a is the odd
+ * integer in [1, M) that maximises the smallest distance between two lattice
+ * points on the unit torus (squared distances in units of 1/M^2, integers),
+ * the smallest such a on ties. */
+int64_t orc_korobov_a(int64_t M)
+{
+    int64_t best = 1, bestd = -1;
+    for (int64_t a = 1; a < M; a += 2) {
+        int64_t z[5];
+        z[0] = 1;
+        for (int j = 1; j < 5; j++) z[j] = (z[j - 1] * a) % M;
+        int64_t dmin = INT64_MAX;
+        for (int64_t k = 1; k < M && dmin > bestd; k++) {
+            int64_t d2 = 0;
+            for (int j = 0; j < 5; j++) {
+                int64_t r = (k * z[j]) % M;
+                if (M - r < r) r = M - r;
+                d2 += r * r;
+            }
+            if (d2 < dmin) dmin = d2;
+        }
+        if (dmin > bestd) {
+            bestd = dmin;
+            best = a;
+        }
+    }
+    return best;
+}
+
+/* The uniform numbers of trial k of node i.  Random trials: three SplitMix64
+ * draws 3s, 3s+1, 3s+2 with s = i M + k (u[3], u[4] unused).  Lattice
+ * trials: the five coordinates of Korobov point k, shifted per node by the
+ * SplitMix64 draws 5i .. 5i+4 modulo 1 (a random shift of the lattice for
+ * every node). */
+static void trial_uniforms(int lattice, uint64_t seed, int64_t i, int64_t k, int64_t M, const int64_t z[5],
+                           double u[5])
+{
+    if (lattice) {
+        for (int j = 0; j < 5; j++) {
+            double t = (double)((k * z[j]) % M) / (double)M + unif53(seed, 5 * (uint64_t)i + (uint64_t)j);
+            if (t >= 1.0) t -= 1.0;
+            u[j] = t;
+        }
+    } else {
+        const uint64_t s = (uint64_t)i * (uint64_t)M + (uint64_t)k;
+        for (int j = 0; j < 3; j++) u[j] = unif53(seed, 3 * s + (uint64_t)j);
+        u[3] = u[4] = 0.0;
+    }
+}
+
+static int hs_tables(orc_problem *p, int trials, uint64_t seed, int lattice)
 {
     int64_t nv = p->nv;
     int64_t *idx = (int64_t *)malloc((size_t)nv * sizeof(int64_t));
@@ -911,21 +963,44 @@ int orc_hs_tables(orc_problem *p, int trials, uint64_t seed)
     p->hs_l = (int32_t *)malloc((size_t)cap * sizeof(int32_t));
     p->hs_m = (int32_t *)malloc((size_t)cap * sizeof(int32_t));
     p->hs_b = (double *)malloc((size_t)cap * sizeof(double));
+    int64_t z[5] = {1, 1, 1, 1, 1};
+    if (lattice) {
+        const int64_t a = orc_korobov_a(trials);
+        for (int j = 1; j < 5; j++) z[j] = (z[j - 1] * a) % trials;
+    }
     int64_t nk = 0, disc = 0;
     for (int64_t i = 0; i < nv; i++) {
         p->hs_start[i] = nk;
         const double *xa = &p->xi[3 * i];
         for (int k = 0; k < trials; k++) {
-            uint64_t s = (uint64_t)i * (uint64_t)trials + (uint64_t)k;
-            double u0 = unif53(seed, 3 * s), u1 = unif53(seed, 3 * s + 1), u2 = unif53(seed, 3 * s + 2);
-            int64_t gam = (int64_t)(u0 * (double)nv);
+            double u[5];
+            trial_uniforms(lattice, seed, i, k, trials, z, u);
+            /* partner: uniform over the nodes, as a storage index (random) or
+             * as the node of axis indices floor(u_d n_d) (lattice: smooth in
+             * the lattice coordinates); unit vector omega from the last two */
+            int64_t gam;
+            double uz, uphi;
+            if (lattice) {
+                int64_t kk[3];
+                for (int d = 0; d < 3; d++) {
+                    kk[d] = (int64_t)(u[d] * (double)p->n[d]);
+                    if (kk[d] > p->n[d] - 1) kk[d] = p->n[d] - 1;
+                }
+                gam = idx[(kk[0] * p->n[1] + kk[1]) * p->n[2] + kk[2]];
+                uz = u[3];
+                uphi = u[4];
+            } else {
+                gam = (int64_t)(u[0] * (double)nv);
+                uz = u[1];
+                uphi = u[2];
+            }
             const double *xb = &p->xi[3 * gam];
             double g2 = 0.0;
             for (int d = 0; d < 3; d++) g2 += (xa[d] - xb[d]) * (xa[d] - xb[d]);
             double gn = sqrt(g2);
-            double z = 2.0 * u1 - 1.0, phi = 2.0 * M_PI * u2;
-            double st = sqrt(fmax(0.0, 1.0 - z * z));
-            double w[3] = {st * cos(phi), st * sin(phi), z};
+            double zc = 2.0 * uz - 1.0, phi = 2.0 * M_PI * uphi;
+            double st = sqrt(fmax(0.0, 1.0 - zc * zc));
+            double w[3] = {st * cos(phi), st * sin(phi), zc};
             double xp[3], xq[3];
             for (int d = 0; d < 3; d++) {
                 double c = 0.5 * (xa[d] + xb[d]);
@@ -949,6 +1024,24 @@ int orc_hs_tables(orc_problem *p, int trials, uint64_t seed)
     p->hs_trials = trials;
     free(idx);
     return 0;
+}
+
+int orc_hs_tables(orc_problem *p, int trials, uint64_t seed) { return hs_tables(p, trials, seed, 0); }
+
+void orc_trial_uniforms(int lattice, uint64_t seed, int64_t i, int64_t k, int64_t M, double *u)
+{
+    int64_t z[5] = {1, 1, 1, 1, 1};
+    if (lattice) {
+        const int64_t a = orc_korobov_a(M);
+        for (int j = 1; j < 5; j++) z[j] = (z[j - 1] * a) % M;
+    }
+    trial_uniforms(lattice, seed, i, k, M, z, u);
+}
+
+int orc_hs_tables_lattice(orc_problem *p, int trials, uint64_t seed)
+{
+    if (trials < 2) return -1;
+    return hs_tables(p, trials, seed, 1);
 }
 
 int64_t orc_hs_nkept(const orc_problem *p) { return p->hs_nkept; }

@@ -95,6 +95,16 @@ int orc_bgk(orc_problem *p, double dt, double kn, double *q);
 
 /* Hard-sphere tables (Eqs. 3-5 with the seeded trial construction). */
 int orc_hs_tables(orc_problem *p, int trials, uint64_t seed);
+/* The same with the trials of each node on a 5-dimensional Korobov rank-1
+ * lattice of `trials` points (multiplier orc_korobov_a(trials)), shifted per
+ * node by seeded uniforms modulo 1: the partner is the node of axis indices
+ * floor(u_d n_d), d < 3, and omega comes from u[3], u[4]. */
+int orc_hs_tables_lattice(orc_problem *p, int trials, uint64_t seed);
+int64_t orc_korobov_a(int64_t M);
+/* The uniform numbers u[5] of trial k (of M) at node i, as the random
+ * (lattice = 0: u[0..2]) or lattice (lattice = 1: u[0..4]) construction
+ * draws them. */
+void orc_trial_uniforms(int lattice, uint64_t seed, int64_t i, int64_t k, int64_t M, double *u);
 int64_t orc_hs_nkept(const orc_problem *p);
 /* per node i: first kept trial index, count of kept trials (CSR) */
 int orc_hs_get_tables(const orc_problem *p, int64_t *start, int32_t *gam,

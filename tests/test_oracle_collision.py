@@ -238,3 +238,73 @@ def test_bgk_frequency_equals_hs_mean_frequency():
     lam = np.sum((f2 - f1) * (f1 - pert)) / np.sum((f1 - pert) ** 2)
     nu_bgk = (1 - lam) / dt
     assert abs(nu_bgk / nu_pairs - 1) < 0.01
+
+
+# ---------------------------------------------------------------- HS, lattice trials
+def test_korobov_lattice_is_stratified():
+    """A rank-1 lattice with generator (1, a, a^2, a^3, a^4) and a odd is, for
+    M a power of two, a permutation in every coordinate: the M points of a
+    node fall one in each interval [m/M, (m+1)/M) of every axis, whatever
+    the node's shift (the shift moves all points by the same amount modulo
+    1).  Random trials do not have this property."""
+    for M in (32, 64, 256):
+        a = O.korobov_a(M)
+        assert a % 2 == 1 and 1 <= a < M
+        for i in (0, 7, 123):
+            u = np.array([O.trial_uniforms(1, 20150303, i, k, M) for k in range(M)])
+            shift = u[0]  # point 0 is the shift itself
+            for j in range(5):
+                cell = np.floor(((u[:, j] - shift[j]) % 1.0) * M + 1e-9).astype(int) % M
+                assert sorted(cell.tolist()) == list(range(M)), (M, i, j)
+    u = np.array([O.trial_uniforms(0, 20150303, 0, k, 64) for k in range(64)])
+    assert len(set(np.floor(u[:, 0] * 64).astype(int).tolist())) < 64
+
+
+def test_korobov_multiplier_maximises_the_lattice_spacing():
+    """The multiplier's defining property, checked by brute force over every
+    odd a: no other a gives a larger smallest torus distance between points."""
+    M = 64
+
+    def spacing(a):
+        z = np.array([pow(a, j, M) for j in range(5)])
+        r = (np.arange(1, M)[:, None] * z[None, :]) % M
+        r = np.minimum(r, M - r)
+        return int((r ** 2).sum(axis=1).min())
+    best = max(spacing(a) for a in range(1, M, 2))
+    a = O.korobov_a(M)
+    assert spacing(a) == best
+    assert all(spacing(b) < best for b in range(1, a, 2))
+
+
+def _nubar(M, seed, lattice):
+    p = _homog(n=(12, 12, 12), vmax=6.0)
+    nc = p.ncells
+    p.init_maxwellian(np.ones(nc), np.ones(nc), np.zeros((nc, 3)), np.ones(nc))
+    p.hs_tables(M, seed, lattice=lattice)
+    f = p.get_f()[0].copy()
+    q, B, Cc = p.hs_collide(1e-6, 1.0, want=True)
+    return float(np.sum(f * B[0]) / np.sum(f))
+
+
+def test_lattice_trials_estimate_the_collision_frequency_better():
+    """sum f B / sum f of a unit Maxwellian estimates sqrt(8/pi).  Over six
+    lattice shifts the lattice estimate scatters less than six random-trial
+    estimates and lies closer to sqrt(8/pi) (the quasi-Monte Carlo gain the
+    Korobov construction is for)."""
+    target = math.sqrt(8 / math.pi)
+    M = 64
+    lat = np.array([_nubar(M, s, True) for s in range(1, 7)])
+    rnd = np.array([_nubar(M, s, False) for s in range(1, 7)])
+    assert lat.std() < 0.7 * rnd.std(), (lat.std(), rnd.std())
+    assert abs(lat.mean() - target) < abs(rnd.mean() - target)
+    assert abs(lat.mean() / target - 1) < 0.03
+
+
+def test_lattice_hs_collision_conserves():
+    p = _homog(n=(10, 10, 10), vmax=5.0)
+    _bimodal(p, w=0.35, a=1.4, T=0.5)
+    p.hs_tables(64, 20150303, lattice=True)
+    f = p.get_f()[0].copy()
+    q, B, Cc = p.hs_collide(1e-4, 0.02, want=True)
+    assert _conservation_residual(q, p.xi, p.dV) < 1e-12
+    assert float(np.sum(q[0] * np.log(f)) * p.dV) < 0
