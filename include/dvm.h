@@ -189,6 +189,16 @@ int dvm_dt_cfl(const dvm_ctx *ctx, double cfl, double *dt);
 /* Hard-sphere trial tables for Eqs. 3-5 (required for DVM_COLL_HS). */
 int dvm_set_collision_tables(dvm_ctx *ctx, int trials, uint64_t seed);
 
+/* The same tables with the trials of each node on a Korobov lattice, the
+ * quasi-Monte Carlo quadrature the paper cites for the collision integral
+ * (Sec. 3, Ref. [5]).  Point k of a rank-1 lattice of `trials` points in
+ * [0,1)^5 has generator (1, a, a^2, a^3, a^4) mod trials, where a is the odd
+ * multiplier with the largest lattice spacing.  The lattice is shifted per
+ * node by seeded uniforms (SplitMix64 draws 5i .. 5i+4) modulo 1.  The
+ * partner is the node with axis indices floor(u_d n_d), d < 3, and omega comes
+ * from u_3, u_4 as in the random tables.  Errors as dvm_set_collision_tables. */
+int dvm_set_collision_tables_lattice(dvm_ctx *ctx, int trials, uint64_t seed);
+
 /* Copy of the hard-sphere trial tables (node-major, entry e = i*trials + k,
  * nv*trials entries each): partner gamma, post-collision nodes l and m
  * (storage indices) and weight b = c (FP32; 0 for a discarded trial, whose

@@ -36,7 +36,7 @@ EXPORTS = [
     "dvm_hs_collide_noalloc", "dvm_learned_set_weights", "dvm_learned_get_weights",
     "dvm_mlp_forward", "dvm_mlp_loss_grad", "dvm_learned_train", "dvm_learned_configure",
     "dvm_learned_collide", "dvm_learned_pairs", "dvm_learned_fallback_count",
-    "dvm_partition_info", "dvm_step_partitioned",
+    "dvm_partition_info", "dvm_step_partitioned", "dvm_set_collision_tables_lattice",
 ]
 MLP_NPARAM = 164672
 HS_NOALLOC_SCRATCH_BYTES = 64 << 20
@@ -123,6 +123,7 @@ def lib():
             "dvm_learned_fallback_count": [P, P],
             "dvm_partition_info": [P, C.c_int, C.c_int, P, P, P, P, i64],
             "dvm_step_partitioned": [P, C.c_int, C.c_int, d],
+            "dvm_set_collision_tables_lattice": [P, C.c_int, C.c_uint64],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -240,8 +241,9 @@ class Solver:
         T = np.ascontiguousarray(np.asarray(T, np.float64).reshape(nc, k))
         self._chk(lib().dvm_init_maxwellian(self._h, k, _p(w), _p(rho), _p(u), _p(T)))
 
-    def set_collision_tables(self, trials, seed):
-        self._chk(lib().dvm_set_collision_tables(self._h, int(trials), int(seed)))
+    def set_collision_tables(self, trials, seed, lattice=False):
+        fn = lib().dvm_set_collision_tables_lattice if lattice else lib().dvm_set_collision_tables
+        self._chk(fn(self._h, int(trials), int(seed)))
 
     def collision_tables(self, trials):
         n = self.nv * trials

@@ -696,17 +696,24 @@ int dvm_dt_cfl(const dvm_ctx *c, double cfl, double *dt)
     return DVM_OK;
 }
 
-int dvm_set_collision_tables(dvm_ctx *c, int trials, uint64_t seed)
+static int set_tables(dvm_ctx *c, int trials, uint64_t seed, bool lattice)
 {
     if (!c || trials < 1) return DVM_EINVAL;
     if (c->state < 2) return fail(c, DVM_ESTATE, "set the velocity grid first");
     if (c->cfg.precision != DVM_F32) return fail(c, DVM_ENOTIMPL, "the hard-sphere operator runs on FP32 storage");
     std::string err;
-    int rc = dvm::hs_build(c->hs, c->n, c->lo, c->hv, c->xi, trials, seed, err,
+    int rc = dvm::hs_build(c->hs, c->n, c->lo, c->hv, c->xi, trials, seed, lattice, err,
                            [c](size_t b) { return dev_alloc(c, b); },
                            [c](void *p) { void *q = p; dev_free(c, q); });
     if (rc) return fail(c, rc, err);
     return DVM_OK;
+}
+
+int dvm_set_collision_tables(dvm_ctx *c, int trials, uint64_t seed) { return set_tables(c, trials, seed, false); }
+
+int dvm_set_collision_tables_lattice(dvm_ctx *c, int trials, uint64_t seed)
+{
+    return set_tables(c, trials, seed, true);
 }
 
 int dvm_get_collision_tables(const dvm_ctx *c, int32_t *gam, int32_t *l, int32_t *m, float *b, int64_t *discarded)

@@ -2,7 +2,12 @@
 //
 // For node i and trial k (stream index s = i*M + k, SplitMix64 draws 3s,
 // 3s+1, 3s+2): the partner gamma is uniform over the Nv nodes; the unit
-// vector omega has z = 2u - 1 and azimuth 2 pi u'.  The post-collision pair
+// vector omega has z = 2u - 1 and azimuth 2 pi u'.  The lattice variant (the
+// Korobov-grid quadrature the paper cites for the collision integral, Ref.
+// [5]) takes the five coordinates of point k of a rank-1 lattice with
+// generator (1, a, a^2, a^3, a^4) mod M, shifted per node by SplitMix64
+// draws 5i .. 5i+4 modulo 1: the partner is the node whose axis indices are
+// floor(u_d n_d), and omega comes from the last two coordinates.  The post-collision pair
 // xi' = c + |g| omega / 2, xi'_* = c - |g| omega / 2 around the pair's mean c
 // is snapped to the nearest nodes l, m (round half away from zero); a trial
 // whose l or m falls off the grid contributes nothing.  The weights
@@ -12,6 +17,8 @@
 // sqrt(8/pi) (mean free path Kn).
 #include "hs.hpp"
 
+#include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstring>
 
@@ -35,6 +42,32 @@ static double uniform01(uint64_t seed, uint64_t n)
     return std::ldexp((double)(splitmix64_at(seed, n) >> 11), -53);
 }
 
+int64_t korobov_multiplier(int64_t M)
+{
+    // the odd a whose lattice has the largest smallest torus distance between
+    // points (integer squared distances in units of 1/M^2), smallest a on ties
+    int64_t best = 1, best_sep = -1;
+    for (int64_t a = 1; a < M; a += 2) {
+        int64_t gen[5] = {1, 0, 0, 0, 0};
+        for (int j = 1; j < 5; j++) gen[j] = gen[j - 1] * a % M;
+        int64_t sep = INT64_MAX;
+        for (int64_t k = 1; k < M && sep > best_sep; k++) {
+            int64_t s2 = 0;
+            for (int j = 0; j < 5; j++) {
+                const int64_t r = k * gen[j] % M;
+                const int64_t t = std::min(r, M - r);
+                s2 += t * t;
+            }
+            sep = std::min(sep, s2);
+        }
+        if (sep > best_sep) {
+            best_sep = sep;
+            best = a;
+        }
+    }
+    return best;
+}
+
 void hs_free(HsTables &t, const DevFree &dfree)
 {
     if (t.d_idx) dfree(t.d_idx);
@@ -50,7 +83,7 @@ void hs_free(HsTables &t, const DevFree &dfree)
 }
 
 int hs_build(HsTables &t, const int n[3], const double lo[3], const double h[3],
-             const std::vector<double> &xi, int trials, uint64_t seed, std::string &err,
+             const std::vector<double> &xi, int trials, uint64_t seed, bool lattice, std::string &err,
              const DevAlloc &alloc, const DevFree &dfree)
 {
     hs_free(t, dfree);
@@ -72,12 +105,36 @@ int hs_build(HsTables &t, const int n[3], const double lo[3], const double h[3],
     t.host_idx.assign((size_t)trials * nv * 2, 0u);
     t.host_b.assign((size_t)trials * nv, 0.0f);
     t.discarded = 0;
+    int64_t gen[5] = {1, 0, 0, 0, 0};
+    if (lattice) {
+        const int64_t am = korobov_multiplier(trials);
+        for (int j = 1; j < 5; j++) gen[j] = gen[j - 1] * am % trials;
+    }
     for (int i = 0; i < nv; i++) {
         const double *a = &xi[3 * (size_t)i];
+        double shift[5] = {0, 0, 0, 0, 0};
+        if (lattice)
+            for (int j = 0; j < 5; j++) shift[j] = uniform01(seed, 5 * (uint64_t)i + (uint64_t)j);
         for (int k = 0; k < trials; k++) {
-            const uint64_t s = (uint64_t)i * (uint64_t)trials + (uint64_t)k;
-            const double u0 = uniform01(seed, 3 * s), u1 = uniform01(seed, 3 * s + 1), u2 = uniform01(seed, 3 * s + 2);
-            const int gam = (int)(u0 * (double)nv);
+            int gam;
+            double u1, u2;
+            if (lattice) {
+                double u[5];
+                for (int j = 0; j < 5; j++) {
+                    u[j] = (double)((int64_t)k * gen[j] % trials) / (double)trials + shift[j];
+                    if (u[j] >= 1.0) u[j] -= 1.0;
+                }
+                int ax[3];
+                for (int d = 0; d < 3; d++) ax[d] = std::min((int)(u[d] * (double)n[d]), n[d] - 1);
+                gam = where[((size_t)ax[0] * n[1] + ax[1]) * n[2] + ax[2]];
+                u1 = u[3];
+                u2 = u[4];
+            } else {
+                const uint64_t s = (uint64_t)i * (uint64_t)trials + (uint64_t)k;
+                gam = (int)(uniform01(seed, 3 * s) * (double)nv);
+                u1 = uniform01(seed, 3 * s + 1);
+                u2 = uniform01(seed, 3 * s + 2);
+            }
             const double *b = &xi[3 * (size_t)gam];
             double g2 = 0.0;
             for (int d = 0; d < 3; d++) g2 += (a[d] - b[d]) * (a[d] - b[d]);

@@ -34,9 +34,15 @@ using DevFree = std::function<void(void *)>;
 // Output n (0-based) of the SplitMix64 stream seeded with `seed`.
 uint64_t splitmix64_at(uint64_t seed, uint64_t n);
 
+// lattice = false: seeded random trials; true: trials on a shifted 5D
+// Korobov lattice (partner by axis indices, omega from the last two
+// coordinates).
 int hs_build(HsTables &t, const int n[3], const double lo[3], const double h[3],
-             const std::vector<double> &xi, int trials, uint64_t seed, std::string &err,
+             const std::vector<double> &xi, int trials, uint64_t seed, bool lattice, std::string &err,
              const DevAlloc &alloc, const DevFree &dfree);
+
+// Korobov multiplier of an M-point rank-1 lattice in five dimensions.
+int64_t korobov_multiplier(int64_t M);
 void hs_free(HsTables &t, const DevFree &dfree);
 
 // Per-cell scratch for ncells cells (B, C and the correction sums).

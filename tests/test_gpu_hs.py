@@ -28,12 +28,13 @@ def _homog_cfg(n=16, vmax=6.0, base=2):
     return c
 
 
-def test_tables_match_oracle():
+@pytest.mark.parametrize("lattice", [False, True])
+def test_tables_match_oracle(lattice):
     c = _homog_cfg(n=16)
     s, o = pair(c, init=False)
     M, seed = 64, 20150303
-    s.set_collision_tables(M, seed)
-    o.hs_tables(M, seed)
+    s.set_collision_tables(M, seed, lattice=lattice)
+    o.hs_tables(M, seed, lattice=lattice)
     gam, l, m, b, disc = s.collision_tables(M)
     start, og, ol, om, ob, odisc = o.hs_get_tables()
     assert disc == odisc
@@ -109,3 +110,19 @@ def test_hs_needs_tables_and_fp32():
     with pytest.raises(D.DvmError) as e:
         s2.set_collision_tables(64, 1)
     assert e.value.code == -9
+
+
+def test_lattice_tables_hs_step_matches_oracle():
+    """Hard-sphere steps with the Korobov-lattice trials: the same collision
+    operator with other tables, so the same parity bar as the random ones."""
+    c = _homog_cfg(n=16)
+    s, o = pair(c)
+    M = 64
+    s.set_collision_tables(M, 11, lattice=True)
+    o.hs_tables(M, 11, lattice=True)
+    dt = 2.5e-5
+    s.step(2, dt)
+    o.step(2, dt, O.COLL_HS, c["kn"])
+    assert rel_linf(s.get_f(), o.get_f()) < 2e-5
+    err = field_errors(s.moments(), o.moments())
+    assert max(err.values()) < 1e-5, err
