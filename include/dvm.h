@@ -126,6 +126,16 @@ int dvm_build_tree(dvm_ctx *ctx, const dvm_tree_spec *spec);
  * changes).  f is discarded. */
 int dvm_refine(dvm_ctx *ctx, const uint8_t *flag, int64_t nleaves);
 
+/* dvm_refine with f carried over (Sec. 3.1: the mesh adapts while the
+ * solution runs; the stencil tables are rebuilt).  Every new cell takes the
+ * f of the old cell whose leaf contains it: a split cell's children start with
+ * the parent's distribution (piecewise-constant injection), which conserves
+ * mass, momentum and energy exactly.  A new fluid cell inside an old solid
+ * leaf, which can appear where the wall is refined, takes the freestream
+ * Maxwellian.  Needs f set (DVM_ESTATE otherwise).  Allocates new f
+ * buffers; the step moments are invalidated. */
+int dvm_refine_project(dvm_ctx *ctx, const uint8_t *flag, int64_t nleaves);
+
 /* Sizes: leaves (including solid ones), cells (non-solid leaves), interior
  * faces, boundary faces, velocity nodes (0 before set_velocity_grid).  Any
  * pointer may be NULL. */

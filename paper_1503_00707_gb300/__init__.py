@@ -37,6 +37,7 @@ EXPORTS = [
     "dvm_mlp_forward", "dvm_mlp_loss_grad", "dvm_learned_train", "dvm_learned_configure",
     "dvm_learned_collide", "dvm_learned_pairs", "dvm_learned_fallback_count",
     "dvm_partition_info", "dvm_step_partitioned", "dvm_set_collision_tables_lattice",
+    "dvm_refine_project",
 ]
 MLP_NPARAM = 164672
 HS_NOALLOC_SCRATCH_BYTES = 64 << 20
@@ -124,6 +125,7 @@ def lib():
             "dvm_partition_info": [P, C.c_int, C.c_int, P, P, P, P, i64],
             "dvm_step_partitioned": [P, C.c_int, C.c_int, d],
             "dvm_set_collision_tables_lattice": [P, C.c_int, C.c_uint64],
+            "dvm_refine_project": [P, P, i64],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -184,6 +186,12 @@ class Solver:
     def refine(self, flags):
         flags = np.ascontiguousarray(flags, dtype=np.uint8)
         self._chk(lib().dvm_refine(self._h, _p(flags), len(flags)))
+        self.counts()
+
+    def refine_project(self, flags):
+        """Refine and carry f over (children take their parent's f)."""
+        flags = np.ascontiguousarray(flags, dtype=np.uint8)
+        self._chk(lib().dvm_refine_project(self._h, _p(flags), len(flags)))
         self.counts()
 
     def counts(self):

@@ -417,6 +417,67 @@ int dvm_refine(dvm_ctx *c, const uint8_t *flag, int64_t n)
     return after_mesh(c);
 }
 
+int dvm_refine_project(dvm_ctx *c, const uint8_t *flag, int64_t n)
+{
+    if (!c || !flag) return DVM_EINVAL;
+    if (c->state < 3) return fail(c, DVM_ESTATE, "f is not set (dvm_refine changes the mesh alone)");
+    // the old mesh's leaves and the device row of each old cell
+    const dvm::Mesh old = c->mesh;
+    const int64_t onc = ncells_of(c);
+    std::string err;
+    int rc = dvm::refine_mesh(c->mesh, flag, n, err);
+    if (rc) return fail(c, rc, err);
+    // keep the old f buffer (cells and inflow ghost) past the rebuild
+    void *oldf = c->d_f[c->cur];
+    c->d_f[c->cur] = nullptr;
+    const int64_t row = (int64_t)c->nv * (int64_t)elem_size(c->cfg.precision);
+    rc = after_mesh(c);
+    // new cell i takes the old cell whose leaf contains it (refinement only
+    // splits, so one does); a new fluid cell inside an old solid leaf takes
+    // the freestream (the old inflow ghost row)
+    std::vector<int64_t> rows;
+    const dvm::Mesh &m = c->mesh;
+    if (!rc) {
+        const int64_t nnc = ncells_of(c);
+        rows.reserve(4 * (size_t)nnc);
+        size_t o = 0;
+        for (int64_t q = 0; q < nnc; q++) {
+            const dvm::Leaf &x = m.leaves[m.leaf_of_cell[q]];
+            // old leaves are in Morton order and tile the domain: the containing
+            // one is the last with key <= the new leaf's key
+            while (o + 1 < old.leaves.size() && old.leaves[o + 1].key <= x.key) o++;
+            const dvm::Leaf &y = old.leaves[o];
+            bool inside = y.lev <= x.lev;
+            for (int d = 0; d < m.spec.dim && inside; d++) inside = (x.i[d] >> (x.lev - y.lev)) == y.i[d];
+            const int64_t oc = inside ? old.cell_of_leaf[o] : -1;
+            rows.insert(rows.end(), {0, q, 1, oc >= 0 ? oc : onc});
+        }
+    }
+    void **d_bufs = nullptr;
+    int64_t *d_rows = nullptr;
+    if (!rc) {
+        d_bufs = static_cast<void **>(dev_alloc(c, 2 * sizeof(void *)));
+        d_rows = static_cast<int64_t *>(dev_alloc(c, std::max<size_t>(rows.size(), 4) * sizeof(int64_t)));
+        if (!d_bufs || !d_rows) rc = fail(c, DVM_ENOMEM, "device allocation (projection)");
+    }
+    if (!rc) {
+        void *hb[2] = {c->d_f[c->cur], oldf};
+        rc = cuda_check(c, cudaMemcpy(d_bufs, hb, sizeof hb, cudaMemcpyHostToDevice), "projection buffers");
+        if (!rc) rc = cuda_check(c, cudaMemcpy(d_rows, rows.data(), rows.size() * sizeof(int64_t), cudaMemcpyHostToDevice),
+                                 "projection rows");
+        if (!rc) rc = dvm::launch_copy_rows(d_bufs, d_rows, (int64_t)rows.size() / 4, row, c->stream);
+        if (!rc) rc = cuda_check(c, cudaStreamSynchronize(c->stream), "projection");
+    }
+    void *p1 = d_bufs, *p2 = d_rows;
+    dev_free(c, p1);
+    dev_free(c, p2);
+    dev_free(c, oldf);
+    if (rc) return rc;
+    c->state = 3;
+    c->have_step_moments = false;
+    return DVM_OK;
+}
+
 int dvm_get_counts(const dvm_ctx *c, int64_t *nleaves, int64_t *ncells, int64_t *nfaces, int64_t *nbfaces, int64_t *nv)
 {
     if (!c) return DVM_EINVAL;
