@@ -16,6 +16,7 @@ from . import build as _build
 BC_PERIODIC, BC_INFLOW, BC_OUTFLOW, BC_WALL = 0, 1, 2, 3
 PRED_NONE, PRED_BALL, PRED_SHELL = 0, 1, 2
 COLL_NONE, COLL_BGK, COLL_HS = 0, 1, 2
+COLL_BGK_ENTROPIC = 4
 
 
 class TreeSpec(C.Structure):
@@ -73,6 +74,7 @@ def lib():
         L.orc_moments.argtypes = [P, P, P, P]
         L.orc_totals.argtypes = [P, P]
         L.orc_bgk.argtypes = [P, C.c_double, C.c_double, P]
+        L.orc_bgk_entropic.argtypes = [P, C.c_double, C.c_double, P]
         L.orc_hs_tables.argtypes = [P, C.c_int, C.c_uint64]
         L.orc_hs_tables_lattice.argtypes = [P, C.c_int, C.c_uint64]
         L.orc_korobov_a.argtypes = [C.c_int64]
@@ -274,6 +276,12 @@ class Problem:
         q = np.zeros((self.ncells, self.nv)) if want_q else None
         if lib().orc_bgk(self._h, dt, kn, _p(q)):
             raise RuntimeError("BGK failed (non-positive moments or singular system)")
+        return q
+
+    def bgk_entropic(self, dt, kn, want_q=False):
+        q = np.zeros((self.ncells, self.nv)) if want_q else None
+        if lib().orc_bgk_entropic(self._h, dt, kn, _p(q)):
+            raise RuntimeError("entropic BGK failed (non-positive moments or no Newton convergence)")
         return q
 
     def hs_tables(self, trials, seed, lattice=False):

@@ -876,6 +876,76 @@ int orc_bgk(orc_problem *p, double dt, double kn, double *q)
     return err ? -1 : 0;
 }
 
+/* Entropic BGK (the discrete entropic equilibrium, a reading of the
+ * correction of Sec. 3.2 that keeps the H-theorem exact): the target is
+ * E = exp(a . psi) with psi = (1, xi, |xi|^2), the five multipliers a chosen
+ * so that sum psi E dV equals sum psi f dV; E minimises sum E ln E dV under
+ * those moments.  Newton's method from the continuous Maxwellian's
+ * multipliers (a0 = ln(rho (2 pi T)^(-3/2)) - |u|^2/(2T), a_d = u_d/T,
+ * a4 = -1/(2T)), every sum over all nodes, until each moment defect is below
+ * 1e-14 of its scale.  Then f <- f + dt nu (E - f), nu as for BGK. */
+int orc_bgk_entropic(orc_problem *p, double dt, double kn, double *q)
+{
+    int64_t nv = p->nv;
+    int err = 0;
+#pragma omp parallel for schedule(dynamic, 16) reduction(| : err)
+    for (int64_t c = 0; c < p->ncells; c++) {
+        double *f = &p->f[c * nv];
+        double rho, u[3], T;
+        cell_moments(p, f, &rho, u, &T);
+        if (!(rho > 0.0) || !(T > 0.0)) { err = 1; continue; }
+        double m[5] = {0}, scale[5] = {0};
+        for (int64_t v = 0; v < nv; v++) {
+            double ps[5];
+            psi5(&p->xi[3 * v], ps);
+            for (int r = 0; r < 5; r++) {
+                m[r] += ps[r] * f[v] * p->dV;
+                scale[r] += fabs(ps[r]) * fabs(f[v]) * p->dV;
+            }
+        }
+        double a[5];
+        const double u2 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+        a[0] = log(rho / pow(2.0 * M_PI * T, 1.5)) - u2 / (2.0 * T);
+        for (int d = 0; d < 3; d++) a[1 + d] = u[d] / T;
+        a[4] = -1.0 / (2.0 * T);
+        int ok = 0;
+        for (int it = 0; it < 50 && !ok; it++) {
+            double G[5] = {0}, J[25] = {0}, da[5];
+            for (int64_t v = 0; v < nv; v++) {
+                double ps[5];
+                psi5(&p->xi[3 * v], ps);
+                double e = 0.0;
+                for (int r = 0; r < 5; r++) e += a[r] * ps[r];
+                e = exp(e) * p->dV;
+                for (int r = 0; r < 5; r++) {
+                    G[r] += ps[r] * e;
+                    for (int t = 0; t < 5; t++) J[r * 5 + t] += ps[r] * ps[t] * e;
+                }
+            }
+            double worst = 0.0;
+            for (int r = 0; r < 5; r++) {
+                G[r] -= m[r];
+                worst = fmax(worst, fabs(G[r]) / scale[r]);
+            }
+            if (worst < 1e-14) { ok = 1; break; }
+            if (orc_solve(5, J, G, da)) break;
+            for (int r = 0; r < 5; r++) a[r] -= da[r];
+        }
+        if (!ok) { err = 1; continue; }
+        double nu = sqrt(8.0 / M_PI) * rho * sqrt(T) / kn;
+        for (int64_t v = 0; v < nv; v++) {
+            double ps[5];
+            psi5(&p->xi[3 * v], ps);
+            double e = 0.0;
+            for (int r = 0; r < 5; r++) e += a[r] * ps[r];
+            double Q = nu * (exp(e) - f[v]);
+            if (q) q[c * nv + v] = Q;
+            f[v] += dt * Q;
+        }
+    }
+    return err ? -1 : 0;
+}
+
 /* ------------------------------------------------------------------------ */
 /* Hard-sphere trials.  For node i and trial k the stream index is i*M + k
  * and draws 3s, 3s+1, 3s+2 give the partner gamma (uniform over the nodes)
@@ -1117,6 +1187,7 @@ int orc_step(orc_problem *p, int nsteps, double dt, int coll, double kn)
         if (orc_transport(p, dt)) return -1;
         if (coll == 1 && orc_bgk(p, dt, kn, NULL)) return -2;
         if (coll == 2 && orc_hs_collide(p, dt, kn, NULL, NULL, NULL)) return -3;
+        if (coll == 4 && orc_bgk_entropic(p, dt, kn, NULL)) return -4;
     }
     return 0;
 }

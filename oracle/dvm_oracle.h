@@ -92,6 +92,10 @@ int orc_totals(const orc_problem *p, double out[5]);
 /* Conservative BGK relaxation of the stored f (forward Euler).  If q is
  * non-null it receives the collision term nu (M~ - f) per element. */
 int orc_bgk(orc_problem *p, double dt, double kn, double *q);
+/* Entropic BGK: target exp(a . psi), psi = (1, xi, |xi|^2), with the five
+ * multipliers from Newton's method so that its discrete moments equal those
+ * of f (the discrete entropic equilibrium); then the same relaxation. */
+int orc_bgk_entropic(orc_problem *p, double dt, double kn, double *q);
 
 /* Hard-sphere tables (Eqs. 3-5 with the seeded trial construction). */
 int orc_hs_tables(orc_problem *p, int trials, uint64_t seed);
@@ -115,7 +119,7 @@ int orc_hs_collide(orc_problem *p, double dt, double kn, double *q,
                    double *Bout, double *Cout);
 
 /* Full steps: transport, then collision on f* (Lie splitting).
- * coll: 0 none, 1 BGK, 2 hard sphere. */
+ * coll: 0 none, 1 BGK, 2 hard sphere, 4 entropic BGK. */
 int orc_step(orc_problem *p, int nsteps, double dt, int coll, double kn);
 
 /* ---- local Knudsen number (continuum-breakdown sensor, Sec. 2.3, Sec. 3.4) ----

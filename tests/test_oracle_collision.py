@@ -308,3 +308,75 @@ def test_lattice_hs_collision_conserves():
     q, B, Cc = p.hs_collide(1e-4, 0.02, want=True)
     assert _conservation_residual(q, p.xi, p.dV) < 1e-12
     assert float(np.sum(q[0] * np.log(f)) * p.dV) < 0
+
+
+# ---------------------------------------------------------------- entropic BGK
+def _entropy(f, dV):
+    return float(np.sum(f * np.log(f)) * dV)
+
+
+def test_entropic_bgk_conserves_and_is_exponential_of_a_quadratic():
+    """The entropic target has the moments of f (conservation of the
+    collision term to 1e-12) and its logarithm is a quadratic in xi with an
+    isotropic square term, the form of the discrete entropic equilibrium."""
+    p = _homog(n=(12, 12, 12), vmax=6.0)
+    _bimodal(p, w=0.35, a=1.4, T=0.5)
+    f = p.get_f()[0].copy()
+    dt, kn = 1e-3, 1.0
+    q = p.bgk_entropic(dt, kn, want_q=True)
+    assert _conservation_residual(q, p.xi, p.dV) < 1e-12
+    # recover E from the step: f1 = f + dt nu (E - f)
+    r, u, T = p.moments()
+    nu = math.sqrt(8 / math.pi) * r[0] * math.sqrt(T[0]) / kn
+    E = f + q[0] / nu
+    X = _psi(p.xi)
+    coef, res, *_ = np.linalg.lstsq(X, np.log(E), rcond=None)
+    assert np.max(np.abs(X @ coef - np.log(E))) < 1e-9
+    assert coef[4] < 0
+
+
+def test_entropic_bgk_fixed_point_and_monotone_entropy():
+    """The entropic equilibrium is a fixed point to rounding, and the
+    homogeneous relaxation towards it decreases the entropy H = sum f ln f dV
+    at every step (exactly: E minimises H under the conserved moments and the
+    update is a convex combination), where the polynomial-corrected target
+    only keeps it to O(d^2)."""
+    p = _homog(n=(12, 12, 12), vmax=6.0)
+    _bimodal(p, w=0.3, a=1.6, T=0.4)
+    dt, kn = 2e-3, 0.05
+    H = [_entropy(p.get_f()[0], p.dV)]
+    for _ in range(40):
+        p.bgk_entropic(dt, kn)
+        H.append(_entropy(p.get_f()[0], p.dV))
+    dH = np.diff(H)
+    assert np.all(dH <= 1e-13 * abs(H[0])), dH.max()
+    assert H[-1] < H[0]
+    # at the end f is (nearly) its own equilibrium: one more step moves it
+    # only by the remaining distance, and an exact equilibrium not at all
+    f = p.get_f()[0].copy()
+    q = p.bgk_entropic(dt, kn, want_q=True)
+    r, u, T = p.moments()
+    nu = math.sqrt(8 / math.pi) * r[0] * math.sqrt(T[0]) / kn
+    E = f + q[0] / nu
+    p.set_f(np.tile(E, (p.ncells, 1)))
+    q2 = p.bgk_entropic(dt, kn, want_q=True)
+    assert np.max(np.abs(q2[0])) < 1e-12 * nu * np.max(E)
+
+
+def test_entropic_equilibrium_has_least_entropy():
+    """Among distributions with the same discrete moments, the entropic
+    equilibrium has the least H: below the polynomial-corrected discrete
+    Maxwellian of the conservative BGK."""
+    p = _homog(n=(10, 10, 10), vmax=5.0)
+    _bimodal(p, w=0.35, a=1.4, T=0.5)
+    f = p.get_f()[0].copy()
+    r, u, T = p.moments()
+    kn = 1.0
+    nu = math.sqrt(8 / math.pi) * r[0] * math.sqrt(T[0]) / kn
+    E = f + p.bgk_entropic(1e-6, kn, want_q=True)[0] / nu
+    p.set_f(np.tile(f, (p.ncells, 1)))
+    Mp = f + p.bgk(1e-6, kn, want_q=True)[0] / nu
+    assert np.all(E > 0) and np.all(Mp > 0)
+    assert _entropy(E, p.dV) < _entropy(Mp, p.dV)
+    X = _psi(p.xi)
+    assert np.allclose(E @ X, Mp @ X, rtol=1e-11, atol=1e-14)
