@@ -45,6 +45,9 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--config", default="c3_sphere_m5")
     ap.add_argument("--precision", choices=["f32", "bf16"], default="f32")
+    ap.add_argument("--collision", choices=["bgk", "entropic"], default="bgk",
+                    help="BGK towards the corrected discrete Maxwellian (default) or the discrete "
+                         "entropic equilibrium")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -62,11 +65,12 @@ def dist_env():
             int(os.environ.get("WORLD_SIZE", 1)))
 
 
-def workload_desc(name, cfg, ncells, nv, prec):
+def workload_desc(name, cfg, ncells, nv, prec, collision="bgk"):
     return ("%s: %dD octree levels %d-%d around a sphere r=%g (%d kinetic cells), %d^3 velocities "
-            "on [%g,%g]^3, Mach %.1f inflow, outflow, specular wall, BGK Kn=%g, %s storage"
+            "on [%g,%g]^3, Mach %.1f inflow, outflow, specular wall, %s Kn=%g, %s storage"
             % (name, cfg["dim"], cfg["base_level"], cfg["max_level"], cfg["r"], ncells, cfg["n"][0],
-               cfg["lo"][0], cfg["hi"][0], cfg["fs_u"][0] / math.sqrt(W.GAMMA), cfg["kn"], prec))
+               cfg["lo"][0], cfg["hi"][0], cfg["fs_u"][0] / math.sqrt(W.GAMMA),
+               "entropic BGK" if collision == "entropic" else "BGK", cfg["kn"], prec))
 
 
 # ---------------------------------------------------------------- clocks
@@ -127,7 +131,7 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------- oracle leg
-def oracle_rate(steps, warmup=0, threads=None):
+def oracle_rate(steps, warmup=0, threads=None, collision="bgk"):
     """FP64 oracle on the 17.7k-cell tree of the same Mach-5 sphere flow with the
     same 24^3 velocity grid: returns (updates/s, cores, sample text, seconds)."""
     import oracle as O
@@ -140,14 +144,16 @@ def oracle_rate(steps, warmup=0, threads=None):
     xyz, _ = o.centres()
     o.init_maxwellian(*W.initial_state(c, xyz))
     dt = o.dt_cfl(c["cfl"])
+    coll = O.COLL_BGK_ENTROPIC if collision == "entropic" else O.COLL_BGK
     if warmup:
-        o.step(warmup, dt, O.COLL_BGK, c["kn"])
+        o.step(warmup, dt, coll, c["kn"])
     t0 = time.perf_counter()
-    o.step(steps, dt, O.COLL_BGK, c["kn"])
+    o.step(steps, dt, coll, c["kn"])
     el = time.perf_counter() - t0
     cores = O.threads()
     sample = ("%d step(s) of the Mach-5 sphere flow on the %s tree (%d cells x %d velocities, "
-              "FP64, BGK), OpenMP over cells" % (steps, CPU_SAMPLE_CONFIG, o.ncells, o.nv))
+              "FP64, %s), OpenMP over cells" % (steps, CPU_SAMPLE_CONFIG, o.ncells, o.nv,
+                                             "entropic BGK" if collision == "entropic" else "BGK"))
     return o.ncells * o.nv * steps / el, cores, sample, el
 
 
@@ -155,14 +161,15 @@ def run_reference(args):
     rank, _, world = dist_env()
     if rank != 0:
         return 0
-    rate, cores, sample, el = oracle_rate(args.steps, warmup=args.warmup)
+    rate, cores, sample, el = oracle_rate(args.steps, warmup=args.warmup, collision=args.collision)
     cfg = W.CONFIGS[args.config]
     line = {
         "impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": workload_desc(args.config, cfg, -1, cfg["n"][0] ** 3, args.precision),
+        "config": {"workload": workload_desc(args.config, cfg, -1, cfg["n"][0] ** 3, args.precision,
+                                             args.collision),
                    "reference_sample": sample, "parallelism": "host cores"},
         "cpu_baseline": {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -335,13 +342,14 @@ def run_ours(args):
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        rate, cores, sample, _ = oracle_rate(1)
+        rate, cores, sample, _ = oracle_rate(1, collision=args.collision)
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
 
     cfg = W.CONFIGS[args.config]
     prec = {"f32": D.F32, "bf16": D.BF16}[args.precision]
     stream = torch.cuda.Stream()
-    s = D.solver_from_config(cfg, prec, D.COLL_BGK, stream=stream)
+    coll = D.COLL_BGK_ENTROPIC if args.collision == "entropic" else D.COLL_BGK
+    s = D.solver_from_config(cfg, prec, coll, stream=stream)
     xyz, _ = s.centres()
     s.init_maxwellian(*W.initial_state(cfg, xyz))
     dt = s.dt_cfl(cfg["cfl"])
@@ -368,7 +376,7 @@ def run_ours(args):
     per_launch_s = ms / 1e3 / args.steps
     peak, peak_kind = _peaks()
     achieved = bytes_per_update * ncells * nv / per_launch_s / 1e9
-    key = "k_step_bgk_%s_%s" % (args.config, args.precision)
+    key = "k_step_%s_%s_%s" % (args.collision, args.config, args.precision)
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": _profiled_traffic("k_step.cu", key), "peak_source": peak_kind,
             "algorithmic_bytes_per_update": bytes_per_update}
@@ -414,7 +422,7 @@ def run_ours(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": workload_desc(args.config, cfg, ncells, nv, args.precision),
+            "config": {"workload": workload_desc(args.config, cfg, ncells, nv, args.precision, args.collision),
                        "cells": ncells, "velocities": nv, "f_values": ncells * nv,
                        "storage": args.precision, "parallelism": "replicas" if world > 1 else "single GPU",
                        "l2": "inputs larger than L2 (f is %.1f GB)" % f_gb},

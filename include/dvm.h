@@ -61,7 +61,21 @@ typedef enum {
 } dvm_status;
 
 enum { DVM_F64 = 0, DVM_F32 = 1, DVM_BF16 = 2 };
-enum { DVM_COLL_NONE = 0, DVM_COLL_BGK = 1, DVM_COLL_HS = 2, DVM_COLL_LEARNED = 3 };
+/* Collision update applied after transport (see dvm_step):
+ *   DVM_COLL_NONE          free molecular flow (transport only);
+ *   DVM_COLL_BGK           BGK relaxation (Sec. 4) towards the discrete
+ *                          Maxwellian times a five-coefficient correction
+ *                          polynomial that restores the moments of f;
+ *   DVM_COLL_HS            the hard-sphere collision integral, Eqs. 3-6;
+ *   DVM_COLL_LEARNED       the learned operator (dvm_set_mlp), gated by the
+ *                          local Knudsen number, falling back to Eqs. 3-6;
+ *   DVM_COLL_BGK_ENTROPIC  BGK relaxation towards the discrete entropic
+ *                          equilibrium exp(a . (1, xi, |xi|^2)) whose moments
+ *                          on the grid equal those of f (Newton's method on a,
+ *                          started from the Maxwellian; the last step's
+ *                          correction is applied as the polynomial, so the
+ *                          moments stay exact to the solve). */
+enum { DVM_COLL_NONE = 0, DVM_COLL_BGK = 1, DVM_COLL_HS = 2, DVM_COLL_LEARNED = 3, DVM_COLL_BGK_ENTROPIC = 4 };
 enum { DVM_BC_PERIODIC = 0, DVM_BC_INFLOW = 1, DVM_BC_OUTFLOW = 2, DVM_BC_WALL = 3 };
 enum { DVM_PRED_NONE = 0, DVM_PRED_BALL = 1, DVM_PRED_SHELL = 2 };
 
@@ -219,8 +233,8 @@ int dvm_get_collision_tables(const dvm_ctx *ctx, int32_t *gam, int32_t *l, int32
 
 /* nsteps explicit steps of size dt: transport (Eq. 2), moments of f*, then
  * the collision update on f* (Lie splitting): BGK relaxation towards the
- * conservatively corrected discrete Maxwellian, or Eqs. 3-6, with forward
- * Euler.  Returns DVM_EUNSTABLE if any cell met a non-positive density or
+ * conservatively corrected discrete Maxwellian or the discrete entropic
+ * equilibrium, or Eqs. 3-6, with forward Euler.  Returns DVM_EUNSTABLE if any cell met a non-positive density or
  * temperature, a singular correction system or nu*dt > 1. */
 int dvm_step(dvm_ctx *ctx, int nsteps, double dt);
 

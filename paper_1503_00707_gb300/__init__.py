@@ -18,7 +18,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libdvm.so")
 
 F64, F32, BF16 = 0, 1, 2
-COLL_NONE, COLL_BGK, COLL_HS, COLL_LEARNED = 0, 1, 2, 3
+COLL_NONE, COLL_BGK, COLL_HS, COLL_LEARNED, COLL_BGK_ENTROPIC = 0, 1, 2, 3, 4
 BC_PERIODIC, BC_INFLOW, BC_OUTFLOW, BC_WALL = 0, 1, 2, 3
 PRED_NONE, PRED_BALL, PRED_SHELL = 0, 1, 2
 

@@ -344,7 +344,7 @@ int dvm_create(dvm_ctx **out, const dvm_config *cfg)
     if (!out || !cfg) return DVM_EINVAL;
     *out = nullptr;
     if (cfg->precision < DVM_F64 || cfg->precision > DVM_BF16) return DVM_EINVAL;
-    if (cfg->collision < DVM_COLL_NONE || cfg->collision > DVM_COLL_LEARNED) return DVM_EINVAL;
+    if (cfg->collision < DVM_COLL_NONE || cfg->collision > DVM_COLL_BGK_ENTROPIC) return DVM_EINVAL;
     if (cfg->collision != DVM_COLL_NONE && !(cfg->kn > 0.0)) return DVM_EINVAL;
     dvm_ctx *c = new (std::nothrow) dvm_ctx();
     if (!c) return DVM_ENOMEM;
@@ -805,7 +805,8 @@ int dvm_step(dvm_ctx *c, int nsteps, double dt)
     dvm::StepParams p{};
     p.dim = c->mesh.spec.dim;
     p.prec = c->cfg.precision;
-    p.coll = c->cfg.collision == DVM_COLL_BGK ? DVM_COLL_BGK : DVM_COLL_NONE;
+    p.coll = (c->cfg.collision == DVM_COLL_BGK || c->cfg.collision == DVM_COLL_BGK_ENTROPIC) ? c->cfg.collision
+                                                                                                : DVM_COLL_NONE;
     p.ncells = ncells_of(c);
     p.nv = c->nv;
     p.P = c->P;
@@ -899,7 +900,8 @@ int dvm_step_partitioned(dvm_ctx *c, int nparts, int nsteps, double dt)
     if (!c || nsteps < 0 || nparts < 1) return DVM_EINVAL;
     if (c->state < 3) return fail(c, DVM_ESTATE, "f is not set");
     if (!(dt > 0.0) || !std::isfinite(dt)) return fail(c, DVM_EINVAL, "dt must be positive");
-    if (c->cfg.collision != DVM_COLL_BGK && c->cfg.collision != DVM_COLL_NONE)
+    if (c->cfg.collision != DVM_COLL_BGK && c->cfg.collision != DVM_COLL_BGK_ENTROPIC &&
+        c->cfg.collision != DVM_COLL_NONE)
         return fail(c, DVM_ENOTIMPL, "the partitioned step runs transport and BGK only");
     const int64_t nc = ncells_of(c);
     if (nparts > nc) return fail(c, DVM_EINVAL, "more parts than cells");
@@ -983,7 +985,8 @@ int dvm_step_partitioned(dvm_ctx *c, int nparts, int nsteps, double dt)
     dvm::StepParams base{};
     base.dim = c->mesh.spec.dim;
     base.prec = c->cfg.precision;
-    base.coll = c->cfg.collision == DVM_COLL_BGK ? DVM_COLL_BGK : DVM_COLL_NONE;
+    base.coll = (c->cfg.collision == DVM_COLL_BGK || c->cfg.collision == DVM_COLL_BGK_ENTROPIC) ? c->cfg.collision
+                                                                                                   : DVM_COLL_NONE;
     base.nv = c->nv;
     base.P = c->P;
     for (int d = 0; d < 3; d++) { base.half[d] = c->half[d]; base.n[d] = c->n[d]; base.hv[d] = c->hv[d]; }

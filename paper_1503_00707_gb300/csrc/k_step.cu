@@ -171,7 +171,7 @@ template <int DIM> __host__ __device__ constexpr int lists_of(int o)
 
 // coefficient slots written by the solver warp for phase 3:
 // f^{n+1} = (1 - nu dt) f* + KN gx gy gz (C0 + Px + Py + Pz)
-enum { CF_KN = 0, CF_C0, CF_OMN, CF_DX, CF_DY, CF_DZ, CF_D4, CF_N };
+enum { CF_KN = 0, CF_C0, CF_OMN, CF_DX, CF_DY, CF_DZ, CF_D4, CF_D0, CF_N };
 
 // per-axis factors of the corrected Maxwellian: g = exp(-c^2/2) and
 // P = d_axis c + d4 c^2, c = (xi - u)/sqrt(T)
@@ -314,113 +314,163 @@ __device__ inline int solve_cell(const StepParams &p, StepSmem<TC> &sm, const Co
     // lane 0's verdict for the whole warp (the lanes' double-float sums may
     // differ in their last bits)
     flags = __shfl_sync(0xffffffffu, flags, 0);
-    if (COLL == DVM_COLL_BGK && flags == 0) {
+    // BGK: one solve for the correction polynomial 1 + d.phi of the
+    // Maxwellian, phi = (1, c, |c|^2 - 3).  Entropic BGK: the target is
+    // exp(-|c|^2/2 + e.phi); the same solve, made at exp(-|c|^2/2 + e.phi)
+    // in place of the Maxwellian, is Newton's step d for e.  The loop adds d
+    // to e until |d| is below ENT_TOL, and the last d is applied as the
+    // polynomial, which keeps the moments exact to the solve (as for BGK)
+    // and differs from exp(-|c|^2/2 + (e + d).phi) by O(d^2).
+    constexpr bool ENT = COLL == DVM_COLL_BGK_ENTROPIC;
+    constexpr int NIT = ENT ? 8 : 1;
+    const TC ENT_TOL = sizeof(TC) == 8 ? (TC)1e-9 : (TC)1e-5;
+    if ((COLL == DVM_COLL_BGK || ENT) && flags == 0) {
         const TC uT[3] = {N::tc(ux), N::tc(uy), N::tc(uz)};
         const X isT = N::rsqrt(T);
         const TC isTt = N::tc(isT);
         const X Kc = rho * K.c15 * isT * isT * isT;  // rho (2 pi T)^(-3/2)
-        // 1D sums of g c^k, k = 0..4 (k = 0, 2 in double-float), with
-        // c = (xi - u)/sqrt(T), g = exp(-c^2/2): lanes 8d .. 8d + 7 take
-        // axis d, lane 8d + s the nodes s, s + 8, s + 16, s + 24; the eight
-        // lanes of an axis then combine in three butterfly levels
         const int ax = lane >> 3, sub = lane & 7;
         const TC ud = ax == 0 ? uT[0] : (ax == 1 ? uT[1] : uT[2]);
         const int nax = ax < 3 ? p.n[ax] : 0;
-        X A0 = N::make((TC)0), A2 = N::make((TC)0);
-        TC A1 = 0, A3 = 0, A4 = 0;
+        TC e[5] = {0, 0, 0, 0, 0};  // entropic: the accumulated e (every lane)
+        TC Kpt = N::tc(Kc);           // prefactor of the target, in TC
+        int done = 1;
 #pragma unroll 1
-        for (int i = sub; i < nax; i += 8) {
-            const TC c = (sm.xin[ax][i] - ud) * isTt;
-            const TC g = tc_exp<TC>((TC)-0.5 * c * c);
-            const TC gc = g * c;
-            A0 = A0 + N::make(g);
-            A2 = A2 + N::make(gc) * c;
-            A1 += gc;
-            A3 += gc * c * c;
-            A4 += gc * c * c * c;
-        }
-#pragma unroll
-        for (int m = 4; m > 0; m >>= 1) {
-            A0 = A0 + N::shfl_xor(A0, m);
-            A2 = A2 + N::shfl_xor(A2, m);
-            A1 += __shfl_xor_sync(0xffffffffu, A1, m);
-            A3 += __shfl_xor_sync(0xffffffffu, A3, m);
-            A4 += __shfl_xor_sync(0xffffffffu, A4, m);
-        }
-        X G0[3], G2[3];
-        TC G1[3], G3[3], G4[3];
-#pragma unroll
-        for (int d = 0; d < 3; d++) {
-            G0[d] = N::shfl(A0, 8 * d);
-            G2[d] = N::shfl(A2, 8 * d);
-            G1[d] = __shfl_sync(0xffffffffu, A1, 8 * d);
-            G3[d] = __shfl_sync(0xffffffffu, A3, 8 * d);
-            G4[d] = __shfl_sync(0xffffffffu, A4, 8 * d);
-        }
-        const X KdV = Kc * K.dV;
-        if (lane == 0) {
-            // moments of M in the centred basis; defects in double-float
-            const X P0 = G0[0] * G0[1] * G0[2];
-            const X Q2 = G2[0] * G0[1] * G0[2] + G0[0] * G2[1] * G0[2] + G0[0] * G0[1] * G2[2];
-            const TC r0 = N::tc(rho - KdV * P0);
-            const TC b04 = N::tc(KdV * (Q2 - P0 - P0 - P0));
-            const TC k = N::tc(KdV);
-            TC g0[3], g2[3];
-#pragma unroll
-            for (int d = 0; d < 3; d++) { g0[d] = N::tc(G0[d]); g2[d] = N::tc(G2[d]); }
-            const TC p0v = g0[0] * g0[1] * g0[2];
-            TC A[25], rhs[5], dd[5];
-            A[0] = N::tc(KdV * P0);
-            A[1] = k * G1[0] * g0[1] * g0[2];
-            A[2] = k * g0[0] * G1[1] * g0[2];
-            A[3] = k * g0[0] * g0[1] * G1[2];
-            A[4] = b04;
-            A[6] = k * g2[0] * g0[1] * g0[2];
-            A[7] = k * G1[0] * G1[1] * g0[2];
-            A[8] = k * G1[0] * g0[1] * G1[2];
-            A[9] = k * (G3[0] * g0[1] * g0[2] + G1[0] * g2[1] * g0[2] + G1[0] * g0[1] * g2[2] -
-                        (TC)3 * G1[0] * g0[1] * g0[2]);
-            A[12] = k * g0[0] * g2[1] * g0[2];
-            A[13] = k * g0[0] * G1[1] * G1[2];
-            A[14] = k * (g2[0] * G1[1] * g0[2] + g0[0] * G3[1] * g0[2] + g0[0] * G1[1] * g2[2] -
-                         (TC)3 * g0[0] * G1[1] * g0[2]);
-            A[18] = k * g0[0] * g0[1] * g2[2];
-            A[19] = k * (g2[0] * g0[1] * G1[2] + g0[0] * g2[1] * G1[2] + g0[0] * g0[1] * G3[2] -
-                         (TC)3 * g0[0] * g0[1] * G1[2]);
-            const TC s2 = g2[0] * g0[1] * g0[2] + g0[0] * g2[1] * g0[2] + g0[0] * g0[1] * g2[2];
-            A[24] = k * (G4[0] * g0[1] * g0[2] + g0[0] * G4[1] * g0[2] + g0[0] * g0[1] * G4[2] +
-                         (TC)2 * (g2[0] * g2[1] * g0[2] + g2[0] * g0[1] * g2[2] + g0[0] * g2[1] * g2[2]) -
-                         (TC)6 * s2 + (TC)9 * p0v);
-#pragma unroll
-            for (int r = 0; r < 5; r++)
-#pragma unroll
-                for (int c2 = 0; c2 < r; c2++) A[r * 5 + c2] = A[c2 * 5 + r];
-            rhs[0] = r0;
-            rhs[1] = -A[1];
-            rhs[2] = -A[2];
-            rhs[3] = -A[3];
-            rhs[4] = -b04;
-            if (!solve5_rcp<TC>(A, rhs, dd)) flags |= ST_SINGULAR;
-            const TC nudt = K.nu0 * N::tc(rho) * sqrt(N::tc(T));
-            if (nudt > (TC)1) flags |= ST_NUDT;
-            TC *cf = sm.coef[b];
-            cf[CF_KN] = nudt * N::tc(Kc);
-            cf[CF_C0] = (TC)1 + dd[0] - (TC)3 * dd[4];
-            cf[CF_OMN] = (TC)1 - nudt;
-            cf[CF_DX] = dd[1];
-            cf[CF_DY] = dd[2];
-            cf[CF_DZ] = dd[3];
-            cf[CF_D4] = dd[4];
-        }
-        __syncwarp();
-        // per-axis factors of the corrected Maxwellian, each lane for its nodes
-        const TC d4 = sm.coef[b][CF_D4];
-        if (ax < 3) {
-            const TC da = sm.coef[b][CF_DX + ax];
+        for (int it = 0; it < NIT; it++) {
+            if constexpr (ENT) {
+                if (it > 0) {
+                    e[0] += sm.coef[b][CF_D0];
+                    e[1] += sm.coef[b][CF_DX];
+                    e[2] += sm.coef[b][CF_DY];
+                    e[3] += sm.coef[b][CF_DZ];
+                    e[4] += sm.coef[b][CF_D4];
+                    __syncwarp();
+                    // the one value used in the defects below and in the
+                    // collision, so that the moments stay exact to the solve
+                    Kpt = N::tc(Kc) * tc_exp<TC>(e[0] - (TC)3 * e[4]);
+                }
+            }
+            const TC ea = ENT ? (ax == 0 ? e[1] : (ax == 1 ? e[2] : e[3])) : (TC)0, e4 = ENT ? e[4] : (TC)0;
+            // 1D sums of g c^k, k = 0..4 (k = 0, 2 in double-float), with
+            // c = (xi - u)/sqrt(T), g = exp(-c^2/2) (entropic: times
+            // exp(d_axis c + d4 c^2)): lanes 8d .. 8d + 7 take axis d, lane
+            // 8d + s the nodes s, s + 8, s + 16, s + 24; the eight lanes of an
+            // axis then combine in three butterfly levels
+            X A0 = N::make((TC)0), A2 = N::make((TC)0);
+            TC A1 = 0, A3 = 0, A4 = 0;
 #pragma unroll 1
             for (int i = sub; i < nax; i += 8) {
                 const TC c = (sm.xin[ax][i] - ud) * isTt;
-                sm.tab[b][ax][i] = TabE<TC>{tc_exp<TC>((TC)-0.5 * c * c), c * (da + d4 * c)};
+                TC ex = (TC)-0.5 * c * c;
+                if constexpr (ENT) ex += c * (ea + e4 * c);
+                const TC g = tc_exp<TC>(ex);
+                const TC gc = g * c;
+                A0 = A0 + N::make(g);
+                A2 = A2 + N::make(gc) * c;
+                A1 += gc;
+                A3 += gc * c * c;
+                A4 += gc * c * c * c;
+            }
+#pragma unroll
+            for (int m = 4; m > 0; m >>= 1) {
+                A0 = A0 + N::shfl_xor(A0, m);
+                A2 = A2 + N::shfl_xor(A2, m);
+                A1 += __shfl_xor_sync(0xffffffffu, A1, m);
+                A3 += __shfl_xor_sync(0xffffffffu, A3, m);
+                A4 += __shfl_xor_sync(0xffffffffu, A4, m);
+            }
+            X G0[3], G2[3];
+            TC G1[3], G3[3], G4[3];
+#pragma unroll
+            for (int d = 0; d < 3; d++) {
+                G0[d] = N::shfl(A0, 8 * d);
+                G2[d] = N::shfl(A2, 8 * d);
+                G1[d] = __shfl_sync(0xffffffffu, A1, 8 * d);
+                G3[d] = __shfl_sync(0xffffffffu, A3, 8 * d);
+                G4[d] = __shfl_sync(0xffffffffu, A4, 8 * d);
+            }
+            const X KdV = ENT && it > 0 ? N::make(Kpt) * K.dV : Kc * K.dV;
+            if (lane == 0) {
+                // moments of the target in the centred basis; defects in
+                // double-float
+                const X P0 = G0[0] * G0[1] * G0[2];
+                const X Q2 = G2[0] * G0[1] * G0[2] + G0[0] * G2[1] * G0[2] + G0[0] * G0[1] * G2[2];
+                const TC r0 = N::tc(rho - KdV * P0);
+                const TC b04 = N::tc(KdV * (Q2 - P0 - P0 - P0));
+                const TC k = N::tc(KdV);
+                TC g0[3], g2[3];
+#pragma unroll
+                for (int d = 0; d < 3; d++) { g0[d] = N::tc(G0[d]); g2[d] = N::tc(G2[d]); }
+                const TC p0v = g0[0] * g0[1] * g0[2];
+                TC A[25], rhs[5], dd[5];
+                A[0] = N::tc(KdV * P0);
+                A[1] = k * G1[0] * g0[1] * g0[2];
+                A[2] = k * g0[0] * G1[1] * g0[2];
+                A[3] = k * g0[0] * g0[1] * G1[2];
+                A[4] = b04;
+                A[6] = k * g2[0] * g0[1] * g0[2];
+                A[7] = k * G1[0] * G1[1] * g0[2];
+                A[8] = k * G1[0] * g0[1] * G1[2];
+                A[9] = k * (G3[0] * g0[1] * g0[2] + G1[0] * g2[1] * g0[2] + G1[0] * g0[1] * g2[2] -
+                            (TC)3 * G1[0] * g0[1] * g0[2]);
+                A[12] = k * g0[0] * g2[1] * g0[2];
+                A[13] = k * g0[0] * G1[1] * G1[2];
+                A[14] = k * (g2[0] * G1[1] * g0[2] + g0[0] * G3[1] * g0[2] + g0[0] * G1[1] * g2[2] -
+                             (TC)3 * g0[0] * G1[1] * g0[2]);
+                A[18] = k * g0[0] * g0[1] * g2[2];
+                A[19] = k * (g2[0] * g0[1] * G1[2] + g0[0] * g2[1] * G1[2] + g0[0] * g0[1] * G3[2] -
+                             (TC)3 * g0[0] * g0[1] * G1[2]);
+                const TC s2 = g2[0] * g0[1] * g0[2] + g0[0] * g2[1] * g0[2] + g0[0] * g0[1] * g2[2];
+                A[24] = k * (G4[0] * g0[1] * g0[2] + g0[0] * G4[1] * g0[2] + g0[0] * g0[1] * G4[2] +
+                             (TC)2 * (g2[0] * g2[1] * g0[2] + g2[0] * g0[1] * g2[2] + g0[0] * g2[1] * g2[2]) -
+                             (TC)6 * s2 + (TC)9 * p0v);
+#pragma unroll
+                for (int r = 0; r < 5; r++)
+#pragma unroll
+                    for (int c2 = 0; c2 < r; c2++) A[r * 5 + c2] = A[c2 * 5 + r];
+                rhs[0] = r0;
+                rhs[1] = -A[1];
+                rhs[2] = -A[2];
+                rhs[3] = -A[3];
+                rhs[4] = -b04;
+                if (!solve5_rcp<TC>(A, rhs, dd)) flags |= ST_SINGULAR;
+                TC *cf = sm.coef[b];
+                cf[CF_D0] = dd[0];
+                cf[CF_C0] = (TC)1 + dd[0] - (TC)3 * dd[4];
+                cf[CF_DX] = dd[1];
+                cf[CF_DY] = dd[2];
+                cf[CF_DZ] = dd[3];
+                cf[CF_D4] = dd[4];
+                bool conv = true;
+#pragma unroll
+                for (int r = 0; r < 5; r++) conv = conv && fabs(dd[r]) < ENT_TOL;  // false on NaN
+                if (!conv && !flags) done = 0;
+            }
+            __syncwarp();
+            if (__shfl_sync(0xffffffffu, done, 0)) break;
+            done = 1;
+        }
+        TC *cf = sm.coef[b];
+        if (lane == 0) {
+            const TC nudt = K.nu0 * N::tc(rho) * sqrt(N::tc(T));
+            if (nudt > (TC)1) flags |= ST_NUDT;
+            cf[CF_KN] = nudt * Kpt;
+            cf[CF_OMN] = (TC)1 - nudt;
+        }
+        __syncwarp();
+        // per-axis factors of the target, each lane for its nodes:
+        // g = exp(-c^2/2) (entropic: exp(-c^2/2 + e_axis c + e4 c^2)) and
+        // P = d_axis c + d4 c^2
+        const TC d4 = cf[CF_D4];
+        if (ax < 3) {
+            const TC da = cf[CF_DX + ax];
+            const TC ea = ENT ? (ax == 0 ? e[1] : (ax == 1 ? e[2] : e[3])) : (TC)0, e4 = ENT ? e[4] : (TC)0;
+#pragma unroll 1
+            for (int i = sub; i < nax; i += 8) {
+                const TC c = (sm.xin[ax][i] - ud) * isTt;
+                TC ex = (TC)-0.5 * c * c;
+                if constexpr (ENT) ex += c * (ea + e4 * c);
+                sm.tab[b][ax][i] = TabE<TC>{tc_exp<TC>(ex), c * (da + d4 * c)};
             }
         }
     }
@@ -567,7 +617,8 @@ __global__ void __launch_bounds__(MAXT, 1) k_step(const StepParams p)
                 next_cell = take_finish(nc);
                 if (lane == 0) {
                     if (flags) atomicOr(p.status, flags);
-                    sm.ok[q] = COLL == DVM_COLL_BGK && (flags & (ST_NONPOS | ST_SINGULAR)) == 0;
+                    sm.ok[q] = (COLL == DVM_COLL_BGK || COLL == DVM_COLL_BGK_ENTROPIC) &&
+                               (flags & (ST_NONPOS | ST_SINGULAR)) == 0;
                 }
             }
             if (lane == 0) sm.dec[q] = dec;
@@ -833,6 +884,7 @@ int launch_typed(const StepParams &p)
     const int ncw = (Q + 31) / 32;
     if (ncw > MAXCW) return DVM_ENOTIMPL;
     if (p.coll == DVM_COLL_BGK) return launch_sized<TS, DIM, DVM_COLL_BGK>(p, ncw);
+    if (p.coll == DVM_COLL_BGK_ENTROPIC) return launch_kernel<TS, DIM, DVM_COLL_BGK_ENTROPIC, 0>(p, ncw);
     return launch_sized<TS, DIM, DVM_COLL_NONE>(p, ncw);
 }
 
@@ -841,7 +893,7 @@ int launch_typed(const StepParams &p)
 int launch_step(const StepParams &p)
 {
     if (p.ncells <= 0) return DVM_OK;
-    if (p.coll != DVM_COLL_NONE && p.coll != DVM_COLL_BGK) return DVM_ENOTIMPL;
+    if (p.coll != DVM_COLL_NONE && p.coll != DVM_COLL_BGK && p.coll != DVM_COLL_BGK_ENTROPIC) return DVM_ENOTIMPL;
     switch (p.prec) {
     case DVM_F64: return p.dim == 3 ? launch_typed<double, 3>(p) : launch_typed<double, 2>(p);
     case DVM_F32: return p.dim == 3 ? launch_typed<float, 3>(p) : launch_typed<float, 2>(p);

@@ -20,22 +20,23 @@ def gpu():
     _build.build()
 
 
-def _solver(c, precision):
-    s = D.solver_from_config(c, precision, D.COLL_BGK)
+def _solver(c, precision, coll=D.COLL_BGK):
+    s = D.solver_from_config(c, precision, coll)
     xyz, _ = s.centres()
     s.init_maxwellian(*W.initial_state(c, xyz))
     return s
 
 
-@pytest.mark.parametrize("name,precision,nparts,steps", [
-    ("c1_2d_bump", D.F64, 3, 10),           # periodic quadtree: halos wrap around
-    ("c2_sphere_m3", D.F32, 5, 6),          # walls, inflow, outflow, 16^3
-    ("c3_sphere_m5_small", D.F32, 4, 3),    # the 24^3 Mach-5 flow
-    ("c3_sphere_m5_small", D.BF16, 2, 3),
+@pytest.mark.parametrize("name,precision,nparts,steps,coll", [
+    ("c1_2d_bump", D.F64, 3, 10, D.COLL_BGK),           # periodic quadtree: halos wrap around
+    ("c2_sphere_m3", D.F32, 5, 6, D.COLL_BGK),          # walls, inflow, outflow, 16^3
+    ("c3_sphere_m5_small", D.F32, 4, 3, D.COLL_BGK),    # the 24^3 Mach-5 flow
+    ("c3_sphere_m5_small", D.BF16, 2, 3, D.COLL_BGK),
+    ("c2_sphere_m3", D.F32, 3, 4, D.COLL_BGK_ENTROPIC),
 ])
-def test_partitioned_step_is_bit_identical(name, precision, nparts, steps):
+def test_partitioned_step_is_bit_identical(name, precision, nparts, steps, coll):
     c = W.CONFIGS[name]
-    a, b = _solver(c, precision), _solver(c, precision)
+    a, b = _solver(c, precision, coll), _solver(c, precision, coll)
     dt = a.dt_cfl(c["cfl"])
     a.step(steps, dt)
     b.step_partitioned(nparts, steps, dt)
