@@ -17,6 +17,7 @@ BC_PERIODIC, BC_INFLOW, BC_OUTFLOW, BC_WALL = 0, 1, 2, 3
 PRED_NONE, PRED_BALL, PRED_SHELL = 0, 1, 2
 COLL_NONE, COLL_BGK, COLL_HS = 0, 1, 2
 COLL_BGK_ENTROPIC = 4
+D2Q9, D3Q19, D3Q27 = 9, 19, 27
 
 
 class TreeSpec(C.Structure):
@@ -92,6 +93,16 @@ def lib():
         L.orc_mlp_backward.argtypes = [C.c_int64, P, P, P, P, P]
         L.orc_learned_collide.argtypes = [P, C.c_double, C.c_double, P, C.c_double, P, P]
         L.orc_learned_apply.argtypes = [P, C.c_double, C.c_double, P, P, C.c_double, P, P]
+        L.orc_lattice_q.argtypes = [C.c_int]
+        L.orc_lattice.argtypes = [C.c_int, P, P]
+        L.orc_create_lattice.restype = P
+        L.orc_create_lattice.argtypes = [C.POINTER(TreeSpec), C.c_int]
+        L.orc_lbm_feq.argtypes = [P, C.c_double, P, P]
+        L.orc_lbm_set_inflow.argtypes = [P, C.c_double, P]
+        L.orc_lbm_init.argtypes = [P, P, P]
+        L.orc_lbm_moments.argtypes = [P, P, P]
+        L.orc_lbm_collide.argtypes = [P, C.c_double, C.c_double]
+        L.orc_lbm_step.argtypes = [P, C.c_int, C.c_double, C.c_double]
         _lib = L
     return _lib
 
@@ -108,6 +119,17 @@ def trial_uniforms(lattice, seed, i, k, M):
     u = np.zeros(5)
     lib().orc_trial_uniforms(int(lattice), int(seed), int(i), int(k), int(M), _p(u))
     return u
+
+
+def lattice(kind):
+    """(c [Q][3] as floats, w [Q]) of D2Q9 / D3Q19 / D3Q27 (Sec. 4)."""
+    q = lib().orc_lattice_q(int(kind))
+    if q < 0:
+        raise ValueError("unknown lattice")
+    c = np.zeros((q, 3))
+    w = np.zeros(q)
+    lib().orc_lattice(int(kind), _p(c), _p(w))
+    return c, w
 
 
 def threads():
@@ -179,8 +201,21 @@ def solve(A, b):
 class Problem:
     """One tree + velocity grid + state, all in FP64 on the host."""
 
-    def __init__(self, spec, n, lo, hi):
+    def __init__(self, spec, n=None, lo=None, hi=None, lattice=None):
         self.spec = spec
+        if lattice is not None:
+            # lattice Boltzmann (Sec. 4): the tree with an LBM velocity set
+            self._h = lib().orc_create_lattice(C.byref(spec), int(lattice))
+            if not self._h:
+                raise ValueError("oracle lattice problem creation failed")
+            self.lattice = int(lattice)
+            self.nleaves = lib().orc_nleaves(self._h)
+            self.ncells = lib().orc_ncells(self._h)
+            self.nv = lib().orc_nv(self._h)
+            self.xi, self.w = globals()["lattice"](lattice)
+            self.dV = 1.0
+            return
+        self.lattice = None
         n = np.asarray(n, dtype=np.int32)
         lo = np.asarray(lo, dtype=np.float64)
         hi = np.asarray(hi, dtype=np.float64)
@@ -271,6 +306,37 @@ class Problem:
         out = np.zeros(5)
         lib().orc_totals(self._h, _p(out))
         return out
+
+    # ---- lattice Boltzmann (Sec. 4)
+    def lbm_feq(self, rho, u):
+        u = np.asarray(u, dtype=np.float64)
+        out = np.zeros(self.nv)
+        assert lib().orc_lbm_feq(self._h, float(rho), _p(u), _p(out)) == 0
+        return out
+
+    def lbm_set_inflow(self, rho, u):
+        u = np.asarray(u, dtype=np.float64)
+        assert lib().orc_lbm_set_inflow(self._h, float(rho), _p(u)) == 0
+
+    def lbm_init(self, rho, u):
+        rho = np.ascontiguousarray(rho, dtype=np.float64).reshape(self.ncells)
+        u = np.ascontiguousarray(u, dtype=np.float64).reshape(self.ncells, 3)
+        assert lib().orc_lbm_init(self._h, _p(rho), _p(u)) == 0
+
+    def lbm_moments(self):
+        rho = np.zeros(self.ncells)
+        u = np.zeros((self.ncells, 3))
+        lib().orc_lbm_moments(self._h, _p(rho), _p(u))
+        return rho, u
+
+    def lbm_collide(self, dt, tau):
+        if lib().orc_lbm_collide(self._h, dt, tau):
+            raise RuntimeError("LBM collision failed (non-positive density)")
+
+    def lbm_step(self, nsteps, dt, tau):
+        rc = lib().orc_lbm_step(self._h, int(nsteps), dt, tau)
+        if rc:
+            raise RuntimeError("LBM step failed (%d)" % rc)
 
     def bgk(self, dt, kn, want_q=False):
         q = np.zeros((self.ncells, self.nv)) if want_q else None

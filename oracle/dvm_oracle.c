@@ -78,6 +78,9 @@ struct orc_problem {
     int32_t *hs_gam, *hs_l, *hs_m;
     double *hs_b;
     int64_t hs_discarded;
+    /* LBM velocity set (0: a DVM grid) and its weights */
+    int lattice;
+    double *lw;
 };
 
 /* ------------------------------------------------------------------------ */
@@ -542,8 +545,8 @@ static double maxwellian(double rho, const double u[3], double T, const double x
     return rho * pow(2.0 * M_PI * T, -1.5) * exp(-q / (2.0 * T));
 }
 
-orc_problem *orc_create(const orc_tree_spec *spec, const int n[3],
-                        const double lo[3], const double hi[3])
+/* the tree, its cells and faces; no velocity set yet */
+static orc_problem *create_tree(const orc_tree_spec *spec)
 {
     if (check_spec(spec)) return NULL;
     orc_problem *p = (orc_problem *)calloc(1, sizeof(orc_problem));
@@ -561,6 +564,14 @@ orc_problem *orc_create(const orc_tree_spec *spec, const int n[3],
         else { p->cell_of_leaf[a] = p->ncells; p->leaf_of_cell[p->ncells++] = a; }
     }
     if (build_faces(p)) { orc_destroy(p); return NULL; }
+    return p;
+}
+
+orc_problem *orc_create(const orc_tree_spec *spec, const int n[3],
+                        const double lo[3], const double hi[3])
+{
+    orc_problem *p = create_tree(spec);
+    if (!p) return NULL;
     for (int d = 0; d < 3; d++) { p->n[d] = n[d]; p->lo[d] = lo[d]; p->hi[d] = hi[d]; }
     p->nv = orc_vgrid_size(n);
     p->xi = (double *)malloc((size_t)p->nv * 3 * sizeof(double));
@@ -599,7 +610,7 @@ void orc_destroy(orc_problem *p)
     free(p->bl); free(p->bother); free(p->bax); free(p->bside); free(p->bkind); free(p->barea);
     free(p->xi); free(p->k);
     for (int d = 0; d < 3; d++) free(p->mirror[d]);
-    free(p->f); free(p->finf);
+    free(p->f); free(p->finf); free(p->lw);
     free(p->hs_start); free(p->hs_gam); free(p->hs_l); free(p->hs_m); free(p->hs_b);
     free(p);
 }
@@ -1181,6 +1192,172 @@ int orc_hs_collide(orc_problem *p, double dt, double kn, double *q,
 
 /* ------------------------------------------------------------------------ */
 /* Lie splitting: transport, then the collision update on f*. */
+/* ------------------------------------------------------------------------ */
+/* Lattice Boltzmann on the tree (Sec. 4): the LBM module is the DVM solver on
+ * a minimal velocity set, D2Q9 (3x3), D3Q19 or D3Q27 (3x3x3), with lattice
+ * weights w_i and lattice speed of sound c_s = 1/sqrt(3).  Transport is the
+ * same finite-volume upwind scheme (orc_transport, Eq. 2, finite-volume LBM
+ * as in the paper's Ref. [44]); a velocity component of 0 carries no flux.
+ * Collision is the BGK form I_i = -(f_i - feq_i)/tau with the second-order
+ * equilibrium
+ *   feq_i = w_i rho (1 + c_i.u/c_s^2 + (c_i.u)^2/(2 c_s^4) - |u|^2/(2 c_s^2)),
+ * rho = sum_i f_i, rho u = sum_i c_i f_i.  Velocity order: increasing |c|^2,
+ * ties lexicographic in (c_x, c_y, c_z) with -1 < 0 < 1.  Weights by |c|^2:
+ * D2Q9 4/9, 1/9, 1/36; D3Q19 1/3, 1/18, 1/36; D3Q27 8/27, 2/27, 1/54, 1/216
+ * (the values fixed by 4th-order isotropy of each set).  dV = 1, so the DVM
+ * moments routine returns rho and u of the lattice. */
+static int lattice_set(int lattice, int dim, double *c, double *w)
+{
+    static const double w9[3] = {4.0 / 9, 1.0 / 9, 1.0 / 36};
+    static const double w19[3] = {1.0 / 3, 1.0 / 18, 1.0 / 36};
+    static const double w27[4] = {8.0 / 27, 2.0 / 27, 1.0 / 54, 1.0 / 216};
+    int q = 0;
+    for (int r = 0; r <= 3; r++)
+        for (int x = -1; x <= 1; x++)
+            for (int y = -1; y <= 1; y++)
+                for (int z = -1; z <= 1; z++) {
+                    int r2 = x * x + y * y + z * z;
+                    if (r2 != r) continue;
+                    double wt;
+                    if (lattice == ORC_D2Q9) {
+                        if (z != 0) continue;
+                        wt = w9[r2];
+                    } else if (lattice == ORC_D3Q19) {
+                        if (r2 == 3) continue;
+                        wt = w19[r2];
+                    } else {
+                        wt = w27[r2];
+                    }
+                    if (c) { c[3 * q] = x; c[3 * q + 1] = y; c[3 * q + 2] = z; }
+                    if (w) w[q] = wt;
+                    q++;
+                }
+    (void)dim;
+    return q;
+}
+
+int orc_lattice_q(int lattice)
+{
+    if (lattice != ORC_D2Q9 && lattice != ORC_D3Q19 && lattice != ORC_D3Q27) return -1;
+    return lattice_set(lattice, 0, NULL, NULL);
+}
+
+int orc_lattice(int lattice, double *c, double *w)
+{
+    if (orc_lattice_q(lattice) < 0) return -1;
+    lattice_set(lattice, 0, c, w);
+    return 0;
+}
+
+orc_problem *orc_create_lattice(const orc_tree_spec *spec, int lattice)
+{
+    int Q = orc_lattice_q(lattice);
+    if (Q < 0 || (lattice == ORC_D2Q9) != (spec->dim == 2)) return NULL;
+    orc_problem *p = create_tree(spec);
+    if (!p) return NULL;
+    p->lattice = lattice;
+    p->nv = Q;
+    p->dV = 1.0;
+    for (int d = 0; d < 3; d++) { p->n[d] = 3; p->lo[d] = -1.5; p->hi[d] = 1.5; p->h[d] = 1.0; }
+    p->xi = (double *)malloc((size_t)Q * 3 * sizeof(double));
+    p->lw = (double *)malloc((size_t)Q * sizeof(double));
+    lattice_set(lattice, spec->dim, p->xi, p->lw);
+    /* mirror maps: the velocity with component d negated (a set member) */
+    for (int d = 0; d < 3; d++) {
+        p->mirror[d] = (int64_t *)malloc((size_t)Q * sizeof(int64_t));
+        for (int v = 0; v < Q; v++) {
+            double r[3] = {p->xi[3 * v], p->xi[3 * v + 1], p->xi[3 * v + 2]};
+            r[d] = -r[d];
+            p->mirror[d][v] = -1;
+            for (int t = 0; t < Q; t++)
+                if (p->xi[3 * t] == r[0] && p->xi[3 * t + 1] == r[1] && p->xi[3 * t + 2] == r[2])
+                    p->mirror[d][v] = t;
+        }
+    }
+    p->f = (double *)calloc((size_t)(p->ncells * Q), sizeof(double));
+    p->finf = (double *)calloc((size_t)Q, sizeof(double));
+    if (!p->f || !p->finf) { orc_destroy(p); return NULL; }
+    double u0[3] = {0, 0, 0};
+    orc_lbm_set_inflow(p, 1.0, u0);
+    return p;
+}
+
+int orc_lbm_feq(const orc_problem *p, double rho, const double u[3], double *feq)
+{
+    if (!p->lattice) return -1;
+    const double cs2 = 1.0 / 3.0;
+    double uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    for (int64_t v = 0; v < p->nv; v++) {
+        const double *c = &p->xi[3 * v];
+        double cu = c[0] * u[0] + c[1] * u[1] + c[2] * u[2];
+        feq[v] = p->lw[v] * rho * (1.0 + cu / cs2 + cu * cu / (2.0 * cs2 * cs2) - uu / (2.0 * cs2));
+    }
+    return 0;
+}
+
+int orc_lbm_set_inflow(orc_problem *p, double rho, const double u[3])
+{
+    p->fs_rho = rho;
+    for (int d = 0; d < 3; d++) p->fs_u[d] = u[d];
+    return orc_lbm_feq(p, rho, u, p->finf);
+}
+
+int orc_lbm_init(orc_problem *p, const double *rho, const double *u)
+{
+    for (int64_t c = 0; c < p->ncells; c++)
+        if (orc_lbm_feq(p, rho[c], &u[3 * c], &p->f[c * p->nv])) return -1;
+    return 0;
+}
+
+/* rho and u of every cell: rho = sum f, u = sum c f / rho */
+int orc_lbm_moments(const orc_problem *p, double *rho, double *u)
+{
+    for (int64_t c = 0; c < p->ncells; c++) {
+        const double *f = &p->f[c * p->nv];
+        double s0 = 0.0, s1[3] = {0, 0, 0};
+        for (int64_t v = 0; v < p->nv; v++) {
+            s0 += f[v];
+            for (int d = 0; d < 3; d++) s1[d] += p->xi[3 * v + d] * f[v];
+        }
+        rho[c] = s0;
+        for (int d = 0; d < 3; d++) u[3 * c + d] = s1[d] / s0;
+    }
+    return 0;
+}
+
+/* f <- f - (dt/tau) (f - feq(rho(f), u(f))) in every cell; -1 if a cell has
+ * rho <= 0 or non-finite moments */
+int orc_lbm_collide(orc_problem *p, double dt, double tau)
+{
+    int err = 0;
+    const double om = dt / tau;
+#pragma omp parallel for schedule(static) reduction(| : err)
+    for (int64_t c = 0; c < p->ncells; c++) {
+        double *f = &p->f[c * p->nv];
+        double rho = 0.0, j[3] = {0, 0, 0};
+        for (int64_t v = 0; v < p->nv; v++) {
+            rho += f[v];
+            for (int d = 0; d < 3; d++) j[d] += p->xi[3 * v + d] * f[v];
+        }
+        if (!(rho > 0.0) || !isfinite(j[0] + j[1] + j[2])) { err = 1; continue; }
+        double u[3] = {j[0] / rho, j[1] / rho, j[2] / rho};
+        double feq[27];
+        orc_lbm_feq(p, rho, u, feq);
+        for (int64_t v = 0; v < p->nv; v++) f[v] -= om * (f[v] - feq[v]);
+    }
+    return err ? -1 : 0;
+}
+
+int orc_lbm_step(orc_problem *p, int nsteps, double dt, double tau)
+{
+    if (!p->lattice) return -1;
+    for (int s = 0; s < nsteps; s++) {
+        if (orc_transport(p, dt)) return -1;
+        if (orc_lbm_collide(p, dt, tau)) return -2;
+    }
+    return 0;
+}
+
 int orc_step(orc_problem *p, int nsteps, double dt, int coll, double kn)
 {
     for (int s = 0; s < nsteps; s++) {

@@ -169,6 +169,24 @@ int orc_learned_apply(orc_problem *p, double dt, double kn, const double *knl, c
  * A is row-major and is overwritten.  Returns 0, or -1 if singular. */
 int orc_solve(int n, double *A, double *b, double *x);
 
+/* Lattice Boltzmann on the tree (Sec. 4): velocity sets, equilibrium, BGK.
+ * Velocities in order of increasing |c|^2, ties lexicographic in
+ * (c_x, c_y, c_z) with -1 < 0 < 1; c [Q][3], w [Q]. */
+enum { ORC_D2Q9 = 9, ORC_D3Q19 = 19, ORC_D3Q27 = 27 };
+int orc_lattice_q(int lattice);
+int orc_lattice(int lattice, double *c, double *w);
+/* a problem on the tree with the lattice as its velocity set (dV = 1);
+ * D2Q9 needs dim 2, the others dim 3 */
+orc_problem *orc_create_lattice(const orc_tree_spec *spec, int lattice);
+int orc_lbm_feq(const orc_problem *p, double rho, const double u[3], double *feq);
+/* the inflow ghost: feq(rho, u) */
+int orc_lbm_set_inflow(orc_problem *p, double rho, const double u[3]);
+int orc_lbm_init(orc_problem *p, const double *rho, const double *u /* [ncells][3] */);
+int orc_lbm_moments(const orc_problem *p, double *rho, double *u);
+int orc_lbm_collide(orc_problem *p, double dt, double tau);
+/* nsteps of transport (Eq. 2) then BGK with forward Euler */
+int orc_lbm_step(orc_problem *p, int nsteps, double dt, double tau);
+
 #ifdef __cplusplus
 }
 #endif
