@@ -56,6 +56,10 @@ def parse():
     ap.add_argument("--learned-only", action="store_true",
                     help="run only the learned-vs-plain collision leg")
     ap.add_argument("--learned-config", default="c5_sphere_m3_hs")
+    ap.add_argument("--no-lbm", action="store_true",
+                    help="skip the lattice Boltzmann leg (D3Q19 / D3Q27 sphere flow)")
+    ap.add_argument("--lbm-only", action="store_true", help="run only the lattice Boltzmann leg")
+    ap.add_argument("--lbm-steps", type=int, default=20)
     ap.add_argument("--learned-steps", type=int, default=10)
     return ap.parse_args()
 
@@ -323,6 +327,75 @@ def _profiled_traffic(kernel_file, key):
     return d["bytes_per_launch"] if d.get("source_sha") == h else None
 
 
+# ---------------------------------------------------------------- lattice Boltzmann
+def lbm_leg(args, stream=None):
+    """The lattice Boltzmann step (Sec. 4) on the 3.34M-cell Ma-0.5 sphere
+    flow, D3Q19 and D3Q27, FP32: one fused transport + BGK kernel per step,
+    timed with CUDA events over --lbm-steps steps after 3 warm-up steps.
+    Algorithmic bytes per cell: f read and written (2 q x 4 B), the 2 dim
+    upwind codes (4 B each), the level byte and the overflow entries."""
+    import numpy as np
+    import torch
+    import paper_1503_00707_gb300 as D
+    out = {}
+    peak, peak_kind = _peaks()
+    for name in ("l3_sphere_d3q19", "l3_sphere_d3q27"):
+        c = W.CONFIGS[name]
+        st = stream or torch.cuda.Stream()
+        s = D.lbm_solver_from_config(c, stream=st)
+        xyz, _ = s.centres()
+        s.lbm_init(*W.lbm_initial_state(c, xyz))
+        dt = s.lbm_dt_cfl(c["cfl"])
+        tau = W.lbm_tau(c, dt)
+        q, ld, novf = s.lbm_info()
+        s.lbm_step(3, dt, tau)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        l0 = D.Solver.launch_count()
+        e0.record(st)
+        s.lbm_step(args.lbm_steps, dt, tau)
+        e1.record(st)
+        torch.cuda.synchronize()
+        launches = D.Solver.launch_count() - l0
+        ms = e0.elapsed_time(e1) / args.lbm_steps
+        nc = s.ncells
+        bpc = 2 * q * 4 + 8 * c["dim"] + 1 + 4.0 * novf / nc
+        achieved = bpc * nc / (ms / 1e3) / 1e9
+        rho, u = s.lbm_moments()
+        ok = bool(np.all(np.isfinite(rho)) and np.all(rho > 0))
+        s.close()
+        cpu = None
+        if not args.no_cpu_baseline:
+            # the oracle on the 17.7k-cell tree of the same flow
+            import oracle as O
+            cs = W.CONFIGS[name.replace("l3_", "l2_") + "_small"]
+            o = O.Problem(O.make_spec(cs["dim"], cs["base_level"], cs["max_level"], cs["pred"], cs["c"], cs["r"],
+                                      cs["beta"], cs["solid"], cs["bc"]), lattice=cs["lattice"])
+            o.lbm_set_inflow(cs["fs_rho"], cs["fs_u"])
+            xo, _ = o.centres()
+            o.lbm_init(*W.lbm_initial_state(cs, xo))
+            dto = o.dt_cfl(cs["cfl"])
+            t0 = time.perf_counter()
+            o.lbm_step(3, dto, W.lbm_tau(cs, dto))
+            cpu = {"value": o.ncells * 3 / (time.perf_counter() - t0), "unit": "cell-updates/s",
+                   "cores": O.threads(), "kind": "oracle",
+                   "sample": "3 steps on the %d-cell tree of the same flow, FP64" % o.ncells}
+        out[name] = {
+            "workload": "%s: 3D octree levels %d-%d around a solid sphere r=%g (%d cells), D3Q%d, Ma 0.5 "
+                        "inflow, outflow, dt/tau=%g, FP32" % (name, c["base_level"], c["max_level"], c["r"], nc, q,
+                                                              c["omega"]),
+            "cells": nc, "q": q, "steps": args.lbm_steps, "ms_per_step": ms,
+            "cell_updates_per_s": nc / (ms / 1e3), "phase_space_updates_per_s": nc * q / (ms / 1e3),
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "peak_source": peak_kind,
+                         "algorithmic_bytes_per_cell": bpc, "traffic": None},
+            "gpu_launches": launches, "moments_finite_positive": ok, "cpu_baseline": cpu,
+            "l2": "inputs larger than L2 (f is %.0f MB per buffer)" % (q * ld * 4 / 1e6),
+        }
+    return out
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -413,6 +486,9 @@ def run_ours(args):
 
     f_gb = s.f_bytes() / 1e9
     s.close()
+    lbm = None
+    if rank == 0 and not args.no_lbm:
+        lbm = lbm_leg(args)
     learned = None
     if rank == 0 and not args.no_learned:
         learned = learned_leg(args)
@@ -427,7 +503,7 @@ def run_ours(args):
                        "storage": args.precision, "parallelism": "replicas" if world > 1 else "single GPU",
                        "l2": "inputs larger than L2 (f is %.1f GB)" % f_gb},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
-            "learned_vs_plain": learned,
+            "learned_vs_plain": learned, "lbm": lbm,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -439,6 +515,13 @@ def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.lbm_only:
+        import torch
+        from paper_1503_00707_gb300 import _build
+        _build.build()
+        torch.cuda.set_device(0)
+        print(json.dumps({"lbm": lbm_leg(args)}), flush=True)
+        return 0
     if args.learned_only:
         import torch
         from paper_1503_00707_gb300 import _build

@@ -76,6 +76,8 @@ enum { DVM_F64 = 0, DVM_F32 = 1, DVM_BF16 = 2 };
  *                          correction is applied as the polynomial, so the
  *                          moments stay exact to the solve). */
 enum { DVM_COLL_NONE = 0, DVM_COLL_BGK = 1, DVM_COLL_HS = 2, DVM_COLL_LEARNED = 3, DVM_COLL_BGK_ENTROPIC = 4 };
+/* Lattice Boltzmann velocity sets (Sec. 4), named by their size. */
+enum { DVM_LBM_D2Q9 = 9, DVM_LBM_D3Q19 = 19, DVM_LBM_D3Q27 = 27 };
 enum { DVM_BC_PERIODIC = 0, DVM_BC_INFLOW = 1, DVM_BC_OUTFLOW = 2, DVM_BC_WALL = 3 };
 enum { DVM_PRED_NONE = 0, DVM_PRED_BALL = 1, DVM_PRED_SHELL = 2 };
 
@@ -375,6 +377,76 @@ int dvm_step_partitioned(dvm_ctx *ctx, int nparts, int nsteps, double dt);
  * call before any stream capture.  Like dvm_step it synchronises the stream
  * once to read the status word. */
 int dvm_hs_collide_noalloc(dvm_ctx *ctx, float *f, int64_t ncells, double dt);
+
+/* ------------------------------------------------------------------------
+ * Lattice Boltzmann on the tree (Sec. 4).  The LBM module is the DVM solver
+ * on a minimal velocity set, D2Q9 (2D trees), D3Q19 or D3Q27 (3D trees).
+ *   - Velocities c_i have components in {-1, 0, 1}.  They are ordered by
+ *     increasing |c|^2, ties lexicographic in (c_x, c_y, c_z) with -1 < 0 < 1.
+ *   - Lattice weights w_i depend on |c|^2 only.  c_s^2 = 1/3.
+ *   - Transport is the finite-volume upwind scheme of Eq. 2 on the tree's
+ *     faces, with the tree's boundary conditions.  The inflow ghost is
+ *     feq(rho_in, u_in); outflow takes the cell itself; a wall takes the
+ *     cell's value at the velocity mirrored along the wall's axis.
+ *   - Collision is f <- f - (dt/tau) (f - feq(rho, u)), with rho = sum f,
+ *     rho u = sum c f and feq_i = w_i rho (1 + 3 c_i.u + 4.5 (c_i.u)^2 -
+ *     1.5 |u|^2), applied after transport (Lie splitting).
+ * f is stored in the context's precision, FP64 or FP32 (BF16:
+ * DVM_ENOTIMPL), separately from the DVM f.  Host arrays of f are
+ * [ncells][q] FP64.  Order: build_tree -> lbm_set_lattice -> (lbm_set_inflow)
+ * -> lbm_init_equilibrium / lbm_set_f -> lbm_step.  A mesh change (build,
+ * refine) keeps the lattice and clears f. */
+
+/* Choose the velocity set (DVM_LBM_*) and allocate f (zero) and the upwind
+ * codes.  DVM_EINVAL for an unknown set or one that does not match the
+ * tree's dimension. */
+int dvm_lbm_set_lattice(dvm_ctx *ctx, int lattice);
+
+/* The upwind codes of the current tree (host work only; needs the tree,
+ * not a device).  codes is [2 dim][ncells]: entry (2d + s, cell) describes
+ * the upwind sources of the cell's side s (0 = minus) along axis d as a
+ * 32-bit code:
+ *   bits 0..26  source cell (the inflow ghost is cell ncells), or, with
+ *               bit 30 set, the index in ovf of the side's first entry;
+ *   bit 27      wall: the cell itself at the velocity mirrored along d;
+ *   bits 28..29 m - 1, where the source's weight is m / (2^(dim-1) h) and a
+ *               full side sums to 2^(dim-1); with bit 30 set, the number of
+ *               entries - 1 (entries in ovf use the same format without
+ *               bit 30);
+ *   bit 30      overflow.
+ * *novf receives the number of overflow entries; codes and ovf may be NULL
+ * (size query). */
+int dvm_lbm_get_codes(const dvm_ctx *ctx, uint32_t *codes, uint32_t *ovf, int64_t *novf);
+
+/* The velocity set: c [q][3] and w [q] (q = the set's size). */
+int dvm_lbm_get_velocities(const dvm_ctx *ctx, int32_t *c, double *w);
+
+/* q, the row stride ld of the device f ([q][ld], ld >= ncells + 1) and the
+ * number of overflow upwind entries (sides with 2 or 4 finer sources);
+ * any pointer may be NULL. */
+int dvm_lbm_info(const dvm_ctx *ctx, int *q, int64_t *ld, int64_t *noverflow);
+
+/* Inflow ghost feq(rho, u) (default rho 1, u 0). */
+int dvm_lbm_set_inflow(dvm_ctx *ctx, double rho, const double u[3]);
+
+/* f = feq(rho[c], u[c][:]) in every cell, in FP64 rounded to storage. */
+int dvm_lbm_init_equilibrium(dvm_ctx *ctx, const double *rho, const double *u);
+
+/* Copy f to/from the host as FP64 [ncells][q]; count = ncells * q. */
+int dvm_lbm_set_f(dvm_ctx *ctx, const double *f, int64_t count);
+int dvm_lbm_get_f(dvm_ctx *ctx, double *f, int64_t count);
+
+/* dt = CFL * h_min / max_i sum_{d<dim} |c_{i,d}|. */
+int dvm_lbm_dt_cfl(const dvm_ctx *ctx, double cfl, double *dt);
+
+/* nsteps steps of transport (Eq. 2) then lattice BGK, one fused kernel per
+ * step.  DVM_EUNSTABLE without stepping if dt/tau > 1, and after the steps
+ * if a cell met rho <= 0 or non-finite moments.  Synchronises the stream
+ * once per call. */
+int dvm_lbm_step(dvm_ctx *ctx, int nsteps, double dt, double tau);
+
+/* rho [ncells] and u [ncells][3] of the stored f, in FP64. */
+int dvm_lbm_moments(dvm_ctx *ctx, double *rho, double *u);
 
 /* Number of kernel launches the library has queued in this process. */
 int dvm_launch_count(int64_t *count);

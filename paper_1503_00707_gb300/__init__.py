@@ -19,6 +19,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libdvm.so")
 
 F64, F32, BF16 = 0, 1, 2
 COLL_NONE, COLL_BGK, COLL_HS, COLL_LEARNED, COLL_BGK_ENTROPIC = 0, 1, 2, 3, 4
+LBM_D2Q9, LBM_D3Q19, LBM_D3Q27 = 9, 19, 27
 BC_PERIODIC, BC_INFLOW, BC_OUTFLOW, BC_WALL = 0, 1, 2, 3
 PRED_NONE, PRED_BALL, PRED_SHELL = 0, 1, 2
 
@@ -37,7 +38,9 @@ EXPORTS = [
     "dvm_mlp_forward", "dvm_mlp_loss_grad", "dvm_learned_train", "dvm_learned_configure",
     "dvm_learned_collide", "dvm_learned_pairs", "dvm_learned_fallback_count",
     "dvm_partition_info", "dvm_step_partitioned", "dvm_set_collision_tables_lattice",
-    "dvm_refine_project",
+    "dvm_refine_project", "dvm_lbm_set_lattice", "dvm_lbm_get_velocities", "dvm_lbm_info",
+    "dvm_lbm_set_inflow", "dvm_lbm_init_equilibrium", "dvm_lbm_set_f", "dvm_lbm_get_f",
+    "dvm_lbm_dt_cfl", "dvm_lbm_step", "dvm_lbm_moments", "dvm_lbm_get_codes",
 ]
 MLP_NPARAM = 164672
 HS_NOALLOC_SCRATCH_BYTES = 64 << 20
@@ -126,6 +129,17 @@ def lib():
             "dvm_step_partitioned": [P, C.c_int, C.c_int, d],
             "dvm_set_collision_tables_lattice": [P, C.c_int, C.c_uint64],
             "dvm_refine_project": [P, P, i64],
+            "dvm_lbm_set_lattice": [P, C.c_int],
+            "dvm_lbm_get_velocities": [P, P, P],
+            "dvm_lbm_info": [P, P, P, P],
+            "dvm_lbm_set_inflow": [P, d, P],
+            "dvm_lbm_init_equilibrium": [P, P, P],
+            "dvm_lbm_set_f": [P, P, i64],
+            "dvm_lbm_get_f": [P, P, i64],
+            "dvm_lbm_dt_cfl": [P, d, P],
+            "dvm_lbm_step": [P, C.c_int, d, d],
+            "dvm_lbm_moments": [P, P, P],
+            "dvm_lbm_get_codes": [P, P, P, P],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -181,6 +195,7 @@ class Solver:
 
     def build_tree(self, spec):
         self._chk(lib().dvm_build_tree(self._h, C.byref(spec)))
+        self.dim = spec.dim
         self.counts()
 
     def refine(self, flags):
@@ -391,6 +406,67 @@ class Solver:
         self._chk(lib().dvm_step_moments(self._h, *[_p(a) for a in out]))
         return out
 
+    # ---- lattice Boltzmann (Sec. 4)
+    def lbm_set_lattice(self, lattice):
+        self._chk(lib().dvm_lbm_set_lattice(self._h, int(lattice)))
+        q = C.c_int()
+        self._chk(lib().dvm_lbm_info(self._h, C.byref(q), None, None))
+        self.q = q.value
+
+    def lbm_codes(self):
+        """(codes [2 dim][ncells] uint32, overflow entries) of the current tree
+        (host work, no device needed)."""
+        no = C.c_int64()
+        self._chk(lib().dvm_lbm_get_codes(self._h, None, None, C.byref(no)))
+        dim = self.dim
+        codes = np.zeros((2 * dim, self.ncells), dtype=np.uint32)
+        ovf = np.zeros(max(no.value, 1), dtype=np.uint32)
+        self._chk(lib().dvm_lbm_get_codes(self._h, _p(codes), _p(ovf), C.byref(no)))
+        return codes, ovf[:no.value]
+
+    def lbm_velocities(self):
+        c = np.zeros((self.q, 3), dtype=np.int32)
+        w = np.zeros(self.q)
+        self._chk(lib().dvm_lbm_get_velocities(self._h, _p(c), _p(w)))
+        return c, w
+
+    def lbm_info(self):
+        """(q, row stride ld of the device f, overflow upwind entries)"""
+        q, ld, no = C.c_int(), C.c_int64(), C.c_int64()
+        self._chk(lib().dvm_lbm_info(self._h, C.byref(q), C.byref(ld), C.byref(no)))
+        return q.value, ld.value, no.value
+
+    def lbm_set_inflow(self, rho, u):
+        u = np.ascontiguousarray(u, dtype=np.float64)
+        self._chk(lib().dvm_lbm_set_inflow(self._h, float(rho), _p(u)))
+
+    def lbm_init(self, rho, u):
+        rho = np.ascontiguousarray(rho, dtype=np.float64).reshape(self.ncells)
+        u = np.ascontiguousarray(u, dtype=np.float64).reshape(self.ncells, 3)
+        self._chk(lib().dvm_lbm_init_equilibrium(self._h, _p(rho), _p(u)))
+
+    def lbm_set_f(self, f):
+        f = np.ascontiguousarray(f, dtype=np.float64).reshape(self.ncells, self.q)
+        self._chk(lib().dvm_lbm_set_f(self._h, _p(f), f.size))
+
+    def lbm_get_f(self):
+        f = np.zeros((self.ncells, self.q))
+        self._chk(lib().dvm_lbm_get_f(self._h, _p(f), f.size))
+        return f
+
+    def lbm_dt_cfl(self, cfl):
+        dt = C.c_double()
+        self._chk(lib().dvm_lbm_dt_cfl(self._h, float(cfl), C.byref(dt)))
+        return dt.value
+
+    def lbm_step(self, nsteps, dt, tau):
+        self._chk(lib().dvm_lbm_step(self._h, int(nsteps), float(dt), float(tau)))
+
+    def lbm_moments(self):
+        rho, u = np.zeros(self.ncells), np.zeros((self.ncells, 3))
+        self._chk(lib().dvm_lbm_moments(self._h, _p(rho), _p(u)))
+        return rho, u
+
     @staticmethod
     def launch_count():
         n = C.c_int64()
@@ -398,6 +474,19 @@ class Solver:
         if rc:
             raise DvmError(rc, "dvm_launch_count")
         return n.value
+
+
+def lbm_solver_from_config(cfg, precision=None, stream=None):
+    """A Solver with the tree and lattice of a lattice Boltzmann workload
+    dictionary and its inflow state, without initialising f."""
+    prec = {"f64": F64, "f32": F32}[precision or cfg["precision"]] \
+        if not isinstance(precision, int) else precision
+    s = Solver(prec, COLL_NONE, 1.0, stream=stream)
+    s.build_tree(tree_spec(cfg["dim"], cfg["base_level"], cfg["max_level"], cfg["pred"], cfg["c"],
+                           cfg["r"], cfg["beta"], cfg["solid"], cfg["bc"]))
+    s.lbm_set_lattice(cfg["lattice"])
+    s.lbm_set_inflow(cfg["fs_rho"], cfg["fs_u"])
+    return s
 
 
 def solver_from_config(cfg, precision=None, collision=None, kn=None, stream=None):

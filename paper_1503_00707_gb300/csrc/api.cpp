@@ -12,6 +12,7 @@
 #include "../../include/dvm.h"
 #include "hs.hpp"
 #include "kernels.hpp"
+#include "lbm.hpp"
 #include "learned.hpp"
 #include "mesh.hpp"
 #include "partition.hpp"
@@ -66,6 +67,18 @@ struct dvm_ctx {
     int32_t *d_used = nullptr;      // 1 where the learned term was applied
     int32_t *d_list = nullptr;      // cells left to the hard-sphere operator
     int *d_lcount = nullptr;        // their number
+    // lattice Boltzmann (dvm_lbm_*): velocity set, f as [q][ld] in two
+    // buffers (column ncells the inflow ghost), upwind codes
+    dvm::LbmLattice lat;
+    int lbm_state = 0;              // 0 no lattice, 1 lattice set, 2 f set
+    int64_t lbm_ld = 0, lbm_novf = 0;
+    void *d_lf[2] = {nullptr, nullptr};
+    int lcur = 0;
+    uint32_t *d_lcodes = nullptr, *d_lovf = nullptr;
+    uint8_t *d_llev = nullptr;
+    double *d_lmom = nullptr;
+    int *d_lstatus = nullptr;
+    double l_rho = 1.0, l_u[3] = {0, 0, 0};
 };
 
 namespace {
@@ -147,6 +160,19 @@ void free_grid_buffers(dvm_ctx *c)
 }
 
 int64_t ncells_of(const dvm_ctx *c) { return (int64_t)c->mesh.leaf_of_cell.size(); }
+
+void free_lbm_buffers(dvm_ctx *c)
+{
+    dev_free(c, c->d_lf[0]);
+    dev_free(c, c->d_lf[1]);
+    dev_free(c, reinterpret_cast<void *&>(c->d_lcodes));
+    dev_free(c, reinterpret_cast<void *&>(c->d_lovf));
+    dev_free(c, reinterpret_cast<void *&>(c->d_llev));
+    dev_free(c, reinterpret_cast<void *&>(c->d_lmom));
+    dev_free(c, reinterpret_cast<void *&>(c->d_lstatus));
+    c->lbm_state = 0;
+    c->lbm_ld = c->lbm_novf = 0;
+}
 
 // The mesh is host work; the device is first touched by set_velocity_grid.
 int ensure_device(dvm_ctx *c)
@@ -358,6 +384,7 @@ void dvm_destroy(dvm_ctx *c)
     if (!c) return;
     free_grid_buffers(c);
     free_mesh_buffers(c);
+    free_lbm_buffers(c);
     dvm::hs_free(c->hs, [c](void *p) { void *q = p; dev_free(c, q); });
     dvm::mlp_free(c->mlp, [c](void *p) { void *q = p; dev_free(c, q); });
     if (c->d_status) cudaFree(c->d_status);
@@ -388,8 +415,14 @@ static int after_mesh(dvm_ctx *c)
 {
     free_grid_buffers(c);
     free_mesh_buffers(c);
+    const int lattice = c->lat.kind;
+    free_lbm_buffers(c);
     c->mesh_on_device = false;
     c->state = 1;
+    if (lattice) {
+        const int rc = dvm_lbm_set_lattice(c, lattice);
+        if (rc) return rc;
+    }
     if (c->nv > 0) {
         int n[3] = {c->n[0], c->n[1], c->n[2]};
         double lo[3] = {c->lo[0], c->lo[1], c->lo[2]}, hi[3] = {c->hi[0], c->hi[1], c->hi[2]};
@@ -1320,6 +1353,263 @@ int dvm_learned_fallback_count(dvm_ctx *c, int64_t *n)
     if (!rc) rc = cuda_check(c, cudaStreamSynchronize(c->stream), "count");
     *n = v;
     return rc;
+}
+
+// ---------------------------------------------------------------- lattice Boltzmann
+
+static void lbm_feq(const dvm::LbmLattice &L, double rho, const double u[3], double *out)
+{
+    // second-order equilibrium with c_s^2 = 1/3 (Sec. 4)
+    const double uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    for (int i = 0; i < L.q; i++) {
+        const double cu = L.c[i][0] * u[0] + L.c[i][1] * u[1] + L.c[i][2] * u[2];
+        out[i] = L.w[i] * rho * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * uu);
+    }
+}
+
+static void store_elem(int prec, void *base, size_t k, double v)
+{
+    if (prec == DVM_F64) static_cast<double *>(base)[k] = v;
+    else static_cast<float *>(base)[k] = (float)v;
+}
+
+static double load_elem(int prec, const void *base, size_t k)
+{
+    return prec == DVM_F64 ? static_cast<const double *>(base)[k] : (double)static_cast<const float *>(base)[k];
+}
+
+// the inflow ghost column of both buffers
+static int lbm_upload_ghost(dvm_ctx *c)
+{
+    double g[27];
+    lbm_feq(c->lat, c->l_rho, c->l_u, g);
+    const int prec = c->cfg.precision;
+    const size_t es = elem_size(prec);
+    std::vector<unsigned char> col((size_t)c->lat.q * es);
+    for (int i = 0; i < c->lat.q; i++) store_elem(prec, col.data(), i, g[i]);
+    const int64_t nc = ncells_of(c);
+    for (int b = 0; b < 2; b++) {
+        int rc = cuda_check(c, cudaMemcpy2D(static_cast<char *>(c->d_lf[b]) + nc * es, c->lbm_ld * es, col.data(), es,
+                                            es, c->lat.q, cudaMemcpyHostToDevice), "upload the inflow ghost");
+        if (rc) return rc;
+    }
+    return DVM_OK;
+}
+
+int dvm_lbm_set_lattice(dvm_ctx *c, int lattice)
+{
+    if (!c) return DVM_EINVAL;
+    if (c->state < 1) return fail(c, DVM_ESTATE, "build the tree first");
+    dvm::LbmLattice lat;
+    if (!dvm::lbm_lattice(lattice, lat)) return fail(c, DVM_EINVAL, "unknown lattice");
+    if ((lattice == DVM_LBM_D2Q9) != (c->mesh.spec.dim == 2))
+        return fail(c, DVM_EINVAL, "D2Q9 needs a 2D tree, D3Q19 and D3Q27 a 3D tree");
+    if (c->cfg.precision != DVM_F64 && c->cfg.precision != DVM_F32)
+        return fail(c, DVM_ENOTIMPL, "the lattice Boltzmann step stores f in FP64 or FP32");
+    int rc = ensure_device(c);
+    if (rc) return rc;
+    free_lbm_buffers(c);
+    std::vector<uint32_t> codes, ovf;
+    std::vector<uint8_t> lev;
+    std::string err;
+    rc = dvm::lbm_build_codes(c->mesh, codes, ovf, lev, err);
+    if (rc) return fail(c, rc, err);
+    const int64_t nc = ncells_of(c);
+    const int64_t ld = (nc + 1 + 31) / 32 * 32;
+    const size_t fb = (size_t)lat.q * ld * elem_size(c->cfg.precision);
+    c->d_lf[0] = dev_alloc(c, fb);
+    c->d_lf[1] = dev_alloc(c, fb);
+    c->d_lcodes = dev_alloc_t<uint32_t>(c, codes.size());
+    c->d_lovf = dev_alloc_t<uint32_t>(c, std::max<size_t>(ovf.size(), 1));
+    c->d_llev = dev_alloc_t<uint8_t>(c, std::max<int64_t>(nc, 1));
+    c->d_lmom = dev_alloc_t<double>(c, 4 * std::max<int64_t>(nc, 1));
+    c->d_lstatus = dev_alloc_t<int>(c, 1);
+    if (!c->d_lf[0] || !c->d_lf[1] || !c->d_lcodes || !c->d_lovf || !c->d_llev || !c->d_lmom || !c->d_lstatus) {
+        free_lbm_buffers(c);
+        return fail(c, DVM_ENOMEM, "device allocation (lattice Boltzmann buffers)");
+    }
+    rc = cuda_check(c, cudaMemcpy(c->d_lcodes, codes.data(), codes.size() * 4, cudaMemcpyHostToDevice), "copy codes");
+    if (!rc && !ovf.empty())
+        rc = cuda_check(c, cudaMemcpy(c->d_lovf, ovf.data(), ovf.size() * 4, cudaMemcpyHostToDevice), "copy codes");
+    if (!rc) rc = cuda_check(c, cudaMemcpy(c->d_llev, lev.data(), lev.size(), cudaMemcpyHostToDevice), "copy levels");
+    if (!rc) rc = cuda_check(c, cudaMemset(c->d_lf[0], 0, fb), "clear f");
+    if (!rc) rc = cuda_check(c, cudaMemset(c->d_lf[1], 0, fb), "clear f");
+    if (rc) {
+        free_lbm_buffers(c);
+        return rc;
+    }
+    c->lat = lat;
+    c->lbm_ld = ld;
+    c->lbm_novf = (int64_t)ovf.size();
+    c->lcur = 0;
+    c->lbm_state = 1;
+    return lbm_upload_ghost(c);
+}
+
+int dvm_lbm_get_codes(const dvm_ctx *c, uint32_t *codes, uint32_t *ovf, int64_t *novf)
+{
+    if (!c || !novf) return DVM_EINVAL;
+    if (c->state < 1) return fail(const_cast<dvm_ctx *>(c), DVM_ESTATE, "build the tree first");
+    std::vector<uint32_t> cd, ov;
+    std::vector<uint8_t> lev;
+    std::string err;
+    const int rc = dvm::lbm_build_codes(c->mesh, cd, ov, lev, err);
+    if (rc) return fail(const_cast<dvm_ctx *>(c), rc, err);
+    if (codes) std::memcpy(codes, cd.data(), cd.size() * 4);
+    if (ovf && !ov.empty()) std::memcpy(ovf, ov.data(), ov.size() * 4);
+    *novf = (int64_t)ov.size();
+    return DVM_OK;
+}
+
+int dvm_lbm_get_velocities(const dvm_ctx *c, int32_t *cv, double *w)
+{
+    if (!c || !cv || !w) return DVM_EINVAL;
+    if (c->lbm_state < 1) return DVM_ESTATE;
+    for (int i = 0; i < c->lat.q; i++) {
+        for (int d = 0; d < 3; d++) cv[3 * i + d] = c->lat.c[i][d];
+        w[i] = c->lat.w[i];
+    }
+    return DVM_OK;
+}
+
+int dvm_lbm_info(const dvm_ctx *c, int *q, int64_t *ld, int64_t *noverflow)
+{
+    if (!c) return DVM_EINVAL;
+    if (c->lbm_state < 1) return DVM_ESTATE;
+    if (q) *q = c->lat.q;
+    if (ld) *ld = c->lbm_ld;
+    if (noverflow) *noverflow = c->lbm_novf;
+    return DVM_OK;
+}
+
+int dvm_lbm_set_inflow(dvm_ctx *c, double rho, const double u[3])
+{
+    if (!c || !u || !(rho > 0.0)) return DVM_EINVAL;
+    if (c->lbm_state < 1) return fail(c, DVM_ESTATE, "set the lattice first");
+    c->l_rho = rho;
+    for (int d = 0; d < 3; d++) c->l_u[d] = u[d];
+    return lbm_upload_ghost(c);
+}
+
+// host [q][ld] image in storage precision -> the current buffer
+static int lbm_upload(dvm_ctx *c, const std::vector<unsigned char> &img)
+{
+    int rc = cuda_check(c, cudaMemcpy(c->d_lf[c->lcur], img.data(), img.size(), cudaMemcpyHostToDevice), "upload f");
+    if (!rc) rc = lbm_upload_ghost(c);
+    if (!rc) c->lbm_state = 2;
+    return rc;
+}
+
+int dvm_lbm_init_equilibrium(dvm_ctx *c, const double *rho, const double *u)
+{
+    if (!c || !rho || !u) return DVM_EINVAL;
+    if (c->lbm_state < 1) return fail(c, DVM_ESTATE, "set the lattice first");
+    const int64_t nc = ncells_of(c), ld = c->lbm_ld;
+    const int prec = c->cfg.precision;
+    std::vector<unsigned char> img((size_t)c->lat.q * ld * elem_size(prec), 0);
+    double g[27];
+    for (int64_t q = 0; q < nc; q++) {
+        lbm_feq(c->lat, rho[q], &u[3 * q], g);
+        for (int i = 0; i < c->lat.q; i++) store_elem(prec, img.data(), (size_t)i * ld + q, g[i]);
+    }
+    return lbm_upload(c, img);
+}
+
+int dvm_lbm_set_f(dvm_ctx *c, const double *f, int64_t count)
+{
+    if (!c || !f) return DVM_EINVAL;
+    if (c->lbm_state < 1) return fail(c, DVM_ESTATE, "set the lattice first");
+    const int64_t nc = ncells_of(c), ld = c->lbm_ld;
+    if (count != nc * c->lat.q) return fail(c, DVM_EINVAL, "count differs from ncells * q");
+    const int prec = c->cfg.precision;
+    std::vector<unsigned char> img((size_t)c->lat.q * ld * elem_size(prec), 0);
+    for (int64_t q = 0; q < nc; q++)
+        for (int i = 0; i < c->lat.q; i++) store_elem(prec, img.data(), (size_t)i * ld + q, f[q * c->lat.q + i]);
+    return lbm_upload(c, img);
+}
+
+int dvm_lbm_get_f(dvm_ctx *c, double *f, int64_t count)
+{
+    if (!c || !f) return DVM_EINVAL;
+    if (c->lbm_state < 2) return fail(c, DVM_ESTATE, "f is not set");
+    const int64_t nc = ncells_of(c), ld = c->lbm_ld;
+    if (count != nc * c->lat.q) return fail(c, DVM_EINVAL, "count differs from ncells * q");
+    const int prec = c->cfg.precision;
+    std::vector<unsigned char> img((size_t)c->lat.q * ld * elem_size(prec));
+    int rc = cuda_check(c, cudaStreamSynchronize(c->stream), "download f");
+    if (!rc) rc = cuda_check(c, cudaMemcpy(img.data(), c->d_lf[c->lcur], img.size(), cudaMemcpyDeviceToHost), "download f");
+    if (rc) return rc;
+    for (int64_t q = 0; q < nc; q++)
+        for (int i = 0; i < c->lat.q; i++) f[q * c->lat.q + i] = load_elem(prec, img.data(), (size_t)i * ld + q);
+    return DVM_OK;
+}
+
+int dvm_lbm_dt_cfl(const dvm_ctx *c, double cfl, double *dt)
+{
+    if (!c || !dt || !(cfl > 0.0)) return DVM_EINVAL;
+    if (c->lbm_state < 1) return DVM_ESTATE;
+    int smax = 0;
+    for (int i = 0; i < c->lat.q; i++) {
+        int s = 0;
+        for (int d = 0; d < c->mesh.spec.dim; d++) s += std::abs(c->lat.c[i][d]);
+        smax = std::max(smax, s);
+    }
+    *dt = cfl * std::ldexp(1.0, -c->mesh.max_cell_level) / smax;
+    return DVM_OK;
+}
+
+int dvm_lbm_step(dvm_ctx *c, int nsteps, double dt, double tau)
+{
+    if (!c || nsteps < 0 || !(dt > 0.0) || !(tau > 0.0)) return DVM_EINVAL;
+    if (c->lbm_state < 2) return fail(c, DVM_ESTATE, "f is not set");
+    if (dt / tau > 1.0) return fail(c, DVM_EUNSTABLE, "dt / tau above 1");
+    if (nsteps == 0) return DVM_OK;
+    int rc = cuda_check(c, cudaMemsetAsync(c->d_lstatus, 0, sizeof(int), c->stream), "clear status");
+    if (rc) return rc;
+    dvm::LbmParams p{};
+    p.prec = c->cfg.precision;
+    p.dim = c->mesh.spec.dim;
+    p.q = c->lat.q;
+    p.ncells = ncells_of(c);
+    p.ld = c->lbm_ld;
+    p.codes = c->d_lcodes;
+    p.ovf = c->d_lovf;
+    p.lev = c->d_llev;
+    p.dt = dt;
+    p.omega = dt / tau;
+    p.status = c->d_lstatus;
+    p.stream = c->stream;
+    for (int s = 0; s < nsteps; s++) {
+        p.f_in = c->d_lf[c->lcur];
+        p.f_out = c->d_lf[c->lcur ^ 1];
+        rc = dvm::launch_lbm(p);
+        if (rc) return fail(c, rc, std::string("lattice Boltzmann launch: ") + cudaGetErrorString(cudaGetLastError()));
+        c->lcur ^= 1;
+    }
+    int st = 0;
+    rc = cuda_check(c, cudaMemcpyAsync(&st, c->d_lstatus, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "status");
+    if (!rc) rc = cuda_check(c, cudaStreamSynchronize(c->stream), "lattice Boltzmann step");
+    if (rc) return rc;
+    if (st) return fail(c, DVM_EUNSTABLE, "a cell reached rho <= 0 or non-finite moments");
+    return DVM_OK;
+}
+
+int dvm_lbm_moments(dvm_ctx *c, double *rho, double *u)
+{
+    if (!c || !rho || !u) return DVM_EINVAL;
+    if (c->lbm_state < 2) return fail(c, DVM_ESTATE, "f is not set");
+    const int64_t nc = ncells_of(c);
+    int rc = dvm::launch_lbm_moments(c->cfg.precision, c->lat.q, c->d_lf[c->lcur], nc, c->lbm_ld, c->d_lmom, c->stream);
+    if (rc) return fail(c, rc, "lattice Boltzmann moments launch");
+    std::vector<double> m((size_t)nc * 4);
+    rc = cuda_check(c, cudaMemcpyAsync(m.data(), c->d_lmom, m.size() * 8, cudaMemcpyDeviceToHost, c->stream), "moments");
+    if (!rc) rc = cuda_check(c, cudaStreamSynchronize(c->stream), "moments");
+    if (rc) return rc;
+    for (int64_t q = 0; q < nc; q++) {
+        rho[q] = m[4 * q];
+        for (int d = 0; d < 3; d++) u[3 * q + d] = m[4 * q + 1 + d];
+    }
+    return DVM_OK;
 }
 
 int dvm_launch_count(int64_t *count)

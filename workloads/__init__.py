@@ -79,6 +79,41 @@ CONFIGS = {
 }
 CONFIGS["c5_sphere_m3_hs"]["trials"] = 128
 
+# ---- lattice Boltzmann (Sec. 4).  The paper's LBM flow is a sphere at
+# Ma = 0.5 and Re = 1000 with D3Q19 (Fig. 9); its GPU timings use trees of
+# 100K and 1M cells (Table 1).  Lattice units: c_s = 1/sqrt(3), so Ma 0.5 is
+# u = 0.5/sqrt(3).  Each flow fixes omega = dt/tau; tau then follows from the
+# CFL time step, and Re = U D / (c_s^2 tau) with D = 2r.
+LBM_D2Q9, LBM_D3Q19, LBM_D3Q27 = 9, 19, 27
+
+
+def _lbm_sphere(lattice, base, top, r, beta, omega, cfl, precision, steps):
+    return dict(
+        lattice=lattice, dim=3, base_level=base, max_level=top, pred=PRED_SHELL, c=(0.5, 0.5, 0.5),
+        r=r, beta=beta, solid=1, bc=(INFLOW, OUTFLOW, OUTFLOW, OUTFLOW, OUTFLOW, OUTFLOW),
+        fs_rho=1.0, fs_u=(0.5 / math.sqrt(3.0), 0.0, 0.0), omega=omega, cfl=cfl,
+        precision=precision, steps=steps, init="lbm_perturbed",
+    )
+
+
+CONFIGS.update({
+    # 2D quadtree levels 4-7 around a solid disk r=0.1 (walls), inflow at
+    # x=0, outflow at x=1, periodic in y; D2Q9, u = 0.1; FP64.
+    "l1_2d_disk_d2q9": dict(
+        lattice=LBM_D2Q9, dim=2, base_level=4, max_level=7, pred=PRED_SHELL, c=(0.5, 0.5, 0.5),
+        r=0.1, beta=3.0, solid=1, bc=(INFLOW, OUTFLOW, PERIODIC, PERIODIC, PERIODIC, PERIODIC),
+        fs_rho=1.0, fs_u=(0.1, 0.0, 0.0), omega=0.5, cfl=0.4, precision="f64", steps=30,
+        init="lbm_perturbed",
+    ),
+    # the Ma-0.5 sphere flow on the 17.7k-cell tree of levels 4-6 (oracle-sized)
+    "l2_sphere_d3q19_small": _lbm_sphere(LBM_D3Q19, 4, 6, 0.1, 3.0, 0.5, 0.4, "f32", 10),
+    "l2_sphere_d3q27_small": _lbm_sphere(LBM_D3Q27, 4, 6, 0.1, 3.0, 0.5, 0.4, "f32", 10),
+    # levels 7-10 around the sphere: 3.34M cells (f is 254 MB per buffer for
+    # D3Q19 in FP32, twice L2); omega 0.85 at CFL 0.3 gives Re ~ 1000
+    "l3_sphere_d3q19": _lbm_sphere(LBM_D3Q19, 7, 10, 0.1, 3.0, 0.85, 0.3, "f32", 100),
+    "l3_sphere_d3q27": _lbm_sphere(LBM_D3Q27, 7, 10, 0.1, 3.0, 0.85, 0.3, "f32", 100),
+})
+
 
 def initial_state(cfg, centres, seed=SEED):
     """Per-cell Maxwellian mixture parameters for `init_maxwellian`.
@@ -117,6 +152,23 @@ def initial_state(cfg, centres, seed=SEED):
         T = np.stack([T1, T2], axis=1)
         return w, rho, u, T
     raise ValueError(kind)
+
+
+def lbm_initial_state(cfg, centres, seed=SEED):
+    """Per-cell (rho [nc], u [nc, 3]) for the lattice Boltzmann flows: the
+    inflow state with seeded perturbations (2% in rho, 0.02 in each active
+    velocity component), so that every term of the step is exercised."""
+    centres = np.asarray(centres, dtype=np.float64)
+    nc = centres.shape[0]
+    g = np.random.default_rng(seed + 7)
+    rho = cfg["fs_rho"] * (1.0 + 0.02 * g.uniform(-1.0, 1.0, nc))
+    u = np.tile(np.asarray(cfg["fs_u"], dtype=np.float64), (nc, 1))
+    u[:, :cfg["dim"]] += 0.02 * g.uniform(-1.0, 1.0, (nc, cfg["dim"]))
+    return rho, u
+
+
+def lbm_tau(cfg, dt):
+    return dt / cfg["omega"]
 
 
 def random_f_perturbation(ncells, nv, seed=SEED, scale=0.05):
