@@ -97,78 +97,117 @@ template <int Q> struct ForV<Q, Q> {
     template <typename F> __device__ __forceinline__ static void run(F &&) {}
 };
 
-// the upwind value of velocity i on side code cd (axis d): sum_e m_e f_e,
-// f_e = f at the source cell, or at the cell itself with the velocity
-// mirrored along d for a wall; the side's weights sum to 2^(dim-1)
-template <typename T, int Q, int I, int D>
-__device__ __forceinline__ T upwind(const T *__restrict__ fin, int64_t ld, uint32_t cd, int64_t cell,
-                                    const uint32_t *__restrict__ ovf)
+// the side list (2d + s) whose sources velocity i takes along axis d: the
+// minus side for c_d > 0, the plus side for c_d < 0
+template <int Q> __host__ __device__ constexpr int side_of(int i, int d)
 {
-    constexpr int jm = Lat<Q>::t.mirror[I][D];
-    if (!(cd & LBM_OVF)) {
-        const int64_t src = cd & LBM_CELL;
-        const int j = (cd & LBM_WALL) ? jm : I;
-        const T v = __ldg(fin + (int64_t)j * ld + src);
-        const uint32_t m = (cd >> LBM_M_SHIFT) & 3u;
-        return m == 3u ? T(4) * v : m == 1u ? T(2) * v : m == 0u ? v : T(3) * v;
+    return Lat<Q>::t.c[i][d] > 0 ? 2 * d : 2 * d + 1;
+}
+
+// compile-time loop over the 2 dim sides
+template <int K, int NS> struct ForS {
+    template <typename F> __device__ __forceinline__ static void run(F &&f)
+    {
+        f(std::integral_constant<int, K>{});
+        ForS<K + 1, NS>::run(f);
     }
-    const uint32_t base = cd & LBM_CELL;
-    const int n = (int)((cd >> LBM_M_SHIFT) & 3u) + 1;
-    T s = T(0);
-    for (int e = 0; e < n; e++) {
-        const uint32_t ce = __ldg(ovf + base + e);
-        const int64_t src = ce & LBM_CELL;
-        const int j = (ce & LBM_WALL) ? jm : I;
-        const T v = __ldg(fin + (int64_t)j * ld + src);
-        s += T((int)((ce >> LBM_M_SHIFT) & 3u) + 1) * v;
-    }
-    return s;
+};
+template <int NS> struct ForS<NS, NS> {
+    template <typename F> __device__ __forceinline__ static void run(F &&) {}
+};
+
+// g_i += w f_e for every velocity i that takes side K, f_e the source's
+// value of velocity i (or of its mirror along the side's axis for a wall)
+template <typename T, int Q, int K>
+__device__ __forceinline__ void add_side(T (&g)[Q], const T *__restrict__ fin, int64_t ld, int64_t src, bool wall,
+                                         T w)
+{
+    constexpr int d = K / 2;
+    ForV<0, Q>::run([&](auto II) {
+        constexpr int i = decltype(II)::value;
+        if constexpr (Lat<Q>::t.c[i][d] != 0 && side_of<Q>(i, d) == K) {
+            constexpr int jm = Lat<Q>::t.mirror[i][d];
+            g[i] += w * __ldg(fin + (int64_t)(wall ? jm : i) * ld + src);
+        }
+    });
+}
+
+// Fused step.  Every side's first source is decoded once (a side with
+// several finer sources starts from its first overflow entry), and all
+// first-source gathers are issued without branches, so a thread keeps its
+// gathers in flight together; the remaining entries of sides with 2 or 4
+// finer sources are added in a second pass that few threads take.
+// CTAs of 256 threads per SM that the register budget is sized for: more
+// registers keep more of a thread's gathers in flight, more CTAs hide more
+// latency
+__host__ __device__ constexpr int lbm_min_blocks(int Q, int tsize)
+{
+    return tsize == 8 ? 2 : Q == 27 ? 3 : Q == 19 ? 4 : 4;
 }
 
 template <typename T, int DIM, int Q>
-__global__ void __launch_bounds__(256, 1) k_lbm(const LbmParams p)
+__global__ void __launch_bounds__(256, lbm_min_blocks(Q, sizeof(T))) k_lbm(const LbmParams p)
 {
     const int64_t cell = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (cell >= p.ncells) return;
     const T *__restrict__ fin = static_cast<const T *>(p.f_in);
     T *__restrict__ fout = static_cast<T *>(p.f_out);
     const int64_t ld = p.ld, nc = p.ncells;
-    uint32_t code[2 * DIM];
+    constexpr int NS = 2 * DIM;
+    uint32_t code[NS];
 #pragma unroll
-    for (int k = 0; k < 2 * DIM; k++) code[k] = __ldg(p.codes + (int64_t)k * nc + cell);
+    for (int k = 0; k < NS; k++) code[k] = __ldg(p.codes + (int64_t)k * nc + cell);
     // dt / h and dt / (2^(dim-1) h), h = 2^-level
-    const T dth = T(p.dt) * T(1ull << p.lev[cell]);
+    const T dth = T(p.dt) * T(1ull << __ldg(p.lev + cell));
     const T dtq = dth * (T(1) / T(1 << (DIM - 1)));
-    T f[Q];
-    ForV<0, Q>::run([&](auto II) {
-        constexpr int i = decltype(II)::value;
-        f[i] = __ldg(fin + (int64_t)i * ld + cell);
-    });
-    // transport, Eq. 2: f*_i = f_i - dt sum_d |c_id| (f_i / h - upwind_d / (2^(dim-1) h))
+    // f_i (1 - dt n_i / h), n_i the number of non-zero components of c_i
+    T g[Q];
     ForV<0, Q>::run([&](auto II) {
         constexpr int i = decltype(II)::value;
         constexpr int cx = Lat<Q>::t.c[i][0], cy = Lat<Q>::t.c[i][1], cz = Lat<Q>::t.c[i][2];
         constexpr int na = (cx != 0) + (cy != 0) + (DIM == 3 && cz != 0);
-        if constexpr (na > 0) {
-            T in = T(0);
-            if constexpr (cx != 0) in += upwind<T, Q, i, 0>(fin, ld, code[cx > 0 ? 0 : 1], cell, p.ovf);
-            if constexpr (cy != 0) in += upwind<T, Q, i, 1>(fin, ld, code[cy > 0 ? 2 : 3], cell, p.ovf);
-            if constexpr (DIM == 3 && cz != 0) in += upwind<T, Q, i, 2>(fin, ld, code[cz > 0 ? 4 : 5], cell, p.ovf);
-            f[i] = f[i] - dth * T(na) * f[i] + dtq * in;
-        }
+        const T v = __ldg(fin + (int64_t)i * ld + cell);
+        g[i] = v - dth * T(na) * v;
     });
+    // transport, Eq. 2: add dt m_e f_e / (2^(dim-1) h) over each upwind
+    // side's sources, first sources for all sides at once
+    bool any_ovf = false;
+    ForS<0, NS>::run([&](auto KK) {
+        constexpr int k = decltype(KK)::value;
+        uint32_t e = code[k];
+        if (e & LBM_OVF) {
+            any_ovf = true;
+            e = __ldg(p.ovf + (e & LBM_CELL));
+        }
+        add_side<T, Q, k>(g, fin, ld, e & LBM_CELL, (e & LBM_WALL) != 0,
+                          dtq * T((int)((e >> LBM_M_SHIFT) & 3u) + 1));
+    });
+    if (any_ovf) {
+        ForS<0, NS>::run([&](auto KK) {
+            constexpr int k = decltype(KK)::value;
+            if (code[k] & LBM_OVF) {
+                const uint32_t base = code[k] & LBM_CELL;
+                const int n = (int)((code[k] >> LBM_M_SHIFT) & 3u) + 1;
+                for (int j = 1; j < n; j++) {
+                    const uint32_t e = __ldg(p.ovf + base + j);
+                    add_side<T, Q, k>(g, fin, ld, e & LBM_CELL, (e & LBM_WALL) != 0,
+                                      dtq * T((int)((e >> LBM_M_SHIFT) & 3u) + 1));
+                }
+            }
+        });
+    }
     // moments of f*
     T rho = T(0), jx = T(0), jy = T(0), jz = T(0);
     ForV<0, Q>::run([&](auto II) {
         constexpr int i = decltype(II)::value;
         constexpr int cx = Lat<Q>::t.c[i][0], cy = Lat<Q>::t.c[i][1], cz = Lat<Q>::t.c[i][2];
-        rho += f[i];
-        if constexpr (cx > 0) jx += f[i];
-        if constexpr (cx < 0) jx -= f[i];
-        if constexpr (cy > 0) jy += f[i];
-        if constexpr (cy < 0) jy -= f[i];
-        if constexpr (cz > 0) jz += f[i];
-        if constexpr (cz < 0) jz -= f[i];
+        rho += g[i];
+        if constexpr (cx > 0) jx += g[i];
+        if constexpr (cx < 0) jx -= g[i];
+        if constexpr (cy > 0) jy += g[i];
+        if constexpr (cy < 0) jy -= g[i];
+        if constexpr (cz > 0) jz += g[i];
+        if constexpr (cz < 0) jz -= g[i];
     });
     const T irho = T(1) / rho;
     const T ux = jx * irho, uy = jy * irho, uz = jz * irho;
@@ -179,10 +218,10 @@ __global__ void __launch_bounds__(256, 1) k_lbm(const LbmParams p)
     ForV<0, Q>::run([&](auto II) {
         constexpr int i = decltype(II)::value;
         constexpr int cx = Lat<Q>::t.c[i][0], cy = Lat<Q>::t.c[i][1], cz = Lat<Q>::t.c[i][2];
-        const T cu = T(cx) * ux + T(cy) * uy + T(cz) * uz;
         constexpr int r2 = Lat<Q>::t.r2[i];
+        const T cu = T(cx) * ux + T(cy) * uy + T(cz) * uz;
         const T feq = lat_w<T, Q>(r2) * rho * (q0 + cu * (T(3) + T(4.5) * cu));
-        fout[(int64_t)i * ld + cell] = f[i] - om * (f[i] - feq);
+        fout[(int64_t)i * ld + cell] = g[i] - om * (g[i] - feq);
     });
 }
 
