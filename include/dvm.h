@@ -152,6 +152,35 @@ int dvm_refine(dvm_ctx *ctx, const uint8_t *flag, int64_t nleaves);
  * buffers; the step moments are invalidated. */
 int dvm_refine_project(dvm_ctx *ctx, const uint8_t *flag, int64_t nleaves);
 
+/* Coarsening (the inverse of dvm_refine; the paper's adaptive runs refine
+ * and coarsen with the flow, Sec. 2.1).  flag[nleaves] marks leaves.  Every
+ * group of 2^dim sibling leaves that are all flagged, whose parent is at or
+ * above the base level, merges into its parent, unless the parent would
+ * then touch a leaf two or more levels finer (2:1 balance across faces,
+ * edges and corners).  Groups are undone one by one until no parent breaks
+ * the balance.  The parent is solid if its centre is inside the sphere (the
+ * rule of the tree build).  Like dvm_refine, the mesh alone: f is cleared. */
+int dvm_coarsen(dvm_ctx *ctx, const uint8_t *flag, int64_t nleaves);
+
+/* dvm_coarsen with f carried over: an unchanged cell keeps its f, and a
+ * merged parent takes the mean of its children's f over the fluid children
+ * (equal volumes, so mass, momentum and energy are kept when all children
+ * are fluid), or the freestream if all were solid. */
+int dvm_coarsen_project(dvm_ctx *ctx, const uint8_t *flag, int64_t nleaves);
+
+/* Local Knudsen number of every cell (the continuum-breakdown sensor, Sec.
+ * 2.3 and Sec. 3.4): Kn_loc = (Kn / rho) max(|grad rho|/rho, |grad T|/T,
+ * |grad u|/sqrt(T)) (the local mean free path Kn/rho over the gradient
+ * length) from the moments of the stored f, each gradient a
+ * face-weighted least-squares fit over the fluid face neighbours (weights
+ * area / |d|^2).  knl [ncells]. */
+int dvm_kn_local(dvm_ctx *ctx, double *knl);
+
+/* Kinetic/fluid flags from the local Knudsen number: kinetic[c] = 1 where
+ * Kn_loc > threshold (the cells the Boltzmann solver keeps), else 0; the
+ * number of kinetic cells in *nkinetic (may be NULL). */
+int dvm_flag_kinetic(dvm_ctx *ctx, double threshold, uint8_t *kinetic, int64_t *nkinetic);
+
 /* Sizes: leaves (including solid ones), cells (non-solid leaves), interior
  * faces, boundary faces, velocity nodes (0 before set_velocity_grid).  Any
  * pointer may be NULL. */

@@ -41,6 +41,7 @@ EXPORTS = [
     "dvm_refine_project", "dvm_lbm_set_lattice", "dvm_lbm_get_velocities", "dvm_lbm_info",
     "dvm_lbm_set_inflow", "dvm_lbm_init_equilibrium", "dvm_lbm_set_f", "dvm_lbm_get_f",
     "dvm_lbm_dt_cfl", "dvm_lbm_step", "dvm_lbm_moments", "dvm_lbm_get_codes",
+    "dvm_coarsen", "dvm_coarsen_project", "dvm_kn_local", "dvm_flag_kinetic",
 ]
 MLP_NPARAM = 164672
 HS_NOALLOC_SCRATCH_BYTES = 64 << 20
@@ -140,6 +141,10 @@ def lib():
             "dvm_lbm_step": [P, C.c_int, d, d],
             "dvm_lbm_moments": [P, P, P],
             "dvm_lbm_get_codes": [P, P, P, P],
+            "dvm_coarsen": [P, P, i64],
+            "dvm_coarsen_project": [P, P, i64],
+            "dvm_kn_local": [P, P],
+            "dvm_flag_kinetic": [P, d, P, P],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -197,6 +202,27 @@ class Solver:
         self._chk(lib().dvm_build_tree(self._h, C.byref(spec)))
         self.dim = spec.dim
         self.counts()
+
+    def coarsen(self, flags):
+        flags = np.ascontiguousarray(flags, dtype=np.uint8)
+        self._chk(lib().dvm_coarsen(self._h, _p(flags), len(flags)))
+        self.counts()
+
+    def coarsen_project(self, flags):
+        flags = np.ascontiguousarray(flags, dtype=np.uint8)
+        self._chk(lib().dvm_coarsen_project(self._h, _p(flags), len(flags)))
+        self.counts()
+
+    def kn_local(self):
+        knl = np.zeros(self.ncells)
+        self._chk(lib().dvm_kn_local(self._h, _p(knl)))
+        return knl
+
+    def flag_kinetic(self, threshold):
+        flags = np.zeros(self.ncells, dtype=np.uint8)
+        n = C.c_int64()
+        self._chk(lib().dvm_flag_kinetic(self._h, float(threshold), _p(flags), C.byref(n)))
+        return flags, n.value
 
     def refine(self, flags):
         flags = np.ascontiguousarray(flags, dtype=np.uint8)

@@ -7,6 +7,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 #include "../../include/dvm.h"
@@ -79,6 +80,10 @@ struct dvm_ctx {
     double *d_lmom = nullptr;
     int *d_lstatus = nullptr;
     double l_rho = 1.0, l_u[3] = {0, 0, 0};
+    // local-Kn sensor outside the learned collision (dvm_kn_local)
+    int64_t ks_cells = 0;
+    int32_t *d_ks_start = nullptr, *d_ks_nb = nullptr;
+    double *d_ks_coef = nullptr, *d_ks_knl = nullptr;
 };
 
 namespace {
@@ -140,6 +145,11 @@ void free_learned_buffers(dvm_ctx *c)
 void free_mesh_buffers(dvm_ctx *c)
 {
     free_learned_buffers(c);
+    dev_free(c, reinterpret_cast<void *&>(c->d_ks_start));
+    dev_free(c, reinterpret_cast<void *&>(c->d_ks_nb));
+    dev_free(c, reinterpret_cast<void *&>(c->d_ks_coef));
+    dev_free(c, reinterpret_cast<void *&>(c->d_ks_knl));
+    c->ks_cells = 0;
     dev_free(c, reinterpret_cast<void *&>(c->d_src));
     dev_free(c, c->d_w);
     dev_free(c, reinterpret_cast<void *&>(c->d_cnt));
@@ -502,6 +512,82 @@ int dvm_refine_project(dvm_ctx *c, const uint8_t *flag, int64_t n)
         if (!rc) rc = cuda_check(c, cudaStreamSynchronize(c->stream), "projection");
     }
     void *p1 = d_bufs, *p2 = d_rows;
+    dev_free(c, p1);
+    dev_free(c, p2);
+    dev_free(c, oldf);
+    if (rc) return rc;
+    c->state = 3;
+    c->have_step_moments = false;
+    return DVM_OK;
+}
+
+int dvm_coarsen(dvm_ctx *c, const uint8_t *flag, int64_t n)
+{
+    if (!c || !flag) return DVM_EINVAL;
+    if (c->state < 1) return fail(c, DVM_ESTATE, "build the tree first");
+    std::string err;
+    int rc = dvm::coarsen_mesh(c->mesh, flag, n, err);
+    if (rc) return fail(c, rc, err);
+    return after_mesh(c);
+}
+
+int dvm_coarsen_project(dvm_ctx *c, const uint8_t *flag, int64_t n)
+{
+    if (!c || !flag) return DVM_EINVAL;
+    if (c->state < 3) return fail(c, DVM_ESTATE, "f is not set (dvm_coarsen changes the mesh alone)");
+    const dvm::Mesh old = c->mesh;
+    const int64_t onc = ncells_of(c);
+    std::string err;
+    int rc = dvm::coarsen_mesh(c->mesh, flag, n, err);
+    if (rc) return fail(c, rc, err);
+    void *oldf = c->d_f[c->cur];
+    c->d_f[c->cur] = nullptr;
+    rc = after_mesh(c);
+    // each new cell: its own old cell if its leaf is unchanged, else the mean
+    // of the old fluid cells among its 2^dim children (the freestream ghost
+    // row when all of them were solid)
+    std::vector<int64_t> start, idx;
+    if (!rc) {
+        const dvm::Mesh &m = c->mesh;
+        const int dim = m.spec.dim, L = m.spec.max_level;
+        std::unordered_map<uint64_t, int64_t> at;  // (level, Morton key) of an old leaf -> old cell
+        at.reserve(old.leaves.size() * 2);
+        for (size_t q = 0; q < old.leaves.size(); q++)
+            at[old.leaves[q].key * 64 + (uint64_t)old.leaves[q].lev] = old.cell_of_leaf[q];
+        const int64_t nnc = ncells_of(c);
+        start.reserve(nnc + 1);
+        start.push_back(0);
+        for (int64_t q = 0; q < nnc; q++) {
+            const dvm::Leaf &x = m.leaves[m.leaf_of_cell[q]];
+            const auto it = at.find(x.key * 64 + (uint64_t)x.lev);
+            if (it != at.end() && it->second >= 0) {
+                idx.push_back(it->second);
+            } else {
+                // children of a merged parent share its key prefix; child k
+                // sets the dim bits below the parent's level
+                const int sh = dim * (L - x.lev - 1);
+                size_t before = idx.size();
+                for (int k = 0; k < (1 << dim); k++) {
+                    const auto jt = at.find((x.key | ((uint64_t)k << sh)) * 64 + (uint64_t)(x.lev + 1));
+                    if (jt != at.end() && jt->second >= 0) idx.push_back(jt->second);
+                }
+                if (idx.size() == before) idx.push_back(onc);
+            }
+            start.push_back((int64_t)idx.size());
+        }
+    }
+    int64_t *d_start = nullptr, *d_idx = nullptr;
+    if (!rc) {
+        d_start = dev_alloc_t<int64_t>(c, start.size());
+        d_idx = dev_alloc_t<int64_t>(c, std::max<size_t>(idx.size(), 1));
+        if (!d_start || !d_idx) rc = fail(c, DVM_ENOMEM, "device allocation (projection)");
+    }
+    if (!rc) rc = cuda_check(c, cudaMemcpy(d_start, start.data(), start.size() * 8, cudaMemcpyHostToDevice), "projection");
+    if (!rc) rc = cuda_check(c, cudaMemcpy(d_idx, idx.data(), idx.size() * 8, cudaMemcpyHostToDevice), "projection");
+    if (!rc) rc = dvm::launch_mean_rows(c->cfg.precision, c->d_f[c->cur], oldf, d_start, d_idx,
+                                        (int64_t)start.size() - 1, c->nv, c->stream);
+    if (!rc) rc = cuda_check(c, cudaStreamSynchronize(c->stream), "projection");
+    void *p1 = d_start, *p2 = d_idx;
     dev_free(c, p1);
     dev_free(c, p2);
     dev_free(c, oldf);
@@ -1100,6 +1186,65 @@ int dvm_moments(dvm_ctx *c, double *rho, double *u, double *T)
     int rc = dvm::launch_moments(c->cfg.precision, c->d_f[c->cur], ncells_of(c), c->nv, c->d_xi, c->dV, c->d_mom2, c->stream);
     if (rc) return fail(c, rc, "moments launch failed");
     return copy_moments(c, c->d_mom2, rho, u, T);
+}
+
+// Local Knudsen number of every cell from the moments of the stored f (the
+// continuum-breakdown sensor of Sec. 2.3 / Sec. 3.4); its sensor stencil is
+// built on first use for the current mesh.
+static int kn_local_device(dvm_ctx *c)
+{
+    const int64_t nc = ncells_of(c);
+    if (c->ks_cells != nc) {
+        dev_free(c, reinterpret_cast<void *&>(c->d_ks_start));
+        dev_free(c, reinterpret_cast<void *&>(c->d_ks_nb));
+        dev_free(c, reinterpret_cast<void *&>(c->d_ks_coef));
+        dev_free(c, reinterpret_cast<void *&>(c->d_ks_knl));
+        c->ks_cells = 0;
+        dvm::KnStencil ks;
+        dvm::build_kn_stencil(c->mesh, ks);
+        const size_t ne = ks.nb.size();
+        c->d_ks_start = dev_alloc_t<int32_t>(c, (size_t)nc + 1);
+        c->d_ks_nb = dev_alloc_t<int32_t>(c, std::max<size_t>(ne, 1));
+        c->d_ks_coef = dev_alloc_t<double>(c, 3 * std::max<size_t>(ne, 1));
+        c->d_ks_knl = dev_alloc_t<double>(c, (size_t)nc);
+        if (!c->d_ks_start || !c->d_ks_nb || !c->d_ks_coef || !c->d_ks_knl)
+            return fail(c, DVM_ENOMEM, "device allocation (Knudsen sensor)");
+        int rc = cuda_check(c, cudaMemcpy(c->d_ks_start, ks.start.data(), ks.start.size() * 4, cudaMemcpyHostToDevice), "copy sensor stencil");
+        if (!rc && ne) rc = cuda_check(c, cudaMemcpy(c->d_ks_nb, ks.nb.data(), ne * 4, cudaMemcpyHostToDevice), "copy sensor stencil");
+        if (!rc && ne) rc = cuda_check(c, cudaMemcpy(c->d_ks_coef, ks.coef.data(), ne * 24, cudaMemcpyHostToDevice), "copy sensor stencil");
+        if (rc) return rc;
+        c->ks_cells = nc;
+    }
+    int rc = dvm::launch_moments(c->cfg.precision, c->d_f[c->cur], nc, c->nv, c->d_xi, c->dV, c->d_mom2, c->stream);
+    if (!rc) rc = dvm::launch_kn_local(c->d_mom2, c->d_ks_start, c->d_ks_nb, c->d_ks_coef, nc, c->cfg.kn, c->d_ks_knl, c->stream);
+    return rc ? fail(c, rc, "Knudsen sensor launch") : DVM_OK;
+}
+
+int dvm_kn_local(dvm_ctx *c, double *knl)
+{
+    if (!c || !knl) return DVM_EINVAL;
+    if (c->state < 3) return fail(c, DVM_ESTATE, "f is not set");
+    if (!(c->cfg.kn > 0.0)) return fail(c, DVM_EINVAL, "the context's Kn must be positive");
+    int rc = kn_local_device(c);
+    if (!rc) rc = cuda_check(c, cudaMemcpyAsync(knl, c->d_ks_knl, (size_t)ncells_of(c) * 8, cudaMemcpyDeviceToHost, c->stream), "copy Kn");
+    if (!rc) rc = cuda_check(c, cudaStreamSynchronize(c->stream), "Knudsen sensor");
+    return rc;
+}
+
+int dvm_flag_kinetic(dvm_ctx *c, double threshold, uint8_t *kinetic, int64_t *nkinetic)
+{
+    if (!c || !kinetic || !(threshold >= 0.0)) return DVM_EINVAL;
+    const int64_t nc = ncells_of(c);
+    std::vector<double> knl((size_t)nc);
+    int rc = dvm_kn_local(c, knl.data());
+    if (rc) return rc;
+    int64_t k = 0;
+    for (int64_t q = 0; q < nc; q++) {
+        kinetic[q] = knl[q] > threshold ? 1 : 0;
+        k += kinetic[q];
+    }
+    if (nkinetic) *nkinetic = k;
+    return DVM_OK;
 }
 
 int dvm_step_moments(dvm_ctx *c, double *rho, double *u, double *T)

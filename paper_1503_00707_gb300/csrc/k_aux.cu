@@ -124,7 +124,42 @@ __global__ void k_copy_rows(void *const *bufs, const int64_t *rows, int64_t n, i
     }
 }
 
+// Row means: destination row r of dst is the mean of source rows
+// idx[start[r] .. start[r+1]) of src (nv values each, storage precision;
+// the sum in FP64 for FP64 storage, FP32 otherwise).
+template <typename T, typename A>
+__global__ void k_mean_rows(T *dst, const T *src, const int64_t *start, const int64_t *idx, int64_t nrows, int nv)
+{
+    for (int64_t r = blockIdx.x; r < nrows; r += gridDim.x) {
+        const int64_t b = start[r], e = start[r + 1];
+        const A inv = A(1) / A(e - b);
+        for (int v = threadIdx.x; v < nv; v += blockDim.x) {
+            A acc = A(0);
+            for (int64_t k = b; k < e; k++) acc += (A)src[idx[k] * nv + v];
+            dst[r * nv + v] = (T)(acc * inv);
+        }
+    }
+}
+
 }  // namespace
+
+int launch_mean_rows(int prec, void *dst, const void *src, const int64_t *start, const int64_t *idx, int64_t nrows,
+                     int nv, cudaStream_t s)
+{
+    if (nrows <= 0) return DVM_OK;
+    const unsigned grid = (unsigned)std::min<int64_t>(nrows, 1 << 16);
+    switch (prec) {
+    case DVM_F64: k_mean_rows<double, double><<<grid, 256, 0, s>>>((double *)dst, (const double *)src, start, idx, nrows, nv); break;
+    case DVM_F32: k_mean_rows<float, float><<<grid, 256, 0, s>>>((float *)dst, (const float *)src, start, idx, nrows, nv); break;
+    case DVM_BF16:
+        k_mean_rows<__nv_bfloat16, float><<<grid, 256, 0, s>>>((__nv_bfloat16 *)dst, (const __nv_bfloat16 *)src, start,
+                                                               idx, nrows, nv);
+        break;
+    default: return DVM_EINVAL;
+    }
+    count_launch();
+    return cudaGetLastError() == cudaSuccess ? DVM_OK : DVM_ECUDA;
+}
 
 int launch_copy_rows(void *const *bufs, const int64_t *rows, int64_t n, int64_t row_bytes, cudaStream_t s)
 {

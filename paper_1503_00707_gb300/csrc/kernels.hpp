@@ -57,6 +57,10 @@ int launch_from_f64(int prec, const double *src, void *dst, int64_t count, cudaS
 // {destination buffer, row, source buffer, row} indexing bufs (device arrays).
 int launch_copy_rows(void *const *bufs, const int64_t *rows, int64_t n, int64_t row_bytes, cudaStream_t s);
 
+// dst row r = mean of src rows idx[start[r] .. start[r+1]) (nv values per row).
+int launch_mean_rows(int prec, void *dst, const void *src, const int64_t *start, const int64_t *idx, int64_t nrows,
+                     int nv, cudaStream_t s);
+
 int64_t launches_issued();
 
 }  // namespace dvm

@@ -426,4 +426,106 @@ int refine_mesh(Mesh &m, const uint8_t *flag, int64_t n, std::string &err)
     return finish(b, m, err);
 }
 
+// Coarsening (the inverse of refinement; the paper's adaptive runs refine
+// and coarsen as the flow changes, Sec. 2.1, Sec. 4, Sec. 5): every group of
+// 2^dim sibling leaves that are all flagged, whose parent is at or above the
+// base level, merges into its parent, unless the parent would then touch a
+// leaf two or more levels finer (2:1 balance across faces, edges and
+// corners).  Groups are undone one by one until no parent breaks the
+// balance; undoing only adds finer leaves, so this ends.
+namespace {
+
+bool parent_breaks_balance(const Builder &b, int lev, const int32_t c[3])
+{
+    const int dim = b.dim, nch = 1 << dim;
+    const int32_t N = (int32_t)1 << lev;
+    const int nz = dim == 3 ? 3 : 1;
+    for (int oz = 0; oz < nz; oz++)
+        for (int oy = 0; oy < 3; oy++)
+            for (int ox = 0; ox < 3; ox++) {
+                const int off[3] = {ox - 1, oy - 1, dim == 3 ? oz - 1 : 0};
+                if (off[0] == 0 && off[1] == 0 && off[2] == 0) continue;
+                int32_t nb[3] = {0, 0, 0};
+                bool ok = true;
+                for (int d = 0; d < dim && ok; d++) {
+                    nb[d] = c[d] + off[d];
+                    if (nb[d] < 0 || nb[d] >= N) {
+                        if (b.per[d]) nb[d] = (nb[d] + N) % N;
+                        else ok = false;
+                    }
+                }
+                if (!ok) continue;
+                // the neighbour's children on the side facing the parent
+                for (int k = 0; k < nch; k++) {
+                    int32_t ch[3] = {0, 0, 0};
+                    bool touch = true;
+                    for (int d = 0; d < dim; d++) {
+                        const int bit = (k >> d) & 1;
+                        if ((off[d] == -1 && bit != 1) || (off[d] == 1 && bit != 0)) touch = false;
+                        ch[d] = 2 * nb[d] + bit;
+                    }
+                    if (touch && b.owner_level(lev + 1, ch) < 0) return true;
+                }
+            }
+    return false;
+}
+
+}  // namespace
+
+int coarsen_mesh(Mesh &m, const uint8_t *flag, int64_t n, std::string &err)
+{
+    if (n != (int64_t)m.leaves.size()) { err = "flag count differs from the leaf count"; return DVM_EINVAL; }
+    Builder b(m.spec);
+    const int dim = b.dim, nch = 1 << dim;
+    for (const Leaf &x : m.leaves) b.leaves.insert(node_code(x.lev, x.i));
+    struct Group { int lev; int32_t c[3]; bool on; };
+    std::vector<Group> g;
+    // the children of one parent are consecutive in Morton order
+    for (int64_t q = 0; q + nch <= n;) {
+        const Leaf &x = m.leaves[q];
+        const int32_t pc[3] = {x.i[0] >> 1, x.i[1] >> 1, x.i[2] >> 1};
+        bool ok = x.lev > m.spec.base_level;
+        for (int k = 0; k < nch && ok; k++) {
+            const Leaf &y = m.leaves[q + k];
+            ok = flag[q + k] && y.lev == x.lev;
+            for (int d = 0; d < dim && ok; d++) ok = (y.i[d] >> 1) == pc[d];
+        }
+        if (ok) {
+            g.push_back({x.lev - 1, {pc[0], pc[1], pc[2]}, true});
+            q += nch;
+        } else {
+            q++;
+        }
+    }
+    auto child = [&](const Group &G, int k, int32_t ch[3]) {
+        for (int d = 0; d < 3; d++) ch[d] = d < dim ? 2 * G.c[d] + ((k >> d) & 1) : 0;
+    };
+    for (const Group &G : g) {
+        for (int k = 0; k < nch; k++) {
+            int32_t ch[3];
+            child(G, k, ch);
+            b.leaves.erase(node_code(G.lev + 1, ch));
+        }
+        b.leaves.insert(node_code(G.lev, G.c));
+    }
+    for (bool changed = true; changed;) {
+        changed = false;
+        for (Group &G : g) {
+            if (!G.on || !parent_breaks_balance(b, G.lev, G.c)) continue;
+            b.leaves.erase(node_code(G.lev, G.c));
+            for (int k = 0; k < nch; k++) {
+                int32_t ch[3];
+                child(G, k, ch);
+                b.leaves.insert(node_code(G.lev + 1, ch));
+            }
+            G.on = false;
+            changed = true;
+        }
+    }
+    const dvm_tree_spec spec = m.spec;
+    m = Mesh();
+    m.spec = spec;
+    return finish(b, m, err);
+}
+
 }  // namespace dvm

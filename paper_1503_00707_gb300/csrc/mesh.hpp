@@ -49,5 +49,7 @@ struct Mesh {
 // Returns DVM_OK or a negative dvm_status, with a message in err.
 int build_mesh(const dvm_tree_spec &spec, Mesh &m, std::string &err);
 int refine_mesh(Mesh &m, const uint8_t *flag, int64_t n, std::string &err);
+// Merge flagged sibling groups into their parents where 2:1 balance allows.
+int coarsen_mesh(Mesh &m, const uint8_t *flag, int64_t n, std::string &err);
 
 }  // namespace dvm
