@@ -205,6 +205,7 @@ template <typename TC> struct StepSmem {
     int ok[NSS];
     int dec[NSS];
     TC xin[3][NAX];   // velocity node values per axis, in index order
+    long long next0[2];  // the cells of slots 4 and 5, taken by warp 0
 };
 
 template <typename TC> struct Consts {
@@ -571,8 +572,19 @@ __global__ void __launch_bounds__(MAXT, 1) k_step(const StepParams p)
     };
 
     if (warp == 0) {
-        // cells of iterations 0..3
+        // cells of iterations 0..3, then those of 4 and 5 for the two solver
+        // warps, all taken in slot order: once a take comes back empty every
+        // later slot is empty too, which the exit of the loops below relies
+        // on (the two solver warps taking 4 and 5 themselves could race)
         for (int k = 0; k < 4; k++) store(fetch(take()), k);
+        {
+            const long long n4 = take();
+            const long long n5 = take();
+            if (lane == 0) {
+                sm.next0[0] = n4;
+                sm.next0[1] = n5;
+            }
+        }
 #pragma unroll
         for (int d = 0; d < 3; d++) {
             const int hd = p.half[d];
@@ -601,7 +613,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_step(const StepParams p)
     if (warp < 2) {
         // ================= solver warps: warp b takes the cells j = b mod 2
         const int par = warp;
-        long long next_cell = take();  // the cell of slot par + 4
+        long long next_cell = sm.next0[par];  // the cell of slot par + 4
         for (int j = par;; j += 2) {
             const int q = j % NSS;
             bar_sync_n(BAR_P + q, nbar);
