@@ -141,6 +141,7 @@ def oracle_rate(steps, warmup=0, threads=None, collision="bgk"):
     import oracle as O
     cores = threads or len(os.sched_getaffinity(0))
     os.environ["OMP_NUM_THREADS"] = str(cores)
+    O.set_threads(cores)
     c = W.CONFIGS[CPU_SAMPLE_CONFIG]
     o = O.Problem(O.make_spec(c["dim"], c["base_level"], c["max_level"], c["pred"], c["c"], c["r"],
                               c["beta"], c["solid"], c["bc"]), c["n"], c["lo"], c["hi"])
@@ -417,6 +418,9 @@ def run_ours(args):
     if rank == 0 and not args.no_cpu_baseline:
         rate, cores, sample, _ = oracle_rate(1, collision=args.collision)
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+        # the same sample on one core
+        rate1, _, _, _ = oracle_rate(1, collision=args.collision, threads=1)
+        cpu["single_core"] = {"value": rate1, "unit": UNIT, "cores": 1}
 
     cfg = W.CONFIGS[args.config]
     prec = {"f32": D.F32, "bf16": D.BF16}[args.precision]

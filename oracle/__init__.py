@@ -50,6 +50,8 @@ def lib():
         d_p = C.POINTER(C.c_double)
         i64 = C.c_int64
         L.orc_threads.restype = C.c_int
+        L.orc_set_threads.argtypes = [C.c_int]
+        L.orc_set_threads.restype = None
         L.orc_splitmix64.restype = C.c_uint64
         L.orc_splitmix64.argtypes = [C.c_uint64, C.c_uint64]
         L.orc_vgrid_size.restype = i64
@@ -134,6 +136,11 @@ def lattice(kind):
 
 def threads():
     return int(lib().orc_threads())
+
+
+def set_threads(n):
+    """OpenMP threads of the oracle's later loops (for timing)."""
+    lib().orc_set_threads(int(n))
 
 
 def splitmix64(seed, n):

@@ -95,6 +95,16 @@ int orc_threads(void)
 #endif
 }
 
+/* the number of OpenMP threads of later loops (timing only) */
+void orc_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
 uint64_t orc_splitmix64(uint64_t seed, uint64_t n)
 {
     uint64_t z = seed + (n + 1u) * 0x9E3779B97F4A7C15ull;

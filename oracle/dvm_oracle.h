@@ -42,6 +42,7 @@ typedef struct orc_problem orc_problem;
 
 /* Number of OpenMP threads the oracle's parallel loops use. */
 int orc_threads(void);
+void orc_set_threads(int n);
 
 /* SplitMix64 output number n (0-based) of the stream seeded with `seed`. */
 uint64_t orc_splitmix64(uint64_t seed, uint64_t n);
