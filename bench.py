@@ -421,6 +421,8 @@ def run_ours(args):
         # the same sample on one core
         rate1, _, _, _ = oracle_rate(1, collision=args.collision, threads=1)
         cpu["single_core"] = {"value": rate1, "unit": UNIT, "cores": 1}
+        import oracle as O
+        O.set_threads(cores)
 
     cfg = W.CONFIGS[args.config]
     prec = {"f32": D.F32, "bf16": D.BF16}[args.precision]
