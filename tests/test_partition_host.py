@@ -7,7 +7,9 @@ cell read its face neighbours (every face is upwind for half of the sign
 groups), so the halo of a range must be exactly the set of cells outside the
 range that share a face with a cell inside it.  The exchange protocol runs
 on two gloo ranks: each rank asks the other for its halo cells and checks
-what it receives."""
+what it receives, then makes the step's two global reductions: the CFL time
+step (minimum over ranks) and the five conservation totals (sum over
+ranks)."""
 import os
 import socket
 
@@ -114,7 +116,22 @@ def _rank(rank, world, port, out):
         reqs = [dist.isend(reply, peer), dist.irecv(got, peer)]
         for r in reqs:
             r.wait()
-        out[rank] = (ok_owned, bool(np.array_equal(got.numpy(), xyz[halo])), int(halo.size))
+        # 3. the step's global reductions: the CFL time step (min over ranks)
+        #    and the five conservation totals (sum over ranks)
+        _, h = s.centres()
+        xi_max = 6.0 - 0.375                  # the 16^3 grid on [-6, 6]: largest |node|
+        smax = 3 * xi_max
+        dt_loc = torch.tensor([0.4 * float(h[c0:c1].min()) / smax], dtype=torch.float64)
+        dist.all_reduce(dt_loc, op=dist.ReduceOp.MIN)
+        ok_dt = float(dt_loc.item()) == 0.4 * float(h.min()) / smax
+        V = h ** 3
+        q = np.stack([1 + 0.1 * np.sin(7 * xyz[:, 0]), np.cos(3 * xyz[:, 1]), xyz[:, 2] ** 2,
+                      xyz[:, 0] * xyz[:, 1], 1.5 + xyz[:, 2]], axis=1)
+        tot = torch.from_numpy((V[c0:c1, None] * q[c0:c1]).sum(axis=0))
+        dist.all_reduce(tot, op=dist.ReduceOp.SUM)
+        want = (V[:, None] * q).sum(axis=0)
+        ok_tot = bool(np.allclose(tot.numpy(), want, rtol=1e-13, atol=0))
+        out[rank] = (ok_owned and ok_dt and ok_tot, bool(np.array_equal(got.numpy(), xyz[halo])), int(halo.size))
         s.close()
     finally:
         dist.destroy_process_group()
