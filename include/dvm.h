@@ -368,6 +368,17 @@ int dvm_learned_fallback_count(dvm_ctx *ctx, int64_t *n);
 int dvm_partition_info(const dvm_ctx *ctx, int nparts, int part, int64_t *c0, int64_t *c1, int64_t *nghost,
                        int64_t *ghosts, int64_t cap);
 
+/* The same with a cost per cell (Sec. 3.3: the SFC pieces carry equal work,
+ * with kinetic cells far heavier than fluid ones): weights [ncells], finite
+ * and >= 0.  Range p ends before the first cell where the weight up to that
+ * cell's middle passes (p + 1) W / nparts (W the total), every range holding
+ * at least one cell.  Each cut then lies within half the largest single
+ * weight of its target, and each range's weight within the largest single
+ * weight of W / nparts, unless a range had to be cut short to leave a cell
+ * for each later range.  Arguments and errors as dvm_partition_info. */
+int dvm_partition_weighted(const dvm_ctx *ctx, int nparts, const double *weights, int part, int64_t *c0,
+                           int64_t *c1, int64_t *nghost, int64_t *ghosts, int64_t cap);
+
 /* nsteps steps of the stored f (transport and BGK collisions only) run as
  * nparts partitions on the current device, the way separate GPUs would run
  * them.  Each part holds its own cells, a copy of its halo and the inflow

@@ -42,6 +42,7 @@ EXPORTS = [
     "dvm_lbm_set_inflow", "dvm_lbm_init_equilibrium", "dvm_lbm_set_f", "dvm_lbm_get_f",
     "dvm_lbm_dt_cfl", "dvm_lbm_step", "dvm_lbm_moments", "dvm_lbm_get_codes",
     "dvm_coarsen", "dvm_coarsen_project", "dvm_kn_local", "dvm_flag_kinetic",
+    "dvm_partition_weighted",
 ]
 MLP_NPARAM = 164672
 HS_NOALLOC_SCRATCH_BYTES = 64 << 20
@@ -145,6 +146,7 @@ def lib():
             "dvm_coarsen_project": [P, P, i64],
             "dvm_kn_local": [P, P],
             "dvm_flag_kinetic": [P, d, P, P],
+            "dvm_partition_weighted": [P, C.c_int, P, C.c_int, P, P, P, P, i64],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -379,6 +381,17 @@ class Solver:
                                            C.byref(ng), None, 0))
         g = np.zeros(ng.value, np.int64)
         self._chk(lib().dvm_partition_info(self._h, int(nparts), int(part), None, None, None, _p(g), g.size))
+        return c0.value, c1.value, g
+
+    def partition_weighted(self, nparts, part, weights):
+        """(c0, c1, ghosts) of `part` for ranges of equal total weight."""
+        w = np.ascontiguousarray(weights, dtype=np.float64)
+        c0, c1, ng = C.c_int64(), C.c_int64(), C.c_int64()
+        self._chk(lib().dvm_partition_weighted(self._h, int(nparts), _p(w), int(part), C.byref(c0), C.byref(c1),
+                                               C.byref(ng), None, 0))
+        g = np.zeros(ng.value, np.int64)
+        self._chk(lib().dvm_partition_weighted(self._h, int(nparts), _p(w), int(part), None, None, None, _p(g),
+                                               g.size))
         return c0.value, c1.value, g
 
     def step_partitioned(self, nparts, nsteps, dt):

@@ -1014,6 +1014,31 @@ int dvm_partition_info(const dvm_ctx *c, int nparts, int part, int64_t *c0, int6
     return DVM_OK;
 }
 
+int dvm_partition_weighted(const dvm_ctx *c, int nparts, const double *weights, int part, int64_t *c0, int64_t *c1,
+                           int64_t *nghost, int64_t *ghosts, int64_t cap)
+{
+    if (!c || !weights || nparts < 1 || part < 0 || part >= nparts) return DVM_EINVAL;
+    dvm_ctx *cc = const_cast<dvm_ctx *>(c);
+    if (c->state < 1) return fail(cc, DVM_ESTATE, "build the tree first");
+    const int64_t nc = ncells_of(c);
+    if (nparts > nc) return fail(cc, DVM_EINVAL, "more parts than cells");
+    for (int64_t q = 0; q < nc; q++)
+        if (!(weights[q] >= 0.0) || !std::isfinite(weights[q])) return fail(cc, DVM_EINVAL, "weights must be finite and >= 0");
+    std::vector<int32_t> enc;
+    dvm::encode_stencils(c->mesh.st_src, nc, enc);
+    std::vector<dvm::Part> parts;
+    dvm::partition_cells(nc, nparts, enc, c->mesh.st_cnt, parts, weights);
+    const dvm::Part &pt = parts[part];
+    if (c0) *c0 = pt.c0;
+    if (c1) *c1 = pt.c1;
+    if (nghost) *nghost = (int64_t)pt.ghosts.size();
+    if (ghosts) {
+        if (cap < (int64_t)pt.ghosts.size()) return fail(cc, DVM_EINVAL, "ghost buffer too small");
+        std::copy(pt.ghosts.begin(), pt.ghosts.end(), ghosts);
+    }
+    return DVM_OK;
+}
+
 int dvm_step_partitioned(dvm_ctx *c, int nparts, int nsteps, double dt)
 {
     if (!c || nsteps < 0 || nparts < 1) return DVM_EINVAL;

@@ -31,15 +31,38 @@ void encode_stencils(const std::vector<int32_t> &st_src, int64_t ncells, std::ve
 }
 
 void partition_cells(int64_t ncells, int nparts, const std::vector<int32_t> &enc,
-                     const std::vector<uint8_t> &st_cnt, std::vector<Part> &parts)
+                     const std::vector<uint8_t> &st_cnt, std::vector<Part> &parts, const double *weight)
 {
     parts.assign(nparts, Part{});
-    const int64_t base = ncells / nparts, extra = ncells % nparts;
-    int64_t c = 0;
-    for (int p = 0; p < nparts; p++) {
-        parts[p].c0 = c;
-        c += base + (p < extra ? 1 : 0);
-        parts[p].c1 = c;
+    if (!weight) {
+        const int64_t base = ncells / nparts, extra = ncells % nparts;
+        int64_t c = 0;
+        for (int p = 0; p < nparts; p++) {
+            parts[p].c0 = c;
+            c += base + (p < extra ? 1 : 0);
+            parts[p].c1 = c;
+        }
+    } else {
+        // cut p at the first cell where the weight before it reaches p W /
+        // nparts, keeping at least one cell per part
+        double W = 0.0;
+        for (int64_t q = 0; q < ncells; q++) W += weight[q];
+        int64_t c = 0;
+        double acc = 0.0;
+        for (int p = 0; p < nparts; p++) {
+            parts[p].c0 = c;
+            if (p == nparts - 1) {
+                c = ncells;
+            } else {
+                const double target = W * (double)(p + 1) / (double)nparts;
+                const int64_t hi = ncells - (nparts - 1 - p);  // leave a cell for each later part
+                int64_t e = c + 1;
+                acc += weight[c];
+                while (e < hi && acc + 0.5 * weight[e] <= target) acc += weight[e++];
+                c = e;
+            }
+            parts[p].c1 = c;
+        }
     }
     for (Part &pt : parts) {
         std::vector<int64_t> g;

@@ -20,11 +20,14 @@ struct Part {
 // counts.
 void encode_stencils(const std::vector<int32_t> &st_src, int64_t ncells, std::vector<int32_t> &enc);
 
-// nparts contiguous ranges of ncells / nparts cells (the first ncells %
-// nparts ranges one cell longer: every cell carries the same work), and the
-// ghost list of each from the encoded stencils.
+// nparts contiguous ranges and the ghost list of each from the encoded
+// stencils.  Without weights: ncells / nparts cells each (the first ncells %
+// nparts ranges one cell longer: every cell carries the same work).  With
+// per-cell weights (>= 0): range p ends at the first cell where the weight up
+// to the cell's middle passes (p + 1) W / nparts, every range non-empty.
 void partition_cells(int64_t ncells, int nparts, const std::vector<int32_t> &enc,
-                     const std::vector<uint8_t> &st_cnt, std::vector<Part> &parts);
+                     const std::vector<uint8_t> &st_cnt, std::vector<Part> &parts,
+                     const double *weight = nullptr);
 
 // The stencils of one part in its local numbering: owned cell c -> c - c0,
 // ghost k -> (c1 - c0) + k, inflow ghost -> (c1 - c0) + ghosts.size().

@@ -71,6 +71,34 @@ def test_halo_is_the_off_range_face_neighbours(name, over, nparts):
     s.close()
 
 
+@pytest.mark.parametrize("nparts", [2, 3, 7])
+def test_weighted_partition_balances_the_cost(nparts):
+    """Kinetic cells (inside a ball, cost 1) far heavier than fluid ones
+    (cost 0.02): the ranges tile the cells in Morton order, every cut lies
+    within half the largest weight of its target, and each range's halo is
+    still its off-range face neighbours."""
+    s = _mesh("c2_sphere_m3", base_level=3, max_level=5)
+    xyz, _ = s.centres()
+    kinetic = ((xyz - np.array([0.35, 0.5, 0.5])) ** 2).sum(axis=1) < 0.2 ** 2
+    w = np.where(kinetic, 1.0, 0.02)
+    Wt = w.sum()
+    prev = 0
+    for p in range(nparts):
+        c0, c1, g = s.partition_weighted(nparts, p, w)
+        assert c0 == prev and c1 > c0
+        prev = c1
+        if p < nparts - 1:
+            assert abs(w[:c1].sum() - Wt * (p + 1) / nparts) <= 0.5 * w.max() + 1e-9
+        assert np.array_equal(g, _expected_halo(s, c0, c1))
+    assert prev == s.ncells
+    # equal weights give ranges within one cell of each other
+    sizes = [np.subtract(*s.partition_weighted(nparts, p, np.ones(s.ncells))[1::-1]) for p in range(nparts)]
+    assert max(sizes) - min(sizes) <= 1
+    with pytest.raises(D.DvmError):
+        s.partition_weighted(nparts, 0, -w)
+    s.close()
+
+
 def test_partition_rejects_bad_arguments():
     s = _mesh("c1_2d_bump")
     for nparts, part in ((0, 0), (2, 2), (2, -1), (s.ncells + 1, 0)):
