@@ -10,7 +10,7 @@
 // are near in the rows, so the gathers hit L1/L2.
 #include <cuda_runtime.h>
 
-#include <atomic>
+#include <type_traits>
 
 #include "../../include/dvm.h"
 #include "lbm.hpp"
