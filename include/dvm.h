@@ -458,6 +458,10 @@ int dvm_lbm_set_lattice(dvm_ctx *ctx, int lattice);
  * (size query). */
 int dvm_lbm_get_codes(const dvm_ctx *ctx, uint32_t *codes, uint32_t *ovf, int64_t *novf);
 
+/* A velocity set without a context: *q its size, c [q][3] and w [q] (any
+ * pointer may be NULL).  DVM_EINVAL for an unknown set. */
+int dvm_lbm_lattice(int lattice, int *q, int32_t *c, double *w);
+
 /* The velocity set: c [q][3] and w [q] (q = the set's size). */
 int dvm_lbm_get_velocities(const dvm_ctx *ctx, int32_t *c, double *w);
 

@@ -42,7 +42,7 @@ EXPORTS = [
     "dvm_lbm_set_inflow", "dvm_lbm_init_equilibrium", "dvm_lbm_set_f", "dvm_lbm_get_f",
     "dvm_lbm_dt_cfl", "dvm_lbm_step", "dvm_lbm_moments", "dvm_lbm_get_codes",
     "dvm_coarsen", "dvm_coarsen_project", "dvm_kn_local", "dvm_flag_kinetic",
-    "dvm_partition_weighted",
+    "dvm_partition_weighted", "dvm_lbm_lattice",
 ]
 MLP_NPARAM = 164672
 HS_NOALLOC_SCRATCH_BYTES = 64 << 20
@@ -147,6 +147,7 @@ def lib():
             "dvm_kn_local": [P, P],
             "dvm_flag_kinetic": [P, d, P, P],
             "dvm_partition_weighted": [P, C.c_int, P, C.c_int, P, P, P, P, i64],
+            "dvm_lbm_lattice": [C.c_int, P, P, P],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -513,6 +514,18 @@ class Solver:
         if rc:
             raise DvmError(rc, "dvm_launch_count")
         return n.value
+
+
+def lbm_lattice(lattice):
+    """(c [q][3] int32, w [q]) of a lattice Boltzmann velocity set (no context)."""
+    q = C.c_int()
+    rc = lib().dvm_lbm_lattice(int(lattice), C.byref(q), None, None)
+    if rc:
+        raise DvmError(rc, "unknown lattice")
+    c = np.zeros((q.value, 3), dtype=np.int32)
+    w = np.zeros(q.value)
+    lib().dvm_lbm_lattice(int(lattice), None, _p(c), _p(w))
+    return c, w
 
 
 def lbm_solver_from_config(cfg, precision=None, stream=None):

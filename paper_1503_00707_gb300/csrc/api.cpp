@@ -1631,6 +1631,19 @@ int dvm_lbm_get_codes(const dvm_ctx *c, uint32_t *codes, uint32_t *ovf, int64_t 
     return DVM_OK;
 }
 
+int dvm_lbm_lattice(int lattice, int *q, int32_t *cv, double *w)
+{
+    dvm::LbmLattice lat;
+    if (!dvm::lbm_lattice(lattice, lat)) return DVM_EINVAL;
+    if (q) *q = lat.q;
+    for (int i = 0; i < lat.q; i++) {
+        if (cv)
+            for (int d = 0; d < 3; d++) cv[3 * i + d] = lat.c[i][d];
+        if (w) w[i] = lat.w[i];
+    }
+    return DVM_OK;
+}
+
 int dvm_lbm_get_velocities(const dvm_ctx *c, int32_t *cv, double *w)
 {
     if (!c || !cv || !w) return DVM_EINVAL;

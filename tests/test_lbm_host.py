@@ -79,3 +79,19 @@ def test_codes_match_oracle_faces(name):
             assert _decode(code, ovf) == exp[cell][side], (cell, side)
     # refined trees have coarse cells next to finer ones
     assert n_ovf_sides > 0 and len(ovf) >= 2 * n_ovf_sides
+
+
+@pytest.mark.parametrize("kind", [D.LBM_D2Q9, D.LBM_D3Q19, D.LBM_D3Q27])
+def test_library_velocity_set_equals_oracle(kind):
+    """The library's velocity set and weights, written independently of the
+    oracle's from the same rule, are the oracle's (which the isotropy pins
+    fix) bit for bit."""
+    c, w = D.lbm_lattice(kind)
+    oc, ow = O.lattice(kind)
+    assert np.array_equal(c.astype(np.float64), oc)
+    assert np.array_equal(w, ow)
+
+
+def test_unknown_lattice_is_rejected():
+    with pytest.raises(D.DvmError):
+        D.lbm_lattice(15)
