@@ -6,8 +6,10 @@ Pinned against: exact conservation of mass, momentum and energy by the
 collision term (the property Eq. 6 is built for), the Maxwellian fixed point,
 the closed-form geometric relaxation of spatially homogeneous BGK, H-theorem
 monotonicity, the hard-sphere mean collision frequency sqrt(8/pi) of a unit
-Maxwellian, the published SplitMix64 output sequence, and an independent
-pure-Python regeneration of the seeded trial tables.
+Maxwellian, the published SplitMix64 output sequence, an independent
+pure-Python regeneration of the seeded trial tables, and the shear-wave
+damping of the whole BGK step against the linearised discrete-velocity BGK
+equation.
 """
 import math
 
@@ -380,3 +382,51 @@ def test_entropic_equilibrium_has_least_entropy():
     assert _entropy(E, p.dV) < _entropy(Mp, p.dV)
     X = _psi(p.xi)
     assert np.allclose(E @ X, Mp @ X, rtol=1e-11, atol=1e-14)
+
+
+def test_bgk_shear_wave_damping_matches_the_discrete_bgk_equation():
+    """A small shear wave u_y = U sin(2 pi x) in the whole DVM-BGK step
+    (transport of Eq. 2, conservative BGK) on uniform periodic quadtrees: the
+    damping rate measured between t = 0.1 and 0.3, extrapolated to h -> 0
+    from levels 4-6 (quadratic Richardson, first-order scheme), equals the
+    shear mode of the discrete-velocity BGK equation linearised about the
+    discrete Maxwellian, -i k diag(xi_x) + nu (Pi - I), with Pi the
+    projection onto span{psi_r M} that keeps the five moments (the
+    linearised corrected target).  That mode is close to mu k^2 with
+    mu = p / nu."""
+    n, vmax, kn, k, U = (8, 8, 8), 4.0, 0.02, 2 * math.pi, 1e-3
+    p0 = O.Problem(O.make_spec(2, 1, 1, O.PRED_NONE), n, (-vmax,) * 3, (vmax,) * 3)
+    xi, dV = p0.xi, p0.dV
+    M0 = np.exp(-(xi ** 2).sum(1) / 2) / (2 * math.pi) ** 1.5
+    Psi = _psi(xi)
+    G = Psi.T @ (M0[:, None] * Psi) * dV
+    Pi = (M0[:, None] * Psi) @ np.linalg.solve(G, Psi.T * dV)
+    rho = M0.sum() * dV
+    T = ((xi ** 2).sum(1) * M0).sum() * dV / rho / 3
+    nu = math.sqrt(8 / math.pi) * rho * math.sqrt(T) / kn
+    ev, V = np.linalg.eig(-1j * k * np.diag(xi[:, 0]) + nu * (Pi - np.eye(len(xi))))
+    exact = -ev[np.argmax(np.abs(xi[:, 1] @ V) / np.linalg.norm(V, axis=0))].real
+    assert abs(exact / (k * k / nu) - 1) < 0.02
+
+    def rate(L):
+        p = O.Problem(O.make_spec(2, L, L, O.PRED_NONE), n, (-vmax,) * 3, (vmax,) * 3)
+        xyz, _ = p.centres()
+        nc = p.ncells
+        u = np.zeros((nc, 3))
+        u[:, 1] = U * np.sin(k * xyz[:, 0])
+        p.init_maxwellian(np.ones(nc), np.ones(nc), u, np.ones(nc))
+        dt = p.dt_cfl(0.4)
+        n1 = int(round(0.1 / dt))
+        dt = 0.1 / n1
+
+        def amp():
+            return 2 * np.mean(p.moments()[1][:, 1] * np.sin(k * xyz[:, 0]))
+
+        p.step(n1, dt, O.COLL_BGK, kn)
+        a1 = amp()
+        p.step(2 * n1, dt, O.COLL_BGK, kn)
+        return -math.log(amp() / a1) / (2 * n1 * dt)
+
+    r4, r5, r6 = rate(4), rate(5), rate(6)
+    extrap = (8 * r6 - 6 * r5 + r4) / 3
+    assert abs(extrap / exact - 1) < 0.01, (r4, r5, r6, extrap, exact)
