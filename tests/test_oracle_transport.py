@@ -182,6 +182,42 @@ def test_moments_of_maxwellian_closed_form():
     assert np.allclose(TT, T, rtol=1e-12)
 
 
+def test_density_of_a_truncated_maxwellian_closed_form():
+    """On a grid that cuts the Maxwellian off (here [-3, 3]^3, 24^3 nodes), the
+    discrete density is the midpoint rule of a truncated Gaussian per axis:
+    the exact integral (erf) plus the Euler-Maclaurin endpoint terms of the
+    midpoint rule, -h^2/24 [g1] + 7 h^4/5760 [g3] (g1, g3 the first and third
+    derivatives at the ends), to O(h^6).  This fixes the node positions, the
+    cell volume dV and the truncation of the Mach-number flows (R17)."""
+    from math import erf, exp, pi, sqrt
+    V, n = 3.0, 24
+    h = 2 * V / n
+    p = O.Problem(_uniform(3, 1), (n,) * 3, (-V,) * 3, (V,) * 3)
+    nc = p.ncells
+
+    def axis_sum(u, T):
+        def g(x):
+            return exp(-(x - u) ** 2 / (2 * T))
+
+        def g1(x):
+            return -(x - u) / T * g(x)
+
+        def g3(x):
+            z = (x - u) / sqrt(T)
+            return -(z ** 3 - 3 * z) / T ** 1.5 * g(x)
+
+        s = sqrt(2 * T)
+        integral = sqrt(2 * pi * T) * (erf((V - u) / s) + erf((V + u) / s)) / 2
+        return integral - h * h / 24 * (g1(V) - g1(-V)) + 7 * h ** 4 / 5760 * (g3(V) - g3(-V))
+
+    for u0, T in ((0.0, 1.0), (1.0, 1.0), (0.5, 0.7)):
+        rho = 1.3
+        p.init_maxwellian(np.ones(nc), np.full(nc, rho), np.tile([u0, 0.0, 0.0], (nc, 1)), np.full(nc, T))
+        r, _, _ = p.moments()
+        want = rho * axis_sum(u0, T) * axis_sum(0.0, T) ** 2 / (2 * pi * T) ** 1.5
+        assert abs(r[0] / want - 1) < 5e-8, (u0, T, r[0] / want - 1)
+
+
 def test_dt_cfl_closed_form():
     def prob(name, n_only=False):
         c = W.CONFIGS[name]
