@@ -50,6 +50,9 @@ MUTANTS = [
     ("third Hermite mode normalisation", "h[3] = (x * x * x - 3.0 * x) / sqrt(6.0);",
      "h[3] = (x * x * x - 3.0 * x) / sqrt(3.0);",
      "tests/test_oracle_learned.py::test_hermite_projection_of_maxwellian_and_modes"),
+    ("velocity nodes off the cell midpoints", "xi[3 * v + d] = lo[d] + ((double)kk[d] + 0.5) * h[d];",
+     "xi[3 * v + d] = lo[d] + ((double)kk[d] + 0.45) * h[d];",
+     "tests/test_oracle_transport.py::test_density_of_a_truncated_maxwellian_closed_form"),
 ]
 
 
