@@ -50,6 +50,9 @@ MUTANTS = [
     ("third Hermite mode normalisation", "h[3] = (x * x * x - 3.0 * x) / sqrt(6.0);",
      "h[3] = (x * x * x - 3.0 * x) / sqrt(3.0);",
      "tests/test_oracle_learned.py::test_hermite_projection_of_maxwellian_and_modes"),
+    ("gain term with one post-collision partner twice", "sc += p->hs_b[t] * f[p->hs_l[t]] * f[p->hs_m[t]];",
+     "sc += p->hs_b[t] * f[p->hs_l[t]] * f[p->hs_l[t]];",
+     "tests/test_oracle_collision.py::test_hs_relaxation_approaches_the_maxwellian_as_trials_grow"),
     ("velocity nodes off the cell midpoints", "xi[3 * v + d] = lo[d] + ((double)kk[d] + 0.5) * h[d];",
      "xi[3 * v + d] = lo[d] + ((double)kk[d] + 0.45) * h[d];",
      "tests/test_oracle_transport.py::test_density_of_a_truncated_maxwellian_closed_form"),
