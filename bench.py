@@ -70,9 +70,10 @@ def dist_env():
 
 
 def workload_desc(name, cfg, ncells, nv, prec, collision="bgk"):
-    return ("%s: %dD octree levels %d-%d around a sphere r=%g (%d kinetic cells), %d^3 velocities "
+    cells = " (%d kinetic cells)" % ncells if ncells >= 0 else ""
+    return ("%s: %dD octree levels %d-%d around a sphere r=%g%s, %d^3 velocities "
             "on [%g,%g]^3, Mach %.1f inflow, outflow, specular wall, %s Kn=%g, %s storage"
-            % (name, cfg["dim"], cfg["base_level"], cfg["max_level"], cfg["r"], ncells, cfg["n"][0],
+            % (name, cfg["dim"], cfg["base_level"], cfg["max_level"], cfg["r"], cells, cfg["n"][0],
                cfg["lo"][0], cfg["hi"][0], cfg["fs_u"][0] / math.sqrt(W.GAMMA),
                "entropic BGK" if collision == "entropic" else "BGK", cfg["kn"], prec))
 
