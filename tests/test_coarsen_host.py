@@ -87,6 +87,28 @@ def test_coarsen_matches_brute_force(case):
     assert sum(2.0 ** (-dim * int(l)) for l in l1) == pytest.approx(1.0, abs=1e-15)
 
 
+@pytest.mark.parametrize("case", [CASES[1], CASES[3]])
+def test_coarsened_mesh_faces_match_brute_force(case):
+    """The faces the library builds for a coarsened tree (the input of every
+    stencil) equal a pairwise box-contact enumeration, walls against solid
+    leaves and domain sides included."""
+    from fractions import Fraction
+    dim, base, L, pred, r, beta, solid, bc, prob, seed = case
+    s = D.Solver(D.F32, D.COLL_BGK, 0.1)
+    s.build_tree(D.tree_spec(dim, base, L, pred, (0.5, 0.5, 0.5), r, beta, solid, bc))
+    flags = (np.random.default_rng(seed).random(s.nleaves) < prob).astype(np.uint8)
+    s.coarsen(flags)
+    keys, lev, sol = s.leaves()
+    m, pl, ax, ar = s.faces()
+    got = sorted((int(a), int(b), int(c), Fraction(float(d))) for a, b, c, d in zip(m, pl, ax, ar))
+    inter, bnd = brute.faces(keys, lev, sol, dim, L, bc)
+    assert got == sorted(inter)
+    bl, bax, bside, bkind, bother, bar = s.bfaces()
+    gotb = sorted((int(a), int(b), int(c), int(d), int(e), Fraction(float(f)))
+                  for a, b, c, d, e, f in zip(bl, bax, bside, bkind, bother, bar))
+    assert gotb == sorted(bnd)
+
+
 def test_coarsen_rejects_bad_flag_count():
     s = D.Solver(D.F32, D.COLL_BGK, 0.1)
     s.build_tree(D.tree_spec(2, 2, 4, 1, (0.5, 0.5, 0.5), 0.2, 0.0, 0, (0,) * 6))
