@@ -163,6 +163,32 @@ def oracle_rate(steps, warmup=0, threads=None, collision="bgk"):
     return o.ncells * o.nv * steps / el, cores, sample, el
 
 
+def oracle_config_rates():
+    """The oracle on the other configurations, all host cores: the 2D bump
+    flow (50 steps, BGK, FP64), the Mach-3 sphere flow (2 steps, BGK) and the
+    hard-sphere bimodal box (1 step, 128 trials).  Returns {name: record}."""
+    import oracle as O
+    out = {}
+    for name, steps, coll in (("c1_2d_bump", 50, O.COLL_BGK), ("c2_sphere_m3", 2, O.COLL_BGK),
+                              ("c4_hs_bimodal", 1, O.COLL_HS)):
+        c = W.CONFIGS[name]
+        o = O.Problem(O.make_spec(c["dim"], c["base_level"], c["max_level"], c["pred"], c["c"], c["r"],
+                                  c["beta"], c["solid"], c["bc"]), c["n"], c["lo"], c["hi"])
+        o.set_freestream(c["fs_rho"], c["fs_u"], c["fs_T"])
+        xyz, _ = o.centres()
+        o.init_maxwellian(*W.initial_state(c, xyz))
+        if coll == O.COLL_HS:
+            o.hs_tables(c["trials"], W.SEED)
+        dt = o.dt_cfl(c["cfl"])
+        t0 = time.perf_counter()
+        o.step(steps, dt, coll, c["kn"])
+        el = time.perf_counter() - t0
+        out[name] = {"value": o.ncells * o.nv * steps / el, "unit": UNIT, "cells": o.ncells,
+                     "velocities": o.nv, "steps": steps, "cores": O.threads(),
+                     "collision": "hard sphere" if coll == O.COLL_HS else "BGK"}
+    return out
+
+
 def run_reference(args):
     rank, _, world = dist_env()
     if rank != 0:
@@ -424,6 +450,7 @@ def run_ours(args):
         cpu["single_core"] = {"value": rate1, "unit": UNIT, "cores": 1}
         import oracle as O
         O.set_threads(cores)
+        cpu["configs"] = oracle_config_rates()
 
     cfg = W.CONFIGS[args.config]
     prec = {"f32": D.F32, "bf16": D.BF16}[args.precision]
