@@ -92,6 +92,8 @@ def lib():
         L.orc_step.argtypes = [P, C.c_int, C.c_double, C.c_int, C.c_double]
         L.orc_solve.argtypes = [C.c_int, P, P, P]
         L.orc_kn_local.argtypes = [P, C.c_double, P]
+        L.orc_refine_project.argtypes = [P, P]
+        L.orc_coarsen_project.argtypes = [P, P]
         L.orc_hermite_project.argtypes = [P, P, P, P]
         L.orc_hermite_target.argtypes = [P, P, P, P]
         L.orc_mlp_forward.argtypes = [C.c_int64, P, P, P]
@@ -288,6 +290,25 @@ class Problem:
         u = np.ascontiguousarray(np.asarray(u, dtype=np.float64).reshape(self.ncells, nmix, 3))
         T = np.ascontiguousarray(np.asarray(T, dtype=np.float64).reshape(self.ncells, nmix))
         lib().orc_init_maxwellian(self._h, nmix, _p(w), _p(rho), _p(u), _p(T))
+
+    def refine_project(self, flags):
+        """Split the flagged leaves, rebalance, carry f over (injection)."""
+        flags = np.ascontiguousarray(flags, dtype=np.uint8)
+        assert flags.size == self.nleaves
+        if lib().orc_refine_project(self._h, _p(flags)):
+            raise RuntimeError("refinement failed")
+        self.nleaves = lib().orc_nleaves(self._h)
+        self.ncells = lib().orc_ncells(self._h)
+
+    def coarsen_project(self, flags):
+        """Merge flagged sibling groups (2:1 balance kept), carry f over
+        (the mean of the fluid children)."""
+        flags = np.ascontiguousarray(flags, dtype=np.uint8)
+        assert flags.size == self.nleaves
+        if lib().orc_coarsen_project(self._h, _p(flags)):
+            raise RuntimeError("coarsening failed")
+        self.nleaves = lib().orc_nleaves(self._h)
+        self.ncells = lib().orc_ncells(self._h)
 
     def get_f(self):
         f = np.zeros((self.ncells, self.nv))

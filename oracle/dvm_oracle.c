@@ -338,6 +338,32 @@ static int check_spec(const orc_tree_spec *s)
     return 0;
 }
 
+/* 2:1 balance for direct and diagonal neighbours, to a fixpoint: every leaf
+ * that touches a leaf two or more levels finer is split; the result is
+ * sorted in Morton order. */
+static int balance_fixpoint(const orc_tree_spec *s, leafvec *cur)
+{
+    int dim = s->dim, L = s->max_level;
+    for (;;) {
+        qsort(cur->v, (size_t)cur->n, sizeof(leaf_t), cmp_leaf);
+        char *mark = (char *)calloc((size_t)cur->n + 1, 1);
+        if (!mark) return -1;
+        int64_t nmark = 0;
+        for (int64_t a = 0; a < cur->n; a++)
+            if (violates_balance(s, L, cur->v, cur->n, &cur->v[a])) { mark[a] = 1; nmark++; }
+        if (nmark == 0) { free(mark); break; }
+        leafvec nxt = {0, 0, 0};
+        for (int64_t a = 0; a < cur->n; a++) {
+            if (mark[a]) { if (push_children(&nxt, &cur->v[a], dim, L)) return -1; }
+            else if (push(&nxt, cur->v[a])) return -1;
+        }
+        free(mark);
+        free(cur->v);
+        *cur = nxt;
+    }
+    return 0;
+}
+
 static int build_tree(const orc_tree_spec *s, leafvec *out)
 {
     int dim = s->dim, L = s->max_level;
@@ -368,23 +394,7 @@ static int build_tree(const orc_tree_spec *s, leafvec *out)
         cur = nxt;
         if (!changed) break;
     }
-    /* 2:1 balance for direct and diagonal neighbours, to a fixpoint */
-    for (;;) {
-        qsort(cur.v, (size_t)cur.n, sizeof(leaf_t), cmp_leaf);
-        char *mark = (char *)calloc((size_t)cur.n, 1);
-        int64_t nmark = 0;
-        for (int64_t a = 0; a < cur.n; a++)
-            if (violates_balance(s, L, cur.v, cur.n, &cur.v[a])) { mark[a] = 1; nmark++; }
-        if (nmark == 0) { free(mark); break; }
-        leafvec nxt = {0, 0, 0};
-        for (int64_t a = 0; a < cur.n; a++) {
-            if (mark[a]) { if (push_children(&nxt, &cur.v[a], dim, L)) return -1; }
-            else if (push(&nxt, cur.v[a])) return -1;
-        }
-        free(mark);
-        free(cur.v);
-        cur = nxt;
-    }
+    if (balance_fixpoint(s, &cur)) return -1;
     for (int64_t a = 0; a < cur.n; a++) cur.v[a].solid = (uint8_t)is_solid(s, &cur.v[a]);
     *out = cur;
     return 0;
@@ -1707,4 +1717,171 @@ int orc_learned_collide(orc_problem *p, double dt, double kn, const double *para
     int rc = orc_learned_apply(p, dt, kn, knl, o, kn_threshold, used, q);
     free(knl); free(a); free(o); free(mom);
     return rc;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Mesh adaptation with f carried over.  The paper's trees are refined and
+ * coarsened as the solution evolves (Sec. 2.1, Sec. 5) and the advection
+ * stencils are rebuilt on every such change (Sec. 3.1, step 4).  Refinement
+ * hands each new cell the distribution of the old leaf that contains it
+ * (piecewise-constant injection); coarsening gives a merged parent the mean
+ * of its children's distributions (equal volumes, so mass, momentum and
+ * energy are kept).  Both replace the leaves, rebuild cells and faces and
+ * keep the velocity grid, the freestream and the hard-sphere tables. */
+
+static void free_mesh(orc_problem *p)
+{
+    free(p->lv); free(p->cell_of_leaf); free(p->leaf_of_cell);
+    free(p->fm); free(p->fp); free(p->fax); free(p->farea);
+    free(p->cf_start); free(p->cf_list);
+    free(p->bl); free(p->bother); free(p->bax); free(p->bside); free(p->bkind); free(p->barea);
+    p->lv = NULL; p->cell_of_leaf = NULL; p->leaf_of_cell = NULL;
+    p->fm = NULL; p->fp = NULL; p->fax = NULL; p->farea = NULL;
+    p->cf_start = NULL; p->cf_list = NULL;
+    p->bl = NULL; p->bother = NULL; p->bax = NULL; p->bside = NULL; p->bkind = NULL; p->barea = NULL;
+    p->nleaves = p->ncells = p->nf = p->nbf = 0;
+}
+
+/* the leaves v[n] (Morton order, solid flags set) become the problem's mesh */
+static int set_mesh(orc_problem *p, leaf_t *v, int64_t n)
+{
+    free_mesh(p);
+    p->lv = v;
+    p->nleaves = n;
+    p->cell_of_leaf = (int64_t *)malloc((size_t)n * sizeof(int64_t));
+    p->leaf_of_cell = (int64_t *)malloc((size_t)n * sizeof(int64_t));
+    if (!p->cell_of_leaf || !p->leaf_of_cell) return -1;
+    for (int64_t a = 0; a < n; a++) {
+        if (v[a].solid) p->cell_of_leaf[a] = -1;
+        else { p->cell_of_leaf[a] = p->ncells; p->leaf_of_cell[p->ncells++] = a; }
+    }
+    return build_faces(p);
+}
+
+int orc_refine_project(orc_problem *p, const uint8_t *flag)
+{
+    const orc_tree_spec *s = &p->spec;
+    int dim = s->dim, L = p->L;
+    /* split every flagged leaf below the deepest level, then balance */
+    leafvec cur = {0, 0, 0};
+    for (int64_t a = 0; a < p->nleaves; a++) {
+        if (flag[a] && p->lv[a].lev < L) { if (push_children(&cur, &p->lv[a], dim, L)) return -1; }
+        else if (push(&cur, p->lv[a])) return -1;
+    }
+    if (balance_fixpoint(s, &cur)) return -1;
+    for (int64_t a = 0; a < cur.n; a++) cur.v[a].solid = (uint8_t)is_solid(s, &cur.v[a]);
+    /* keep the old mesh's leaves and f while the new mesh is built */
+    int64_t on = p->nleaves, nv = p->nv;
+    leaf_t *olv = p->lv;
+    int64_t *ocell = p->cell_of_leaf;
+    double *of = p->f;
+    p->lv = NULL;
+    p->cell_of_leaf = NULL;
+    p->f = NULL;
+    if (set_mesh(p, cur.v, cur.n)) { free(olv); free(ocell); free(of); return -1; }
+    p->f = (double *)malloc((size_t)(p->ncells * nv) * sizeof(double));
+    if (!p->f) { free(olv); free(ocell); free(of); return -1; }
+    for (int64_t j = 0; j < p->ncells; j++) {
+        /* the old leaf holding the new cell's anchor contains the whole cell */
+        int64_t a = locate(olv, on, p->lv[p->leaf_of_cell[j]].key);
+        int64_t oc = ocell[a];
+        const double *src = oc >= 0 ? of + oc * nv : p->finf;
+        memcpy(p->f + j * nv, src, (size_t)nv * sizeof(double));
+    }
+    free(olv); free(ocell); free(of);
+    return 0;
+}
+
+int orc_coarsen_project(orc_problem *p, const uint8_t *flag)
+{
+    const orc_tree_spec *s = &p->spec;
+    int dim = s->dim, L = p->L, nch = 1 << dim;
+    int64_t on = p->nleaves, nv = p->nv;
+    const leaf_t *ol = p->lv;
+    /* candidate merges: nch consecutive leaves (children of one box occupy a
+     * contiguous Morton range) that are all the children of one parent at or
+     * above the base level, and all flagged */
+    int64_t *first = (int64_t *)malloc((size_t)on * sizeof(int64_t));
+    char *on_g = (char *)malloc((size_t)on + 1);
+    if (!first || !on_g) return -1;
+    int64_t ng = 0;
+    for (int64_t q = 0; q + nch <= on;) {
+        const leaf_t *a = &ol[q];
+        int ok = a->lev > s->base_level;
+        for (int k = 0; k < nch && ok; k++) {
+            const leaf_t *b = &ol[q + k];
+            ok = flag[q + k] && b->lev == a->lev;
+            for (int d = 0; d < dim && ok; d++) ok = (b->i[d] >> 1) == (a->i[d] >> 1) && (b->i[d] & 1) == ((k >> d) & 1);
+        }
+        if (ok) { first[ng] = q; on_g[ng++] = 1; q += nch; }
+        else q++;
+    }
+    /* undo every merge whose parent touches a leaf two or more levels finer,
+     * until none is left (undoing only adds finer leaves, so the set that
+     * remains is the largest consistent one, whatever the order) */
+    leafvec cur = {0, 0, 0};
+    int64_t *src0 = NULL, *srcn = NULL;
+    for (;;) {
+        free(cur.v);
+        cur.v = NULL; cur.n = cur.cap = 0;
+        free(src0); free(srcn);
+        src0 = (int64_t *)malloc((size_t)on * sizeof(int64_t));
+        srcn = (int64_t *)malloc((size_t)on * sizeof(int64_t));
+        if (!src0 || !srcn) return -1;
+        int64_t g = 0;
+        for (int64_t q = 0; q < on;) {
+            while (g < ng && first[g] < q) g++;
+            if (g < ng && first[g] == q && on_g[g]) {
+                leaf_t par;
+                memset(&par, 0, sizeof par);
+                par.lev = ol[q].lev - 1;
+                for (int d = 0; d < dim; d++) par.i[d] = ol[q].i[d] >> 1;
+                set_key(&par, dim, L);
+                src0[cur.n] = q; srcn[cur.n] = nch;
+                if (push(&cur, par)) return -1;
+                q += nch;
+            } else {
+                src0[cur.n] = q; srcn[cur.n] = 1;
+                if (push(&cur, ol[q])) return -1;
+                q++;
+            }
+        }
+        int changed = 0;
+        for (int64_t a = 0; a < cur.n; a++)
+            if (srcn[a] > 1 && violates_balance(s, L, cur.v, cur.n, &cur.v[a])) {
+                for (g = 0; g < ng; g++)
+                    if (first[g] == src0[a]) on_g[g] = 0;
+                changed = 1;
+            }
+        if (!changed) break;
+    }
+    free(first); free(on_g);
+    for (int64_t a = 0; a < cur.n; a++) cur.v[a].solid = (uint8_t)is_solid(s, &cur.v[a]);
+    /* f of the new cells: an unchanged cell keeps its own, a merged parent
+     * takes the mean over its fluid children, or the freestream if all were
+     * solid */
+    leaf_t *olv = p->lv;
+    int64_t *ocell = p->cell_of_leaf;
+    double *of = p->f;
+    p->lv = NULL;
+    p->cell_of_leaf = NULL;
+    p->f = NULL;
+    if (set_mesh(p, cur.v, cur.n)) { free(olv); free(ocell); free(of); free(src0); free(srcn); return -1; }
+    p->f = (double *)calloc((size_t)(p->ncells * nv), sizeof(double));
+    if (!p->f) return -1;
+    for (int64_t j = 0; j < p->ncells; j++) {
+        int64_t a = p->leaf_of_cell[j];
+        double *dst = p->f + j * nv;
+        int64_t nf = 0;
+        for (int64_t k = src0[a]; k < src0[a] + srcn[a]; k++) {
+            if (ocell[k] < 0) continue;
+            const double *src = of + ocell[k] * nv;
+            for (int64_t v = 0; v < nv; v++) dst[v] += src[v];
+            nf++;
+        }
+        if (nf == 0) memcpy(dst, p->finf, (size_t)nv * sizeof(double));
+        else for (int64_t v = 0; v < nv; v++) dst[v] /= (double)nf;
+    }
+    free(olv); free(ocell); free(of); free(src0); free(srcn);
+    return 0;
 }

@@ -170,6 +170,20 @@ int orc_learned_apply(orc_problem *p, double dt, double kn, const double *knl, c
  * A is row-major and is overwritten.  Returns 0, or -1 if singular. */
 int orc_solve(int n, double *A, double *b, double *x);
 
+/* ---- mesh adaptation with f carried over (Sec. 2.1; Sec. 3.1 step 4) ----
+ * flag [nleaves] marks leaves of the current Morton leaf list.
+ * orc_refine_project: every flagged leaf below max_level is split, then the
+ * tree is balanced 2:1 to a fixpoint; each new fluid cell takes the f of the
+ * old leaf that contains it (the freestream if that leaf was solid).
+ * orc_coarsen_project: every 2^dim sibling leaves that are all flagged, with
+ * their parent at or above the base level, merge into the parent, unless the
+ * parent would touch a leaf two or more levels finer (such merges are undone
+ * until none is left); a merged parent's f is the mean of its fluid
+ * children's f (the freestream if all were solid), an unchanged cell keeps
+ * its f.  Both rebuild cells and faces; 0 on success. */
+int orc_refine_project(orc_problem *p, const uint8_t *flag);
+int orc_coarsen_project(orc_problem *p, const uint8_t *flag);
+
 /* Lattice Boltzmann on the tree (Sec. 4): velocity sets, equilibrium, BGK.
  * Velocities in order of increasing |c|^2, ties lexicographic in
  * (c_x, c_y, c_z) with -1 < 0 < 1; c [Q][3], w [Q]. */
