@@ -26,8 +26,15 @@
  *     of order returns DVM_ESTATE.
  *   - Work is queued on the stream set by dvm_set_stream (default: the legacy
  *     default stream).  dvm_step synchronises that stream once per call to
- *     read the device status word.  No kernel traps; every device wait is
- *     bounded and reports DVM_ETIMEOUT.
+ *     read the device status word.  No kernel traps.  The waits on
+ *     asynchronous bulk copies (mbarrier waits of the hard-sphere, projection
+ *     and network kernels) are bounded to about a second and report
+ *     DVM_ETIMEOUT.  The step kernels' CTA-internal barriers (__syncthreads,
+ *     and the named barriers between the transport and solver warps of
+ *     dvm_step) carry no time bound, as no hardware barrier can; they
+ *     complete because every warp of a CTA walks the same finite list of
+ *     cells: CTA b of a grid of G takes cells b, b + G, b + 2G, ..., a list
+ *     that every warp computes from the launch shape alone.
  *   - A context is not thread-safe; use one context per host thread.
  *
  * Velocity ordering (Sec. 3.1 step 1): the Nv = nx*ny*nz nodes are stored as
@@ -83,7 +90,9 @@ enum { DVM_PRED_NONE = 0, DVM_PRED_BALL = 1, DVM_PRED_SHELL = 2 };
 
 typedef struct {
     int precision;   /* storage of f: DVM_F64 (FP64 arithmetic throughout), DVM_F32 or
-                        DVM_BF16 (FP32 arithmetic, FP64 moment finish and 5x5 solve) */
+                        DVM_BF16 (FP32 transport and collision arithmetic; the moment
+                        sums, the Eq. 6 correction systems and their solves in
+                        double-float, an FP64-class arithmetic of about 48 bits) */
     int collision;   /* DVM_COLL_*                                                  */
     double kn;       /* Knudsen number of Eq. 1                                     */
 } dvm_config;
@@ -279,6 +288,36 @@ int dvm_moments(dvm_ctx *ctx, double *rho, double *u, double *T);
  * post-collision state up to storage rounding). */
 int dvm_step_moments(dvm_ctx *ctx, double *rho, double *u, double *T);
 
+/* Conservation residual of the last collision update (Sec. 3.2, Eq. 6: the
+ * correction makes the discrete collision term conserve mass, momentum and
+ * energy), per cell: res [ncells][5] = sum_i psi_r(xi_i) q_i dV with
+ * psi = (1, xi_x, xi_y, xi_z, |xi|^2), where q is the collision term of the
+ * update f <- f* + dt q (BGK and entropic BGK: q = nu (M~ - f*)) or
+ * f <- f* + dt/Kn q (hard sphere, learned: q = I), the term defined by the
+ * update's per-axis tables and its correction coefficients.  The sums and the
+ * 5x5 solve behind it are formed in FP64-class arithmetic (double-float or
+ * FP64) on the device, so res measures how far the defined term is from
+ * conserving exactly; the FP32 evaluation of q at each node and the store of
+ * f round like FP32 storage and are not part of it.  Cells whose update was
+ * refused (non-positive moments) hold 0.  DVM_ESTATE before the first
+ * collision step, or after dvm_step_partitioned (which does not record it).
+ * Synchronises the stream. */
+int dvm_step_residual(dvm_ctx *ctx, double *res);
+
+/* Phase timing of dvm_step (a diagnostic, off by default).  With enable != 0
+ * every later step records CUDA events on the stream between its phases and
+ * waits for the last one (one host synchronisation per step), adding the
+ * phase times to three totals in ms: [0] the transport launch (for BGK and
+ * entropic BGK the whole fused step), [1] the collision kernels (hard sphere:
+ * the B, C and correction kernels; learned: sensor, projection, network and
+ * application), [2] the hard-sphere update of the cells the learned operator
+ * left over.  Enabling or disabling resets the totals. */
+int dvm_set_timing(dvm_ctx *ctx, int enable);
+
+/* The phase totals ms[3] and the number of steps behind them (steps may be
+ * NULL); the totals are reset. */
+int dvm_step_timing(dvm_ctx *ctx, double *ms, int64_t *steps);
+
 /* ---- learned collision operator: the network --------------------------------
  * 64 -> 256 -> 256 -> 256 -> 64 multilayer perceptron with SiLU hidden
  * activations (not in the paper).  Parameters are a flat FP32 vector of
@@ -407,15 +446,22 @@ int dvm_step_partitioned(dvm_ctx *ctx, int nparts, int nsteps, double dt);
  *           scratch, at most DVM_HS_NOALLOC_SCRATCH_BYTES: larger sizes
  *           return DVM_EINVAL before any work is queued;
  *   dt      time step.
+ * f must be 16-byte aligned (DVM_EINVAL otherwise): each cell's row is read
+ * by one bulk copy.
  * Uses the context's velocity grid, collision tables, Kn and stream, all
  * set up beforehand (DVM_ESTATE otherwise; FP32 storage only).  Scratch is
  * a fixed array in the library's device image: every GPU that loads the
  * library holds it until the process exits, every call shares it (its
  * contents are those of the last call; nothing in it needs to start at
  * zero), and calls whose work overlaps on the GPU race on it.  The first
- * call on a device looks up the array's device address; make that first
- * call before any stream capture.  Like dvm_step it synchronises the stream
- * once to read the status word. */
+ * call on a device (and the first after that device's context has been
+ * re-created, e.g. by cudaDeviceReset) looks up the array's device address;
+ * make that first call before any stream capture begins.  Every call
+ * synchronises the stream once to read the status word.  On DVM_EUNSTABLE
+ * (a singular correction, or dt/Kn max(P B) > 1) f already holds the
+ * applied update, invalid as it may be: a caller that needs to roll back
+ * keeps its own copy of f.  Non-positive density or temperature in a cell
+ * also returns DVM_EUNSTABLE; that cell's f is left unchanged. */
 int dvm_hs_collide_noalloc(dvm_ctx *ctx, float *f, int64_t ncells, double dt);
 
 /* ------------------------------------------------------------------------

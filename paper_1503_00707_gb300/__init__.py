@@ -42,7 +42,8 @@ EXPORTS = [
     "dvm_lbm_set_inflow", "dvm_lbm_init_equilibrium", "dvm_lbm_set_f", "dvm_lbm_get_f",
     "dvm_lbm_dt_cfl", "dvm_lbm_step", "dvm_lbm_moments", "dvm_lbm_get_codes",
     "dvm_coarsen", "dvm_coarsen_project", "dvm_kn_local", "dvm_flag_kinetic",
-    "dvm_partition_weighted", "dvm_lbm_lattice",
+    "dvm_partition_weighted", "dvm_lbm_lattice", "dvm_step_residual", "dvm_set_timing",
+    "dvm_step_timing",
 ]
 MLP_NPARAM = 164672
 HS_NOALLOC_SCRATCH_BYTES = 64 << 20
@@ -148,6 +149,9 @@ def lib():
             "dvm_flag_kinetic": [P, d, P, P],
             "dvm_partition_weighted": [P, C.c_int, P, C.c_int, P, P, P, P, i64],
             "dvm_lbm_lattice": [C.c_int, P, P, P],
+            "dvm_step_residual": [P, P],
+            "dvm_set_timing": [P, C.c_int],
+            "dvm_step_timing": [P, P, P],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -445,6 +449,23 @@ class Solver:
             out = (np.zeros(self.ncells), np.zeros((self.ncells, 3)), np.zeros(self.ncells))
         self._chk(lib().dvm_step_moments(self._h, *[_p(a) for a in out]))
         return out
+
+    def step_residual(self):
+        """[ncells][5] conservation residual sum_i psi_r q_i dV of the last
+        collision update, psi = (1, xi, |xi|^2) (see dvm_step_residual)."""
+        out = np.zeros((self.ncells, 5))
+        self._chk(lib().dvm_step_residual(self._h, _p(out)))
+        return out
+
+    def set_timing(self, enable=True):
+        self._chk(lib().dvm_set_timing(self._h, int(bool(enable))))
+
+    def step_timing(self):
+        """(ms[3] per phase: transport, collision, fallback; steps), reset after reading."""
+        ms = np.zeros(3)
+        n = C.c_int64()
+        self._chk(lib().dvm_step_timing(self._h, _p(ms), C.byref(n)))
+        return ms, n.value
 
     # ---- lattice Boltzmann (Sec. 4)
     def lbm_set_lattice(self, lattice):

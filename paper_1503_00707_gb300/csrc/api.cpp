@@ -49,8 +49,14 @@ struct dvm_ctx {
     double *d_xi = nullptr;
     double *d_mom = nullptr;     // step moments [ncells][5]
     double *d_mom2 = nullptr;    // moments of stored f
+    double *d_res = nullptr;     // conservation residual of the last step's collision term [ncells][5]
+    bool have_res = false;
+    // phase timing of dvm_step (dvm_set_timing): events and running totals
+    bool timing = false;
+    cudaEvent_t tev[4] = {nullptr, nullptr, nullptr, nullptr};
+    double tms[3] = {0.0, 0.0, 0.0};
+    int64_t tsteps = 0;
     int *d_status = nullptr;
-    unsigned long long *d_counter = nullptr;
     bool have_step_moments = false;
     bool mesh_on_device = false;
     dvm::HsTables hs;
@@ -165,8 +171,10 @@ void free_grid_buffers(dvm_ctx *c)
     dev_free(c, reinterpret_cast<void *&>(c->d_xi));
     dev_free(c, reinterpret_cast<void *&>(c->d_mom));
     dev_free(c, reinterpret_cast<void *&>(c->d_mom2));
+    dev_free(c, reinterpret_cast<void *&>(c->d_res));
     c->f_elems = 0;
     c->have_step_moments = false;
+    c->have_res = false;
 }
 
 int64_t ncells_of(const dvm_ctx *c) { return (int64_t)c->mesh.leaf_of_cell.size(); }
@@ -198,8 +206,6 @@ int ensure_device(dvm_ctx *c)
         c->d_status = nullptr;
         return fail(c, DVM_ECUDA, "device status word allocation failed");
     }
-    // the step kernel's cell dispenser shares the allocation
-    c->d_counter = reinterpret_cast<unsigned long long *>(c->d_status + 2);
     return DVM_OK;
 }
 
@@ -323,6 +329,7 @@ dvm::StepParams collision_params(dvm_ctx *c, double *mom)
     p.nv = c->nv;
     p.P = c->P;
     p.mom_out = mom;
+    p.dV = c->dV;
     p.status = c->d_status;
     p.stream = c->stream;
     return p;
@@ -331,7 +338,8 @@ dvm::StepParams collision_params(dvm_ctx *c, double *mom)
 // Learned collision update of f (FP32, [ncells][nv]) whose moments are mom:
 // sensor, projection, network (or the given device o), application with the
 // checks, then the hard-sphere operator on the cells left over.
-int learned_collide_device(dvm_ctx *c, float *f, double *mom, double dt, const float *o_in, float *q_out)
+int learned_collide_device(dvm_ctx *c, float *f, double *mom, double dt, const float *o_in, float *q_out,
+                           cudaEvent_t mid = nullptr)
 {
     const int64_t nc = ncells_of(c);
     int rc = dvm::launch_kn_local(mom, c->d_kn_start, c->d_kn_nb, c->d_kn_coef, nc, c->cfg.kn, c->d_knl, c->stream);
@@ -348,9 +356,11 @@ int learned_collide_device(dvm_ctx *c, float *f, double *mom, double dt, const f
         o_eq = c->d_lo + (size_t)nc * 64;
     }
     rc = dvm::launch_learned_apply(f, mom, o, o_eq, c->d_knl, c->kn_thr, c->d_amag, nc, c->n, dt / c->cfg.kn, c->d_used,
-                                   c->d_list, c->d_lcount, q_out, c->d_status, c->stream);
+                                   c->d_list, c->d_lcount, q_out, c->dV, c->d_res, c->d_status, c->stream);
     if (rc) return fail(c, rc, "learned collision launch failed");
+    if (mid) cudaEventRecord(mid, c->stream);
     dvm::StepParams p = collision_params(c, mom);
+    p.res_out = c->d_res;  // the cells left to the hard-sphere operator
     rc = dvm::launch_hs_general(c->hs, p, f, c->d_list, c->d_lcount, nullptr, c->cfg.kn, dt);
     return rc ? fail(c, rc, "hard-sphere fallback launch failed") : DVM_OK;
 }
@@ -398,6 +408,8 @@ void dvm_destroy(dvm_ctx *c)
     dvm::hs_free(c->hs, [c](void *p) { void *q = p; dev_free(c, q); });
     dvm::mlp_free(c->mlp, [c](void *p) { void *q = p; dev_free(c, q); });
     if (c->d_status) cudaFree(c->d_status);
+    for (int k = 0; k < 4; k++)
+        if (c->tev[k]) cudaEventDestroy(c->tev[k]);
     delete c;
 }
 
@@ -724,7 +736,8 @@ int dvm_set_velocity_grid(dvm_ctx *c, const int n[3], const double lo[3], const 
     c->d_xi = dev_alloc_t<double>(c, 3 * (size_t)c->nv);
     c->d_mom = dev_alloc_t<double>(c, 5 * (size_t)nc);
     c->d_mom2 = dev_alloc_t<double>(c, 5 * (size_t)nc);
-    if (!c->d_f[0] || !c->d_f[1] || !c->d_amag || !c->d_amag_f || !c->d_xi || !c->d_mom || !c->d_mom2) {
+    c->d_res = dev_alloc_t<double>(c, 5 * (size_t)nc);
+    if (!c->d_f[0] || !c->d_f[1] || !c->d_amag || !c->d_amag_f || !c->d_xi || !c->d_mom || !c->d_mom2 || !c->d_res) {
         free_grid_buffers(c);
         return fail(c, DVM_ENOMEM, "device allocation (f buffers)");
     }
@@ -938,11 +951,14 @@ int dvm_step(dvm_ctx *c, int nsteps, double dt)
     p.amag_f = c->d_amag_f;
     p.dt = dt;
     p.kn = c->cfg.kn;
+    p.nu_coef = 1.5957691216057308 / c->cfg.kn;
     p.dV = c->dV;
     p.mom_out = c->d_mom;
     p.status = c->d_status;
-    p.counter = c->d_counter;
     p.stream = c->stream;
+    // the BGK step kernel writes the residual of its collision term; the
+    // hard-sphere and learned updates write theirs after the transport launch
+    const bool bgk = c->cfg.collision == DVM_COLL_BGK || c->cfg.collision == DVM_COLL_BGK_ENTROPIC;
     if (c->cfg.collision == DVM_COLL_HS) {
         int rc = dvm::hs_prepare(c->hs, p.ncells, [c](size_t b) { return dev_alloc(c, b); },
                                  [c](void *q) { void *r = q; dev_free(c, r); });
@@ -955,23 +971,36 @@ int dvm_step(dvm_ctx *c, int nsteps, double dt)
     for (int s = 0; s < nsteps; s++) {
         p.f_in = c->d_f[c->cur];
         p.f_out = c->d_f[1 - c->cur];
-        if (cudaMemsetAsync(c->d_counter, 0, sizeof(unsigned long long), c->stream) != cudaSuccess) {
-            cudaGetLastError();
-            return fail(c, DVM_ECUDA, "counter reset failed");
-        }
+        p.res_out = bgk ? c->d_res : nullptr;
+        if (c->timing) cudaEventRecord(c->tev[0], c->stream);
         int rc = dvm::launch_step(p);
         if (rc) return fail(c, rc, rc == DVM_ENOTIMPL ? "velocity grid too large for the step kernel" : "step launch failed");
+        if (c->timing) cudaEventRecord(c->tev[1], c->stream);
+        p.res_out = c->d_res;
         if (c->cfg.collision == DVM_COLL_HS) {
             rc = dvm::launch_hs_collide(c->hs, p, c->d_f[1 - c->cur], c->cfg.kn, dt);
             if (rc) return fail(c, rc, "hard-sphere collision launch failed");
+            if (c->timing) cudaEventRecord(c->tev[2], c->stream);
         }
         if (c->cfg.collision == DVM_COLL_LEARNED) {
-            rc = learned_collide_device(c, static_cast<float *>(c->d_f[1 - c->cur]), c->d_mom, dt, nullptr, nullptr);
+            rc = learned_collide_device(c, static_cast<float *>(c->d_f[1 - c->cur]), c->d_mom, dt, nullptr, nullptr,
+                                        c->timing ? c->tev[2] : nullptr);
             if (rc) return rc;
+        }
+        if (c->timing) {
+            if (bgk || c->cfg.collision == DVM_COLL_NONE) cudaEventRecord(c->tev[2], c->stream);
+            cudaEventRecord(c->tev[3], c->stream);
+            rc = cuda_check(c, cudaEventSynchronize(c->tev[3]), "phase timing");
+            if (rc) return rc;
+            float t[3] = {0, 0, 0};
+            for (int k = 0; k < 3; k++) cudaEventElapsedTime(&t[k], c->tev[k], c->tev[k + 1]);
+            for (int k = 0; k < 3; k++) c->tms[k] += t[k];
+            c->tsteps++;
         }
         c->cur = 1 - c->cur;
     }
     c->have_step_moments = nsteps > 0 || c->have_step_moments;
+    if (nsteps > 0) c->have_res = c->cfg.collision != DVM_COLL_NONE;
     int st = 0;
     int rc = cuda_check(c, cudaMemcpyAsync(&st, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "read status");
     if (!rc) rc = cuda_check(c, cudaStreamSynchronize(c->stream), "step");
@@ -1138,9 +1167,9 @@ int dvm_step_partitioned(dvm_ctx *c, int nparts, int nsteps, double dt)
     base.amag_f = c->d_amag_f;
     base.dt = dt;
     base.kn = c->cfg.kn;
+    base.nu_coef = 1.5957691216057308 / c->cfg.kn;
     base.dV = c->dV;
     base.status = c->d_status;
-    base.counter = c->d_counter;
     base.stream = c->stream;
     for (int s = 0; s < nsteps && !rc; s++) {
         const int b = s & 1;
@@ -1158,8 +1187,7 @@ int dvm_step_partitioned(dvm_ctx *c, int nparts, int nsteps, double dt)
             q.st_cnt = c->d_cnt + pt.c0 * 8;
             q.inv_h = static_cast<const char *>(c->d_invh) + pt.c0 * tcs;
             q.mom_out = dev[p].mom;
-            rc = cuda_check(c, cudaMemsetAsync(c->d_counter, 0, sizeof(unsigned long long), c->stream), "counter reset");
-            if (!rc) rc = dvm::launch_step(q);
+            rc = dvm::launch_step(q);
             if (rc && rc != DVM_ECUDA) rc = fail(c, rc, "step launch failed");
         }
     }
@@ -1182,6 +1210,7 @@ int dvm_step_partitioned(dvm_ctx *c, int nparts, int nsteps, double dt)
     for (void *q : tmp) dev_free(c, q);
     if (rc) return rc;
     c->have_step_moments = nsteps > 0 || c->have_step_moments;
+    if (nsteps > 0) c->have_res = false;
     if (st) {
         cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream);
         return fail(c, DVM_EUNSTABLE, "unstable step (non-positive moments, singular system or nu dt > 1)");
@@ -1279,9 +1308,47 @@ int dvm_step_moments(dvm_ctx *c, double *rho, double *u, double *T)
     return copy_moments(c, c->d_mom, rho, u, T);
 }
 
+int dvm_set_timing(dvm_ctx *c, int enable)
+{
+    if (!c) return DVM_EINVAL;
+    if (enable && !c->tev[0])
+        for (int k = 0; k < 4; k++)
+            if (cudaEventCreate(&c->tev[k]) != cudaSuccess) {
+                cudaGetLastError();
+                return fail(c, DVM_ECUDA, "event creation failed");
+            }
+    c->timing = enable != 0;
+    c->tms[0] = c->tms[1] = c->tms[2] = 0.0;
+    c->tsteps = 0;
+    return DVM_OK;
+}
+
+int dvm_step_timing(dvm_ctx *c, double *ms, int64_t *steps)
+{
+    if (!c || !ms) return DVM_EINVAL;
+    for (int k = 0; k < 3; k++) ms[k] = c->tms[k];
+    if (steps) *steps = c->tsteps;
+    c->tms[0] = c->tms[1] = c->tms[2] = 0.0;
+    c->tsteps = 0;
+    return DVM_OK;
+}
+
+int dvm_step_residual(dvm_ctx *c, double *res)
+{
+    if (!c || !res) return DVM_EINVAL;
+    if (!c->have_res) return fail(c, DVM_ESTATE, "no collision step has run since the grid was set");
+    const int64_t nc = ncells_of(c);
+    int rc = cuda_check(c, cudaMemcpyAsync(res, c->d_res, (size_t)nc * 5 * sizeof(double), cudaMemcpyDeviceToHost,
+                                           c->stream), "copy residual");
+    if (!rc) rc = cuda_check(c, cudaStreamSynchronize(c->stream), "residual");
+    return rc;
+}
+
 int dvm_hs_collide_noalloc(dvm_ctx *c, float *f, int64_t ncells, double dt)
 {
     if (!c || !f || ncells < 1) return DVM_EINVAL;
+    if (reinterpret_cast<uintptr_t>(f) % 16)
+        return fail(c, DVM_EINVAL, "f must be 16-byte aligned (each cell's row is read by one bulk copy)");
     if (c->state < 2 || !c->hs.ready) return fail(c, DVM_ESTATE, "set the velocity grid and the collision tables first");
     if (c->cfg.precision != DVM_F32) return fail(c, DVM_ENOTIMPL, "the hard-sphere operator runs on FP32 storage");
     if (!(dt > 0.0) || !std::isfinite(dt)) return fail(c, DVM_EINVAL, "dt must be positive");
@@ -1484,6 +1551,7 @@ int dvm_learned_collide(dvm_ctx *c, double dt, const float *o_in, double *knl, f
     if (!rc && used) rc = cuda_check(c, cudaMemcpy(used, c->d_used, (size_t)nc * 4, cudaMemcpyDeviceToHost), "copy used");
     if (!rc && q) rc = cuda_check(c, cudaMemcpy(q, dq.p, (size_t)nc * c->nv * 4, cudaMemcpyDeviceToHost), "copy q");
     c->have_step_moments = false;
+    c->have_res = true;
     return rc;
 }
 

@@ -232,6 +232,49 @@ __device__ inline bool solve5_rcp(const T A[25], const T b[5], T x[5])
     return true;
 }
 
+// LDL^T factor of a symmetric positive definite 5x5 matrix (unit lower L,
+// reciprocal pivots Di); false if a pivot is not positive and finite.
+template <typename T> __device__ inline bool ldl5(const T A[25], T L[5][5], T Di[5])
+{
+    T D[5];
+#pragma unroll
+    for (int j = 0; j < 5; j++) {
+        T d = A[j * 5 + j];
+#pragma unroll
+        for (int k = 0; k < j; k++) d -= L[j][k] * L[j][k] * D[k];
+        if (!(d > (T)0) || !isfinite(d)) return false;
+        D[j] = d;
+        Di[j] = rcp_rn(d);
+#pragma unroll
+        for (int i = j + 1; i < 5; i++) {
+            T s = A[i * 5 + j];
+#pragma unroll
+            for (int k = 0; k < j; k++) s -= L[i][k] * L[j][k] * D[k];
+            L[i][j] = s * Di[j];
+        }
+    }
+    return true;
+}
+
+template <typename T> __device__ inline void ldl5_solve(const T L[5][5], const T Di[5], const T b[5], T x[5])
+{
+    T y[5];
+#pragma unroll
+    for (int i = 0; i < 5; i++) {
+        T s = b[i];
+#pragma unroll
+        for (int k = 0; k < i; k++) s -= L[i][k] * y[k];
+        y[i] = s;
+    }
+#pragma unroll
+    for (int i = 4; i >= 0; i--) {
+        T s = y[i] * Di[i];
+#pragma unroll
+        for (int k = i + 1; k < 5; k++) s -= L[k][i] * x[k];
+        x[i] = s;
+    }
+}
+
 }  // namespace dvm
 
 namespace dvm {

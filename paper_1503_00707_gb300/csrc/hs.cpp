@@ -73,10 +73,12 @@ void hs_free(HsTables &t, const DevFree &dfree)
     if (t.d_idx) dfree(t.d_idx);
     if (t.d_b) dfree(t.d_b);
     if (t.d_xi) dfree(t.d_xi);
+    if (t.d_jpk) dfree(t.d_jpk);
     if (t.d_bc) dfree(t.d_bc);
     t.d_idx = nullptr;
     t.d_b = nullptr;
     t.d_xi = nullptr;
+    t.d_jpk = nullptr;
     t.d_bc = nullptr;
     t.bc_cells = 0;
     t.ready = false;
@@ -89,6 +91,12 @@ int hs_build(HsTables &t, const int n[3], const double lo[3], const double h[3],
     hs_free(t, dfree);
     const int nv = n[0] * n[1] * n[2];
     if (nv > 65535) { err = "hard-sphere tables need Nv < 65536"; return DVM_ENOTIMPL; }
+    // the correction's exact integer basis (1, j, |j|^2) needs one spacing on
+    // every axis and |j|^4 < 2^24 (n <= 32)
+    if (h[0] != h[1] || h[0] != h[2] || n[0] > 32 || n[1] > 32 || n[2] > 32) {
+        err = "hard-sphere collisions need the same velocity spacing on every axis and n <= 32";
+        return DVM_ENOTIMPL;
+    }
     if (!hs_trials_supported(trials)) {
         err = "trials per node must be 32, 64, ..., 1024 (a power-of-two multiple of 32)";
         return DVM_ENOTIMPL;
@@ -169,15 +177,27 @@ int hs_build(HsTables &t, const int n[3], const double lo[3], const double h[3],
         }
     }
     std::vector<float> xf(3 * (size_t)nv);
-    for (int v = 0; v < nv; v++)
-        for (int d = 0; d < 3; d++) xf[(size_t)d * nv + v] = (float)xi[3 * (size_t)v + d];
+    std::vector<uint32_t> jp((size_t)nv);
+    for (int v = 0; v < nv; v++) {
+        uint32_t w = 0;
+        for (int d = 0; d < 3; d++) {
+            xf[(size_t)d * nv + v] = (float)xi[3 * (size_t)v + d];
+            // node k of axis d: xi = lo + (k + 1/2) h = (h/2) (2k + 1 - n)
+            const int k = (int)std::lround((xi[3 * (size_t)v + d] - lo[d]) / h[d] - 0.5);
+            w |= (uint32_t)(2 * k + 1 - n[d] + 64) << (8 * d);
+        }
+        jp[v] = w;
+    }
+    t.hh = 0.5 * h[0];
     t.d_idx = alloc(t.host_idx.size() * 4);
     t.d_b = static_cast<float *>(alloc(t.host_b.size() * 4));
     t.d_xi = static_cast<float *>(alloc(xf.size() * 4));
-    if (!t.d_idx || !t.d_b || !t.d_xi) { err = "device allocation (collision tables)"; return DVM_ENOMEM; }
+    t.d_jpk = static_cast<uint32_t *>(alloc(jp.size() * 4));
+    if (!t.d_idx || !t.d_b || !t.d_xi || !t.d_jpk) { err = "device allocation (collision tables)"; return DVM_ENOMEM; }
     if (cudaMemcpy(t.d_idx, t.host_idx.data(), t.host_idx.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(t.d_b, t.host_b.data(), t.host_b.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(t.d_xi, xf.data(), xf.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaMemcpy(t.d_xi, xf.data(), xf.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(t.d_jpk, jp.data(), jp.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess) {
         cudaGetLastError();
         err = "copy collision tables";
         return DVM_ECUDA;

@@ -13,9 +13,11 @@
 //            B_i = sum_k b f_gamma (Eq. 4) and C_i = sum_k c f_l f_m (Eq. 5)
 //            for its nodes to a per-cell scratch array.
 //  k_hs_corr per cell: the five coefficients of P (Eq. 6) from the moment
-//            system, solved in the centred basis (1, c, |c|^2 - 3),
-//            c = (xi - u)/sqrt(T), then I = -f P B + C and
-//            f <- f + dt/Kn I in place.
+//            system, its sums formed exactly in an integer basis and
+//            carried in double-float, solved in FP64 in the centred basis
+//            (1, c, |c|^2 - 3), c = (xi - u)/sqrt(T), and refined against
+//            the exact sums; then I = -f P B + C and f <- f + dt/Kn I in
+//            place.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -129,76 +131,173 @@ __global__ void __launch_bounds__(HT, 2)
     }
 }
 
-__global__ void __launch_bounds__(CT)
-    k_hs_corr(float *__restrict__ f, const float2 *__restrict__ bc, const float *__restrict__ xi3,
-              const double *__restrict__ mom, int nv, float dtkn, const int32_t *__restrict__ list,
-              const int *__restrict__ count, float *__restrict__ q_out, int *status)
+// Sum2 accumulation (Ogita, Rump and Oishi, 2005) of exact products:
+// s + e carries the running sum to about twice the FP32 precision.
+struct Acc2 {
+    float s, e;
+};
+// a += (x + xl) k, with x k split exactly (FMA) and xl k a small correction
+__device__ inline void acc2_prod(Acc2 &a, float x, float xl, float k)
 {
-    __shared__ float red[CT / 32][20];
-    __shared__ float sd[6];
+    const float p = x * k;
+    const float pe = fmaf(x, k, -p);
+    const float s = a.s + p;
+    const float bb = s - a.s;
+    const float se = (a.s - (s - bb)) + (p - bb);
+    a.s = s;
+    a.e += se + fmaf(xl, k, pe);
+}
+
+constexpr int NSUM = 20;  // 15 distinct entries of the moment matrix, 5 gain moments
+
+// k_hs_corr: one CTA per cell.  The correction polynomial of Eq. 6,
+// P = 1 + d.phi, phi = (1, c, |c|^2 - 3), c = (xi - u)/sqrt(T), makes
+// I = C - f P B conserve mass, momentum and energy.  The system is formed
+// exactly: with xi_d = (h/2) j_d (j_d odd integers, the same h on every
+// axis) the integer basis psi^ = (1, j_x, j_y, j_z, |j|^2) spans the same
+// polynomials, so the 15 sums A^_rs = sum_i psi^_r psi^_s f_i B_i and the 5
+// sums c^_r = sum_i psi^_r C_i have integer weights below 2^24 and products
+// split exactly (FMA); Sum2 carries them to double-float, and one thread
+// solves A^ e = c^, e = (1, 0, 0, 0, 0) + L^T d (L the map psi^ -> phi), in
+// FP64: the factor of L A^ L^T (well conditioned), refined twice against the
+// residual of the exact sums.  That residual, sum_i psi_r I_i dV with
+// psi = (1, xi, |xi|^2), goes to res (may be null).  Then I_i is evaluated
+// in FP32 with the FP32 copy of d and f <- f + dt/Kn I (or I to q_out).
+__global__ void __launch_bounds__(CT, 2)
+    k_hs_corr(float *__restrict__ f, const float2 *__restrict__ bc, const float *__restrict__ xi3,
+              const uint32_t *__restrict__ jpk, double hh, double dV, const double *__restrict__ mom, int nv,
+              float dtkn, const int32_t *__restrict__ list, const int *__restrict__ count, float *__restrict__ q_out,
+              double *__restrict__ res, int *status)
+{
+    __shared__ ffn part[NSUM][CT];
+    __shared__ double S[NSUM];
+    __shared__ float sd[5];
     // row blockIdx.x of B and C belongs to this cell (an entry of the list, if any)
     const int64_t row = blockIdx.x;
     if (list && row >= (int64_t)*count) return;
     const int64_t cell = list ? (int64_t)list[row] : row;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const double *mo = mom + cell * 5;
-    const float ux = (float)mo[1], uy = (float)mo[2], uz = (float)mo[3];
-    const float T = (float)mo[4];
-    const float ist = T > 0.0f ? rsqrtf(T) : 0.0f;
+    const double rho = mo[0], Td = mo[4];
+    if (!(rho > 0.0) || !(Td > 0.0) || !isfinite(rho + Td + mo[1] + mo[2] + mo[3])) {
+        // no correction exists: report, leave f as it is
+        if (tid == 0) {
+            atomicOr(status, ST_NONPOS);
+            if (res)
+                for (int r = 0; r < 5; r++) res[cell * 5 + r] = 0.0;
+        }
+        return;
+    }
     float *fc = f + cell * (int64_t)nv;
     const float2 *bcc = bc + row * (int64_t)nv;
-    float acc[20];
+    Acc2 acc[NSUM];
 #pragma unroll
-    for (int k = 0; k < 20; k++) acc[k] = 0.0f;
+    for (int k = 0; k < NSUM; k++) acc[k] = Acc2{0.0f, 0.0f};
     for (int v = tid; v < nv; v += CT) {
         const float fv = fc[v];
         const float2 q = bcc[v];
-        const float cx = (xi3[v] - ux) * ist, cy = (xi3[nv + v] - uy) * ist, cz = (xi3[2 * nv + v] - uz) * ist;
-        const float ph[5] = {1.0f, cx, cy, cz, cx * cx + cy * cy + cz * cz - 3.0f};
-        const float fB = fv * q.x, g = q.y - fB;
+        const uint32_t jp = jpk[v];
+        const float jx = (float)((int)(jp & 0xffu) - 64), jy = (float)((int)((jp >> 8) & 0xffu) - 64),
+                    jz = (float)((int)((jp >> 16) & 0xffu) - 64);
+        const float wv[5] = {1.0f, jx, jy, jz, jx * jx + jy * jy + jz * jz};
+        const float w = fv * q.x, wl = fmaf(fv, q.x, -w);  // f B = w + wl exactly
 #pragma unroll
         for (int r = 0, k = 0; r < 5; r++) {
 #pragma unroll
-            for (int c = r; c < 5; c++, k++) acc[k] = fmaf(ph[r] * ph[c], fB, acc[k]);
-            acc[15 + r] = fmaf(ph[r], g, acc[15 + r]);
+            for (int s = r; s < 5; s++, k++) acc2_prod(acc[k], w, wl, wv[r] * wv[s]);
+            acc2_prod(acc[15 + r], q.y, 0.0f, wv[r]);
         }
     }
 #pragma unroll
-    for (int k = 0; k < 20; k++) {
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) acc[k] += __shfl_down_sync(0xffffffffu, acc[k], off);
-        if (lane == 0) red[warp][k] = acc[k];
+    for (int k = 0; k < NSUM; k++) {
+        const float s = acc[k].s + acc[k].e;
+        const float bb = s - acc[k].s;
+        part[k][tid] = ffn{s, (acc[k].s - (s - bb)) + (acc[k].e - bb)};
     }
     __syncthreads();
-    if (warp == 0) {
-        ffn s[20];
+    // warp w adds sums w, w + 8, w + 16 over the CTA in double-float
+    for (int k = warp; k < NSUM; k += CT / 32) {
+        ffn a = part[k][lane];
 #pragma unroll
-        for (int k = 0; k < 20; k++) {
-            s[k] = ffn{lane < CT / 32 ? red[lane][k] : 0.0f, 0.0f};
+        for (int t = lane + 32; t < CT; t += 32) a = a + part[k][t];
 #pragma unroll
-            for (int m = 16; m > 0; m >>= 1)
-                s[k] = s[k] + ffn{__shfl_xor_sync(0xffffffffu, s[k].hi, m), __shfl_xor_sync(0xffffffffu, s[k].lo, m)};
+        for (int m = 16; m > 0; m >>= 1)
+            a = a + ffn{__shfl_xor_sync(0xffffffffu, a.hi, m), __shfl_xor_sync(0xffffffffu, a.lo, m)};
+        if (lane == 0) S[k] = (double)a.hi + (double)a.lo;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        double Aj[25], cj[5];
+        for (int r = 0, k = 0; r < 5; r++)
+            for (int s = r; s < 5; s++, k++) Aj[r * 5 + s] = Aj[s * 5 + r] = S[k];
+        for (int r = 0; r < 5; r++) cj[r] = S[15 + r];
+        const double isT = 1.0 / sqrt(Td), al = hh * isT;
+        const double be[3] = {-mo[1] * isT, -mo[2] * isT, -mo[3] * isT};
+        // phi = L psi^: phi_d = be_d + al j_d, phi_4 = |be|^2 - 3 + 2 al be.j + al^2 |j|^2
+        double L[25];
+        for (int k = 0; k < 25; k++) L[k] = 0.0;
+        L[0] = 1.0;
+        for (int d = 0; d < 3; d++) {
+            L[(1 + d) * 5] = be[d];
+            L[(1 + d) * 5 + 1 + d] = al;
+            L[20 + 1 + d] = 2.0 * al * be[d];
         }
-        if (lane == 0) {
-            float A[25], rhs[5], d[5];
-            int k = 0;
-            for (int r = 0; r < 5; r++)
-                for (int c = r; c < 5; c++) {
-                    const float v = s[k++].hi;
-                    A[r * 5 + c] = v;
-                    A[c * 5 + r] = v;
-                }
-            for (int r = 0; r < 5; r++) rhs[r] = s[15 + r].hi + s[15 + r].lo;
-            int ok = solve5<float>(A, rhs, d);
-            if (!ok) {
-                atomicOr(status, ST_SINGULAR);
-                for (int r = 0; r < 5; r++) d[r] = 0.0f;
+        L[20] = be[0] * be[0] + be[1] * be[1] + be[2] * be[2] - 3.0;
+        L[24] = al * al;
+        // preconditioner L A^ L^T
+        double T1[25], Ap[25];
+        for (int r = 0; r < 5; r++)
+            for (int s = 0; s < 5; s++) {
+                double t = 0.0;
+                for (int k = 0; k < 5; k++) t += L[r * 5 + k] * Aj[k * 5 + s];
+                T1[r * 5 + s] = t;
             }
-            for (int r = 0; r < 5; r++) sd[r] = d[r];
-            sd[5] = ok ? 1.0f : 0.0f;
+        for (int r = 0; r < 5; r++)
+            for (int s = 0; s < 5; s++) {
+                double t = 0.0;
+                for (int k = 0; k < 5; k++) t += T1[r * 5 + k] * L[s * 5 + k];
+                Ap[r * 5 + s] = t;
+            }
+        double Lf[5][5], Di[5], d[5] = {0, 0, 0, 0, 0}, R[5];
+        const bool ok = ldl5<double>(Ap, Lf, Di);
+        for (int it = 0; it < 3; it++) {
+            // e = (1, 0, 0, 0, 0) + L^T d; R = c^ - A^ e
+            double e[5];
+            for (int s = 0; s < 5; s++) {
+                double t = s == 0 ? 1.0 : 0.0;
+                for (int k = 0; k < 5; k++) t += L[k * 5 + s] * d[k];
+                e[s] = t;
+            }
+            for (int r = 0; r < 5; r++) {
+                double t = cj[r];
+                for (int s = 0; s < 5; s++) t -= Aj[r * 5 + s] * e[s];
+                R[r] = t;
+            }
+            if (it == 2 || !ok) break;
+            double LR[5], dl[5];
+            for (int r = 0; r < 5; r++) {
+                double t = 0.0;
+                for (int k = 0; k < 5; k++) t += L[r * 5 + k] * R[k];
+                LR[r] = t;
+            }
+            ldl5_solve<double>(Lf, Di, LR, dl);
+            for (int r = 0; r < 5; r++) d[r] += dl[r];
+        }
+        bool fin = ok;
+        for (int r = 0; r < 5; r++) fin = fin && isfinite(d[r]);
+        if (!fin) {
+            atomicOr(status, ST_SINGULAR);
+            for (int r = 0; r < 5; r++) d[r] = 0.0;
+        }
+        for (int r = 0; r < 5; r++) sd[r] = (float)d[r];
+        if (res) {
+            const double sc[5] = {dV, dV * hh, dV * hh, dV * hh, dV * hh * hh};
+            for (int r = 0; r < 5; r++) res[cell * 5 + r] = fin ? sc[r] * R[r] : 0.0;
         }
     }
     __syncthreads();
+    const float ux = (float)mo[1], uy = (float)mo[2], uz = (float)mo[3];
+    const float ist = rsqrtf((float)Td);
     const float d0 = sd[0], dx = sd[1], dy = sd[2], dz = sd[3], d4 = sd[4];
     float worst = 0.0f;
     for (int v = tid; v < nv; v += CT) {
@@ -263,9 +362,9 @@ int launch_hs_collide(HsTables &t, const StepParams &p, void *f, double kn, doub
     count_launch();
     if (cudaGetLastError() != cudaSuccess) return DVM_ECUDA;
     k_hs_corr<<<(unsigned)p.ncells, CT, 0, p.stream>>>(static_cast<float *>(f),
-                                                      reinterpret_cast<const float2 *>(t.d_bc), t.d_xi,
-                                                      p.mom_out, p.nv, (float)(dt / kn), nullptr, nullptr, nullptr,
-                                                      p.status);
+                                                      reinterpret_cast<const float2 *>(t.d_bc), t.d_xi, t.d_jpk,
+                                                      t.hh, p.dV, p.mom_out, p.nv, (float)(dt / kn), nullptr,
+                                                      nullptr, nullptr, p.res_out, p.status);
     count_launch();
     return cudaGetLastError() == cudaSuccess ? DVM_OK : DVM_ECUDA;
 }
@@ -299,8 +398,9 @@ int launch_hs_general(HsTables &t, const StepParams &p, float *f, const int32_t 
     count_launch();
     if (cudaGetLastError() != cudaSuccess) return DVM_ECUDA;
     k_hs_corr<<<(unsigned)p.ncells, CT, 0, p.stream>>>(f, reinterpret_cast<const float2 *>(t.d_bc), t.d_xi,
-                                                      p.mom_out, p.nv, q_out ? 0.0f : (float)(dt / kn), list, count,
-                                                      q_out, p.status);
+                                                      t.d_jpk, t.hh, p.dV, p.mom_out, p.nv,
+                                                      q_out ? 0.0f : (float)(dt / kn), list, count, q_out,
+                                                      q_out ? nullptr : p.res_out, p.status);
     count_launch();
     return cudaGetLastError() == cudaSuccess ? DVM_OK : DVM_ECUDA;
 }
@@ -315,11 +415,40 @@ constexpr size_t NOALLOC_BYTES = (size_t)DVM_HS_NOALLOC_SCRATCH_BYTES;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];
 
 std::mutex g_noalloc_mu;
-void *g_noalloc_ptr[256] = {nullptr};
+struct NoallocSlot {
+    void *ctx = nullptr;  // the context the address belongs to
+    void *ptr = nullptr;
+};
+NoallocSlot g_noalloc[256];
+
+// The calling thread's current context (a CUcontext), through the driver
+// entry point that the runtime hands out; null if it cannot be had.  Called
+// with g_noalloc_mu held.
+void *current_context()
+{
+    using Fn = int (*)(void **);
+    static Fn fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<Fn>(f);
+        else
+            cudaGetLastError();
+    }
+    void *ctx = nullptr;
+    if (!fn || fn(&ctx) != 0) return nullptr;
+    return ctx;
+}
 
 // Device address of the fixed scratch on the current device.  In host code
 // g_noalloc_scratch names a host-side stand-in, so the address is looked up
-// once per device, with that device current.
+// with the device current: once per device, and again if the device's
+// context has been re-created since (after cudaDeviceReset the old address
+// is stale).
 int noalloc_scratch(void **ptr)
 {
     int dev = 0;
@@ -328,15 +457,18 @@ int noalloc_scratch(void **ptr)
         return DVM_ECUDA;
     }
     std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (!g_noalloc_ptr[dev]) {
+    NoallocSlot &slot = g_noalloc[dev];
+    void *ctx = current_context();
+    if (!slot.ptr || !ctx || slot.ctx != ctx) {
         void *p = nullptr;
         if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
             cudaGetLastError();
             return DVM_ECUDA;
         }
-        g_noalloc_ptr[dev] = p;
+        slot.ptr = p;
+        slot.ctx = current_context();  // the lookup has made the context current
     }
-    *ptr = g_noalloc_ptr[dev];
+    *ptr = slot.ptr;
     return DVM_OK;
 }
 
@@ -349,13 +481,7 @@ int launch_hs_collide_noalloc(HsTables &t, const StepParams &p, float *f, const 
     if (!t.ready || t.nv != p.nv) return DVM_ESTATE;
     const size_t need_bc = (size_t)p.ncells * p.nv * 2 * sizeof(float);
     if (need_bc + (size_t)p.ncells * 5 * sizeof(double) > NOALLOC_BYTES) return DVM_EINVAL;
-    void *base = nullptr;
-    int rc = noalloc_scratch(&base);
-    if (rc) return rc;
-    float *bc = static_cast<float *>(base);
-    double *mom = reinterpret_cast<double *>(static_cast<unsigned char *>(base) + need_bc);
-    rc = launch_moments(DVM_F32, f, p.ncells, p.nv, xi, dV, mom, p.stream);
-    if (rc) return rc;
+    // every check comes before the first launch, so that a refusal queues no work
     const int tpn = t.trials / HE, npc = HT / tpn;
     const int chunks = (p.nv + npc - 1) / npc;
     const size_t dyn = 2 * (size_t)p.nv * sizeof(float);
@@ -367,6 +493,13 @@ int launch_hs_collide_noalloc(HsTables &t, const StepParams &p, float *f, const 
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_hs_bc, HT, dyn) != cudaSuccess || occ < 1)
         return DVM_ENOTIMPL;
+    void *base = nullptr;
+    int rc = noalloc_scratch(&base);
+    if (rc) return rc;
+    float *bc = static_cast<float *>(base);
+    double *mom = reinterpret_cast<double *>(static_cast<unsigned char *>(base) + need_bc);
+    rc = launch_moments(DVM_F32, f, p.ncells, p.nv, xi, dV, mom, p.stream);
+    if (rc) return rc;
     int64_t splits = std::max<int64_t>(1, (2 * (int64_t)nsm * occ + chunks - 1) / chunks);
     splits = std::min<int64_t>(splits, p.ncells);
     const int64_t per = (p.ncells + splits - 1) / splits;
@@ -376,8 +509,9 @@ int launch_hs_collide_noalloc(HsTables &t, const StepParams &p, float *f, const 
         per, nullptr, nullptr, p.status);
     count_launch();
     if (cudaGetLastError() != cudaSuccess) return DVM_ECUDA;
-    k_hs_corr<<<(unsigned)p.ncells, CT, 0, p.stream>>>(f, reinterpret_cast<const float2 *>(bc), t.d_xi, mom, p.nv,
-                                                      (float)(dt / kn), nullptr, nullptr, nullptr, p.status);
+    k_hs_corr<<<(unsigned)p.ncells, CT, 0, p.stream>>>(f, reinterpret_cast<const float2 *>(bc), t.d_xi, t.d_jpk,
+                                                      t.hh, dV, mom, p.nv, (float)(dt / kn), nullptr, nullptr,
+                                                      nullptr, nullptr, p.status);
     count_launch();
     return cudaGetLastError() == cudaSuccess ? DVM_OK : DVM_ECUDA;
 }

@@ -254,7 +254,8 @@ __global__ void __launch_bounds__(AT) k_lapply(float *__restrict__ f, const doub
                                                const double *__restrict__ knl,
                                                double thr, const double *__restrict__ amag, int3 n, float dtkn,
                                                int32_t *__restrict__ used, int32_t *__restrict__ list,
-                                               int *__restrict__ count, float *__restrict__ q_out, int *status)
+                                               int *__restrict__ count, float *__restrict__ q_out, double dV,
+                                               double *__restrict__ res, int *status)
 {
     extern __shared__ __align__(128) float dsm[];
     __shared__ float4 H[3][MAXN];
@@ -262,8 +263,8 @@ __global__ void __launch_bounds__(AT) k_lapply(float *__restrict__ f, const doub
     __shared__ float S1[16][MAXN];
     __shared__ float4 ZT[MAXN];  // (exp(-cz^2/2), d3 cz + d4 cz^2, cz^2/2, 0)
     __shared__ float os[64];
-    __shared__ float sums[3][14];
-    __shared__ float rred[2][5];
+    __shared__ double sums[3][14];
+    __shared__ double rred[2][5];
     __shared__ double cc[5];
     __shared__ double ered[AT / 32], qred[AT / 32];
     __shared__ int good;
@@ -306,21 +307,24 @@ __global__ void __launch_bounds__(AT) k_lapply(float *__restrict__ f, const doub
     axis_tables(amag, n, u, ist, H, G, tid, AT);
     __syncthreads();
     const int nz = n.z;
-    // per-axis sums: E_k = sum e c^k (k < 5), G_ak = sum e He_a c^k (a = 1..3, k < 3)
+    // per-axis sums: E_k = sum e c^k (k < 5), G_ak = sum e He_a c^k (a = 1..3,
+    // k < 3), in FP64 over the FP32 table values: the term these tables define
+    // then has its moments, and the correction below closes them, to FP64
+    // rounding
     if (tid < 42) {
         const int d = tid / 14, k = tid % 14;
         const int nd = d == 0 ? n.x : (d == 1 ? n.y : n.z);
-        float s = 0.0f;
+        double s = 0.0;
         for (int i = 0; i < nd; i++) {
             const float4 h = H[d][i];
-            const float c = G[d][i];
-            float t;
+            const double c = (double)G[d][i];
+            double t;
             if (k < 5) {
-                t = h.w;
+                t = (double)h.w;
                 for (int q = 0; q < k; q++) t *= c;
             } else {
                 const int a = (k - 5) / 3, kk = (k - 5) % 3;
-                t = h.w * (a == 0 ? h.x : (a == 1 ? h.y : h.z));
+                t = (double)h.w * (double)(a == 0 ? h.x : (a == 1 ? h.y : h.z));
                 for (int q = 0; q < kk; q++) t *= c;
             }
             s += t;
@@ -348,20 +352,20 @@ __global__ void __launch_bounds__(AT) k_lapply(float *__restrict__ f, const doub
     // moments of the reconstructed term: sum_m o_m R_r(m), R_r = sum e H_m phi_r
     if (tid < 64) {
         const int a = tid >> 4, b = (tid >> 2) & 3, c = tid & 3;
-        float gx[3], gy[3], gz[3];
+        double gx[3], gy[3], gz[3];
 #pragma unroll
         for (int k = 0; k < 3; k++) {
             gx[k] = a == 0 ? sums[0][k] : sums[0][5 + 3 * (a - 1) + k];
             gy[k] = b == 0 ? sums[1][k] : sums[1][5 + 3 * (b - 1) + k];
             gz[k] = c == 0 ? sums[2][k] : sums[2][5 + 3 * (c - 1) + k];
         }
-        const float w = os[tid];
-        float r[5];
+        const double w = os[tid];
+        double r[5];
         r[0] = gx[0] * gy[0] * gz[0];
         r[1] = gx[1] * gy[0] * gz[0];
         r[2] = gx[0] * gy[1] * gz[0];
         r[3] = gx[0] * gy[0] * gz[1];
-        r[4] = gx[2] * gy[0] * gz[0] + gx[0] * gy[2] * gz[0] + gx[0] * gy[0] * gz[2] - 3.0f * r[0];
+        r[4] = gx[2] * gy[0] * gz[0] + gx[0] * gy[2] * gz[0] + gx[0] * gy[0] * gz[2] - 3.0 * r[0];
 #pragma unroll
         for (int k = 0; k < 5; k++) {
             r[k] *= w;
@@ -398,24 +402,39 @@ __global__ void __launch_bounds__(AT) k_lapply(float *__restrict__ f, const doub
                 2.0 * (X[2] * Y[2] * Z[0] + X[2] * Y[0] * Z[2] + X[0] * Y[2] * Z[2]) - 6.0 * s2 + 9.0 * a00;
         for (int r = 0; r < 5; r++)
             for (int c = 0; c < r; c++) A[r * 5 + c] = A[c * 5 + r];
-        for (int r = 0; r < 5; r++) rhs[r] = (double)rsq * ((double)rred[0][r] + (double)rred[1][r]);
+        for (int r = 0; r < 5; r++) rhs[r] = (double)rsq * (rred[0][r] + rred[1][r]);
         double A0[25], b0[5];
         for (int k = 0; k < 25; k++) A0[k] = A[k];
         for (int k = 0; k < 5; k++) b0[k] = rhs[k];
         bool ok = valid && solve5<double>(A, rhs, x);
         if (ok) {
             // conservation residual of the correction, in FP64
-            double rn = 0.0, sc = 0.0;
+            double rn = 0.0, sc = 0.0, rv[5];
             for (int r = 0; r < 5; r++) {
                 double s = -b0[r], t = fabs(b0[r]);
                 for (int c = 0; c < 5; c++) {
                     s += A0[r * 5 + c] * x[c];
                     t += fabs(A0[r * 5 + c] * x[c]);
                 }
+                rv[r] = -s;
                 rn = fmax(rn, fabs(s));
                 sc = fmax(sc, t);
             }
             ok = rn <= 1e-12 * sc;
+            if (ok && res) {
+                // sum_i phi_r Q_i dV = dV Mc (rhs - A d), taken to
+                // psi = (1, xi, |xi|^2) with xi = sqrt(T) c + u
+                const double k = dV * Mc, uu[3] = {mo[1], mo[2], mo[3]};
+                double o5[5], dot = 0.0, u2 = 0.0;
+                o5[0] = k * rv[0];
+                for (int d = 0; d < 3; d++) {
+                    o5[1 + d] = k * (sq * rv[1 + d] + uu[d] * rv[0]);
+                    dot += uu[d] * rv[1 + d];
+                    u2 += uu[d] * uu[d];
+                }
+                o5[4] = k * (T * (rv[4] + 3.0 * rv[0]) + 2.0 * sq * dot + u2 * rv[0]);
+                for (int r = 0; r < 5; r++) res[cell * 5 + r] = o5[r];
+            }
         }
         for (int k = 0; k < 5; k++) cc[k] = ok ? x[k] : 0.0;
         good = ok ? 1 : 0;
@@ -561,7 +580,7 @@ int launch_hermite_project(const float *f, const double *mom, const double *amag
 
 int launch_learned_apply(float *f, const double *mom, const float *o, const float *o_eq, const double *knl, double thr,
                          const double *amag, int64_t ncells, const int n[3], double dtkn, int32_t *used,
-                         int32_t *list, int *count, float *q_out, int *status, cudaStream_t s)
+                         int32_t *list, int *count, float *q_out, double dV, double *res, int *status, cudaStream_t s)
 {
     if (!grid_ok(n)) return DVM_ENOTIMPL;
     if (ncells <= 0) return DVM_OK;
@@ -570,7 +589,7 @@ int launch_learned_apply(float *f, const double *mom, const float *o, const floa
     if (cudaFuncSetAttribute(k_lapply, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) != cudaSuccess)
         return DVM_ECUDA;
     k_lapply<<<(unsigned)ncells, AT, dyn, s>>>(f, mom, o, o_eq, knl, thr, amag, make_int3(n[0], n[1], n[2]), (float)dtkn,
-                                                used, list, count, q_out, status);
+                                                used, list, count, q_out, dV, res, status);
     count_launch();
     return cudaGetLastError() == cudaSuccess ? DVM_OK : DVM_ECUDA;
 }

@@ -7,9 +7,12 @@
 // warp-uniform, since it depends on the group only through the signs of the
 // velocity components (Sec. 3.1).
 //
-// Persistent CTAs take the Morton-ordered cells from a global counter, so
-// the cells in flight on the whole GPU form one contiguous Morton window and
-// upwind neighbours are served from L2.
+// Persistent CTAs take the Morton-ordered cells in a fixed order: CTA b of a
+// grid of G takes cells b, b + G, b + 2G, ...  Every cell costs about the
+// same, so the cells in flight on the whole GPU form one contiguous Morton
+// window and upwind neighbours are served from L2.  The assignment is a
+// function of the slot alone, so once a CTA's slot is empty every later slot
+// is empty too; the exits of the warp loops below rely on that.
 //
 // Compute warps, iteration j:
 //   phase 1  f*_i = (1 - dt invh sum_d |xi_d,i|) f_i + sum_d dt |xi_d,i| sum_k
@@ -30,7 +33,7 @@
 // M~ = M (1 + d.phi) (the correction form of Eq. 6) that make M~ carry the
 // moments of f*; per-axis tables g = exp(-c^2/2), P = d_axis c + d4 c^2)
 // runs while the compute warps transport cells j + 1 and j + 2.  Solver warps
-// also dispatch the cells, four iterations ahead.
+// also fetch the cells' stencils, four iterations ahead.
 //
 // Phase 3: f^{n+1} = (1 - nu dt) f* + nu dt M~ with M~ = rho (2 pi T)^(-3/2)
 //   gx gy gz (1 + d0 - 3 d4 + Px + Py + Pz), nu = sqrt(8/pi) rho sqrt(T)/Kn.
@@ -196,8 +199,9 @@ template <typename TC> struct CellSlot {
 };
 
 template <typename TC> struct StepSmem {
+    using X = typename Num<TC>::X;
     CellSlot<TC> slot[NSL];
-    TC red[NSS][MAXCW][7];
+    X red[NSS][MAXCW][7];  // per compute warp: the seven moment partials of a cell
     long long cellp[NSS];  // cell of the partials in red (-1: none)
     TabE<TC> tab[NSS][3][NAX];
     TC coef[NSS][CF_N];
@@ -205,7 +209,11 @@ template <typename TC> struct StepSmem {
     int ok[NSS];
     int dec[NSS];
     TC xin[3][NAX];   // velocity node values per axis, in index order
-    long long next0[2];  // the cells of slots 4 and 5, taken by warp 0
+    // the final solve of each solver warp: 1D sums, matrix entries,
+    // right-hand side, solution and residual
+    double g1d[2][3][5];
+    double sys[2][15];
+    double rhs[2][5], dsol[2][5], resid[2][5];
 };
 
 template <typename TC> struct Consts {
@@ -267,6 +275,138 @@ template <typename TC> __device__ inline TC warp_reduce7(const TC (&m)[7], int l
     return c;
 }
 
+// ---------------------------------------------------------------- exact moment partials
+// Error-free transformations (Dekker 1971): a + b = s + e and a b = p + e
+// exactly, e recovered in FP32.
+__device__ inline ffn two_sum(float a, float b)
+{
+    const float s = a + b;
+    const float bb = s - a;
+    return {s, (a - (s - bb)) + (b - bb)};
+}
+__device__ inline ffn two_prod(float a, float b)
+{
+    const float p = a * b;
+    return {p, fmaf(a, b, -p)};
+}
+
+__device__ inline float2 f2_add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+// b - a, rounded once
+__device__ inline float2 f2_sub(float2 b, float2 a) { return __ffma2_rn(a, make_float2(-1.0f, -1.0f), b); }
+
+// Signed sums over the eight sign groups, per position (packed pairs):
+// S = sum_o x_o and X, Y, Z = sum_o s_d(o) x_o with s_d = +1 in the groups of
+// positive xi_d (group o = 4[xi_x > 0] + 2[xi_y > 0] + [xi_z > 0]).
+__device__ inline void group_sums(const float2 (&x)[8], float2 &S, float2 &X, float2 &Y, float2 &Z)
+{
+    float2 pz[4], mz[4];
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        pz[k] = f2_add(x[2 * k], x[2 * k + 1]);
+        mz[k] = f2_sub(x[2 * k + 1], x[2 * k]);
+    }
+    Z = f2_add(f2_add(mz[0], mz[1]), f2_add(mz[2], mz[3]));
+    const float2 pp0 = f2_add(pz[0], pz[1]), pm0 = f2_sub(pz[1], pz[0]);
+    const float2 pp1 = f2_add(pz[2], pz[3]), pm1 = f2_sub(pz[3], pz[2]);
+    Y = f2_add(pm0, pm1);
+    S = f2_add(pp0, pp1);
+    X = f2_sub(pp1, pp0);
+}
+
+// The seven moment partials of one thread's 32 values of f* (8 groups x 4
+// consecutive z positions, node indices jx, jy, jz0 + 2e as odd integers,
+// xi_d = (h_d/2) s_d j_d):
+//   sum f, jx sum s_x f, jy sum s_y f, sum s_z jz f, jx^2 sum f, jy^2 sum f,
+//   sum jz^2 f
+// as double-float numbers, exact to about 2^-38 of the thread's sum |f|.
+// Each value is split x = q + r against sigma = 2^k >= 16 sum |x| (the
+// extraction of Rump, Ogita and Oishi, 2008): q = fl(fl(sigma + x) - sigma)
+// and r = x - q are exact, q is a multiple of 2^(k-24) and |r| <= 2^(k-24).
+// Every signed sum of the q's with integer weights of total size below 16
+// then stays a multiple of 2^(k-24) below 2^k, hence exact in FP32; the
+// weights jz = jz0 + 2e enter through
+//   sum_e jz_e Z_e = jz0 sum Z + 2 (Z_1 + 2 Z_2 + 3 Z_3),
+//   sum_e jz_e^2 S_e = jz0^2 sum S + 4 jz0 (S_1 + 2 S_2 + 3 S_3) + 4 (S_1 + 4 S_2 + 9 S_3)
+// and exact products; the r's, 2^-19 of sum |x| at most, are summed in FP32.
+__device__ inline void thread_moments(const QV<float> (&cur)[8], float jx, float jy, float jz0, ffn (&m)[7])
+{
+    float B = 0.0f;
+#pragma unroll
+    for (int o = 0; o < 8; o++)
+        B += (fabsf(cur[o].a.x) + fabsf(cur[o].a.y)) + (fabsf(cur[o].b.x) + fabsf(cur[o].b.y));
+    // B < 2^(ex - 126): sigma = 2^(ex - 122) >= 16 B (B finite)
+    const int ex = min((__float_as_int(B) >> 23) & 0xff, 249);
+    const float sg = __int_as_float((ex + 5) << 23);
+    const float2 s2 = make_float2(sg, sg);
+    float2 qa[8], qb[8], ra[8], rb[8];
+#pragma unroll
+    for (int o = 0; o < 8; o++) {
+        qa[o] = f2_sub(f2_add(cur[o].a, s2), s2);
+        qb[o] = f2_sub(f2_add(cur[o].b, s2), s2);
+        ra[o] = f2_sub(cur[o].a, qa[o]);
+        rb[o] = f2_sub(cur[o].b, qb[o]);
+    }
+    // exact parts: per position e = 0..3 (pairs a = (0, 1), b = (2, 3))
+    float2 Sa, Xa, Ya, Za, Sb, Xb, Yb, Zb;
+    group_sums(qa, Sa, Xa, Ya, Za);
+    group_sums(qb, Sb, Xb, Yb, Zb);
+    const float Sq = (Sa.x + Sa.y) + (Sb.x + Sb.y);
+    const float Xq = (Xa.x + Xa.y) + (Xb.x + Xb.y);
+    const float Yq = (Ya.x + Ya.y) + (Yb.x + Yb.y);
+    const float Zq = (Za.x + Za.y) + (Zb.x + Zb.y);
+    const float Az = (Za.y + (Zb.x + Zb.x)) + 3.0f * Zb.y;
+    const float A1 = (Sa.y + (Sb.x + Sb.x)) + 3.0f * Sb.y;
+    const float A2 = (Sa.y + 4.0f * Sb.x) + 9.0f * Sb.y;
+    // rounding parts, in FP32
+    group_sums(ra, Sa, Xa, Ya, Za);
+    group_sums(rb, Sb, Xb, Yb, Zb);
+    const float Sr = (Sa.x + Sa.y) + (Sb.x + Sb.y);
+    const float Xr = (Xa.x + Xa.y) + (Xb.x + Xb.y);
+    const float Yr = (Ya.x + Ya.y) + (Yb.x + Yb.y);
+    const float Zr = (Za.x + Za.y) + (Zb.x + Zb.y);
+    const float Azr = (Za.y + 2.0f * Zb.x) + 3.0f * Zb.y;
+    const float A1r = (Sa.y + 2.0f * Sb.x) + 3.0f * Sb.y;
+    const float A2r = (Sa.y + 4.0f * Sb.x) + 9.0f * Sb.y;
+    const float jx2 = jx * jx, jy2 = jy * jy, jz2 = jz0 * jz0, jz4 = 4.0f * jz0;
+    ffn t[7];
+    t[0] = ffn{Sq, 0.0f};
+    t[1] = two_prod(jx, Xq);
+    t[2] = two_prod(jy, Yq);
+    t[3] = two_prod(jz0, Zq) + ffn{2.0f * Az, 0.0f};
+    t[4] = two_prod(jx2, Sq);
+    t[5] = two_prod(jy2, Sq);
+    t[6] = (two_prod(jz2, Sq) + two_prod(jz4, A1)) + ffn{4.0f * A2, 0.0f};
+    const float r[7] = {Sr, jx * Xr, jy * Yr, fmaf(jz0, Zr, 2.0f * Azr), jx2 * Sr, jy2 * Sr,
+                        fmaf(jz2, Sr, fmaf(jz4, A1r, 4.0f * A2r))};
+#pragma unroll
+    for (int k = 0; k < 7; k++) {
+        const ffn u = two_sum(t[k].hi, t[k].lo + r[k]);
+        m[k] = u;
+    }
+}
+
+// warp_reduce7 on double-float numbers (the same reduce-scatter): returns,
+// in lane l, the warp total of sum l >> 2 (l < 28)
+__device__ inline ffn warp_reduce7_df(const ffn (&m)[7], int lane)
+{
+    auto sx = [](ffn v, int k) -> ffn {
+        return {__shfl_xor_sync(0xffffffffu, v.hi, k), __shfl_xor_sync(0xffffffffu, v.lo, k)};
+    };
+    ffn a[4], b[2];
+    const bool h4 = lane & 16, h3 = lane & 8, h2 = lane & 4;
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+        const ffn lo = m[i], hi = i < 3 ? m[4 + i] : ffn{0.0f, 0.0f};
+        a[i] = (h4 ? hi : lo) + sx(h4 ? lo : hi, 16);
+    }
+#pragma unroll
+    for (int i = 0; i < 2; i++) b[i] = (h3 ? a[2 + i] : a[i]) + sx(h3 ? a[i] : a[2 + i], 8);
+    ffn c = (h2 ? b[1] : b[0]) + sx(h2 ? b[0] : b[1], 4);
+    c = c + sx(c, 2);
+    c = c + sx(c, 1);
+    return c;
+}
+
 template <typename T> __device__ inline uint32_t dep_of(const QV<T> &q)
 {
     if constexpr (sizeof(T) == 8) return (uint32_t)__double2loint(q.a);
@@ -274,15 +414,59 @@ template <typename T> __device__ inline uint32_t dep_of(const QV<T> &q)
 }
 
 // ---------------------------------------------------------------- solver
-// Phase 2 of one cell on one warp: moments of f* from the compute warps'
-// partials, the conservatively corrected Maxwellian's coefficients and
-// per-axis tables into slot b.  Returns the status flags of the cell.  The
-// code is kept compact (rolled loops) because it runs once per cell between
-// the compute warps' instruction streams: straight-line code of this length
-// would be fetched from beyond the instruction cache every time.
+// The 15 distinct entries (r <= s) of the moment matrix of the target in the
+// centred basis phi = (1, c_x, c_y, c_z, |c|^2 - 3):
+//   A_rs = K dV sum_i phi_r phi_s g_x g_y g_z = K dV sum_t coef_t Gx[a_t] Gy[b_t] Gz[c_t],
+// G_d[k] = sum_n g_d(n) c_d(n)^k the 1D sums of axis d.  Each term is packed
+// as coef (signed byte) | a << 8 | b << 12 | c << 16; coef 0 pads.  Entry 14,
+// (|c|^2 - 3)^2, has ten terms and is split over two lanes.
+#define DVM_T(cf, a, b, c) ((int32_t)((cf) & 0xff) | ((a) << 8) | ((b) << 12) | ((c) << 16))
+__constant__ int32_t c_terms[15][10] = {
+    {DVM_T(1, 0, 0, 0)},
+    {DVM_T(1, 1, 0, 0)},
+    {DVM_T(1, 0, 1, 0)},
+    {DVM_T(1, 0, 0, 1)},
+    {DVM_T(1, 2, 0, 0), DVM_T(1, 0, 2, 0), DVM_T(1, 0, 0, 2), DVM_T(-3, 0, 0, 0)},
+    {DVM_T(1, 2, 0, 0)},
+    {DVM_T(1, 1, 1, 0)},
+    {DVM_T(1, 1, 0, 1)},
+    {DVM_T(1, 3, 0, 0), DVM_T(1, 1, 2, 0), DVM_T(1, 1, 0, 2), DVM_T(-3, 1, 0, 0)},
+    {DVM_T(1, 0, 2, 0)},
+    {DVM_T(1, 0, 1, 1)},
+    {DVM_T(1, 2, 1, 0), DVM_T(1, 0, 3, 0), DVM_T(1, 0, 1, 2), DVM_T(-3, 0, 1, 0)},
+    {DVM_T(1, 0, 0, 2)},
+    {DVM_T(1, 2, 0, 1), DVM_T(1, 0, 2, 1), DVM_T(1, 0, 0, 3), DVM_T(-3, 0, 0, 1)},
+    {DVM_T(1, 4, 0, 0), DVM_T(1, 0, 4, 0), DVM_T(1, 0, 0, 4), DVM_T(2, 2, 2, 0), DVM_T(2, 2, 0, 2),
+     DVM_T(2, 0, 2, 2), DVM_T(-6, 2, 0, 0), DVM_T(-6, 0, 2, 0), DVM_T(-6, 0, 0, 2), DVM_T(9, 0, 0, 0)},
+};
+#undef DVM_T
+
+// index of entry (r, s) among the 15 distinct ones
+__device__ inline int sym_e(int r, int s)
+{
+    const int a = r < s ? r : s, c = r < s ? s : r;
+    return a * 5 - (a * (a - 1)) / 2 + (c - a);
+}
+
+// Phase 2 of one cell on one warp (parity par): moments of f* from the
+// compute warps' partials, the coefficients of the target and its per-axis
+// tables into slot b.  Returns the status flags of the cell.  The code is
+// kept compact (rolled loops) because it runs once per cell between the
+// compute warps' instruction streams: straight-line code of this length would
+// be fetched from beyond the instruction cache every time.
+//
+// Precision (FP32/BF16 storage): the moment sums arrive in double-float and
+// give rho, u, T in double-float; the target's 1D sums, the 5x5 system of
+// Eq. 6's correction and its solution are formed in FP64 (an FP32 LDL^T
+// factor refined twice against FP64 residuals), so that the collision term
+// nu (M~ - f*) defined by the per-axis tables g and the FP64 coefficients
+// carries the moments of f* to FP64-class accuracy.  Its residual sum_i psi_r Q_i dV,
+// psi = (1, xi, |xi|^2), goes to res_out.  The FP32 evaluation of M~ at each
+// node (and the FP32 copy of the coefficients it uses) rounds like the FP32
+// store that follows it.
 template <typename TC, int COLL>
 __device__ inline int solve_cell(const StepParams &p, StepSmem<TC> &sm, const Consts<TC> &K, int b, int ncw,
-                                 long long cell)
+                                 long long cell, int par)
 {
     using N = Num<TC>;
     using X = typename N::X;
@@ -294,7 +478,7 @@ __device__ inline int solve_cell(const StepParams &p, StepSmem<TC> &sm, const Co
         const int k = lane >> 2;
         if (k < 7) {
 #pragma unroll 1
-            for (int w = lane & 3; w < ncw; w += 4) acc = acc + N::make(sm.red[b][w][k]);
+            for (int w = lane & 3; w < ncw; w += 4) acc = acc + sm.red[b][w][k];
         }
         acc = acc + N::shfl_xor(acc, 1);
         acc = acc + N::shfl_xor(acc, 2);
@@ -315,165 +499,285 @@ __device__ inline int solve_cell(const StepParams &p, StepSmem<TC> &sm, const Co
     // lane 0's verdict for the whole warp (the lanes' double-float sums may
     // differ in their last bits)
     flags = __shfl_sync(0xffffffffu, flags, 0);
-    // BGK: one solve for the correction polynomial 1 + d.phi of the
-    // Maxwellian, phi = (1, c, |c|^2 - 3).  Entropic BGK: the target is
-    // exp(-|c|^2/2 + e.phi); the same solve, made at exp(-|c|^2/2 + e.phi)
-    // in place of the Maxwellian, is Newton's step d for e.  The loop adds d
-    // to e until |d| is below ENT_TOL, and the last d is applied as the
-    // polynomial, which keeps the moments exact to the solve (as for BGK)
-    // and differs from exp(-|c|^2/2 + (e + d).phi) by O(d^2).
+    auto dbl = [](X v) -> double {
+        if constexpr (sizeof(TC) == 4) return (double)v.hi + (double)v.lo;
+        else return v;
+    };
+    // BGK: the target is the Maxwellian times the correction polynomial
+    // 1 + d.phi, phi = (1, c, |c|^2 - 3), of Eq. 6's form.  Entropic BGK: the
+    // target is exp(-|c|^2/2 + e.phi) (1 + d.phi); Newton steps on e (the
+    // same solve, made at the current target) run in the compute precision
+    // until the step is below ENT_TOL, and the last solve, below, gives the
+    // polynomial d that closes the moments (O(d^2) from the exponential).
     constexpr bool ENT = COLL == DVM_COLL_BGK_ENTROPIC;
     constexpr int NIT = ENT ? 8 : 1;
     const TC ENT_TOL = sizeof(TC) == 8 ? (TC)1e-9 : (TC)1e-5;
+    const int ax = lane >> 3, sub = lane & 7;
+    const int nax = ax < 3 ? p.n[ax] : 0;
     if ((COLL == DVM_COLL_BGK || ENT) && flags == 0) {
         const TC uT[3] = {N::tc(ux), N::tc(uy), N::tc(uz)};
         const X isT = N::rsqrt(T);
         const TC isTt = N::tc(isT);
         const X Kc = rho * K.c15 * isT * isT * isT;  // rho (2 pi T)^(-3/2)
-        const int ax = lane >> 3, sub = lane & 7;
         const TC ud = ax == 0 ? uT[0] : (ax == 1 ? uT[1] : uT[2]);
-        const int nax = ax < 3 ? p.n[ax] : 0;
         TC e[5] = {0, 0, 0, 0, 0};  // entropic: the accumulated e (every lane)
-        TC Kpt = N::tc(Kc);           // prefactor of the target, in TC
-        int done = 1;
+        if constexpr (ENT) {
+            TC Kpt = N::tc(Kc);
 #pragma unroll 1
-        for (int it = 0; it < NIT; it++) {
-            if constexpr (ENT) {
-                if (it > 0) {
-                    e[0] += sm.coef[b][CF_D0];
-                    e[1] += sm.coef[b][CF_DX];
-                    e[2] += sm.coef[b][CF_DY];
-                    e[3] += sm.coef[b][CF_DZ];
-                    e[4] += sm.coef[b][CF_D4];
-                    __syncwarp();
-                    // the one value used in the defects below and in the
-                    // collision, so that the moments stay exact to the solve
-                    Kpt = N::tc(Kc) * tc_exp<TC>(e[0] - (TC)3 * e[4]);
+            for (int it = 0; it < NIT; it++) {
+                const TC ea = ax == 0 ? e[1] : (ax == 1 ? e[2] : e[3]), e4 = e[4];
+                // 1D sums of g c^k, k = 0..4 (k = 0, 2 in double-float), with
+                // c = (xi - u)/sqrt(T), g = exp(-c^2/2 + e_axis c + e4 c^2):
+                // lanes 8d .. 8d + 7 take axis d, lane 8d + s the nodes s,
+                // s + 8, ...; the eight lanes of an axis then combine
+                X A0 = N::make((TC)0), A2 = N::make((TC)0);
+                TC A1 = 0, A3 = 0, A4 = 0;
+#pragma unroll 1
+                for (int i = sub; i < nax; i += 8) {
+                    const TC c = (sm.xin[ax][i] - ud) * isTt;
+                    const TC g = tc_exp<TC>((TC)-0.5 * c * c + c * (ea + e4 * c));
+                    const TC gc = g * c;
+                    A0 = A0 + N::make(g);
+                    A2 = A2 + N::make(gc) * c;
+                    A1 += gc;
+                    A3 += gc * c * c;
+                    A4 += gc * c * c * c;
+                }
+#pragma unroll
+                for (int m = 4; m > 0; m >>= 1) {
+                    A0 = A0 + N::shfl_xor(A0, m);
+                    A2 = A2 + N::shfl_xor(A2, m);
+                    A1 += __shfl_xor_sync(0xffffffffu, A1, m);
+                    A3 += __shfl_xor_sync(0xffffffffu, A3, m);
+                    A4 += __shfl_xor_sync(0xffffffffu, A4, m);
+                }
+                X G0[3], G2[3];
+                TC G1[3], G3[3], G4[3];
+#pragma unroll
+                for (int d = 0; d < 3; d++) {
+                    G0[d] = N::shfl(A0, 8 * d);
+                    G2[d] = N::shfl(A2, 8 * d);
+                    G1[d] = __shfl_sync(0xffffffffu, A1, 8 * d);
+                    G3[d] = __shfl_sync(0xffffffffu, A3, 8 * d);
+                    G4[d] = __shfl_sync(0xffffffffu, A4, 8 * d);
+                }
+                const X KdV = N::make(Kpt) * K.dV;
+                int done = 1;
+                if (lane == 0) {
+                    const X P0 = G0[0] * G0[1] * G0[2];
+                    const X Q2 = G2[0] * G0[1] * G0[2] + G0[0] * G2[1] * G0[2] + G0[0] * G0[1] * G2[2];
+                    const TC k = N::tc(KdV);
+                    TC g0[3], g2[3];
+#pragma unroll
+                    for (int d = 0; d < 3; d++) { g0[d] = N::tc(G0[d]); g2[d] = N::tc(G2[d]); }
+                    const TC p0v = g0[0] * g0[1] * g0[2];
+                    TC A[25], rhs[5], dd[5];
+                    A[0] = N::tc(KdV * P0);
+                    A[1] = k * G1[0] * g0[1] * g0[2];
+                    A[2] = k * g0[0] * G1[1] * g0[2];
+                    A[3] = k * g0[0] * g0[1] * G1[2];
+                    A[4] = N::tc(KdV * (Q2 - P0 - P0 - P0));
+                    A[6] = k * g2[0] * g0[1] * g0[2];
+                    A[7] = k * G1[0] * G1[1] * g0[2];
+                    A[8] = k * G1[0] * g0[1] * G1[2];
+                    A[9] = k * (G3[0] * g0[1] * g0[2] + G1[0] * g2[1] * g0[2] + G1[0] * g0[1] * g2[2] -
+                                (TC)3 * G1[0] * g0[1] * g0[2]);
+                    A[12] = k * g0[0] * g2[1] * g0[2];
+                    A[13] = k * g0[0] * G1[1] * G1[2];
+                    A[14] = k * (g2[0] * G1[1] * g0[2] + g0[0] * G3[1] * g0[2] + g0[0] * G1[1] * g2[2] -
+                                 (TC)3 * g0[0] * G1[1] * g0[2]);
+                    A[18] = k * g0[0] * g0[1] * g2[2];
+                    A[19] = k * (g2[0] * g0[1] * G1[2] + g0[0] * g2[1] * G1[2] + g0[0] * g0[1] * G3[2] -
+                                 (TC)3 * g0[0] * g0[1] * G1[2]);
+                    const TC s2 = g2[0] * g0[1] * g0[2] + g0[0] * g2[1] * g0[2] + g0[0] * g0[1] * g2[2];
+                    A[24] = k * (G4[0] * g0[1] * g0[2] + g0[0] * G4[1] * g0[2] + g0[0] * g0[1] * G4[2] +
+                                 (TC)2 * (g2[0] * g2[1] * g0[2] + g2[0] * g0[1] * g2[2] + g0[0] * g2[1] * g2[2]) -
+                                 (TC)6 * s2 + (TC)9 * p0v);
+#pragma unroll
+                    for (int r = 0; r < 5; r++)
+#pragma unroll
+                        for (int c2 = 0; c2 < r; c2++) A[r * 5 + c2] = A[c2 * 5 + r];
+                    rhs[0] = N::tc(rho - KdV * P0);
+                    rhs[1] = -A[1];
+                    rhs[2] = -A[2];
+                    rhs[3] = -A[3];
+                    rhs[4] = -A[4];
+                    const bool okk = solve5_rcp<TC>(A, rhs, dd);
+                    bool conv = okk;
+#pragma unroll
+                    for (int r = 0; r < 5; r++) {
+                        if (!okk) dd[r] = 0;
+                        conv = conv && fabs(dd[r]) < ENT_TOL;  // false on NaN
+                        sm.coef[b][r == 0 ? CF_D0 : CF_DX + r - 1] = dd[r];
+                    }
+                    if (!okk) flags |= ST_SINGULAR;
+                    done = conv || !okk;
+                }
+                __syncwarp();
+                e[0] += sm.coef[b][CF_D0];
+                e[1] += sm.coef[b][CF_DX];
+                e[2] += sm.coef[b][CF_DY];
+                e[3] += sm.coef[b][CF_DZ];
+                e[4] += sm.coef[b][CF_D4];
+                Kpt = N::tc(Kc) * tc_exp<TC>(e[0] - (TC)3 * e[4]);
+                __syncwarp();
+                if (__shfl_sync(0xffffffffu, done, 0)) break;
+            }
+        }
+        // ---- the final solve, in FP64 (a few dozen FP64 instructions per
+        // lane: shorter dependent chains than double-float on this GPU)
+        const double rd = dbl(rho), Td = dbl(T);
+        const double u3[3] = {dbl(ux), dbl(uy), dbl(uz)};
+        const double isTd = rsqrt(Td);
+        // K of the target: rho (2 pi T)^(-3/2) (entropic: times exp(e0 - 3 e4))
+        double Kd = rd * 0.06349363593424097 * isTd * isTd * isTd;
+        if constexpr (ENT) Kd *= (double)tc_exp<TC>(e[0] - (TC)3 * e[4]);
+        const double KdV = Kd * p.dV;
+        {
+            // 1D sums G_d[k] = sum_n g_d(n) c_d(n)^k, k = 0..4, with the node
+            // xi = (h_d/2) J, J = 2n + 1 - n_d, c = (xi - u)/sqrt(T), and g
+            // from c rounded to TC (the table value the collision uses)
+            double G[5] = {0, 0, 0, 0, 0};
+            if (ax < 3) {
+                const double hh = 0.5 * p.hv[ax], ua = u3[ax];
+                const TC ea = ENT ? (ax == 0 ? e[1] : (ax == 1 ? e[2] : e[3])) : (TC)0, e4 = ENT ? e[4] : (TC)0;
+#pragma unroll 1
+                for (int i = sub; i < nax; i += 8) {
+                    const double c = (hh * (double)(2 * i + 1 - nax) - ua) * isTd;
+                    const TC cf = (TC)c;
+                    TC ex = (TC)-0.5 * cf * cf;
+                    if constexpr (ENT) ex += cf * (ea + e4 * cf);
+                    const TC gt = tc_exp<TC>(ex);
+                    sm.tab[b][ax][i] = TabE<TC>{gt, cf};  // p holds c until the solve is done
+                    const double g = (double)gt, gc = g * c, gc2 = gc * c;
+                    G[0] += g;
+                    G[1] += gc;
+                    G[2] += gc2;
+                    G[3] += gc2 * c;
+                    G[4] += gc2 * c * c;
                 }
             }
-            const TC ea = ENT ? (ax == 0 ? e[1] : (ax == 1 ? e[2] : e[3])) : (TC)0, e4 = ENT ? e[4] : (TC)0;
-            // 1D sums of g c^k, k = 0..4 (k = 0, 2 in double-float), with
-            // c = (xi - u)/sqrt(T), g = exp(-c^2/2) (entropic: times
-            // exp(d_axis c + d4 c^2)): lanes 8d .. 8d + 7 take axis d, lane
-            // 8d + s the nodes s, s + 8, s + 16, s + 24; the eight lanes of an
-            // axis then combine in three butterfly levels
-            X A0 = N::make((TC)0), A2 = N::make((TC)0);
-            TC A1 = 0, A3 = 0, A4 = 0;
+#pragma unroll
+            for (int m = 4; m > 0; m >>= 1)
+#pragma unroll
+                for (int k = 0; k < 5; k++) G[k] += __shfl_xor_sync(0xffffffffu, G[k], m);
+            if (sub == 0 && ax < 3)
+#pragma unroll
+                for (int k = 0; k < 5; k++) sm.g1d[par][ax][k] = G[k];
+        }
+        __syncwarp();
+        {
+            // the 15 entries on lanes 0..15 (entry 14 on lanes 14 and 15)
+            double a = 0.0;
+            if (lane < 16) {
+                const int en = lane < 15 ? lane : 14, t0 = lane == 15 ? 5 : 0;
 #pragma unroll 1
-            for (int i = sub; i < nax; i += 8) {
-                const TC c = (sm.xin[ax][i] - ud) * isTt;
-                TC ex = (TC)-0.5 * c * c;
-                if constexpr (ENT) ex += c * (ea + e4 * c);
-                const TC g = tc_exp<TC>(ex);
-                const TC gc = g * c;
-                A0 = A0 + N::make(g);
-                A2 = A2 + N::make(gc) * c;
-                A1 += gc;
-                A3 += gc * c * c;
-                A4 += gc * c * c * c;
+                for (int t = t0; t < t0 + 5; t++) {
+                    const int32_t w = c_terms[en][t];
+                    const int cf = (int)(int8_t)(w & 0xff);
+                    if (cf != 0)
+                        a += (double)cf * sm.g1d[par][0][(w >> 8) & 15] * sm.g1d[par][1][(w >> 12) & 15] *
+                             sm.g1d[par][2][(w >> 16) & 15];
+                }
             }
+            const double other = __shfl_sync(0xffffffffu, a, 15);
+            if (lane == 14) a += other;
+            if (lane < 15) sm.sys[par][lane] = a * KdV;
+        }
+        __syncwarp();
+        // right-hand side: the moments of f* in phi are (rho, 0, 0, 0, 0) by
+        // the definition of u and T, less those of the uncorrected target
+        // (row 0 of the matrix); the TC factor of lane 0, then two refinements
+        // against FP64 residuals rhs - A d computed one row per lane
+        TC Lf[5][5], Dif[5];
+        int fok = 1;
+        if (lane == 0) {
+            TC Af[25], r[5], dl[5];
 #pragma unroll
-            for (int m = 4; m > 0; m >>= 1) {
-                A0 = A0 + N::shfl_xor(A0, m);
-                A2 = A2 + N::shfl_xor(A2, m);
-                A1 += __shfl_xor_sync(0xffffffffu, A1, m);
-                A3 += __shfl_xor_sync(0xffffffffu, A3, m);
-                A4 += __shfl_xor_sync(0xffffffffu, A4, m);
-            }
-            X G0[3], G2[3];
-            TC G1[3], G3[3], G4[3];
+            for (int r2 = 0; r2 < 5; r2++)
 #pragma unroll
-            for (int d = 0; d < 3; d++) {
-                G0[d] = N::shfl(A0, 8 * d);
-                G2[d] = N::shfl(A2, 8 * d);
-                G1[d] = __shfl_sync(0xffffffffu, A1, 8 * d);
-                G3[d] = __shfl_sync(0xffffffffu, A3, 8 * d);
-                G4[d] = __shfl_sync(0xffffffffu, A4, 8 * d);
-            }
-            const X KdV = ENT && it > 0 ? N::make(Kpt) * K.dV : Kc * K.dV;
-            if (lane == 0) {
-                // moments of the target in the centred basis; defects in
-                // double-float
-                const X P0 = G0[0] * G0[1] * G0[2];
-                const X Q2 = G2[0] * G0[1] * G0[2] + G0[0] * G2[1] * G0[2] + G0[0] * G0[1] * G2[2];
-                const TC r0 = N::tc(rho - KdV * P0);
-                const TC b04 = N::tc(KdV * (Q2 - P0 - P0 - P0));
-                const TC k = N::tc(KdV);
-                TC g0[3], g2[3];
+                for (int c2 = 0; c2 < 5; c2++) Af[r2 * 5 + c2] = (TC)sm.sys[par][sym_e(r2, c2)];
+            sm.rhs[par][0] = rd - sm.sys[par][0];
 #pragma unroll
-                for (int d = 0; d < 3; d++) { g0[d] = N::tc(G0[d]); g2[d] = N::tc(G2[d]); }
-                const TC p0v = g0[0] * g0[1] * g0[2];
-                TC A[25], rhs[5], dd[5];
-                A[0] = N::tc(KdV * P0);
-                A[1] = k * G1[0] * g0[1] * g0[2];
-                A[2] = k * g0[0] * G1[1] * g0[2];
-                A[3] = k * g0[0] * g0[1] * G1[2];
-                A[4] = b04;
-                A[6] = k * g2[0] * g0[1] * g0[2];
-                A[7] = k * G1[0] * G1[1] * g0[2];
-                A[8] = k * G1[0] * g0[1] * G1[2];
-                A[9] = k * (G3[0] * g0[1] * g0[2] + G1[0] * g2[1] * g0[2] + G1[0] * g0[1] * g2[2] -
-                            (TC)3 * G1[0] * g0[1] * g0[2]);
-                A[12] = k * g0[0] * g2[1] * g0[2];
-                A[13] = k * g0[0] * G1[1] * G1[2];
-                A[14] = k * (g2[0] * G1[1] * g0[2] + g0[0] * G3[1] * g0[2] + g0[0] * G1[1] * g2[2] -
-                             (TC)3 * g0[0] * G1[1] * g0[2]);
-                A[18] = k * g0[0] * g0[1] * g2[2];
-                A[19] = k * (g2[0] * g0[1] * G1[2] + g0[0] * g2[1] * G1[2] + g0[0] * g0[1] * G3[2] -
-                             (TC)3 * g0[0] * g0[1] * G1[2]);
-                const TC s2 = g2[0] * g0[1] * g0[2] + g0[0] * g2[1] * g0[2] + g0[0] * g0[1] * g2[2];
-                A[24] = k * (G4[0] * g0[1] * g0[2] + g0[0] * G4[1] * g0[2] + g0[0] * g0[1] * G4[2] +
-                             (TC)2 * (g2[0] * g2[1] * g0[2] + g2[0] * g0[1] * g2[2] + g0[0] * g2[1] * g2[2]) -
-                             (TC)6 * s2 + (TC)9 * p0v);
+            for (int r2 = 1; r2 < 5; r2++) sm.rhs[par][r2] = -sm.sys[par][r2];
+            fok = ldl5<TC>(Af, Lf, Dif) ? 1 : 0;
 #pragma unroll
-                for (int r = 0; r < 5; r++)
+            for (int r2 = 0; r2 < 5; r2++) r[r2] = (TC)sm.rhs[par][r2];
+            if (fok) ldl5_solve<TC>(Lf, Dif, r, dl);
+            else flags |= ST_SINGULAR;
 #pragma unroll
-                    for (int c2 = 0; c2 < r; c2++) A[r * 5 + c2] = A[c2 * 5 + r];
-                rhs[0] = r0;
-                rhs[1] = -A[1];
-                rhs[2] = -A[2];
-                rhs[3] = -A[3];
-                rhs[4] = -b04;
-                if (!solve5_rcp<TC>(A, rhs, dd)) flags |= ST_SINGULAR;
-                TC *cf = sm.coef[b];
-                cf[CF_D0] = dd[0];
-                cf[CF_C0] = (TC)1 + dd[0] - (TC)3 * dd[4];
-                cf[CF_DX] = dd[1];
-                cf[CF_DY] = dd[2];
-                cf[CF_DZ] = dd[3];
-                cf[CF_D4] = dd[4];
-                bool conv = true;
+            for (int r2 = 0; r2 < 5; r2++) sm.dsol[par][r2] = fok ? (double)dl[r2] : 0.0;
+        }
+        __syncwarp();
+#pragma unroll 1
+        for (int it = 0; it < 3; it++) {
+            if (lane < 5) {
+                double s = sm.rhs[par][lane];
 #pragma unroll
-                for (int r = 0; r < 5; r++) conv = conv && fabs(dd[r]) < ENT_TOL;  // false on NaN
-                if (!conv && !flags) done = 0;
+                for (int c2 = 0; c2 < 5; c2++) s -= sm.sys[par][sym_e(lane, c2)] * sm.dsol[par][c2];
+                sm.resid[par][lane] = s;
             }
             __syncwarp();
-            if (__shfl_sync(0xffffffffu, done, 0)) break;
-            done = 1;
+            if (it == 2) break;
+            if (lane == 0 && fok) {
+                TC r[5], dl[5];
+#pragma unroll
+                for (int r2 = 0; r2 < 5; r2++) r[r2] = (TC)sm.resid[par][r2];
+                ldl5_solve<TC>(Lf, Dif, r, dl);
+#pragma unroll
+                for (int r2 = 0; r2 < 5; r2++) sm.dsol[par][r2] += (double)dl[r2];
+            }
+            __syncwarp();
         }
         TC *cf = sm.coef[b];
         if (lane == 0) {
+            const double d0 = sm.dsol[par][0], d4 = sm.dsol[par][4];
+            cf[CF_D0] = (TC)d0;
+            cf[CF_DX] = (TC)sm.dsol[par][1];
+            cf[CF_DY] = (TC)sm.dsol[par][2];
+            cf[CF_DZ] = (TC)sm.dsol[par][3];
+            cf[CF_D4] = (TC)d4;
+            cf[CF_C0] = (TC)(1.0 + d0 - 3.0 * d4);
             const TC nudt = K.nu0 * N::tc(rho) * sqrt(N::tc(T));
             if (nudt > (TC)1) flags |= ST_NUDT;
-            cf[CF_KN] = nudt * Kpt;
+            cf[CF_KN] = nudt * (TC)Kd;
             cf[CF_OMN] = (TC)1 - nudt;
+            if (p.res_out) {
+                // sum_i psi_r Q_i dV of Q = nu (M~ - f*): the phi moments of
+                // M~ - f* are A d - rhs, taken to psi = (1, xi, |xi|^2) with
+                // xi = c / isT + u
+                double r[5];
+#pragma unroll
+                for (int r2 = 0; r2 < 5; r2++) r[r2] = fok ? -sm.resid[par][r2] : 0.0;
+                const double sT = Td * isTd;
+                const double nu = p.nu_coef * rd * sT;
+                double *o = p.res_out + cell * 5;
+                o[0] = nu * r[0];
+                double dot = 0.0, uu = 0.0;
+#pragma unroll
+                for (int d = 0; d < 3; d++) {
+                    o[1 + d] = nu * (sT * r[1 + d] + u3[d] * r[0]);
+                    dot += u3[d] * r[1 + d];
+                    uu += u3[d] * u3[d];
+                }
+                o[4] = nu * (Td * (r[4] + 3.0 * r[0]) + 2.0 * sT * dot + uu * r[0]);
+            }
         }
         __syncwarp();
         // per-axis factors of the target, each lane for its nodes:
-        // g = exp(-c^2/2) (entropic: exp(-c^2/2 + e_axis c + e4 c^2)) and
-        // P = d_axis c + d4 c^2
+        // g (stored above) and P = c (d_axis + d4 c)
         const TC d4 = cf[CF_D4];
         if (ax < 3) {
             const TC da = cf[CF_DX + ax];
-            const TC ea = ENT ? (ax == 0 ? e[1] : (ax == 1 ? e[2] : e[3])) : (TC)0, e4 = ENT ? e[4] : (TC)0;
 #pragma unroll 1
             for (int i = sub; i < nax; i += 8) {
-                const TC c = (sm.xin[ax][i] - ud) * isTt;
-                TC ex = (TC)-0.5 * c * c;
-                if constexpr (ENT) ex += c * (ea + e4 * c);
-                sm.tab[b][ax][i] = TabE<TC>{tc_exp<TC>(ex), c * (da + d4 * c)};
+                const TC c = sm.tab[b][ax][i].p;
+                sm.tab[b][ax][i].p = c * (da + d4 * c);
             }
         }
+    } else if (lane == 0 && p.res_out) {
+#pragma unroll
+        for (int r2 = 0; r2 < 5; r2++) p.res_out[cell * 5 + r2] = 0.0;
     }
     if (lane == 0) {
         sm.mom[b][0] = rho;
@@ -515,10 +819,10 @@ __global__ void __launch_bounds__(MAXT, 1) k_step(const StepParams p)
     const TS *__restrict__ fin = static_cast<const TS *>(p.f_in);
     TS *__restrict__ fout = static_cast<TS *>(p.f_out);
 
-    // cell dispatch (one warp): a cell index from the global counter, its
-    // stencil fetched into registers, then stored into a slot; split so
-    // that a solver overlaps the counter's round trip and the loads with its
-    // own work.
+    // cell dispatch (one warp): the cell of slot k (its k-th iteration) is
+    // blockIdx.x + k gridDim.x, or none (-1) past the last cell; its stencil
+    // is fetched into registers, then stored into a slot, split so that a
+    // solver overlaps the loads with its own work.
     // raw loaded values only: anything computed from them waits for the
     // loads, so it is left to store(), after the solve
     struct Sten {
@@ -528,12 +832,10 @@ __global__ void __launch_bounds__(MAXT, 1) k_step(const StepParams p)
         int cnt;
         TC invh;
     };
-    auto take_issue = [&]() -> unsigned long long { return lane == 0 ? atomicAdd(p.counter, 1ull) : 0ull; };
-    auto take_finish = [&](unsigned long long c) -> long long {
-        c = __shfl_sync(0xffffffffu, c, 0);
-        return c < (unsigned long long)p.ncells ? (long long)c : -1;
+    auto cell_of = [&](int k) -> long long {
+        const long long c = (long long)blockIdx.x + (long long)k * gridDim.x;
+        return c < p.ncells ? c : -1;
     };
-    auto take = [&]() -> long long { return take_finish(take_issue()); };
     auto fetch = [&](long long cell) {
         Sten t{cell, 0, 0, (TC)0, 0, (TC)0};
         if (cell >= 0) {
@@ -572,19 +874,9 @@ __global__ void __launch_bounds__(MAXT, 1) k_step(const StepParams p)
     };
 
     if (warp == 0) {
-        // cells of iterations 0..3, then those of 4 and 5 for the two solver
-        // warps, all taken in slot order: once a take comes back empty every
-        // later slot is empty too, which the exit of the loops below relies
-        // on (the two solver warps taking 4 and 5 themselves could race)
-        for (int k = 0; k < 4; k++) store(fetch(take()), k);
-        {
-            const long long n4 = take();
-            const long long n5 = take();
-            if (lane == 0) {
-                sm.next0[0] = n4;
-                sm.next0[1] = n5;
-            }
-        }
+        // the stencils of iterations 0..3; the solver warps fetch those of
+        // iteration j + 4 while they solve cell j
+        for (int k = 0; k < 4; k++) store(fetch(cell_of(k)), k);
 #pragma unroll
         for (int d = 0; d < 3; d++) {
             const int hd = p.half[d];
@@ -613,20 +905,17 @@ __global__ void __launch_bounds__(MAXT, 1) k_step(const StepParams p)
     if (warp < 2) {
         // ================= solver warps: warp b takes the cells j = b mod 2
         const int par = warp;
-        long long next_cell = sm.next0[par];  // the cell of slot par + 4
         for (int j = par;; j += 2) {
             const int q = j % NSS;
             bar_sync_n(BAR_P + q, nbar);
             const long long cell = sm.cellp[q];
             const int dec = cell < 0 ? DEC_END : DEC_GO;
             if (dec == DEC_GO) {
-                // the stencil of iteration j + 4: its loads and the next take
-                // are in flight during the solve
-                const Sten nst = fetch(next_cell);
-                const unsigned long long nc = take_issue();
-                const int flags = solve_cell<TC, COLL>(p, sm, K, q, ncw, cell);
+                // the stencil of iteration j + 4: its loads are in flight
+                // during the solve
+                const Sten nst = fetch(cell_of(j + 4));
+                const int flags = solve_cell<TC, COLL>(p, sm, K, q, ncw, cell, par);
                 store(nst, j + 4);
-                next_cell = take_finish(nc);
                 if (lane == 0) {
                     if (flags) atomicOr(p.status, flags);
                     sm.ok[q] = (COLL == DVM_COLL_BGK || COLL == DVM_COLL_BGK_ENTROPIC) &&
@@ -754,37 +1043,44 @@ __global__ void __launch_bounds__(MAXT, 1) k_step(const StepParams p)
                 if (o == NST) on = point(j + 1);
                 copy_group(on, (o + NST) & 7, o % NST, dep_of(fs));
             }
-            // seven integer-weighted partial sums of this thread:
+            // the seven integer-weighted partial sums of this thread:
             // sum f, sum s_x j_x f, sum s_y j_y f, sum s_z j_z f, sum j_x^2 f,
             // sum j_y^2 f, sum j_z^2 f  (xi_d = (h_d/2) s_d j_d, j_d odd)
-            Q4 T0 = q_splat((TC)0), Tz = q_splat((TC)0);
-            TC Sx = 0, Sy = 0;
-#pragma unroll
-            for (int o = 0; o < 8; o++) {
-                T0 = q_add(T0, cur[o]);
-                Tz = q_add(Tz, (o & 1) ? cur[o] : q_neg(cur[o]));
-                const TC qs = q_sum(cur[o]);
-                Sx += (o & 4) ? qs : -qs;
-                Sy += (o & 2) ? qs : -qs;
-            }
             const int kx = mpk & 0xff, ky = (mpk >> 8) & 0xff, kz = mpk >> 16;
-            const TC jx = (TC)(2 * kx + 1), jy = (TC)(2 * ky + 1);
-            TC jz[VEC], jz2[VEC];
+            if constexpr (sizeof(TC) == 4) {
+                ffn m[7];
+                thread_moments(cur, (float)(2 * kx + 1), (float)(2 * ky + 1), (float)(2 * kz + 1), m);
+                const ffn tot = warp_reduce7_df(m, lane);
+                if ((lane & 3) == 0 && lane < 28) sm.red[q][cw][lane >> 2] = tot;
+            } else {
+                Q4 T0 = q_splat((TC)0), Tz = q_splat((TC)0);
+                TC Sx = 0, Sy = 0;
 #pragma unroll
-            for (int e = 0; e < VEC; e++) {
-                jz[e] = (TC)(2 * (kz + e) + 1);
-                jz2[e] = jz[e] * jz[e];
+                for (int o = 0; o < 8; o++) {
+                    T0 = q_add(T0, cur[o]);
+                    Tz = q_add(Tz, (o & 1) ? cur[o] : q_neg(cur[o]));
+                    const TC qs = q_sum(cur[o]);
+                    Sx += (o & 4) ? qs : -qs;
+                    Sy += (o & 2) ? qs : -qs;
+                }
+                const TC jx = (TC)(2 * kx + 1), jy = (TC)(2 * ky + 1);
+                TC jz[VEC], jz2[VEC];
+#pragma unroll
+                for (int e = 0; e < VEC; e++) {
+                    jz[e] = (TC)(2 * (kz + e) + 1);
+                    jz2[e] = jz[e] * jz[e];
+                }
+                TC m[7];
+                m[0] = q_sum(T0);
+                m[1] = jx * Sx;
+                m[2] = jy * Sy;
+                m[3] = q_sum(q_mul(q_make(jz), Tz));
+                m[4] = jx * jx * m[0];
+                m[5] = jy * jy * m[0];
+                m[6] = q_sum(q_mul(q_make(jz2), T0));
+                const TC tot = warp_reduce7<TC>(m, lane);
+                if ((lane & 3) == 0 && lane < 28) sm.red[q][cw][lane >> 2] = tot;
             }
-            TC m[7];
-            m[0] = q_sum(T0);
-            m[1] = jx * Sx;
-            m[2] = jy * Sy;
-            m[3] = q_sum(q_mul(q_make(jz), Tz));
-            m[4] = jx * jx * m[0];
-            m[5] = jy * jy * m[0];
-            m[6] = q_sum(q_mul(q_make(jz2), T0));
-            const TC tot = warp_reduce7<TC>(m, lane);
-            if ((lane & 3) == 0 && lane < 28) sm.red[q][cw][lane >> 2] = tot;
         }
         if (ctid == 0) sm.cellp[q] = cell;
         bar_arrive_n(BAR_P + q, nbar);

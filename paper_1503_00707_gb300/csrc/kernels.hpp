@@ -31,10 +31,12 @@ struct StepParams {
     const double *amag;      // [3][32] |xi| of the positive-side nodes m = 0..half-1
     const float *amag_f;     // same, rounded to FP32
     double dt, kn, dV;
+    double nu_coef;          // sqrt(8/pi) / Kn: the BGK frequency is nu_coef rho sqrt(T)
     double hv[3];            // velocity spacing per axis
     double *mom_out;         // [ncells][5]: rho, u[3], T of f*
+    double *res_out;         // [ncells][5] or null: sum_i psi_r Q_i dV of the BGK collision
+                             // term, psi = (1, xi, |xi|^2)
     int *status;
-    unsigned long long *counter;  // cell dispenser of the step kernel, zeroed before each launch
     cudaStream_t stream;
 };
 

@@ -49,6 +49,7 @@ int launch_hermite_project(const float *f, const double *mom, const double *amag
 // of the cells that used it.
 int launch_learned_apply(float *f, const double *mom, const float *o, const float *o_eq, const double *knl, double thr,
                          const double *amag, int64_t ncells, const int n[3], double dtkn, int32_t *used,
-                         int32_t *list, int *count, float *q_out, int *status, cudaStream_t s);
+                         int32_t *list, int *count, float *q_out, double dV, double *res, int *status,
+                         cudaStream_t s);
 
 }  // namespace dvm

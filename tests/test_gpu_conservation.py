@@ -1,0 +1,135 @@
+"""Conservation of the collision term on the GPU (Sec. 3.2, Eq. 6: the five
+correction coefficients make the discrete collision term conserve mass,
+momentum and energy), per cell, on the FP32 and BF16 storage paths.
+
+The library reports, per cell, sum_i psi_r q_i dV (psi = (1, xi, |xi|^2)) of
+the collision term its correction defines, formed in FP64-class arithmetic
+on the device (dvm_step_residual).  The bar is the one the oracle's own pins
+use: |sum_i psi_r q_i dV| <= 1e-12 sum_i |psi_r q_i| dV, with the scale
+taken from the oracle's q at the same state.  Every state here is far from
+equilibrium (30% random perturbation, or the bimodal box), so that the
+scale is of the order of the moments themselves.
+
+The FP32 evaluation of q at each node and the FP32 store are not part of the
+defined term; the moments of the stored f against those of f* show them at
+the FP32 level.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import paper_1503_00707_gb300 as D
+import workloads as W
+from tests.gpu_util import pair, rel_linf
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def gpu():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    from paper_1503_00707_gb300 import _build
+    _build.build()
+
+
+def _psi(xi):
+    return np.stack([np.ones(len(xi)), xi[:, 0], xi[:, 1], xi[:, 2], (xi * xi).sum(1)], 1)
+
+
+def _ratio(res, q, xi, dV, cells=None):
+    """max over cells and moments of |res| / sum_i |psi_r q_i| dV."""
+    ps = np.abs(_psi(xi))
+    if cells is not None:
+        res, q = res[cells], q[cells]
+    scale = np.abs(q) @ ps * dV
+    assert np.all(scale > 0)
+    return float(np.max(np.abs(res) / scale))
+
+
+def _perturbed(c, precision, collision=None, scale=0.3):
+    s, o = pair(c, precision=precision, collision=collision)
+    f0 = o.get_f() * W.random_f_perturbation(o.ncells, o.nv, scale=scale)
+    s.set_f(f0)
+    o.set_f(s.get_f())  # the same values (storage-rounded) on both sides
+    return s, o
+
+
+@pytest.mark.parametrize("name,prec", [("c2_sphere_m3", "f32"), ("c3_sphere_m5_small", "f32"),
+                                       ("c3_sphere_m5_small", "bf16")])
+def test_bgk_collision_term_conserves_per_cell(name, prec):
+    c = W.CONFIGS[name]
+    s, o = _perturbed(c, prec)
+    dt = o.dt_cfl(c["cfl"])
+    s.step(1, dt)
+    res = s.step_residual()
+    o.transport(dt)
+    q = o.bgk(dt, c["kn"], want_q=True)
+    assert _ratio(res, q, o.xi.reshape(-1, 3), o.dV) <= 1e-12
+    # the stored f (FP32 apply and store) keeps the moments of f* to FP32 level
+    r1, u1, T1 = s.moments()
+    rs, us, Ts = s.step_moments()
+    tol = 2e-6 if prec == "f32" else 2e-2
+    assert rel_linf(r1, rs) < tol and rel_linf(T1, Ts) < tol
+
+
+def test_entropic_bgk_collision_term_conserves_per_cell():
+    c = W.CONFIGS["c3_sphere_m5_small"]
+    s, o = _perturbed(c, "f32", collision=D.COLL_BGK_ENTROPIC)
+    dt = o.dt_cfl(c["cfl"])
+    s.step(1, dt)
+    res = s.step_residual()
+    o.transport(dt)
+    q = o.bgk_entropic(dt, c["kn"], want_q=True)
+    assert _ratio(res, q, o.xi.reshape(-1, 3), o.dV) <= 1e-12
+
+
+def test_bgk_fp64_collision_term_conserves_per_cell():
+    c = W.CONFIGS["c1_2d_bump"]
+    s, o = _perturbed(c, "f64")
+    dt = o.dt_cfl(c["cfl"])
+    s.step(1, dt)
+    res = s.step_residual()
+    o.transport(dt)
+    q = o.bgk(dt, c["kn"], want_q=True)
+    assert _ratio(res, q, o.xi.reshape(-1, 3), o.dV) <= 1e-12
+
+
+def test_hard_sphere_collision_term_conserves_per_cell():
+    c = dict(W.CONFIGS["c4_hs_bimodal"])
+    c.update(base_level=3, max_level=4)  # the bimodal box on a smaller tree
+    s, o = pair(c)
+    s.set_collision_tables(c["trials"], W.SEED)
+    o.hs_tables(c["trials"], W.SEED)
+    o.set_f(s.get_f())
+    dt = o.dt_cfl(c["cfl"]) / 16
+    s.step(1, dt)
+    res = s.step_residual()
+    o.transport(dt)
+    q, _, _ = o.hs_collide(dt, c["kn"], want=True)
+    assert _ratio(res, q, o.xi.reshape(-1, 3), o.dV) <= 1e-12
+
+
+def test_learned_collision_term_conserves_per_cell():
+    c = dict(W.CONFIGS["c4_hs_bimodal"])
+    c.update(base_level=2, max_level=3, coll=D.COLL_LEARNED)
+    s, o = pair(c, collision=D.COLL_LEARNED)
+    s.set_collision_tables(64, W.SEED)
+    o.hs_tables(64, W.SEED)
+    o.set_f(s.get_f())
+    knl = o.kn_local(c["kn"])
+    s.learned_configure(float(np.median(knl)))
+    a_o, _ = o.hermite_project()
+    e0 = np.zeros(64)
+    e0[0] = 1.0
+    oin = (-2.0 * (a_o - e0)).astype(np.float32)
+    r = s.learned_collide(2.5e-5, o=oin, want=("used", "q"))
+    res = s.step_residual()
+    used = r["used"].astype(bool)
+    assert 0 < used.sum() < s.ncells
+    # learned cells: the scale from the applied term itself
+    assert _ratio(res, r["q"].astype(np.float64), o.xi.reshape(-1, 3), o.dV, cells=used) <= 1e-12
+    # cells that fell back: the hard-sphere term of the same state
+    q, _, _ = o.hs_collide(0.0, c["kn"], want=True)
+    assert _ratio(res, q, o.xi.reshape(-1, 3), o.dV, cells=~used) <= 1e-12
