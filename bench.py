@@ -60,7 +60,9 @@ def parse():
                     help="skip the lattice Boltzmann leg (D3Q19 / D3Q27 sphere flow)")
     ap.add_argument("--lbm-only", action="store_true", help="run only the lattice Boltzmann leg")
     ap.add_argument("--lbm-steps", type=int, default=20)
-    ap.add_argument("--learned-steps", type=int, default=10)
+    ap.add_argument("--learned-steps", type=int, default=5)
+    ap.add_argument("--develop-steps", type=int, default=1500,
+                    help="BGK steps that develop the sphere flow before the learned-vs-plain leg")
     return ap.parse_args()
 
 
@@ -227,16 +229,35 @@ def init_params(seed):
     return np.concatenate(out).astype(np.float32)
 
 
+def _residual_ratio(res, rho, u, T):
+    """max over cells and moments of |sum_i psi_r q_i dV| / (rho^2 sqrt(T) L_r),
+    L = (1, |u| + sqrt(T) (x3), |u|^2 + 3 T): the residual against the natural
+    size of a collision term of the cell (q ~ rho^2 sqrt(T) M)."""
+    import numpy as np
+    sT = np.sqrt(T)
+    un = np.sqrt((u * u).sum(1))
+    L = np.stack([np.ones_like(T), un + sT, un + sT, un + sT, un * un + 3 * T], 1)
+    scale = (rho * rho * sT)[:, None] * L
+    ok = np.all(scale > 0, axis=1)
+    return float(np.max(np.abs(res[ok]) / scale[ok])) if ok.any() else None
+
+
 def learned_leg(args):
-    """The learned collision operator against the plain hard-sphere operator on
-    the same GPU: the network is trained on the GPU (the library's tcgen05
-    forward/backward and Adam) on (a, o) pairs that the hard-sphere operator
-    makes along the relaxation of the bimodal periodic box; then the Mach-3
-    sphere flow runs the same steps under each operator from the same state.
-    Reported: cell-updates/s of each (CUDA events, whole dvm_step calls:
-    transport, collision, fallback), the relative L-infinity error of rho, u
-    and T of the learned run against the plain run, and the cells that fell
-    back to the plain operator in the last step."""
+    """The learned collision operator against the plain hard-sphere operator
+    on the same GPU, from a developed flow.  The network is trained on the
+    GPU (the library's tcgen05 forward/backward and Adam) on (a, o) pairs
+    that the hard-sphere operator makes along the relaxation of the bimodal
+    periodic box.  The Mach-3 sphere flow is developed from the freestream
+    with BGK (the same mean free path) for --develop-steps steps at the CFL
+    step, until the bow shock stands ahead of the sphere; from that one
+    snapshot of f each operator runs --learned-steps steps.  Reported: the
+    snapshot's state (peak density over the freestream, cells with local
+    Kn above the gate), cell-updates/s of each operator (CUDA events over
+    whole dvm_step calls), the phase split (transport, learned kernels,
+    fallback hard-sphere kernels) from a separate timed pass, the relative
+    L-infinity error of rho, u and T of the learned run against the plain
+    run, the fallback count, and the largest conservation residual of the
+    applied collision term."""
     import numpy as np
     import torch
     import paper_1503_00707_gb300 as D
@@ -269,19 +290,38 @@ def learned_leg(args):
     net.close()
 
     cfg = W.CONFIGS[args.learned_config]
+    # the developed flow
+    stream = torch.cuda.Stream()
+    dev = D.solver_from_config(cfg, D.F32, D.COLL_BGK, stream=stream)
+    xyz, _ = dev.centres()
+    dev.init_maxwellian(*W.initial_state(cfg, xyz))
+    dtd = dev.dt_cfl(cfg["cfl"])
+    t0 = time.perf_counter()
+    dev.step(args.develop_steps, dtd)
+    dev_s = time.perf_counter() - t0
+    rho_d, u_d, T_d = dev.moments()
+    kn_d = dev.kn_local()
+    nbytes = dev.f_bytes()
+    snap = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
+    dev.download_f(snap.data_ptr(), nbytes)
+    torch.cuda.synchronize()
+    dev.close()
+    snapshot = {"develop_steps": args.develop_steps, "t": args.develop_steps * dtd, "seconds": dev_s,
+                "rho_max_over_freestream": float(rho_d.max() / cfg["fs_rho"]),
+                "T_max": float(T_d.max()), "cells_kn_above_gate": int((kn_d >= 0.05).sum())}
+    sys.stderr.write("learned leg: developed %d BGK steps (t = %.3g) in %.1f s, rho_max %.2f\n"
+                     % (args.develop_steps, args.develop_steps * dtd, dev_s, snapshot["rho_max_over_freestream"]))
+
     res = {}
     for name, coll in (("plain", D.COLL_HS), ("learned", D.COLL_LEARNED)):
-        stream = torch.cuda.Stream()
         s = D.solver_from_config(cfg, D.F32, coll, stream=stream)
-        xyz, _ = s.centres()
-        s.init_maxwellian(*W.initial_state(cfg, xyz))
+        s.upload_f(snap.data_ptr(), nbytes)
         s.set_collision_tables(cfg["trials"], seed)
         if coll == D.COLL_LEARNED:
             s.set_weights(weights)
             s.learned_configure(0.05)
         # explicit Euler on the collision term needs dt/Kn max(P B) <= 1
         dt = s.dt_cfl(cfg["cfl"]) / 10
-        s.step(1, dt)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
@@ -289,31 +329,48 @@ def learned_leg(args):
         e1.record(stream)
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1)
+        mom = s.moments()
+        resid = s.step_residual()
+        fb = s.learned_fallback_count() if coll == D.COLL_LEARNED else None
+        rs, us, Ts = s.step_moments()
+        ratio = _residual_ratio(resid, rs, us, Ts)
+        # the phase split, from one more step with phase events
+        s.set_timing(True)
+        s.step(1, dt)
+        split, _ = s.step_timing()
+        s.set_timing(False)
         sys.stderr.write("learned leg: %s %.1f ms per step on %d cells\n" % (name, ms / args.learned_steps, s.ncells))
         res[name] = {"value": s.ncells * s.nv * args.learned_steps / (ms / 1e3), "unit": UNIT,
-                     "ms_per_step": ms / args.learned_steps, "moments": s.moments(),
-                     "cells": s.ncells,
-                     "fallback": s.learned_fallback_count() if coll == D.COLL_LEARNED else None}
+                     "ms_per_step": ms / args.learned_steps, "moments": mom, "cells": s.ncells,
+                     "fallback": fb, "residual": ratio,
+                     "split_ms": {"transport": split[0], "collision": split[1], "fallback": split[2]}}
         s.close()
+    del snap
 
     def rel(a, b):
         return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
     (r1, u1, T1), (r2, u2, T2) = res["learned"]["moments"], res["plain"]["moments"]
     nc = res["plain"]["cells"]
-    return {
-        "workload": "%s: Mach-3 sphere flow, %d cells x 24^3 velocities, hard-sphere integral with %d "
-                    "trials per node (plain) vs the learned operator gated at Kn_loc < 0.05 with "
-                    "hard-sphere fallback, %d timed steps after 1, from the freestream"
-                    % (args.learned_config, nc, cfg["trials"], args.learned_steps),
-        "plain": {"value": res["plain"]["value"], "unit": UNIT, "ms_per_step": res["plain"]["ms_per_step"]},
-        "learned": {"value": res["learned"]["value"], "unit": UNIT,
-                    "ms_per_step": res["learned"]["ms_per_step"]},
+    out = {
+        "workload": "%s: Mach-3 sphere flow, %d cells x 24^3 velocities, developed with BGK for %d steps "
+                    "(bow shock standing), then %d steps of the hard-sphere integral with %d trials per node "
+                    "(plain) vs the learned operator gated at Kn_loc < 0.05 with hard-sphere fallback, "
+                    "from the same snapshot"
+                    % (args.learned_config, nc, args.develop_steps, args.learned_steps, cfg["trials"]),
+        "snapshot": snapshot,
         "speedup": res["learned"]["value"] / res["plain"]["value"],
         "field_rel_linf": {"rho": rel(r1, r2), "u": rel(u1, u2), "T": rel(T1, T2)},
         "fallback_cells": res["learned"]["fallback"], "cells": nc,
         "training": {"pairs": int(X.shape[0]), "epochs": 20, "loss_start": loss0, "loss_end": loss,
                      "seconds": train_s},
     }
+    for name in ("plain", "learned"):
+        r = res[name]
+        out[name] = {"value": r["value"], "unit": UNIT, "ms_per_step": r["ms_per_step"],
+                     "split_ms_per_step": r["split_ms"],
+                     "conservation_residual_max": r["residual"],
+                     "conservation_residual_scale": "rho^2 sqrt(T) (1, |u|+sqrt(T), |u|^2+3T) per cell"}
+    return out
 
 
 # ---------------------------------------------------------------- our arm
