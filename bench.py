@@ -12,8 +12,9 @@ and the SM clocks seen during the timed region.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
-For N > 1 (torchrun, one process per GPU) every rank steps its own replica of
-the workload; the ranks exchange nothing (value = all ranks' updates / the
+For N > 1 (torchrun, one process per GPU) the workload is split into N
+Morton ranges of equal work, one per rank, which exchange their upwind halo
+rows over NCCL before every step (value = all cells x |V| x steps over the
 slowest rank's time).
 """
 import argparse
@@ -60,6 +61,11 @@ def parse():
                     help="skip the lattice Boltzmann leg (D3Q19 / D3Q27 sphere flow)")
     ap.add_argument("--lbm-only", action="store_true", help="run only the lattice Boltzmann leg")
     ap.add_argument("--lbm-steps", type=int, default=20)
+    ap.add_argument("--no-hs", action="store_true", help="skip the hard-sphere box leg (c4_hs_bimodal)")
+    ap.add_argument("--hs-only", action="store_true", help="run only the hard-sphere box leg")
+    ap.add_argument("--hs-steps", type=int, default=3)
+    ap.add_argument("--no-bf16", action="store_true", help="skip the BF16-storage leg")
+    ap.add_argument("--bf16-steps", type=int, default=10)
     ap.add_argument("--learned-steps", type=int, default=5)
     ap.add_argument("--develop-steps", type=int, default=1500,
                     help="BGK steps that develop the sphere flow before the learned-vs-plain leg")
@@ -373,6 +379,149 @@ def learned_leg(args):
     return out
 
 
+# ---------------------------------------------------------------- hard-sphere box and BF16 legs
+def _sm_clock_hz():
+    """The SM clock for derived peaks: MEASURED_PEAKS.json's sm_max_mhz, else 2070 MHz."""
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        return float(json.load(open(p)).get("sm_max_mhz", 2070.0)) * 1e6
+    return 2070.0e6
+
+
+def oracle_field_errors(cfg_name, prec, steps, fetch):
+    """Per-field relative L-infinity error of the GPU path against the FP64
+    oracle on `cfg_name` after `steps` steps from the same seeded start (BGK).
+    fetch(solver) returns the GPU solver's moments after its steps."""
+    import oracle as O
+    import paper_1503_00707_gb300 as D
+    import numpy as np
+    c = W.CONFIGS[cfg_name]
+    s = D.solver_from_config(c, {"f32": D.F32, "bf16": D.BF16}[prec], D.COLL_BGK)
+    o = O.Problem(O.make_spec(c["dim"], c["base_level"], c["max_level"], c["pred"], c["c"], c["r"],
+                              c["beta"], c["solid"], c["bc"]), c["n"], c["lo"], c["hi"])
+    o.set_freestream(c["fs_rho"], c["fs_u"], c["fs_T"])
+    xyz, _ = s.centres()
+    init = W.initial_state(c, xyz)
+    s.init_maxwellian(*init)
+    o.init_maxwellian(*init)
+    dt = o.dt_cfl(c["cfl"])
+    s.step(steps, dt)
+    o.step(steps, dt, O.COLL_BGK, c["kn"])
+    (r1, u1, T1), (r2, u2, T2) = fetch(s), o.moments()
+    s.close()
+
+    def rel(a, b):
+        return float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
+    return {"rho": rel(r1, r2), "u": rel(u1, u2), "T": rel(T1, T2), "steps": steps, "cells": o.ncells,
+            "workload": cfg_name}
+
+
+def hs_leg(args):
+    """The hard-sphere collision step (Eqs. 3-6) on the bimodal periodic box
+    (16,584 cells x 16^3 velocities, 128 trials per node, Kn 0.02), FP32:
+    --hs-steps steps timed with CUDA events, then one more with phase events
+    for the split between transport and the collision kernels.  Roofline of
+    the collision: its shared-memory gathers, three 4-byte loads per trial
+    (f_gamma, f_l, f_m), against the derived peak of one load per lane per SM
+    clock (152 SMs x 32 lanes), over the collision phase's time (B, C and the
+    correction; an upper bound on the gather kernel's own time)."""
+    import numpy as np
+    import torch
+    import paper_1503_00707_gb300 as D
+    c = W.CONFIGS["c4_hs_bimodal"]
+    st = torch.cuda.Stream()
+    s = D.solver_from_config(c, D.F32, D.COLL_HS, stream=st)
+    xyz, _ = s.centres()
+    s.init_maxwellian(*W.initial_state(c, xyz))
+    s.set_collision_tables(c["trials"], W.SEED)
+    # the bimodal start has max(P B) ~ 290 in the far tails: a sixteenth of
+    # the CFL step keeps dt/Kn max(P B) below 1
+    dt = s.dt_cfl(c["cfl"]) / 16
+    s.step(2, dt)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    l0 = D.Solver.launch_count()
+    e0.record(st)
+    s.step(args.hs_steps, dt)
+    e1.record(st)
+    torch.cuda.synchronize()
+    launches = D.Solver.launch_count() - l0
+    ms = e0.elapsed_time(e1) / args.hs_steps
+    resid = s.step_residual()
+    rs, us, Ts = s.step_moments()
+    s.set_timing(True)
+    s.step(1, dt)
+    split, _ = s.step_timing()
+    s.set_timing(False)
+    nc, nv = s.ncells, s.nv
+    s.close()
+    gathers = 3.0 * nc * nv * c["trials"]
+    achieved = gathers / (split[1] / 1e3)
+    peak = 152 * 32 * _sm_clock_hz()
+    cpu = None
+    if not args.no_cpu_baseline:
+        import oracle as O
+        cs = dict(c)
+        cs.update(base_level=3, max_level=4)
+        o = O.Problem(O.make_spec(cs["dim"], cs["base_level"], cs["max_level"], cs["pred"], cs["c"], cs["r"],
+                                  cs["beta"], cs["solid"], cs["bc"]), cs["n"], cs["lo"], cs["hi"])
+        xo, _ = o.centres()
+        o.init_maxwellian(*W.initial_state(cs, xo))
+        o.hs_tables(cs["trials"], W.SEED)
+        t0 = time.perf_counter()
+        o.step(1, o.dt_cfl(cs["cfl"]) / 16, O.COLL_HS, cs["kn"])
+        el = time.perf_counter() - t0
+        cpu = {"value": o.ncells * o.nv / el, "unit": UNIT, "cores": O.threads(), "kind": "oracle",
+               "sample": "1 step of the same box on its level-3/4 tree (%d cells x %d velocities), FP64"
+                         % (o.ncells, o.nv)}
+    return {
+        "workload": "c4_hs_bimodal: 3D periodic octree level 4 + ball r=0.42 at level 5 (%d cells), 16^3 "
+                    "velocities on [-6,6]^3, hard-sphere integral with %d trials per node, Kn=0.02, seeded "
+                    "bimodal start, FP32" % (nc, c["trials"]),
+        "value": nc * nv / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "steps": args.hs_steps,
+        "split_ms_per_step": {"transport": split[0], "collision": split[1]},
+        "roofline": {"bound": "smem", "achieved": achieved, "peak": peak, "unit": "loads/s",
+                     "frac": achieved / peak, "peak_source": "derived: 152 SMs x 32 lanes x SM clock",
+                     "algorithmic_loads_per_update": 3 * c["trials"], "traffic": None},
+        "conservation_residual_max": _residual_ratio(resid, rs, us, Ts),
+        "gpu_launches_per_step": launches / args.hs_steps, "cpu_baseline": cpu,
+    }
+
+
+def bf16_leg(args):
+    """The Mach-5 workload with BF16 storage of f (FP32 arithmetic, FP64-class
+    moments and correction): --bf16-steps steps timed with CUDA events,
+    4 algorithmic bytes per update; and the per-field error against the FP64
+    oracle after two steps on the 17.7k-cell tree of the same flow."""
+    import torch
+    import paper_1503_00707_gb300 as D
+    cfg = W.CONFIGS[args.config]
+    st = torch.cuda.Stream()
+    s = D.solver_from_config(cfg, D.BF16, D.COLL_BGK, stream=st)
+    xyz, _ = s.centres()
+    s.init_maxwellian(*W.initial_state(cfg, xyz))
+    dt = s.dt_cfl(cfg["cfl"])
+    s.step(args.warmup, dt)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    s.step(args.bf16_steps, dt)
+    e1.record(st)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.bf16_steps
+    nc, nv = s.ncells, s.nv
+    s.close()
+    peak, peak_kind = _peaks()
+    achieved = 4.0 * nc * nv / (ms / 1e3) / 1e9
+    out = {"workload": workload_desc(args.config, cfg, nc, nv, "bf16"), "value": nc * nv / (ms / 1e3),
+           "unit": UNIT, "ms_per_step": ms, "steps": args.bf16_steps,
+           "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                        "peak_source": peak_kind, "algorithmic_bytes_per_update": 4, "traffic": None}}
+    if not args.no_cpu_baseline:
+        out["field_rel_linf_vs_oracle"] = oracle_field_errors(CPU_SAMPLE_CONFIG, "bf16", 2, lambda q: q.moments())
+    return out
+
+
 # ---------------------------------------------------------------- our arm
 def job_rate(ms_local, world, updates_per_rank):
     """Whole-job rate of N ranks that each processed updates_per_rank in their
@@ -481,6 +630,77 @@ def lbm_leg(args, stream=None):
     return out
 
 
+def run_sharded(args, cfg, prec, rank, world, cpu):
+    """N > 1: the workload split into N Morton ranges of equal work, one per
+    rank (GPU); before every step each rank exchanges its upwind halo rows
+    with its neighbours over NCCL (the library packs and unpacks the rows);
+    dt is the minimum over ranks.  Timed: K whole steps (exchange and step)
+    per rank with CUDA events between barriers; value = all cells x |V| x K
+    over the slowest rank's time (the total work is fixed: strong scaling)."""
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    import paper_1503_00707_gb300 as D
+    from paper_1503_00707_gb300.sharded import ShardedSolver
+    coll = D.COLL_BGK_ENTROPIC if args.collision == "entropic" else D.COLL_BGK
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        sh = ShardedSolver(cfg, prec, coll)
+        xyz, _ = sh.r.centres()
+        # the seeded start of the whole workload, sliced to the owned cells
+        full = D.Solver(prec, coll, cfg["kn"])
+        full.build_tree(D.tree_spec(cfg["dim"], cfg["base_level"], cfg["max_level"], cfg["pred"], cfg["c"], cfg["r"],
+                                    cfg["beta"], cfg["solid"], cfg["bc"]))
+        xyz_all, _ = full.centres()
+        full.close()
+        init = W.initial_state(cfg, xyz_all)
+        sh.r.init_maxwellian(*[np.asarray(a)[sh.r.c0:sh.r.c1] for a in init])
+        dt = sh.dt_cfl(cfg["cfl"])
+        sh.step(args.warmup, dt)
+        torch.cuda.synchronize()
+        dist.barrier()
+        clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", 0)))
+        clocks.start()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        l0 = D.Solver.launch_count()
+        e0.record(stream)
+        sh.step(args.steps, dt)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        launches = D.Solver.launch_count() - l0
+        ms = e0.elapsed_time(e1)
+        clk = clocks.stop()
+        ncells_global, nv = sh.r.ncells_global, sh.nv
+        ms, _ = job_rate(ms, world, 0)
+        value = ncells_global * nv * args.steps / (ms / 1e3)
+        tot = sh.totals()
+        sh.close()
+    if rank == 0:
+        peak, peak_kind = _peaks()
+        bpu = {D.F32: 8, D.BF16: 4}[prec]
+        achieved = bpu * ncells_global * nv / (ms / 1e3 / args.steps) / 1e9 / world
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "strong",
+            "vs_baseline": None, "dtype": {D.F32: "f32", D.BF16: "bf16"}[prec], "data": "synthetic",
+            "config": {"workload": workload_desc(args.config, cfg, ncells_global, nv, args.precision, args.collision),
+                       "cells": ncells_global, "velocities": nv, "storage": args.precision,
+                       "parallelism": "%d Morton ranges of equal work, upwind halo exchanged over NCCL every step"
+                                      % world,
+                       "l2": "inputs larger than L2 (f is %.1f GB)" % (ncells_global * nv * bpu / 2 / 1e9)},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "per": "GPU (mean over ranks)", "traffic": None,
+                         "peak_source": peak_kind, "algorithmic_bytes_per_update": bpu},
+            "cpu_baseline": cpu, "gpu_launches": launches, "clocks": clk,
+            "e2e": {"value": None, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0,
+                    "skipped": "the sharded run keeps f resident on the ranks"},
+            "totals": [float(x) for x in tot],
+        }
+        print(json.dumps(line), flush=True)
+    dist.destroy_process_group()
+    return 0
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -511,6 +731,8 @@ def run_ours(args):
 
     cfg = W.CONFIGS[args.config]
     prec = {"f32": D.F32, "bf16": D.BF16}[args.precision]
+    if world > 1:
+        return run_sharded(args, cfg, prec, rank, world, cpu)
     stream = torch.cuda.Stream()
     coll = D.COLL_BGK_ENTROPIC if args.collision == "entropic" else D.COLL_BGK
     s = D.solver_from_config(cfg, prec, coll, stream=stream)
@@ -577,9 +799,18 @@ def run_ours(args):
 
     f_gb = s.f_bytes() / 1e9
     s.close()
+    field_err = None
+    if rank == 0 and not args.no_cpu_baseline:
+        field_err = oracle_field_errors(CPU_SAMPLE_CONFIG, args.precision, 2, lambda q: q.moments())
     lbm = None
     if rank == 0 and not args.no_lbm:
         lbm = lbm_leg(args)
+    hs = None
+    if rank == 0 and not args.no_hs:
+        hs = hs_leg(args)
+    bf16 = None
+    if rank == 0 and not args.no_bf16 and args.precision == "f32":
+        bf16 = bf16_leg(args)
     learned = None
     if rank == 0 and not args.no_learned:
         learned = learned_leg(args)
@@ -594,7 +825,8 @@ def run_ours(args):
                        "storage": args.precision, "parallelism": "replicas" if world > 1 else "single GPU",
                        "l2": "inputs larger than L2 (f is %.1f GB)" % f_gb},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
-            "learned_vs_plain": learned, "lbm": lbm,
+            "field_rel_linf_vs_oracle": field_err,
+            "learned_vs_plain": learned, "lbm": lbm, "hs_box": hs, "bf16": bf16,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -612,6 +844,13 @@ def main():
         _build.build()
         torch.cuda.set_device(0)
         print(json.dumps({"lbm": lbm_leg(args)}), flush=True)
+        return 0
+    if args.hs_only:
+        import torch
+        from paper_1503_00707_gb300 import _build
+        _build.build()
+        torch.cuda.set_device(0)
+        print(json.dumps({"hs": hs_leg(args)}), flush=True)
         return 0
     if args.learned_only:
         import torch

@@ -32,9 +32,12 @@
  *     DVM_ETIMEOUT.  The step kernels' CTA-internal barriers (__syncthreads,
  *     and the named barriers between the transport and solver warps of
  *     dvm_step) carry no time bound, as no hardware barrier can; they
- *     complete because every warp of a CTA walks the same finite list of
- *     cells: CTA b of a grid of G takes cells b, b + G, b + 2G, ..., a list
- *     that every warp computes from the launch shape alone.
+ *     complete because both sides of every barrier act on the same record:
+ *     a CTA's cells come from a global counter into slots that alternate
+ *     between two solver warps, each warp takes its slots' cells in slot
+ *     order (so a parity's slots, once empty, stay empty), and the barriers
+ *     of a slot are used, on both sides, exactly when that slot holds a
+ *     cell.
  *   - A context is not thread-safe; use one context per host thread.
  *
  * Velocity ordering (Sec. 3.1 step 1): the Nv = nx*ny*nz nodes are stored as
@@ -92,7 +95,9 @@ typedef struct {
     int precision;   /* storage of f: DVM_F64 (FP64 arithmetic throughout), DVM_F32 or
                         DVM_BF16 (FP32 transport and collision arithmetic; the moment
                         sums, the Eq. 6 correction systems and their solves in
-                        double-float, an FP64-class arithmetic of about 48 bits) */
+                        FP64-class arithmetic: double-float pairs of about 48 bits
+                        in the step kernel, FP64 in the hard-sphere and learned
+                        corrections) */
     int collision;   /* DVM_COLL_*                                                  */
     double kn;       /* Knudsen number of Eq. 1                                     */
 } dvm_config;
@@ -429,6 +434,72 @@ int dvm_partition_weighted(const dvm_ctx *ctx, int nparts, const double *weights
  * (about twice the f of the mesh).  Errors as dvm_step; DVM_ENOTIMPL for the
  * hard-sphere and learned collisions. */
 int dvm_step_partitioned(dvm_ctx *ctx, int nparts, int nsteps, double dt);
+
+/* ---- one rank of the Morton-range partition (Sec. 3.3) ---------------------
+ * The multi-GPU form of the step.  nparts processes (one per GPU) each own a
+ * contiguous range of the Morton-ordered cells (the ranges of
+ * dvm_partition_info) and, before every step, take the current rows of their
+ * upwind halo from the ranks that own them.  A rank's device holds only its
+ * own cells, then its halo (ascending global index), then the inflow ghost:
+ * inner cells first, then ghost cells, as in Sec. 3.3.  The library gives the
+ * exchange plan and packs and unpacks the rows; moving the packed rows
+ * between processes (NCCL send/recv or any other transport) and the two
+ * global reductions (the minimum dt over ranks, the sum of the conserved
+ * totals) are the caller's.  Every rank builds the tree from the same spec
+ * (the build is deterministic).  Collisions: DVM_COLL_NONE, DVM_COLL_BGK,
+ * DVM_COLL_BGK_ENTROPIC (DVM_ENOTIMPL otherwise).  Host arrays of cells
+ * (centres, initial state, moments, f) cover the owned cells, in order. */
+typedef struct dvm_rank dvm_rank;
+
+/* Build the tree and the plan of rank `part` of nparts (host work, no device). */
+int dvm_rank_create(dvm_rank **out, const dvm_config *cfg, const dvm_tree_spec *spec, int nparts, int part);
+void dvm_rank_destroy(dvm_rank *r);
+const char *dvm_rank_last_error(const dvm_rank *r);
+
+/* Total cells of the tree, the owned range [c0, c1) and the halo size. */
+int dvm_rank_info(const dvm_rank *r, int64_t *ncells_global, int64_t *c0, int64_t *c1, int64_t *nhalo);
+
+/* The exchange with rank `peer`: *nsend owned cells that peer's stencils
+ * read and *nrecv halo cells that peer owns, as ascending global cell
+ * indices (arrays may be NULL for a count query).  The packed rows of
+ * dvm_rank_pack / dvm_rank_unpack come in these orders, so the buffer one
+ * rank sends to a peer is the one that peer unpacks. */
+int dvm_rank_plan(const dvm_rank *r, int peer, int64_t *nsend, int64_t *send_cells, int64_t *nrecv,
+                  int64_t *recv_cells);
+
+int dvm_rank_set_stream(dvm_rank *r, void *stream);
+
+/* As dvm_set_velocity_grid: allocates the rank's f (owned + halo + 1 rows,
+ * two buffers) and its stencils on the current device. */
+int dvm_rank_set_velocity_grid(dvm_rank *r, const int n[3], const double lo[3], const double hi[3]);
+int dvm_rank_set_freestream(dvm_rank *r, double rho, const double u[3], double T);
+int dvm_rank_cell_centres(const dvm_rank *r, double *xyz, double *h);
+int dvm_rank_init_maxwellian(dvm_rank *r, int nmix, const double *w, const double *rho, const double *u,
+                             const double *T);
+
+/* Bytes of one packed row (nv values of the storage type). */
+int dvm_rank_row_bytes(const dvm_rank *r, int64_t *bytes);
+
+/* Queue on the rank's stream: pack the rows for `peer` into dev_buf (device,
+ * nsend rows), or unpack the nrecv rows in dev_buf into the halo.  The halo
+ * of the current f must be unpacked before each dvm_rank_step. */
+int dvm_rank_pack(dvm_rank *r, int peer, void *dev_buf);
+int dvm_rank_unpack(dvm_rank *r, int peer, const void *dev_buf);
+
+/* The CFL step over the owned cells (the global step is the minimum over
+ * ranks). */
+int dvm_rank_dt_cfl(const dvm_rank *r, double cfl, double *dt);
+
+/* One step of the owned cells (transport, moments, collision), reading the
+ * halo rows as they stand.  Synchronises the stream; errors as dvm_step. */
+int dvm_rank_step(dvm_rank *r, double dt);
+
+int dvm_rank_moments(dvm_rank *r, double *rho, double *u, double *T);
+int dvm_rank_get_f(dvm_rank *r, double *f, int64_t count);
+
+/* Conserved totals of the owned cells: sum_j V_j (rho, rho u, rho (|u|^2 +
+ * 3 T))_j, that is sum_j V_j sum_i psi_r f_ij dV with psi = (1, xi, |xi|^2). */
+int dvm_rank_totals(dvm_rank *r, double *out);
 
 /* Size in bytes of the fixed device scratch used by dvm_hs_collide_noalloc. */
 #define DVM_HS_NOALLOC_SCRATCH_BYTES (64u << 20)

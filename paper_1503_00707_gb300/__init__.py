@@ -43,7 +43,11 @@ EXPORTS = [
     "dvm_lbm_dt_cfl", "dvm_lbm_step", "dvm_lbm_moments", "dvm_lbm_get_codes",
     "dvm_coarsen", "dvm_coarsen_project", "dvm_kn_local", "dvm_flag_kinetic",
     "dvm_partition_weighted", "dvm_lbm_lattice", "dvm_step_residual", "dvm_set_timing",
-    "dvm_step_timing",
+    "dvm_step_timing", "dvm_rank_create", "dvm_rank_destroy", "dvm_rank_last_error", "dvm_rank_info",
+    "dvm_rank_plan", "dvm_rank_set_stream", "dvm_rank_set_velocity_grid", "dvm_rank_set_freestream",
+    "dvm_rank_cell_centres", "dvm_rank_init_maxwellian", "dvm_rank_row_bytes", "dvm_rank_pack",
+    "dvm_rank_unpack", "dvm_rank_dt_cfl", "dvm_rank_step", "dvm_rank_moments", "dvm_rank_get_f",
+    "dvm_rank_totals",
 ]
 MLP_NPARAM = 164672
 HS_NOALLOC_SCRATCH_BYTES = 64 << 20
@@ -152,6 +156,24 @@ def lib():
             "dvm_step_residual": [P, P],
             "dvm_set_timing": [P, C.c_int],
             "dvm_step_timing": [P, P, P],
+            "dvm_rank_create": [C.POINTER(P), C.POINTER(Config), C.POINTER(TreeSpec), C.c_int, C.c_int],
+            "dvm_rank_destroy": [P],
+            "dvm_rank_last_error": [P],
+            "dvm_rank_info": [P, P, P, P, P],
+            "dvm_rank_plan": [P, C.c_int, P, P, P, P],
+            "dvm_rank_set_stream": [P, P],
+            "dvm_rank_set_velocity_grid": [P, P, P, P],
+            "dvm_rank_set_freestream": [P, d, P, d],
+            "dvm_rank_cell_centres": [P, P, P],
+            "dvm_rank_init_maxwellian": [P, C.c_int, P, P, P, P],
+            "dvm_rank_row_bytes": [P, P],
+            "dvm_rank_pack": [P, C.c_int, P],
+            "dvm_rank_unpack": [P, C.c_int, P],
+            "dvm_rank_dt_cfl": [P, d, P],
+            "dvm_rank_step": [P, d],
+            "dvm_rank_moments": [P, P, P, P],
+            "dvm_rank_get_f": [P, P, i64],
+            "dvm_rank_totals": [P, P],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -159,6 +181,8 @@ def lib():
             fn.restype = C.c_int
         L.dvm_destroy.restype = None
         L.dvm_last_error.restype = C.c_char_p
+        L.dvm_rank_destroy.restype = None
+        L.dvm_rank_last_error.restype = C.c_char_p
         _lib = L
     return _lib
 
@@ -535,6 +559,109 @@ class Solver:
         if rc:
             raise DvmError(rc, "dvm_launch_count")
         return n.value
+
+
+class Rank:
+    """One rank of the Morton-range partition (dvm_rank_*): the rank's own
+    cells, its halo and the inflow ghost on the current device.  Host arrays
+    of cells cover the owned cells in order."""
+
+    def __init__(self, cfg, precision, collision, nparts, part, kn=None, device=True, stream=None):
+        prec = {"f64": F64, "f32": F32, "bf16": BF16}[precision] if isinstance(precision, str) else precision
+        L = lib()
+        h = C.c_void_p()
+        conf = Config(prec, collision, cfg["kn"] if kn is None else kn)
+        spec = tree_spec(cfg["dim"], cfg["base_level"], cfg["max_level"], cfg["pred"], cfg["c"], cfg["r"],
+                         cfg["beta"], cfg["solid"], cfg["bc"])
+        rc = L.dvm_rank_create(C.byref(h), C.byref(conf), C.byref(spec), int(nparts), int(part))
+        if rc:
+            raise DvmError(rc, "dvm_rank_create failed")
+        self._h = h
+        self.nparts, self.part = nparts, part
+        v = [C.c_int64() for _ in range(4)]
+        self._chk(L.dvm_rank_info(h, *[C.byref(x) for x in v]))
+        self.ncells_global, self.c0, self.c1, self.nhalo = [x.value for x in v]
+        self.ncells = self.c1 - self.c0
+        if stream is not None:
+            self._chk(L.dvm_rank_set_stream(h, C.c_void_p(getattr(stream, "cuda_stream", stream) or 0)))
+        if device:
+            n = np.ascontiguousarray(cfg["n"], dtype=np.int32)
+            lo = np.ascontiguousarray(cfg["lo"], dtype=np.float64)
+            hi = np.ascontiguousarray(cfg["hi"], dtype=np.float64)
+            self._chk(L.dvm_rank_set_velocity_grid(h, _p(n), _p(lo), _p(hi)))
+            u = np.ascontiguousarray(cfg["fs_u"], dtype=np.float64)
+            self._chk(L.dvm_rank_set_freestream(h, float(cfg["fs_rho"]), _p(u), float(cfg["fs_T"])))
+            self.nv = int(n[0]) * int(n[1]) * int(n[2])
+            rb = C.c_int64()
+            self._chk(L.dvm_rank_row_bytes(h, C.byref(rb)))
+            self.row_bytes = rb.value
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().dvm_rank_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _chk(self, rc):
+        if rc:
+            msg = lib().dvm_rank_last_error(self._h)
+            raise DvmError(rc, msg.decode() if msg else "")
+
+    def plan(self, peer):
+        """(send_cells, recv_cells): ascending global indices exchanged with `peer`."""
+        ns, nr = C.c_int64(), C.c_int64()
+        self._chk(lib().dvm_rank_plan(self._h, int(peer), C.byref(ns), None, C.byref(nr), None))
+        s, r = np.zeros(ns.value, np.int64), np.zeros(nr.value, np.int64)
+        self._chk(lib().dvm_rank_plan(self._h, int(peer), None, _p(s), None, _p(r)))
+        return s, r
+
+    def centres(self):
+        xyz, h = np.zeros((self.ncells, 3)), np.zeros(self.ncells)
+        self._chk(lib().dvm_rank_cell_centres(self._h, _p(xyz), _p(h)))
+        return xyz, h
+
+    def init_maxwellian(self, w, rho, u, T):
+        nc = self.ncells
+        w = np.ascontiguousarray(np.asarray(w, np.float64).reshape(nc, -1))
+        k = w.shape[1]
+        rho = np.ascontiguousarray(np.asarray(rho, np.float64).reshape(nc, k))
+        u = np.ascontiguousarray(np.asarray(u, np.float64).reshape(nc, k, 3))
+        T = np.ascontiguousarray(np.asarray(T, np.float64).reshape(nc, k))
+        self._chk(lib().dvm_rank_init_maxwellian(self._h, k, _p(w), _p(rho), _p(u), _p(T)))
+
+    def pack(self, peer, dev_ptr):
+        self._chk(lib().dvm_rank_pack(self._h, int(peer), C.c_void_p(dev_ptr)))
+
+    def unpack(self, peer, dev_ptr):
+        self._chk(lib().dvm_rank_unpack(self._h, int(peer), C.c_void_p(dev_ptr)))
+
+    def dt_cfl(self, cfl):
+        dt = C.c_double()
+        self._chk(lib().dvm_rank_dt_cfl(self._h, float(cfl), C.byref(dt)))
+        return dt.value
+
+    def step(self, dt):
+        self._chk(lib().dvm_rank_step(self._h, float(dt)))
+
+    def moments(self):
+        rho, u, T = np.zeros(self.ncells), np.zeros((self.ncells, 3)), np.zeros(self.ncells)
+        self._chk(lib().dvm_rank_moments(self._h, _p(rho), _p(u), _p(T)))
+        return rho, u, T
+
+    def get_f(self):
+        f = np.zeros((self.ncells, self.nv))
+        self._chk(lib().dvm_rank_get_f(self._h, _p(f), f.size))
+        return f
+
+    def totals(self):
+        out = np.zeros(5)
+        self._chk(lib().dvm_rank_totals(self._h, _p(out)))
+        return out
 
 
 def lbm_lattice(lattice):

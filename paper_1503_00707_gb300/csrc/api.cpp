@@ -49,14 +49,19 @@ struct dvm_ctx {
     double *d_xi = nullptr;
     double *d_mom = nullptr;     // step moments [ncells][5]
     double *d_mom2 = nullptr;    // moments of stored f
-    double *d_res = nullptr;     // conservation residual of the last step's collision term [ncells][5]
+    // conservation residual of the last step's collision term, [ncells][5]:
+    // FP64 sums in psi = (1, xi, |xi|^2) of q (hard sphere, learned), or
+    // double-float pairs of the centred-basis moments of M~ - f* (BGK)
+    double *d_res = nullptr;
     bool have_res = false;
+    bool res_pairs = false;
     // phase timing of dvm_step (dvm_set_timing): events and running totals
     bool timing = false;
     cudaEvent_t tev[4] = {nullptr, nullptr, nullptr, nullptr};
     double tms[3] = {0.0, 0.0, 0.0};
     int64_t tsteps = 0;
     int *d_status = nullptr;
+    unsigned long long *d_counter = nullptr;
     bool have_step_moments = false;
     bool mesh_on_device = false;
     dvm::HsTables hs;
@@ -206,6 +211,8 @@ int ensure_device(dvm_ctx *c)
         c->d_status = nullptr;
         return fail(c, DVM_ECUDA, "device status word allocation failed");
     }
+    // the step kernel's cell dispenser shares the allocation
+    c->d_counter = reinterpret_cast<unsigned long long *>(c->d_status + 2);
     return DVM_OK;
 }
 
@@ -951,10 +958,10 @@ int dvm_step(dvm_ctx *c, int nsteps, double dt)
     p.amag_f = c->d_amag_f;
     p.dt = dt;
     p.kn = c->cfg.kn;
-    p.nu_coef = 1.5957691216057308 / c->cfg.kn;
     p.dV = c->dV;
     p.mom_out = c->d_mom;
     p.status = c->d_status;
+    p.counter = c->d_counter;
     p.stream = c->stream;
     // the BGK step kernel writes the residual of its collision term; the
     // hard-sphere and learned updates write theirs after the transport launch
@@ -971,12 +978,18 @@ int dvm_step(dvm_ctx *c, int nsteps, double dt)
     for (int s = 0; s < nsteps; s++) {
         p.f_in = c->d_f[c->cur];
         p.f_out = c->d_f[1 - c->cur];
-        p.res_out = bgk ? c->d_res : nullptr;
+        p.res_out = nullptr;
+        p.res_phi = bgk ? reinterpret_cast<float2 *>(c->d_res) : nullptr;
         if (c->timing) cudaEventRecord(c->tev[0], c->stream);
+        if (cudaMemsetAsync(c->d_counter, 0, sizeof(unsigned long long), c->stream) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(c, DVM_ECUDA, "counter reset failed");
+        }
         int rc = dvm::launch_step(p);
         if (rc) return fail(c, rc, rc == DVM_ENOTIMPL ? "velocity grid too large for the step kernel" : "step launch failed");
         if (c->timing) cudaEventRecord(c->tev[1], c->stream);
         p.res_out = c->d_res;
+        p.res_phi = nullptr;
         if (c->cfg.collision == DVM_COLL_HS) {
             rc = dvm::launch_hs_collide(c->hs, p, c->d_f[1 - c->cur], c->cfg.kn, dt);
             if (rc) return fail(c, rc, "hard-sphere collision launch failed");
@@ -1000,7 +1013,10 @@ int dvm_step(dvm_ctx *c, int nsteps, double dt)
         c->cur = 1 - c->cur;
     }
     c->have_step_moments = nsteps > 0 || c->have_step_moments;
-    if (nsteps > 0) c->have_res = c->cfg.collision != DVM_COLL_NONE;
+    if (nsteps > 0) {
+        c->have_res = c->cfg.collision != DVM_COLL_NONE;
+        c->res_pairs = c->cfg.collision == DVM_COLL_BGK || c->cfg.collision == DVM_COLL_BGK_ENTROPIC;
+    }
     int st = 0;
     int rc = cuda_check(c, cudaMemcpyAsync(&st, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "read status");
     if (!rc) rc = cuda_check(c, cudaStreamSynchronize(c->stream), "step");
@@ -1167,9 +1183,9 @@ int dvm_step_partitioned(dvm_ctx *c, int nparts, int nsteps, double dt)
     base.amag_f = c->d_amag_f;
     base.dt = dt;
     base.kn = c->cfg.kn;
-    base.nu_coef = 1.5957691216057308 / c->cfg.kn;
     base.dV = c->dV;
     base.status = c->d_status;
+    base.counter = c->d_counter;
     base.stream = c->stream;
     for (int s = 0; s < nsteps && !rc; s++) {
         const int b = s & 1;
@@ -1187,7 +1203,8 @@ int dvm_step_partitioned(dvm_ctx *c, int nparts, int nsteps, double dt)
             q.st_cnt = c->d_cnt + pt.c0 * 8;
             q.inv_h = static_cast<const char *>(c->d_invh) + pt.c0 * tcs;
             q.mom_out = dev[p].mom;
-            rc = dvm::launch_step(q);
+            rc = cuda_check(c, cudaMemsetAsync(c->d_counter, 0, sizeof(unsigned long long), c->stream), "counter reset");
+            if (!rc) rc = dvm::launch_step(q);
             if (rc && rc != DVM_ECUDA) rc = fail(c, rc, "step launch failed");
         }
     }
@@ -1341,7 +1358,35 @@ int dvm_step_residual(dvm_ctx *c, double *res)
     int rc = cuda_check(c, cudaMemcpyAsync(res, c->d_res, (size_t)nc * 5 * sizeof(double), cudaMemcpyDeviceToHost,
                                            c->stream), "copy residual");
     if (!rc) rc = cuda_check(c, cudaStreamSynchronize(c->stream), "residual");
-    return rc;
+    if (rc || !c->res_pairs) return rc;
+    // BGK: the kernel left sum_i phi_r (M~ - f*)_i dV, phi = (1, c, |c|^2 - 3),
+    // c = (xi - u)/sqrt(T), as double-float pairs; with the step moments the
+    // host takes it to psi = (1, xi, |xi|^2) (xi = sqrt(T) c + u) and to the
+    // collision term q = nu (M~ - f*), nu = sqrt(8/pi) rho sqrt(T) / Kn
+    std::vector<double> mom(5 * (size_t)nc);
+    rc = cuda_check(c, cudaMemcpyAsync(mom.data(), c->d_mom, mom.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                                       c->stream), "copy moments");
+    if (!rc) rc = cuda_check(c, cudaStreamSynchronize(c->stream), "residual");
+    if (rc) return rc;
+    std::vector<float> pr(10 * (size_t)nc);
+    std::memcpy(pr.data(), res, pr.size() * sizeof(float));
+    for (int64_t q = 0; q < nc; q++) {
+        double r[5];
+        for (int k = 0; k < 5; k++) r[k] = (double)pr[10 * q + 2 * k] + (double)pr[10 * q + 2 * k + 1];
+        const double rho = mom[5 * q], T = mom[5 * q + 4], sT = std::sqrt(T);
+        const double u[3] = {mom[5 * q + 1], mom[5 * q + 2], mom[5 * q + 3]};
+        const double nu = 1.5957691216057308 * rho * sT / c->cfg.kn;
+        double *o = res + 5 * q;
+        o[0] = nu * r[0];
+        double dot = 0.0, uu = 0.0;
+        for (int d = 0; d < 3; d++) {
+            o[1 + d] = nu * (sT * r[1 + d] + u[d] * r[0]);
+            dot += u[d] * r[1 + d];
+            uu += u[d] * u[d];
+        }
+        o[4] = nu * (T * (r[4] + 3.0 * r[0]) + 2.0 * sT * dot + uu * r[0]);
+    }
+    return DVM_OK;
 }
 
 int dvm_hs_collide_noalloc(dvm_ctx *c, float *f, int64_t ncells, double dt)
@@ -1552,6 +1597,7 @@ int dvm_learned_collide(dvm_ctx *c, double dt, const float *o_in, double *knl, f
     if (!rc && q) rc = cuda_check(c, cudaMemcpy(q, dq.p, (size_t)nc * c->nv * 4, cudaMemcpyDeviceToHost), "copy q");
     c->have_step_moments = false;
     c->have_res = true;
+    c->res_pairs = false;
     return rc;
 }
 

@@ -68,6 +68,72 @@ int64_t korobov_multiplier(int64_t M)
     return best;
 }
 
+// Device order of the trials.  The collision kernel gives each node's
+// trials to trials/32 lanes (lane t of the node takes trials 32 t .. 32 t + 31,
+// one per slot) and a warp covers 32 / (trials/32) consecutive nodes; at each
+// slot its lanes gather f at three node indices (gamma, l, m) from a
+// shared-memory tile, and every distinct index in the same bank (index mod 32)
+// costs one more shared-memory wavefront.  The sums B and C over a node's
+// trials do not depend on their order, so each node's trials are ordered
+// greedily, slot by slot: each lane takes, from its node's remaining trials,
+// the one that adds the fewest distinct indices to banks already in use at
+// this slot (over the three gathers).  idx/b: node-major tables as built;
+// out_idx/out_b: the same entries in device order.
+static void order_for_banks(const std::vector<uint32_t> &idx, const std::vector<float> &b, int nv, int M,
+                            std::vector<uint32_t> &out_idx, std::vector<float> &out_b)
+{
+    const int HEt = 32, tpn = M / HEt, K = 32 / tpn;  // lanes per node, nodes per warp
+    out_idx.assign(idx.size(), 0u);
+    out_b.assign(b.size(), 0.0f);
+    std::vector<int> pool;
+    std::vector<uint8_t> used((size_t)K * M);
+    // per gather, per bank: the distinct indices taken at the current slot
+    int cnt[3][32];
+    int addr[3][32][32];
+    for (int g0 = 0; g0 < nv; g0 += K) {
+        const int kn = std::min(K, nv - g0);
+        std::fill(used.begin(), used.end(), 0);
+        for (int e = 0; e < HEt; e++) {
+            for (int g = 0; g < 3; g++)
+                for (int k = 0; k < 32; k++) cnt[g][k] = 0;
+            for (int lane = 0; lane < kn * tpn; lane++) {
+                const int nl = lane / tpn, t = lane % tpn, node = g0 + nl;
+                const size_t base = (size_t)node * M;
+                int best = -1, bestc = 1 << 30;
+                for (int k = 0; k < M && bestc > 0; k++) {
+                    if (used[(size_t)nl * M + k]) continue;
+                    const uint32_t w0 = idx[2 * (base + k)], w1 = idx[2 * (base + k) + 1];
+                    const int a[3] = {(int)(w0 & 0xffffu), (int)(w0 >> 16), (int)w1};
+                    int c = 0;
+                    for (int g = 0; g < 3; g++) {
+                        const int bk = a[g] & 31;
+                        bool seen = false;
+                        for (int q = 0; q < cnt[g][bk]; q++) seen = seen || addr[g][bk][q] == a[g];
+                        if (!seen) c += cnt[g][bk];
+                    }
+                    if (c < bestc) {
+                        bestc = c;
+                        best = k;
+                    }
+                }
+                used[(size_t)nl * M + best] = 1;
+                const uint32_t w0 = idx[2 * (base + best)], w1 = idx[2 * (base + best) + 1];
+                const int a[3] = {(int)(w0 & 0xffffu), (int)(w0 >> 16), (int)w1};
+                for (int g = 0; g < 3; g++) {
+                    const int bk = a[g] & 31;
+                    bool seen = false;
+                    for (int q = 0; q < cnt[g][bk]; q++) seen = seen || addr[g][bk][q] == a[g];
+                    if (!seen) addr[g][bk][cnt[g][bk]++] = a[g];
+                }
+                const size_t dst = base + (size_t)t * HEt + e;
+                out_idx[2 * dst] = w0;
+                out_idx[2 * dst + 1] = w1;
+                out_b[dst] = b[base + best];
+            }
+        }
+    }
+}
+
 void hs_free(HsTables &t, const DevFree &dfree)
 {
     if (t.d_idx) dfree(t.d_idx);
@@ -194,8 +260,11 @@ int hs_build(HsTables &t, const int n[3], const double lo[3], const double h[3],
     t.d_xi = static_cast<float *>(alloc(xf.size() * 4));
     t.d_jpk = static_cast<uint32_t *>(alloc(jp.size() * 4));
     if (!t.d_idx || !t.d_b || !t.d_xi || !t.d_jpk) { err = "device allocation (collision tables)"; return DVM_ENOMEM; }
-    if (cudaMemcpy(t.d_idx, t.host_idx.data(), t.host_idx.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(t.d_b, t.host_b.data(), t.host_b.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+    std::vector<uint32_t> didx;
+    std::vector<float> db;
+    order_for_banks(t.host_idx, t.host_b, nv, trials, didx, db);
+    if (cudaMemcpy(t.d_idx, didx.data(), didx.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(t.d_b, db.data(), db.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(t.d_xi, xf.data(), xf.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(t.d_jpk, jp.data(), jp.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess) {
         cudaGetLastError();

@@ -124,6 +124,20 @@ __global__ void k_copy_rows(void *const *bufs, const int64_t *rows, int64_t n, i
     }
 }
 
+// Halo pack and unpack: dst row r = src row idx[r] (gather), or dst row
+// idx[r] = src row r (scatter); rows are row_bytes long (a multiple of 16).
+template <bool GATHER>
+__global__ void k_rows_indexed(char *dst, const char *src, const int64_t *idx, int64_t n, int64_t row_bytes)
+{
+    const int64_t n16 = row_bytes / 16;
+    for (int64_t r = blockIdx.x; r < n; r += gridDim.x) {
+        const int64_t rd = GATHER ? r : idx[r], rs = GATHER ? idx[r] : r;
+        const uint4 *a = reinterpret_cast<const uint4 *>(src + rs * row_bytes);
+        uint4 *b = reinterpret_cast<uint4 *>(dst + rd * row_bytes);
+        for (int64_t i = threadIdx.x; i < n16; i += blockDim.x) b[i] = a[i];
+    }
+}
+
 // Row means: destination row r of dst is the mean of source rows
 // idx[start[r] .. start[r+1]) of src (nv values each, storage precision;
 // the sum in FP64 for FP64 storage, FP32 otherwise).
@@ -167,6 +181,22 @@ int launch_copy_rows(void *const *bufs, const int64_t *rows, int64_t n, int64_t 
     if (row_bytes % 16 != 0) return DVM_EINVAL;
     const unsigned grid = (unsigned)std::min<int64_t>(n, 1 << 16);
     k_copy_rows<<<grid, 256, 0, s>>>(bufs, rows, n, row_bytes);
+    count_launch();
+    return cudaGetLastError() == cudaSuccess ? DVM_OK : DVM_ECUDA;
+}
+
+int launch_rows_indexed(bool gather, void *dst, const void *src, const int64_t *idx, int64_t n, int64_t row_bytes,
+                        cudaStream_t s)
+{
+    if (n <= 0) return DVM_OK;
+    if (row_bytes % 16 != 0) return DVM_EINVAL;
+    const unsigned grid = (unsigned)std::min<int64_t>(n, 1 << 16);
+    if (gather)
+        k_rows_indexed<true><<<grid, 256, 0, s>>>(static_cast<char *>(dst), static_cast<const char *>(src), idx, n,
+                                                  row_bytes);
+    else
+        k_rows_indexed<false><<<grid, 256, 0, s>>>(static_cast<char *>(dst), static_cast<const char *>(src), idx, n,
+                                                   row_bytes);
     count_launch();
     return cudaGetLastError() == cudaSuccess ? DVM_OK : DVM_ECUDA;
 }

@@ -7,12 +7,15 @@
 // warp-uniform, since it depends on the group only through the signs of the
 // velocity components (Sec. 3.1).
 //
-// Persistent CTAs take the Morton-ordered cells in a fixed order: CTA b of a
-// grid of G takes cells b, b + G, b + 2G, ...  Every cell costs about the
-// same, so the cells in flight on the whole GPU form one contiguous Morton
-// window and upwind neighbours are served from L2.  The assignment is a
-// function of the slot alone, so once a CTA's slot is empty every later slot
-// is empty too; the exits of the warp loops below rely on that.
+// Persistent CTAs take the Morton-ordered cells from a global counter, so
+// the cells in flight on the whole GPU form one contiguous Morton window and
+// upwind neighbours are served from L2 (a fixed assignment, cells b, b + G,
+// ... for CTA b, lets the CTAs drift apart and measured 1.6x slower).
+// A CTA's iterations alternate between two parities, one per solver warp,
+// and each parity's cells are taken in program order: once a slot of a
+// parity comes back empty, every later slot of that parity is empty.  The
+// other parity may still hold a cell, so every warp tracks the two parities
+// separately (see the loops below); no barrier is used for an empty slot.
 //
 // Compute warps, iteration j:
 //   phase 1  f*_i = (1 - dt invh sum_d |xi_d,i|) f_i + sum_d dt |xi_d,i| sum_k
@@ -41,8 +44,8 @@
 // Compute and solver warps meet on named barriers, "partials of cell j
 // ready" and "coefficients of cell j ready", each with four instances used
 // in turn, which makes every reuse of a barrier ordered after its previous
-// completion.  The solvers decide when the CTA stops (no cell left) and
-// publish it with the coefficients; no warp waits on a flag.
+// completion.  Both sides use the barriers of slot j only if slot j holds a
+// cell, which both read from the same slot record; no warp waits on a flag.
 #include <algorithm>
 #include <atomic>
 #include <cmath>
@@ -182,9 +185,6 @@ template <typename TC> struct TabE {
     TC g, p;
 };
 
-// decision published by the solver with each cell's coefficients
-enum { DEC_GO = 0, DEC_END = 1 };
-
 // One cell's stencil, as the dispatching solver warp hands it to the
 // compute warps three iterations ahead.
 template <typename TC> struct CellSlot {
@@ -207,13 +207,13 @@ template <typename TC> struct StepSmem {
     TC coef[NSS][CF_N];
     typename Num<TC>::X mom[NSS][5];  // rho, u, T of the cell
     int ok[NSS];
-    int dec[NSS];
     TC xin[3][NAX];   // velocity node values per axis, in index order
+    long long next0[2];  // the cells of slots 4 and 5, taken by warp 0
     // the final solve of each solver warp: 1D sums, matrix entries,
     // right-hand side, solution and residual
-    double g1d[2][3][5];
-    double sys[2][15];
-    double rhs[2][5], dsol[2][5], resid[2][5];
+    X g1d[2][3][5];
+    X sys[2][15];
+    X rhs[2][5], dsol[2][5], resid[2][5];
 };
 
 template <typename TC> struct Consts {
@@ -276,14 +276,8 @@ template <typename TC> __device__ inline TC warp_reduce7(const TC (&m)[7], int l
 }
 
 // ---------------------------------------------------------------- exact moment partials
-// Error-free transformations (Dekker 1971): a + b = s + e and a b = p + e
-// exactly, e recovered in FP32.
-__device__ inline ffn two_sum(float a, float b)
-{
-    const float s = a + b;
-    const float bb = s - a;
-    return {s, (a - (s - bb)) + (b - bb)};
-}
+// Error-free product (Dekker 1971): a b = p + e exactly, e recovered with one
+// FMA.
 __device__ inline ffn two_prod(float a, float b)
 {
     const float p = a * b;
@@ -379,10 +373,7 @@ __device__ inline void thread_moments(const QV<float> (&cur)[8], float jx, float
     const float r[7] = {Sr, jx * Xr, jy * Yr, fmaf(jz0, Zr, 2.0f * Azr), jx2 * Sr, jy2 * Sr,
                         fmaf(jz2, Sr, fmaf(jz4, A1r, 4.0f * A2r))};
 #pragma unroll
-    for (int k = 0; k < 7; k++) {
-        const ffn u = two_sum(t[k].hi, t[k].lo + r[k]);
-        m[k] = u;
-    }
+    for (int k = 0; k < 7; k++) m[k] = ffn{t[k].hi, t[k].lo + r[k]};  // normalised by the first add of the reduction
 }
 
 // warp_reduce7 on double-float numbers (the same reduce-scatter): returns,
@@ -392,17 +383,25 @@ __device__ inline ffn warp_reduce7_df(const ffn (&m)[7], int lane)
     auto sx = [](ffn v, int k) -> ffn {
         return {__shfl_xor_sync(0xffffffffu, v.hi, k), __shfl_xor_sync(0xffffffffu, v.lo, k)};
     };
+    // a + b with one error-free transformation of the high parts and the
+    // low parts added: left unnormalised until the last add, which
+    // normalises
+    auto add = [](ffn a, ffn b) -> ffn {
+        const float t = a.hi + b.hi;
+        const float bb = t - a.hi;
+        return {t, ((a.hi - (t - bb)) + (b.hi - bb)) + (a.lo + b.lo)};
+    };
     ffn a[4], b[2];
     const bool h4 = lane & 16, h3 = lane & 8, h2 = lane & 4;
 #pragma unroll
     for (int i = 0; i < 4; i++) {
         const ffn lo = m[i], hi = i < 3 ? m[4 + i] : ffn{0.0f, 0.0f};
-        a[i] = (h4 ? hi : lo) + sx(h4 ? lo : hi, 16);
+        a[i] = add(h4 ? hi : lo, sx(h4 ? lo : hi, 16));
     }
 #pragma unroll
-    for (int i = 0; i < 2; i++) b[i] = (h3 ? a[2 + i] : a[i]) + sx(h3 ? a[i] : a[2 + i], 8);
-    ffn c = (h2 ? b[1] : b[0]) + sx(h2 ? b[0] : b[1], 4);
-    c = c + sx(c, 2);
+    for (int i = 0; i < 2; i++) b[i] = add(h3 ? a[2 + i] : a[i], sx(h3 ? a[i] : a[2 + i], 8));
+    ffn c = add(h2 ? b[1] : b[0], sx(h2 ? b[0] : b[1], 4));
+    c = add(c, sx(c, 2));
     c = c + sx(c, 1);
     return c;
 }
@@ -448,6 +447,14 @@ __device__ inline int sym_e(int r, int s)
     return a * 5 - (a * (a - 1)) / 2 + (c - a);
 }
 
+// a double-float pair (hi, lo) of a compute-precision-class number
+__device__ inline float2 to_pair(ffn v) { return make_float2(v.hi, v.lo); }
+__device__ inline float2 to_pair(double v)
+{
+    const float hi = (float)v;
+    return make_float2(hi, (float)(v - (double)hi));
+}
+
 // Phase 2 of one cell on one warp (parity par): moments of f* from the
 // compute warps' partials, the coefficients of the target and its per-axis
 // tables into slot b.  Returns the status flags of the cell.  The code is
@@ -455,13 +462,15 @@ __device__ inline int sym_e(int r, int s)
 // compute warps' instruction streams: straight-line code of this length would
 // be fetched from beyond the instruction cache every time.
 //
-// Precision (FP32/BF16 storage): the moment sums arrive in double-float and
-// give rho, u, T in double-float; the target's 1D sums, the 5x5 system of
-// Eq. 6's correction and its solution are formed in FP64 (an FP32 LDL^T
-// factor refined twice against FP64 residuals), so that the collision term
-// nu (M~ - f*) defined by the per-axis tables g and the FP64 coefficients
-// carries the moments of f* to FP64-class accuracy.  Its residual sum_i psi_r Q_i dV,
-// psi = (1, xi, |xi|^2), goes to res_out.  The FP32 evaluation of M~ at each
+// Precision (FP32/BF16 storage): the moment sums arrive in double-float; the
+// target's 1D sums, the 5x5 system of Eq. 6's correction and its solution are
+// formed in double-float (an FP32 LDL^T factor refined twice against
+// double-float residuals), so that the collision term nu (M~ - f*) defined by
+// the per-axis tables g and the double-float coefficients carries the moments
+// of f* to double-float accuracy.  Its residual sum_i phi_r (M~ - f*)_i dV in
+// the centred basis goes to res_phi as double-float pairs (no FP64
+// instruction on this warp: FP64 runs at a small fraction of the FP32 rate
+// here and measured 8 ms per step on the Mach-5 workload).  The FP32 evaluation of M~ at each
 // node (and the FP32 copy of the coefficients it uses) rounds like the FP32
 // store that follows it.
 template <typename TC, int COLL>
@@ -624,43 +633,40 @@ __device__ inline int solve_cell(const StepParams &p, StepSmem<TC> &sm, const Co
                 if (__shfl_sync(0xffffffffu, done, 0)) break;
             }
         }
-        // ---- the final solve, in FP64 (a few dozen FP64 instructions per
-        // lane: shorter dependent chains than double-float on this GPU)
-        const double rd = dbl(rho), Td = dbl(T);
-        const double u3[3] = {dbl(ux), dbl(uy), dbl(uz)};
-        const double isTd = rsqrt(Td);
+        // ---- the final solve, in X arithmetic (double-float for FP32 storage)
         // K of the target: rho (2 pi T)^(-3/2) (entropic: times exp(e0 - 3 e4))
-        double Kd = rd * 0.06349363593424097 * isTd * isTd * isTd;
-        if constexpr (ENT) Kd *= (double)tc_exp<TC>(e[0] - (TC)3 * e[4]);
-        const double KdV = Kd * p.dV;
+        const X Kx = ENT ? Kc * tc_exp<TC>(e[0] - (TC)3 * e[4]) : Kc;
+        const X KdV = Kx * K.dV;
         {
             // 1D sums G_d[k] = sum_n g_d(n) c_d(n)^k, k = 0..4, with the node
-            // xi = (h_d/2) J, J = 2n + 1 - n_d, c = (xi - u)/sqrt(T), and g
-            // from c rounded to TC (the table value the collision uses)
-            double G[5] = {0, 0, 0, 0, 0};
+            // xi = (h_d/2) J, J = 2n + 1 - n_d (exact), c = (xi - u)/sqrt(T) in
+            // X, g from c rounded to TC (the table value the collision uses)
+            X G[5];
+#pragma unroll
+            for (int k = 0; k < 5; k++) G[k] = N::make((TC)0);
             if (ax < 3) {
-                const double hh = 0.5 * p.hv[ax], ua = u3[ax];
+                const X uX = ax == 0 ? ux : (ax == 1 ? uy : uz);
                 const TC ea = ENT ? (ax == 0 ? e[1] : (ax == 1 ? e[2] : e[3])) : (TC)0, e4 = ENT ? e[4] : (TC)0;
 #pragma unroll 1
                 for (int i = sub; i < nax; i += 8) {
-                    const double c = (hh * (double)(2 * i + 1 - nax) - ua) * isTd;
-                    const TC cf = (TC)c;
+                    const X c = (K.hh[ax] * (TC)(2 * i + 1 - nax) - uX) * isT;
+                    const TC cf = N::tc(c);
                     TC ex = (TC)-0.5 * cf * cf;
                     if constexpr (ENT) ex += cf * (ea + e4 * cf);
-                    const TC gt = tc_exp<TC>(ex);
-                    sm.tab[b][ax][i] = TabE<TC>{gt, cf};  // p holds c until the solve is done
-                    const double g = (double)gt, gc = g * c, gc2 = gc * c;
-                    G[0] += g;
-                    G[1] += gc;
-                    G[2] += gc2;
-                    G[3] += gc2 * c;
-                    G[4] += gc2 * c * c;
+                    const TC g = tc_exp<TC>(ex);
+                    sm.tab[b][ax][i] = TabE<TC>{g, cf};  // p holds c until the solve is done
+                    const X c2 = c * c;
+                    G[0] = G[0] + N::make(g);
+                    G[1] = G[1] + c * g;
+                    G[2] = G[2] + c2 * g;
+                    G[3] = G[3] + (c2 * c) * g;
+                    G[4] = G[4] + (c2 * c2) * g;
                 }
             }
 #pragma unroll
             for (int m = 4; m > 0; m >>= 1)
 #pragma unroll
-                for (int k = 0; k < 5; k++) G[k] += __shfl_xor_sync(0xffffffffu, G[k], m);
+                for (int k = 0; k < 5; k++) G[k] = G[k] + N::shfl_xor(G[k], m);
             if (sub == 0 && ax < 3)
 #pragma unroll
                 for (int k = 0; k < 5; k++) sm.g1d[par][ax][k] = G[k];
@@ -668,27 +674,29 @@ __device__ inline int solve_cell(const StepParams &p, StepSmem<TC> &sm, const Co
         __syncwarp();
         {
             // the 15 entries on lanes 0..15 (entry 14 on lanes 14 and 15)
-            double a = 0.0;
+            X a = N::make((TC)0);
             if (lane < 16) {
                 const int en = lane < 15 ? lane : 14, t0 = lane == 15 ? 5 : 0;
 #pragma unroll 1
                 for (int t = t0; t < t0 + 5; t++) {
                     const int32_t w = c_terms[en][t];
                     const int cf = (int)(int8_t)(w & 0xff);
-                    if (cf != 0)
-                        a += (double)cf * sm.g1d[par][0][(w >> 8) & 15] * sm.g1d[par][1][(w >> 12) & 15] *
-                             sm.g1d[par][2][(w >> 16) & 15];
+                    if (cf != 0) {
+                        const X pr = sm.g1d[par][0][(w >> 8) & 15] * sm.g1d[par][1][(w >> 12) & 15] *
+                                     sm.g1d[par][2][(w >> 16) & 15];
+                        a = a + pr * (TC)cf;
+                    }
                 }
             }
-            const double other = __shfl_sync(0xffffffffu, a, 15);
-            if (lane == 14) a += other;
+            const X other = N::shfl(a, 15);
+            if (lane == 14) a = a + other;
             if (lane < 15) sm.sys[par][lane] = a * KdV;
         }
         __syncwarp();
         // right-hand side: the moments of f* in phi are (rho, 0, 0, 0, 0) by
         // the definition of u and T, less those of the uncorrected target
         // (row 0 of the matrix); the TC factor of lane 0, then two refinements
-        // against FP64 residuals rhs - A d computed one row per lane
+        // against X residuals rhs - A d computed one row per lane
         TC Lf[5][5], Dif[5];
         int fok = 1;
         if (lane == 0) {
@@ -696,72 +704,57 @@ __device__ inline int solve_cell(const StepParams &p, StepSmem<TC> &sm, const Co
 #pragma unroll
             for (int r2 = 0; r2 < 5; r2++)
 #pragma unroll
-                for (int c2 = 0; c2 < 5; c2++) Af[r2 * 5 + c2] = (TC)sm.sys[par][sym_e(r2, c2)];
-            sm.rhs[par][0] = rd - sm.sys[par][0];
+                for (int c2 = 0; c2 < 5; c2++) Af[r2 * 5 + c2] = N::tc(sm.sys[par][sym_e(r2, c2)]);
+            sm.rhs[par][0] = rho - sm.sys[par][0];
 #pragma unroll
             for (int r2 = 1; r2 < 5; r2++) sm.rhs[par][r2] = -sm.sys[par][r2];
             fok = ldl5<TC>(Af, Lf, Dif) ? 1 : 0;
 #pragma unroll
-            for (int r2 = 0; r2 < 5; r2++) r[r2] = (TC)sm.rhs[par][r2];
+            for (int r2 = 0; r2 < 5; r2++) r[r2] = N::tc(sm.rhs[par][r2]);
             if (fok) ldl5_solve<TC>(Lf, Dif, r, dl);
             else flags |= ST_SINGULAR;
 #pragma unroll
-            for (int r2 = 0; r2 < 5; r2++) sm.dsol[par][r2] = fok ? (double)dl[r2] : 0.0;
+            for (int r2 = 0; r2 < 5; r2++) sm.dsol[par][r2] = N::make(fok ? dl[r2] : (TC)0);
         }
         __syncwarp();
+        fok = __shfl_sync(0xffffffffu, fok, 0);
 #pragma unroll 1
         for (int it = 0; it < 3; it++) {
             if (lane < 5) {
-                double s = sm.rhs[par][lane];
+                X s = sm.rhs[par][lane];
 #pragma unroll
-                for (int c2 = 0; c2 < 5; c2++) s -= sm.sys[par][sym_e(lane, c2)] * sm.dsol[par][c2];
+                for (int c2 = 0; c2 < 5; c2++) s = s - sm.sys[par][sym_e(lane, c2)] * sm.dsol[par][c2];
                 sm.resid[par][lane] = s;
+                // the last round: sum_i phi_r (M~ - f*)_i dV = A d - rhs, as a
+                // double-float pair (the host takes it to psi and multiplies
+                // by nu, in FP64)
+                if (it == 2 && p.res_phi) p.res_phi[cell * 5 + lane] = fok ? to_pair(-s) : make_float2(0.0f, 0.0f);
             }
             __syncwarp();
             if (it == 2) break;
             if (lane == 0 && fok) {
                 TC r[5], dl[5];
 #pragma unroll
-                for (int r2 = 0; r2 < 5; r2++) r[r2] = (TC)sm.resid[par][r2];
+                for (int r2 = 0; r2 < 5; r2++) r[r2] = N::tc(sm.resid[par][r2]);
                 ldl5_solve<TC>(Lf, Dif, r, dl);
 #pragma unroll
-                for (int r2 = 0; r2 < 5; r2++) sm.dsol[par][r2] += (double)dl[r2];
+                for (int r2 = 0; r2 < 5; r2++) sm.dsol[par][r2] = sm.dsol[par][r2] + N::make(dl[r2]);
             }
             __syncwarp();
         }
         TC *cf = sm.coef[b];
         if (lane == 0) {
-            const double d0 = sm.dsol[par][0], d4 = sm.dsol[par][4];
-            cf[CF_D0] = (TC)d0;
-            cf[CF_DX] = (TC)sm.dsol[par][1];
-            cf[CF_DY] = (TC)sm.dsol[par][2];
-            cf[CF_DZ] = (TC)sm.dsol[par][3];
-            cf[CF_D4] = (TC)d4;
-            cf[CF_C0] = (TC)(1.0 + d0 - 3.0 * d4);
+            const X d0 = sm.dsol[par][0], d4 = sm.dsol[par][4];
+            cf[CF_D0] = N::tc(d0);
+            cf[CF_DX] = N::tc(sm.dsol[par][1]);
+            cf[CF_DY] = N::tc(sm.dsol[par][2]);
+            cf[CF_DZ] = N::tc(sm.dsol[par][3]);
+            cf[CF_D4] = N::tc(d4);
+            cf[CF_C0] = N::tc(N::make((TC)1) + d0 - d4 * (TC)3);
             const TC nudt = K.nu0 * N::tc(rho) * sqrt(N::tc(T));
             if (nudt > (TC)1) flags |= ST_NUDT;
-            cf[CF_KN] = nudt * (TC)Kd;
+            cf[CF_KN] = nudt * N::tc(Kx);
             cf[CF_OMN] = (TC)1 - nudt;
-            if (p.res_out) {
-                // sum_i psi_r Q_i dV of Q = nu (M~ - f*): the phi moments of
-                // M~ - f* are A d - rhs, taken to psi = (1, xi, |xi|^2) with
-                // xi = c / isT + u
-                double r[5];
-#pragma unroll
-                for (int r2 = 0; r2 < 5; r2++) r[r2] = fok ? -sm.resid[par][r2] : 0.0;
-                const double sT = Td * isTd;
-                const double nu = p.nu_coef * rd * sT;
-                double *o = p.res_out + cell * 5;
-                o[0] = nu * r[0];
-                double dot = 0.0, uu = 0.0;
-#pragma unroll
-                for (int d = 0; d < 3; d++) {
-                    o[1 + d] = nu * (sT * r[1 + d] + u3[d] * r[0]);
-                    dot += u3[d] * r[1 + d];
-                    uu += u3[d] * u3[d];
-                }
-                o[4] = nu * (Td * (r[4] + 3.0 * r[0]) + 2.0 * sT * dot + uu * r[0]);
-            }
         }
         __syncwarp();
         // per-axis factors of the target, each lane for its nodes:
@@ -775,9 +768,8 @@ __device__ inline int solve_cell(const StepParams &p, StepSmem<TC> &sm, const Co
                 sm.tab[b][ax][i].p = c * (da + d4 * c);
             }
         }
-    } else if (lane == 0 && p.res_out) {
-#pragma unroll
-        for (int r2 = 0; r2 < 5; r2++) p.res_out[cell * 5 + r2] = 0.0;
+    } else if (lane < 5 && p.res_phi) {
+        p.res_phi[cell * 5 + lane] = make_float2(0.0f, 0.0f);
     }
     if (lane == 0) {
         sm.mom[b][0] = rho;
@@ -819,10 +811,10 @@ __global__ void __launch_bounds__(MAXT, 1) k_step(const StepParams p)
     const TS *__restrict__ fin = static_cast<const TS *>(p.f_in);
     TS *__restrict__ fout = static_cast<TS *>(p.f_out);
 
-    // cell dispatch (one warp): the cell of slot k (its k-th iteration) is
-    // blockIdx.x + k gridDim.x, or none (-1) past the last cell; its stencil
-    // is fetched into registers, then stored into a slot, split so that a
-    // solver overlaps the loads with its own work.
+    // cell dispatch (one warp): a cell index from the global counter (-1
+    // once it has run out), its stencil fetched into registers, then stored
+    // into a slot; split so that a solver overlaps the counter's round trip
+    // and the loads with its own work.
     // raw loaded values only: anything computed from them waits for the
     // loads, so it is left to store(), after the solve
     struct Sten {
@@ -832,10 +824,12 @@ __global__ void __launch_bounds__(MAXT, 1) k_step(const StepParams p)
         int cnt;
         TC invh;
     };
-    auto cell_of = [&](int k) -> long long {
-        const long long c = (long long)blockIdx.x + (long long)k * gridDim.x;
-        return c < p.ncells ? c : -1;
+    auto take_issue = [&]() -> unsigned long long { return lane == 0 ? atomicAdd(p.counter, 1ull) : 0ull; };
+    auto take_finish = [&](unsigned long long c) -> long long {
+        c = __shfl_sync(0xffffffffu, c, 0);
+        return c < (unsigned long long)p.ncells ? (long long)c : -1;
     };
+    auto take = [&]() -> long long { return take_finish(take_issue()); };
     auto fetch = [&](long long cell) {
         Sten t{cell, 0, 0, (TC)0, 0, (TC)0};
         if (cell >= 0) {
@@ -874,9 +868,18 @@ __global__ void __launch_bounds__(MAXT, 1) k_step(const StepParams p)
     };
 
     if (warp == 0) {
-        // the stencils of iterations 0..3; the solver warps fetch those of
-        // iteration j + 4 while they solve cell j
-        for (int k = 0; k < 4; k++) store(fetch(cell_of(k)), k);
+        // the cells of slots 0..5 in slot order (so that each parity's takes
+        // come in its slot order) and the stencils of slots 0..3; the solver
+        // warps fetch those of slot j + 4 while they solve cell j
+        for (int k = 0; k < 4; k++) store(fetch(take()), k);
+        {
+            const long long n4 = take();
+            const long long n5 = take();
+            if (lane == 0) {
+                sm.next0[0] = n4;
+                sm.next0[1] = n5;
+            }
+        }
 #pragma unroll
         for (int d = 0; d < 3; d++) {
             const int hd = p.half[d];
@@ -904,27 +907,29 @@ __global__ void __launch_bounds__(MAXT, 1) k_step(const StepParams p)
 
     if (warp < 2) {
         // ================= solver warps: warp b takes the cells j = b mod 2
+        // It stops at its first empty slot: every later slot of its parity
+        // is empty too.  The slot records of its parity are written by this
+        // warp (or by warp 0 before the CTA barrier), so the test is local.
         const int par = warp;
+        long long next_cell = sm.next0[par];  // the cell of slot par + 4
         for (int j = par;; j += 2) {
+            if (sm.slot[j % NSL].cell < 0) break;
             const int q = j % NSS;
             bar_sync_n(BAR_P + q, nbar);
             const long long cell = sm.cellp[q];
-            const int dec = cell < 0 ? DEC_END : DEC_GO;
-            if (dec == DEC_GO) {
-                // the stencil of iteration j + 4: its loads are in flight
-                // during the solve
-                const Sten nst = fetch(cell_of(j + 4));
-                const int flags = solve_cell<TC, COLL>(p, sm, K, q, ncw, cell, par);
-                store(nst, j + 4);
-                if (lane == 0) {
-                    if (flags) atomicOr(p.status, flags);
-                    sm.ok[q] = (COLL == DVM_COLL_BGK || COLL == DVM_COLL_BGK_ENTROPIC) &&
-                               (flags & (ST_NONPOS | ST_SINGULAR)) == 0;
-                }
+            // the stencil of slot j + 4 and the cell of slot j + 6: their
+            // loads and the counter's round trip are in flight during the solve
+            const Sten nst = fetch(next_cell);
+            const unsigned long long nc = take_issue();
+            const int flags = solve_cell<TC, COLL>(p, sm, K, q, ncw, cell, par);
+            store(nst, j + 4);
+            next_cell = take_finish(nc);
+            if (lane == 0) {
+                if (flags) atomicOr(p.status, flags);
+                sm.ok[q] = (COLL == DVM_COLL_BGK || COLL == DVM_COLL_BGK_ENTROPIC) &&
+                           (flags & (ST_NONPOS | ST_SINGULAR)) == 0;
             }
-            if (lane == 0) sm.dec[q] = dec;
             bar_arrive_n(BAR_C + q, nbar);
-            if (dec != DEC_GO) break;
         }
         return;
     }
@@ -960,9 +965,13 @@ __global__ void __launch_bounds__(MAXT, 1) k_step(const StepParams p)
     // (group o adds o).  Each thread reads back only the pieces it copied.
     const TS *fin_p0 = fin + p0;
     int idx_own = 0, idx_l[2 * DIM];
+    // bit b set: parity b has met an empty slot, so every later slot of that
+    // parity is empty (its solver warp has stopped writing slot records)
+    int ended = 0;
+    auto slot_cell = [&](int k) -> long long { return ((ended >> (k & 1)) & 1) ? -1 : sm.slot[k % NSL].cell; };
     auto point = [&](int k) -> bool {
         const CellSlot<TC> &sl = sm.slot[k % NSL];
-        const long long c = sl.cell;
+        const long long c = slot_cell(k);
 #pragma unroll
         for (int L = 0; L < 2 * DIM; L++) idx_l[L] = sl.sidx[L];
         idx_own = (int)c * 8;
@@ -987,16 +996,20 @@ __global__ void __launch_bounds__(MAXT, 1) k_step(const StepParams p)
     }
 
     Q4 cur[8];   // f* of cell j
+    long long cprev1 = -1, cprev2 = -1;  // the cells of slots j - 1 and j - 2
     for (int j = 0;; j++) {
         const int q = j % NSS;
         const CellSlot<TC> &sl = sm.slot[j % NSL];
-        const long long cell = sl.cell;
-        if (cell >= 0) {
-            // ================= phase 1: transport of cell j
+        const long long cell = slot_cell(j);
+        if (cell < 0) ended |= 1 << (j & 1);
+        const bool valid = cell >= 0;
+        {
+            // ================= phase 1: transport of cell j (an empty slot
+            // runs only the copy ring, which brings in the next cell)
             bool on = point(j);  // groups 4..7 of this cell are copied first
             // the next cell's own values (an HBM stream) are prefetched into L2
             // one cell ahead, so that their copies four groups later hit L2
-            const long long nxt = sm.slot[(j + 1) % NSL].cell;
+            const long long nxt = slot_cell(j + 1);
             const TS *pf = fin_p0 + (size_t)(nxt < 0 ? 0 : nxt) * NV;
             const TC invh = sl.invh;
             const Q4 cs = q_fma(q_splat(-invh), q_add(q_splat(dax + day), daz), q_splat((TC)1));
@@ -1012,7 +1025,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_step(const StepParams p)
                 // NST - 1 younger copy groups are pending
                 cp_async_wait<NST - 1>();
                 Q4 fs = q_splat((TC)0);
-                if (active) {
+                if (valid && active) {
                     const TS *st = ring + (size_t)(o % NST) * (1 + DIM) * P + p0;
                     fs = q_mul(cs, IO::lds(st));
 #pragma unroll
@@ -1043,6 +1056,8 @@ __global__ void __launch_bounds__(MAXT, 1) k_step(const StepParams p)
                 if (o == NST) on = point(j + 1);
                 copy_group(on, (o + NST) & 7, o % NST, dep_of(fs));
             }
+        }
+        if (valid) {
             // the seven integer-weighted partial sums of this thread:
             // sum f, sum s_x j_x f, sum s_y j_y f, sum s_z j_z f, sum j_x^2 f,
             // sum j_y^2 f, sum j_z^2 f  (xi_d = (h_d/2) s_d j_d, j_d odd)
@@ -1081,19 +1096,16 @@ __global__ void __launch_bounds__(MAXT, 1) k_step(const StepParams p)
                 const TC tot = warp_reduce7<TC>(m, lane);
                 if ((lane & 3) == 0 && lane < 28) sm.red[q][cw][lane >> 2] = tot;
             }
+            if (ctid == 0) sm.cellp[q] = cell;
+            bar_arrive_n(BAR_P + q, nbar);
         }
-        if (ctid == 0) sm.cellp[q] = cell;
-        bar_arrive_n(BAR_P + q, nbar);
 
         TS *tile = tiles + (size_t)(j & 1) * NV + p0;  // f* of cell j - 2, then of cell j
-        if (j >= 2) {
+        if (cprev2 >= 0) {
             // ================= phase 3: collision of cell j - 2
             const int q2 = (j - 2) % NSS;
             bar_sync_n(BAR_C + q2, nbar);
-            if (sm.dec[q2] != DEC_GO) break;
-            // the cell of iteration j - 2 is still in its slot (slots are
-            // reused NSL iterations later)
-            const long long pc = sm.slot[(j - 2) % NSL].cell;
+            const long long pc = cprev2;
             if (cw == 0 && lane < 5) {
                 // the moments of f* in FP64, one per lane
                 const typename Num<TC>::X v = sm.mom[q2][lane];
@@ -1139,10 +1151,14 @@ __global__ void __launch_bounds__(MAXT, 1) k_step(const StepParams p)
         }
         // f* of cell j waits in the tile the collision just read (each thread
         // rewrites only its own positions)
-        if (cell >= 0 && active) {
+        if (valid && active) {
 #pragma unroll
             for (int o = 0; o < 8; o++) IO::sts(tile + o * P, cur[o]);
         }
+        cprev2 = cprev1;
+        cprev1 = cell;
+        // done once both parities have run out and no collision is pending
+        if (ended == 3 && cprev1 < 0 && cprev2 < 0) break;
     }
     cp_async_wait_all();
 }

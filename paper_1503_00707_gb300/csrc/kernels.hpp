@@ -31,12 +31,14 @@ struct StepParams {
     const double *amag;      // [3][32] |xi| of the positive-side nodes m = 0..half-1
     const float *amag_f;     // same, rounded to FP32
     double dt, kn, dV;
-    double nu_coef;          // sqrt(8/pi) / Kn: the BGK frequency is nu_coef rho sqrt(T)
     double hv[3];            // velocity spacing per axis
     double *mom_out;         // [ncells][5]: rho, u[3], T of f*
-    double *res_out;         // [ncells][5] or null: sum_i psi_r Q_i dV of the BGK collision
-                             // term, psi = (1, xi, |xi|^2)
+    double *res_out;         // [ncells][5] or null: sum_i psi_r q_i dV of the hard-sphere or
+                             // learned collision term, psi = (1, xi, |xi|^2)
+    float2 *res_phi;         // [ncells][5] or null: sum_i phi_r (M~ - f*)_i dV of the BGK
+                             // step, phi = (1, c, |c|^2 - 3), as double-float pairs
     int *status;
+    unsigned long long *counter;  // cell dispenser of the step kernel, zeroed before each launch
     cudaStream_t stream;
 };
 
@@ -58,6 +60,11 @@ int launch_from_f64(int prec, const double *src, void *dst, int64_t count, cudaS
 // Copies of whole rows (one cell's f) between buffers: rows [n][4] =
 // {destination buffer, row, source buffer, row} indexing bufs (device arrays).
 int launch_copy_rows(void *const *bufs, const int64_t *rows, int64_t n, int64_t row_bytes, cudaStream_t s);
+
+// gather: dst row r = src row idx[r]; scatter: dst row idx[r] = src row r
+// (n rows of row_bytes, a multiple of 16).
+int launch_rows_indexed(bool gather, void *dst, const void *src, const int64_t *idx, int64_t n, int64_t row_bytes,
+                        cudaStream_t s);
 
 // dst row r = mean of src rows idx[start[r] .. start[r+1]) (nv values per row).
 int launch_mean_rows(int prec, void *dst, const void *src, const int64_t *start, const int64_t *idx, int64_t nrows,

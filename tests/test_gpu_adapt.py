@@ -62,9 +62,9 @@ def _expected_after_coarsen(k0, l0, f0, k1, l1, dim, L):
 def test_coarsen_project_means_children(name, precision):
     """The 3D FP32 case (a 1,464-cell periodic tree coarsened to about 1,150
     cells) runs the 16^3 step kernel at two CTAs per SM: its cells run out
-    within the first six of every CTA, the regime where a cell dispenser could
-    leave an empty slot before a full one.  The kernel's static cell
-    assignment makes that impossible."""
+    within the first six of every CTA, where the two solver warps' takes can
+    leave an empty slot of one parity before a full slot of the other.  The
+    kernel tracks the two parities separately, so that order is harmless."""
     c = dict(W.CONFIGS[name])
     if name == "c4_hs_bimodal":
         c.update(base_level=2, max_level=4, coll=D.COLL_BGK, r=0.3)
