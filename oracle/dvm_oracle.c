@@ -983,8 +983,9 @@ int orc_bgk_entropic(orc_problem *p, double dt, double kn, double *q)
  * and the unit vector omega (z = 2u - 1, phi = 2 pi u').  The post-collision
  * pair xi' = c + |g| omega / 2, xi'_* = c - |g| omega / 2 (c the mean of xi_i
  * and xi_gamma) is mapped to its nearest nodes l, m; a trial whose l or m
- * falls outside the grid is dropped.  With M_kept kept trials,
- * b = c = Nv dV |g| / (sqrt(2) M_kept), the Monte-Carlo weights of
+ * falls outside the grid is dropped.  With M the number of trials drawn
+ * (dropped ones included: they stand for partners in the tails, where f is
+ * negligible), b = c = Nv dV |g| / (sqrt(2) M), the Monte-Carlo weights of
  * I = 1/(4 sqrt(2) pi) int int (f'f'_* - f f_*) |g| dOmega dxi_*. */
 static int nearest_node(const orc_problem *p, const double x[3], int32_t kk[3])
 {
@@ -1662,9 +1663,17 @@ int orc_learned_apply(orc_problem *p, double dt, double kn, const double *knl, c
                 ent += Q[v] * log(f[v] > 0.0 ? f[v] : 1e-300) * p->dV;
                 qabs += fabs(Q[v]) * p->dV;
             }
-            /* entropy production non-positive within the rounding of its
-             * evaluation: 1e-5 of sum |Q| dV (an equilibrium cell, where it
-             * is zero up to rounding, passes) */
+            /* entropy production sum Q ln f dV non-positive (H-theorem),
+             * up to the error of its evaluation.  The bound 1e-5 sum |Q| dV
+             * is set by the FP32 evaluation on the device, which sums
+             * Q ln(f/M) (ln M is a collision invariant, so the exact sum is
+             * the same) with about 54 terms per thread: a relative error of
+             * at most 54 * 2^-24 = 3.2e-6 of sum |Q| |ln(f/M)| dV, and ln(f/M)
+             * is O(1) where Q is not negligible.  A term whose exact
+             * production is <= 0 is therefore kept on both sides; here in
+             * FP64 the invariant part sum Q ln M cancels to the correction's
+             * residual (1e-12 of its scale).  An equilibrium cell, where the
+             * production is zero up to rounding, passes. */
             if (ok && !(ent <= 1e-5 * qabs)) ok = 0;
             free(M);
         }

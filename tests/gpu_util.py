@@ -29,10 +29,39 @@ def pair(c, precision=None, collision=None, init=True):
         xyz, _ = s.centres()
         xo, _ = o.centres()
         assert np.array_equal(xyz, xo)
-        w, r, u, T = W.initial_state(c, xyz)
+        w, r, u, T = W.initial_state(c, xo)
         s.init_maxwellian(w, r, u, T)
         o.init_maxwellian(w, r, u, T)
     return s, o
+
+
+def storage_round(f, precision):
+    """f rounded to the CUDA path's storage precision ("f64", "f32", "bf16"), as
+    float64: the values both sides start from when they must start alike."""
+    if precision == "f64":
+        return np.array(f, dtype=np.float64)
+    if precision == "f32":
+        return np.asarray(f, dtype=np.float32).astype(np.float64)
+    return bf16_round(np.asarray(f, dtype=np.float32)).astype(np.float64)
+
+
+def same_start(s, o, f, precision):
+    """Set the solver and the oracle to f (computed on the oracle's side)
+    rounded to the storage precision; returns the rounded values."""
+    fr = storage_round(f, precision)
+    s.set_f(fr)
+    o.set_f(fr)
+    return fr
+
+
+def volume_totals(f, o, dim):
+    """sum_j V_j sum_i psi_r f_ij dV, r = mass, momentum, energy, for any f on
+    the oracle's tree, from its cell sizes and velocity nodes (independent of
+    either side's totals routine)."""
+    _, h = o.centres()
+    xi = o.xi.reshape(-1, 3)
+    psi = np.stack([np.ones(len(xi)), xi[:, 0], xi[:, 1], xi[:, 2], (xi * xi).sum(1)], 1)
+    return ((h ** dim)[:, None] * (np.asarray(f, np.float64) @ psi)).sum(0) * o.dV
 
 
 def rel_linf(a, b):

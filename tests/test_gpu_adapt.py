@@ -13,7 +13,7 @@ import pytest
 import oracle as O
 import paper_1503_00707_gb300 as D
 import workloads as W
-from tests.gpu_util import oracle_for, pair, rel_linf
+from tests.gpu_util import oracle_for, pair, rel_linf, same_start
 
 pytestmark = pytest.mark.gpu
 
@@ -105,8 +105,8 @@ def test_adapt_project_and_step_match_oracle(name, precision, tol, kind):
     c = _adapt_cfg(name)
     s, o = pair(c, precision=precision, collision=D.COLL_BGK)
     dt = o.dt_cfl(c["cfl"])
-    s.step(2, dt)
-    o.set_f(s.get_f())  # the same values on both sides
+    o.step(2, dt, O.COLL_BGK, c["kn"])
+    same_start(s, o, o.get_f(), precision)  # a developed state, the same values on both sides
     rng = np.random.default_rng(21)
     if kind == "coarsen":
         flags = (rng.random(s.nleaves) < 0.85).astype(np.uint8)
@@ -160,8 +160,8 @@ def test_kn_local_matches_oracle(name, precision, tol):
     c = W.CONFIGS[name]
     s, o = pair(c, precision=precision)
     dt = o.dt_cfl(c["cfl"])
-    s.step(5, dt)
-    o.set_f(s.get_f())
+    o.step(5, dt, O.COLL_BGK, c["kn"])
+    same_start(s, o, o.get_f(), precision)
     knl = s.kn_local()
     ko = o.kn_local(c["kn"])
     assert rel_linf(knl, ko) < tol

@@ -20,7 +20,7 @@ import pytest
 import oracle as O
 import paper_1503_00707_gb300 as D
 import workloads as W
-from tests.gpu_util import pair, rel_linf
+from tests.gpu_util import pair, rel_linf, same_start
 
 pytestmark = pytest.mark.gpu
 
@@ -50,9 +50,8 @@ def _ratio(res, q, xi, dV, cells=None):
 
 def _perturbed(c, precision, collision=None, scale=0.3):
     s, o = pair(c, precision=precision, collision=collision)
-    f0 = o.get_f() * W.random_f_perturbation(o.ncells, o.nv, scale=scale)
-    s.set_f(f0)
-    o.set_f(s.get_f())  # the same values (storage-rounded) on both sides
+    # the same values (rounded to the storage precision) on both sides
+    same_start(s, o, o.get_f() * W.random_f_perturbation(o.ncells, o.nv, scale=scale), precision)
     return s, o
 
 
@@ -102,7 +101,7 @@ def test_hard_sphere_collision_term_conserves_per_cell():
     s, o = pair(c)
     s.set_collision_tables(c["trials"], W.SEED)
     o.hs_tables(c["trials"], W.SEED)
-    o.set_f(s.get_f())
+    same_start(s, o, o.get_f(), "f32")
     dt = o.dt_cfl(c["cfl"]) / 16
     s.step(1, dt)
     res = s.step_residual()
@@ -117,7 +116,7 @@ def test_learned_collision_term_conserves_per_cell():
     s, o = pair(c, collision=D.COLL_LEARNED)
     s.set_collision_tables(64, W.SEED)
     o.hs_tables(64, W.SEED)
-    o.set_f(s.get_f())
+    same_start(s, o, o.get_f(), "f32")
     knl = o.kn_local(c["kn"])
     s.learned_configure(float(np.median(knl)))
     a_o, _ = o.hermite_project()

@@ -10,7 +10,7 @@ import pytest
 import oracle as O
 import paper_1503_00707_gb300 as D
 import workloads as W
-from tests.gpu_util import bf16_round, pair, random_params, rel_linf
+from tests.gpu_util import bf16_round, pair, random_params, rel_linf, same_start
 
 pytestmark = pytest.mark.gpu
 
@@ -39,9 +39,11 @@ def _setup(threshold=None):
     s, o = pair(c, collision=D.COLL_LEARNED)
     s.set_collision_tables(TRIALS, SEED)
     o.hs_tables(TRIALS, SEED)
-    o.set_f(s.get_f())  # both sides start from the same FP32 values
-    knl = o.kn_local(c["kn"])
-    thr = float(np.median(knl)) if threshold is None else threshold
+    same_start(s, o, o.get_f(), "f32")  # both sides start from the same FP32 values
+    knl = np.sort(o.kn_local(c["kn"]))
+    # half way between the two middle values: no cell's local Kn lies within
+    # rounding of the threshold, so both sides split the cells alike
+    thr = float(0.5 * (knl[len(knl) // 2 - 1] + knl[len(knl) // 2])) if threshold is None else threshold
     s.learned_configure(thr)
     return c, s, o, thr
 
@@ -98,8 +100,8 @@ def test_apply_given_outputs_matches_oracle():
     e0[0] = 1.0
     oin = (-2.0 * (a_o - e0)).astype(np.float32)
     dt = 2.5e-5
-    r = s.learned_collide(dt, o=oin, want=("knl", "used", "q"))
-    used_o, q_o = o.learned_apply(dt, c["kn"], r["knl"], oin.astype(np.float64), thr, want_q=True)
+    r = s.learned_collide(dt, o=oin, want=("used", "q"))
+    used_o, q_o = o.learned_apply(dt, c["kn"], o.kn_local(c["kn"]), oin.astype(np.float64), thr, want_q=True)
     assert np.array_equal(r["used"], used_o)
     assert 0 < used_o.sum() < nc
     lm = used_o.astype(bool)
@@ -117,10 +119,11 @@ def test_network_outputs_match_oracle_network():
     c, s, o, thr = _setup()
     params = random_params(5)
     s.set_weights(params)
-    r = s.learned_collide(1e-5, want=("a", "o", "used"))
-    # the oracle network on the GPU's inputs rounded as the tensor cores see
-    # them (the weights are BF16-exact)
-    y = O.mlp_forward(params.astype(np.float64), bf16_round(r["a"]).astype(np.float64))
+    r = s.learned_collide(1e-5, want=("o", "used"))
+    # the oracle network on the oracle's Hermite coefficients rounded to BF16,
+    # as the tensor cores see them (the weights are BF16-exact)
+    a_o, _ = o.hermite_project()
+    y = O.mlp_forward(params.astype(np.float64), bf16_round(a_o).astype(np.float64))
     assert np.max(np.abs(r["o"] - y)) < 2e-2 * np.max(np.abs(y))
 
 
@@ -128,8 +131,9 @@ def test_training_pairs_match_oracle():
     c, s, o, thr = _setup()
     a, t = s.learned_pairs()
     a_o, mom = o.hermite_project()
+    f_keep = o.get_f()
     I, _, _ = o.hs_collide(0.0, 1.0, want=True)
-    o.set_f(s.get_f())  # hs_collide with dt = 0 keeps f; restore exactly anyway
+    o.set_f(f_keep)  # hs_collide with dt = 0 keeps f; restore exactly anyway
     t_o = o.hermite_target(I, mom)
     assert np.max(np.abs(a - a_o)) < 2e-5 * np.max(np.abs(a_o))
     assert np.max(np.abs(t - t_o)) < 1e-3 * np.max(np.abs(t_o))

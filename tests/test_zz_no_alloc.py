@@ -17,7 +17,7 @@ import pytest
 
 import paper_1503_00707_gb300 as D
 import workloads as W
-from tests.gpu_util import oracle_for, rel_linf
+from tests.gpu_util import oracle_for, rel_linf, storage_round
 
 pytestmark = pytest.mark.gpu
 
@@ -35,13 +35,16 @@ def _uniform_hs_solver():
     c = dict(W.CONFIGS["c4_hs_bimodal"])
     c.update(base_level=1, max_level=1, pred=0, n=(16, 16, 16), lo=(-6.0,) * 3, hi=(6.0,) * 3)
     s = D.solver_from_config(c, D.F32, D.COLL_HS)
-    nc = s.ncells
-    u = np.zeros((nc, 2, 3))
-    u[:, 0, 0], u[:, 1, 0] = 1.4, -1.2
-    # the same bimodal state in every cell: transport is the identity
-    s.init_maxwellian(np.tile([0.45, 0.55], (nc, 1)), np.ones((nc, 2)), u, np.tile([0.6, 0.7], (nc, 1)))
+    s.init_maxwellian(*_bimodal(s.ncells))
     s.set_collision_tables(64, 20150303)
     return s, c
+
+
+def _bimodal(nc):
+    """The same two-beam state in every cell: transport is the identity."""
+    u = np.zeros((nc, 2, 3))
+    u[:, 0, 0], u[:, 1, 0] = 1.4, -1.2
+    return np.tile([0.45, 0.55], (nc, 1)), np.ones((nc, 2)), u, np.tile([0.6, 0.7], (nc, 1))
 
 
 def test_noalloc_matches_step_on_two_calls():
@@ -68,13 +71,16 @@ def test_noalloc_matches_oracle_on_two_calls():
     import torch
     s, c = _uniform_hs_solver()
     o = oracle_for(c)
+    o.init_maxwellian(*_bimodal(o.ncells))
     o.hs_tables(64, 20150303)
     dt = 2.5e-5
-    f = s.get_f()
-    buf = torch.tensor(f, dtype=torch.float32, device="cuda").contiguous()
-    torch.cuda.synchronize()
+    buf = torch.empty((s.ncells, s.nv), dtype=torch.float32, device="cuda")
     for call in range(2):
-        o.set_f(buf.double().cpu().numpy())
+        # both sides start each call from the oracle's values in FP32
+        f = storage_round(o.get_f(), "f32")
+        o.set_f(f)
+        buf.copy_(torch.from_numpy(f.astype(np.float32)))
+        torch.cuda.synchronize()
         o.hs_collide(dt, c["kn"])
         s.hs_collide_noalloc(buf.data_ptr(), s.ncells, dt)
         got = buf.double().cpu().numpy()
