@@ -67,6 +67,8 @@ def parse():
     ap.add_argument("--no-bf16", action="store_true", help="skip the BF16-storage leg")
     ap.add_argument("--bf16-steps", type=int, default=10)
     ap.add_argument("--learned-steps", type=int, default=5)
+    ap.add_argument("--train-epochs", type=int, default=20,
+                    help="epochs of network training before the learned-vs-plain leg")
     ap.add_argument("--develop-steps", type=int, default=1500,
                     help="BGK steps that develop the sphere flow before the learned-vs-plain leg")
     return ap.parse_args()
@@ -289,7 +291,7 @@ def learned_leg(args):
     net.set_weights(init_params(seed))
     loss0, _ = net.mlp_loss_grad(X, T, want_grad=False)
     t0 = time.perf_counter()
-    loss = net.train(X, T, epochs=20, batch=1024, lr=1e-3, seed=seed)
+    loss = net.train(X, T, epochs=args.train_epochs, batch=1024, lr=1e-3, seed=seed) if args.train_epochs else loss0
     train_s = time.perf_counter() - t0
     sys.stderr.write("learned leg: %d pairs, loss %.4g -> %.4g in %.1f s\n" % (X.shape[0], loss0, loss, train_s))
     weights = net.get_weights()
@@ -326,13 +328,17 @@ def learned_leg(args):
         if coll == D.COLL_LEARNED:
             s.set_weights(weights)
             s.learned_configure(0.05)
-        # explicit Euler on the collision term needs dt/Kn max(P B) <= 1
-        dt = s.dt_cfl(cfg["cfl"]) / 10
+        # explicit Euler on the hard-sphere term needs dt/Kn max(P B) <= 1;
+        # max(P B) of the developed Mach-3 flow on [-8,8]^3 is a few hundred
+        dt = min(s.dt_cfl(cfg["cfl"]) / 10, cfg["kn"] / 1000)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        # an NVTX range names the timed steps of each operator (for profilers)
+        torch.cuda.nvtx.range_push("learned_leg_" + name)
         e0.record(stream)
         s.step(args.learned_steps, dt)
         e1.record(stream)
+        torch.cuda.nvtx.range_pop()
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1)
         mom = s.moments()
@@ -358,16 +364,16 @@ def learned_leg(args):
     (r1, u1, T1), (r2, u2, T2) = res["learned"]["moments"], res["plain"]["moments"]
     nc = res["plain"]["cells"]
     out = {
-        "workload": "%s: Mach-3 sphere flow, %d cells x 24^3 velocities, developed with BGK for %d steps "
+        "workload": "%s: Mach-3 sphere flow, Kn=%g, %d cells x 24^3 velocities, developed with BGK for %d steps "
                     "(bow shock standing), then %d steps of the hard-sphere integral with %d trials per node "
                     "(plain) vs the learned operator gated at Kn_loc < 0.05 with hard-sphere fallback, "
                     "from the same snapshot"
-                    % (args.learned_config, nc, args.develop_steps, args.learned_steps, cfg["trials"]),
+                    % (args.learned_config, cfg["kn"], nc, args.develop_steps, args.learned_steps, cfg["trials"]),
         "snapshot": snapshot,
         "speedup": res["learned"]["value"] / res["plain"]["value"],
         "field_rel_linf": {"rho": rel(r1, r2), "u": rel(u1, u2), "T": rel(T1, T2)},
         "fallback_cells": res["learned"]["fallback"], "cells": nc,
-        "training": {"pairs": int(X.shape[0]), "epochs": 20, "loss_start": loss0, "loss_end": loss,
+        "training": {"pairs": int(X.shape[0]), "epochs": args.train_epochs, "loss_start": loss0, "loss_end": loss,
                      "seconds": train_s},
     }
     for name in ("plain", "learned"):
@@ -623,7 +629,8 @@ def lbm_leg(args, stream=None):
             "cell_updates_per_s": nc / (ms / 1e3), "phase_space_updates_per_s": nc * q / (ms / 1e3),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "peak_source": peak_kind,
-                         "algorithmic_bytes_per_cell": bpc, "traffic": None},
+                         "algorithmic_bytes_per_cell": bpc,
+                         "traffic": _profiled_traffic("k_lbm.cu", "k_lbm_%s_f32" % name)},
             "gpu_launches": launches, "moments_finite_positive": ok, "cpu_baseline": cpu,
             "l2": "inputs larger than L2 (f is %.0f MB per buffer)" % (q * ld * 4 / 1e6),
         }
