@@ -303,7 +303,9 @@ def learned_leg(args):
     dev = D.solver_from_config(cfg, D.F32, D.COLL_BGK, stream=stream)
     xyz, _ = dev.centres()
     dev.init_maxwellian(*W.initial_state(cfg, xyz))
-    dtd = dev.dt_cfl(cfg["cfl"])
+    # nu dt <= 1 with nu = sqrt(8/pi) rho sqrt(T)/Kn, rho sqrt(T) up to about 7
+    # in the shock layer: dt <= Kn/20 (the CFL step on the full tree is below it)
+    dtd = min(dev.dt_cfl(cfg["cfl"]), cfg["kn"] / 20)
     t0 = time.perf_counter()
     dev.step(args.develop_steps, dtd)
     dev_s = time.perf_counter() - t0

@@ -526,9 +526,8 @@ int dvm_rank_totals(dvm_rank *r, double *out);
  * contents are those of the last call; nothing in it needs to start at
  * zero), and calls whose work overlaps on the GPU race on it.  The first
  * call on a device (and the first after that device's context has been
- * re-created, e.g. by cudaDeviceReset) looks up the array's device address;
- * make that first call before any stream capture begins.  Every call
- * synchronises the stream once to read the status word.  On DVM_EUNSTABLE
+ * re-created, e.g. by cudaDeviceReset) looks up the array's device address.
+ * Every call synchronises the stream once to read the status word.  On DVM_EUNSTABLE
  * (a singular correction, or dt/Kn max(P B) > 1) f already holds the
  * applied update, invalid as it may be: a caller that needs to roll back
  * keeps its own copy of f.  Non-positive density or temperature in a cell

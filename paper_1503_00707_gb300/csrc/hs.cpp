@@ -18,9 +18,11 @@
 #include "hs.hpp"
 
 #include <algorithm>
+#include <atomic>
 #include <climits>
 #include <cmath>
 #include <cstring>
+#include <thread>
 
 #include "../../include/dvm.h"
 
@@ -74,64 +76,190 @@ int64_t korobov_multiplier(int64_t M)
 // slot its lanes gather f at three node indices (gamma, l, m) from a
 // shared-memory tile, and every distinct index in the same bank (index mod 32)
 // costs one more shared-memory wavefront.  The sums B and C over a node's
-// trials do not depend on their order, so each node's trials are ordered
-// greedily, slot by slot: each lane takes, from its node's remaining trials,
-// the one that adds the fewest distinct indices to banks already in use at
-// this slot (over the three gathers).  idx/b: node-major tables as built;
-// out_idx/out_b: the same entries in device order.
-static void order_for_banks(const std::vector<uint32_t> &idx, const std::vector<float> &b, int nv, int M,
-                            std::vector<uint32_t> &out_idx, std::vector<float> &out_b)
-{
-    const int HEt = 32, tpn = M / HEt, K = 32 / tpn;  // lanes per node, nodes per warp
-    out_idx.assign(idx.size(), 0u);
-    out_b.assign(b.size(), 0.0f);
-    std::vector<int> pool;
-    std::vector<uint8_t> used((size_t)K * M);
-    // per gather, per bank: the distinct indices taken at the current slot
+// trials do not depend on their order, so the order is chosen per warp to
+// keep those wavefronts few:
+//   1. greedily, slot by slot: each lane takes, from its node's remaining
+//      trials, the one that adds the fewest distinct indices to banks already
+//      in use at this slot (over the three gathers);
+//   2. then by local search: swaps of two trials of one node between two
+//      slots, kept when they lower the slots' wavefronts (the largest count
+//      of distinct indices in a bank, summed over the three gathers) or keep
+//      them and spread the indices more evenly over the banks.  Each warp's
+//      search draws from its own seeded stream, so the order does not depend
+//      on the host threads that run the warps in parallel.
+// On the 16^3 and 24^3 grids with 128 trials the mean wavefronts per gather
+// go from 3.0 (seeded order) to 1.85 (greedy) to about 1.55.
+namespace {
+
+struct BankSlot {
+    // per gather and bank: the distinct indices of the slot and how many
+    // lanes take each
     int cnt[3][32];
     int addr[3][32][32];
-    for (int g0 = 0; g0 < nv; g0 += K) {
-        const int kn = std::min(K, nv - g0);
-        std::fill(used.begin(), used.end(), 0);
-        for (int e = 0; e < HEt; e++) {
-            for (int g = 0; g < 3; g++)
-                for (int k = 0; k < 32; k++) cnt[g][k] = 0;
-            for (int lane = 0; lane < kn * tpn; lane++) {
-                const int nl = lane / tpn, t = lane % tpn, node = g0 + nl;
-                const size_t base = (size_t)node * M;
-                int best = -1, bestc = 1 << 30;
-                for (int k = 0; k < M && bestc > 0; k++) {
-                    if (used[(size_t)nl * M + k]) continue;
-                    const uint32_t w0 = idx[2 * (base + k)], w1 = idx[2 * (base + k) + 1];
-                    const int a[3] = {(int)(w0 & 0xffffu), (int)(w0 >> 16), (int)w1};
-                    int c = 0;
-                    for (int g = 0; g < 3; g++) {
-                        const int bk = a[g] & 31;
-                        bool seen = false;
-                        for (int q = 0; q < cnt[g][bk]; q++) seen = seen || addr[g][bk][q] == a[g];
-                        if (!seen) c += cnt[g][bk];
-                    }
-                    if (c < bestc) {
-                        bestc = c;
-                        best = k;
-                    }
+    int mult[3][32][32];
+    void clear()
+    {
+        for (int g = 0; g < 3; g++)
+            for (int k = 0; k < 32; k++) cnt[g][k] = 0;
+    }
+    void add(const int a3[3], int sgn)
+    {
+        for (int g = 0; g < 3; g++) {
+            const int a = a3[g], bk = a & 31;
+            int pos = -1;
+            for (int q = 0; q < cnt[g][bk]; q++)
+                if (addr[g][bk][q] == a) pos = q;
+            if (sgn > 0) {
+                if (pos < 0) {
+                    pos = cnt[g][bk]++;
+                    addr[g][bk][pos] = a;
+                    mult[g][bk][pos] = 0;
                 }
-                used[(size_t)nl * M + best] = 1;
-                const uint32_t w0 = idx[2 * (base + best)], w1 = idx[2 * (base + best) + 1];
-                const int a[3] = {(int)(w0 & 0xffffu), (int)(w0 >> 16), (int)w1};
-                for (int g = 0; g < 3; g++) {
-                    const int bk = a[g] & 31;
-                    bool seen = false;
-                    for (int q = 0; q < cnt[g][bk]; q++) seen = seen || addr[g][bk][q] == a[g];
-                    if (!seen) addr[g][bk][cnt[g][bk]++] = a[g];
-                }
-                const size_t dst = base + (size_t)t * HEt + e;
-                out_idx[2 * dst] = w0;
-                out_idx[2 * dst + 1] = w1;
-                out_b[dst] = b[base + best];
+                mult[g][bk][pos]++;
+            } else if (--mult[g][bk][pos] == 0) {
+                const int last = --cnt[g][bk];
+                addr[g][bk][pos] = addr[g][bk][last];
+                mult[g][bk][pos] = mult[g][bk][last];
             }
         }
     }
+    // wavefronts over the three gathers, and the sum of squared bank loads
+    void cost(int &w, int &sq) const
+    {
+        w = 0;
+        sq = 0;
+        for (int g = 0; g < 3; g++) {
+            int mx = 1;
+            for (int k = 0; k < 32; k++) {
+                mx = std::max(mx, cnt[g][k]);
+                sq += cnt[g][k] * cnt[g][k];
+            }
+            w += mx;
+        }
+    }
+    // distinct indices the trial would add to occupied banks
+    int added(const int a3[3]) const
+    {
+        int c = 0;
+        for (int g = 0; g < 3; g++) {
+            const int a = a3[g], bk = a & 31;
+            bool seen = false;
+            for (int q = 0; q < cnt[g][bk]; q++) seen = seen || addr[g][bk][q] == a;
+            if (!seen) c += cnt[g][bk];
+        }
+        return c;
+    }
+};
+
+inline uint64_t mix64(uint64_t x)
+{
+    x += 0x9e3779b97f4a7c15ull;
+    x = (x ^ (x >> 30)) * 0xbf58476d1ce4e5b9ull;
+    x = (x ^ (x >> 27)) * 0x94d049bb133111ebull;
+    return x ^ (x >> 31);
+}
+
+// The order of the warp whose first node is g0: ord[node * M + t * 32 + e] is
+// the trial (of that node) that lane t of the node takes at slot e.
+void order_warp(const std::vector<uint32_t> &idx, int nv, int M, int g0, int iters, std::vector<int> &ord)
+{
+    const int HEt = 32, tpn = M / HEt, K = 32 / tpn;
+    const int kn = std::min(K, nv - g0);
+    auto trial = [&](int nl, int k, int a3[3]) {
+        const size_t q = (size_t)(g0 + nl) * M + k;
+        const uint32_t w0 = idx[2 * q], w1 = idx[2 * q + 1];
+        a3[0] = (int)(w0 & 0xffffu);
+        a3[1] = (int)(w0 >> 16);
+        a3[2] = (int)w1;
+    };
+    std::vector<BankSlot> S(HEt);
+    std::vector<uint8_t> used((size_t)kn * M, 0);
+    int a3[3];
+    for (int e = 0; e < HEt; e++) {
+        S[e].clear();
+        for (int lane = 0; lane < kn * tpn; lane++) {
+            const int nl = lane / tpn, t = lane % tpn;
+            int best = -1, bestc = INT_MAX;
+            for (int k = 0; k < M && bestc > 0; k++) {
+                if (used[(size_t)nl * M + k]) continue;
+                trial(nl, k, a3);
+                const int c = S[e].added(a3);
+                if (c < bestc) {
+                    bestc = c;
+                    best = k;
+                }
+            }
+            used[(size_t)nl * M + best] = 1;
+            trial(nl, best, a3);
+            S[e].add(a3, +1);
+            ord[(size_t)(g0 + nl) * M + t * HEt + e] = best;
+        }
+    }
+    int W[32], Q[32];
+    for (int e = 0; e < HEt; e++) S[e].cost(W[e], Q[e]);
+    uint64_t st = mix64(0x5eed0000ull + (uint64_t)g0);
+    int b1[3], b2[3];
+    for (int it = 0; it < iters; it++) {
+        st = mix64(st);
+        const int nl = (int)(st % (uint64_t)kn);
+        const int p1 = (int)((st >> 20) % (uint64_t)M), p2 = (int)((st >> 40) % (uint64_t)M);
+        const int e1 = p1 % HEt, e2 = p2 % HEt;
+        if (e1 == e2) continue;
+        int *o1 = &ord[(size_t)(g0 + nl) * M + p1], *o2 = &ord[(size_t)(g0 + nl) * M + p2];
+        trial(nl, *o1, b1);
+        trial(nl, *o2, b2);
+        S[e1].add(b1, -1);
+        S[e2].add(b2, -1);
+        S[e1].add(b2, +1);
+        S[e2].add(b1, +1);
+        int w1, q1, w2, q2;
+        S[e1].cost(w1, q1);
+        S[e2].cost(w2, q2);
+        const int dw = w1 + w2 - W[e1] - W[e2], dq = q1 + q2 - Q[e1] - Q[e2];
+        if (dw < 0 || (dw == 0 && dq <= 0)) {
+            std::swap(*o1, *o2);
+            W[e1] = w1;
+            Q[e1] = q1;
+            W[e2] = w2;
+            Q[e2] = q2;
+        } else {
+            S[e1].add(b2, -1);
+            S[e2].add(b1, -1);
+            S[e1].add(b1, +1);
+            S[e2].add(b2, +1);
+        }
+    }
+}
+
+}  // namespace
+
+// idx/b: node-major tables as built; out_idx/out_b: the same entries in
+// device order.
+static void order_for_banks(const std::vector<uint32_t> &idx, const std::vector<float> &b, int nv, int M,
+                            std::vector<uint32_t> &out_idx, std::vector<float> &out_b)
+{
+    const int HEt = 32, tpn = M / HEt, K = 32 / tpn;
+    const int nwarps = (nv + K - 1) / K;
+    std::vector<int> ord((size_t)nv * M);
+    const int iters = 60 * M * K;  // ~60 tries per trial of the warp
+    const int nth = (int)std::max(1u, std::min(32u, std::thread::hardware_concurrency()));
+    std::atomic<int> next{0};
+    auto work = [&]() {
+        for (int w = next++; w < nwarps; w = next++) order_warp(idx, nv, M, w * K, iters, ord);
+    };
+    std::vector<std::thread> pool;
+    for (int i = 1; i < nth; i++) pool.emplace_back(work);
+    work();
+    for (auto &th : pool) th.join();
+    out_idx.assign(idx.size(), 0u);
+    out_b.assign(b.size(), 0.0f);
+    for (int node = 0; node < nv; node++)
+        for (int p = 0; p < M; p++) {
+            const size_t src = (size_t)node * M + ord[(size_t)node * M + p], dst = (size_t)node * M + p;
+            out_idx[2 * dst] = idx[2 * src];
+            out_idx[2 * dst + 1] = idx[2 * src + 1];
+            out_b[dst] = b[src];
+        }
 }
 
 void hs_free(HsTables &t, const DevFree &dfree)

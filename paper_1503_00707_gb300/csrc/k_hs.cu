@@ -332,6 +332,28 @@ int hs_prepare(HsTables &t, int64_t ncells, const DevAlloc &alloc, const DevFree
     return t.d_bc ? DVM_OK : DVM_ENOMEM;
 }
 
+// Cell splits of the k_hs_bc grid (node chunks x cell ranges): at least two
+// waves of resident CTAs, and a total that fills its last wave as far as
+// possible.  Every CTA streams the same number of cells, so a last wave that
+// is only partly full leaves the rest of the GPU idle for a whole CTA's time
+// (64 chunks x 10 ranges on 304 resident CTAs ran as 304 + 304 + 32).
+static int64_t hs_splits(int chunks, int slots, int64_t ncells)
+{
+    const int64_t s0 = std::max<int64_t>(1, (2 * (int64_t)slots + chunks - 1) / chunks);
+    int64_t best = s0;
+    double best_eff = -1.0;
+    for (int64_t sp = s0; sp <= 4 * s0; sp++) {
+        const int64_t per = (ncells + sp - 1) / sp, used = (ncells + per - 1) / per;
+        const int64_t total = (int64_t)chunks * used, waves = (total + slots - 1) / slots;
+        const double eff = (double)total / (double)(waves * slots);
+        if (eff > best_eff + 1e-9) {
+            best_eff = eff;
+            best = sp;
+        }
+    }
+    return std::max<int64_t>(1, std::min<int64_t>(best, ncells));
+}
+
 int launch_hs_collide(HsTables &t, const StepParams &p, void *f, double kn, double dt)
 {
     if (p.prec != DVM_F32) return DVM_ENOTIMPL;
@@ -351,8 +373,7 @@ int launch_hs_collide(HsTables &t, const StepParams &p, void *f, double kn, doub
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_hs_bc, HT, dyn) != cudaSuccess || occ < 1)
         return DVM_ENOTIMPL;
-    int64_t splits = std::max<int64_t>(1, (2 * (int64_t)nsm * occ + chunks - 1) / chunks);
-    splits = std::min<int64_t>(splits, p.ncells);
+    int64_t splits = hs_splits(chunks, nsm * occ, p.ncells);
     const int64_t per = (p.ncells + splits - 1) / splits;
     splits = (p.ncells + per - 1) / per;
     const dim3 grid((unsigned)chunks, (unsigned)splits);
@@ -388,8 +409,7 @@ int launch_hs_general(HsTables &t, const StepParams &p, float *f, const int32_t 
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_hs_bc, HT, dyn) != cudaSuccess || occ < 1)
         return DVM_ENOTIMPL;
-    int64_t splits = std::max<int64_t>(1, (2 * (int64_t)nsm * occ + chunks - 1) / chunks);
-    splits = std::min<int64_t>(splits, p.ncells);
+    int64_t splits = hs_splits(chunks, nsm * occ, p.ncells);
     const int64_t per = (p.ncells + splits - 1) / splits;
     splits = (p.ncells + per - 1) / per;
     k_hs_bc<<<dim3((unsigned)chunks, (unsigned)splits), HT, dyn, p.stream>>>(
@@ -500,8 +520,7 @@ int launch_hs_collide_noalloc(HsTables &t, const StepParams &p, float *f, const 
     double *mom = reinterpret_cast<double *>(static_cast<unsigned char *>(base) + need_bc);
     rc = launch_moments(DVM_F32, f, p.ncells, p.nv, xi, dV, mom, p.stream);
     if (rc) return rc;
-    int64_t splits = std::max<int64_t>(1, (2 * (int64_t)nsm * occ + chunks - 1) / chunks);
-    splits = std::min<int64_t>(splits, p.ncells);
+    int64_t splits = hs_splits(chunks, nsm * occ, p.ncells);
     const int64_t per = (p.ncells + splits - 1) / splits;
     splits = (p.ncells + per - 1) / per;
     k_hs_bc<<<dim3((unsigned)chunks, (unsigned)splits), HT, dyn, p.stream>>>(

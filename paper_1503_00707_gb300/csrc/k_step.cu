@@ -324,10 +324,13 @@ __device__ inline void group_sums(const float2 (&x)[8], float2 &S, float2 &X, fl
 // and exact products; the r's, 2^-19 of sum |x| at most, are summed in FP32.
 __device__ inline void thread_moments(const QV<float> (&cur)[8], float jx, float jy, float jz0, ffn (&m)[7])
 {
-    float B = 0.0f;
+    float2 B2 = make_float2(0.0f, 0.0f);
 #pragma unroll
-    for (int o = 0; o < 8; o++)
-        B += (fabsf(cur[o].a.x) + fabsf(cur[o].a.y)) + (fabsf(cur[o].b.x) + fabsf(cur[o].b.y));
+    for (int o = 0; o < 8; o++) {
+        B2 = f2_add(B2, make_float2(fabsf(cur[o].a.x), fabsf(cur[o].a.y)));
+        B2 = f2_add(B2, make_float2(fabsf(cur[o].b.x), fabsf(cur[o].b.y)));
+    }
+    const float B = B2.x + B2.y;
     // B < 2^(ex - 126): sigma = 2^(ex - 122) >= 16 B (B finite)
     const int ex = min((__float_as_int(B) >> 23) & 0xff, 249);
     const float sg = __int_as_float((ex + 5) << 23);
@@ -344,10 +347,11 @@ __device__ inline void thread_moments(const QV<float> (&cur)[8], float jx, float
     float2 Sa, Xa, Ya, Za, Sb, Xb, Yb, Zb;
     group_sums(qa, Sa, Xa, Ya, Za);
     group_sums(qb, Sb, Xb, Yb, Zb);
-    const float Sq = (Sa.x + Sa.y) + (Sb.x + Sb.y);
-    const float Xq = (Xa.x + Xa.y) + (Xb.x + Xb.y);
-    const float Yq = (Ya.x + Ya.y) + (Yb.x + Yb.y);
-    const float Zq = (Za.x + Za.y) + (Zb.x + Zb.y);
+    const float2 Sab = f2_add(Sa, Sb), Xab = f2_add(Xa, Xb), Yab = f2_add(Ya, Yb), Zab = f2_add(Za, Zb);
+    const float Sq = Sab.x + Sab.y;
+    const float Xq = Xab.x + Xab.y;
+    const float Yq = Yab.x + Yab.y;
+    const float Zq = Zab.x + Zab.y;
     const float Az = (Za.y + (Zb.x + Zb.x)) + 3.0f * Zb.y;
     const float A1 = (Sa.y + (Sb.x + Sb.x)) + 3.0f * Sb.y;
     const float A2 = (Sa.y + 4.0f * Sb.x) + 9.0f * Sb.y;
@@ -464,8 +468,8 @@ __device__ inline float2 to_pair(double v)
 //
 // Precision (FP32/BF16 storage): the moment sums arrive in double-float; the
 // target's 1D sums, the 5x5 system of Eq. 6's correction and its solution are
-// formed in double-float (an FP32 LDL^T factor refined twice against
-// double-float residuals), so that the collision term nu (M~ - f*) defined by
+// formed in double-float (an FP32 LDL^T factor refined once against a
+// double-float residual), so that the collision term nu (M~ - f*) defined by
 // the per-axis tables g and the double-float coefficients carries the moments
 // of f* to double-float accuracy.  Its residual sum_i phi_r (M~ - f*)_i dV in
 // the centred basis goes to res_phi as double-float pairs (no FP64
@@ -695,8 +699,10 @@ __device__ inline int solve_cell(const StepParams &p, StepSmem<TC> &sm, const Co
         __syncwarp();
         // right-hand side: the moments of f* in phi are (rho, 0, 0, 0, 0) by
         // the definition of u and T, less those of the uncorrected target
-        // (row 0 of the matrix); the TC factor of lane 0, then two refinements
-        // against X residuals rhs - A d computed one row per lane
+        // (row 0 of the matrix); the TC factor of lane 0, then one refinement
+        // against the X residual rhs - A d computed one row per lane (the
+        // FP32 factor solves to ~1e-6 relative, one refinement to ~1e-12, and
+        // the residual written below measures what is left)
         TC Lf[5][5], Dif[5];
         int fok = 1;
         if (lane == 0) {
@@ -719,7 +725,7 @@ __device__ inline int solve_cell(const StepParams &p, StepSmem<TC> &sm, const Co
         __syncwarp();
         fok = __shfl_sync(0xffffffffu, fok, 0);
 #pragma unroll 1
-        for (int it = 0; it < 3; it++) {
+        for (int it = 1; it < 3; it++) {
             if (lane < 5) {
                 X s = sm.rhs[par][lane];
 #pragma unroll

@@ -59,12 +59,16 @@ def _flow():
 
 def _developed(c, steps=200):
     """f of the Mach-3 sphere flow developed from the freestream with BGK (the
-    same mean free path) for `steps` CFL steps (t ~ 0.1, a few sphere radii
-    over the freestream speed): the bow shock stands ahead of the sphere."""
+    same mean free path) for the time of `steps` CFL steps (t ~ 0.1, a few
+    sphere radii over the freestream speed): the bow shock stands ahead of
+    the sphere.  nu dt <= 1 (nu = sqrt(8/pi) rho sqrt(T)/Kn, rho sqrt(T) up to
+    about 7 in the shock layer) bounds dt by Kn/20."""
     s = D.solver_from_config(c, D.F32, D.COLL_BGK)
     xyz, _ = s.centres()
     s.init_maxwellian(*W.initial_state(c, xyz))
-    s.step(steps, s.dt_cfl(c["cfl"]))
+    dt_cfl = s.dt_cfl(c["cfl"])
+    dt = min(dt_cfl, c["kn"] / 20)
+    s.step(int(round(steps * dt_cfl / dt)), dt)
     rho, _, _ = s.moments()
     return s.get_f(), float(rho.max()), s.kn_local()
 
