@@ -8,7 +8,11 @@ cells and a 24^3 velocity grid (1.40e10 f values, FP32 storage).  Also
 reported: the fraction of the measured HBM roofline reached by the step
 kernel, the same metric end to end through the C ABI with host buffers,
 the FP64 CPU oracle on the host cores (a bounded sample of the workload),
-and the SM clocks seen during the timed region.
+and the SM clocks seen during the timed region.  Further legs (each can be
+skipped): the FP32 fields against the oracle, BF16 storage, the same flow at
+Kn 0.1 and 1, the hard-sphere box with its gather roofline, the learned
+collision operator against the plain one from a developed flow, and the
+lattice Boltzmann flows.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -65,6 +69,7 @@ def parse():
     ap.add_argument("--hs-only", action="store_true", help="run only the hard-sphere box leg")
     ap.add_argument("--hs-steps", type=int, default=3)
     ap.add_argument("--no-bf16", action="store_true", help="skip the BF16-storage leg")
+    ap.add_argument("--no-kn-sweep", action="store_true", help="skip the Kn = 0.1 and 1 steps of the main flow")
     ap.add_argument("--bf16-steps", type=int, default=10)
     ap.add_argument("--learned-steps", type=int, default=5)
     ap.add_argument("--train-epochs", type=int, default=20,
@@ -808,6 +813,26 @@ def run_ours(args):
 
     f_gb = s.f_bytes() / 1e9
     s.close()
+    # the same flow at the other ends of the Kn range of the Mach-5 runs
+    # (0.01-1): the step does the same work, and nu dt stays below 1
+    kn_sweep = None
+    if rank == 0 and not args.no_kn_sweep:
+        kn_sweep = {}
+        for kn in (0.1, 1.0):
+            c2 = dict(cfg, kn=kn)
+            s2 = D.solver_from_config(c2, prec, coll, stream=stream)
+            x2, _ = s2.centres()
+            s2.init_maxwellian(*W.initial_state(c2, x2))
+            s2.step(3, dt)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            s2.step(5, dt)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms2 = e0.elapsed_time(e1) / 5
+            kn_sweep["kn=%g" % kn] = {"ms_per_step": ms2, "value": ncells * nv / (ms2 / 1e3), "unit": UNIT,
+                                      "steps": 5}
+            s2.close()
     field_err = None
     if rank == 0 and not args.no_cpu_baseline:
         field_err = oracle_field_errors(CPU_SAMPLE_CONFIG, args.precision, 2, lambda q: q.moments())
@@ -828,14 +853,14 @@ def run_ours(args):
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
             "config": {"workload": workload_desc(args.config, cfg, ncells, nv, args.precision, args.collision),
                        "cells": ncells, "velocities": nv, "f_values": ncells * nv,
                        "storage": args.precision, "parallelism": "replicas" if world > 1 else "single GPU",
                        "l2": "inputs larger than L2 (f is %.1f GB)" % f_gb},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
             "field_rel_linf_vs_oracle": field_err,
-            "learned_vs_plain": learned, "lbm": lbm, "hs_box": hs, "bf16": bf16,
+            "learned_vs_plain": learned, "lbm": lbm, "hs_box": hs, "bf16": bf16, "kn_sweep": kn_sweep,
         }
         print(json.dumps(line), flush=True)
     if world > 1:

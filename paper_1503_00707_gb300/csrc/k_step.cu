@@ -214,6 +214,9 @@ template <typename TC> struct StepSmem {
     X g1d[2][3][5];
     X sys[2][15];
     X rhs[2][5], dsol[2][5], resid[2][5];
+    // c_terms in shared memory: each lane of the matrix assembly reads its own
+    // entry, which a constant-memory load would serialise
+    int32_t terms[15][10];
 };
 
 template <typename TC> struct Consts {
@@ -683,7 +686,7 @@ __device__ inline int solve_cell(const StepParams &p, StepSmem<TC> &sm, const Co
                 const int en = lane < 15 ? lane : 14, t0 = lane == 15 ? 5 : 0;
 #pragma unroll 1
                 for (int t = t0; t < t0 + 5; t++) {
-                    const int32_t w = c_terms[en][t];
+                    const int32_t w = sm.terms[en][t];
                     const int cf = (int)(int8_t)(w & 0xff);
                     if (cf != 0) {
                         const X pr = sm.g1d[par][0][(w >> 8) & 15] * sm.g1d[par][1][(w >> 12) & 15] *
@@ -878,6 +881,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_step(const StepParams p)
         // come in its slot order) and the stencils of slots 0..3; the solver
         // warps fetch those of slot j + 4 while they solve cell j
         for (int k = 0; k < 4; k++) store(fetch(take()), k);
+        for (int i = lane; i < 150; i += 32) (&sm.terms[0][0])[i] = (&c_terms[0][0])[i];
         {
             const long long n4 = take();
             const long long n5 = take();
