@@ -226,73 +226,86 @@ __global__ void __launch_bounds__(CT, 2)
         if (lane == 0) S[k] = (double)a.hi + (double)a.lo;
     }
     __syncthreads();
-    if (tid == 0) {
-        double Aj[25], cj[5];
-        for (int r = 0, k = 0; r < 5; r++)
-            for (int s = r; s < 5; s++, k++) Aj[r * 5 + s] = Aj[s * 5 + r] = S[k];
-        for (int r = 0; r < 5; r++) cj[r] = S[15 + r];
+    if (warp == 0) {
+        // The 5x5 solve on the lanes of warp 0, in FP64.  phi = L psi^ with
+        //   phi_0 = 1, phi_d = be_d + al j_d, phi_4 = |be|^2 - 3 + 2 al be.j + al^2 |j|^2,
+        // al = (h/2)/sqrt(T), be = -u/sqrt(T); the system A^ e = c^ with
+        // e = (1, 0, 0, 0, 0) + L^T d is factored through the well-conditioned
+        // centred-basis matrix L A^ L^T (an LDL^T on lane 0) and refined twice
+        // against the residual of the exact sums.  Lane 5 r + s holds entry
+        // (r, s) of the 5x5 products; lanes 0..4 hold the vectors.
         const double isT = 1.0 / sqrt(Td), al = hh * isT;
-        const double be[3] = {-mo[1] * isT, -mo[2] * isT, -mo[3] * isT};
-        // phi = L psi^: phi_d = be_d + al j_d, phi_4 = |be|^2 - 3 + 2 al be.j + al^2 |j|^2
-        double L[25];
-        for (int k = 0; k < 25; k++) L[k] = 0.0;
-        L[0] = 1.0;
-        for (int d = 0; d < 3; d++) {
-            L[(1 + d) * 5] = be[d];
-            L[(1 + d) * 5 + 1 + d] = al;
-            L[20 + 1 + d] = 2.0 * al * be[d];
-        }
-        L[20] = be[0] * be[0] + be[1] * be[1] + be[2] * be[2] - 3.0;
-        L[24] = al * al;
-        // preconditioner L A^ L^T
-        double T1[25], Ap[25];
-        for (int r = 0; r < 5; r++)
-            for (int s = 0; s < 5; s++) {
-                double t = 0.0;
-                for (int k = 0; k < 5; k++) t += L[r * 5 + k] * Aj[k * 5 + s];
-                T1[r * 5 + s] = t;
+        const double be0 = -mo[1] * isT, be1 = -mo[2] * isT, be2 = -mo[3] * isT;
+        auto Lm = [&](int r, int k) -> double {
+            if (r == 0) return k == 0 ? 1.0 : 0.0;
+            if (r < 4) {
+                const double b = r == 1 ? be0 : (r == 2 ? be1 : be2);
+                return k == 0 ? b : (k == r ? al : 0.0);
             }
-        for (int r = 0; r < 5; r++)
-            for (int s = 0; s < 5; s++) {
-                double t = 0.0;
-                for (int k = 0; k < 5; k++) t += T1[r * 5 + k] * L[s * 5 + k];
-                Ap[r * 5 + s] = t;
-            }
-        double Lf[5][5], Di[5], d[5] = {0, 0, 0, 0, 0}, R[5];
-        const bool ok = ldl5<double>(Ap, Lf, Di);
+            if (k == 0) return be0 * be0 + be1 * be1 + be2 * be2 - 3.0;
+            if (k < 4) return 2.0 * al * (k == 1 ? be0 : (k == 2 ? be1 : be2));
+            return al * al;
+        };
+        // entry (r, s) of A^ (index of the upper-triangle sum)
+        auto Aj = [&](int r, int q) -> double {
+            const int lo = r < q ? r : q, hi = r < q ? q : r;
+            return S[lo * 5 - (lo * (lo - 1)) / 2 + (hi - lo)];
+        };
+        auto bcast = [](double v, int src) -> double { return __shfl_sync(0xffffffffu, v, src); };
+        const int r5 = lane < 25 ? lane / 5 : 0, s5 = lane < 25 ? lane % 5 : 0;
+        // T1 = L A^ (lane 5 r + s), then Ap = T1 L^T
+        double t1 = 0.0;
+#pragma unroll
+        for (int k = 0; k < 5; k++) t1 = fma(Lm(r5, k), Aj(k, s5), t1);
+        double ap = 0.0;
+#pragma unroll
+        for (int k = 0; k < 5; k++) ap = fma(bcast(t1, r5 * 5 + k), Lm(s5, k), ap);
+        double Ap[25];
+#pragma unroll
+        for (int k = 0; k < 25; k++) Ap[k] = bcast(ap, k);
+        double Lf[5][5], Di[5];
+        bool ok = true;
+        if (lane == 0) ok = ldl5<double>(Ap, Lf, Di);
+        ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+        // lane r < 5: d_r; every lane: the whole d after each broadcast
+        double d[5] = {0.0, 0.0, 0.0, 0.0, 0.0}, R = 0.0;
+        const int rv = lane < 5 ? lane : 0;
         for (int it = 0; it < 3; it++) {
-            // e = (1, 0, 0, 0, 0) + L^T d; R = c^ - A^ e
-            double e[5];
-            for (int s = 0; s < 5; s++) {
-                double t = s == 0 ? 1.0 : 0.0;
-                for (int k = 0; k < 5; k++) t += L[k * 5 + s] * d[k];
-                e[s] = t;
-            }
-            for (int r = 0; r < 5; r++) {
-                double t = cj[r];
-                for (int s = 0; s < 5; s++) t -= Aj[r * 5 + s] * e[s];
-                R[r] = t;
-            }
+            // e_s = (s == 0) + sum_k L_ks d_k on lane s, then R_r = c^_r - sum_s A^_rs e_s
+            double e = rv == 0 ? 1.0 : 0.0;
+#pragma unroll
+            for (int k = 0; k < 5; k++) e = fma(Lm(k, rv), d[k], e);
+            double ev[5];
+#pragma unroll
+            for (int k = 0; k < 5; k++) ev[k] = bcast(e, k);
+            R = S[15 + rv];
+#pragma unroll
+            for (int q = 0; q < 5; q++) R = fma(-Aj(rv, q), ev[q], R);
             if (it == 2 || !ok) break;
-            double LR[5], dl[5];
-            for (int r = 0; r < 5; r++) {
-                double t = 0.0;
-                for (int k = 0; k < 5; k++) t += L[r * 5 + k] * R[k];
-                LR[r] = t;
-            }
-            ldl5_solve<double>(Lf, Di, LR, dl);
-            for (int r = 0; r < 5; r++) d[r] += dl[r];
+            // LR = L R on lane r, then the LDL^T solve on lane 0
+            double Rv[5];
+#pragma unroll
+            for (int k = 0; k < 5; k++) Rv[k] = bcast(R, k);
+            double lr = 0.0;
+#pragma unroll
+            for (int k = 0; k < 5; k++) lr = fma(Lm(rv, k), Rv[k], lr);
+            double LR[5], dl[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+            for (int k = 0; k < 5; k++) LR[k] = bcast(lr, k);
+            if (lane == 0) ldl5_solve<double>(Lf, Di, LR, dl);
+#pragma unroll
+            for (int k = 0; k < 5; k++) d[k] += bcast(dl[k], 0);
         }
         bool fin = ok;
-        for (int r = 0; r < 5; r++) fin = fin && isfinite(d[r]);
-        if (!fin) {
-            atomicOr(status, ST_SINGULAR);
-            for (int r = 0; r < 5; r++) d[r] = 0.0;
-        }
-        for (int r = 0; r < 5; r++) sd[r] = (float)d[r];
-        if (res) {
-            const double sc[5] = {dV, dV * hh, dV * hh, dV * hh, dV * hh * hh};
-            for (int r = 0; r < 5; r++) res[cell * 5 + r] = fin ? sc[r] * R[r] : 0.0;
+#pragma unroll
+        for (int k = 0; k < 5; k++) fin = fin && isfinite(d[k]);
+        if (lane == 0 && !fin) atomicOr(status, ST_SINGULAR);
+        if (lane < 5) {
+            sd[lane] = fin ? (float)d[lane] : 0.0f;
+            if (res) {
+                const double sc = lane == 0 ? dV : (lane < 4 ? dV * hh : dV * hh * hh);
+                res[cell * 5 + lane] = fin ? sc * R : 0.0;
+            }
         }
     }
     __syncthreads();
