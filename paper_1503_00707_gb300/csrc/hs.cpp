@@ -383,6 +383,7 @@ int hs_build(HsTables &t, const int n[3], const double lo[3], const double h[3],
         jp[v] = w;
     }
     t.hh = 0.5 * h[0];
+    for (int d = 0; d < 3; d++) t.half[d] = n[d] / 2;
     t.d_idx = alloc(t.host_idx.size() * 4);
     t.d_b = static_cast<float *>(alloc(t.host_b.size() * 4));
     t.d_xi = static_cast<float *>(alloc(xf.size() * 4));

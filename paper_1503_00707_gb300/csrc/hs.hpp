@@ -26,6 +26,7 @@ struct HsTables {
     float *d_xi = nullptr;            // node velocities [3][nv], FP32
     uint32_t *d_jpk = nullptr;        // per node: xi_d = hh j_d, j_d odd, packed as bytes j_d + 64
     double hh = 0.0;                  // half the velocity spacing (the same on every axis)
+    int half[3] = {0, 0, 0};          // nodes per axis / 2 (the grid's sign-group shape)
     float *d_bc = nullptr;            // scratch: B and C of every cell [ncells][nv][2]
     int64_t bc_cells = 0;
 };

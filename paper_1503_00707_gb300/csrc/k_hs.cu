@@ -166,8 +166,8 @@ constexpr int NSUM = 20;  // 15 distinct entries of the moment matrix, 5 gain mo
 __global__ void __launch_bounds__(CT, 2)
     k_hs_corr(float *__restrict__ f, const float2 *__restrict__ bc, const float *__restrict__ xi3,
               const uint32_t *__restrict__ jpk, double hh, double dV, const double *__restrict__ mom, int nv,
-              float dtkn, const int32_t *__restrict__ list, const int *__restrict__ count, float *__restrict__ q_out,
-              double *__restrict__ res, int *status)
+              int3 half, float dtkn, const int32_t *__restrict__ list, const int *__restrict__ count,
+              float *__restrict__ q_out, double *__restrict__ res, int *status)
 {
     __shared__ ffn part[NSUM][CT];
     __shared__ double S[NSUM];
@@ -190,23 +190,72 @@ __global__ void __launch_bounds__(CT, 2)
     }
     float *fc = f + cell * (int64_t)nv;
     const float2 *bcc = bc + row * (int64_t)nv;
+    // The sums over the nodes, pencil by pencil: a pencil is the line of nodes
+    // along z at fixed (x, y) node indices, both z signs (sign groups 2 o_xy
+    // and 2 o_xy + 1, positions pos .. pos + hz - 1 in each).  Along a pencil
+    // j_x = a and j_y = b are fixed, so with W_k = sum f B j_z^k (k <= 4) and
+    // C_k = sum C j_z^k (k <= 2), s2 = a^2 + b^2, every sum of the system is a
+    // combination of the pencil sums with integer coefficients, e.g.
+    //   sum f B |j|^2 = s2 W_0 + W_2,  sum f B |j|^4 = s2^2 W_0 + 2 s2 W_2 + W_4.
+    // Products by integers below 2^24 split exactly (FMA), so the sums stay
+    // Sum2-exact, at 8 accumulations per node and 27 per pencil instead of
+    // 20 per node.  The entries are numbered as the upper triangle of the 5x5
+    // matrix over (1, j_x, j_y, j_z, |j|^2), then the 5 right-hand sums.
     Acc2 acc[NSUM];
 #pragma unroll
     for (int k = 0; k < NSUM; k++) acc[k] = Acc2{0.0f, 0.0f};
-    for (int v = tid; v < nv; v += CT) {
-        const float fv = fc[v];
-        const float2 q = bcc[v];
-        const uint32_t jp = jpk[v];
-        const float jx = (float)((int)(jp & 0xffu) - 64), jy = (float)((int)((jp >> 8) & 0xffu) - 64),
-                    jz = (float)((int)((jp >> 16) & 0xffu) - 64);
-        const float wv[5] = {1.0f, jx, jy, jz, jx * jx + jy * jy + jz * jz};
-        const float w = fv * q.x, wl = fmaf(fv, q.x, -w);  // f B = w + wl exactly
+    const int hxy = half.x * half.y, P = hxy * half.z, npen = 4 * hxy;
+    for (int pen = tid; pen < npen; pen += CT) {
+        const int oxy = pen / hxy, pos = (pen - oxy * hxy) * half.z;
+        const uint32_t jp0 = jpk[2 * oxy * P + pos];
+        const float a = (float)((int)(jp0 & 0xffu) - 64), b = (float)((int)((jp0 >> 8) & 0xffu) - 64);
+        Acc2 W[5], Cs[3];
 #pragma unroll
-        for (int r = 0, k = 0; r < 5; r++) {
+        for (int k = 0; k < 5; k++) W[k] = Acc2{0.0f, 0.0f};
 #pragma unroll
-            for (int s = r; s < 5; s++, k++) acc2_prod(acc[k], w, wl, wv[r] * wv[s]);
-            acc2_prod(acc[15 + r], q.y, 0.0f, wv[r]);
+        for (int k = 0; k < 3; k++) Cs[k] = Acc2{0.0f, 0.0f};
+#pragma unroll
+        for (int oz = 0; oz < 2; oz++) {
+            const int v0 = (2 * oxy + oz) * P + pos;
+            for (int m = 0; m < half.z; m++) {
+                const int v = v0 + m;
+                const float fv = fc[v];
+                const float2 q = bcc[v];
+                const float jz = (float)((int)((jpk[v] >> 16) & 0xffu) - 64);
+                const float jz2 = jz * jz;
+                const float w = fv * q.x, wl = fmaf(fv, q.x, -w);  // f B = w + wl exactly
+                acc2_prod(W[0], w, wl, 1.0f);
+                acc2_prod(W[1], w, wl, jz);
+                acc2_prod(W[2], w, wl, jz2);
+                acc2_prod(W[3], w, wl, jz2 * jz);
+                acc2_prod(W[4], w, wl, jz2 * jz2);
+                acc2_prod(Cs[0], q.y, 0.0f, 1.0f);
+                acc2_prod(Cs[1], q.y, 0.0f, jz);
+                acc2_prod(Cs[2], q.y, 0.0f, jz2);
+            }
         }
+        const float s2 = a * a + b * b;
+        auto put = [&](int k, const Acc2 &x, float coef) { acc2_prod(acc[k], x.s, x.e, coef); };
+        put(0, W[0], 1.0f);                                         // (1, 1)
+        put(1, W[0], a);                                            // (1, j_x)
+        put(2, W[0], b);                                            // (1, j_y)
+        put(3, W[1], 1.0f);                                         // (1, j_z)
+        put(4, W[0], s2); put(4, W[2], 1.0f);                       // (1, |j|^2)
+        put(5, W[0], a * a);                                        // (j_x, j_x)
+        put(6, W[0], a * b);                                        // (j_x, j_y)
+        put(7, W[1], a);                                            // (j_x, j_z)
+        put(8, W[0], a * s2); put(8, W[2], a);                      // (j_x, |j|^2)
+        put(9, W[0], b * b);                                        // (j_y, j_y)
+        put(10, W[1], b);                                           // (j_y, j_z)
+        put(11, W[0], b * s2); put(11, W[2], b);                    // (j_y, |j|^2)
+        put(12, W[2], 1.0f);                                        // (j_z, j_z)
+        put(13, W[1], s2); put(13, W[3], 1.0f);                     // (j_z, |j|^2)
+        put(14, W[0], s2 * s2); put(14, W[2], 2.0f * s2); put(14, W[4], 1.0f);  // (|j|^2, |j|^2)
+        put(15, Cs[0], 1.0f);
+        put(16, Cs[0], a);
+        put(17, Cs[0], b);
+        put(18, Cs[1], 1.0f);
+        put(19, Cs[0], s2); put(19, Cs[2], 1.0f);
     }
 #pragma unroll
     for (int k = 0; k < NSUM; k++) {
@@ -397,8 +446,9 @@ int launch_hs_collide(HsTables &t, const StepParams &p, void *f, double kn, doub
     if (cudaGetLastError() != cudaSuccess) return DVM_ECUDA;
     k_hs_corr<<<(unsigned)p.ncells, CT, 0, p.stream>>>(static_cast<float *>(f),
                                                       reinterpret_cast<const float2 *>(t.d_bc), t.d_xi, t.d_jpk,
-                                                      t.hh, p.dV, p.mom_out, p.nv, (float)(dt / kn), nullptr,
-                                                      nullptr, nullptr, p.res_out, p.status);
+                                                      t.hh, p.dV, p.mom_out, p.nv,
+                                                      make_int3(t.half[0], t.half[1], t.half[2]), (float)(dt / kn),
+                                                      nullptr, nullptr, nullptr, p.res_out, p.status);
     count_launch();
     return cudaGetLastError() == cudaSuccess ? DVM_OK : DVM_ECUDA;
 }
@@ -432,6 +482,7 @@ int launch_hs_general(HsTables &t, const StepParams &p, float *f, const int32_t 
     if (cudaGetLastError() != cudaSuccess) return DVM_ECUDA;
     k_hs_corr<<<(unsigned)p.ncells, CT, 0, p.stream>>>(f, reinterpret_cast<const float2 *>(t.d_bc), t.d_xi,
                                                       t.d_jpk, t.hh, p.dV, p.mom_out, p.nv,
+                                                      make_int3(t.half[0], t.half[1], t.half[2]),
                                                       q_out ? 0.0f : (float)(dt / kn), list, count, q_out,
                                                       q_out ? nullptr : p.res_out, p.status);
     count_launch();
@@ -542,8 +593,8 @@ int launch_hs_collide_noalloc(HsTables &t, const StepParams &p, float *f, const 
     count_launch();
     if (cudaGetLastError() != cudaSuccess) return DVM_ECUDA;
     k_hs_corr<<<(unsigned)p.ncells, CT, 0, p.stream>>>(f, reinterpret_cast<const float2 *>(bc), t.d_xi, t.d_jpk,
-                                                      t.hh, dV, mom, p.nv, (float)(dt / kn), nullptr, nullptr,
-                                                      nullptr, nullptr, p.status);
+                                                      t.hh, dV, mom, p.nv, make_int3(t.half[0], t.half[1], t.half[2]),
+                                                      (float)(dt / kn), nullptr, nullptr, nullptr, nullptr, p.status);
     count_launch();
     return cudaGetLastError() == cudaSuccess ? DVM_OK : DVM_ECUDA;
 }
