@@ -50,6 +50,7 @@ struct GemmArgs {
     int64_t ldt;
     int act;                // 0 none, 1 SiLU
     int *status;
+    int vec;                // set by gemm(): Cf and H rows take 16-byte vector stores
 };
 
 __device__ inline float silu(float x) { return x / (1.0f + __expf(-x)); }
@@ -127,7 +128,35 @@ __global__ void __launch_bounds__(GT) k_gemm(const GemmArgs g)
         for (int col = 0; col < g.N; col += 16) {
             float v[16];
             tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)col, v);
-            if (row < g.M) {
+            if (row < g.M && g.vec) {
+                // the thread's 16 values of its row: contiguous in Cf and H,
+                // so each goes out as 16-byte stores (a column of HT, across
+                // the warp's rows, is contiguous as it is)
+                float z[16];
+                uint32_t hp[8];
+#pragma unroll
+                for (int j = 0; j < 16; j++) z[j] = v[j] + (g.bias ? g.bias[col + j] : 0.0f);
+#pragma unroll
+                for (int j = 0; j < 16; j += 2) {
+                    const float h0 = g.act ? silu(z[j]) : z[j], h1 = g.act ? silu(z[j + 1]) : z[j + 1];
+                    const __nv_bfloat162 p2 = __floats2bfloat162_rn(h0, h1);
+                    hp[j / 2] = *reinterpret_cast<const uint32_t *>(&p2);
+                    if (g.HT) {
+                        g.HT[(int64_t)(col + j) * g.ldt + row] = p2.x;
+                        g.HT[(int64_t)(col + j + 1) * g.ldt + row] = p2.y;
+                    }
+                }
+                if (g.Cf) {
+                    float4 *d = reinterpret_cast<float4 *>(g.Cf + row * g.ldc + col);
+#pragma unroll
+                    for (int q = 0; q < 4; q++) d[q] = make_float4(z[4 * q], z[4 * q + 1], z[4 * q + 2], z[4 * q + 3]);
+                }
+                if (g.H) {
+                    uint4 *d = reinterpret_cast<uint4 *>(g.H + row * g.ldh + col);
+                    d[0] = make_uint4(hp[0], hp[1], hp[2], hp[3]);
+                    d[1] = make_uint4(hp[4], hp[5], hp[6], hp[7]);
+                }
+            } else if (row < g.M) {
 #pragma unroll
                 for (int j = 0; j < 16; j++) {
                     float z = v[j] + (g.bias ? g.bias[col + j] : 0.0f);
@@ -147,9 +176,12 @@ __global__ void __launch_bounds__(GT) k_gemm(const GemmArgs g)
     if (warp == 0) tmem_dealloc(tmem, ncols);
 }
 
-int gemm(const GemmArgs &g, cudaStream_t s)
+int gemm(const GemmArgs &g0, cudaStream_t s)
 {
+    GemmArgs g = g0;
     if (g.M <= 0) return DVM_OK;
+    g.vec = (reinterpret_cast<uintptr_t>(g.Cf) % 16 == 0 && g.ldc % 4 == 0 &&
+             reinterpret_cast<uintptr_t>(g.H) % 16 == 0 && g.ldh % 8 == 0) ? 1 : 0;
     if (g.K % 64 || g.N % 16 || g.N < 16 || g.N > 256) return DVM_EINVAL;
     const size_t dyn = 2 * (size_t)(STAGE_A + (uint32_t)g.N * 128u) + 1024;
     static bool configured = false;
