@@ -174,7 +174,11 @@ __global__ void __launch_bounds__(PT) k_proj(const float *__restrict__ f, const 
     const double *mo = mom + cell * 5;
     const double rho = mo[0], T = mo[4];
     const float u[3] = {(float)mo[1], (float)mo[2], (float)mo[3]};
-    const float ist = T > 0.0 ? (float)(1.0 / sqrt(T)) : 0.0f;
+    // 1/sqrt(T) in FP64 once, for the CTA
+    __shared__ float ist_s;
+    if (tid == 0) ist_s = T > 0.0 ? (float)(1.0 / sqrt(T)) : 0.0f;
+    __syncthreads();
+    const float ist = ist_s;
     axis_tables(amag, n, u, ist, H, nullptr, tid, PT);
     if (!tile_arrived(&bar, &abort_flag, status)) return;  // includes a barrier
     if (out_eq && tid < 12) {
@@ -270,6 +274,8 @@ __global__ void __launch_bounds__(AT) k_lapply(float *__restrict__ f, const doub
     __shared__ int good;
     __shared__ __align__(8) uint64_t bar;
     __shared__ int abort_flag;
+    __shared__ double pro_d[2];  // sqrt(T), Mc
+    __shared__ float pro_f[4];   // 1/sqrt(T), Mc, ln Mc, rho sqrt(T)
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t cell = blockIdx.x;
@@ -291,19 +297,28 @@ __global__ void __launch_bounds__(AT) k_lapply(float *__restrict__ f, const doub
         mbar_fence_init();
     }
     __syncthreads();
-    if (tid == 0) {
-        mbar_expect_tx(&bar, bytes);
-        bulk_g2s(tile, f + cell * nv, bytes, &bar);
-    }
     const double *mo = mom + cell * 5;
     const double rho = mo[0], T = mo[4];
     const bool valid = rho > 0.0 && T > 0.0 && isfinite(rho) && isfinite(T);
-    const double sq = valid ? sqrt(T) : 1.0;
-    const float u[3] = {(float)mo[1], (float)mo[2], (float)mo[3]};
-    const float ist = (float)(1.0 / sq);
-    const double Mc = valid ? rho * 0.06349363593424097 / (T * sq) : 1.0;  // rho (2 pi T)^(-3/2)
-    const float Mcf = (float)Mc, lnMc = (float)log(Mc), rsq = (float)(rho * sq);
+    if (tid == 0) {
+        mbar_expect_tx(&bar, bytes);
+        bulk_g2s(tile, f + cell * nv, bytes, &bar);
+        // the FP64 scalars of the cell, once (FP64 runs at a small fraction
+        // of the FP32 rate on this GPU)
+        const double sq0 = valid ? sqrt(T) : 1.0;
+        const double Mc0 = valid ? rho * 0.06349363593424097 / (T * sq0) : 1.0;  // rho (2 pi T)^(-3/2)
+        pro_d[0] = sq0;
+        pro_d[1] = Mc0;
+        pro_f[0] = (float)(1.0 / sq0);
+        pro_f[1] = (float)Mc0;
+        pro_f[2] = (float)log(Mc0);
+        pro_f[3] = (float)(rho * sq0);
+    }
     if (tid < 64) os[tid] = o[cell * 64 + tid] - (o_eq ? o_eq[cell * 64 + tid] : 0.0f);
+    __syncthreads();
+    const double sq = pro_d[0], Mc = pro_d[1];
+    const float u[3] = {(float)mo[1], (float)mo[2], (float)mo[3]};
+    const float ist = pro_f[0], Mcf = pro_f[1], lnMc = pro_f[2], rsq = pro_f[3];
     axis_tables(amag, n, u, ist, H, G, tid, AT);
     __syncthreads();
     const int nz = n.z;
