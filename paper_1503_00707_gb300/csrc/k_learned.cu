@@ -174,9 +174,16 @@ __global__ void __launch_bounds__(PT) k_proj(const float *__restrict__ f, const 
     const double *mo = mom + cell * 5;
     const double rho = mo[0], T = mo[4];
     const float u[3] = {(float)mo[1], (float)mo[2], (float)mo[3]};
-    // 1/sqrt(T) in FP64 once, for the CTA
+    // the FP64 scalars once, for the CTA: 1/sqrt(T), the output scale and the
+    // Maxwellian's prefactor dV (2 pi T)^(-3/2)
     __shared__ float ist_s;
-    if (tid == 0) ist_s = T > 0.0 ? (float)(1.0 / sqrt(T)) : 0.0f;
+    __shared__ double scale_s, pre_s;
+    if (tid == 0) {
+        const double sqT = sqrt(T);
+        ist_s = T > 0.0 ? (float)(1.0 / sqT) : 0.0f;
+        scale_s = MODE == 0 ? dV / rho : dV / (rho * rho * sqT);
+        pre_s = dV * 0.06349363593424097 / (T * sqT);
+    }
     __syncthreads();
     const float ist = ist_s;
     axis_tables(amag, n, u, ist, H, nullptr, tid, PT);
@@ -240,13 +247,11 @@ __global__ void __launch_bounds__(PT) k_proj(const float *__restrict__ f, const 
         float s = 0.0f;
 #pragma unroll
         for (int w = 0; w < PT / 32; w++) s += red[w][tid];
-        const double scale = MODE == 0 ? dV / rho : dV / (rho * rho * sqrt(T));
-        out[row * 64 + tid] = (float)((double)s * scale);
+        out[row * 64 + tid] = (float)((double)s * scale_s);
         if (out_eq) {
             // a of M(rho, u, T) sampled at the nodes: dV (2 pi T)^(-3/2) times
             // the product of per-axis sums
-            const double pre = dV * 0.06349363593424097 / (T * sqrt(T));
-            out_eq[row * 64 + tid] = (float)(pre * (double)gsum[0][tid >> 4] * (double)gsum[1][(tid >> 2) & 3] *
+            out_eq[row * 64 + tid] = (float)(pre_s * (double)gsum[0][tid >> 4] * (double)gsum[1][(tid >> 2) & 3] *
                                              (double)gsum[2][tid & 3]);
         }
     }
@@ -323,28 +328,34 @@ __global__ void __launch_bounds__(AT) k_lapply(float *__restrict__ f, const doub
     __syncthreads();
     const int nz = n.z;
     // per-axis sums: E_k = sum e c^k (k < 5), G_ak = sum e He_a c^k (a = 1..3,
-    // k < 3), in FP64 over the FP32 table values: the term these tables define
-    // then has its moments, and the correction below closes them, to FP64
-    // rounding
+    // k < 3), in double-float over the FP32 table values (products of FP32
+    // numbers split exactly by FMA; FP64 would run on this GPU's narrow FP64
+    // pipe): the term these tables define then has its moments, and the
+    // correction below closes them, to double-float rounding
     if (tid < 42) {
         const int d = tid / 14, k = tid % 14;
         const int nd = d == 0 ? n.x : (d == 1 ? n.y : n.z);
-        double s = 0.0;
+        ffn s{0.0f, 0.0f};
         for (int i = 0; i < nd; i++) {
             const float4 h = H[d][i];
-            const double c = (double)G[d][i];
-            double t;
+            const float c = G[d][i];
+            int pw;
+            float w0;
             if (k < 5) {
-                t = (double)h.w;
-                for (int q = 0; q < k; q++) t *= c;
+                w0 = h.w;
+                pw = k;
             } else {
-                const int a = (k - 5) / 3, kk = (k - 5) % 3;
-                t = (double)h.w * (double)(a == 0 ? h.x : (a == 1 ? h.y : h.z));
-                for (int q = 0; q < kk; q++) t *= c;
+                const int a = (k - 5) / 3;
+                w0 = a == 0 ? h.x : (a == 1 ? h.y : h.z);
+                pw = (k - 5) % 3;
             }
-            s += t;
+            // t = e (or e He_a) times c^pw, as a double-float product
+            const float p0 = k < 5 ? w0 : h.w * w0;
+            ffn t{p0, k < 5 ? 0.0f : fmaf(h.w, w0, -p0)};
+            for (int q = 0; q < pw; q++) t = t * c;
+            s = s + t;
         }
-        sums[d][k] = s;
+        sums[d][k] = (double)s.hi + (double)s.lo;
     }
     // S1[4a+b][iz] = sum_c o_abc He_c(iz)
     for (int idx = tid; idx < 16 * nz; idx += AT) {
@@ -509,15 +520,16 @@ __global__ void __launch_bounds__(AT) k_lapply(float *__restrict__ f, const doub
                 }
             });
     }
-    double e64 = (double)ent, q64 = (double)qabs;
+    // warp sums in FP32 (their rounding is far below the gate's 1e-5), the
+    // eight warp totals in FP64
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
-        e64 += __shfl_xor_sync(0xffffffffu, e64, off);
-        q64 += __shfl_xor_sync(0xffffffffu, q64, off);
+        ent += __shfl_xor_sync(0xffffffffu, ent, off);
+        qabs += __shfl_xor_sync(0xffffffffu, qabs, off);
     }
     if (lane == 0) {
-        ered[warp] = e64;
-        qred[warp] = q64;
+        ered[warp] = (double)ent;
+        qred[warp] = (double)qabs;
     }
     __syncthreads();
     if (tid == 0) {
