@@ -142,6 +142,31 @@ __device__ inline bool tile_arrived(uint64_t *bar, int *abort, int *status)
     return true;
 }
 
+// The 15 distinct entries (r <= s) of the moment matrix of the target in the
+// centred basis phi = (1, c_x, c_y, c_z, |c|^2 - 3) as sums of products of the
+// per-axis sums X[a] Y[b] Z[c] (E_k of axis d): each term packed as
+// coef (signed byte) | a << 8 | b << 12 | c << 16; coef 0 pads.
+#define DVM_LT(cf, a, b, c) ((int32_t)((cf) & 0xff) | ((a) << 8) | ((b) << 12) | ((c) << 16))
+__device__ const int32_t lt_terms[15][10] = {
+    {DVM_LT(1, 0, 0, 0)},
+    {DVM_LT(1, 1, 0, 0)},
+    {DVM_LT(1, 0, 1, 0)},
+    {DVM_LT(1, 0, 0, 1)},
+    {DVM_LT(1, 2, 0, 0), DVM_LT(1, 0, 2, 0), DVM_LT(1, 0, 0, 2), DVM_LT(-3, 0, 0, 0)},
+    {DVM_LT(1, 2, 0, 0)},
+    {DVM_LT(1, 1, 1, 0)},
+    {DVM_LT(1, 1, 0, 1)},
+    {DVM_LT(1, 3, 0, 0), DVM_LT(1, 1, 2, 0), DVM_LT(1, 1, 0, 2), DVM_LT(-3, 1, 0, 0)},
+    {DVM_LT(1, 0, 2, 0)},
+    {DVM_LT(1, 0, 1, 1)},
+    {DVM_LT(1, 2, 1, 0), DVM_LT(1, 0, 3, 0), DVM_LT(1, 0, 1, 2), DVM_LT(-3, 0, 1, 0)},
+    {DVM_LT(1, 0, 0, 2)},
+    {DVM_LT(1, 2, 0, 1), DVM_LT(1, 0, 2, 1), DVM_LT(1, 0, 0, 3), DVM_LT(-3, 0, 0, 1)},
+    {DVM_LT(1, 4, 0, 0), DVM_LT(1, 0, 4, 0), DVM_LT(1, 0, 0, 4), DVM_LT(2, 2, 2, 0), DVM_LT(2, 2, 0, 2),
+     DVM_LT(2, 0, 2, 2), DVM_LT(-6, 2, 0, 0), DVM_LT(-6, 0, 2, 0), DVM_LT(-6, 0, 0, 2), DVM_LT(9, 0, 0, 0)},
+};
+#undef DVM_LT
+
 // ---------------------------------------------------------------- projection
 template <int MODE>
 __global__ void __launch_bounds__(PT) k_proj(const float *__restrict__ f, const double *__restrict__ mom,
@@ -403,67 +428,95 @@ __global__ void __launch_bounds__(AT) k_lapply(float *__restrict__ f, const doub
             for (int k = 0; k < 5; k++) rred[warp][k] = r[k];
     }
     __syncthreads();
-    if (tid == 0) {
-        // the moment system over dV Mc: A_rs = sum e phi_r phi_s from per-axis sums
-        double X[5], Y[5], Z[5];
-        for (int k = 0; k < 5; k++) { X[k] = sums[0][k]; Y[k] = sums[1][k]; Z[k] = sums[2][k]; }
-        double A[25], rhs[5], x[5];
-        const double a00 = X[0] * Y[0] * Z[0];
-        const double s2 = X[2] * Y[0] * Z[0] + X[0] * Y[2] * Z[0] + X[0] * Y[0] * Z[2];
-        A[0] = a00;
-        A[1] = X[1] * Y[0] * Z[0];
-        A[2] = X[0] * Y[1] * Z[0];
-        A[3] = X[0] * Y[0] * Z[1];
-        A[4] = s2 - 3.0 * a00;
-        A[6] = X[2] * Y[0] * Z[0];
-        A[7] = X[1] * Y[1] * Z[0];
-        A[8] = X[1] * Y[0] * Z[1];
-        A[9] = X[3] * Y[0] * Z[0] + X[1] * Y[2] * Z[0] + X[1] * Y[0] * Z[2] - 3.0 * A[1];
-        A[12] = X[0] * Y[2] * Z[0];
-        A[13] = X[0] * Y[1] * Z[1];
-        A[14] = X[2] * Y[1] * Z[0] + X[0] * Y[3] * Z[0] + X[0] * Y[1] * Z[2] - 3.0 * A[2];
-        A[18] = X[0] * Y[0] * Z[2];
-        A[19] = X[2] * Y[0] * Z[1] + X[0] * Y[2] * Z[1] + X[0] * Y[0] * Z[3] - 3.0 * A[3];
-        A[24] = X[4] * Y[0] * Z[0] + X[0] * Y[4] * Z[0] + X[0] * Y[0] * Z[4] +
-                2.0 * (X[2] * Y[2] * Z[0] + X[2] * Y[0] * Z[2] + X[0] * Y[2] * Z[2]) - 6.0 * s2 + 9.0 * a00;
-        for (int r = 0; r < 5; r++)
-            for (int c = 0; c < r; c++) A[r * 5 + c] = A[c * 5 + r];
-        for (int r = 0; r < 5; r++) rhs[r] = (double)rsq * (rred[0][r] + rred[1][r]);
-        double A0[25], b0[5];
-        for (int k = 0; k < 25; k++) A0[k] = A[k];
-        for (int k = 0; k < 5; k++) b0[k] = rhs[k];
-        bool ok = valid && solve5<double>(A, rhs, x);
-        if (ok) {
-            // conservation residual of the correction, in FP64
-            double rn = 0.0, sc = 0.0, rv[5];
-            for (int r = 0; r < 5; r++) {
-                double s = -b0[r], t = fabs(b0[r]);
-                for (int c = 0; c < 5; c++) {
-                    s += A0[r * 5 + c] * x[c];
-                    t += fabs(A0[r * 5 + c] * x[c]);
-                }
-                rv[r] = -s;
-                rn = fmax(rn, fabs(s));
-                sc = fmax(sc, t);
-            }
-            ok = rn <= 1e-12 * sc;
-            if (ok && res) {
-                // sum_i phi_r Q_i dV = dV Mc (rhs - A d), taken to
-                // psi = (1, xi, |xi|^2) with xi = sqrt(T) c + u
-                const double k = dV * Mc, uu[3] = {mo[1], mo[2], mo[3]};
-                double o5[5], dot = 0.0, u2 = 0.0;
-                o5[0] = k * rv[0];
-                for (int d = 0; d < 3; d++) {
-                    o5[1 + d] = k * (sq * rv[1 + d] + uu[d] * rv[0]);
-                    dot += uu[d] * rv[1 + d];
-                    u2 += uu[d] * uu[d];
-                }
-                o5[4] = k * (T * (rv[4] + 3.0 * rv[0]) + 2.0 * sq * dot + u2 * rv[0]);
-                for (int r = 0; r < 5; r++) res[cell * 5 + r] = o5[r];
+    if (warp == 0) {
+        // The moment system over dV Mc, A_rs = sum e phi_r phi_s, from the
+        // per-axis sums: entry r <= s on lane sym(r, s) as a sum of products
+        // X[a] Y[b] Z[c] with integer coefficients (lt_terms), then the 5x5
+        // solve: an FP32 LDL^T factor on lane 0 refined twice against FP64
+        // residuals computed one row per lane (the system is symmetric
+        // positive definite and well conditioned), its FP64 residual checked
+        // against 1e-12 of its scale.  FP64 stays on few instructions: this
+        // GPU's FP64 pipe takes about 32 cycles per warp instruction.
+        double ae = 0.0;
+        if (lane < 15) {
+#pragma unroll 1
+            for (int t = 0; t < 10; t++) {
+                const int32_t w = lt_terms[lane][t];
+                const int cf = (int)(int8_t)(w & 0xff);
+                if (cf != 0)
+                    ae = fma((double)cf, sums[0][(w >> 8) & 15] * sums[1][(w >> 12) & 15] * sums[2][(w >> 16) & 15],
+                             ae);
             }
         }
-        for (int k = 0; k < 5; k++) cc[k] = ok ? x[k] : 0.0;
-        good = ok ? 1 : 0;
+        auto sym = [](int r, int q) {
+            const int lo = r < q ? r : q, hi = r < q ? q : r;
+            return lo * 5 - (lo * (lo - 1)) / 2 + (hi - lo);
+        };
+        const int rv = lane < 5 ? lane : 0;
+        double Arow[5];  // row rv of A
+#pragma unroll
+        for (int q = 0; q < 5; q++) Arow[q] = __shfl_sync(0xffffffffu, ae, sym(rv, q));
+        const double b0 = (double)rsq * (rred[0][rv] + rred[1][rv]);
+        // the FP32 factor on lane 0
+        float Af[25];
+#pragma unroll
+        for (int e = 0; e < 25; e++) Af[e] = (float)__shfl_sync(0xffffffffu, ae, sym(e / 5, e % 5));
+        float Lf[5][5], Dif[5];
+        bool ok = valid;
+        if (lane == 0) ok = ok && ldl5<float>(Af, Lf, Dif);
+        ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+        double x[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+        double rres = b0;  // b - A x on lane r
+        for (int it = 0; it < 3 && ok; it++) {
+            float rf[5], dl[5] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+            for (int q = 0; q < 5; q++) rf[q] = (float)__shfl_sync(0xffffffffu, rres, q);
+            if (lane == 0) ldl5_solve<float>(Lf, Dif, rf, dl);
+#pragma unroll
+            for (int q = 0; q < 5; q++) x[q] += (double)__shfl_sync(0xffffffffu, dl[q], 0);
+            rres = b0;
+#pragma unroll
+            for (int q = 0; q < 5; q++) rres = fma(-Arow[q], x[q], rres);
+        }
+        bool fin = ok;
+#pragma unroll
+        for (int q = 0; q < 5; q++) fin = fin && isfinite(x[q]);
+        if (fin) {
+            // |A x - b| against max_r (|b_r| + sum_s |A_rs x_s|)
+            double t = fabs(b0);
+#pragma unroll
+            for (int q = 0; q < 5; q++) t += fabs(Arow[q] * x[q]);
+            double rn = lane < 5 ? fabs(rres) : 0.0, sc = lane < 5 ? t : 0.0;
+#pragma unroll
+            for (int off = 4; off > 0; off >>= 1) {
+                rn = fmax(rn, __shfl_xor_sync(0xffffffffu, rn, off));
+                sc = fmax(sc, __shfl_xor_sync(0xffffffffu, sc, off));
+            }
+            rn = __shfl_sync(0xffffffffu, rn, 0);
+            sc = __shfl_sync(0xffffffffu, sc, 0);
+            fin = rn <= 1e-12 * sc;
+        }
+        if (fin && res) {
+            // sum_i phi_r Q_i dV = dV Mc (rhs - A d), taken to psi = (1, xi,
+            // |xi|^2) with xi = sqrt(T) c + u
+            double rvv[5];
+#pragma unroll
+            for (int q = 0; q < 5; q++) rvv[q] = __shfl_sync(0xffffffffu, rres, q);
+            if (lane < 5) {
+                const double k = dV * Mc, uu[3] = {mo[1], mo[2], mo[3]};
+                double o5;
+                if (lane == 0) o5 = k * rvv[0];
+                else if (lane < 4) o5 = k * (sq * rvv[lane] + uu[lane - 1] * rvv[0]);
+                else {
+                    const double dot = uu[0] * rvv[1] + uu[1] * rvv[2] + uu[2] * rvv[3];
+                    o5 = k * (T * (rvv[4] + 3.0 * rvv[0]) + 2.0 * sq * dot +
+                              (uu[0] * uu[0] + uu[1] * uu[1] + uu[2] * uu[2]) * rvv[0]);
+                }
+                res[cell * 5 + lane] = o5;
+            }
+        }
+        if (lane < 5) cc[lane] = fin ? x[lane] : 0.0;
+        if (lane == 0) good = fin ? 1 : 0;
     }
     __syncthreads();
     const float d0 = (float)cc[0], d1 = (float)cc[1], d2 = (float)cc[2], d3 = (float)cc[3], d4 = (float)cc[4];
