@@ -147,7 +147,9 @@ int dvm_set_allocator(dvm_ctx *ctx, void *(*alloc_fn)(size_t, void *),
 
 /* Build the balanced tree, its Morton order, the face lists and the
  * per-cell upwind stencils (Sec. 2.1; Sec. 3.1 step 4).  Host work, once per
- * mesh.  Rebuilding discards f. */
+ * mesh.  Rebuilding discards f.  DVM_EINVAL unless 1 <= base_level <=
+ * max_level <= 19, and for a tree without a fluid leaf (every leaf inside
+ * the solid body): there is nothing to step. */
 int dvm_build_tree(dvm_ctx *ctx, const dvm_tree_spec *spec);
 
 /* Split every leaf i with flag[i] != 0 (indices into the Morton leaf list of
