@@ -853,7 +853,7 @@ def run_ours(args):
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
+            "scaling": "strong", "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
             "config": {"workload": workload_desc(args.config, cfg, ncells, nv, args.precision, args.collision),
                        "cells": ncells, "velocities": nv, "f_values": ncells * nv,
                        "storage": args.precision, "parallelism": "replicas" if world > 1 else "single GPU",
