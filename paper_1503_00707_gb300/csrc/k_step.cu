@@ -1197,6 +1197,7 @@ int launch_kernel(const StepParams &p, int ncw)
 }
 
 // compile-time group sizes for the 24^3 and 16^3 grids of 3D FP32/BF16 runs
+// (BGK, entropic BGK and transport alone)
 template <typename TS, int DIM, int COLL>
 int launch_sized(const StepParams &p, int ncw)
 {
@@ -1218,7 +1219,7 @@ int launch_typed(const StepParams &p)
     const int ncw = (Q + 31) / 32;
     if (ncw > MAXCW) return DVM_ENOTIMPL;
     if (p.coll == DVM_COLL_BGK) return launch_sized<TS, DIM, DVM_COLL_BGK>(p, ncw);
-    if (p.coll == DVM_COLL_BGK_ENTROPIC) return launch_kernel<TS, DIM, DVM_COLL_BGK_ENTROPIC, 0>(p, ncw);
+    if (p.coll == DVM_COLL_BGK_ENTROPIC) return launch_sized<TS, DIM, DVM_COLL_BGK_ENTROPIC>(p, ncw);
     return launch_sized<TS, DIM, DVM_COLL_NONE>(p, ncw);
 }
 
