@@ -62,6 +62,12 @@ def lib():
         L.orc_build_tree.argtypes = [C.POINTER(TreeSpec), i64, C.POINTER(i64), P, P, P]
         L.orc_create.restype = P
         L.orc_create.argtypes = [C.POINTER(TreeSpec), P, P, P]
+        L.orc_create_sparse.restype = P
+        L.orc_create_sparse.argtypes = [C.POINTER(TreeSpec), P, P, P]
+        L.orc_step_inputs.restype = i64
+        L.orc_step_inputs.argtypes = [P, i64, P, P]
+        L.orc_maxwellian_rows.argtypes = [P, i64, C.c_int, P, P, P, P, P]
+        L.orc_step_cells_bgk.argtypes = [P, i64, P, i64, P, P, C.c_double, C.c_double, P]
         L.orc_destroy.argtypes = [P]
         for nm in ("orc_nleaves", "orc_ncells", "orc_nv", "orc_n_faces", "orc_n_bfaces", "orc_hs_nkept"):
             getattr(L, nm).restype = i64
@@ -213,8 +219,13 @@ def solve(A, b):
 class Problem:
     """One tree + velocity grid + state, all in FP64 on the host."""
 
-    def __init__(self, spec, n=None, lo=None, hi=None, lattice=None):
+    def __init__(self, spec, n=None, lo=None, hi=None, lattice=None, store_f=True):
+        """store_f=False: no f storage (trees whose f does not fit in host
+        memory); only the geometry, dt_cfl, set_freestream and the
+        selected-cell calls (step_inputs, maxwellian_rows, step_cells_bgk)
+        apply then."""
         self.spec = spec
+        self.store_f = bool(store_f) and lattice is None
         if lattice is not None:
             # lattice Boltzmann (Sec. 4): the tree with an LBM velocity set
             self._h = lib().orc_create_lattice(C.byref(spec), int(lattice))
@@ -231,7 +242,8 @@ class Problem:
         n = np.asarray(n, dtype=np.int32)
         lo = np.asarray(lo, dtype=np.float64)
         hi = np.asarray(hi, dtype=np.float64)
-        self._h = lib().orc_create(C.byref(spec), _p(n), _p(lo), _p(hi))
+        create = lib().orc_create if store_f else lib().orc_create_sparse
+        self._h = create(C.byref(spec), _p(n), _p(lo), _p(hi))
         if not self._h:
             raise ValueError("oracle problem creation failed")
         self.nleaves = lib().orc_nleaves(self._h)
@@ -289,7 +301,8 @@ class Problem:
         rho = np.ascontiguousarray(np.asarray(rho, dtype=np.float64).reshape(self.ncells, nmix))
         u = np.ascontiguousarray(np.asarray(u, dtype=np.float64).reshape(self.ncells, nmix, 3))
         T = np.ascontiguousarray(np.asarray(T, dtype=np.float64).reshape(self.ncells, nmix))
-        lib().orc_init_maxwellian(self._h, nmix, _p(w), _p(rho), _p(u), _p(T))
+        if lib().orc_init_maxwellian(self._h, nmix, _p(w), _p(rho), _p(u), _p(T)):
+            raise RuntimeError("this problem holds no f")
 
     def refine_project(self, flags):
         """Split the flagged leaves, rebalance, carry f over (injection)."""
@@ -312,12 +325,48 @@ class Problem:
 
     def get_f(self):
         f = np.zeros((self.ncells, self.nv))
-        lib().orc_get_f(self._h, _p(f))
+        if lib().orc_get_f(self._h, _p(f)):
+            raise RuntimeError("this problem holds no f")
         return f
 
     def set_f(self, f):
         f = np.ascontiguousarray(f, dtype=np.float64).reshape(self.ncells, self.nv)
-        lib().orc_set_f(self._h, _p(f))
+        if lib().orc_set_f(self._h, _p(f)):
+            raise RuntimeError("this problem holds no f")
+
+    def step_inputs(self, cells):
+        """The sorted distinct cells whose f one step of `cells` reads."""
+        cells = np.ascontiguousarray(cells, dtype=np.int64)
+        k = lib().orc_step_inputs(self._h, cells.size, _p(cells), None)
+        if k < 0:
+            raise IndexError("cell index out of range")
+        out = np.zeros(k, dtype=np.int64)
+        lib().orc_step_inputs(self._h, cells.size, _p(cells), _p(out))
+        return out
+
+    def maxwellian_rows(self, w, rho, u, T):
+        """Rows of the mixture init_maxwellian sets, for len(w) cells:
+        w, rho, T [n, nmix], u [n, nmix, 3]."""
+        w = np.ascontiguousarray(np.asarray(w, dtype=np.float64))
+        n, nmix = w.shape
+        rho = np.ascontiguousarray(np.asarray(rho, dtype=np.float64).reshape(n, nmix))
+        u = np.ascontiguousarray(np.asarray(u, dtype=np.float64).reshape(n, nmix, 3))
+        T = np.ascontiguousarray(np.asarray(T, dtype=np.float64).reshape(n, nmix))
+        out = np.zeros((n, self.nv))
+        lib().orc_maxwellian_rows(self._h, n, nmix, _p(w), _p(rho), _p(u), _p(T), _p(out))
+        return out
+
+    def step_cells_bgk(self, cells, inputs, fin, dt, kn):
+        """One step (transport, then conservative BGK) of `cells` from the
+        rows fin of `inputs` (as step_inputs gives them)."""
+        cells = np.ascontiguousarray(cells, dtype=np.int64)
+        inputs = np.ascontiguousarray(inputs, dtype=np.int64)
+        fin = np.ascontiguousarray(fin, dtype=np.float64).reshape(inputs.size, self.nv)
+        out = np.zeros((cells.size, self.nv))
+        if lib().orc_step_cells_bgk(self._h, cells.size, _p(cells), inputs.size, _p(inputs), _p(fin),
+                                    float(dt), float(kn), _p(out)):
+            raise RuntimeError("selected-cell step failed")
+        return out
 
     def dt_cfl(self, cfl):
         return lib().orc_dt_cfl(self._h, cfl)

@@ -587,8 +587,8 @@ static orc_problem *create_tree(const orc_tree_spec *spec)
     return p;
 }
 
-orc_problem *orc_create(const orc_tree_spec *spec, const int n[3],
-                        const double lo[3], const double hi[3])
+static orc_problem *create_grid(const orc_tree_spec *spec, const int n[3], const double lo[3],
+                                const double hi[3], int with_f)
 {
     orc_problem *p = create_tree(spec);
     if (!p) return NULL;
@@ -613,12 +613,24 @@ orc_problem *orc_create(const orc_tree_spec *spec, const int n[3],
         }
     }
     free(idx);
-    p->f = (double *)calloc((size_t)(p->ncells * p->nv), sizeof(double));
+    p->f = with_f ? (double *)calloc((size_t)(p->ncells * p->nv), sizeof(double)) : NULL;
     p->finf = (double *)calloc((size_t)p->nv, sizeof(double));
-    if (!p->f || !p->finf) { orc_destroy(p); return NULL; }
+    if ((with_f && !p->f) || !p->finf) { orc_destroy(p); return NULL; }
     double u0[3] = {0, 0, 0};
     orc_set_freestream(p, 1.0, u0, 1.0);
     return p;
+}
+
+orc_problem *orc_create(const orc_tree_spec *spec, const int n[3],
+                        const double lo[3], const double hi[3])
+{
+    return create_grid(spec, n, lo, hi, 1);
+}
+
+orc_problem *orc_create_sparse(const orc_tree_spec *spec, const int n[3],
+                               const double lo[3], const double hi[3])
+{
+    return create_grid(spec, n, lo, hi, 0);
 }
 
 void orc_destroy(orc_problem *p)
@@ -694,26 +706,20 @@ int orc_set_freestream(orc_problem *p, double rho, const double u[3], double T)
 int orc_init_maxwellian(orc_problem *p, int nmix, const double *w,
                         const double *rho, const double *u, const double *T)
 {
-    for (int64_t c = 0; c < p->ncells; c++)
-        for (int64_t v = 0; v < p->nv; v++) {
-            double s = 0.0;
-            for (int m = 0; m < nmix; m++) {
-                int64_t q = c * nmix + m;
-                s += w[q] * maxwellian(rho[q], &u[3 * q], T[q], &p->xi[3 * v]);
-            }
-            p->f[c * p->nv + v] = s;
-        }
-    return 0;
+    if (!p->f) return -1; /* a problem without f storage */
+    return orc_maxwellian_rows(p, p->ncells, nmix, w, rho, u, T, p->f);
 }
 
 int orc_get_f(const orc_problem *p, double *f)
 {
+    if (!p->f) return -1; /* a problem without f storage */
     memcpy(f, p->f, (size_t)(p->ncells * p->nv) * sizeof(double));
     return 0;
 }
 
 int orc_set_f(orc_problem *p, const double *f)
 {
+    if (!p->f) return -1; /* a problem without f storage */
     memcpy(p->f, f, (size_t)(p->ncells * p->nv) * sizeof(double));
     return 0;
 }
@@ -742,47 +748,60 @@ double orc_dt_cfl(const orc_problem *p, double cfl)
  * domain side it is the ghost value (inflow: freestream Maxwellian;
  * outflow: the cell's own value; specular wall: the cell's value at the
  * reflected velocity). */
-int orc_transport(orc_problem *p, double dt)
+/* f* of cell c into out; row(ctx, k) gives the f row of cell k */
+typedef const double *(*row_fn)(const orc_problem *p, const void *ctx, int64_t k);
+
+static void transport_cell(const orc_problem *p, int64_t c, row_fn row, const void *ctx, double dt, double *out)
 {
     int dim = p->spec.dim;
     int64_t nv = p->nv;
-    double *fs = (double *)malloc((size_t)(p->ncells * nv) * sizeof(double));
-    if (!fs) return -1;
-    const double *f = p->f;
-#pragma omp parallel for schedule(dynamic, 8)
-    for (int64_t c = 0; c < p->ncells; c++) {
-        double *out = &fs[c * nv];
-        const double *own = &f[c * nv];
-        double V = ldexp(1.0, -p->lv[p->leaf_of_cell[c]].lev * dim);
-        for (int64_t v = 0; v < nv; v++) out[v] = own[v];
-        for (int64_t e = p->cf_start[c]; e < p->cf_start[c + 1]; e++) {
-            int64_t q = p->cf_list[e];
-            if (q >= 0) {
-                /* interior face: flux from minus to plus along +axis */
-                int d = p->fax[q];
-                int64_t a = p->cell_of_leaf[p->fm[q]], b = p->cell_of_leaf[p->fp[q]];
-                double sgn = (a == c) ? 1.0 : -1.0; /* outward normal of this cell */
-                for (int64_t v = 0; v < nv; v++) {
-                    double x = p->xi[3 * v + d];
-                    double up = x > 0.0 ? f[a * nv + v] : f[b * nv + v];
-                    double flux = x * p->farea[q] * up;
-                    out[v] -= sgn * dt * flux / V;
-                }
-            } else {
-                q = -1 - q;
-                int d = p->bax[q];
-                for (int64_t v = 0; v < nv; v++) {
-                    double xn = (p->bside[q] ? 1.0 : -1.0) * p->xi[3 * v + d];
-                    double up;
-                    if (xn > 0.0) up = own[v];
-                    else if (p->bkind[q] == ORC_BC_INFLOW) up = p->finf[v];
-                    else if (p->bkind[q] == ORC_BC_WALL) up = own[p->mirror[d][v]];
-                    else up = own[v];
-                    out[v] -= dt * xn * p->barea[q] * up / V;
-                }
+    const double *own = row(p, ctx, c);
+    double V = ldexp(1.0, -p->lv[p->leaf_of_cell[c]].lev * dim);
+    for (int64_t v = 0; v < nv; v++) out[v] = own[v];
+    for (int64_t e = p->cf_start[c]; e < p->cf_start[c + 1]; e++) {
+        int64_t q = p->cf_list[e];
+        if (q >= 0) {
+            /* interior face: flux from minus to plus along +axis */
+            int d = p->fax[q];
+            int64_t a = p->cell_of_leaf[p->fm[q]], b = p->cell_of_leaf[p->fp[q]];
+            double sgn = (a == c) ? 1.0 : -1.0; /* outward normal of this cell */
+            const double *fa = row(p, ctx, a), *fb = row(p, ctx, b);
+            for (int64_t v = 0; v < nv; v++) {
+                double x = p->xi[3 * v + d];
+                double up = x > 0.0 ? fa[v] : fb[v];
+                double flux = x * p->farea[q] * up;
+                out[v] -= sgn * dt * flux / V;
+            }
+        } else {
+            q = -1 - q;
+            int d = p->bax[q];
+            for (int64_t v = 0; v < nv; v++) {
+                double xn = (p->bside[q] ? 1.0 : -1.0) * p->xi[3 * v + d];
+                double up;
+                if (xn > 0.0) up = own[v];
+                else if (p->bkind[q] == ORC_BC_INFLOW) up = p->finf[v];
+                else if (p->bkind[q] == ORC_BC_WALL) up = own[p->mirror[d][v]];
+                else up = own[v];
+                out[v] -= dt * xn * p->barea[q] * up / V;
             }
         }
     }
+}
+
+static const double *row_dense(const orc_problem *p, const void *ctx, int64_t k)
+{
+    (void)ctx;
+    return &p->f[k * p->nv];
+}
+
+int orc_transport(orc_problem *p, double dt)
+{
+    if (!p->f) return -1; /* a problem without f storage */
+    int64_t nv = p->nv;
+    double *fs = (double *)malloc((size_t)(p->ncells * nv) * sizeof(double));
+    if (!fs) return -1;
+#pragma omp parallel for schedule(dynamic, 8)
+    for (int64_t c = 0; c < p->ncells; c++) transport_cell(p, c, row_dense, NULL, dt, &fs[c * nv]);
     free(p->f);
     p->f = fs;
     return 0;
@@ -809,6 +828,7 @@ static void cell_moments(const orc_problem *p, const double *f, double *rho,
 
 int orc_moments(const orc_problem *p, double *rho, double *u, double *T)
 {
+    if (!p->f) return -1; /* a problem without f storage */
     for (int64_t c = 0; c < p->ncells; c++)
         cell_moments(p, &p->f[c * p->nv], &rho[c], &u[3 * c], &T[c]);
     return 0;
@@ -816,6 +836,7 @@ int orc_moments(const orc_problem *p, double *rho, double *u, double *T)
 
 int orc_totals(const orc_problem *p, double out[5])
 {
+    if (!p->f) return -1; /* a problem without f storage */
     for (int r = 0; r < 5; r++) out[r] = 0.0;
     int dim = p->spec.dim;
     for (int64_t c = 0; c < p->ncells; c++) {
@@ -871,38 +892,139 @@ static void psi5(const double *x, double ps[5])
  * polynomial 1 + d0 + d.xi + d2 |xi|^2 (the correction form of Eq. 6) whose
  * five coefficients make its discrete moments equal those of f; then
  * f <- f + dt nu (M~ - f), nu = sqrt(8/pi) rho sqrt(T) / Kn. */
+/* the update of one cell's f (in place); q (may be NULL) gets the term */
+static int bgk_cell(const orc_problem *p, double *f, double dt, double kn, double *q)
+{
+    int64_t nv = p->nv;
+    double rho, u[3], T;
+    cell_moments(p, f, &rho, u, &T);
+    double *M = (double *)malloc((size_t)nv * sizeof(double));
+    double A[25] = {0}, rhs[5] = {0}, d[5];
+    for (int64_t v = 0; v < nv; v++) {
+        double ps[5];
+        psi5(&p->xi[3 * v], ps);
+        M[v] = maxwellian(rho, u, T, &p->xi[3 * v]);
+        for (int r = 0; r < 5; r++) {
+            for (int s = 0; s < 5; s++) A[r * 5 + s] += ps[r] * ps[s] * M[v] * p->dV;
+            rhs[r] += ps[r] * (f[v] - M[v]) * p->dV;
+        }
+    }
+    if (!(rho > 0.0) || !(T > 0.0) || orc_solve(5, A, rhs, d)) { free(M); return -1; }
+    double nu = sqrt(8.0 / M_PI) * rho * sqrt(T) / kn;
+    for (int64_t v = 0; v < nv; v++) {
+        double ps[5];
+        psi5(&p->xi[3 * v], ps);
+        double P = 1.0;
+        for (int r = 0; r < 5; r++) P += d[r] * ps[r];
+        double Q = nu * (M[v] * P - f[v]);
+        if (q) q[v] = Q;
+        f[v] += dt * Q;
+    }
+    free(M);
+    return 0;
+}
+
 int orc_bgk(orc_problem *p, double dt, double kn, double *q)
 {
+    if (!p->f) return -1; /* a problem without f storage */
     int64_t nv = p->nv;
     int err = 0;
 #pragma omp parallel for schedule(dynamic, 16) reduction(| : err)
-    for (int64_t c = 0; c < p->ncells; c++) {
-        double *f = &p->f[c * nv];
-        double rho, u[3], T;
-        cell_moments(p, f, &rho, u, &T);
-        double *M = (double *)malloc((size_t)nv * sizeof(double));
-        double A[25] = {0}, rhs[5] = {0}, d[5];
-        for (int64_t v = 0; v < nv; v++) {
-            double ps[5];
-            psi5(&p->xi[3 * v], ps);
-            M[v] = maxwellian(rho, u, T, &p->xi[3 * v]);
-            for (int r = 0; r < 5; r++) {
-                for (int s = 0; s < 5; s++) A[r * 5 + s] += ps[r] * ps[s] * M[v] * p->dV;
-                rhs[r] += ps[r] * (f[v] - M[v]) * p->dV;
+    for (int64_t c = 0; c < p->ncells; c++)
+        if (bgk_cell(p, &p->f[c * nv], dt, kn, q ? &q[c * nv] : NULL)) err = 1;
+    return err ? -1 : 0;
+}
+
+/* ---- one step of selected cells, for trees whose f does not fit in host
+ * memory: the cells a step of `cells` reads, their f rows supplied by the
+ * caller, and the stepped rows (transport, Eq. 2, then conservative BGK). */
+static int cmp_i64(const void *a, const void *b)
+{
+    const int64_t x = *(const int64_t *)a, y = *(const int64_t *)b;
+    return x < y ? -1 : (x > y ? 1 : 0);
+}
+
+int64_t orc_step_inputs(const orc_problem *p, int64_t n, const int64_t *cells, int64_t *out)
+{
+    int64_t cap = 0;
+    for (int64_t i = 0; i < n; i++) {
+        if (cells[i] < 0 || cells[i] >= p->ncells) return -1;
+        cap += 1 + 2 * (p->cf_start[cells[i] + 1] - p->cf_start[cells[i]]);
+    }
+    int64_t *t = (int64_t *)malloc((size_t)(cap > 0 ? cap : 1) * sizeof(int64_t));
+    int64_t m = 0;
+    for (int64_t i = 0; i < n; i++) {
+        const int64_t c = cells[i];
+        t[m++] = c;
+        for (int64_t e = p->cf_start[c]; e < p->cf_start[c + 1]; e++) {
+            const int64_t q = p->cf_list[e];
+            if (q >= 0) {
+                t[m++] = p->cell_of_leaf[p->fm[q]];
+                t[m++] = p->cell_of_leaf[p->fp[q]];
             }
         }
-        if (!(rho > 0.0) || !(T > 0.0) || orc_solve(5, A, rhs, d)) { err = 1; free(M); continue; }
-        double nu = sqrt(8.0 / M_PI) * rho * sqrt(T) / kn;
-        for (int64_t v = 0; v < nv; v++) {
-            double ps[5];
-            psi5(&p->xi[3 * v], ps);
-            double P = 1.0;
-            for (int r = 0; r < 5; r++) P += d[r] * ps[r];
-            double Q = nu * (M[v] * P - f[v]);
-            if (q) q[c * nv + v] = Q;
-            f[v] += dt * Q;
+    }
+    qsort(t, (size_t)m, sizeof(int64_t), cmp_i64);
+    int64_t k = 0;
+    for (int64_t i = 0; i < m; i++)
+        if (k == 0 || t[i] != t[k - 1]) t[k++] = t[i];
+    if (out) memcpy(out, t, (size_t)k * sizeof(int64_t));
+    free(t);
+    return k;
+}
+
+int orc_maxwellian_rows(const orc_problem *p, int64_t nrows, int nmix, const double *w, const double *rho,
+                        const double *u, const double *T, double *out)
+{
+    for (int64_t c = 0; c < nrows; c++)
+        for (int64_t v = 0; v < p->nv; v++) {
+            double s = 0.0;
+            for (int m = 0; m < nmix; m++) {
+                int64_t q = c * nmix + m;
+                s += w[q] * maxwellian(rho[q], &u[3 * q], T[q], &p->xi[3 * v]);
+            }
+            out[c * p->nv + v] = s;
         }
-        free(M);
+    return 0;
+}
+
+typedef struct {
+    int64_t n;
+    const int64_t *cells;
+    const double *rows;
+} row_table;
+
+static const double *row_sparse(const orc_problem *p, const void *ctx, int64_t k)
+{
+    const row_table *t = (const row_table *)ctx;
+    int64_t lo = 0, hi = t->n - 1;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) / 2;
+        if (t->cells[mid] < k) lo = mid + 1;
+        else hi = mid;
+    }
+    return t->n > 0 && t->cells[lo] == k ? &t->rows[lo * p->nv] : NULL;
+}
+
+int orc_step_cells_bgk(const orc_problem *p, int64_t n, const int64_t *cells, int64_t ninp, const int64_t *inputs,
+                       const double *fin, double dt, double kn, double *out)
+{
+    row_table t = {ninp, inputs, fin};
+    for (int64_t i = 0; i < n; i++) {
+        /* every row the cell reads must be supplied */
+        if (!row_sparse(p, &t, cells[i])) return -1;
+        for (int64_t e = p->cf_start[cells[i]]; e < p->cf_start[cells[i] + 1]; e++) {
+            const int64_t q = p->cf_list[e];
+            if (q >= 0 && (!row_sparse(p, &t, p->cell_of_leaf[p->fm[q]]) || !row_sparse(p, &t, p->cell_of_leaf[p->fp[q]])))
+                return -1;
+        }
+    }
+    int err = 0;
+#pragma omp parallel for schedule(dynamic, 1) reduction(| : err)
+    for (int64_t i = 0; i < n; i++) {
+        double *o = &out[i * p->nv];
+        transport_cell(p, cells[i], row_sparse, &t, dt, o);
+        if (bgk_cell(p, o, dt, kn, NULL)) err = 1;
     }
     return err ? -1 : 0;
 }
@@ -917,6 +1039,7 @@ int orc_bgk(orc_problem *p, double dt, double kn, double *q)
  * 1e-14 of its scale.  Then f <- f + dt nu (E - f), nu as for BGK. */
 int orc_bgk_entropic(orc_problem *p, double dt, double kn, double *q)
 {
+    if (!p->f) return -1; /* a problem without f storage */
     int64_t nv = p->nv;
     int err = 0;
 #pragma omp parallel for schedule(dynamic, 16) reduction(| : err)
@@ -1167,6 +1290,7 @@ int orc_hs_get_tables(const orc_problem *p, int64_t *start, int32_t *gam,
 int orc_hs_collide(orc_problem *p, double dt, double kn, double *q,
                    double *Bout, double *Cout)
 {
+    if (!p->f) return -1; /* a problem without f storage */
     if (!p->hs_start) return -1;
     int64_t nv = p->nv;
     int err = 0;
@@ -1381,6 +1505,7 @@ int orc_lbm_step(orc_problem *p, int nsteps, double dt, double tau)
 
 int orc_step(orc_problem *p, int nsteps, double dt, int coll, double kn)
 {
+    if (!p->f) return -1; /* a problem without f storage */
     for (int s = 0; s < nsteps; s++) {
         if (orc_transport(p, dt)) return -1;
         if (coll == 1 && orc_bgk(p, dt, kn, NULL)) return -2;
@@ -1398,6 +1523,7 @@ int orc_step(orc_problem *p, int nsteps, double dt, int coll, double kn)
  * neighbour spread, e.g. a cell walled in along that axis, is set to 0). */
 int orc_kn_local(const orc_problem *p, double kn, double *out)
 {
+    if (!p->f) return -1; /* a problem without f storage */
     int64_t nc = p->ncells;
     int dim = p->spec.dim;
     double *rho = (double *)malloc((size_t)nc * sizeof(double));
@@ -1472,6 +1598,7 @@ static double mode_value(const double hx[4], const double hy[4], const double hz
 
 int orc_hermite_project(const orc_problem *p, const double *f, double *a, double *mom)
 {
+    if (!f && !p->f) return -1; /* a problem without f storage */
     const double *F = f ? f : p->f;
     for (int64_t c = 0; c < p->ncells; c++) {
         const double *fc = &F[c * p->nv];
@@ -1611,6 +1738,7 @@ int orc_mlp_backward(int64_t n, const double *params, const double *x, const dou
 int orc_learned_apply(orc_problem *p, double dt, double kn, const double *knl, const double *o,
                       double kn_threshold, int32_t *used, double *q)
 {
+    if (!p->f) return -1; /* a problem without f storage */
     int64_t nc = p->ncells, nv = p->nv;
     /* the plain operator for every cell (the fallback, and the yardstick of the learned error) */
     double *qhs = NULL;
@@ -1699,6 +1827,7 @@ int orc_learned_apply(orc_problem *p, double dt, double kn, const double *knl, c
 int orc_learned_collide(orc_problem *p, double dt, double kn, const double *params,
                         double kn_threshold, int32_t *used, double *q)
 {
+    if (!p->f) return -1; /* a problem without f storage */
     int64_t nc = p->ncells, nv = p->nv;
     double *knl = (double *)malloc((size_t)nc * sizeof(double));
     double *a = (double *)malloc((size_t)nc * 128 * sizeof(double));
@@ -1769,6 +1898,7 @@ static int set_mesh(orc_problem *p, leaf_t *v, int64_t n)
 
 int orc_refine_project(orc_problem *p, const uint8_t *flag)
 {
+    if (!p->f) return -1; /* a problem without f storage */
     const orc_tree_spec *s = &p->spec;
     int dim = s->dim, L = p->L;
     /* split every flagged leaf below the deepest level, then balance */
@@ -1803,6 +1933,7 @@ int orc_refine_project(orc_problem *p, const uint8_t *flag)
 
 int orc_coarsen_project(orc_problem *p, const uint8_t *flag)
 {
+    if (!p->f) return -1; /* a problem without f storage */
     const orc_tree_spec *s = &p->spec;
     int dim = s->dim, L = p->L, nch = 1 << dim;
     int64_t on = p->nleaves, nv = p->nv;

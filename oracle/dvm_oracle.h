@@ -60,6 +60,11 @@ int orc_build_tree(const orc_tree_spec *spec, int64_t cap, int64_t *n,
 /* ---- problem object ---- */
 orc_problem *orc_create(const orc_tree_spec *spec, const int n[3],
                         const double lo[3], const double hi[3]);
+/* The same tree and velocity grid without f storage, for trees whose f does
+ * not fit in host memory: only the geometry queries, orc_set_freestream,
+ * orc_dt_cfl and the selected-cell calls below apply to it. */
+orc_problem *orc_create_sparse(const orc_tree_spec *spec, const int n[3],
+                               const double lo[3], const double hi[3]);
 void orc_destroy(orc_problem *p);
 int64_t orc_nleaves(const orc_problem *p);
 int64_t orc_ncells(const orc_problem *p);
@@ -118,6 +123,23 @@ int orc_hs_get_tables(const orc_problem *p, int64_t *start, int32_t *gam,
  * Euler.  q (optional): collision term I per element; Bout, Cout optional. */
 int orc_hs_collide(orc_problem *p, double dt, double kn, double *q,
                    double *Bout, double *Cout);
+
+/* ---- one step of selected cells (transport, Eq. 2, then conservative BGK),
+ * with the f rows supplied by the caller; the per-cell arithmetic is that of
+ * orc_transport and orc_bgk. ----
+ * orc_step_inputs: the sorted distinct cells whose f a step of cells[0..n)
+ * reads (the cells and their face neighbours); returns their count (out may
+ * be NULL to size it), -1 for a cell index out of range. */
+int64_t orc_step_inputs(const orc_problem *p, int64_t n, const int64_t *cells, int64_t *out);
+/* out[c][v] = sum_m w[c,m] M(rho[c,m], u[c,m,:], T[c,m]) at every node, for
+ * nrows rows given their mixture parameters (as orc_init_maxwellian). */
+int orc_maxwellian_rows(const orc_problem *p, int64_t nrows, int nmix, const double *w, const double *rho,
+                        const double *u, const double *T, double *out);
+/* out[i][v]: cell cells[i] after one step from the state whose rows fin[k]
+ * belong to inputs[k] (sorted, as orc_step_inputs gives them); -1 if a row
+ * the step reads is missing or a cell's moments are not admissible. */
+int orc_step_cells_bgk(const orc_problem *p, int64_t n, const int64_t *cells, int64_t ninp, const int64_t *inputs,
+                       const double *fin, double dt, double kn, double *out);
 
 /* Full steps: transport, then collision on f* (Lie splitting).
  * coll: 0 none, 1 BGK, 2 hard sphere, 4 entropic BGK. */

@@ -22,8 +22,8 @@ MUTANTS = [
      "tests/test_oracle_lbm.py::test_equilibrium_moments"),
     ("LBM relaxation factor", "const double om = dt / tau;", "const double om = 0.5 * dt / tau;",
      "tests/test_oracle_lbm.py::test_shear_wave_damping_matches_the_bgk_equation"),
-    ("transport takes the downwind cell", "double up = x > 0.0 ? f[a * nv + v] : f[b * nv + v];",
-     "double up = x > 0.0 ? f[b * nv + v] : f[a * nv + v];",
+    ("transport takes the downwind cell", "double up = x > 0.0 ? fa[v] : fb[v];",
+     "double up = x > 0.0 ? fb[v] : fa[v];",
      "tests/test_oracle_transport.py::test_transport_fourier_closed_form"),
     ("wall ghost without the mirror", "up = own[p->mirror[d][v]];", "up = own[v];",
      "tests/test_oracle_transport.py::test_transport_specular_walls_conserve_mass_and_energy"),
