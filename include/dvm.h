@@ -245,6 +245,17 @@ int dvm_init_maxwellian(dvm_ctx *ctx, int nmix, const double *w, const double *r
 int dvm_get_f(dvm_ctx *ctx, double *f, int64_t count);
 int dvm_set_f(dvm_ctx *ctx, const double *f, int64_t count);
 
+/* Copy the f rows of n selected cells to the host as FP64: out[i][v] = f of
+ * cell cells[i] at velocity node v (out holds n * nv doubles; cells are host
+ * indices in the dvm_get_f / dvm_cell_centres order, repeats allowed).  The
+ * rows are gathered and converted on the device, so only n * nv values cross
+ * the host link: this inspects trees whose whole f is too large to copy.
+ * Device scratch of at most about 16.8M elements is allocated for the call
+ * and freed before it returns; the call synchronises the context's stream.
+ * DVM_EINVAL for an index outside [0, ncells) (nothing is copied),
+ * DVM_ESTATE before f is set, DVM_ENOMEM if the scratch cannot be had. */
+int dvm_get_f_rows(dvm_ctx *ctx, int64_t n, const int64_t *cells, double *out);
+
 /* Copy f to/from host memory in the storage format (ncells*nv elements of
  * 8, 4 or 2 bytes; pinned memory gives asynchronous copies on the stream). */
 int dvm_upload_f(dvm_ctx *ctx, const void *host, int64_t bytes);

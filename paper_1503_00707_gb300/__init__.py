@@ -31,7 +31,7 @@ EXPORTS = [
     "dvm_create", "dvm_destroy", "dvm_last_error", "dvm_set_stream", "dvm_set_allocator",
     "dvm_build_tree", "dvm_refine", "dvm_get_counts", "dvm_get_leaves", "dvm_get_faces",
     "dvm_get_bfaces", "dvm_cell_centres", "dvm_set_velocity_grid", "dvm_get_velocities",
-    "dvm_set_freestream", "dvm_init_maxwellian", "dvm_get_f", "dvm_set_f", "dvm_upload_f",
+    "dvm_set_freestream", "dvm_init_maxwellian", "dvm_get_f", "dvm_get_f_rows", "dvm_set_f", "dvm_upload_f",
     "dvm_download_f", "dvm_f_device", "dvm_dt_cfl", "dvm_set_collision_tables", "dvm_step",
     "dvm_moments", "dvm_step_moments", "dvm_launch_count", "dvm_get_collision_tables",
     "dvm_hs_collide_noalloc", "dvm_learned_set_weights", "dvm_learned_get_weights",
@@ -111,6 +111,7 @@ def lib():
             "dvm_set_freestream": [P, d, P, d],
             "dvm_init_maxwellian": [P, C.c_int, P, P, P, P],
             "dvm_get_f": [P, P, i64],
+            "dvm_get_f_rows": [P, i64, P, P],
             "dvm_set_f": [P, P, i64],
             "dvm_upload_f": [P, P, i64],
             "dvm_download_f": [P, P, i64],
@@ -431,6 +432,13 @@ class Solver:
         f = np.zeros((self.ncells, self.nv))
         self._chk(lib().dvm_get_f(self._h, _p(f), f.size))
         return f
+
+    def get_f_rows(self, cells):
+        """f of the given cells, [len(cells), nv] FP64, gathered on the device."""
+        cells = np.ascontiguousarray(cells, dtype=np.int64)
+        out = np.zeros((cells.size, self.nv))
+        self._chk(lib().dvm_get_f_rows(self._h, cells.size, _p(cells), _p(out)))
+        return out
 
     def set_f(self, f):
         f = np.ascontiguousarray(f, dtype=np.float64).reshape(self.ncells, self.nv)

@@ -838,6 +838,39 @@ int dvm_get_f(dvm_ctx *c, double *f, int64_t count)
     return convert_chunks(c, f, nullptr, count);
 }
 
+int dvm_get_f_rows(dvm_ctx *c, int64_t n, const int64_t *cells, double *out)
+{
+    if (!c || n < 0 || (n > 0 && (!cells || !out))) return DVM_EINVAL;
+    if (c->state < 3) return fail(c, DVM_ESTATE, "f is not set");
+    const int64_t nc = ncells_of(c);
+    for (int64_t i = 0; i < n; i++)
+        if (cells[i] < 0 || cells[i] >= nc) return fail(c, DVM_EINVAL, "cell index out of range");
+    if (n == 0) return DVM_OK;
+    const size_t es = elem_size(c->cfg.precision);
+    const int64_t nv = c->nv;
+    const int64_t rows = std::max<int64_t>(1, std::min<int64_t>(n, (1 << 24) / nv));
+    int64_t *didx = dev_alloc_t<int64_t>(c, rows);
+    char *gath = dev_alloc_t<char>(c, (size_t)(rows * nv) * es);
+    double *stage = dev_alloc_t<double>(c, rows * nv);
+    int rc = DVM_OK;
+    if (!didx || !gath || !stage) rc = fail(c, DVM_ENOMEM, "device allocation (row gather)");
+    for (int64_t s0 = 0; s0 < n && !rc; s0 += rows) {
+        const int64_t k = std::min(rows, n - s0);
+        rc = cuda_check(c, cudaMemcpyAsync(didx, cells + s0, k * 8, cudaMemcpyHostToDevice, c->stream), "copy cells");
+        if (!rc) rc = dvm::launch_rows_indexed(true, gath, c->d_f[c->cur], didx, k, nv * (int64_t)es, c->stream);
+        if (!rc) rc = dvm::launch_to_f64(c->cfg.precision, gath, stage, k * nv, c->stream);
+        if (!rc) rc = cuda_check(c, cudaMemcpyAsync(out + s0 * nv, stage, k * nv * 8, cudaMemcpyDeviceToHost, c->stream), "copy rows");
+        if (!rc) rc = cuda_check(c, cudaStreamSynchronize(c->stream), "row gather");
+    }
+    void *p = didx;
+    dev_free(c, p);
+    p = gath;
+    dev_free(c, p);
+    p = stage;
+    dev_free(c, p);
+    return rc;
+}
+
 int dvm_set_f(dvm_ctx *c, const double *f, int64_t count)
 {
     if (!c || !f) return DVM_EINVAL;
