@@ -23,12 +23,18 @@ def gpu():
     _build.build()
 
 
-@pytest.mark.parametrize("prec,tol", [("f32", 1e-5), ("bf16", 1e-2)])
-def test_mach5_full_size_sampled_cells(prec, tol):
+@pytest.mark.parametrize("prec,tol,tol_rho", [("f32", 1e-5, 1e-5), ("bf16", 2e-2, 1e-2)])
+def test_mach5_full_size_sampled_cells(prec, tol, tol_rho):
     """Two BGK steps from per-cell random two-beam states (every cell away
     from equilibrium); the per-element error on the sampled rows, relative
-    to their largest value, within the storage precision's bound (FP32:
-    1e-5; BF16: its 8-bit mantissa, 4e-3 per step)."""
+    to their largest value, within the storage precision's bound.  FP32:
+    1e-5.  BF16 keeps 8 significant bits (unit roundoff u = 2^-8); an element
+    is rounded five times on the way (the initial state, then per step f*
+    parked in shared memory and the stored result), each a relative error
+    below u, and transport and relaxation are convex combinations, so the
+    per-element bound is 5u = 1.95e-2.  The sampled densities, sums of
+    independently rounded values, stay within the 1e-2 of the other BF16
+    field checks."""
     c = dict(W.CONFIGS["c3_sphere_m5"], init="bimodal")
     s = D.solver_from_config(c, {"f32": D.F32, "bf16": D.BF16}[prec], D.COLL_BGK)
     try:
@@ -47,7 +53,7 @@ def test_mach5_full_size_sampled_cells(prec, tol):
         assert rel_linf(got, want) < tol
         # the density of each sampled cell, from its rows
         rho_g, rho_o = got.sum(1) * o.dV, want.sum(1) * o.dV
-        assert np.max(np.abs(rho_g - rho_o) / rho_o) < tol
+        assert np.max(np.abs(rho_g - rho_o) / rho_o) < tol_rho
     finally:
         s.close()
 
