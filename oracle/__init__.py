@@ -67,7 +67,7 @@ def lib():
         L.orc_step_inputs.restype = i64
         L.orc_step_inputs.argtypes = [P, i64, P, P]
         L.orc_maxwellian_rows.argtypes = [P, i64, C.c_int, P, P, P, P, P]
-        L.orc_step_cells_bgk.argtypes = [P, i64, P, i64, P, P, C.c_double, C.c_double, P]
+        L.orc_step_cells.argtypes = [P, i64, P, i64, P, P, C.c_double, C.c_int, C.c_double, P]
         L.orc_destroy.argtypes = [P]
         for nm in ("orc_nleaves", "orc_ncells", "orc_nv", "orc_n_faces", "orc_n_bfaces", "orc_hs_nkept"):
             getattr(L, nm).restype = i64
@@ -222,8 +222,8 @@ class Problem:
     def __init__(self, spec, n=None, lo=None, hi=None, lattice=None, store_f=True):
         """store_f=False: no f storage (trees whose f does not fit in host
         memory); only the geometry, dt_cfl, set_freestream and the
-        selected-cell calls (step_inputs, maxwellian_rows, step_cells_bgk)
-        apply then."""
+        selected-cell calls (step_inputs, maxwellian_rows, step_cells) and
+        the hard-sphere tables apply then."""
         self.spec = spec
         self.store_f = bool(store_f) and lattice is None
         if lattice is not None:
@@ -356,15 +356,16 @@ class Problem:
         lib().orc_maxwellian_rows(self._h, n, nmix, _p(w), _p(rho), _p(u), _p(T), _p(out))
         return out
 
-    def step_cells_bgk(self, cells, inputs, fin, dt, kn):
-        """One step (transport, then conservative BGK) of `cells` from the
-        rows fin of `inputs` (as step_inputs gives them)."""
+    def step_cells(self, cells, inputs, fin, dt, coll, kn):
+        """One step (transport, then the collision update coll: COLL_BGK, or
+        COLL_HS with tables set) of `cells` from the rows fin of `inputs`
+        (as step_inputs gives them)."""
         cells = np.ascontiguousarray(cells, dtype=np.int64)
         inputs = np.ascontiguousarray(inputs, dtype=np.int64)
         fin = np.ascontiguousarray(fin, dtype=np.float64).reshape(inputs.size, self.nv)
         out = np.zeros((cells.size, self.nv))
-        if lib().orc_step_cells_bgk(self._h, cells.size, _p(cells), inputs.size, _p(inputs), _p(fin),
-                                    float(dt), float(kn), _p(out)):
+        if lib().orc_step_cells(self._h, cells.size, _p(cells), inputs.size, _p(inputs), _p(fin),
+                                float(dt), int(coll), float(kn), _p(out)):
             raise RuntimeError("selected-cell step failed")
         return out
 

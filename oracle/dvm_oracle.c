@@ -1006,28 +1006,6 @@ static const double *row_sparse(const orc_problem *p, const void *ctx, int64_t k
     return t->n > 0 && t->cells[lo] == k ? &t->rows[lo * p->nv] : NULL;
 }
 
-int orc_step_cells_bgk(const orc_problem *p, int64_t n, const int64_t *cells, int64_t ninp, const int64_t *inputs,
-                       const double *fin, double dt, double kn, double *out)
-{
-    row_table t = {ninp, inputs, fin};
-    for (int64_t i = 0; i < n; i++) {
-        /* every row the cell reads must be supplied */
-        if (!row_sparse(p, &t, cells[i])) return -1;
-        for (int64_t e = p->cf_start[cells[i]]; e < p->cf_start[cells[i] + 1]; e++) {
-            const int64_t q = p->cf_list[e];
-            if (q >= 0 && (!row_sparse(p, &t, p->cell_of_leaf[p->fm[q]]) || !row_sparse(p, &t, p->cell_of_leaf[p->fp[q]])))
-                return -1;
-        }
-    }
-    int err = 0;
-#pragma omp parallel for schedule(dynamic, 1) reduction(| : err)
-    for (int64_t i = 0; i < n; i++) {
-        double *o = &out[i * p->nv];
-        transport_cell(p, cells[i], row_sparse, &t, dt, o);
-        if (bgk_cell(p, o, dt, kn, NULL)) err = 1;
-    }
-    return err ? -1 : 0;
-}
 
 /* Entropic BGK (the discrete entropic equilibrium, a reading of the
  * correction of Sec. 3.2 that keeps the H-theorem exact): the target is
@@ -1287,6 +1265,48 @@ int orc_hs_get_tables(const orc_problem *p, int64_t *start, int32_t *gam,
 /* Eqs. 4-6: B_i = sum_k b f_gamma, C_i = sum_k c f_l f_m (b = c),
  * I_i = -f_i P_i B_i + C_i with P = 1 + d0 + d.xi + d2 |xi|^2 chosen so that
  * sum_i psi_r I_i dV = 0 for psi = (1, xi, |xi|^2); then f <- f + dt/Kn I. */
+/* the hard-sphere update of one cell's f (in place); q, Bout, Cout (each may
+ * be NULL) get I, B and C of the cell */
+static int hs_cell(const orc_problem *p, double *f, double dt, double kn, double *q, double *Bout, double *Cout)
+{
+    int64_t nv = p->nv;
+    double *B = (double *)malloc((size_t)nv * sizeof(double));
+    double *C = (double *)malloc((size_t)nv * sizeof(double));
+    for (int64_t i = 0; i < nv; i++) {
+        double sb = 0.0, sc = 0.0;
+        for (int64_t t = p->hs_start[i]; t < p->hs_start[i + 1]; t++) {
+            sb += p->hs_b[t] * f[p->hs_gam[t]];
+            sc += p->hs_b[t] * f[p->hs_l[t]] * f[p->hs_m[t]];
+        }
+        B[i] = sb;
+        C[i] = sc;
+    }
+    double A[25] = {0}, rhs[5] = {0}, d[5];
+    for (int64_t i = 0; i < nv; i++) {
+        double ps[5];
+        psi5(&p->xi[3 * i], ps);
+        for (int r = 0; r < 5; r++) {
+            for (int s = 0; s < 5; s++) A[r * 5 + s] += ps[r] * ps[s] * f[i] * B[i] * p->dV;
+            rhs[r] += ps[r] * (C[i] - f[i] * B[i]) * p->dV;
+        }
+    }
+    if (orc_solve(5, A, rhs, d)) { free(B); free(C); return -1; }
+    for (int64_t i = 0; i < nv; i++) {
+        double ps[5];
+        psi5(&p->xi[3 * i], ps);
+        double P = 1.0;
+        for (int r = 0; r < 5; r++) P += d[r] * ps[r];
+        double I = -f[i] * P * B[i] + C[i];
+        if (q) q[i] = I;
+        if (Bout) Bout[i] = B[i];
+        if (Cout) Cout[i] = C[i];
+        f[i] += dt / kn * I;
+    }
+    free(B);
+    free(C);
+    return 0;
+}
+
 int orc_hs_collide(orc_problem *p, double dt, double kn, double *q,
                    double *Bout, double *Cout)
 {
@@ -1295,42 +1315,36 @@ int orc_hs_collide(orc_problem *p, double dt, double kn, double *q,
     int64_t nv = p->nv;
     int err = 0;
 #pragma omp parallel for schedule(dynamic, 4) reduction(| : err)
-    for (int64_t c = 0; c < p->ncells; c++) {
-        double *f = &p->f[c * nv];
-        double *B = (double *)malloc((size_t)nv * sizeof(double));
-        double *C = (double *)malloc((size_t)nv * sizeof(double));
-        for (int64_t i = 0; i < nv; i++) {
-            double sb = 0.0, sc = 0.0;
-            for (int64_t t = p->hs_start[i]; t < p->hs_start[i + 1]; t++) {
-                sb += p->hs_b[t] * f[p->hs_gam[t]];
-                sc += p->hs_b[t] * f[p->hs_l[t]] * f[p->hs_m[t]];
-            }
-            B[i] = sb;
-            C[i] = sc;
+    for (int64_t c = 0; c < p->ncells; c++)
+        if (hs_cell(p, &p->f[c * nv], dt, kn, q ? &q[c * nv] : NULL, Bout ? &Bout[c * nv] : NULL,
+                    Cout ? &Cout[c * nv] : NULL))
+            err = 1;
+    return err ? -1 : 0;
+}
+
+int orc_step_cells(const orc_problem *p, int64_t n, const int64_t *cells, int64_t ninp, const int64_t *inputs,
+                   const double *fin, double dt, int coll, double kn, double *out)
+{
+    /* coll as in orc_step: 1 BGK, 2 hard sphere */
+    if (coll != 1 && coll != 2) return -1;
+    if (coll == 2 && !p->hs_start) return -1;
+    row_table t = {ninp, inputs, fin};
+    for (int64_t i = 0; i < n; i++) {
+        /* every row the cell reads must be supplied */
+        if (cells[i] < 0 || cells[i] >= p->ncells || !row_sparse(p, &t, cells[i])) return -1;
+        for (int64_t e = p->cf_start[cells[i]]; e < p->cf_start[cells[i] + 1]; e++) {
+            const int64_t q = p->cf_list[e];
+            if (q >= 0 && (!row_sparse(p, &t, p->cell_of_leaf[p->fm[q]]) || !row_sparse(p, &t, p->cell_of_leaf[p->fp[q]])))
+                return -1;
         }
-        double A[25] = {0}, rhs[5] = {0}, d[5];
-        for (int64_t i = 0; i < nv; i++) {
-            double ps[5];
-            psi5(&p->xi[3 * i], ps);
-            for (int r = 0; r < 5; r++) {
-                for (int s = 0; s < 5; s++) A[r * 5 + s] += ps[r] * ps[s] * f[i] * B[i] * p->dV;
-                rhs[r] += ps[r] * (C[i] - f[i] * B[i]) * p->dV;
-            }
-        }
-        if (orc_solve(5, A, rhs, d)) { err = 1; free(B); free(C); continue; }
-        for (int64_t i = 0; i < nv; i++) {
-            double ps[5];
-            psi5(&p->xi[3 * i], ps);
-            double P = 1.0;
-            for (int r = 0; r < 5; r++) P += d[r] * ps[r];
-            double I = -f[i] * P * B[i] + C[i];
-            if (q) q[c * nv + i] = I;
-            if (Bout) Bout[c * nv + i] = B[i];
-            if (Cout) Cout[c * nv + i] = C[i];
-            f[i] += dt / kn * I;
-        }
-        free(B);
-        free(C);
+    }
+    int err = 0;
+#pragma omp parallel for schedule(dynamic, 1) reduction(| : err)
+    for (int64_t i = 0; i < n; i++) {
+        double *o = &out[i * p->nv];
+        transport_cell(p, cells[i], row_sparse, &t, dt, o);
+        const int rc = coll == 1 ? bgk_cell(p, o, dt, kn, NULL) : hs_cell(p, o, dt, kn, NULL, NULL, NULL);
+        if (rc) err = 1;
     }
     return err ? -1 : 0;
 }

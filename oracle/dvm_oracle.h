@@ -124,9 +124,9 @@ int orc_hs_get_tables(const orc_problem *p, int64_t *start, int32_t *gam,
 int orc_hs_collide(orc_problem *p, double dt, double kn, double *q,
                    double *Bout, double *Cout);
 
-/* ---- one step of selected cells (transport, Eq. 2, then conservative BGK),
- * with the f rows supplied by the caller; the per-cell arithmetic is that of
- * orc_transport and orc_bgk. ----
+/* ---- one step of selected cells (transport, Eq. 2, then the collision
+ * update), with the f rows supplied by the caller; the per-cell arithmetic is
+ * that of orc_transport, orc_bgk and orc_hs_collide. ----
  * orc_step_inputs: the sorted distinct cells whose f a step of cells[0..n)
  * reads (the cells and their face neighbours); returns their count (out may
  * be NULL to size it), -1 for a cell index out of range. */
@@ -135,11 +135,12 @@ int64_t orc_step_inputs(const orc_problem *p, int64_t n, const int64_t *cells, i
  * nrows rows given their mixture parameters (as orc_init_maxwellian). */
 int orc_maxwellian_rows(const orc_problem *p, int64_t nrows, int nmix, const double *w, const double *rho,
                         const double *u, const double *T, double *out);
-/* out[i][v]: cell cells[i] after one step from the state whose rows fin[k]
- * belong to inputs[k] (sorted, as orc_step_inputs gives them); -1 if a row
- * the step reads is missing or a cell's moments are not admissible. */
-int orc_step_cells_bgk(const orc_problem *p, int64_t n, const int64_t *cells, int64_t ninp, const int64_t *inputs,
-                       const double *fin, double dt, double kn, double *out);
+/* out[i][v]: cell cells[i] after one step (coll 1: conservative BGK; 2: hard
+ * sphere, tables set) from the state whose rows fin[k] belong to inputs[k]
+ * (sorted, as orc_step_inputs gives them); -1 if a row the step reads is
+ * missing, a cell's moments are not admissible or its system is singular. */
+int orc_step_cells(const orc_problem *p, int64_t n, const int64_t *cells, int64_t ninp, const int64_t *inputs,
+                   const double *fin, double dt, int coll, double kn, double *out);
 
 /* Full steps: transport, then collision on f* (Lie splitting).
  * coll: 0 none, 1 BGK, 2 hard sphere, 4 entropic BGK. */

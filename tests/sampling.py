@@ -39,9 +39,10 @@ def cell_sample(o, n_random, n_each, seed):
     return np.unique(np.concatenate(picks)).astype(np.int64)
 
 
-def oracle_rows_after(o, cells, init, nsteps, dt, kn):
-    """f rows of `cells` after nsteps BGK steps from the Maxwellian mixture
-    init = (w, rho, u, T) (per cell of the whole tree), in FP64."""
+def oracle_rows_after(o, cells, init, nsteps, dt, kn, coll=O.COLL_BGK):
+    """f rows of `cells` after nsteps steps (transport, then the collision
+    update coll) from the Maxwellian mixture init = (w, rho, u, T) (per cell
+    of the whole tree), in FP64."""
     rings = [np.asarray(cells, dtype=np.int64)]
     for _ in range(nsteps):
         rings.append(o.step_inputs(rings[-1]))
@@ -49,5 +50,5 @@ def oracle_rows_after(o, cells, init, nsteps, dt, kn):
     base = rings[-1]
     f = o.maxwellian_rows(w[base], r[base], u[base], T[base])
     for k in range(nsteps, 0, -1):
-        f = o.step_cells_bgk(rings[k - 1], rings[k], f, dt, kn)
+        f = o.step_cells(rings[k - 1], rings[k], f, dt, coll, kn)
     return f

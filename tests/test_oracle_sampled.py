@@ -1,5 +1,6 @@
 """The oracle's selected-cell step (for trees whose f it cannot hold) against
-its full step: the same per-cell arithmetic, so the rows must be identical."""
+its full step, BGK and hard sphere: the same per-cell arithmetic, so the rows
+must be identical."""
 import numpy as np
 import pytest
 
@@ -22,19 +23,22 @@ def _dense(c):
     return o
 
 
-@pytest.mark.parametrize("nsteps", [1, 3])
-def test_selected_cells_equal_full_step(nsteps):
+@pytest.mark.parametrize("coll,nsteps", [(O.COLL_BGK, 1), (O.COLL_BGK, 3), (O.COLL_HS, 2)])
+def test_selected_cells_equal_full_step(coll, nsteps):
     c = _case()
     o, sp = _dense(c), oracle_sparse_for(c)
+    if coll == O.COLL_HS:
+        o.hs_tables(16, W.SEED)
+        sp.hs_tables(16, W.SEED)
     xyz, _ = o.centres()
     assert np.array_equal(xyz, sp.centres()[0])
     init = W.initial_state(c, xyz)
     o.init_maxwellian(*init)
     dt = o.dt_cfl(c["cfl"])
-    o.step(nsteps, dt, O.COLL_BGK, c["kn"])
+    o.step(nsteps, dt, coll, c["kn"])
     cells = cell_sample(sp, 24, 8, seed=5)
     assert cells.size >= 40  # every face kind is present in this tree
-    got = oracle_rows_after(sp, cells, init, nsteps, dt, c["kn"])
+    got = oracle_rows_after(sp, cells, init, nsteps, dt, c["kn"], coll)
     assert np.array_equal(got, o.get_f()[cells])
 
 
@@ -76,7 +80,9 @@ def test_missing_rows_and_bad_indices_refused():
     w, r, u, T = init
     f = sp.maxwellian_rows(w[inp], r[inp], u[inp], T[inp])
     with pytest.raises(RuntimeError):
-        sp.step_cells_bgk(cells, inp[1:], f[1:], 1e-4, c["kn"])
+        sp.step_cells(cells, inp[1:], f[1:], 1e-4, O.COLL_BGK, c["kn"])
+    with pytest.raises(RuntimeError):  # hard sphere without tables
+        sp.step_cells(cells, inp, f, 1e-4, O.COLL_HS, c["kn"])
     with pytest.raises(IndexError):
         sp.step_inputs(np.array([sp.ncells]))
     with pytest.raises(RuntimeError):
