@@ -1028,6 +1028,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_step(const StepParams p)
             for (int L = 0; L < 4; L++) aw[L] = (L < 2 ? dax : day) * sl.w[L * 4];
             wz[0] = sl.w[16];
             wz[1] = sl.w[20];
+            const Q4 dz0 = q_mul(daz, q_splat(wz[0])), dz1 = q_mul(daz, q_splat(wz[1]));
             const int xm = sl.xmask;
 #pragma unroll
             for (int o = 0; o < 8; o++) {
@@ -1041,7 +1042,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_step(const StepParams p)
 #pragma unroll
                     for (int d = 0; d < DIM; d++) {
                         const int L = list_of(o, d);
-                        const Q4 w = d < 2 ? q_splat(aw[L]) : q_mul(daz, q_splat(wz[L - 4]));
+                        const Q4 w = d < 2 ? q_splat(aw[L]) : (L == 4 ? dz0 : dz1);
                         fs = q_fma(w, IO::lds(st + (1 + d) * P), fs);
                     }
                     if (xm & lists_of<DIM>(o)) {
@@ -1130,8 +1131,17 @@ __global__ void __launch_bounds__(MAXT, 1) k_step(const StepParams p)
                     const TabE<TC> *tx = sm.tab[q2][0], *ty = sm.tab[q2][1], *tz = sm.tab[q2][2];
                     const TC KN = sm.coef[q2][CF_KN], C0 = sm.coef[q2][CF_C0];
                     const Q4 omn = q_splat(sm.coef[q2][CF_OMN]);
-                    // per z sign: the z factors gz and gz Pz of the thread's
-                    // nodes, then the four x-y sign pairs
+                    // the x-y factors of the four x-y sign pairs (the same for
+                    // both z signs), then per z sign the z factors gz and gz Pz
+                    // of the thread's nodes
+                    TC Axy[4], Bxy[4];
+#pragma unroll
+                    for (int sxy = 0; sxy < 4; sxy++) {
+                        const TabE<TC> a = tx[(sxy & 2) ? hxx + mx : hxx - 1 - mx];
+                        const TabE<TC> c = ty[(sxy & 1) ? hyy + my : hyy - 1 - my];
+                        Bxy[sxy] = KN * a.g * c.g;
+                        Axy[sxy] = Bxy[sxy] * (C0 + a.p + c.p);
+                    }
 #pragma unroll
                     for (int pz = 0; pz < 2; pz++) {
                         TC g[VEC], gp[VEC];
@@ -1144,10 +1154,8 @@ __global__ void __launch_bounds__(MAXT, 1) k_step(const StepParams p)
                         const Q4 Z1 = q_make(g), Z2 = q_make(gp);
 #pragma unroll
                         for (int sxy = 0; sxy < 4; sxy++) {
-                            const TabE<TC> a = tx[(sxy & 2) ? hxx + mx : hxx - 1 - mx];
-                            const TabE<TC> c = ty[(sxy & 1) ? hyy + my : hyy - 1 - my];
-                            const TC B = KN * a.g * c.g;
-                            const TC A = B * (C0 + a.p + c.p);
+                            const TC B = Bxy[sxy];
+                            const TC A = Axy[sxy];
                             const int o = 2 * sxy + pz;
                             const Q4 mt = q_fma(q_splat(A), Z1, q_mul(q_splat(B), Z2));
                             IO::stg(dst + o * P, q_fma(omn, IO::lds(tile + o * P), mt));

@@ -77,6 +77,23 @@ def test_sphere_fp32(name):
     assert rel_linf(r1, r2) < 1e-5 and np.max(np.abs(u1 - u2)) < 1e-5
 
 
+@pytest.mark.parametrize("name", ["l3_sphere_d3q19", "l3_sphere_d3q27"])
+def test_sphere_full_size_fp32(name):
+    """The bench's lattice Boltzmann workload at its full size (3,336,104
+    cells on levels 7-10, f twice the size of L2), five steps, every element
+    against the FP64 oracle."""
+    c = W.CONFIGS[name]
+    s, o = _pair(c)
+    assert s.ncells == o.ncells == 3336104
+    dt = o.dt_cfl(c["cfl"])
+    tau = W.lbm_tau(c, dt)
+    s.lbm_step(5, dt, tau)
+    o.lbm_step(5, dt, tau)
+    assert rel_linf(s.lbm_get_f(), o.get_f()) < 1e-5
+    (r1, u1), (r2, u2) = s.lbm_moments(), o.lbm_moments()
+    assert rel_linf(r1, r2) < 1e-5 and np.max(np.abs(u1 - u2)) < 1e-5
+
+
 def test_sphere_d3q27_fp64():
     c = W.CONFIGS["l2_sphere_d3q27_small"]
     s, o = _pair(c, "f64")
