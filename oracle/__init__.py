@@ -68,6 +68,7 @@ def lib():
         L.orc_step_inputs.argtypes = [P, i64, P, P]
         L.orc_maxwellian_rows.argtypes = [P, i64, C.c_int, P, P, P, P, P]
         L.orc_step_cells.argtypes = [P, i64, P, i64, P, P, C.c_double, C.c_int, C.c_double, P]
+        L.orc_step_cells_learned.argtypes = [P, i64, P, i64, P, P, C.c_double, C.c_double, P, C.c_double, P, P, P]
         L.orc_destroy.argtypes = [P]
         for nm in ("orc_nleaves", "orc_ncells", "orc_nv", "orc_n_faces", "orc_n_bfaces", "orc_hs_nkept"):
             getattr(L, nm).restype = i64
@@ -368,6 +369,23 @@ class Problem:
                                 float(dt), int(coll), float(kn), _p(out)):
             raise RuntimeError("selected-cell step failed")
         return out
+
+    def step_cells_learned(self, cells, inputs, fin, dt, kn, params, threshold):
+        """One learned step (transport, then the learned update with the
+        hard-sphere fallback) of `cells` from the rows fin of `inputs`, which
+        must cover two rings of face neighbours.  Returns (rows, local Kn,
+        used flags) of the cells."""
+        cells = np.ascontiguousarray(cells, dtype=np.int64)
+        inputs = np.ascontiguousarray(inputs, dtype=np.int64)
+        fin = np.ascontiguousarray(fin, dtype=np.float64).reshape(inputs.size, self.nv)
+        params = np.ascontiguousarray(params, dtype=np.float64)
+        out = np.zeros((cells.size, self.nv))
+        knl = np.zeros(cells.size)
+        used = np.zeros(cells.size, dtype=np.int32)
+        if lib().orc_step_cells_learned(self._h, cells.size, _p(cells), inputs.size, _p(inputs), _p(fin), float(dt),
+                                        float(kn), _p(params), float(threshold), _p(knl), _p(used), _p(out)):
+            raise RuntimeError("selected-cell learned step failed")
+        return out, knl, used
 
     def dt_cfl(self, cfl):
         return lib().orc_dt_cfl(self._h, cfl)

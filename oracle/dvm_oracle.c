@@ -1535,62 +1535,68 @@ int orc_step(orc_problem *p, int nsteps, double dt, int coll, double kn)
  *   min_g sum_k w_k (q_k - q_j - g.(x_k - x_j))^2,  w_k = A_k / |x_k - x_j|^2,
  * which is exact for linear fields on any 2:1 stencil (a component with no
  * neighbour spread, e.g. a cell walled in along that axis, is set to 0). */
+/* local Kn of cell c from the moments (rho, u [3 per cell], T) and centres
+ * xc [3 per cell] of the cell and its fluid face neighbours */
+static double kn_cell(const orc_problem *p, int64_t c, double kn, const double *rho, const double *u, const double *T,
+                      const double *xc)
+{
+    int dim = p->spec.dim;
+    double q[5] = {rho[c], T[c], u[3 * c], u[3 * c + 1], u[3 * c + 2]};
+    double N[9] = {0}, R[5][3] = {{0}};
+    for (int64_t e = p->cf_start[c]; e < p->cf_start[c + 1]; e++) {
+        int64_t f = p->cf_list[e];
+        if (f < 0) continue; /* boundary face: no fluid neighbour */
+        int64_t a = p->cell_of_leaf[p->fm[f]], b = p->cell_of_leaf[p->fp[f]];
+        int64_t nb = (a == c) ? b : a;
+        double d[3] = {0, 0, 0}, d2 = 0.0;
+        for (int k = 0; k < dim; k++) {
+            d[k] = xc[3 * nb + k] - xc[3 * c + k];
+            if (p->spec.bc[2 * k] == ORC_BC_PERIODIC) {
+                if (d[k] > 0.5) d[k] -= 1.0;
+                if (d[k] < -0.5) d[k] += 1.0;
+            }
+            d2 += d[k] * d[k];
+        }
+        double w = p->farea[f] / d2;
+        double qn[5] = {rho[nb], T[nb], u[3 * nb], u[3 * nb + 1], u[3 * nb + 2]};
+        for (int r = 0; r < dim; r++) {
+            for (int k = 0; k < dim; k++) N[r * 3 + k] += w * d[r] * d[k];
+            for (int m = 0; m < 5; m++) R[m][r] += w * d[r] * (qn[m] - q[m]);
+        }
+    }
+    double grad[5][3] = {{0}};
+    for (int m = 0; m < 5; m++) {
+        double A[9], bb[3], g[3] = {0, 0, 0};
+        for (int r = 0; r < dim; r++) {
+            for (int k = 0; k < dim; k++) A[r * dim + k] = N[r * 3 + k];
+            bb[r] = R[m][r];
+        }
+        if (orc_solve(dim, A, bb, g) == 0)
+            for (int r = 0; r < dim; r++) grad[m][r] = g[r];
+    }
+    double gr = 0, gT = 0, gu = 0;
+    for (int d = 0; d < 3; d++) {
+        gr += grad[0][d] * grad[0][d];
+        gT += grad[1][d] * grad[1][d];
+        for (int k = 2; k < 5; k++) gu += grad[k][d] * grad[k][d];
+    }
+    double m = sqrt(gr) / rho[c];
+    if (sqrt(gT) / T[c] > m) m = sqrt(gT) / T[c];
+    if (sqrt(gu) / sqrt(T[c]) > m) m = sqrt(gu) / sqrt(T[c]);
+    return kn / rho[c] * m;
+}
+
 int orc_kn_local(const orc_problem *p, double kn, double *out)
 {
     if (!p->f) return -1; /* a problem without f storage */
     int64_t nc = p->ncells;
-    int dim = p->spec.dim;
     double *rho = (double *)malloc((size_t)nc * sizeof(double));
     double *u = (double *)malloc((size_t)nc * 3 * sizeof(double));
     double *T = (double *)malloc((size_t)nc * sizeof(double));
     double *xc = (double *)malloc((size_t)nc * 3 * sizeof(double));
     orc_moments(p, rho, u, T);
     orc_cell_centres(p, xc, NULL);
-    for (int64_t c = 0; c < nc; c++) {
-        double q[5] = {rho[c], T[c], u[3 * c], u[3 * c + 1], u[3 * c + 2]};
-        double N[9] = {0}, R[5][3] = {{0}};
-        for (int64_t e = p->cf_start[c]; e < p->cf_start[c + 1]; e++) {
-            int64_t f = p->cf_list[e];
-            if (f < 0) continue; /* boundary face: no fluid neighbour */
-            int64_t a = p->cell_of_leaf[p->fm[f]], b = p->cell_of_leaf[p->fp[f]];
-            int64_t nb = (a == c) ? b : a;
-            double d[3] = {0, 0, 0}, d2 = 0.0;
-            for (int k = 0; k < dim; k++) {
-                d[k] = xc[3 * nb + k] - xc[3 * c + k];
-                if (p->spec.bc[2 * k] == ORC_BC_PERIODIC) {
-                    if (d[k] > 0.5) d[k] -= 1.0;
-                    if (d[k] < -0.5) d[k] += 1.0;
-                }
-                d2 += d[k] * d[k];
-            }
-            double w = p->farea[f] / d2;
-            double qn[5] = {rho[nb], T[nb], u[3 * nb], u[3 * nb + 1], u[3 * nb + 2]};
-            for (int r = 0; r < dim; r++) {
-                for (int k = 0; k < dim; k++) N[r * 3 + k] += w * d[r] * d[k];
-                for (int m = 0; m < 5; m++) R[m][r] += w * d[r] * (qn[m] - q[m]);
-            }
-        }
-        double grad[5][3] = {{0}};
-        for (int m = 0; m < 5; m++) {
-            double A[9], bb[3], g[3] = {0, 0, 0};
-            for (int r = 0; r < dim; r++) {
-                for (int k = 0; k < dim; k++) A[r * dim + k] = N[r * 3 + k];
-                bb[r] = R[m][r];
-            }
-            if (orc_solve(dim, A, bb, g) == 0)
-                for (int r = 0; r < dim; r++) grad[m][r] = g[r];
-        }
-        double gr = 0, gT = 0, gu = 0;
-        for (int d = 0; d < 3; d++) {
-            gr += grad[0][d] * grad[0][d];
-            gT += grad[1][d] * grad[1][d];
-            for (int k = 2; k < 5; k++) gu += grad[k][d] * grad[k][d];
-        }
-        double m = sqrt(gr) / rho[c];
-        if (sqrt(gT) / T[c] > m) m = sqrt(gT) / T[c];
-        if (sqrt(gu) / sqrt(T[c]) > m) m = sqrt(gu) / sqrt(T[c]);
-        out[c] = kn / rho[c] * m;
-    }
+    for (int64_t c = 0; c < nc; c++) out[c] = kn_cell(p, c, kn, rho, u, T, xc);
     free(rho); free(u); free(T); free(xc);
     return 0;
 }
@@ -1610,31 +1616,35 @@ static double mode_value(const double hx[4], const double hy[4], const double hz
     return hx[m >> 4] * hy[(m >> 2) & 3] * hz[m & 3];
 }
 
+/* the 64 coefficients of one cell's f (and its rho, u, T into mom5 unless
+ * NULL) */
+static void hermite_cell(const orc_problem *p, const double *fc, double *a64, double *mom5)
+{
+    double rho, u[3], T;
+    cell_moments(p, fc, &rho, u, &T);
+    double sq = sqrt(T);
+    double acc[64] = {0};
+    for (int64_t v = 0; v < p->nv; v++) {
+        const double *x = &p->xi[3 * v];
+        double hx[4], hy[4], hz[4];
+        hermite4((x[0] - u[0]) / sq, hx);
+        hermite4((x[1] - u[1]) / sq, hy);
+        hermite4((x[2] - u[2]) / sq, hz);
+        for (int m = 0; m < 64; m++) acc[m] += fc[v] * mode_value(hx, hy, hz, m);
+    }
+    for (int m = 0; m < 64; m++) a64[m] = acc[m] * p->dV / rho;
+    if (mom5) {
+        mom5[0] = rho;
+        for (int d = 0; d < 3; d++) mom5[1 + d] = u[d];
+        mom5[4] = T;
+    }
+}
+
 int orc_hermite_project(const orc_problem *p, const double *f, double *a, double *mom)
 {
     if (!f && !p->f) return -1; /* a problem without f storage */
     const double *F = f ? f : p->f;
-    for (int64_t c = 0; c < p->ncells; c++) {
-        const double *fc = &F[c * p->nv];
-        double rho, u[3], T;
-        cell_moments(p, fc, &rho, u, &T);
-        double sq = sqrt(T);
-        double acc[64] = {0};
-        for (int64_t v = 0; v < p->nv; v++) {
-            const double *x = &p->xi[3 * v];
-            double hx[4], hy[4], hz[4];
-            hermite4((x[0] - u[0]) / sq, hx);
-            hermite4((x[1] - u[1]) / sq, hy);
-            hermite4((x[2] - u[2]) / sq, hz);
-            for (int m = 0; m < 64; m++) acc[m] += fc[v] * mode_value(hx, hy, hz, m);
-        }
-        for (int m = 0; m < 64; m++) a[c * 64 + m] = acc[m] * p->dV / rho;
-        if (mom) {
-            mom[c * 5] = rho;
-            for (int d = 0; d < 3; d++) mom[c * 5 + 1 + d] = u[d];
-            mom[c * 5 + 4] = T;
-        }
-    }
+    for (int64_t c = 0; c < p->ncells; c++) hermite_cell(p, &F[c * p->nv], &a[c * 64], mom ? &mom[c * 5] : NULL);
     return 0;
 }
 
@@ -1749,6 +1759,82 @@ int orc_mlp_backward(int64_t n, const double *params, const double *x, const dou
 /* ------------------------------------------------------------------------ */
 /* Learned collision with conservative projection, entropy check, fallback:
  * the application of given network outputs o, gated by the given local Kn. */
+/* the learned update of one cell's f (in place): gate on its local Kn,
+ * reconstruction of the network term o64 in the cell's Hermite basis,
+ * conservative correction, entropy check; qhs_c (the plain hard-sphere term
+ * of the cell, may be NULL) replaces the term where the gate or a check
+ * rejects it.  -1 if it is rejected and there is no plain term. */
+static int learned_cell(const orc_problem *p, double *f, double knl, const double *o64, double kn_threshold,
+                        const double *qhs_c, double dt, double kn, int32_t *used, double *q_c)
+{
+    int64_t nv = p->nv;
+    double rho, u[3], T;
+    cell_moments(p, f, &rho, u, &T);
+    double sq = sqrt(T);
+    double *Q = (double *)malloc((size_t)nv * sizeof(double));
+    int ok = knl < kn_threshold;
+    if (ok) {
+        double A[25] = {0}, rhs[5] = {0}, cc[5];
+        double *M = (double *)malloc((size_t)nv * sizeof(double));
+        for (int64_t v = 0; v < nv; v++) {
+            const double *x = &p->xi[3 * v];
+            double g[3], hx[4], hy[4], hz[4];
+            for (int d = 0; d < 3; d++) g[d] = (x[d] - u[d]) / sq;
+            hermite4(g[0], hx);
+            hermite4(g[1], hy);
+            hermite4(g[2], hz);
+            double s = 0.0;
+            for (int m = 0; m < 64; m++) s += o64[m] * mode_value(hx, hy, hz, m);
+            M[v] = maxwellian(rho, u, T, x);
+            Q[v] = rho * sq * M[v] * s;
+            double ph[5] = {1.0, g[0], g[1], g[2], g[0] * g[0] + g[1] * g[1] + g[2] * g[2] - 3.0};
+            for (int r = 0; r < 5; r++) {
+                for (int k = 0; k < 5; k++) A[r * 5 + k] += ph[r] * ph[k] * M[v] * p->dV;
+                rhs[r] += ph[r] * Q[v] * p->dV;
+            }
+        }
+        if (orc_solve(5, A, rhs, cc)) ok = 0;
+        double ent = 0.0, qabs = 0.0;
+        for (int64_t v = 0; v < nv && ok; v++) {
+            const double *x = &p->xi[3 * v];
+            double g[3];
+            for (int d = 0; d < 3; d++) g[d] = (x[d] - u[d]) / sq;
+            double ph[5] = {1.0, g[0], g[1], g[2], g[0] * g[0] + g[1] * g[1] + g[2] * g[2] - 3.0};
+            double corr = 0.0;
+            for (int r = 0; r < 5; r++) corr += cc[r] * ph[r];
+            Q[v] -= M[v] * corr;
+            ent += Q[v] * log(f[v] > 0.0 ? f[v] : 1e-300) * p->dV;
+            qabs += fabs(Q[v]) * p->dV;
+        }
+        /* entropy production sum Q ln f dV non-positive (H-theorem),
+         * up to the error of its evaluation.  The bound 1e-5 sum |Q| dV
+         * is set by the FP32 evaluation on the device, which sums
+         * Q ln(f/M) (ln M is a collision invariant, so the exact sum is
+         * the same) with about 54 terms per thread: a relative error of
+         * at most 54 * 2^-24 = 3.2e-6 of sum |Q| |ln(f/M)| dV, and ln(f/M)
+         * is O(1) where Q is not negligible.  A term whose exact
+         * production is <= 0 is therefore kept on both sides; here in
+         * FP64 the invariant part sum Q ln M cancels to the correction's
+         * residual (1e-12 of its scale).  An equilibrium cell, where the
+         * production is zero up to rounding, passes. */
+        if (ok && !(ent <= 1e-5 * qabs)) ok = 0;
+        free(M);
+    }
+    if (!ok) {
+        if (!qhs_c) { free(Q); return -1; }
+        for (int64_t v = 0; v < nv; v++) Q[v] = qhs_c[v];
+    }
+    if (used) *used = ok;
+    for (int64_t v = 0; v < nv; v++) {
+        if (q_c) q_c[v] = Q[v];
+        f[v] += dt / kn * Q[v];
+    }
+    free(Q);
+    return 0;
+}
+
+/* Learned collision with conservative projection, entropy check, fallback:
+ * the application of given network outputs o, gated by the given local Kn. */
 int orc_learned_apply(orc_problem *p, double dt, double kn, const double *knl, const double *o,
                       double kn_threshold, int32_t *used, double *q)
 {
@@ -1765,73 +1851,31 @@ int orc_learned_apply(orc_problem *p, double dt, double kn, const double *knl, c
         free(f0);
     }
     int err = 0;
-    for (int64_t c = 0; c < nc; c++) {
-        double *f = &p->f[c * nv];
-        double rho, u[3], T;
-        cell_moments(p, f, &rho, u, &T);
-        double sq = sqrt(T);
-        double *Q = (double *)malloc((size_t)nv * sizeof(double));
-        int ok = knl[c] < kn_threshold;
-        if (ok) {
-            double A[25] = {0}, rhs[5] = {0}, cc[5];
-            double *M = (double *)malloc((size_t)nv * sizeof(double));
-            for (int64_t v = 0; v < nv; v++) {
-                const double *x = &p->xi[3 * v];
-                double g[3], hx[4], hy[4], hz[4];
-                for (int d = 0; d < 3; d++) g[d] = (x[d] - u[d]) / sq;
-                hermite4(g[0], hx);
-                hermite4(g[1], hy);
-                hermite4(g[2], hz);
-                double s = 0.0;
-                for (int m = 0; m < 64; m++) s += o[c * 64 + m] * mode_value(hx, hy, hz, m);
-                M[v] = maxwellian(rho, u, T, x);
-                Q[v] = rho * sq * M[v] * s;
-                double ph[5] = {1.0, g[0], g[1], g[2], g[0] * g[0] + g[1] * g[1] + g[2] * g[2] - 3.0};
-                for (int r = 0; r < 5; r++) {
-                    for (int k = 0; k < 5; k++) A[r * 5 + k] += ph[r] * ph[k] * M[v] * p->dV;
-                    rhs[r] += ph[r] * Q[v] * p->dV;
-                }
-            }
-            if (orc_solve(5, A, rhs, cc)) ok = 0;
-            double ent = 0.0, qabs = 0.0;
-            for (int64_t v = 0; v < nv && ok; v++) {
-                const double *x = &p->xi[3 * v];
-                double g[3];
-                for (int d = 0; d < 3; d++) g[d] = (x[d] - u[d]) / sq;
-                double ph[5] = {1.0, g[0], g[1], g[2], g[0] * g[0] + g[1] * g[1] + g[2] * g[2] - 3.0};
-                double corr = 0.0;
-                for (int r = 0; r < 5; r++) corr += cc[r] * ph[r];
-                Q[v] -= M[v] * corr;
-                ent += Q[v] * log(f[v] > 0.0 ? f[v] : 1e-300) * p->dV;
-                qabs += fabs(Q[v]) * p->dV;
-            }
-            /* entropy production sum Q ln f dV non-positive (H-theorem),
-             * up to the error of its evaluation.  The bound 1e-5 sum |Q| dV
-             * is set by the FP32 evaluation on the device, which sums
-             * Q ln(f/M) (ln M is a collision invariant, so the exact sum is
-             * the same) with about 54 terms per thread: a relative error of
-             * at most 54 * 2^-24 = 3.2e-6 of sum |Q| |ln(f/M)| dV, and ln(f/M)
-             * is O(1) where Q is not negligible.  A term whose exact
-             * production is <= 0 is therefore kept on both sides; here in
-             * FP64 the invariant part sum Q ln M cancels to the correction's
-             * residual (1e-12 of its scale).  An equilibrium cell, where the
-             * production is zero up to rounding, passes. */
-            if (ok && !(ent <= 1e-5 * qabs)) ok = 0;
-            free(M);
-        }
-        if (!ok) {
-            if (!qhs) { err = 1; free(Q); continue; }
-            for (int64_t v = 0; v < nv; v++) Q[v] = qhs[c * nv + v];
-        }
-        if (used) used[c] = ok;
-        for (int64_t v = 0; v < nv; v++) {
-            if (q) q[c * nv + v] = Q[v];
-            f[v] += dt / kn * Q[v];
-        }
-        free(Q);
-    }
+    for (int64_t c = 0; c < nc; c++)
+        if (learned_cell(p, &p->f[c * nv], knl[c], &o[c * 64], kn_threshold, qhs ? &qhs[c * nv] : NULL, dt, kn,
+                         used ? &used[c] : NULL, q ? &q[c * nv] : NULL))
+            err = 1;
     free(qhs);
     return err ? -1 : 0;
+}
+
+/* the 64 coefficients of the Maxwellian M(rho, u, T) sampled at the nodes,
+ * in its own Hermite basis (mom5 = rho, u, T) */
+static void hermite_maxwellian_cell(const orc_problem *p, const double *mom5, double *a64)
+{
+    const double rho = mom5[0], T = mom5[4], *u = &mom5[1];
+    const double sq = sqrt(T);
+    double acc[64] = {0};
+    for (int64_t v = 0; v < p->nv; v++) {
+        const double *x = &p->xi[3 * v];
+        double hx[4], hy[4], hz[4];
+        hermite4((x[0] - u[0]) / sq, hx);
+        hermite4((x[1] - u[1]) / sq, hy);
+        hermite4((x[2] - u[2]) / sq, hz);
+        const double M = maxwellian(rho, u, T, x);
+        for (int m = 0; m < 64; m++) acc[m] += M * mode_value(hx, hy, hz, m);
+    }
+    for (int m = 0; m < 64; m++) a64[m] = acc[m] * p->dV / rho;
 }
 
 /* The whole learned update: local Kn, projection, network, application.
@@ -1842,33 +1886,90 @@ int orc_learned_collide(orc_problem *p, double dt, double kn, const double *para
                         double kn_threshold, int32_t *used, double *q)
 {
     if (!p->f) return -1; /* a problem without f storage */
-    int64_t nc = p->ncells, nv = p->nv;
+    int64_t nc = p->ncells;
     double *knl = (double *)malloc((size_t)nc * sizeof(double));
     double *a = (double *)malloc((size_t)nc * 128 * sizeof(double));
     double *o = (double *)malloc((size_t)nc * 128 * sizeof(double));
     double *mom = (double *)malloc((size_t)nc * 5 * sizeof(double));
     orc_kn_local(p, kn, knl);
     orc_hermite_project(p, NULL, a, mom);
-    for (int64_t c = 0; c < nc; c++) {
-        const double rho = mom[c * 5], T = mom[c * 5 + 4], *u = &mom[c * 5 + 1];
-        const double sq = sqrt(T);
-        double acc[64] = {0};
-        for (int64_t v = 0; v < nv; v++) {
-            const double *x = &p->xi[3 * v];
-            double hx[4], hy[4], hz[4];
-            hermite4((x[0] - u[0]) / sq, hx);
-            hermite4((x[1] - u[1]) / sq, hy);
-            hermite4((x[2] - u[2]) / sq, hz);
-            const double M = maxwellian(rho, u, T, x);
-            for (int m = 0; m < 64; m++) acc[m] += M * mode_value(hx, hy, hz, m);
-        }
-        for (int m = 0; m < 64; m++) a[(nc + c) * 64 + m] = acc[m] * p->dV / rho;
-    }
+    for (int64_t c = 0; c < nc; c++) hermite_maxwellian_cell(p, &mom[c * 5], &a[(nc + c) * 64]);
     orc_mlp_forward(2 * nc, params, a, o);
     for (int64_t k = 0; k < nc * 64; k++) o[k] -= o[nc * 64 + k];
     int rc = orc_learned_apply(p, dt, kn, knl, o, kn_threshold, used, q);
     free(knl); free(a); free(o); free(mom);
     return rc;
+}
+
+/* One learned step (transport, Eq. 2, then the learned update with the
+ * hard-sphere fallback) of selected cells from supplied rows: the rows of
+ * inputs must cover the cells' face neighbours and theirs (the local Kn
+ * reads the moments of the neighbours' f*).  Per-cell arithmetic as in the
+ * full step; knl_out and used (may be NULL) get the cells' local Kn and
+ * gate outcome. */
+int orc_step_cells_learned(const orc_problem *p, int64_t n, const int64_t *cells, int64_t ninp,
+                           const int64_t *inputs, const double *fin, double dt, double kn, const double *params,
+                           double kn_threshold, double *knl_out, int32_t *used, double *out)
+{
+    if (!p->hs_start) return -1;
+    const int64_t nv = p->nv, nc = p->ncells;
+    /* the cells whose f* the step reads: the cells and their face neighbours */
+    const int64_t n1 = orc_step_inputs(p, n, cells, NULL);
+    if (n1 < 0) return -1;
+    int64_t *ring = (int64_t *)malloc((size_t)(n1 > 0 ? n1 : 1) * sizeof(int64_t));
+    orc_step_inputs(p, n, cells, ring);
+    row_table t = {ninp, inputs, fin};
+    for (int64_t i = 0; i < n1; i++) {
+        int miss = !row_sparse(p, &t, ring[i]);
+        for (int64_t e = p->cf_start[ring[i]]; e < p->cf_start[ring[i] + 1] && !miss; e++) {
+            const int64_t q = p->cf_list[e];
+            if (q >= 0 && (!row_sparse(p, &t, p->cell_of_leaf[p->fm[q]]) || !row_sparse(p, &t, p->cell_of_leaf[p->fp[q]])))
+                miss = 1;
+        }
+        if (miss) { free(ring); return -1; }
+    }
+    double *fs = (double *)malloc((size_t)(n1 * nv) * sizeof(double));
+    double *rho = (double *)calloc((size_t)nc, sizeof(double));
+    double *u = (double *)calloc((size_t)nc * 3, sizeof(double));
+    double *T = (double *)calloc((size_t)nc, sizeof(double));
+    double *xc = (double *)malloc((size_t)nc * 3 * sizeof(double));
+    orc_cell_centres(p, xc, NULL);
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t i = 0; i < n1; i++) {
+        transport_cell(p, ring[i], row_sparse, &t, dt, &fs[i * nv]);
+        cell_moments(p, &fs[i * nv], &rho[ring[i]], &u[3 * ring[i]], &T[ring[i]]);
+    }
+    row_table ts = {n1, ring, fs};
+    double *a = (double *)malloc((size_t)(n > 0 ? n : 1) * 128 * sizeof(double));
+    double *o = (double *)malloc((size_t)(n > 0 ? n : 1) * 128 * sizeof(double));
+    double *knl = (double *)malloc((size_t)(n > 0 ? n : 1) * sizeof(double));
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t i = 0; i < n; i++) {
+        double mom5[5];
+        knl[i] = kn_cell(p, cells[i], kn, rho, u, T, xc);
+        hermite_cell(p, row_sparse(p, &ts, cells[i]), &a[i * 64], mom5);
+        hermite_maxwellian_cell(p, mom5, &a[(n + i) * 64]);
+    }
+    orc_mlp_forward(2 * n, params, a, o);
+    for (int64_t k = 0; k < n * 64; k++) o[k] -= o[n * 64 + k];
+    int err = 0;
+#pragma omp parallel for schedule(dynamic, 1) reduction(| : err)
+    for (int64_t i = 0; i < n; i++) {
+        double *row = &out[i * nv];
+        memcpy(row, row_sparse(p, &ts, cells[i]), (size_t)nv * sizeof(double));
+        /* the plain term of the cell: the hard-sphere update with dt = 0, Kn = 1 */
+        double *f0 = (double *)malloc((size_t)nv * sizeof(double));
+        double *qhs = (double *)malloc((size_t)nv * sizeof(double));
+        memcpy(f0, row, (size_t)nv * sizeof(double));
+        if (hs_cell(p, f0, 0.0, 1.0, qhs, NULL, NULL)) err = 1;
+        else if (learned_cell(p, row, knl[i], &o[i * 64], kn_threshold, qhs, dt, kn, used ? &used[i] : NULL, NULL))
+            err = 1;
+        if (knl_out) knl_out[i] = knl[i];
+        free(f0);
+        free(qhs);
+    }
+    free(ring); free(fs); free(rho); free(u); free(T); free(xc); free(a); free(o); free(knl);
+    return err ? -1 : 0;
 }
 
 /* ------------------------------------------------------------------------ */

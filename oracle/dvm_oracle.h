@@ -188,6 +188,16 @@ int orc_learned_collide(orc_problem *p, double dt, double kn, const double *para
  * orc_hermite_project, orc_mlp_forward and this). */
 int orc_learned_apply(orc_problem *p, double dt, double kn, const double *knl, const double *o,
                       double kn_threshold, int32_t *used, double *q);
+/* One learned step (transport, then the learned update with the hard-sphere
+ * fallback, as orc_step with no collision followed by orc_learned_collide)
+ * of cells[0..n) from supplied rows; inputs (sorted) must cover the cells'
+ * face neighbours and theirs, as orc_step_inputs applied twice gives them.
+ * out [n][nv]; knl_out [n] and used [n] (may be NULL) get each cell's local
+ * Kn and whether the learned term was kept.  -1 on a missing row, missing
+ * tables or a failed update. */
+int orc_step_cells_learned(const orc_problem *p, int64_t n, const int64_t *cells, int64_t ninp,
+                           const int64_t *inputs, const double *fin, double dt, double kn, const double *params,
+                           double kn_threshold, double *knl_out, int32_t *used, double *out);
 
 /* Gaussian elimination with partial pivoting on an n x n system (n <= 8);
  * A is row-major and is overwritten.  Returns 0, or -1 if singular. */

@@ -1,14 +1,17 @@
-"""The Mach-5 sphere flow at its full size (1,014,080 cells x 13,824 velocities,
-the bench's workload) against the oracle on sampled cells: the GPU steps the
-whole tree; the oracle steps only the sample, from the rows its face
-neighbourhood reads (tests/sampling.py).  The sample covers wall, inflow and
-outflow faces and level changes, as well as seeded random cells."""
+"""The bench's workloads at their full size against the oracle on sampled
+cells: the Mach-5 sphere flow with BGK (1,014,080 cells x 13,824 velocities)
+and the Mach-3 sphere flow with the hard-sphere integral (253,360 cells x
+13,824 velocities), plain and with the learned operator.  The
+GPU steps the whole tree; the oracle steps only the sample, from the rows its
+face neighbourhood reads (tests/sampling.py).  The sample covers wall, inflow
+and outflow faces and level changes, as well as seeded random cells."""
 import numpy as np
 import pytest
 
+import oracle as O
 import paper_1503_00707_gb300 as D
 import workloads as W
-from tests.gpu_util import pair, rel_linf
+from tests.gpu_util import pair, random_params, rel_linf
 from tests.sampling import cell_sample, oracle_rows_after, oracle_sparse_for
 
 pytestmark = pytest.mark.gpu
@@ -54,6 +57,93 @@ def test_mach5_full_size_sampled_cells(prec, tol, tol_rho):
         # the density of each sampled cell, from its rows
         rho_g, rho_o = got.sum(1) * o.dV, want.sum(1) * o.dV
         assert np.max(np.abs(rho_g - rho_o) / rho_o) < tol_rho
+    finally:
+        s.close()
+
+
+def test_mach3_hard_sphere_full_size_sampled_cells():
+    """Two hard-sphere steps (Eqs. 3-6, 128 trials per node, Kn 0.003) from a
+    two-beam state perturbed per cell by up to 5%; dt = Kn/1000 keeps dt/Kn
+    max(P B) below 1 (about 130 in the far tails of this state, against
+    about 900 for the fully random two-beam states, which the library
+    refuses at this dt).  Per-element bar 2e-5 (up to 128 FP32 products
+    summed per node, table weights rounded to FP32), as in the other
+    hard-sphere tests."""
+    c = dict(W.CONFIGS["c5_sphere_m3_hs"], init="bimodal_near")
+    s = D.solver_from_config(c, D.F32, D.COLL_HS)
+    try:
+        o = oracle_sparse_for(c)
+        assert s.ncells == o.ncells == 253360 and s.nv == o.nv == 13824
+        xyz, _ = s.centres()
+        xo, _ = o.centres()
+        assert np.array_equal(xyz, xo)
+        s.set_collision_tables(c["trials"], W.SEED)
+        o.hs_tables(c["trials"], W.SEED)
+        init = W.initial_state(c, xo)
+        s.init_maxwellian(*init)
+        dt = min(o.dt_cfl(c["cfl"]), c["kn"] / 1000)
+        cells = cell_sample(o, 64, 16, seed=12)
+        s.step(2, dt)
+        got = s.get_f_rows(cells)
+        want = oracle_rows_after(o, cells, init, 2, dt, c["kn"], O.COLL_HS)
+        assert rel_linf(got, want) < 2e-5
+        # the two steps moved the sampled rows far beyond the bar
+        start = oracle_rows_after(o, cells, init, 0, dt, c["kn"])
+        assert rel_linf(want, start) > 1e-3
+    finally:
+        s.close()
+
+
+def _split_threshold(knl):
+    """A threshold in the widest relative gap of the middle half of the
+    sampled local Kn numbers: both sides put every sampled cell on the same
+    side of it."""
+    k = np.sort(knl)
+    lo, hi = len(k) // 4, 3 * len(k) // 4
+    gaps = (k[lo + 1:hi + 1] - k[lo:hi]) / k[lo + 1:hi + 1]
+    i = lo + int(np.argmax(gaps))
+    assert gaps.max() > 1e-3
+    return float(0.5 * (k[i] + k[i + 1]))
+
+
+def test_mach3_learned_full_size_sampled_cells():
+    """One learned step (Kn gate, 64-mode projection, BF16 network, conservative
+    correction, entropy check, hard-sphere fallback) on the full tree from a
+    two-beam state perturbed per cell by up to 5%, so that the local Kn
+    spreads and the gate splits the sampled cells.  The oracle steps the
+    sample with the same network in FP64 from two rings of neighbour rows.
+    Bar 2e-3 per element, as for the learned step on the small tree (BF16
+    network outputs within 2e-2 of the FP64 network's, carried into f by
+    dt/Kn); the gate's threshold sits in a gap of the sampled local Kn."""
+    c = dict(W.CONFIGS["c5_sphere_m3_hs"], init="bimodal_near")
+    s = D.solver_from_config(c, D.F32, D.COLL_LEARNED)
+    try:
+        o = oracle_sparse_for(c)
+        assert s.ncells == o.ncells == 253360
+        xyz, _ = s.centres()
+        xo, _ = o.centres()
+        assert np.array_equal(xyz, xo)
+        s.set_collision_tables(c["trials"], W.SEED)
+        o.hs_tables(c["trials"], W.SEED)
+        # a seeded network whose term passes the entropy check in these
+        # cells (their states are alike, so the check agrees across them)
+        params = random_params(1, gain=0.3, bias=0.0)
+        s.set_weights(params)
+        init = W.initial_state(c, xo)
+        s.init_maxwellian(*init)
+        dt = min(o.dt_cfl(c["cfl"]), c["kn"] / 1000)
+        cells = cell_sample(o, 96, 16, seed=13)
+        ring2 = o.step_inputs(o.step_inputs(cells))
+        w, r, u, T = init
+        fin = o.maxwellian_rows(w[ring2], r[ring2], u[ring2], T[ring2])
+        _, knl, _ = o.step_cells_learned(cells, ring2, fin, dt, c["kn"], params.astype(np.float64), -1.0)
+        thr = _split_threshold(knl)
+        want, _, used = o.step_cells_learned(cells, ring2, fin, dt, c["kn"], params.astype(np.float64), thr)
+        assert 0 < used.sum() < cells.size  # both branches among the sampled cells
+        s.learned_configure(thr)
+        s.step(1, dt)
+        got = s.get_f_rows(cells)
+        assert rel_linf(got, want) < 2e-3
     finally:
         s.close()
 

@@ -32,7 +32,7 @@ MUTANTS = [
      "tests/test_oracle_collision.py::test_bgk_frequency_equals_hs_mean_frequency"),
     ("hard-sphere weight normalisation", "/ (sqrt(2.0) * (double)trials)", "/ (2.0 * (double)trials)",
      "tests/test_oracle_collision.py::test_hs_mean_collision_frequency_of_maxwellian"),
-    ("local Kn without the mean free path 1/rho", "out[c] = kn / rho[c] * m;", "out[c] = kn * m;",
+    ("local Kn without the mean free path 1/rho", "return kn / rho[c] * m;", "return kn * m;",
      "tests/test_oracle_learned.py::test_kn_local_linear_fields_exact_on_uniform_tree"),
     ("entropic Newton step with the wrong sign", "for (int r = 0; r < 5; r++) a[r] -= da[r];",
      "for (int r = 0; r < 5; r++) a[r] += da[r];",

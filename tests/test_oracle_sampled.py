@@ -6,6 +6,7 @@ import pytest
 
 import oracle as O
 import workloads as W
+from tests.gpu_util import random_params
 from tests.sampling import cell_sample, oracle_rows_after, oracle_sparse_for
 
 
@@ -87,3 +88,37 @@ def test_missing_rows_and_bad_indices_refused():
         sp.step_inputs(np.array([sp.ncells]))
     with pytest.raises(RuntimeError):
         sp.get_f()
+
+
+def test_selected_cells_learned_equal_full_step():
+    """Transport, then the learned update with the hard-sphere fallback: the
+    sampled rows, local Kn and gate outcomes equal the full step's bit for
+    bit, with the threshold splitting the cells."""
+    c = dict(_case(), init="bimodal_near")
+    o, sp = _dense(c), oracle_sparse_for(c)
+    o.hs_tables(16, W.SEED)
+    sp.hs_tables(16, W.SEED)
+    xyz, _ = o.centres()
+    init = W.initial_state(c, xyz)
+    o.init_maxwellian(*init)
+    params = random_params(3, gain=0.3, bias=0.0).astype(np.float64)
+    dt = o.dt_cfl(c["cfl"]) / 4
+    o.step(1, dt, O.COLL_NONE, c["kn"])
+    knl = o.kn_local(c["kn"])
+    ks = np.sort(knl)
+    thr = float(0.5 * (ks[len(ks) // 2 - 1] + ks[len(ks) // 2]))
+    used, _ = o.learned_collide(dt, c["kn"], params, thr)
+    cells = cell_sample(sp, 24, 8, seed=6)
+    ring2 = sp.step_inputs(sp.step_inputs(cells))
+    w, r, u, T = init
+    fin = sp.maxwellian_rows(w[ring2], r[ring2], u[ring2], T[ring2])
+    rows, knl_s, used_s = sp.step_cells_learned(cells, ring2, fin, dt, c["kn"], params, thr)
+    assert np.array_equal(knl_s, knl[cells])
+    assert np.array_equal(used_s, used[cells])
+    assert 0 < used_s.sum() < cells.size
+    assert np.array_equal(rows, o.get_f()[cells])
+    # one ring of rows is not enough: the local Kn reads the neighbours' f*
+    ring1 = sp.step_inputs(cells)
+    f1 = sp.maxwellian_rows(w[ring1], r[ring1], u[ring1], T[ring1])
+    with pytest.raises(RuntimeError):
+        sp.step_cells_learned(cells, ring1, f1, dt, c["kn"], params, thr)

@@ -156,6 +156,25 @@ def initial_state(cfg, centres, seed=SEED):
         u = np.stack([a1[:, None] * nvec, -a2[:, None] * nvec], axis=1)
         T = np.stack([T1, T2], axis=1)
         return w, rho, u, T
+    if kind == "bimodal_near":
+        # one two-beam state (weights 1/2, beams of speed 1.5 along +-x,
+        # temperatures 0.6) perturbed per cell by seeded relative amounts of
+        # up to 5%: away from equilibrium everywhere, with gradients small
+        # enough that the local Kn of a Kn = 0.003 flow spreads across 0.05
+        g = np.random.default_rng(seed + 3)
+        e = 0.05
+        w1 = 0.5 * (1.0 + e * g.uniform(-1.0, 1.0, nc))
+        a1 = 1.5 * (1.0 + e * g.uniform(-1.0, 1.0, nc))
+        a2 = 1.5 * (1.0 + e * g.uniform(-1.0, 1.0, nc))
+        T1 = 0.6 * (1.0 + e * g.uniform(-1.0, 1.0, nc))
+        T2 = 0.6 * (1.0 + e * g.uniform(-1.0, 1.0, nc))
+        nvec = np.stack([np.ones(nc), e * g.uniform(-1.0, 1.0, nc), e * g.uniform(-1.0, 1.0, nc)], axis=1)
+        nvec /= np.linalg.norm(nvec, axis=1, keepdims=True)
+        w = np.stack([w1, 1.0 - w1], axis=1)
+        rho = np.ones((nc, 2))
+        u = np.stack([a1[:, None] * nvec, -a2[:, None] * nvec], axis=1)
+        T = np.stack([T1, T2], axis=1)
+        return w, rho, u, T
     raise ValueError(kind)
 
 
