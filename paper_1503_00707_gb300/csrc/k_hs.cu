@@ -6,8 +6,9 @@
 // gathers f across cells from a velocity-major copy; here the roles are
 // swapped to keep every gather on chip:
 //
-//  k_hs_bc   table-stationary: a CTA holds the trials of 64 nodes in
-//            registers (32 per thread) and streams cells through a
+//  k_hs_bc   table-stationary: a CTA holds the trials of 64 nodes (256
+//            threads) or, on grids of more than 6144 nodes, 128 nodes (512
+//            threads) in registers (32 per thread) and streams cells through a
 //            double-buffered shared-memory tile, each tile a single bulk
 //            copy (cp.async.bulk, completion on an mbarrier).  It writes
 //            B_i = sum_k b f_gamma (Eq. 4) and C_i = sum_k c f_l f_m (Eq. 5)
@@ -35,11 +36,12 @@ void count_launch();
 
 namespace {
 
-constexpr int HT = 256;   // threads per CTA of k_hs_bc
 constexpr int HE = 32;    // trials held per thread
 constexpr int CT = 256;   // threads per CTA of k_hs_corr
 
-__global__ void __launch_bounds__(HT, 2)
+// HT threads per CTA (256 or 512; at most 128 registers a thread either way)
+template <int HT>
+__global__ void __launch_bounds__(HT, 512 / HT)
     k_hs_bc(const float *__restrict__ fs, float2 *__restrict__ bc, int64_t ncells, int nv, int M,
             const uint2 *__restrict__ idx, const float *__restrict__ bw, int64_t cells_per_cta,
             const int32_t *__restrict__ list, const int *__restrict__ count, int *status)
@@ -416,34 +418,67 @@ static int64_t hs_splits(int chunks, int slots, int64_t ncells)
     return std::max<int64_t>(1, std::min<int64_t>(best, ncells));
 }
 
+// The launch shape of k_hs_bc for nv nodes and ncells rows.  Each CTA streams
+// the whole f of every cell of its range through shared memory for the trials
+// of its nodes, so the tile is worth 3 M npc / nv gathers per loaded value:
+// 1.8 at 24^3 with 64 nodes per CTA, 3.6 with 128.  Grids of more than 6144
+// nodes take 512 threads (128 nodes), the others 256 (measured: 24^3, 543.9 ->
+// 389.8 ms per step on the 253k-cell flow; 16^3 is 1.5% faster with 256).
+// Every check that can refuse the launch is made here, before anything is
+// queued.
+struct BcLaunch {
+    int threads = 0;
+    dim3 grid;
+    size_t dyn = 0;
+    int64_t per = 0;  // rows per CTA
+};
+
+static int bc_plan(const HsTables &t, int nv, int64_t ncells, BcLaunch &L)
+{
+    const int ht = nv > 6144 ? 512 : 256;
+    const int tpn = t.trials / HE, npc = ht / tpn;
+    const int chunks = (nv + npc - 1) / npc;
+    const size_t dyn = 2 * (size_t)nv * sizeof(float);
+    if (dyn > 200 * 1024) return DVM_ENOTIMPL;
+    auto kern = ht == 512 ? k_hs_bc<512> : k_hs_bc<256>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) != cudaSuccess)
+        return DVM_ECUDA;
+    int dev = 0, nsm = 0, occ = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, ht, dyn) != cudaSuccess || occ < 1)
+        return DVM_ENOTIMPL;
+    int64_t splits = hs_splits(chunks, nsm * occ, ncells);
+    L.per = (ncells + splits - 1) / splits;
+    splits = (ncells + L.per - 1) / L.per;
+    L.threads = ht;
+    L.grid = dim3((unsigned)chunks, (unsigned)splits);
+    L.dyn = dyn;
+    return DVM_OK;
+}
+
+static int bc_launch(const BcLaunch &L, const HsTables &t, const float *f, float2 *bc, int64_t ncells, int nv,
+                     const int32_t *list, const int *count, cudaStream_t s, int *status)
+{
+    const uint2 *idx = static_cast<const uint2 *>(t.d_idx);
+    if (L.threads == 512)
+        k_hs_bc<512><<<L.grid, 512, L.dyn, s>>>(f, bc, ncells, nv, t.trials, idx, t.d_b, L.per, list, count, status);
+    else
+        k_hs_bc<256><<<L.grid, 256, L.dyn, s>>>(f, bc, ncells, nv, t.trials, idx, t.d_b, L.per, list, count, status);
+    count_launch();
+    return cudaGetLastError() == cudaSuccess ? DVM_OK : DVM_ECUDA;
+}
+
 int launch_hs_collide(HsTables &t, const StepParams &p, void *f, double kn, double dt)
 {
     if (p.prec != DVM_F32) return DVM_ENOTIMPL;
     if (!t.ready || t.nv != p.nv || !t.d_bc) return DVM_ESTATE;
-    const int tpn = t.trials / HE, npc = HT / tpn;
-    const int chunks = (p.nv + npc - 1) / npc;
-    const size_t dyn = 2 * (size_t)p.nv * sizeof(float);
-    static bool configured = false;
-    if (!configured) {
-        if (cudaFuncSetAttribute(k_hs_bc, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) != cudaSuccess)
-            return DVM_ECUDA;
-        configured = true;
-    }
-    if (dyn > 200 * 1024) return DVM_ENOTIMPL;
-    int dev = 0, nsm = 0, occ = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_hs_bc, HT, dyn) != cudaSuccess || occ < 1)
-        return DVM_ENOTIMPL;
-    int64_t splits = hs_splits(chunks, nsm * occ, p.ncells);
-    const int64_t per = (p.ncells + splits - 1) / splits;
-    splits = (p.ncells + per - 1) / per;
-    const dim3 grid((unsigned)chunks, (unsigned)splits);
-    k_hs_bc<<<grid, HT, dyn, p.stream>>>(static_cast<const float *>(f), reinterpret_cast<float2 *>(t.d_bc),
-                                          p.ncells, p.nv, t.trials, static_cast<const uint2 *>(t.d_idx), t.d_b,
-                                          per, nullptr, nullptr, p.status);
-    count_launch();
-    if (cudaGetLastError() != cudaSuccess) return DVM_ECUDA;
+    BcLaunch L;
+    int rc = bc_plan(t, p.nv, p.ncells, L);
+    if (!rc)
+        rc = bc_launch(L, t, static_cast<const float *>(f), reinterpret_cast<float2 *>(t.d_bc), p.ncells, p.nv,
+                       nullptr, nullptr, p.stream, p.status);
+    if (rc) return rc;
     k_hs_corr<<<(unsigned)p.ncells, CT, 0, p.stream>>>(static_cast<float *>(f),
                                                       reinterpret_cast<const float2 *>(t.d_bc), t.d_xi, t.d_jpk,
                                                       t.hh, p.dV, p.mom_out, p.nv,
@@ -461,25 +496,12 @@ int launch_hs_general(HsTables &t, const StepParams &p, float *f, const int32_t 
     if (p.prec != DVM_F32) return DVM_ENOTIMPL;
     if (!t.ready || t.nv != p.nv || !t.d_bc || t.bc_cells < p.ncells) return DVM_ESTATE;
     if (p.ncells <= 0) return DVM_OK;
-    const int tpn = t.trials / HE, npc = HT / tpn;
-    const int chunks = (p.nv + npc - 1) / npc;
-    const size_t dyn = 2 * (size_t)p.nv * sizeof(float);
-    if (dyn > 200 * 1024) return DVM_ENOTIMPL;
-    if (cudaFuncSetAttribute(k_hs_bc, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) != cudaSuccess)
-        return DVM_ECUDA;
-    int dev = 0, nsm = 0, occ = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_hs_bc, HT, dyn) != cudaSuccess || occ < 1)
-        return DVM_ENOTIMPL;
-    int64_t splits = hs_splits(chunks, nsm * occ, p.ncells);
-    const int64_t per = (p.ncells + splits - 1) / splits;
-    splits = (p.ncells + per - 1) / per;
-    k_hs_bc<<<dim3((unsigned)chunks, (unsigned)splits), HT, dyn, p.stream>>>(
-        f, reinterpret_cast<float2 *>(t.d_bc), p.ncells, p.nv, t.trials, static_cast<const uint2 *>(t.d_idx), t.d_b,
-        per, list, count, p.status);
-    count_launch();
-    if (cudaGetLastError() != cudaSuccess) return DVM_ECUDA;
+    BcLaunch L;
+    int rc = bc_plan(t, p.nv, p.ncells, L);
+    if (!rc)
+        rc = bc_launch(L, t, f, reinterpret_cast<float2 *>(t.d_bc), p.ncells, p.nv, list, count, p.stream,
+                       p.status);
+    if (rc) return rc;
     k_hs_corr<<<(unsigned)p.ncells, CT, 0, p.stream>>>(f, reinterpret_cast<const float2 *>(t.d_bc), t.d_xi,
                                                       t.d_jpk, t.hh, p.dV, p.mom_out, p.nv,
                                                       make_int3(t.half[0], t.half[1], t.half[2]),
@@ -566,32 +588,18 @@ int launch_hs_collide_noalloc(HsTables &t, const StepParams &p, float *f, const 
     const size_t need_bc = (size_t)p.ncells * p.nv * 2 * sizeof(float);
     if (need_bc + (size_t)p.ncells * 5 * sizeof(double) > NOALLOC_BYTES) return DVM_EINVAL;
     // every check comes before the first launch, so that a refusal queues no work
-    const int tpn = t.trials / HE, npc = HT / tpn;
-    const int chunks = (p.nv + npc - 1) / npc;
-    const size_t dyn = 2 * (size_t)p.nv * sizeof(float);
-    if (dyn > 200 * 1024) return DVM_ENOTIMPL;
-    if (cudaFuncSetAttribute(k_hs_bc, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) != cudaSuccess)
-        return DVM_ECUDA;
-    int dev = 0, nsm = 0, occ = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_hs_bc, HT, dyn) != cudaSuccess || occ < 1)
-        return DVM_ENOTIMPL;
+    BcLaunch L;
+    int rc = bc_plan(t, p.nv, p.ncells, L);
+    if (rc) return rc;
     void *base = nullptr;
-    int rc = noalloc_scratch(&base);
+    rc = noalloc_scratch(&base);
     if (rc) return rc;
     float *bc = static_cast<float *>(base);
     double *mom = reinterpret_cast<double *>(static_cast<unsigned char *>(base) + need_bc);
     rc = launch_moments(DVM_F32, f, p.ncells, p.nv, xi, dV, mom, p.stream);
     if (rc) return rc;
-    int64_t splits = hs_splits(chunks, nsm * occ, p.ncells);
-    const int64_t per = (p.ncells + splits - 1) / splits;
-    splits = (p.ncells + per - 1) / per;
-    k_hs_bc<<<dim3((unsigned)chunks, (unsigned)splits), HT, dyn, p.stream>>>(
-        f, reinterpret_cast<float2 *>(bc), p.ncells, p.nv, t.trials, static_cast<const uint2 *>(t.d_idx), t.d_b,
-        per, nullptr, nullptr, p.status);
-    count_launch();
-    if (cudaGetLastError() != cudaSuccess) return DVM_ECUDA;
+    rc = bc_launch(L, t, f, reinterpret_cast<float2 *>(bc), p.ncells, p.nv, nullptr, nullptr, p.stream, p.status);
+    if (rc) return rc;
     k_hs_corr<<<(unsigned)p.ncells, CT, 0, p.stream>>>(f, reinterpret_cast<const float2 *>(bc), t.d_xi, t.d_jpk,
                                                       t.hh, dV, mom, p.nv, make_int3(t.half[0], t.half[1], t.half[2]),
                                                       (float)(dt / kn), nullptr, nullptr, nullptr, nullptr, p.status);
