@@ -10,7 +10,8 @@ kernel, the same metric end to end through the C ABI with host buffers,
 the FP64 CPU oracle on the host cores (a bounded sample of the workload),
 and the SM clocks seen during the timed region.  Further legs (each can be
 skipped): the FP32 fields against the oracle, BF16 storage, the same flow at
-Kn 0.1 and 1, the hard-sphere box with its gather roofline, the learned
+Kn 0.1 and 1, the hard-sphere step with its gather roofline (the 16^3 box
+and the 253k-cell 24^3 sphere flow), the learned
 collision operator against the plain one from a developed flow, and the
 lattice Boltzmann flows.
 
@@ -68,6 +69,8 @@ def parse():
     ap.add_argument("--no-hs", action="store_true", help="skip the hard-sphere box leg (c4_hs_bimodal)")
     ap.add_argument("--hs-only", action="store_true", help="run only the hard-sphere box leg")
     ap.add_argument("--hs-steps", type=int, default=3)
+    ap.add_argument("--hs-config", choices=["c4_hs_bimodal", "c5_sphere_m3_hs"], default="c4_hs_bimodal",
+                    help="the workload of --hs-only")
     ap.add_argument("--no-bf16", action="store_true", help="skip the BF16-storage leg")
     ap.add_argument("--no-kn-sweep", action="store_true", help="skip the Kn = 0.1 and 1 steps of the main flow")
     ap.add_argument("--bf16-steps", type=int, default=10)
@@ -429,27 +432,32 @@ def oracle_field_errors(cfg_name, prec, steps, fetch):
             "workload": cfg_name}
 
 
-def hs_leg(args):
-    """The hard-sphere collision step (Eqs. 3-6) on the bimodal periodic box
-    (16,584 cells x 16^3 velocities, 128 trials per node, Kn 0.02), FP32:
-    --hs-steps steps timed with CUDA events, then one more with phase events
-    for the split between transport and the collision kernels.  Roofline of
-    the collision: its shared-memory gathers, three 4-byte loads per trial
-    (f_gamma, f_l, f_m), against the derived peak of one load per lane per SM
-    clock (152 SMs x 32 lanes), over the collision phase's time (B, C and the
-    correction; an upper bound on the gather kernel's own time)."""
+def hs_leg(args, name="c4_hs_bimodal"):
+    """The hard-sphere collision step (Eqs. 3-6), FP32, 128 trials per node:
+    on the bimodal periodic box (c4_hs_bimodal: 16,584 cells x 16^3
+    velocities, Kn 0.02), or on the Mach-3 sphere flow (c5_sphere_m3_hs:
+    253,360 cells x 24^3, Kn 0.003) from a two-beam state perturbed by up to
+    5% per cell.  --hs-steps steps timed with CUDA events, then one more with
+    phase events for the split between transport and the collision kernels.
+    Roofline of the collision: its shared-memory gathers, three 4-byte loads
+    per trial (f_gamma, f_l, f_m), against the derived peak of one load per
+    lane per SM clock (152 SMs x 32 lanes), over the collision phase's time
+    (B, C and the correction; an upper bound on the gather kernel's own
+    time)."""
     import numpy as np
     import torch
     import paper_1503_00707_gb300 as D
-    c = W.CONFIGS["c4_hs_bimodal"]
+    box = name == "c4_hs_bimodal"
+    c = dict(W.CONFIGS[name]) if box else dict(W.CONFIGS[name], init="bimodal_near")
     st = torch.cuda.Stream()
     s = D.solver_from_config(c, D.F32, D.COLL_HS, stream=st)
     xyz, _ = s.centres()
     s.init_maxwellian(*W.initial_state(c, xyz))
     s.set_collision_tables(c["trials"], W.SEED)
-    # the bimodal start has max(P B) ~ 290 in the far tails: a sixteenth of
-    # the CFL step keeps dt/Kn max(P B) below 1
-    dt = s.dt_cfl(c["cfl"]) / 16
+    # the bimodal box has max(P B) ~ 290 in the far tails: a sixteenth of
+    # the CFL step keeps dt/Kn max(P B) below 1; the perturbed two-beam flow
+    # (max(P B) ~ 130) takes dt = Kn/1000
+    dt = s.dt_cfl(c["cfl"]) / 16 if box else min(s.dt_cfl(c["cfl"]), c["kn"] / 1000)
     s.step(2, dt)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -472,7 +480,7 @@ def hs_leg(args):
     achieved = gathers / (split[1] / 1e3)
     peak = 152 * 32 * _sm_clock_hz()
     cpu = None
-    if not args.no_cpu_baseline:
+    if box and not args.no_cpu_baseline:
         import oracle as O
         cs = dict(c)
         cs.update(base_level=3, max_level=4)
@@ -487,10 +495,16 @@ def hs_leg(args):
         cpu = {"value": o.ncells * o.nv / el, "unit": UNIT, "cores": O.threads(), "kind": "oracle",
                "sample": "1 step of the same box on its level-3/4 tree (%d cells x %d velocities), FP64"
                          % (o.ncells, o.nv)}
-    return {
-        "workload": "c4_hs_bimodal: 3D periodic octree level 4 + ball r=0.42 at level 5 (%d cells), 16^3 "
+    if box:
+        workload = ("c4_hs_bimodal: 3D periodic octree level 4 + ball r=0.42 at level 5 (%d cells), 16^3 "
                     "velocities on [-6,6]^3, hard-sphere integral with %d trials per node, Kn=0.02, seeded "
-                    "bimodal start, FP32" % (nc, c["trials"]),
+                    "bimodal start, FP32" % (nc, c["trials"]))
+    else:
+        workload = ("c5_sphere_m3_hs: Mach-3 sphere flow on levels 4-8 (%d cells), 24^3 velocities on [-8,8]^3, "
+                    "hard-sphere integral with %d trials per node, Kn=0.003, dt=Kn/1000, from a two-beam state "
+                    "perturbed by up to 5%% per cell, FP32" % (nc, c["trials"]))
+    return {
+        "workload": workload,
         "value": nc * nv / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "steps": args.hs_steps,
         "split_ms_per_step": {"transport": split[0], "collision": split[1]},
         "roofline": {"bound": "smem", "achieved": achieved, "peak": peak, "unit": "loads/s",
@@ -845,9 +859,10 @@ def run_ours(args):
     lbm = None
     if rank == 0 and not args.no_lbm:
         lbm = lbm_leg(args)
-    hs = None
+    hs = hs_flow = None
     if rank == 0 and not args.no_hs:
         hs = hs_leg(args)
+        hs_flow = hs_leg(args, "c5_sphere_m3_hs")
     bf16 = None
     if rank == 0 and not args.no_bf16 and args.precision == "f32":
         bf16 = bf16_leg(args)
@@ -866,7 +881,7 @@ def run_ours(args):
                        "l2": "inputs larger than L2 (f is %.1f GB)" % f_gb},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
             "field_rel_linf_vs_oracle": field_err,
-            "learned_vs_plain": learned, "lbm": lbm, "hs_box": hs, "bf16": bf16, "kn_sweep": kn_sweep,
+            "learned_vs_plain": learned, "lbm": lbm, "hs_box": hs, "hs_flow": hs_flow, "bf16": bf16, "kn_sweep": kn_sweep,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -890,7 +905,7 @@ def main():
         from paper_1503_00707_gb300 import _build
         _build.build()
         torch.cuda.set_device(0)
-        print(json.dumps({"hs": hs_leg(args)}), flush=True)
+        print(json.dumps({"hs": hs_leg(args, args.hs_config)}), flush=True)
         return 0
     if args.learned_only:
         import torch
