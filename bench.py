@@ -828,10 +828,10 @@ def run_ours(args):
 
     f_gb = s.f_bytes() / 1e9
     s.close()
-    # the oracle's CPU legs run after the e2e leg, so that its 56 GB pinned
-    # host buffer is allocated before the oracle's working sets have been
-    # through host memory (measured on one box: e2e 4.5e10 cell-updates/s
-    # this way, 2.3e10-2.5e10 with the oracle first)
+    # the oracle's CPU legs run after the e2e leg, so that the 56 GB pinned
+    # host buffer is allocated before the oracle's working sets pass through
+    # host memory (the e2e rate still varies from box to box with the host
+    # link: 2.3e10-4.5e10 cell-updates/s in full runs, in either order)
     cpu = cpu_leg() if rank == 0 and not args.no_cpu_baseline else None
     # the same flow at the other ends of the Kn range of the Mach-5 runs
     # (0.01-1): the step does the same work, and nu dt stays below 1
