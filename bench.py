@@ -69,8 +69,8 @@ def parse():
     ap.add_argument("--no-hs", action="store_true", help="skip the hard-sphere box leg (c4_hs_bimodal)")
     ap.add_argument("--hs-only", action="store_true", help="run only the hard-sphere box leg")
     ap.add_argument("--hs-steps", type=int, default=3)
-    ap.add_argument("--hs-config", choices=["c4_hs_bimodal", "c5_sphere_m3_hs"], default="c4_hs_bimodal",
-                    help="the workload of --hs-only")
+    ap.add_argument("--hs-config", choices=["c4_hs_bimodal", "c5_sphere_m3_hs", "c5_sphere_m3_hs_small"],
+                    default="c4_hs_bimodal", help="the workload of --hs-only")
     ap.add_argument("--no-bf16", action="store_true", help="skip the BF16-storage leg")
     ap.add_argument("--no-kn-sweep", action="store_true", help="skip the Kn = 0.1 and 1 steps of the main flow")
     ap.add_argument("--bf16-steps", type=int, default=10)
@@ -500,9 +500,9 @@ def hs_leg(args, name="c4_hs_bimodal"):
                     "velocities on [-6,6]^3, hard-sphere integral with %d trials per node, Kn=0.02, seeded "
                     "bimodal start, FP32" % (nc, c["trials"]))
     else:
-        workload = ("c5_sphere_m3_hs: Mach-3 sphere flow on levels 4-8 (%d cells), 24^3 velocities on [-8,8]^3, "
+        workload = ("%s: Mach-3 sphere flow on levels %d-%d (%d cells), 24^3 velocities on [-8,8]^3, "
                     "hard-sphere integral with %d trials per node, Kn=0.003, dt=Kn/1000, from a two-beam state "
-                    "perturbed by up to 5%% per cell, FP32" % (nc, c["trials"]))
+                    "perturbed by up to 5%% per cell, FP32" % (name, c["base_level"], c["max_level"], nc, c["trials"]))
     return {
         "workload": workload,
         "value": nc * nv / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "steps": args.hs_steps,

@@ -148,15 +148,18 @@ def test_mach3_learned_full_size_sampled_cells():
         s.close()
 
 
-def test_row_gather_equals_full_copy():
-    """dvm_get_f_rows gives exactly the rows of dvm_get_f, repeats and any
-    order allowed; an index out of range is refused (DVM_EINVAL)."""
-    c = dict(W.CONFIGS["c3_sphere_m5_small"], init="bimodal")
-    s, _ = pair(c, collision=D.COLL_BGK)
+@pytest.mark.parametrize("name,prec", [("c3_sphere_m5_small", "f32"), ("c3_sphere_m5_small", "bf16"),
+                                       ("c1_2d_bump", "f64")])
+def test_row_gather_equals_full_copy(name, prec):
+    """dvm_get_f_rows gives exactly the rows of dvm_get_f (each storage
+    precision converted the same way), repeats and any order allowed; an
+    index out of range is refused (DVM_EINVAL)."""
+    c = dict(W.CONFIGS[name], init="bimodal")
+    s, _ = pair(c, precision=prec, collision=D.COLL_BGK)
     try:
         s.step(1, s.dt_cfl(0.4))
         f = s.get_f()
-        cells = np.array([s.ncells - 1, 0, 17, 17, 5000, 3], dtype=np.int64)
+        cells = np.array([s.ncells - 1, 0, 17, 17, s.ncells // 2, 3], dtype=np.int64)
         assert np.array_equal(s.get_f_rows(cells), f[cells])
         assert s.get_f_rows(np.zeros(0, dtype=np.int64)).shape == (0, s.nv)
         with pytest.raises(D.DvmError) as e:
