@@ -165,7 +165,10 @@ constexpr int NSUM = 20;  // 15 distinct entries of the moment matrix, 5 gain mo
 // residual of the exact sums.  That residual, sum_i psi_r I_i dV with
 // psi = (1, xi, |xi|^2), goes to res (may be null).  Then I_i is evaluated
 // in FP32 with the FP32 copy of d and f <- f + dt/Kn I (or I to q_out).
-__global__ void __launch_bounds__(CT, 2)
+// three CTAs per SM (80 registers): other cells' sums overlap one CTA's
+// serial solve (C4: 7.56 -> 7.29 ms per step; two or four CTAs were slower on
+// one of the 16^3 and 24^3 grids)
+__global__ void __launch_bounds__(CT, 3)
     k_hs_corr(float *__restrict__ f, const float2 *__restrict__ bc, const float *__restrict__ xi3,
               const uint32_t *__restrict__ jpk, double hh, double dV, const double *__restrict__ mom, int nv,
               int3 half, float dtkn, const int32_t *__restrict__ list, const int *__restrict__ count,
