@@ -543,7 +543,8 @@ def bf16_leg(args):
     out = {"workload": workload_desc(args.config, cfg, nc, nv, "bf16"), "value": nc * nv / (ms / 1e3),
            "unit": UNIT, "ms_per_step": ms, "steps": args.bf16_steps,
            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                        "peak_source": peak_kind, "algorithmic_bytes_per_update": 4, "traffic": None}}
+                        "peak_source": peak_kind, "algorithmic_bytes_per_update": 4,
+                        "traffic": _profiled_traffic("k_step.cu", "k_step_bgk_%s_bf16" % args.config)}}
     if not args.no_cpu_baseline:
         out["field_rel_linf_vs_oracle"] = oracle_field_errors(CPU_SAMPLE_CONFIG, "bf16", 2, lambda q: q.moments())
     return out
