@@ -161,6 +161,9 @@ def test_row_gather_equals_full_copy(name, prec):
         f = s.get_f()
         cells = np.array([s.ncells - 1, 0, 17, 17, s.ncells // 2, 3], dtype=np.int64)
         assert np.array_equal(s.get_f_rows(cells), f[cells])
+        # more rows than one device chunk holds (2^24 values: 1,213 rows at 24^3)
+        many = np.random.default_rng(3).integers(0, s.ncells, size=min(3000, 3 * s.ncells))
+        assert np.array_equal(s.get_f_rows(many), f[many])
         assert s.get_f_rows(np.zeros(0, dtype=np.int64)).shape == (0, s.nv)
         with pytest.raises(D.DvmError) as e:
             s.get_f_rows(np.array([0, s.ncells]))
