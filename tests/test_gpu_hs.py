@@ -79,6 +79,29 @@ def test_homogeneous_bimodal_step(M):
     assert rel_linf(fs, f0) > 1e-5
 
 
+@pytest.mark.parametrize("M", [32, 64])
+def test_24_cubed_grid_few_trials(M):
+    """The 24^3 grid runs the 512-thread gather CTAs; with 32 and 64 trials a
+    node has one or two lanes (128 and 256 nodes per CTA).  A periodic box of
+    8 cells from per-cell two-beam states, two steps against the oracle."""
+    c = _homog_cfg(n=24, vmax=8.0, base=1)
+    s, o = pair(c)
+    s.set_collision_tables(M, 11)
+    o.hs_tables(M, 11)
+    # the random two-beam start reaches max(P B) of several thousand in the
+    # far tails of [-8,8]^3 with few trials (1e-5 was refused at 32 trials):
+    # dt/Kn = 1.25e-4
+    dt = 2.5e-6
+    f0 = o.get_f()
+    s.step(2, dt)
+    o.step(2, dt, O.COLL_HS, c["kn"])
+    fo = o.get_f()
+    assert rel_linf(s.get_f(), fo) < 2e-5
+    assert rel_linf(fo, f0) > 1e-4  # the two steps moved f well beyond the bar
+    err = field_errors(s.moments(), o.moments())
+    assert max(err.values()) < 1e-5, err
+
+
 def test_c4_hs_bimodal_two_steps():
     c = W.CONFIGS["c4_hs_bimodal"]
     s, o = pair(c)
