@@ -53,6 +53,12 @@ MUTANTS = [
     ("gain term with one post-collision partner twice", "sc += p->hs_b[t] * f[p->hs_l[t]] * f[p->hs_m[t]];",
      "sc += p->hs_b[t] * f[p->hs_l[t]] * f[p->hs_l[t]];",
      "tests/test_oracle_collision.py::test_hs_relaxation_approaches_the_maxwellian_as_trials_grow"),
+    ("selected-cell inputs miss the plus-side neighbours", "t[m++] = p->cell_of_leaf[p->fp[q]];",
+     "t[m++] = p->cell_of_leaf[p->fm[q]];",
+     "tests/test_oracle_sampled.py::test_inputs_hold_cells_and_neighbours"),
+    ("selected-cell row lookup off by one", "if (t->cells[mid] < k) lo = mid + 1;",
+     "if (t->cells[mid] <= k) lo = mid + 1;",
+     "tests/test_oracle_sampled.py::test_selected_cells_equal_full_step"),
     ("velocity nodes off the cell midpoints", "xi[3 * v + d] = lo[d] + ((double)kk[d] + 0.5) * h[d];",
      "xi[3 * v + d] = lo[d] + ((double)kk[d] + 0.45) * h[d];",
      "tests/test_oracle_transport.py::test_density_of_a_truncated_maxwellian_closed_form"),
