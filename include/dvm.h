@@ -250,8 +250,10 @@ int dvm_set_f(dvm_ctx *ctx, const double *f, int64_t count);
  * indices in the dvm_get_f / dvm_cell_centres order, repeats allowed).  The
  * rows are gathered and converted on the device, so only n * nv values cross
  * the host link: this inspects trees whose whole f is too large to copy.
- * Device scratch of at most about 16.8M elements is allocated for the call
- * and freed before it returns; the call synchronises the context's stream.
+ * Device scratch is allocated for the call and freed before it returns: the
+ * row indices, and up to 2^24 values of f (rows are copied in chunks of at
+ * most that many values) in the storage precision and again in FP64; the
+ * call synchronises the context's stream.
  * DVM_EINVAL for an index outside [0, ncells) (nothing is copied),
  * DVM_ESTATE before f is set, DVM_ENOMEM if the scratch cannot be had. */
 int dvm_get_f_rows(dvm_ctx *ctx, int64_t n, const int64_t *cells, double *out);
